@@ -1,0 +1,412 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+printed in the paper, definitions (moments by summation), a second printed
+form of the same quantity, conservation laws, an independently written
+uniform-grid cascaded LBM, symmetry, and analytic flow solutions.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import goc_inputs as gi
+import oracle
+from oracle.metric import map_metric, map_position
+
+E1 = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+E2 = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+MX = [0, 1, 0, 2, 0, 1, 2, 1, 2]
+MY = [0, 0, 1, 0, 2, 1, 1, 2, 2]
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _periodic_spec(nx=6, ny=5, **kw):
+    spec = dict(nx=nx, ny=ny, map1={"kind": "sine", "a": 0.3}, map2={"kind": "sine", "a": -0.2},
+                walls={"W": None, "E": None, "S": None, "N": None}, tau=0.8)
+    spec.update(kw)
+    return spec
+
+
+# ---------------------------------------------------------------- metric ---
+@pytest.mark.parametrize("kind,kw", [("tanh2", {"beta": 1.5}), ("tanh2", {"beta": 3.0}),
+                                     ("sine", {"a": 0.4}), ("roberts", {"gamma": 1.06, "alpha": 0.5})])
+def test_metric_matches_finite_differences_of_the_map(kind, kw):
+    """h = dx/dxi (Eq. metricfactor) and theta = h'/h^2 (Eq. curvaturematrix)
+    against centred finite differences of the map itself (Sec. 6)."""
+    n = 64
+    xi = np.linspace(0.7, n - 0.7, 37)
+    eps = 1e-4
+    h_fd = (map_position(kind, n, xi + eps, **kw) - map_position(kind, n, xi - eps, **kw)) / (2 * eps)
+    h, th = map_metric(kind, n, xi, **kw)
+    np.testing.assert_allclose(h, h_fd, rtol=1e-7)
+    hp, _ = map_metric(kind, n, xi + eps, **kw)
+    hm, _ = map_metric(kind, n, xi - eps, **kw)
+    np.testing.assert_allclose(th, (hp - hm) / (2 * eps) / h ** 2, rtol=1e-6, atol=1e-12)
+
+
+def test_tanh_map_spans_the_domain_and_cs_rule():
+    """Walls at y = 0 and y = N (Eq. hypertanh_transformation1) and
+    c_s^2 = q^2/3 with q the smallest metric factor (Eq. GOC-LBE_CFL)."""
+    n = 64
+    assert map_position("tanh2", n, np.array([0.0]), beta=1.5)[0] == pytest.approx(0.0, abs=1e-12)
+    assert map_position("tanh2", n, np.array([float(n)]), beta=1.5)[0] == pytest.approx(n, rel=1e-14)
+    spec = gi.cfg1_poiseuille().lattice_spec(1.0)
+    m = oracle.build_metric(spec)
+    h_first = 1.5 / math.tanh(1.5) / math.cosh(1.5 * (1 / 64 - 1)) ** 2
+    assert m.q() == pytest.approx(min(1.0, h_first), rel=1e-14)
+    assert m.cs2() == pytest.approx(m.q() ** 2 / 3, rel=1e-15)
+
+
+# ----------------------------------------------------------- moment algebra -
+def test_raw_moment_matrix_is_the_monomial_basis_and_its_printed_inverse():
+    """P (Eq. Q-momentbasis) by its definition; P^-1 equals the printed
+    expansions of App. E Step 5 / App. C.1 (golden fixture)."""
+    o = oracle.Oracle(_periodic_spec())
+    P, Pi = o.p_matrices()
+    for k in range(9):
+        np.testing.assert_array_equal(P[k], E1 ** MX[k] * E2 ** MY[k])
+    printed = np.loadtxt(os.path.join(GOLDEN, "p_inverse_appE_step5.txt"))
+    np.testing.assert_allclose(Pi, printed, atol=1e-15)
+
+
+def test_frame_matrix_gives_central_moments_by_definition():
+    """F(U) m = central moments sum f (e1-U1)^m (e2-U2)^n (Eq. 9B, Eq. Fmatrix),
+    and F(U)^-1 = F(-U) (stated below Eq. Fmatrix)."""
+    o = oracle.Oracle(_periodic_spec())
+    rng = np.random.default_rng(1)
+    P, _ = o.p_matrices()
+    for _ in range(20):
+        f = rng.uniform(0.01, 1.0, 9)
+        u, v = rng.uniform(-0.3, 0.3, 2)
+        Fm = o.frame_matrix(u, v)
+        central = np.array([np.sum(f * (E1 - u) ** MX[k] * (E2 - v) ** MY[k]) for k in range(9)])
+        np.testing.assert_allclose(Fm @ (P @ f), central, rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(Fm @ o.frame_matrix(-u, v * -1), np.eye(9), atol=1e-14)
+
+
+def test_central_equilibria_are_the_binomial_transform_of_the_raw_ones():
+    """Eq. cmequilibriaGOC is the binomial transform of Eq. GOCmomentequilibria
+    up to third order (Appendix E.1); k22^eq = c_s^4 rho by choice.  This also
+    fixes the sign of q21, q12: the printed ones fail the same check."""
+    o = oracle.Oracle(_periodic_spec())
+    op = oracle.Oracle(_periodic_spec(), q3_printed=True)
+    _, Pi = o.p_matrices()
+    rng = np.random.default_rng(2)
+    for _ in range(30):
+        rho = rng.uniform(0.8, 1.2)
+        u, v = rng.uniform(-0.2, 0.2, 2)
+        h1, h2 = rng.uniform(0.2, 3.0, 2)
+        feq = Pi @ o.raw_equilibria(rho, u, v, h1, h2)
+        central = np.array([np.sum(feq * (E1 - u) ** MX[k] * (E2 - v) ** MY[k]) for k in range(9)])
+        keq = o.central_equilibria(rho, u, v, h1, h2)
+        np.testing.assert_allclose(keq[:8], central[:8], rtol=1e-12, atol=1e-15)
+        assert keq[8] == pytest.approx(o.par["cs2"] ** 2 * rho, rel=1e-14)
+        bad = op.central_equilibria(rho, u, v, h1, h2)
+        assert abs(bad[6] - central[6]) > 1e-6 * abs(u * u * v) * abs(h1 - 1) ** 2 * abs(h2 - 1) or abs(u * v) < 1e-3
+
+
+def _E3_E4_form(par, rho, U1, U2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2):
+    """n3^eq(1), n4^eq(1) from Eq. 79a/79b with the deviations E3 (Eq. 63b) and
+    E4 (Eq. 66b); an independent printed form of Eqs. 82-85."""
+    cs2, nu, ze = par["cs2"], par["nu"], par["zeta"]
+    w3, w4 = par["omega"][3], par["omega"][4]
+    tc11 = rho * (ze + nu) * U2 * t12 + rho * (ze - nu) * U1 * t21
+    tc22 = rho * (ze + nu) * U1 * t21 + rho * (ze - nu) * U2 * t12
+    E3 = (1 / w3) * ((2 * cs2 - h2 + (3 * U1 ** 2 + cs2) * h2 / h1 ** 2) * rho * dU1
+                     + (2 * cs2 - h1 + (3 * U2 ** 2 + cs2) * h1 / h2 ** 2) * rho * dU2
+                     + ((3 * cs2 - U1 ** 2) * h2 / h1 ** 2 - h2 - U2 ** 2 / h2) * U1 * dr1
+                     + ((3 * cs2 - U2 ** 2) * h1 / h2 ** 2 - h1 - U1 ** 2 / h1) * U2 * dr2
+                     - 2 * rho * U1 * (U1 ** 2 + cs2) * h2 / h1 * t11
+                     - 2 * rho * U2 * (U2 ** 2 + cs2) * h1 / h2 * t22
+                     + rho * U1 * (h2 / h1 * (3 * cs2 + U1 ** 2) + 2 * cs2 * h1 / h2 - h1 * h2) * t21
+                     + rho * U2 * (h1 / h2 * (3 * cs2 + U2 ** 2) + 2 * cs2 * h2 / h1 - h1 * h2) * t12)
+    E4 = (1 / w4) * ((2 * cs2 - h2 + (3 * U1 ** 2 + cs2) * h2 / h1 ** 2) * rho * dU1
+                     + (-2 * cs2 + h1 - (3 * U2 ** 2 + cs2) * h1 / h2 ** 2) * rho * dU2
+                     + ((3 * cs2 - U1 ** 2) * h2 / h1 ** 2 - h2 + U2 ** 2 / h2) * U1 * dr1
+                     + (-(3 * cs2 - U2 ** 2) * h1 / h2 ** 2 + h1 - U1 ** 2 / h1) * U2 * dr2
+                     - 2 * rho * U1 * (U1 ** 2 + cs2) * h2 / h1 * t11
+                     + 2 * rho * U2 * (U2 ** 2 + cs2) * h1 / h2 * t22
+                     + rho * U1 * ((3 * cs2 + U1 ** 2) * h2 / h1 - 2 * cs2 * h1 / h2 - h1 * h2) * t21
+                     + rho * U2 * (-(3 * cs2 + U2 ** 2) * h1 / h2 + 2 * cs2 * h2 / h1 + h1 * h2) * t12)
+    a11 = rho * (nu + ze) * h2 / h1 ** 2 * dU1 + rho * (ze - nu) / h1 * dU2 + h2 / h1 * tc11
+    a22 = rho * (nu + ze) * h1 / h2 ** 2 * dU2 + rho * (ze - nu) / h2 * dU1 + h1 / h2 * tc22
+    n3 = 2 * rho * ze * dU1 + 2 * rho * ze * dU2 - a11 - a22 - (1 - w3 / 2) * E3
+    n4 = 2 * rho * nu * dU1 - 2 * rho * nu * dU2 - a11 + a22 - (1 - w4 / 2) * E4
+    return n3, n4
+
+
+def test_correction_coefficients_match_the_E3_E4_form():
+    """Eqs. 82-85 (D_{3,k}, D_{4,k}, C3, C4) agree with Eq. 79 + Eqs. 63b/66b on
+    random inputs, curvature terms included (C4 read with h2/h1 at theta21 and
+    h1/h2 at theta12, as E4 and the SRT copy print them)."""
+    rng = np.random.default_rng(3)
+    for tz in (1.0, 0.7, 1.3):
+        o = oracle.Oracle(_periodic_spec(tau_zeta=tz, tau=0.9))
+        for _ in range(40):
+            args = [rng.uniform(0.8, 1.2), *rng.uniform(-0.1, 0.1, 2), *rng.uniform(0.3, 2.5, 2),
+                    *rng.uniform(-0.05, 0.05, 4), *rng.uniform(-0.02, 0.02, 4)]
+            n3, n4 = o.corrections(*args)
+            r3, r4 = _E3_E4_form(o.par, *args)
+            scale = max(abs(r3), abs(r4), 1e-12)
+            assert abs(n3 - r3) < 1e-12 * scale
+            assert abs(n4 - r4) < 1e-12 * scale
+
+
+# ------------------------------------------------------------- conservation -
+def test_mass_is_conserved_on_a_stretched_periodic_grid():
+    """sum f = sum h1 h2 rho is a collision invariant (sigma_00 = 0, Eq.
+    GOCmomentsources) and streaming moves it around: drift <= 1e-12."""
+    u1, u2 = gi.random_periodic_fields(16, 12, seed=5, amp=0.05)
+    spec = _periodic_spec(16, 12, init={"u1": u1, "u2": u2}, fext=(1e-5, -2e-5))
+    o = oracle.Oracle(spec)
+    m0 = o.state()[0].sum()
+    o.step(3000)
+    rho, *_ = o.fields()
+    m1 = (rho * o.metric.h1 * o.metric.h2).sum()
+    assert abs(m1 - m0) / m0 < 1e-12
+
+
+def test_mass_is_conserved_with_bounce_back_and_a_moving_lid():
+    p = gi.cfg2_cavity(n=12, beta=1.2, Re=50.0, u_lid=0.03)
+    o = oracle.Oracle(p.lattice_spec(oracle.build_metric(p.lattice_spec(1.0)).cs2()))
+    m0 = o.state()[0].sum()
+    o.step(2000)
+    assert abs(o.state()[0].sum() - m0) / m0 < 1e-12
+
+
+def test_momentum_grows_by_the_effective_force():
+    """With omega1 = omega2 = 1 on a periodic grid, sum h2 rho U1 increases per
+    step by exactly sum F1 of that step (the trapezoidal shift of Eq.
+    GOChydrodynamicfields with the lagged force)."""
+    u1, u2 = gi.random_periodic_fields(10, 8, seed=9, amp=0.03)
+    spec = _periodic_spec(10, 8, init={"u1": u1, "u2": u2}, fext=(3e-5, 1e-5))
+    o = oracle.Oracle(spec)
+    h1, h2 = o.metric.h1, o.metric.h2
+    for _ in range(5):
+        rho, U1, U2, *_ = o.fields()
+        p1, p2 = (h2 * rho * U1).sum(), (h1 * rho * U2).sum()
+        o.step(1)
+        _, F1, F2, _ = o.state()
+        rho, U1, U2, *_ = o.fields()
+        assert (h2 * rho * U1).sum() - p1 == pytest.approx(F1.sum(), rel=1e-9, abs=1e-16)
+        assert (h1 * rho * U2).sum() - p2 == pytest.approx(F2.sum(), rel=1e-9, abs=1e-16)
+
+
+def test_first_order_rates_do_not_matter_for_a_constant_force():
+    """k10, k01 relax to their equilibria plus the force shift, so omega1 and
+    omega2 drop out of the update when the force does not change between
+    steps (App. E Step 3g with Eq. cmsourcesGOC)."""
+    u1, u2 = gi.random_periodic_fields(8, 8, seed=4, amp=0.05)
+    base = dict(nx=8, ny=8, map1={"kind": "uniform"}, map2={"kind": "uniform"},
+                walls={"W": None, "E": None, "S": None, "N": None}, tau=0.7,
+                fext=(1e-4, -5e-5), init={"u1": u1, "u2": u2})
+    out = []
+    for om in (1.0, 0.55):
+        o = oracle.Oracle(dict(base, omega_set={1: om, 2: 1.7 - om}))
+        f, F1, F2, g = o.state()
+        o.set_state(f, F1 + 1e-4, F2 - 5e-5, None)   # stored force = the constant force
+        o.step(40)
+        out.append(o.fields()[1:3])
+    scale = np.abs(out[0][0]).max()
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=0, atol=1e-13 * scale)
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=0, atol=1e-13 * scale)
+
+
+# ------------------------------------------------- reduction to uniform LBM -
+def _cascaded_uniform(f, Fext, omega, steps, walls=None, ulid=0.0):
+    """Independent uniform-grid central-moment D2Q9 LBM (c_s^2 = 1/3): central
+    moments by definition, equilibria (rho, 0, 0, rho/3, rho/3, 0, 0, 0, rho/9),
+    sources (0, F1, F2, 0...), relaxation of k2s/k2d, inverse by a linear solve,
+    streaming by np.roll (periodic) or half-way bounce-back with the textbook
+    moving-wall term 2 w rho e.u / c_s^2.  Lagged force: F = 0 in the first step."""
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    ny, nx = f.shape[1:]
+    Fprev = np.zeros(2)
+    f = f.copy()
+    for s in range(steps):
+        rho = f.sum(0)
+        u = ((f * E1[:, None, None]).sum(0) + 0.5 * Fprev[0]) / rho
+        v = ((f * E2[:, None, None]).sum(0) + 0.5 * Fprev[1]) / rho
+        ft = np.empty_like(f)
+        for j in range(ny):
+            for i in range(nx):
+                M = np.array([(E1 - u[j, i]) ** MX[k] * (E2 - v[j, i]) ** MY[k] for k in range(9)])
+                kc = M @ f[:, j, i]
+                r = rho[j, i]
+                keq = np.array([r, 0, 0, r / 3, r / 3, 0, 0, 0, r / 9])
+                sig = np.array([0, Fext[0], Fext[1], 0, 0, 0, 0, 0, 0.0])
+                n = kc.copy(); n[3], n[4] = kc[3] + kc[4], kc[3] - kc[4]
+                ne = keq.copy(); ne[3], ne[4] = keq[3] + keq[4], keq[3] - keq[4]
+                nt = n + omega * (ne - n) + (1 - omega / 2) * sig
+                kt = nt.copy(); kt[3], kt[4] = 0.5 * (nt[3] + nt[4]), 0.5 * (nt[3] - nt[4])
+                ft[:, j, i] = np.linalg.solve(M, kt)
+        Fprev = np.array(Fext, dtype=float)
+        if walls is None:
+            for a in range(9):
+                f[a] = np.roll(np.roll(ft[a], E2[a], axis=0), E1[a], axis=1)
+        else:
+            opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+            f = np.zeros_like(ft)
+            for j in range(ny):
+                for i in range(nx):
+                    for a in range(9):
+                        ti, tj = i + E1[a], j + E2[a]
+                        if 0 <= ti < nx and 0 <= tj < ny:
+                            f[a, tj, ti] = ft[a, j, i]
+                        else:
+                            b = opp[a]
+                            add = 0.0
+                            if tj >= ny:   # moving lid crossed: incoming b gets 2 w_b rho (e_b . u)/cs2
+                                add = 2 * w[b] * rho[j, i] * (E1[b] * ulid) * 3.0
+                            f[b, j, i] = ft[a, j, i] + add
+    return f
+
+
+def test_uniform_grid_reduces_to_the_cascaded_central_moment_lbm():
+    """With h1 = h2 = 1 (so c_s^2 = 1/3) and the cubic Galilean-invariance terms
+    dropped, the GOC scheme is the standard central-moment LBM (Sec. 4, last
+    paragraph; App. B (ii))."""
+    u1, u2 = gi.random_periodic_fields(6, 5, seed=11, amp=0.06)
+    spec = dict(nx=6, ny=5, map1={"kind": "uniform"}, map2={"kind": "uniform"},
+                walls={"W": None, "E": None, "S": None, "N": None}, tau=0.75, tau_zeta=0.9,
+                omega_free=0.8, fext=(2e-4, -1e-4), gi=0, init={"u1": u1, "u2": u2})
+    o = oracle.Oracle(spec)
+    assert o.par["cs2"] == pytest.approx(1 / 3, rel=1e-15)
+    f0 = o.state()[0]
+    o.step(25)
+    ref = _cascaded_uniform(f0, (2e-4, -1e-4), np.array(o.par["omega"]), 25)
+    np.testing.assert_allclose(o.state()[0], ref, rtol=0, atol=1e-14)
+
+
+def test_uniform_cavity_reduces_to_the_textbook_moving_wall():
+    """At h = 1 the moving-wall rule of Eq. 103 is the textbook momentum-
+    augmented bounce-back (noted below Eq. 103)."""
+    spec = dict(nx=5, ny=6, map1={"kind": "uniform"}, map2={"kind": "uniform"},
+                walls={"W": {"u": 0.0}, "E": {"u": 0.0}, "S": {"u": 0.0}, "N": {"u": 0.04}},
+                tau=0.8, gi=0, fext=(0.0, 0.0))
+    o = oracle.Oracle(spec)
+    f0 = o.state()[0]
+    o.step(20)
+    ref = _cascaded_uniform(f0, (0.0, 0.0), np.array(o.par["omega"]), 20, walls=True, ulid=0.04)
+    np.testing.assert_allclose(o.state()[0], ref, rtol=0, atol=1e-14)
+
+
+# ----------------------------------------------------------------- symmetry -
+def test_transposed_problem_gives_the_transposed_solution():
+    """Swapping xi1 and xi2 (maps, walls, force, initial field) must swap
+    U1 <-> U2 and transpose every field: pins the index symmetry of the
+    corrections (D3k, D4k, C3, C4 with n4 changing sign), forces and BCs."""
+    u1, u2 = gi.random_periodic_fields(9, 7, seed=2, amp=0.04)
+    a = dict(nx=9, ny=7, map1={"kind": "tanh2", "beta": 1.3}, map2={"kind": "sine", "a": 0.25},
+             walls={"W": {"u": 0.0}, "E": {"u": 0.02}, "S": None, "N": None}, tau=0.7, tau_zeta=0.8,
+             fext=(3e-5, 7e-5), init={"u1": u1 * 0.3, "u2": u2 * 0.3})
+    b = dict(nx=7, ny=9, map1={"kind": "sine", "a": 0.25}, map2={"kind": "tanh2", "beta": 1.3},
+             walls={"S": {"u": 0.0}, "N": {"u": 0.02}, "W": None, "E": None}, tau=0.7, tau_zeta=0.8,
+             fext=(7e-5, 3e-5), init={"u1": (u2 * 0.3).T, "u2": (u1 * 0.3).T})
+    oa, ob = oracle.Oracle(a), oracle.Oracle(b)
+    oa.step(200)
+    ob.step(200)
+    ra, ua, va, *_ = oa.fields()
+    rb, ub, vb, *_ = ob.fields()
+    np.testing.assert_allclose(ra, rb.T, rtol=1e-13)
+    np.testing.assert_allclose(ua, vb.T, atol=1e-14 * max(1.0, np.abs(ua).max()))
+    np.testing.assert_allclose(va, ub.T, atol=1e-14 * max(1.0, np.abs(va).max()))
+
+
+# ---------------------------------------------------------- analytic flows --
+def test_cfg1_poiseuille_follows_the_transient_analytic_series():
+    """cfg1 after 2000 steps from rest against the series solution of the
+    body-force channel (steady profile of Sec. 7.1 minus its decaying sine
+    modes)."""
+    p = gi.cfg1_poiseuille()
+    cs2 = oracle.build_metric(p.lattice_spec(1.0)).cs2()
+    spec = p.lattice_spec(cs2)
+    o = oracle.Oracle(spec, threads=4)
+    o.step(p.steps)
+    _, u1, u2, *_ = o.fields()
+    d = spec["derived"]
+    s = map_position("tanh2", p.ny, np.arange(p.ny) + 0.5, beta=1.5) / d["H"]
+    ut = 4 * d["U"] * s * (1 - s)
+    for n in range(1, 600, 2):
+        ut -= 32 * d["U"] / (n * math.pi) ** 3 * np.sin(n * math.pi * s) * math.exp(
+            -(n * math.pi) ** 2 * d["nu"] * p.steps / d["H"] ** 2)
+    for i in range(p.nx):
+        assert np.linalg.norm(u1[:, i] - ut) / np.linalg.norm(ut) < 2e-3
+
+
+def _steady_poiseuille_error(ny, beta=1.5, tau=0.8):
+    p = gi.Problem("poiseuille", 1, ny, {"kind": "uniform"}, {"kind": "tanh2", "beta": beta},
+                   {"Re": 10.0, "tau": tau})
+    cs2 = oracle.build_metric(p.lattice_spec(1.0)).cs2()
+    spec = p.lattice_spec(cs2)
+    d = spec["derived"]
+    s = map_position("tanh2", ny, np.arange(ny) + 0.5, beta=beta) / d["H"]
+    ua = 4 * d["U"] * s * (1 - s)
+    spec["init"] = {"u1": np.repeat(ua[:, None], 1, axis=1), "u2": 0.0}
+    o = oracle.Oracle(spec)
+    o.step(int(2.0 * d["H"] ** 2 / d["nu"]))
+    _, u1, *_ = o.fields()
+    return np.linalg.norm(u1[:, 0] - ua) / np.linalg.norm(ua)
+
+
+def test_steady_poiseuille_converges_at_second_order():
+    e = [_steady_poiseuille_error(n) for n in (16, 32, 64)]
+    orders = [math.log2(e[k] / e[k + 1]) for k in range(2)]
+    assert e[-1] < 2e-3
+    assert min(orders) > 1.8, (e, orders)
+
+
+def _tg_rate(n, a):
+    p = gi.taylor_green(n=n, a=a, u0=0.01, tau=0.8)
+    cs2 = oracle.build_metric(p.lattice_spec(1.0)).cs2()
+    o = oracle.Oracle(p.lattice_spec(cs2), threads=4)
+    m = o.metric
+    nu, k = o.par["nu"], 2 * math.pi / n
+    T = int(0.5 / (4 * nu * k * k))
+    ts, ks = [], []
+    for _ in range(5):
+        rho, u1, u2, *_ = o.fields()
+        ts.append(o.steps_done)
+        ks.append((rho * (u1 ** 2 + u2 ** 2) * m.h1 * m.h2).sum())
+        o.step(T // 4)
+    return -np.polyfit(ts[1:], np.log(ks[1:]), 1)[0] / (4 * nu * k * k)
+
+
+def test_taylor_green_decay_rate_uniform_and_stretched():
+    """Kinetic energy of the Taylor-Green vortex decays as exp(-4 nu k^2 t);
+    on the stretched grid this needs every correction term of Eqs. 82-85."""
+    assert _tg_rate(64, 0.0) == pytest.approx(1.0, abs=1e-3)
+    r32, r64 = _tg_rate(32, 0.3), _tg_rate(64, 0.3)
+    assert abs(r64 - 1.0) < 0.01
+    assert abs(r32 - 1.0) / abs(r64 - 1.0) > 3.0     # second order
+
+
+def _hartmann_error(ny, Ha=10.0, beta=1.5):
+    p = gi.Problem("hartmann", 1, ny, {"kind": "uniform"}, {"kind": "tanh2", "beta": beta},
+                   {"Ha": Ha, "Re": 10.0, "tau": 1.0, "tau_m": 1.0})
+    cs2 = oracle.build_metric(p.lattice_spec(1.0)).cs2()
+    spec = p.lattice_spec(cs2)
+    d = spec["derived"]
+    ys = map_position("tanh2", ny, np.arange(ny) + 0.5, beta=beta) / d["H"] - 1.0
+    Ur = d["H"] ** 2 * d["Fx"] / d["nu"]
+    Br = d["H"] ** 2 * d["Fx"] / math.sqrt(d["nu"] * d["eta"])
+    ua = Ur / (Ha * math.tanh(Ha)) * (1 - np.cosh(Ha * ys) / math.cosh(Ha))
+    ba = Br * (-ys / Ha + np.sinh(Ha * ys) / (Ha * math.tanh(Ha) * math.cosh(Ha)))
+    spec["init"] = {"u1": ua[:, None], "u2": 0.0}
+    o = oracle.Oracle(spec)
+    o.initialize(b1=ba[:, None], b2=d["B0"])
+    o.step(int(1.5 * d["H"] ** 2 / d["nu"]))
+    _, u1, _, b1, b2 = o.fields()
+    return (np.linalg.norm(u1[:, 0] - ua) / np.linalg.norm(ua),
+            np.linalg.norm(b1[:, 0] - ba) / np.linalg.norm(ba),
+            np.abs(b2 - d["B0"]).max() / d["B0"])
+
+
+def test_hartmann_flow_matches_the_analytic_profiles_at_second_order():
+    """Coupled NSE + MIE (App. G) against u_x(y), B_x(y) of Sec. 7.4."""
+    e32, e64 = _hartmann_error(32), _hartmann_error(64)
+    assert e64[0] < 1e-3 and e64[1] < 3e-3
+    assert e32[0] / e64[0] > 3.3 and e32[1] / e64[1] > 3.3
+    assert e64[2] < 2e-3
