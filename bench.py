@@ -1,0 +1,324 @@
+"""Benchmark of the GOC-LBM hot path (prints one JSON line).
+
+Default workload: the lid-driven cavity of 512 x 512 nodes, tanh clustering
+(beta = 2) toward all four walls, Re = 1000, lid velocity 0.05, D2Q9
+central-moment MRT, FP32 storage.  One benchmark step is one solve chunk of
+1000 fused time steps (graph-replayed launches of the step kernel) on data
+resident in HBM; 20 chunks are the full 20000-step job.  Between timed steps
+L2 is flushed by writing a 256 MiB buffer (the 23 MB lattice itself fits in
+the 126 MB L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--storage fp32|fp16|bf16] [--chunk T]
+
+Under torchrun every rank runs an independent replica (a single lattice is
+not sharded); value is the sum over ranks, timed as the maximum over ranks.
+--impl reference times the FP64 CPU oracle (the method as written) on this
+host on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import goc_inputs as gi  # noqa: E402
+
+METRIC = "MLUPS & % of HBM peak (FP32 vs FP16 store); batched p50/p99 solve latency"
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_cavity512_fp32.txt")
+KERNEL_SOURCES = ["paper_2607_15362_b300/csrc/goc_step.cuh", "paper_2607_15362_b300/csrc/goc_device.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    vals = dict(line.split("=", 1) for line in txt.splitlines() if "=" in line and not line.startswith("#"))
+    if vals.get("kernel_source_hash", "").strip() != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def setup_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2607_15362_b300 as goc
+
+    world, rank, local = setup_dist()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    prob = gi.cfg2_cavity()
+    _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
+    spec = prob.lattice_spec(cs2)
+    lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream)
+    nodes = prob.nodes
+    chunk = args.chunk
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_step():
+        lat.step(chunk)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)          # L2 flush between timed steps (not timed)
+            ev[k][0].record(stream)
+            one_step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(world)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    ms_total = allmax(world, sum(ms_steps))
+    ms_per_step = ms_total / args.steps
+    mlups = world * nodes * chunk * args.steps / (ms_total * 1e-3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    rho0 = np.ones((prob.ny, prob.nx))
+    zero = np.zeros((prob.ny, prob.nx))
+    outs = [np.empty((prob.ny, prob.nx)) for _ in range(5)]
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for k in range(args.steps):
+        lat.init_fields(rho=rho0, u1=zero, u2=zero)       # H2D of the step's input fields
+        one_step()
+        res = lat.moments()                                # D2H of the result fields
+        outs[0] = res[0]
+    torch.cuda.synchronize()
+    e_wall = allmax(world, time.perf_counter() - e0)
+    e2e = world * nodes * chunk * args.steps / e_wall / 1e6
+    h2d = 5 * nodes * 8
+    d2h = 5 * nodes * 8
+
+    # ---- roofline of the step kernel ----------------------------------------
+    peaks, src = measured_peaks()
+    bpn = lat.bytes_per_node
+    launch_s = ms_per_step * 1e-3 / chunk
+    achieved = bpn * nodes / launch_s / 1e9
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    traffic = profile_traffic()
+    clocks = clk.summary()
+
+    # ---- CPU baseline: the FP64 oracle on this host (rank 0 only) ----------
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(prob, spec, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "fp32" else f"f32 arithmetic, {args.storage} storage",
+            "data": "synthetic (lid-driven cavity from rest, seeded parameters)",
+            "config": {"workload": prob.name + f"_{args.storage}", "nodes": nodes,
+                       "lb_steps_per_bench_step": chunk, "map": "tanh beta=2 on both axes",
+                       "Re": 1000, "u_lid": round(spec["walls"]["N"]["u"], 6), "lid_mach": 0.087, "storage": args.storage,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single lattice",
+                       "l2": "flushed between timed steps (256 MiB write); lattice (23 MB) is L2-resident within a step"},
+            "e2e": {"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": src, "bytes_per_node": bpn,
+                         "kernel": "goc::step_kernel<float,false>", "launch_us": round(launch_s * 1e6, 3)},
+            "cpu_baseline": cpu,
+            "gpu_launches": args.steps * chunk,
+            "clocks": clocks,
+            "wall_s": round(wall, 3),
+        }
+        print(json.dumps(line))
+    lat.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(prob, spec_lib, budget_s: float = 15.0):
+    """FP64 oracle, as it stands, on this host's cores: a bounded number of
+    time steps of the same 512^2 cavity, scaled to MLUPS."""
+    import oracle
+    cores = os.cpu_count() or 1
+    cs2 = oracle.build_metric(prob.lattice_spec(1.0)).cs2()
+    o = oracle.Oracle(prob.lattice_spec(cs2), threads=cores)
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    n = max(1, min(200, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": round(prob.nodes * n / dt / 1e6, 3), "unit": "MLUPS", "cores": o.threads,
+            "kind": "oracle", "sample": f"{n} time steps of the {prob.nx}x{prob.ny} cavity after 1 warm-up step"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    prob = gi.cfg2_cavity()
+    cores = os.cpu_count() or 1
+    cs2 = oracle.build_metric(prob.lattice_spec(1.0)).cs2()
+    o = oracle.Oracle(prob.lattice_spec(cs2), threads=cores)
+    per_step = max(1, args.ref_steps_per_step)
+    for _ in range(args.warmup):
+        o.step(per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per_step)
+    dt = time.perf_counter() - t0
+    value = prob.nodes * per_step * args.steps / dt / 1e6
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": prob.name + "_fp32", "nodes": prob.nodes,
+                   "lb_steps_per_bench_step": per_step, "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": o.threads, "kind": "oracle",
+                         "sample": f"{per_step} time steps per benchmark step of the {prob.nx}x{prob.ny} cavity"},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--chunk", type=int, default=1000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-steps-per-step", type=int, default=4)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * goc.h -- C ABI of the B300 GOC-LBM library (libgoc.so).
+ *
+ * The library advances lattice Boltzmann solutions of the Navier-Stokes
+ * equations in general orthogonal coordinates (GOC): the central-moment MRT
+ * GOC-LBM for D2Q9 (Appendix E, "Summary of the Algorithmic Steps of the
+ * Central Moment GOC-LBM") coupled, optionally, with the D2Q5 vector GOC-LB
+ * scheme for the magnetic induction equation (Appendix G).  Every step runs
+ * in the library's own CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *  - Plain C types only.  Every call returns a goc_status (0 = success, < 0 =
+ *    error); goc_last_error() gives a thread-local message for the last error.
+ *    No call aborts the process.
+ *  - Ownership: the library owns all device memory it allocates (freed by
+ *    goc_destroy / goc_batch_destroy).  The caller owns every host buffer it
+ *    passes; the library never keeps a host pointer after a call returns.
+ *  - Streams: all device work of a lattice runs on goc_exec.cuda_stream
+ *    (a cudaStream_t; NULL = the legacy default stream).  goc_step returns
+ *    after enqueueing; calls that return data to the host synchronise that
+ *    stream only.
+ *  - Layout of host field arrays: row-major [ny][nx], node (i, j) at j*nx + i,
+ *    i along xi1, j along xi2.  Lattice units: Delta xi = Delta t = 1.
+ *  - Geometry: straight orthogonal grids x = x(xi1), y = y(xi2) (Appendix B,
+ *    case (i)), so theta12 = theta21 = 0.  Node placement: wall axes are
+ *    cell-centred (eta_j = (j + 1/2)/N, walls half a spacing outside the
+ *    first and last node, physical length N); periodic axes use eta_i = i/N.
+ */
+#ifndef GOC_H
+#define GOC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GOC_OK = 0,
+    GOC_EINVAL = -1,       /* invalid argument (message says which) */
+    GOC_ENOMEM = -2,       /* device or host allocation failed */
+    GOC_ECUDA = -3,        /* a CUDA runtime call failed */
+    GOC_EDIVERGED = -4,    /* NaN/Inf or non-positive density detected */
+    GOC_ETIMEOUT = -5,     /* a bounded device-side wait ran out */
+    GOC_EBUSY = -6,        /* batch is full / HBM budget exhausted */
+    GOC_EUNSUPPORTED = -7  /* valid request that this build does not support */
+} goc_status;
+
+/* Opaque handle of one lattice; owned by the library. */
+typedef struct goc_lattice goc_lattice;
+
+/* Boundary of one side of the lattice. Sides: 0 = W (xi1 = 0), 1 = E,
+ * 2 = S (xi2 = 0), 3 = N.  Opposite sides must both be periodic or both walls. */
+typedef enum { GOC_BC_PERIODIC = 0, GOC_BC_WALL = 1 } goc_bc;
+
+/* Stretching maps of one axis (Sec. 6).
+ *  UNIFORM  x = xi.
+ *  TANH2    clustering at both walls, Eq. hypertanh_transformation1 /
+ *           Eq. metriccoefficient (Sec. 6.1): x = (N/2)[1 + tanh(beta(2 eta-1))/tanh beta].
+ *  SINE     periodic stretching x = xi + (a N/2pi) sin(2 pi xi/N) (|a| < 1).
+ *  ROBERTS  Roberts boundary-layer map, Eq. y_Roberts / Eq. h2_Roberts
+ *           (Sec. 6.2), lambda = (gamma+1)/(gamma-1). */
+typedef enum { GOC_MAP_UNIFORM = 0, GOC_MAP_TANH2 = 1, GOC_MAP_SINE = 2, GOC_MAP_ROBERTS = 3 } goc_map_kind;
+
+typedef struct {
+    int nx, ny;             /* nodes along xi1, xi2; >= 3 along a wall axis, >= 1 otherwise */
+    int bc[4];              /* goc_bc per side W, E, S, N */
+    double wall_u[4];       /* tangential wall velocity: S/N along xi1, W/E along xi2
+                               (momentum-augmented bounce-back, Eq. 101 / Eq. 103) */
+    double wall_b[4][2];    /* (B1, B2) imposed at each wall for the MIE anti-bounce-back
+                               (Appendix G, "Boundary Conditions for the Magnetic Field") */
+} goc_grid;
+
+typedef struct {
+    int kind[2];            /* goc_map_kind for xi1, xi2 */
+    double beta[2];         /* TANH2 clustering parameter (0 = uniform) */
+    double a[2];            /* SINE amplitude */
+    double gamma[2];        /* ROBERTS gamma (> 1) */
+    double alpha[2];        /* ROBERTS alpha (0 or 1/2) */
+} goc_map;
+
+typedef struct {
+    double rho0;            /* reference density (initial state), > 0 */
+    double tau;             /* shear relaxation time: omega4 = omega5 = 1/tau (used if nu <= 0) */
+    double nu;              /* kinematic viscosity nu = cs^2 (1/omega5 - 1/2) (Eq. 73); > 0 overrides tau */
+    double tau_zeta;        /* omega3 = 1/tau_zeta, zeta = cs^2 (tau_zeta - 1/2) (Eq. 76); 0 -> 1 */
+    double omega_free;      /* omega0,1,2,6,7,8 (preparatory step (d)); 0 -> 1 */
+    double fext[2];         /* external body force, GOC components F_ext,1, F_ext,2 */
+    int gi_correction;      /* 1: full coefficients of Eqs. 83/85 (default);
+                               0: the cubic Galilean-invariance terms dropped */
+} goc_flow;
+
+typedef struct {
+    int enabled;            /* couple the D2Q5 MIE scheme (Appendix G) */
+    double tau_m;           /* magnetic relaxation time (used if eta <= 0) */
+    double eta;             /* magnetic resistivity eta = csm^2 (tau_m - 1/2); > 0 overrides tau_m */
+    double mu_m;            /* magnetic permeability (current density J = curl B / mu_m); 0 -> 1 */
+    double b_init[2];       /* uniform initial field (B1, B2); also the storage reference state */
+} goc_mhd;
+
+/* Population storage in HBM.  All arithmetic is FP32.  Populations are
+ * stored as deviations from the node's rest equilibrium at rho0
+ * (f_rest = P^-1 (h1 h2 rho0, 0, 0, h2/h1 rho0 cs^2, h1/h2 rho0 cs^2, 0, 0, 0, rho0 cs^4));
+ * FP16/BF16 store them divided by one per-lattice scale. */
+typedef enum { GOC_FP32 = 0, GOC_FP16_DEV = 1, GOC_BF16_DEV = 2 } goc_storage;
+
+typedef struct {
+    int storage;            /* goc_storage */
+    void *cuda_stream;      /* cudaStream_t for all work of this lattice; NULL = default stream */
+    int device;             /* CUDA device ordinal; < 0 = current device */
+    int check_every;        /* goc_run_until: steps between residual checks; 0 -> 100 */
+} goc_exec;
+
+/* ---- lifecycle --------------------------------------------------------- */
+
+/* q = min(min h1, min h2) and cs^2 = q^2/3 of a grid/map pair (Eq. GOC-LBE_CFL),
+ * computed by the library's FP64 metric kernel.  Either output may be NULL. */
+goc_status goc_metric_info(const goc_grid *grid, const goc_map *map, double *q, double *cs2);
+
+/* Create a lattice: FP64 metric precompute (preparatory step (a)), cs rule
+ * (step (c)), relaxation rates (step (d)), device allocation and the initial
+ * state at rest with rho = rho0, U = 0, B = b_init (Appendix C.1).
+ * mhd may be NULL (no MIE); exec may be NULL (FP32, default stream).
+ * On success *out owns the lattice; on failure *out is NULL. */
+goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *flow,
+                      const goc_mhd *mhd, const goc_exec *exec, goc_lattice **out);
+
+/* Re-initialise from host fields (each [ny][nx] doubles, NULL = default:
+ * rho0, 0, 0, b_init): f = P^-1 m^eq,eff(rho, U) with finite-difference
+ * gradients (Appendix C.1), g = g^eq(B, U) + g^corr, stored force F = 0.
+ * Resets the step counter.  Synchronises the stream. */
+goc_status goc_init_fields(goc_lattice *lat, const double *rho, const double *u1,
+                           const double *u2, const double *b1, const double *b2);
+
+/* NULL-safe.  Synchronises the stream and frees all device memory. */
+void goc_destroy(goc_lattice *lat);
+
+/* ---- the hot loop ------------------------------------------------------ */
+
+/* Enqueue nsteps time steps (each one fused launch: pull-streaming with
+ * boundary conditions, hydrodynamic fields, normal gradients, stresses,
+ * effective and Lorentz forces, central-moment collision, MIE collision,
+ * store).  Asynchronous; returns launch errors only.  nsteps >= 0. */
+goc_status goc_step(goc_lattice *lat, long long nsteps);
+
+/* Step until the residual R = ||U^n - U^(n-1)||_2 / ||U^n||_2 (max with the
+ * B residual when the MIE is on; Sec. 7.3) falls below tol, checking every
+ * exec.check_every steps, or max_steps is reached.  *done (may be NULL)
+ * receives the steps taken, *residual (may be NULL) the last residual.
+ * Synchronises.  Returns GOC_EDIVERGED on NaN. */
+goc_status goc_run_until(goc_lattice *lat, double tol, long long max_steps,
+                         long long *done, double *residual);
+
+/* Block the host until the lattice's stream has drained. */
+goc_status goc_sync(goc_lattice *lat);
+
+/* ---- results ----------------------------------------------------------- */
+
+/* Macroscopic fields of the current state into caller-owned host arrays
+ * ([ny][nx] doubles each; any may be NULL): rho, U1, U2 (with the stored
+ * force, Eq. GOChydrodynamicfields), B1, B2 (Eq. 13_C; zero without MIE).
+ * cartesian != 0 maps vector components with Eq. vectormapping; on the
+ * straight grids of this library the GOC unit vectors coincide with the
+ * Cartesian ones, so the values are the same.  Synchronises. */
+goc_status goc_moments(goc_lattice *lat, int cartesian, double *rho, double *u1,
+                       double *u2, double *b1, double *b2);
+
+/* Same fields as FP32 into caller-owned DEVICE memory out[5][ny][nx]
+ * (rho, U1, U2, B1, B2), enqueued on the lattice stream (no sync). */
+goc_status goc_moments_device(goc_lattice *lat, float *out);
+
+/* FP64 reductions of the current state: total mass sum f = sum h1 h2 rho,
+ * and the residuals of the last goc_run_until check (0 before any).
+ * Any pointer may be NULL.  Synchronises. */
+goc_status goc_diagnostics(goc_lattice *lat, double *mass, double *residual_u,
+                           double *residual_b);
+
+/* Steps taken since creation / the last goc_init_fields. */
+long long goc_steps_done(const goc_lattice *lat);
+
+/* Number of nodes and bytes of device memory held by the lattice. */
+goc_status goc_footprint(const goc_lattice *lat, long long *nodes, long long *device_bytes);
+
+/* Algorithmic HBM bytes one node update moves (populations and stored force
+ * read and written once, plus the per-node share of the metric tables). */
+double goc_bytes_per_node(const goc_lattice *lat);
+
+/* ---- checkpoint / resume ----------------------------------------------- */
+
+/* Serialise the full state (populations, stored force, MIE populations,
+ * step counter) into a caller buffer.  With buf == NULL only *bytes is set.
+ * Restoring into a lattice created with the same arguments and stepping
+ * gives bitwise the same results as never stopping. */
+goc_status goc_get_state(goc_lattice *lat, void *buf, size_t *bytes);
+goc_status goc_set_state(goc_lattice *lat, const void *buf, size_t bytes);
+
+/* ---- batched execution of many independent lattices -------------------- */
+
+typedef struct goc_batch goc_batch;
+
+/* A batch holds up to max_lattices lattices whose total device footprint
+ * stays within hbm_budget_bytes; all run on one stream. */
+goc_status goc_batch_create(long long hbm_budget_bytes, int max_lattices,
+                            const goc_exec *exec, goc_batch **out);
+void goc_batch_destroy(goc_batch *b);
+
+/* Admit a lattice (same arguments as goc_create; exec's stream and storage
+ * come from the batch unless exec != NULL).  Returns GOC_EBUSY if the budget
+ * or the slot count would be exceeded.  *slot receives the slot id. */
+goc_status goc_batch_add(goc_batch *b, const goc_grid *grid, const goc_map *map,
+                         const goc_flow *flow, const goc_mhd *mhd, int storage, int *slot);
+
+/* Remove a lattice and free its memory. */
+goc_status goc_batch_remove(goc_batch *b, int slot);
+
+/* Advance every resident lattice by nsteps with one persistent launch per
+ * time step (work items = (lattice, tile) over all lattices). */
+goc_status goc_batch_step(goc_batch *b, long long nsteps);
+
+/* Access one resident lattice (owned by the batch; do not destroy). */
+goc_status goc_batch_lattice(goc_batch *b, int slot, goc_lattice **lat);
+
+/* Bytes the batch currently holds on the device and its budget. */
+goc_status goc_batch_usage(const goc_batch *b, long long *used, long long *budget, int *count);
+
+/* ---- errors ------------------------------------------------------------ */
+const char *goc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GOC_H */

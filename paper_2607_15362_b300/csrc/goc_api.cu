@@ -1,0 +1,1022 @@
+// goc_api.cu -- host side of the C ABI declared in include/goc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/goc.h"
+#include "goc_aux.cuh"
+#include "goc_device.cuh"
+#include "goc_step.cuh"
+
+using namespace goc;
+
+namespace {
+
+thread_local std::string g_err;
+
+goc_status fail(goc_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(GOC_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+size_t elem_size(int storage) { return storage == GOC_FP32 ? 4 : 2; }
+
+constexpr int kGraphSteps = 64;   // steps per captured graph (even: one buffer cycle per 2)
+
+}  // namespace
+
+struct goc_lattice {
+    goc_grid grid;
+    goc_map map;
+    goc_flow flow;
+    goc_mhd mhd;
+    int storage = GOC_FP32;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int check_every = 100;
+    int nx = 0, ny = 0, pitch = 0;
+    long long plane = 0;
+    // device memory
+    void *f[2] = {nullptr, nullptr};
+    void *F[2] = {nullptr, nullptr};
+    void *g[2] = {nullptr, nullptr};
+    float *tab1 = nullptr, *tab2 = nullptr;      // [7][nx], [7][ny]
+    double *m1 = nullptr, *m2 = nullptr;         // FP64 h, theta per axis: [2][n+2]
+    float *uout[2] = {nullptr, nullptr};
+    int *flag = nullptr;
+    double *red = nullptr;                       // 8 doubles
+    double *mom = nullptr;                       // [5][ny][nx]
+    size_t device_bytes = 0;
+    // parameters
+    double q = 1.0, cs2 = 1.0 / 3.0, nu = 0, zeta = 0, tau = 1, csm2 = 0, taum = 1, eta = 0;
+    double hw[4] = {1, 1, 1, 1};
+    StepParams sp;
+    int cur = 0;
+    long long steps = 0;
+    double res_u = 0.0, res_b = 0.0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_cur = 0;                           // buffer the captured graph starts from
+    bool owns_stream = false;
+    bool in_batch = false;                       // stepped only through goc_batch_step
+    bool fresh = false;                          // buffer holds f^0 (pre-collision): next step reads in place
+};
+
+namespace {
+
+template <class S>
+goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
+    dim3 grid((L->nx + TX - 1) / TX, (L->ny + TY - 1) / TY), block(TX, TY);
+    if (L->mhd.enabled) step_kernel<S, true><<<grid, block, 0, L->stream>>>(p);
+    else step_kernel<S, false><<<grid, block, 0, L->stream>>>(p);
+    CU(cudaGetLastError());
+    return GOC_OK;
+}
+
+StepParams params_for(goc_lattice *L, int src, float *uout) {
+    StepParams p = L->sp;
+    p.fin = L->f[src];
+    p.fout = L->f[src ^ 1];
+    p.Fin = L->F[src];
+    p.Fout = L->F[src ^ 1];
+    p.gin = L->g[src];
+    p.gout = L->g[src ^ 1];
+    p.uout = uout;
+    return p;
+}
+
+goc_status launch_one(goc_lattice *L, float *uout) {
+    StepParams p = params_for(L, L->cur, uout);
+    p.nopull = L->fresh ? 1 : 0;
+    goc_status st;
+    switch (L->storage) {
+        case GOC_FP16_DEV: st = launch_step_t<__half>(L, p); break;
+        case GOC_BF16_DEV: st = launch_step_t<__nv_bfloat16>(L, p); break;
+        default: st = launch_step_t<float>(L, p); break;
+    }
+    if (st != GOC_OK) return st;
+    L->cur ^= 1;
+    L->steps++;
+    L->fresh = false;
+    return GOC_OK;
+}
+
+goc_status ensure_graph(goc_lattice *L) {
+    if (L->graph) return GOC_OK;
+    // capture kGraphSteps launches on a private stream (the lattice stream may
+    // be the legacy default stream, which cannot be captured)
+    cudaStream_t cs;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t keep = L->stream;
+    int cur = L->cur;
+    long long steps = L->steps;
+    bool fresh = L->fresh;
+    L->fresh = false;
+    L->stream = cs;
+    cudaGraph_t gr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    goc_status st = GOC_OK;
+    if (e == cudaSuccess) {
+        for (int k = 0; k < kGraphSteps && st == GOC_OK; k++) st = launch_one(L, nullptr);
+        e = cudaStreamEndCapture(cs, &gr);
+    }
+    L->stream = keep;
+    L->cur = cur;
+    L->steps = steps;
+    L->fresh = fresh;
+    cudaStreamDestroy(cs);
+    if (st != GOC_OK) return st;
+    if (e != cudaSuccess) return fail(GOC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    L->graph_cur = cur;
+    e = cudaGraphInstantiate(&L->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+        L->graph = nullptr;
+        return fail(GOC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    return GOC_OK;
+}
+
+goc_status validate(const goc_grid *grid, const goc_map *map) {
+    if (!grid || !map) return fail(GOC_EINVAL, "grid and map are required");
+    if (grid->nx < 1 || grid->ny < 1) return fail(GOC_EINVAL, "nx, ny must be >= 1 (got %d, %d)", grid->nx, grid->ny);
+    if ((long long)grid->nx * grid->ny > (1LL << 31) || grid->ny > 65535)
+        return fail(GOC_EINVAL, "lattice too large (nx*ny <= 2^31, ny <= 65535)");
+    for (int s = 0; s < 4; s++)
+        if (grid->bc[s] != GOC_BC_PERIODIC && grid->bc[s] != GOC_BC_WALL)
+            return fail(GOC_EINVAL, "bc[%d] must be GOC_BC_PERIODIC or GOC_BC_WALL", s);
+    if (grid->bc[0] != grid->bc[1] || grid->bc[2] != grid->bc[3])
+        return fail(GOC_EINVAL, "opposite sides must both be periodic or both walls");
+    if (grid->bc[0] == GOC_BC_WALL && grid->nx < 3) return fail(GOC_EINVAL, "a wall axis needs >= 3 nodes");
+    if (grid->bc[2] == GOC_BC_WALL && grid->ny < 3) return fail(GOC_EINVAL, "a wall axis needs >= 3 nodes");
+    for (int a = 0; a < 2; a++) {
+        int k = map->kind[a];
+        if (k < 0 || k > 3) return fail(GOC_EINVAL, "map kind[%d] = %d unknown", a, k);
+        int per = grid->bc[a == 0 ? 0 : 2] == GOC_BC_PERIODIC;
+        if ((k == GOC_MAP_TANH2 || k == GOC_MAP_ROBERTS) && per && !(k == GOC_MAP_TANH2 && map->beta[a] == 0.0))
+            return fail(GOC_EINVAL, "axis %d: wall-clustering map on a periodic axis", a);
+        if (k == GOC_MAP_SINE && !per) return fail(GOC_EINVAL, "axis %d: sine map needs a periodic axis", a);
+        if (k == GOC_MAP_SINE && !(std::fabs(map->a[a]) < 1.0)) return fail(GOC_EINVAL, "sine amplitude must be < 1");
+        if (k == GOC_MAP_TANH2 && !(map->beta[a] >= 0.0)) return fail(GOC_EINVAL, "beta must be >= 0");
+        if (k == GOC_MAP_ROBERTS && !(map->gamma[a] > 1.0)) return fail(GOC_EINVAL, "Roberts gamma must be > 1");
+        if (k == GOC_MAP_ROBERTS && !(map->alpha[a] == 0.0 || map->alpha[a] == 0.5))
+            return fail(GOC_EINVAL, "Roberts alpha must be 0 or 1/2");
+    }
+    return GOC_OK;
+}
+
+MapParams map_params(const goc_grid *grid, const goc_map *map, int axis) {
+    MapParams m;
+    m.kind = map->kind[axis];
+    m.n = axis == 0 ? grid->nx : grid->ny;
+    m.periodic = grid->bc[axis == 0 ? 0 : 2] == GOC_BC_PERIODIC;
+    m.beta = map->beta[axis];
+    m.a = map->a[axis];
+    m.gamma = map->gamma[axis];
+    m.alpha = map->alpha[axis];
+    return m;
+}
+
+// FP64 metric of both axes on the device: d1, d2 = [2][n+2] (h, theta); q.
+goc_status compute_metric(const goc_grid *grid, const goc_map *map, cudaStream_t st,
+                          double *d1, double *d2, double *qdev) {
+    MapParams a = map_params(grid, map, 0), b = map_params(grid, map, 1);
+    metric_axis_kernel<<<(a.n + 2 + 127) / 128, 128, 0, st>>>(a, d1, d1 + a.n + 2);
+    metric_axis_kernel<<<(b.n + 2 + 127) / 128, 128, 0, st>>>(b, d2, d2 + b.n + 2);
+    min_h_kernel<<<1, 256, 0, st>>>(d1, a.n, d2, b.n, qdev);
+    CU(cudaGetLastError());
+    return GOC_OK;
+}
+
+void free_lattice(goc_lattice *L) {
+    if (!L) return;
+    if (L->stream || true) cudaStreamSynchronize(L->stream);
+    if (L->graph) cudaGraphExecDestroy(L->graph);
+    void *ptrs[] = {L->f[0], L->f[1], L->F[0], L->F[1], L->g[0], L->g[1], L->tab1, L->tab2,
+                    L->m1, L->m2, L->uout[0], L->uout[1], L->flag, L->red, L->mom};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (L->owns_stream && L->stream) cudaStreamDestroy(L->stream);
+    delete L;
+}
+
+template <class T>
+goc_status dalloc(goc_lattice *L, T **p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? GOC_ENOMEM : GOC_ECUDA, "cudaMalloc(%zu) failed: %s",
+                    bytes, cudaGetErrorString(e));
+    }
+    L->device_bytes += bytes;
+    return GOC_OK;
+}
+
+goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const double *u2,
+                    const double *b1, const double *b2) {
+    const long long N = (long long)L->nx * L->ny;
+    std::vector<double> host(5 * N);
+    for (long long n = 0; n < N; n++) {
+        host[n] = rho ? rho[n] : L->flow.rho0;
+        host[N + n] = u1 ? u1[n] : 0.0;
+        host[2 * N + n] = u2 ? u2[n] : 0.0;
+        host[3 * N + n] = b1 ? b1[n] : L->mhd.b_init[0];
+        host[4 * N + n] = b2 ? b2[n] : L->mhd.b_init[1];
+    }
+    double *dev = nullptr;
+    CU(cudaMalloc(&dev, 5 * N * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), 5 * N * sizeof(double), cudaMemcpyHostToDevice, L->stream);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return fail(GOC_ECUDA, "init copy failed: %s", cudaGetErrorString(e));
+    }
+    InitParams q;
+    q.sp = params_for(L, L->cur, nullptr);   // writes the current buffer
+    q.sp.fout = L->f[L->cur];
+    q.sp.Fout = L->F[L->cur];
+    q.sp.gout = L->g[L->cur];
+    q.h1d = L->m1;
+    q.t1d = L->m1 + L->nx + 2;
+    q.h2d = L->m2;
+    q.t2d = L->m2 + L->ny + 2;
+    q.cs2 = L->cs2;
+    q.nu = L->nu;
+    q.zeta = L->zeta;
+    q.rho0 = L->flow.rho0;
+    q.csm2 = L->csm2;
+    q.eta = L->eta;
+    q.gi = L->flow.gi_correction;
+    q.mhd = L->mhd.enabled;
+    q.rho = dev;
+    q.u1 = dev + N;
+    q.u2 = dev + 2 * N;
+    q.b1 = dev + 3 * N;
+    q.b2 = dev + 4 * N;
+    dim3 grid((L->nx + 127) / 128, L->ny), block(128);
+    switch (L->storage) {
+        case GOC_FP16_DEV: init_kernel<__half><<<grid, block, 0, L->stream>>>(q); break;
+        case GOC_BF16_DEV: init_kernel<__nv_bfloat16><<<grid, block, 0, L->stream>>>(q); break;
+        default: init_kernel<float><<<grid, block, 0, L->stream>>>(q); break;
+    }
+    e = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(L->stream);
+    cudaFree(dev);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(GOC_ECUDA, "init kernel failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    L->steps = 0;
+    L->res_u = L->res_b = 0.0;
+    L->fresh = true;
+    return GOC_OK;
+}
+
+__global__ void to_float_kernel(const double *in, float *out, long long n) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < n) out[k] = (float)in[k];
+}
+
+// Macroscopic fields of the current state into L->mom ([5][ny][nx] FP64).
+goc_status moments_to_device(goc_lattice *L) {
+    const long long N = (long long)L->nx * L->ny;
+    if (!L->mom) {
+        CU(cudaMalloc(&L->mom, 5 * N * sizeof(double)));
+        L->device_bytes += 5 * N * sizeof(double);
+    }
+    StepParams p = params_for(L, L->cur, nullptr);
+    p.nopull = L->fresh ? 1 : 0;
+    dim3 grid((L->nx + 127) / 128, L->ny), block(128);
+    const bool m = L->mhd.enabled;
+    switch (L->storage) {
+        case GOC_FP16_DEV:
+            if (m) moments_kernel<__half, true><<<grid, block, 0, L->stream>>>(p, L->mom);
+            else moments_kernel<__half, false><<<grid, block, 0, L->stream>>>(p, L->mom);
+            break;
+        case GOC_BF16_DEV:
+            if (m) moments_kernel<__nv_bfloat16, true><<<grid, block, 0, L->stream>>>(p, L->mom);
+            else moments_kernel<__nv_bfloat16, false><<<grid, block, 0, L->stream>>>(p, L->mom);
+            break;
+        default:
+            if (m) moments_kernel<float, true><<<grid, block, 0, L->stream>>>(p, L->mom);
+            else moments_kernel<float, false><<<grid, block, 0, L->stream>>>(p, L->mom);
+    }
+    CU(cudaGetLastError());
+    return GOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *goc_last_error(void) { return g_err.c_str(); }
+
+goc_status goc_metric_info(const goc_grid *grid, const goc_map *map, double *q, double *cs2) {
+    goc_status st = validate(grid, map);
+    if (st != GOC_OK) return st;
+    double *d = nullptr;
+    size_t n1 = grid->nx + 2, n2 = grid->ny + 2;
+    CU(cudaMalloc(&d, (2 * n1 + 2 * n2 + 1) * sizeof(double)));
+    st = compute_metric(grid, map, 0, d, d + 2 * n1, d + 2 * n1 + 2 * n2);
+    double qh = 0;
+    cudaError_t e = cudaMemcpy(&qh, d + 2 * n1 + 2 * n2, sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (st != GOC_OK) return st;
+    if (e != cudaSuccess) return fail(GOC_ECUDA, "metric copy failed: %s", cudaGetErrorString(e));
+    if (q) *q = qh;
+    if (cs2) *cs2 = qh * qh / 3.0;
+    return GOC_OK;
+}
+
+goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *flow,
+                      const goc_mhd *mhd, const goc_exec *exec, goc_lattice **out) {
+    if (!out) return fail(GOC_EINVAL, "out is NULL");
+    *out = nullptr;
+    goc_status st = validate(grid, map);
+    if (st != GOC_OK) return st;
+    if (!flow) return fail(GOC_EINVAL, "flow is required");
+    if (!(flow->rho0 > 0.0)) return fail(GOC_EINVAL, "rho0 must be > 0");
+    if (flow->nu <= 0.0 && !(flow->tau > 0.5)) return fail(GOC_EINVAL, "need nu > 0 or tau > 1/2");
+    if (exec && (exec->storage < 0 || exec->storage > 2)) return fail(GOC_EINVAL, "unknown storage %d", exec->storage);
+    goc_lattice *L = new (std::nothrow) goc_lattice();
+    if (!L) return fail(GOC_ENOMEM, "host allocation failed");
+    L->grid = *grid;
+    L->map = *map;
+    L->flow = *flow;
+    if (L->flow.tau_zeta == 0.0) L->flow.tau_zeta = 1.0;
+    if (L->flow.omega_free == 0.0) L->flow.omega_free = 1.0;
+    std::memset(&L->mhd, 0, sizeof L->mhd);
+    if (mhd && mhd->enabled) {
+        L->mhd = *mhd;
+        if (L->mhd.mu_m == 0.0) L->mhd.mu_m = 1.0;
+        if (L->mhd.eta <= 0.0 && !(L->mhd.tau_m > 0.5)) {
+            delete L;
+            return fail(GOC_EINVAL, "MIE needs eta > 0 or tau_m > 1/2");
+        }
+    }
+    if (exec) {
+        L->storage = exec->storage;
+        L->stream = (cudaStream_t)exec->cuda_stream;
+        L->check_every = exec->check_every > 0 ? exec->check_every : 100;
+        if (exec->device >= 0) {
+            cudaError_t e = cudaSetDevice(exec->device);
+            if (e != cudaSuccess) {
+                delete L;
+                return fail(GOC_ECUDA, "cudaSetDevice(%d): %s", exec->device, cudaGetErrorString(e));
+            }
+        }
+    }
+    cudaGetDevice(&L->device);
+    L->nx = grid->nx;
+    L->ny = grid->ny;
+    L->pitch = (grid->nx + 31) / 32 * 32;
+    L->plane = (long long)L->pitch * L->ny;
+    const size_t es = elem_size(L->storage);
+#define TRY(x)                 \
+    do {                       \
+        goc_status s_ = (x);   \
+        if (s_ != GOC_OK) {    \
+            free_lattice(L);   \
+            return s_;         \
+        }                      \
+    } while (0)
+    for (int b = 0; b < 2; b++) {
+        TRY(dalloc(L, &L->f[b], 9 * L->plane * es));
+        TRY(dalloc(L, &L->F[b], 2 * L->plane * es));
+        if (L->mhd.enabled) TRY(dalloc(L, &L->g[b], 10 * L->plane * es));
+    }
+    TRY(dalloc(L, &L->tab1, 7 * (size_t)L->nx * sizeof(float)));
+    TRY(dalloc(L, &L->tab2, 7 * (size_t)L->ny * sizeof(float)));
+    TRY(dalloc(L, &L->m1, 2 * (size_t)(L->nx + 2) * sizeof(double)));
+    TRY(dalloc(L, &L->m2, 2 * (size_t)(L->ny + 2) * sizeof(double)));
+    TRY(dalloc(L, &L->flag, sizeof(int)));
+    TRY(dalloc(L, &L->red, 8 * sizeof(double)));
+    // metric (FP64), q, cs2 (Eq. GOC-LBE_CFL)
+    TRY(compute_metric(grid, map, L->stream, L->m1, L->m2, L->red));
+    double hw1[2], hw2[2], qh;
+    {
+        cudaError_t e = cudaMemcpyAsync(&qh, L->red, sizeof(double), cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hw1, L->m1 + L->nx, 2 * sizeof(double), cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hw2, L->m2 + L->ny, 2 * sizeof(double), cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+        if (e != cudaSuccess) {
+            free_lattice(L);
+            return fail(GOC_ECUDA, "metric readback failed: %s", cudaGetErrorString(e));
+        }
+    }
+    L->q = qh;
+    L->cs2 = qh * qh / 3.0;
+    if (L->flow.nu > 0.0) {
+        L->nu = L->flow.nu;
+        L->tau = L->nu / L->cs2 + 0.5;
+    } else {
+        L->tau = L->flow.tau;
+        L->nu = L->cs2 * (L->tau - 0.5);
+    }
+    L->zeta = L->cs2 * (L->flow.tau_zeta - 0.5);
+    if (L->mhd.enabled) {
+        L->csm2 = L->cs2;   // c_sm = c_s (Eq. GOC-LBE_CFL-MIE)
+        if (L->mhd.eta > 0.0) {
+            L->eta = L->mhd.eta;
+            L->taum = L->eta / L->csm2 + 0.5;
+        } else {
+            L->taum = L->mhd.tau_m;
+            L->eta = L->csm2 * (L->taum - 0.5);
+        }
+    }
+    // wall-normal metric at each wall: W/E -> h1(0), h1(n); S/N -> h2(0), h2(n)
+    L->hw[0] = hw1[0];
+    L->hw[1] = hw1[1];
+    L->hw[2] = hw2[0];
+    L->hw[3] = hw2[1];
+    const double rho0cs2 = L->flow.rho0 * L->cs2;
+    const int per_x = grid->bc[0] == GOC_BC_PERIODIC, per_y = grid->bc[2] == GOC_BC_PERIODIC;
+    axis_tables_kernel<<<(L->nx + 127) / 128, 128, 0, L->stream>>>(L->m1, L->m1 + L->nx + 2, L->nx, per_x, rho0cs2,
+                                                                   L->cs2, L->tab1);
+    axis_tables_kernel<<<(L->ny + 127) / 128, 128, 0, L->stream>>>(L->m2, L->m2 + L->ny + 2, L->ny, per_y, rho0cs2,
+                                                                   L->cs2, L->tab2);
+    {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            free_lattice(L);
+            return fail(GOC_ECUDA, "table kernel failed: %s", cudaGetErrorString(e));
+        }
+    }
+    // step parameters
+    StepParams &p = L->sp;
+    std::memset(&p, 0, sizeof p);
+    p.nx = L->nx;
+    p.ny = L->ny;
+    p.pitch = L->pitch;
+    p.plane = L->plane;
+    p.per_x = per_x;
+    p.per_y = per_y;
+    auto axis = [](float *t, int n) {
+        Axis a;
+        a.h = t;
+        a.ih = t + n;
+        a.th = t + 2 * n;
+        a.rm = t + 3 * n;
+        a.rp = t + 4 * n;
+        a.dm = t + 5 * n;
+        a.dp = t + 6 * n;
+        return a;
+    };
+    p.ax1 = axis(L->tab1, L->nx);
+    p.ax2 = axis(L->tab2, L->ny);
+    p.rho0 = (float)L->flow.rho0;
+    p.cs2 = (float)L->cs2;
+    p.nu = (float)L->nu;
+    p.zeta = (float)L->zeta;
+    for (int k = 0; k < 9; k++) p.om[k] = (float)L->flow.omega_free;
+    p.om[3] = (float)(1.0 / L->flow.tau_zeta);
+    p.om[4] = p.om[5] = (float)(1.0 / L->tau);
+    p.fext1 = (float)L->flow.fext[0];
+    p.fext2 = (float)L->flow.fext[1];
+    p.gi = L->flow.gi_correction ? 1.f : 0.f;
+    for (int s = 0; s < 4; s++) {
+        p.uw[s] = grid->bc[s] == GOC_BC_WALL ? (float)grid->wall_u[s] : 0.f;
+        p.hwn[s] = (float)L->hw[s];
+        if (p.uw[s] != 0.f) p.moving = 1;
+        p.bw[s][0] = (float)grid->wall_b[s][0];
+        p.bw[s][1] = (float)grid->wall_b[s][1];
+    }
+    // storage scales (1 for FP32; for 16-bit a per-lattice velocity scale)
+    p.sf = p.isf = p.sF = p.isF = p.sg = p.isg = 1.f;
+    if (L->storage != GOC_FP32) {
+        double uref = 1e-3 * std::sqrt(L->cs2);
+        for (int s = 0; s < 4; s++) uref = std::max(uref, std::fabs((double)p.uw[s]));
+        double hmax = 1.0;   // scale so that |deviation| / s stays well inside the 16-bit range
+        double sf = L->flow.rho0 * uref * hmax / 256.0;
+        p.sf = (float)sf;
+        p.isf = (float)(1.0 / sf);
+        p.sF = (float)(sf * 1e-3);
+        p.isF = (float)(1.0 / (sf * 1e-3));
+        p.sg = (float)sf;
+        p.isg = (float)(1.0 / sf);
+    }
+    if (L->mhd.enabled) {
+        p.csm2 = (float)L->csm2;
+        p.icsm2 = (float)(1.0 / L->csm2);
+        p.taum = (float)L->taum;
+        p.itaum = (float)(1.0 / L->taum);
+        p.eta = (float)L->eta;
+        p.imum = (float)(1.0 / L->mhd.mu_m);
+        p.W0 = (float)(1.0 - 2.0 * L->csm2);
+        p.W1 = (float)(0.5 * L->csm2);
+        p.brest[0] = (float)L->mhd.b_init[0];
+        p.brest[1] = (float)L->mhd.b_init[1];
+        double bmax = std::max(std::fabs(L->mhd.b_init[0]), std::fabs(L->mhd.b_init[1]));
+        if (L->storage != GOC_FP32 && bmax > 0) {
+            p.sg = (float)(bmax / 256.0);
+            p.isg = (float)(256.0 / bmax);
+        }
+    }
+    p.flag = L->flag;
+    TRY(run_init(L, nullptr, nullptr, nullptr, nullptr, nullptr));
+    {
+        cudaError_t e = cudaMemsetAsync(L->flag, 0, sizeof(int), L->stream);
+        if (e != cudaSuccess) {
+            free_lattice(L);
+            return fail(GOC_ECUDA, "memset failed");
+        }
+    }
+#undef TRY
+    *out = L;
+    return GOC_OK;
+}
+
+goc_status goc_init_fields(goc_lattice *L, const double *rho, const double *u1, const double *u2,
+                           const double *b1, const double *b2) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    return run_init(L, rho, u1, u2, b1, b2);
+}
+
+void goc_destroy(goc_lattice *L) { free_lattice(L); }
+
+goc_status goc_step(goc_lattice *L, long long nsteps) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (nsteps < 0) return fail(GOC_EINVAL, "nsteps must be >= 0");
+    if (L->in_batch) return fail(GOC_EINVAL, "this lattice belongs to a batch: step it with goc_batch_step");
+    if (L->fresh && nsteps > 0) {   // first step after initialisation: no streaming of f^0
+        goc_status st = launch_one(L, nullptr);
+        if (st != GOC_OK) return st;
+        nsteps--;
+    }
+    if (nsteps > kGraphSteps) {
+        goc_status st = ensure_graph(L);
+        if (st != GOC_OK) return st;
+        if (L->cur != L->graph_cur) {   // align the buffer parity with the captured graph
+            if ((st = launch_one(L, nullptr)) != GOC_OK) return st;
+            nsteps--;
+        }
+        while (nsteps >= kGraphSteps) {
+            CU(cudaGraphLaunch(L->graph, L->stream));
+            L->steps += kGraphSteps;   // kGraphSteps is even: the current buffer is unchanged
+            nsteps -= kGraphSteps;
+        }
+    }
+    for (long long s = 0; s < nsteps; s++) {
+        goc_status st = launch_one(L, nullptr);
+        if (st != GOC_OK) return st;
+    }
+    return GOC_OK;
+}
+
+goc_status goc_sync(goc_lattice *L) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    CU(cudaStreamSynchronize(L->stream));
+    return GOC_OK;
+}
+
+long long goc_steps_done(const goc_lattice *L) { return L ? L->steps : -1; }
+
+goc_status goc_footprint(const goc_lattice *L, long long *nodes, long long *bytes) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (nodes) *nodes = (long long)L->nx * L->ny;
+    if (bytes) *bytes = (long long)L->device_bytes + (L->mom ? 0 : 0);
+    return GOC_OK;
+}
+
+double goc_bytes_per_node(const goc_lattice *L) {
+    if (!L) return 0.0;
+    const double es = (double)elem_size(L->storage);
+    double b = 2.0 * (9.0 + 2.0) * es;                  // populations + stored force, read + write
+    if (L->mhd.enabled) b += 2.0 * 10.0 * es;           // MIE populations
+    b += 4.0 * 7.0 * (1.0 / L->ny + 1.0 / L->nx);       // per-axis tables amortised over the lattice
+    return b;
+}
+
+goc_status goc_moments(goc_lattice *L, int cartesian, double *rho, double *u1, double *u2,
+                       double *b1, double *b2) {
+    (void)cartesian;   // straight grids: GOC unit vectors are the Cartesian ones
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    goc_status st = moments_to_device(L);
+    if (st != GOC_OK) return st;
+    const long long N = (long long)L->nx * L->ny;
+    double *outs[5] = {rho, u1, u2, b1, b2};
+    for (int k = 0; k < 5; k++)
+        if (outs[k]) CU(cudaMemcpyAsync(outs[k], L->mom + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    CU(cudaStreamSynchronize(L->stream));
+    return GOC_OK;
+}
+
+goc_status goc_moments_device(goc_lattice *L, float *out) {
+    if (!L || !out) return fail(GOC_EINVAL, "lattice and out are required");
+    goc_status st = moments_to_device(L);
+    if (st != GOC_OK) return st;
+    const long long n = 5LL * L->nx * L->ny;
+    to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, L->stream>>>(L->mom, out, n);
+    CU(cudaGetLastError());
+    return GOC_OK;
+}
+
+goc_status goc_diagnostics(goc_lattice *L, double *mass, double *residual_u, double *residual_b) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (mass) {
+        StepParams p = params_for(L, L->cur, nullptr);
+        CU(cudaMemsetAsync(L->red, 0, sizeof(double), L->stream));
+        switch (L->storage) {
+            case GOC_FP16_DEV: mass_kernel<__half><<<296, 256, 0, L->stream>>>(p, L->red); break;
+            case GOC_BF16_DEV: mass_kernel<__nv_bfloat16><<<296, 256, 0, L->stream>>>(p, L->red); break;
+            default: mass_kernel<float><<<296, 256, 0, L->stream>>>(p, L->red); break;
+        }
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(mass, L->red, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+        CU(cudaStreamSynchronize(L->stream));
+    }
+    if (residual_u) *residual_u = L->res_u;
+    if (residual_b) *residual_b = L->res_b;
+    return GOC_OK;
+}
+
+goc_status goc_run_until(goc_lattice *L, double tol, long long max_steps, long long *done, double *residual) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (max_steps < 0) return fail(GOC_EINVAL, "max_steps must be >= 0");
+    if (!L->uout[0]) {
+        for (int b = 0; b < 2; b++) {
+            cudaError_t e = cudaMalloc(&L->uout[b], 4 * L->plane * sizeof(float));
+            if (e != cudaSuccess) return fail(GOC_ENOMEM, "residual buffers: %s", cudaGetErrorString(e));
+            L->device_bytes += 4 * L->plane * sizeof(float);
+        }
+    }
+    long long taken = 0;
+    double R = 1e300;
+    int h_flag = 0;
+    const int K = std::max(2, L->check_every);
+    while (taken < max_steps) {
+        long long chunk = std::min<long long>(K, max_steps - taken);
+        if (chunk >= 2) {
+            goc_status st = goc_step(L, chunk - 2);
+            if (st != GOC_OK) return st;
+            if ((st = launch_one(L, L->uout[0])) != GOC_OK) return st;
+            if ((st = launch_one(L, L->uout[1])) != GOC_OK) return st;
+            CU(cudaMemsetAsync(L->red, 0, 4 * sizeof(double), L->stream));
+            residual_kernel<<<296, 256, 0, L->stream>>>(L->uout[0], L->uout[1], L->plane, L->nx, L->ny, L->pitch, L->red);
+            CU(cudaGetLastError());
+            double h[4];
+            CU(cudaMemcpyAsync(h, L->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+            CU(cudaMemcpyAsync(&h_flag, L->flag, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+            CU(cudaStreamSynchronize(L->stream));
+            taken += chunk;
+            L->res_u = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+            L->res_b = (L->mhd.enabled && h[3] > 0) ? std::sqrt(h[2] / h[3]) : 0.0;
+            R = std::max(L->res_u, L->res_b);
+            if (h_flag || !std::isfinite(R)) {
+                if (done) *done = taken;
+                if (residual) *residual = R;
+                return fail(GOC_EDIVERGED, "lattice diverged after %lld steps", L->steps);
+            }
+            if (R < tol) break;
+        } else {
+            goc_status st = goc_step(L, chunk);
+            if (st != GOC_OK) return st;
+            taken += chunk;
+        }
+    }
+    if (done) *done = taken;
+    if (residual) *residual = R;
+    return GOC_OK;
+}
+
+goc_status goc_get_state(goc_lattice *L, void *buf, size_t *bytes) {
+    if (!L || !bytes) return fail(GOC_EINVAL, "lattice and bytes are required");
+    const size_t es = elem_size(L->storage);
+    const size_t nf = 9 * L->plane * es, nF = 2 * L->plane * es, ng = L->mhd.enabled ? 10 * L->plane * es : 0;
+    const size_t total = 64 + nf + nF + ng;
+    if (!buf) {
+        *bytes = total;
+        return GOC_OK;
+    }
+    if (*bytes < total) return fail(GOC_EINVAL, "buffer too small (%zu < %zu)", *bytes, total);
+    char *c = static_cast<char *>(buf);
+    long long hdr[8] = {0x474f434c4154ll, L->nx, L->ny, L->storage, L->mhd.enabled, L->steps, (long long)total,
+                        L->fresh ? 1 : 0};
+    std::memcpy(c, hdr, sizeof hdr);
+    CU(cudaMemcpyAsync(c + 64, L->f[L->cur], nf, cudaMemcpyDeviceToHost, L->stream));
+    CU(cudaMemcpyAsync(c + 64 + nf, L->F[L->cur], nF, cudaMemcpyDeviceToHost, L->stream));
+    if (ng) CU(cudaMemcpyAsync(c + 64 + nf + nF, L->g[L->cur], ng, cudaMemcpyDeviceToHost, L->stream));
+    CU(cudaStreamSynchronize(L->stream));
+    *bytes = total;
+    return GOC_OK;
+}
+
+goc_status goc_set_state(goc_lattice *L, const void *buf, size_t bytes) {
+    if (!L || !buf) return fail(GOC_EINVAL, "lattice and buf are required");
+    const char *c = static_cast<const char *>(buf);
+    long long hdr[8];
+    if (bytes < sizeof hdr) return fail(GOC_EINVAL, "state buffer too small");
+    std::memcpy(hdr, c, sizeof hdr);
+    const size_t es = elem_size(L->storage);
+    const size_t nf = 9 * L->plane * es, nF = 2 * L->plane * es, ng = L->mhd.enabled ? 10 * L->plane * es : 0;
+    if (hdr[0] != 0x474f434c4154ll || hdr[1] != L->nx || hdr[2] != L->ny || hdr[3] != L->storage ||
+        hdr[4] != L->mhd.enabled || (size_t)hdr[6] != 64 + nf + nF + ng || bytes < 64 + nf + nF + ng)
+        return fail(GOC_EINVAL, "state does not match this lattice");
+    CU(cudaMemcpyAsync(L->f[L->cur], c + 64, nf, cudaMemcpyHostToDevice, L->stream));
+    CU(cudaMemcpyAsync(L->F[L->cur], c + 64 + nf, nF, cudaMemcpyHostToDevice, L->stream));
+    if (ng) CU(cudaMemcpyAsync(L->g[L->cur], c + 64 + nf + nF, ng, cudaMemcpyHostToDevice, L->stream));
+    CU(cudaStreamSynchronize(L->stream));
+    L->steps = hdr[5];
+    L->fresh = hdr[7] != 0;
+    return GOC_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Batched execution: all resident lattices advance together, one persistent
+// launch per time step and storage type, captured in a CUDA graph.
+// ============================================================================
+struct goc_batch {
+    long long budget = 0, used = 0;
+    int max_lat = 0;
+    int storage = GOC_FP32;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<goc_lattice *> slots;
+    std::vector<long long> bytes;
+    bool dirty = true;
+    // per storage group: params[2][n], tile offsets[n+1]
+    struct Group {
+        int storage = 0, n = 0, total = 0, grid = 0;
+        StepParams *d_params = nullptr;   // [3][n]: parity 0, parity 1, first step after a rebuild
+        int *d_off = nullptr;
+        std::vector<int> members;
+    } groups[3];
+    long long phase = 0;
+    bool first_pending = false;   // next launch uses the first-step parameters (fresh members read in place)
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+constexpr int kBatchGraphSteps = 32;
+
+long long estimate_bytes(const goc_grid *grid, const goc_mhd *mhd, int storage) {
+    const long long pitch = (grid->nx + 31) / 32 * 32;
+    const long long plane = pitch * grid->ny;
+    const long long es = (long long)elem_size(storage);
+    long long b = 2 * (9 + 2) * plane * es;
+    if (mhd && mhd->enabled) b += 2 * 10 * plane * es;
+    b += 7LL * 4 * (grid->nx + grid->ny) + 16LL * (grid->nx + grid->ny + 4) + 128;
+    return b;
+}
+
+void free_groups(goc_batch *B) {
+    for (auto &g : B->groups) {
+        if (g.d_params) cudaFree(g.d_params);
+        if (g.d_off) cudaFree(g.d_off);
+        g.d_params = nullptr;
+        g.d_off = nullptr;
+        g.n = g.total = 0;
+        g.members.clear();
+    }
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+}
+
+template <class S>
+int persistent_grid(int total) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S>, NT, 0);
+    int g = std::max(1, sms * std::max(1, per));
+    return std::min(total, g);
+}
+
+goc_status rebuild(goc_batch *B) {
+    free_groups(B);
+    for (int s = 0; s < 3; s++) B->groups[s].storage = s;
+    for (int k = 0; k < (int)B->slots.size(); k++)
+        if (B->slots[k]) B->groups[B->slots[k]->storage].members.push_back(k);
+    for (auto &g : B->groups) {
+        g.n = (int)g.members.size();
+        if (!g.n) continue;
+        std::vector<StepParams> hp(3 * g.n);
+        std::vector<int> off(g.n + 1, 0);
+        for (int m = 0; m < g.n; m++) {
+            goc_lattice *L = B->slots[g.members[m]];
+            hp[m] = params_for(L, L->cur, nullptr);
+            hp[g.n + m] = params_for(L, L->cur ^ 1, nullptr);
+            hp[2 * g.n + m] = hp[m];
+            hp[2 * g.n + m].nopull = L->fresh ? 1 : 0;
+            off[m + 1] = off[m] + ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
+        }
+        g.total = off[g.n];
+        CU(cudaMalloc(&g.d_params, hp.size() * sizeof(StepParams)));
+        CU(cudaMalloc(&g.d_off, off.size() * sizeof(int)));
+        CU(cudaMemcpyAsync(g.d_params, hp.data(), hp.size() * sizeof(StepParams), cudaMemcpyHostToDevice, B->stream));
+        CU(cudaMemcpyAsync(g.d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+        switch (g.storage) {
+            case GOC_FP16_DEV: g.grid = persistent_grid<__half>(g.total); break;
+            case GOC_BF16_DEV: g.grid = persistent_grid<__nv_bfloat16>(g.total); break;
+            default: g.grid = persistent_grid<float>(g.total); break;
+        }
+    }
+    CU(cudaStreamSynchronize(B->stream));
+    B->phase = 0;
+    B->dirty = false;
+    B->first_pending = true;
+    return GOC_OK;
+}
+
+goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first = false) {
+    for (auto &g : B->groups) {
+        if (!g.n) continue;
+        const StepParams *p = g.d_params + (first ? 2 : ((B->phase + s) & 1)) * g.n;
+        switch (g.storage) {
+            case GOC_FP16_DEV: batch_step_kernel<__half><<<g.grid, dim3(TX, TY), 0, st>>>(p, g.d_off, g.n); break;
+            case GOC_BF16_DEV: batch_step_kernel<__nv_bfloat16><<<g.grid, dim3(TX, TY), 0, st>>>(p, g.d_off, g.n); break;
+            default: batch_step_kernel<float><<<g.grid, dim3(TX, TY), 0, st>>>(p, g.d_off, g.n); break;
+        }
+        CU(cudaGetLastError());
+    }
+    return GOC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+goc_status goc_batch_create(long long hbm_budget_bytes, int max_lattices, const goc_exec *exec, goc_batch **out) {
+    if (!out) return fail(GOC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (hbm_budget_bytes <= 0 || max_lattices <= 0) return fail(GOC_EINVAL, "budget and max_lattices must be > 0");
+    goc_batch *B = new (std::nothrow) goc_batch();
+    if (!B) return fail(GOC_ENOMEM, "host allocation failed");
+    B->budget = hbm_budget_bytes;
+    B->max_lat = max_lattices;
+    if (exec) {
+        B->storage = exec->storage;
+        B->stream = (cudaStream_t)exec->cuda_stream;
+        if (exec->device >= 0) cudaSetDevice(exec->device);
+    }
+    cudaGetDevice(&B->device);
+    B->slots.assign(max_lattices, nullptr);
+    B->bytes.assign(max_lattices, 0);
+    *out = B;
+    return GOC_OK;
+}
+
+void goc_batch_destroy(goc_batch *B) {
+    if (!B) return;
+    cudaStreamSynchronize(B->stream);
+    for (auto *L : B->slots)
+        if (L) free_lattice(L);
+    free_groups(B);
+    delete B;
+}
+
+goc_status goc_batch_add(goc_batch *B, const goc_grid *grid, const goc_map *map, const goc_flow *flow,
+                         const goc_mhd *mhd, int storage, int *slot) {
+    if (!B || !slot) return fail(GOC_EINVAL, "batch and slot are required");
+    *slot = -1;
+    if (!grid) return fail(GOC_EINVAL, "grid is required");
+    int free_slot = -1;
+    for (int k = 0; k < B->max_lat; k++)
+        if (!B->slots[k]) {
+            free_slot = k;
+            break;
+        }
+    if (free_slot < 0) return fail(GOC_EBUSY, "batch is full (%d lattices)", B->max_lat);
+    const long long need = estimate_bytes(grid, mhd, storage);
+    if (B->used + need > B->budget)
+        return fail(GOC_EBUSY, "HBM budget exhausted (%lld + %lld > %lld bytes)", B->used, need, B->budget);
+    goc_exec ex;
+    std::memset(&ex, 0, sizeof ex);
+    ex.storage = storage;
+    ex.cuda_stream = B->stream;
+    ex.device = -1;
+    goc_lattice *L = nullptr;
+    goc_status st = goc_create(grid, map, flow, mhd, &ex, &L);
+    if (st != GOC_OK) return st;
+    L->in_batch = true;
+    B->slots[free_slot] = L;
+    B->bytes[free_slot] = (long long)L->device_bytes;
+    B->used += (long long)L->device_bytes;
+    B->dirty = true;
+    *slot = free_slot;
+    return GOC_OK;
+}
+
+goc_status goc_batch_remove(goc_batch *B, int slot) {
+    if (!B || slot < 0 || slot >= B->max_lat || !B->slots[slot]) return fail(GOC_EINVAL, "no lattice in slot %d", slot);
+    cudaStreamSynchronize(B->stream);
+    B->used -= B->bytes[slot];
+    free_lattice(B->slots[slot]);
+    B->slots[slot] = nullptr;
+    B->bytes[slot] = 0;
+    B->dirty = true;
+    return GOC_OK;
+}
+
+goc_status goc_batch_step(goc_batch *B, long long nsteps) {
+    if (!B) return fail(GOC_EINVAL, "batch is NULL");
+    if (nsteps < 0) return fail(GOC_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return GOC_OK;
+    if (B->dirty) {
+        goc_status st = rebuild(B);
+        if (st != GOC_OK) return st;
+    }
+    bool any = false;
+    for (auto &g : B->groups) any = any || g.n > 0;
+    if (!any) return GOC_OK;
+    if (B->first_pending) {   // first step after a rebuild (parity 0, fresh members unstreamed)
+        goc_status st = batch_launch(B, B->stream, 0, true);
+        if (st != GOC_OK) return st;
+        B->first_pending = false;
+        B->phase += 1;
+        for (auto *L : B->slots)
+            if (L) {
+                L->steps += 1;
+                L->cur ^= 1;
+                L->fresh = false;
+            }
+        if (--nsteps == 0) return GOC_OK;
+    }
+    long long left = nsteps;
+    auto single = [&]() -> goc_status {
+        goc_status st = batch_launch(B, B->stream, 0);
+        B->phase += 1;
+        return st;
+    };
+    if (left >= kBatchGraphSteps && (B->phase & 1)) {   // the graph starts on an even phase
+        goc_status st = single();
+        if (st != GOC_OK) return st;
+        left--;
+    }
+    if (left >= kBatchGraphSteps) {
+        if (!B->graph) {
+            cudaStream_t cs;
+            CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t gr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            goc_status st = GOC_OK;
+            for (int k = 0; k < kBatchGraphSteps && st == GOC_OK && e == cudaSuccess; k++) st = batch_launch(B, cs, k);
+            if (e == cudaSuccess) e = cudaStreamEndCapture(cs, &gr);
+            cudaStreamDestroy(cs);
+            if (st != GOC_OK) return st;
+            if (e != cudaSuccess) return fail(GOC_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&B->graph, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) {
+                B->graph = nullptr;
+                return fail(GOC_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+            }
+        }
+        while (left >= kBatchGraphSteps) {
+            CU(cudaGraphLaunch(B->graph, B->stream));
+            B->phase += kBatchGraphSteps;
+            left -= kBatchGraphSteps;
+        }
+    }
+    while (left > 0) {
+        goc_status st = single();
+        if (st != GOC_OK) return st;
+        left--;
+    }
+    for (auto *L : B->slots)
+        if (L) {
+            L->steps += nsteps;
+            L->cur ^= (int)(nsteps & 1);
+        }
+    return GOC_OK;
+}
+
+goc_status goc_batch_lattice(goc_batch *B, int slot, goc_lattice **lat) {
+    if (!B || !lat || slot < 0 || slot >= B->max_lat || !B->slots[slot]) return fail(GOC_EINVAL, "no lattice in slot %d", slot);
+    *lat = B->slots[slot];
+    return GOC_OK;
+}
+
+goc_status goc_batch_usage(const goc_batch *B, long long *used, long long *budget, int *count) {
+    if (!B) return fail(GOC_EINVAL, "batch is NULL");
+    if (used) *used = B->used;
+    if (budget) *budget = B->budget;
+    if (count) {
+        int c = 0;
+        for (auto *L : B->slots) c += L != nullptr;
+        *count = c;
+    }
+    return GOC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// goc_aux.cuh -- metric precompute (FP64), initial state, moment export and
+// FP64 reductions.
+#pragma once
+
+#include "goc_device.cuh"
+#include "goc_step.cuh"
+
+namespace goc {
+
+// ---- metric factors of one axis in FP64 (Sec. 6; Eq. metricfactor,
+// Eq. curvaturematrix).  Entries 0..n-1 are the nodes, n and n+1 the walls
+// at xi = 0 and xi = n.
+struct MapParams {
+    int kind;          // 0 uniform, 1 tanh2, 2 sine, 3 roberts
+    int n, periodic;
+    double beta, a, gamma, alpha;
+};
+
+__device__ void map_h_theta(const MapParams &m, double xi, double &h, double &th) {
+    const double n = (double)m.n;
+    if (m.kind == 0 || (m.kind == 1 && m.beta == 0.0)) {
+        h = 1.0;
+        th = 0.0;
+    } else if (m.kind == 1) {   // Eq. metriccoefficient with cell-centred nodes, L = n
+        const double arg = m.beta * (2.0 * xi / n - 1.0);
+        const double ch = cosh(arg);
+        const double sech2 = 1.0 / (ch * ch);
+        h = m.beta / tanh(m.beta) * sech2;
+        th = -(4.0 * tanh(m.beta) / n) * tanh(arg) / sech2;
+    } else if (m.kind == 2) {   // periodic sine stretching
+        const double ph = 2.0 * 3.14159265358979323846 * xi / n;
+        h = 1.0 + m.a * cos(ph);
+        th = -m.a * (2.0 * 3.14159265358979323846 / n) * sin(ph) / (h * h);
+    } else {                    // Roberts (Eq. h2_Roberts), lambda = (gamma+1)/(gamma-1)
+        const double lam = (m.gamma + 1.0) / (m.gamma - 1.0);
+        const double s = (xi / n - m.alpha) / (1.0 - m.alpha);
+        const double ls = pow(lam, s);
+        h = (2.0 * m.gamma / (2.0 * m.alpha + 1.0)) * log(lam) / (1.0 - m.alpha) * ls / ((1.0 + ls) * (1.0 + ls));
+        th = (1.0 / n) * ((1.0 + 2.0 * m.alpha) / (2.0 * m.gamma)) * (1.0 / ls - ls);
+    }
+}
+
+__global__ void metric_axis_kernel(MapParams m, double *h, double *th) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m.n + 2) return;
+    double xi;
+    if (k < m.n) xi = m.periodic ? (double)k : (double)k + 0.5;
+    else xi = (k == m.n) ? 0.0 : (double)m.n;
+    double hv, tv;
+    map_h_theta(m, xi, hv, tv);
+    h[k] = hv;
+    th[k] = tv;
+}
+
+// q = min over the nodes of both axes (Eq. GOC-LBE_CFL): one block.
+__global__ void min_h_kernel(const double *h1, int n1, const double *h2, int n2, double *q) {
+    __shared__ double red[32];
+    double v = 1e300;
+    for (int k = threadIdx.x; k < n1; k += blockDim.x) v = fmin(v, h1[k]);
+    for (int k = threadIdx.x; k < n2; k += blockDim.x) v = fmin(v, h2[k]);
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 1e300;
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) *q = v;
+    }
+}
+
+// FP32 tables of one axis from the FP64 metric: h, 1/h, theta, the pull
+// corrections of the storage reference (see goc_step.cuh)
+//   rm[k] = rho0 cs2 [ (1/h(k-1) - 1/h(k))/2 - (theta(k-1) + theta(k))/4 ],
+//   rp[k] = rho0 cs2 [ (1/h(k+1) - 1/h(k))/2 + (theta(k+1) + theta(k))/4 ],
+// and the MIE pull corrections (multiplied by B_rest and the other axis' h)
+//   dm[k] = W1 (h(k-1) - h(k)) + csm2 (h^2 theta(k-1) + h^2 theta(k))/4,
+//   dp[k] = W1 (h(k+1) - h(k)) - csm2 (h^2 theta(k+1) + h^2 theta(k))/4, W1 = csm2/2.
+// Entries whose neighbour lies beyond a wall are never used (that link
+// bounces back) and are set to 0.
+__global__ void axis_tables_kernel(const double *h, const double *th, int n, int periodic,
+                                   double rho0cs2, double csm2, float *out /* [7][n] */) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const bool has_m = periodic || k > 0, has_p = periodic || k < n - 1;
+    const int km = periodic ? (k - 1 + n) % n : (k > 0 ? k - 1 : k);
+    const int kp = periodic ? (k + 1) % n : (k < n - 1 ? k + 1 : k);
+    out[0 * n + k] = (float)h[k];
+    out[1 * n + k] = (float)(1.0 / h[k]);
+    out[2 * n + k] = (float)th[k];
+    out[3 * n + k] = has_m ? (float)(rho0cs2 * (0.5 * (1.0 / h[km] - 1.0 / h[k]) - 0.25 * (th[km] + th[k]))) : 0.f;
+    out[4 * n + k] = has_p ? (float)(rho0cs2 * (0.5 * (1.0 / h[kp] - 1.0 / h[k]) + 0.25 * (th[kp] + th[k]))) : 0.f;
+    const double W1 = 0.5 * csm2;
+    const double ht = h[k] * h[k] * th[k], htm = h[km] * h[km] * th[km], htp = h[kp] * h[kp] * th[kp];
+    out[5 * n + k] = has_m ? (float)(W1 * (h[km] - h[k]) + 0.25 * csm2 * (htm + ht)) : 0.f;
+    out[6 * n + k] = has_p ? (float)(W1 * (h[kp] - h[k]) - 0.25 * csm2 * (htp + ht)) : 0.f;
+}
+
+// ---- initial state (Appendix C.1): f = P^-1 m^eq,eff(rho, U), gradients by
+// the same second-order differences as the step; g = g^eq(0) + g^corr.
+// FP64 arithmetic (one-off).  Fields are [ny][nx] doubles on the device.
+struct InitParams {
+    StepParams sp;
+    const double *h1d, *h2d, *t1d, *t2d;   // FP64 node metric per axis
+    double cs2, nu, zeta, rho0, csm2, eta;
+    int gi, mhd;
+    const double *rho, *u1, *u2, *b1, *b2;
+};
+
+__device__ double dfd64(const double *phi, int i, int j, int nx, int ny, int axis, int per) {
+    auto at = [&](int ii, int jj) { return phi[(long long)jj * nx + ii]; };
+    const int k = axis == 0 ? i : j, n = axis == 0 ? nx : ny;
+    auto nb = [&](int off) {
+        int kk = k + off;
+        if (per) kk = ((kk % n) + n) % n;
+        return axis == 0 ? at(kk, j) : at(i, kk);
+    };
+    if (per || (k > 0 && k < n - 1)) return 0.5 * (nb(1) - nb(-1));
+    if (k == 0) return 0.5 * (-3.0 * nb(0) + 4.0 * nb(1) - nb(2));
+    return 0.5 * (3.0 * nb(0) - 4.0 * nb(-1) + nb(-2));
+}
+
+template <class S>
+__global__ void init_kernel(const InitParams q) {
+    const StepParams &p = q.sp;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx || j >= p.ny) return;
+    const long long n = (long long)j * p.nx + i, idx = (long long)j * p.pitch + i;
+    const double h1 = q.h1d[i], h2 = q.h2d[j], t11 = q.t1d[i], t22 = q.t2d[j];
+    const double rho = q.rho[n], U1 = q.u1[n], U2 = q.u2[n];
+    const double dU1 = dfd64(q.u1, i, j, p.nx, p.ny, 0, p.per_x);
+    const double dU2 = dfd64(q.u2, i, j, p.nx, p.ny, 1, p.per_y);
+    const double dr1 = dfd64(q.rho, i, j, p.nx, p.ny, 0, p.per_x);
+    const double dr2 = dfd64(q.rho, i, j, p.nx, p.ny, 1, p.per_y);
+    const double cs2 = q.cs2, nu = q.nu, ze = q.zeta;
+    const double gi = q.gi ? 1.0 : 0.0;
+    const double a1 = gi * U1 * U1 / cs2, a2 = gi * U2 * U2 / cs2;
+    // Eqs. 83 / 85 on a straight grid (theta12 = theta21 = 0)
+    const double D31 = rho * (2 * ze - (ze + nu) * h2 / (h1 * h1) - (ze - nu) / h2
+                              - ze * (2 - h2 / cs2 + (3 * a1 + 1) * h2 / (h1 * h1)));
+    const double D32 = rho * (2 * ze - (ze + nu) * h1 / (h2 * h2) - (ze - nu) / h1
+                              - ze * (2 - h1 / cs2 + (3 * a2 + 1) * h1 / (h2 * h2)));
+    const double D33 = -ze * ((3 - a1) * h2 / (h1 * h1) - h2 / cs2 - a2 / h2) * U1;
+    const double D34 = -ze * ((3 - a2) * h1 / (h2 * h2) - h1 / cs2 - a1 / h1) * U2;
+    const double C3 = rho * ze * (2 * U1 * (a1 + 1) * h2 / h1 * t11 + 2 * U2 * (a2 + 1) * h1 / h2 * t22);
+    const double D41 = rho * (2 * nu - (ze + nu) * h2 / (h1 * h1) + (ze - nu) / h2
+                              - nu * (2 - h2 / cs2 + (3 * a1 + 1) * h2 / (h1 * h1)));
+    const double D42 = rho * (-2 * nu + (ze + nu) * h1 / (h2 * h2) - (ze - nu) / h1
+                              - nu * (-2 + h1 / cs2 - (3 * a2 + 1) * h1 / (h2 * h2)));
+    const double D43 = -nu * ((3 - a1) * h2 / (h1 * h1) - h2 / cs2 + a2 / h2) * U1;
+    const double D44 = -nu * (-(3 - a2) * h1 / (h2 * h2) + h1 / cs2 - a1 / h1) * U2;
+    const double C4 = rho * nu * (2 * U1 * (a1 + 1) * h2 / h1 * t11 - 2 * U2 * (a2 + 1) * h1 / h2 * t22);
+    const double n3 = D31 * dU1 + D32 * dU2 + D33 * dr1 + D34 * dr2 + C3;
+    const double n4 = D41 * dU1 + D42 * dU2 + D43 * dr1 + D44 * dr2 + C4;
+    // m^eq,eff - m_rest(rho0), bare order (Eq. GOCmomentequilibria)
+    const double r = h2 / h1, s = h1 / h2, H = h1 * h2;
+    const double k2s = r * rho * U1 * U1 + s * rho * U2 * U2 + (r + s) * rho * cs2 + n3;
+    const double k2d = r * rho * U1 * U1 - s * rho * U2 * U2 + (r - s) * rho * cs2 + n4;
+    const double m0 = H * (rho - q.rho0);
+    const double m1 = h2 * rho * U1, m2 = h1 * rho * U2;
+    const double m3 = 0.5 * (k2s + k2d) - r * q.rho0 * cs2;
+    const double m4 = 0.5 * (k2s - k2d) - s * q.rho0 * cs2;
+    const double m5 = rho * U1 * U2;
+    const double m6 = rho * (cs2 + U1 * U1) * U2 / h1;
+    const double m7 = rho * (cs2 + U2 * U2) * U1 / h2;
+    const double m8 = rho * cs2 * cs2 + rho * cs2 * (U1 * U1 + U2 * U2) + rho * U1 * U1 * U2 * U2
+                      - q.rho0 * cs2 * cs2;
+    double d[9];
+    d[0] = m0 - m3 - m4 + m8;
+    d[1] = 0.5 * (m1 + m3 - m7 - m8);
+    d[2] = 0.5 * (m2 + m4 - m6 - m8);
+    d[3] = 0.5 * (-m1 + m3 + m7 - m8);
+    d[4] = 0.5 * (-m2 + m4 + m6 - m8);
+    d[5] = 0.25 * (m5 + m6 + m7 + m8);
+    d[6] = 0.25 * (-m5 + m6 - m7 + m8);
+    d[7] = 0.25 * (m5 - m6 - m7 + m8);
+    d[8] = 0.25 * (-m5 - m6 + m7 + m8);
+    // pre-collision reference f_ref- = f_rest - F_rest/4 on links 1, 3 (xi1) and 2, 4 (xi2)
+    const double F1r = -h2 * q.rho0 * cs2 * t11, F2r = -h1 * q.rho0 * cs2 * t22;
+    d[1] += 0.25 * F1r;
+    d[3] -= 0.25 * F1r;
+    d[2] += 0.25 * F2r;
+    d[4] -= 0.25 * F2r;
+    S *fout = static_cast<S *>(p.fout);
+    for (int a = 0; a < 9; a++) Store<S>::st(fout + a * p.plane + idx, (float)(d[a] * p.isf));
+    S *Fout = static_cast<S *>(p.Fout);   // F^{-1} = 0, i.e. F_dev = -F_rest
+    Store<S>::st(Fout + idx, (float)(h2 * q.rho0 * cs2 * t11 * p.isF));
+    Store<S>::st(Fout + p.plane + idx, (float)(h1 * q.rho0 * cs2 * t22 * p.isF));
+    if (!q.mhd) return;
+    S *gout = static_cast<S *>(p.gout);
+    const double B[2] = {q.b1[n], q.b2[n]}, U[2] = {U1, U2};
+    const double *Bf[2] = {q.b1, q.b2};
+    for (int c = 0; c < 2; c++) {
+        const double dB1 = dfd64(Bf[c], i, j, p.nx, p.ny, 0, p.per_x);
+        const double dB2 = dfd64(Bf[c], i, j, p.nx, p.ny, 1, p.per_y);
+        const double A1 = U1 * B[c] - B[0] * U[c], A2 = U2 * B[c] - B[1] * U[c];
+        const double lc1 = q.eta * (H - h2 / h1) * dB1 + q.eta * h1 * H * t11 * B[c];
+        const double lc2 = q.eta * (H - h1 / h2) * dB2 + q.eta * H * h2 * t22 * B[c];
+        // relative to the pre-collision reference g_ref- = W H B_rest - e.M/2 with
+        // M = csm2/2 (h1 H theta11, H h2 theta22) B_rest
+        const double M1 = 0.5 * q.csm2 * h1 * H * t11 * p.brest[c], M2 = 0.5 * q.csm2 * H * h2 * t22 * p.brest[c];
+        for (int a = 0; a < 5; a++) {
+            const double W = a == 0 ? 1.0 - 2.0 * q.csm2 : 0.5 * q.csm2;
+            const double geq = W * (H * (B[c] - p.brest[c]) + g1(a) * (h2 * A1 + lc1) / q.csm2
+                                    + g2(a) * (h1 * A2 + lc2) / q.csm2)
+                               + 0.5 * (g1(a) * M1 + g2(a) * M2);
+            Store<S>::st(gout + (c * 5 + a) * p.plane + idx, (float)(geq * p.isg));
+        }
+    }
+}
+
+// ---- macroscopic fields of the current state (FP64 output [5][ny][nx]) ----
+template <class S, bool MHD>
+__global__ void moments_kernel(const StepParams p, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx || j >= p.ny) return;
+    const float h1 = p.ax1.h[i], h2 = p.ax2.h[j];
+    float d[9];
+    pull_node<S>(p, i, j, h1, h2, d);
+    const long long idx = (long long)j * p.pitch + i;
+    const S *Fin = static_cast<const S *>(p.Fin);
+    const float F1p = Store<S>::ld(Fin + idx) * p.sF;   // F - F_rest of the previous step
+    const float F2p = Store<S>::ld(Fin + p.plane + idx) * p.sF;
+    float drho, U1, U2;
+    fields_from(p, d, F1p, F2p, h1, h2, drho, U1, U2);
+    const long long N = (long long)p.nx * p.ny, n = (long long)j * p.nx + i;
+    out[n] = (double)p.rho0 + (double)drho;
+    out[N + n] = U1;
+    out[2 * N + n] = U2;
+    double B1 = 0.0, B2 = 0.0;
+    if constexpr (MHD) {
+        float gd[5];
+        pull_mie<S>(p, i, j, h1, h2, 0, gd);
+        B1 = (double)p.brest[0] + (double)((gd[0] + gd[1] + gd[2] + gd[3] + gd[4]) / (h1 * h2));
+        pull_mie<S>(p, i, j, h1, h2, 1, gd);
+        B2 = (double)p.brest[1] + (double)((gd[0] + gd[1] + gd[2] + gd[3] + gd[4]) / (h1 * h2));
+    }
+    out[3 * N + n] = B1;
+    out[4 * N + n] = B2;
+}
+
+// ---- FP64 reductions ---------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int K>
+__device__ void block_add(double (&v)[K], double *dst) {
+    __shared__ double red[K][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) red[k][w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double s = lane < (int)(blockDim.x >> 5) ? red[k][lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) atomicAdd(dst + k, s);
+        }
+    }
+}
+
+// Total mass sum_nodes sum_a f (= sum h1 h2 rho): post-collision deviations
+// plus h1 h2 rho0 per node (mass is a collision invariant).
+template <class S>
+__global__ void mass_kernel(const StepParams p, double *out) {
+    double acc[1] = {0.0};
+    const long long N = (long long)p.nx * p.ny;
+    const S *f = static_cast<const S *>(p.fin);
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(n / p.nx), i = (int)(n - (long long)j * p.nx);
+        const long long idx = (long long)j * p.pitch + i;
+        double s = 0.0;
+        for (int a = 0; a < 9; a++) s += (double)Store<S>::ld(f + a * p.plane + idx) * p.sf;
+        acc[0] += s + (double)p.ax1.h[i] * (double)p.ax2.h[j] * p.rho0;
+    }
+    block_add<1>(acc, out);
+}
+
+// Residual sums between two field snapshots [4][plane]: |dU|^2, |U|^2, |dB|^2, |B|^2.
+__global__ void residual_kernel(const float *a, const float *b, long long plane, int nx, int ny,
+                                int pitch, double *out) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long N = (long long)nx * ny;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(n / nx), i = (int)(n - (long long)j * nx);
+        const long long idx = (long long)j * pitch + i;
+        const double u1 = b[idx], u2 = b[plane + idx], B1 = b[2 * plane + idx], B2 = b[3 * plane + idx];
+        const double du1 = u1 - a[idx], du2 = u2 - a[plane + idx];
+        const double dB1 = B1 - a[2 * plane + idx], dB2 = B2 - a[3 * plane + idx];
+        acc[0] += du1 * du1 + du2 * du2;
+        acc[1] += u1 * u1 + u2 * u2;
+        acc[2] += dB1 * dB1 + dB2 * dB2;
+        acc[3] += B1 * B1 + B2 * B2;
+    }
+    block_add<4>(acc, out);
+}
+
+}  // namespace goc

@@ -1,0 +1,90 @@
+// goc_device.cuh -- device-side data structures and helpers of the GOC-LBM
+// kernels (sm_103a).  All arithmetic of the time step is FP32; the metric
+// precompute and the reductions use FP64.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace goc {
+
+// D2Q9 velocities (Eq. 1a/1b) and D2Q5 velocities (Eq. D2Q5a/b).
+__host__ __device__ constexpr int e1(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
+__host__ __device__ constexpr int e2(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
+__host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5); }
+__host__ __device__ constexpr int g1(int a) { return a == 1 ? 1 : (a == 3 ? -1 : 0); }
+__host__ __device__ constexpr int g2(int a) { return a == 2 ? 1 : (a == 4 ? -1 : 0); }
+__host__ __device__ constexpr int gopp(int a) { return a == 0 ? 0 : ((a + 1) & 3) + 1; }
+
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp");
+
+enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
+
+// Per-axis FP32 tables (straight grids: h1 = h1(xi1), h2 = h2(xi2)).
+struct Axis {
+    const float *h;    // metric factor at the nodes
+    const float *ih;   // 1/h
+    const float *th;   // theta_kk = h'/h^2
+    const float *rm;   // rest-state pull correction, source k-1: 0.5 rho0 cs2 (1/h(k-1) - 1/h(k))
+    const float *rp;   // rest-state pull correction, source k+1: 0.5 rho0 cs2 (1/h(k+1) - 1/h(k))
+    const float *dm;   // MIE pull corrections, source k-1: W1 (h(k-1) - h(k)) + csm2 (h^2 theta(k-1) + h^2 theta(k))/4
+    const float *dp;   //                      source k+1: W1 (h(k+1) - h(k)) - csm2 (h^2 theta(k+1) + h^2 theta(k))/4
+};
+
+// Everything one step needs, passed by value.
+struct StepParams {
+    int nx, ny, pitch;         // pitch in elements (multiple of 32)
+    long long plane;           // ny * pitch
+    int per_x, per_y;          // periodic axes
+    int nopull;                // 1: the input buffer holds pre-collision populations (the
+                               // initial state f^0 of Appendix C.1): read them in place
+    const void *fin;           // [9][plane] stored post-collision deviations (input)
+    void *fout;                // [9][plane] (output)
+    const void *Fin;           // [2][plane] stored effective force of the previous step
+    void *Fout;
+    const void *gin;           // [10][plane] MIE vector populations (component-major)
+    void *gout;
+    Axis ax1, ax2;
+    float rho0, cs2, nu, zeta;
+    float om[9];
+    float fext1, fext2;
+    float gi;                  // 1: full correction coefficients, 0: cubic terms dropped
+    float uw[4];               // tangential wall velocity per side
+    float hwn[4];              // wall-normal metric factor at each wall (W/E: h1, S/N: h2)
+    int moving;                // any moving wall
+    float sf, isf;             // population storage scale and its inverse (1 for FP32)
+    float sF, isF;             // force storage scale
+    float sg, isg;             // MIE storage scale
+    // MIE (Appendix G)
+    float csm2, icsm2, taum, itaum, eta, imum, W0, W1;
+    float brest[2];            // reference (storage) field
+    float bw[4][2];            // wall fields
+    // optional outputs
+    float *uout;               // [4][plane]: U1, U2, B1, B2 of this step's time level (may be null)
+    int *flag;                 // divergence flag (may be null)
+};
+
+// ---- storage formats ------------------------------------------------------
+template <class S> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+__device__ __forceinline__ int wrapi(int k, int n) {
+    k %= n;
+    return k < 0 ? k + n : k;
+}
+
+}  // namespace goc

@@ -1,0 +1,175 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import goc_inputs as gi
+import oracle
+import paper_2607_15362_b300 as goc
+
+pytestmark = pytest.mark.gpu
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_pair(spec, steps, storage="fp32", threads=8):
+    o = oracle.Oracle(spec, threads=threads)
+    L = goc.Lattice(spec, storage=storage)
+    o.step(steps)
+    L.step(steps)
+    return o, L, o.fields(), L.moments()
+
+
+def cs2_of(problem):
+    return oracle.build_metric(problem.lattice_spec(1.0)).cs2()
+
+
+def test_library_cs_rule_matches_the_oracle(gpu):
+    for p in (gi.cfg1_poiseuille(), gi.cfg2_cavity(), gi.cfg3_hartmann()):
+        spec = p.lattice_spec(1.0)
+        q, cs2 = goc.metric_info(spec)
+        m = oracle.build_metric(spec)
+        assert q == pytest.approx(m.q(), rel=1e-14)
+        assert cs2 == pytest.approx(m.cs2(), rel=1e-14)
+
+
+def test_cfg1_poiseuille_fp32_matches_the_oracle(gpu):
+    """cfg1 (32 x 64, tanh beta = 1.5, Re = 10): FP32 velocity relative L2
+    <= 1e-5 after 1000 and after 2000 steps."""
+    p = gi.cfg1_poiseuille()
+    spec = p.lattice_spec(cs2_of(p))
+    o = oracle.Oracle(spec, threads=8)
+    L = goc.Lattice(spec)
+    for n in (1000, 1000):
+        o.step(n)
+        L.step(n)
+        ro, uo, vo, *_ = o.fields()
+        rg, ug, vg, *_ = L.moments()
+        assert relerr(np.stack([ug, vg]), np.stack([uo, vo])) <= 1e-5
+        assert np.abs(rg - ro).max() <= 1e-6
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 12), (37, 29), (64, 48)])
+def test_cavity_fp32_matches_the_oracle_on_ragged_tiles(gpu, nx, ny):
+    """Walls on all sides, moving lid, tanh clustering on both axes; sizes that
+    leave ragged tiles in x and y."""
+    prob = gi.Problem("cavity", nx, ny, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
+                      {"Re": 100.0, "u_lid": 0.05})
+    spec = prob.lattice_spec(cs2_of(prob))
+    o, L, fo, fg = run_pair(spec, 1000)
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+
+
+def test_stretched_periodic_vortex_fp32_matches_the_oracle(gpu):
+    """Sine-stretched periodic grid with a random smooth initial field: every
+    correction term (Eqs. 82-85) and both geometric forces are active."""
+    u1, u2 = gi.random_periodic_fields(40, 24, seed=3, amp=0.03)
+    spec = dict(nx=40, ny=24, map1={"kind": "sine", "a": 0.3}, map2={"kind": "sine", "a": -0.25},
+                walls={"W": None, "E": None, "S": None, "N": None}, tau=0.7, tau_zeta=0.8,
+                fext=(1e-6, -2e-6), init={"u1": u1, "u2": u2})
+    o, L, fo, fg = run_pair(spec, 500)
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+
+
+def test_hartmann_strip_fp32_matches_the_oracle(gpu):
+    """Coupled NSE + MIE (Appendix G) on a wall-normal tanh grid: FP32 velocity
+    and induced field within 1e-5 relative L2 after 1000 steps; the induced
+    field's FP32 rounding drift stays below 5e-5 at 3000 steps."""
+    prob = gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
+                      {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0})
+    spec = prob.lattice_spec(cs2_of(prob))
+    B0 = spec["derived"]["B0"]
+    o = oracle.Oracle(spec, threads=8)
+    L = goc.Lattice(spec)
+    for n, tol_b in ((1000, 1e-5), (3000, 5e-5)):
+        o.step(n - o.steps_done)
+        L.step(n - L.steps_done)
+        fo, fg = o.fields(), L.moments()
+        assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+        assert relerr(fg[3], fo[3]) <= tol_b
+        assert np.abs(fg[4] - fo[4]).max() <= 1e-6 * B0
+
+
+def test_mass_is_conserved_on_the_gpu(gpu):
+    prob = gi.Problem("cavity", 48, 40, {"kind": "tanh2", "beta": 1.5}, {"kind": "tanh2", "beta": 1.5},
+                      {"Re": 200.0, "u_lid": 0.05})
+    spec = prob.lattice_spec(cs2_of(prob))
+    L = goc.Lattice(spec)
+    m0 = L.mass()
+    L.step(2000)
+    assert abs(L.mass() - m0) / m0 < 1e-6
+
+
+def test_checkpoint_restore_is_bitwise(gpu):
+    p = gi.cfg1_poiseuille()
+    spec = p.lattice_spec(cs2_of(p))
+    a = goc.Lattice(spec)
+    a.step(150)
+    st = a.get_state()
+    a.step(130)
+    b = goc.Lattice(spec)
+    b.set_state(st)
+    b.step(130)
+    for x, y in zip(a.moments(), b.moments()):
+        np.testing.assert_array_equal(x, y)
+    assert b.steps_done == 280
+
+
+def _mixed_specs():
+    out = []
+    for prob in (gi.cfg1_poiseuille(),
+                 gi.Problem("cavity", 37, 29, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
+                            {"Re": 100.0, "u_lid": 0.05}),
+                 gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
+                            {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0})):
+        out.append(prob.lattice_spec(cs2_of(prob)))
+    return out
+
+
+def test_batched_lattices_match_individual_runs_bitwise(gpu):
+    """One persistent launch per step over uneven lattices (NSE and NSE+MIE
+    mixed) gives bitwise the same FP32 result as each lattice alone."""
+    specs = _mixed_specs()
+    batch = goc.Batch(hbm_budget_bytes=1 << 30, max_lattices=8)
+    slots = [batch.add(s) for s in specs]
+    batch.step(1)
+    batch.step(150)      # graph part (32-step graphs) plus remainder, odd phase start
+    batch.step(49)
+    for spec, slot in zip(specs, slots):
+        alone = goc.Lattice(spec)
+        alone.step(200)
+        for x, y in zip(batch.lattice(slot).moments(), alone.moments()):
+            np.testing.assert_array_equal(x, y)
+    # a late admission joins the running batch and still matches its own run
+    late = batch.add(specs[1])
+    batch.step(70)
+    alone = goc.Lattice(specs[1])
+    alone.step(70)
+    for x, y in zip(batch.lattice(late).moments(), alone.moments()):
+        np.testing.assert_array_equal(x, y)
+    used, budget, count = batch.usage()
+    assert count == 4 and 0 < used <= budget
+    batch.close()
+
+
+def test_batch_admission_respects_the_hbm_budget(gpu):
+    specs = _mixed_specs()
+    batch = goc.Batch(hbm_budget_bytes=200_000, max_lattices=8)
+    assert batch.try_add(specs[0]) is not None      # 32 x 64 fits
+    assert batch.try_add(gi.cfg2_cavity().lattice_spec(0.007)) is None   # 512^2 does not
+    batch.close()
+
+
+def test_run_until_reaches_the_residual_and_reports_it(gpu):
+    prob = gi.Problem("poiseuille", 2, 24, {"kind": "uniform"}, {"kind": "tanh2", "beta": 1.0},
+                      {"Re": 5.0, "tau": 1.0})
+    spec = prob.lattice_spec(cs2_of(prob))
+    L = goc.Lattice(spec, check_every=200)
+    done, res = L.run_until(1e-7, 400000)
+    assert res < 1e-7 and 0 < done < 400000
+    assert L.residuals()[0] == pytest.approx(res)
