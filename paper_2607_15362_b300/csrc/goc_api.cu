@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -79,15 +80,92 @@ struct goc_lattice {
     bool owns_stream = false;
     bool in_batch = false;                       // stepped only through goc_batch_step
     bool fresh = false;                          // buffer holds f^0 (pre-collision): next step reads in place
+    CUtensorMap tmf[2], tmF[2], tmg[2];          // TMA descriptors of both buffers
+    bool tma_ok = false;
 };
 
 namespace {
 
+// ---- TMA descriptors -------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3D map [planes][ny][nx] of a population buffer (row pitch `pitch` elements),
+// box [planes][by][bx]; out-of-range elements read as zero.
+bool encode_planes(CUtensorMap *m, int storage, void *base, int nx, int ny, int pitch, int planes, int bx, int by) {
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc || !base) return false;
+    const cuuint64_t es = storage == GOC_FP32 ? 4 : 2;
+    const CUtensorMapDataType dt = storage == GOC_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : storage == GOC_FP16_DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)pitch * ny * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class S>
+bool encode_lattice_maps(goc_lattice *L) {
+    using T = Tiling<S>;
+    bool ok = true;
+    for (int b = 0; b < 2; b++) {
+        ok = ok && encode_planes(&L->tmf[b], L->storage, L->f[b], L->nx, L->ny, L->pitch, 9, T::BX, T::BY);
+        ok = ok && encode_planes(&L->tmF[b], L->storage, L->F[b], L->nx, L->ny, L->pitch, 2, T::BX, T::BY);
+        if (L->mhd.enabled)
+            ok = ok && encode_planes(&L->tmg[b], L->storage, L->g[b], L->nx, L->ny, L->pitch, 10, T::BX, T::BYG);
+    }
+    return ok;
+}
+
+// Dynamic shared memory of a step kernel and its persistent grid size.
+template <class S, bool MHD>
+int step_grid(int ntiles, size_t *smem) {
+    using T = Tiling<S>;
+    const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
+    *smem = bytes;
+    static int cached = -1;
+    if (cached < 0) {
+        cudaFuncSetAttribute(step_kernel<S, MHD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD>, NT, bytes);
+        cached = std::max(1, sms * std::max(1, per));
+    }
+    return std::min(ntiles, cached);
+}
+
 template <class S>
 goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
-    dim3 grid((L->nx + TX - 1) / TX, (L->ny + TY - 1) / TY), block(TX, TY);
-    if (L->mhd.enabled) step_kernel<S, true><<<grid, block, 0, L->stream>>>(p);
-    else step_kernel<S, false><<<grid, block, 0, L->stream>>>(p);
+    const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
+    size_t smem = 0;
+    if (L->mhd.enabled) {
+        const int grid = step_grid<S, true>(ntiles, &smem);
+        step_kernel<S, true><<<grid, dim3(TX, TY), smem, L->stream>>>(p);
+    } else {
+        const int grid = step_grid<S, false>(ntiles, &smem);
+        step_kernel<S, false><<<grid, dim3(TX, TY), smem, L->stream>>>(p);
+    }
     CU(cudaGetLastError());
     return GOC_OK;
 }
@@ -101,6 +179,12 @@ StepParams params_for(goc_lattice *L, int src, float *uout) {
     p.gin = L->g[src];
     p.gout = L->g[src ^ 1];
     p.uout = uout;
+    p.use_tma = L->tma_ok ? 1 : 0;
+    if (L->tma_ok) {
+        p.tm_f = L->tmf[src];
+        p.tm_F = L->tmF[src];
+        if (L->mhd.enabled) p.tm_g = L->tmg[src];
+    }
     return p;
 }
 
@@ -483,6 +567,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     p.ax2 = axis(L->tab2, L->ny);
     p.rho0 = (float)L->flow.rho0;
     p.cs2 = (float)L->cs2;
+    p.ics2 = (float)(1.0 / L->cs2);
     p.nu = (float)L->nu;
     p.zeta = (float)L->zeta;
     for (int k = 0; k < 9; k++) p.om[k] = (float)L->flow.omega_free;
@@ -507,8 +592,8 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         double sf = L->flow.rho0 * uref * hmax / 256.0;
         p.sf = (float)sf;
         p.isf = (float)(1.0 / sf);
-        p.sF = (float)(sf * 1e-3);
-        p.isF = (float)(1.0 / (sf * 1e-3));
+        p.sF = (float)sf;   // the stored force deviation starts at h rho0 cs2 theta (F = 0 before step 1)
+        p.isF = (float)(1.0 / sf);
         p.sg = (float)sf;
         p.isg = (float)(1.0 / sf);
     }
@@ -530,6 +615,12 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         }
     }
     p.flag = L->flag;
+    switch (L->storage) {
+        case GOC_FP16_DEV: L->tma_ok = encode_lattice_maps<__half>(L); break;
+        case GOC_BF16_DEV: L->tma_ok = encode_lattice_maps<__nv_bfloat16>(L); break;
+        default: L->tma_ok = encode_lattice_maps<float>(L); break;
+    }
+    if (std::getenv("GOC_DISABLE_TMA")) L->tma_ok = false;
     TRY(run_init(L, nullptr, nullptr, nullptr, nullptr, nullptr));
     {
         cudaError_t e = cudaMemsetAsync(L->flag, 0, sizeof(int), L->stream);
@@ -758,6 +849,7 @@ struct goc_batch {
         int storage = 0, n = 0, total = 0, grid = 0;
         StepParams *d_params = nullptr;   // [3][n]: parity 0, parity 1, first step after a rebuild
         int *d_off = nullptr;
+        int stage_bytes = 0;
         std::vector<int> members;
     } groups[3];
     long long phase = 0;
@@ -793,13 +885,25 @@ void free_groups(goc_batch *B) {
 }
 
 template <class S>
-int persistent_grid(int total) {
+int persistent_grid(int total, int stage_bytes) {
+    using T = Tiling<S>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(batch_step_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T::STAGE_MHD);
+        attr = true;
+    }
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S>, NT, 2 * (size_t)stage_bytes);
     int g = std::max(1, sms * std::max(1, per));
     return std::min(total, g);
+}
+
+template <class S>
+int stage_bytes_for(bool any_mhd) {
+    using T = Tiling<S>;
+    return any_mhd ? T::STAGE_MHD : T::STAGE_NSE;
 }
 
 goc_status rebuild(goc_batch *B) {
@@ -821,14 +925,25 @@ goc_status rebuild(goc_batch *B) {
             off[m + 1] = off[m] + ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
         }
         g.total = off[g.n];
+        bool any_mhd = false;
+        for (int m = 0; m < g.n; m++) any_mhd = any_mhd || B->slots[g.members[m]]->mhd.enabled;
         CU(cudaMalloc(&g.d_params, hp.size() * sizeof(StepParams)));
         CU(cudaMalloc(&g.d_off, off.size() * sizeof(int)));
         CU(cudaMemcpyAsync(g.d_params, hp.data(), hp.size() * sizeof(StepParams), cudaMemcpyHostToDevice, B->stream));
         CU(cudaMemcpyAsync(g.d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream));
         switch (g.storage) {
-            case GOC_FP16_DEV: g.grid = persistent_grid<__half>(g.total); break;
-            case GOC_BF16_DEV: g.grid = persistent_grid<__nv_bfloat16>(g.total); break;
-            default: g.grid = persistent_grid<float>(g.total); break;
+            case GOC_FP16_DEV:
+                g.stage_bytes = stage_bytes_for<__half>(any_mhd);
+                g.grid = persistent_grid<__half>(g.total, g.stage_bytes);
+                break;
+            case GOC_BF16_DEV:
+                g.stage_bytes = stage_bytes_for<__nv_bfloat16>(any_mhd);
+                g.grid = persistent_grid<__nv_bfloat16>(g.total, g.stage_bytes);
+                break;
+            default:
+                g.stage_bytes = stage_bytes_for<float>(any_mhd);
+                g.grid = persistent_grid<float>(g.total, g.stage_bytes);
+                break;
         }
     }
     CU(cudaStreamSynchronize(B->stream));
@@ -842,10 +957,17 @@ goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first =
     for (auto &g : B->groups) {
         if (!g.n) continue;
         const StepParams *p = g.d_params + (first ? 2 : ((B->phase + s) & 1)) * g.n;
+        const size_t smem = 2 * (size_t)g.stage_bytes;
         switch (g.storage) {
-            case GOC_FP16_DEV: batch_step_kernel<__half><<<g.grid, dim3(TX, TY), 0, st>>>(p, g.d_off, g.n); break;
-            case GOC_BF16_DEV: batch_step_kernel<__nv_bfloat16><<<g.grid, dim3(TX, TY), 0, st>>>(p, g.d_off, g.n); break;
-            default: batch_step_kernel<float><<<g.grid, dim3(TX, TY), 0, st>>>(p, g.d_off, g.n); break;
+            case GOC_FP16_DEV:
+                batch_step_kernel<__half><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n, g.stage_bytes);
+                break;
+            case GOC_BF16_DEV:
+                batch_step_kernel<__nv_bfloat16><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n, g.stage_bytes);
+                break;
+            default:
+                batch_step_kernel<float><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n, g.stage_bytes);
+                break;
         }
         CU(cudaGetLastError());
     }

@@ -215,15 +215,13 @@ __global__ void moments_kernel(const StepParams p, double *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= p.nx || j >= p.ny) return;
+    const SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
+                           p.plane, p.pitch, p.sf, p.sF, p.sg};
     const float h1 = p.ax1.h[i], h2 = p.ax2.h[j];
     float d[9];
-    pull_node<S>(p, i, j, h1, h2, d);
-    const long long idx = (long long)j * p.pitch + i;
-    const S *Fin = static_cast<const S *>(p.Fin);
-    const float F1p = Store<S>::ld(Fin + idx) * p.sF;   // F - F_rest of the previous step
-    const float F2p = Store<S>::ld(Fin + p.plane + idx) * p.sF;
+    pull_node<true>(p, src, i, j, h1, h2, d);
     float drho, U1, U2;
-    fields_from(p, d, F1p, F2p, h1, h2, drho, U1, U2);
+    fields_from(p, d, src.Fv(0, i, j), src.Fv(1, i, j), p.ax1.ih[i], p.ax2.ih[j], drho, U1, U2);   // F - F_rest of the previous step
     const long long N = (long long)p.nx * p.ny, n = (long long)j * p.nx + i;
     out[n] = (double)p.rho0 + (double)drho;
     out[N + n] = U1;
@@ -231,9 +229,9 @@ __global__ void moments_kernel(const StepParams p, double *out) {
     double B1 = 0.0, B2 = 0.0;
     if constexpr (MHD) {
         float gd[5];
-        pull_mie<S>(p, i, j, h1, h2, 0, gd);
+        pull_mie<true>(p, src, i, j, h1, h2, 0, gd);
         B1 = (double)p.brest[0] + (double)((gd[0] + gd[1] + gd[2] + gd[3] + gd[4]) / (h1 * h2));
-        pull_mie<S>(p, i, j, h1, h2, 1, gd);
+        pull_mie<true>(p, src, i, j, h1, h2, 1, gd);
         B2 = (double)p.brest[1] + (double)((gd[0] + gd[1] + gd[2] + gd[3] + gd[4]) / (h1 * h2));
     }
     out[3 * N + n] = B1;

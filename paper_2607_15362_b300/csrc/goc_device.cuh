@@ -3,6 +3,7 @@
 // precompute and the reductions use FP64.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (type only; tensor maps are encoded through the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -48,7 +49,7 @@ struct StepParams {
     const void *gin;           // [10][plane] MIE vector populations (component-major)
     void *gout;
     Axis ax1, ax2;
-    float rho0, cs2, nu, zeta;
+    float rho0, cs2, ics2, nu, zeta;
     float om[9];
     float fext1, fext2;
     float gi;                  // 1: full correction coefficients, 0: cubic terms dropped
@@ -64,21 +65,29 @@ struct StepParams {
     float bw[4][2];            // wall fields
     // optional outputs
     float *uout;               // [4][plane]: U1, U2, B1, B2 of this step's time level (may be null)
-    int *flag;                 // divergence flag (may be null)
+    int *flag;                 // status flag (may be null): 1 divergence, 2 a TMA wait timed out
+    // TMA descriptors of the input buffers (3D: [planes][ny][nx])
+    int use_tma;
+    CUtensorMap tm_f;          // box [9][TY + 2 HYS][TX + 2 HXS]
+    CUtensorMap tm_F;          // box [2][TY + 2 HYS][TX + 2 HXS]
+    CUtensorMap tm_g;          // box [10][TY + 2][TX + 2 HXS]
 };
 
-// ---- storage formats ------------------------------------------------------
+// ---- storage formats (ld: global read-only path, lds: shared memory) -------
 template <class S> struct Store;
 template <> struct Store<float> {
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float lds(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <> struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 

@@ -173,3 +173,30 @@ def test_run_until_reaches_the_residual_and_reports_it(gpu):
     done, res = L.run_until(1e-7, 400000)
     assert res < 1e-7 and 0 < done < 400000
     assert L.residuals()[0] == pytest.approx(res)
+
+
+@pytest.mark.parametrize("kind", ["cavity", "channel", "hartmann"])
+def test_interior_tiles_match_the_oracle(gpu, kind):
+    """Lattices wide enough to contain interior tiles (the check-free path) as
+    well as wall tiles and periodic-wrap tiles."""
+    if kind == "cavity":
+        prob = gi.Problem("cavity", 130, 90, {"kind": "tanh2", "beta": 1.5}, {"kind": "tanh2", "beta": 1.3},
+                          {"Re": 300.0, "u_lid": 0.05})
+        steps = 600
+    elif kind == "channel":
+        prob = gi.Problem("poiseuille", 100, 72, {"kind": "uniform"}, {"kind": "tanh2", "beta": 1.8},
+                          {"Re": 10.0, "tau": 0.8})
+        steps = 600
+    else:
+        prob = gi.Problem("hartmann", 100, 64, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
+                          {"Ha": 15.0, "Re": 15.0, "tau": 1.0, "tau_m": 1.0})
+        steps = 600
+    spec = prob.lattice_spec(cs2_of(prob))
+    if kind == "channel":   # add a transverse perturbation so that every term is exercised
+        u1, u2 = gi.random_periodic_fields(prob.nx, prob.ny, seed=8, amp=0.002)
+        spec["init"] = {"u1": u1, "u2": u2}
+    o, L, fo, fg = run_pair(spec, steps)
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+    if prob.mhd:
+        assert relerr(fg[3], fo[3]) <= 1e-5
