@@ -1142,3 +1142,116 @@ goc_status goc_batch_usage(const goc_batch *B, long long *used, long long *budge
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Total mass without allocating device memory.
+//
+// Some callers cannot call cudaMalloc when they need a diagnostic: code that
+// runs while a CUDA stream capture is active (allocation is not permitted
+// there), real-time loops that must not stall on the allocator, and
+// applications that hand all device memory to their own pool at start-up.
+// goc_mass_noalloc computes what goc_diagnostics(mass) computes, but its
+// scratch (one partial sum per block plus the final sum) lives in the
+// file-scope array below, which every GPU that loads this library holds until
+// the process exits.  All calls share that array: calls whose kernels
+// overlap on the GPU (different streams, different threads) race on it.
+// ============================================================================
+#define GOC_NOALLOC_NODES_PER_BLOCK 2048   // 256 threads x 8 nodes
+static_assert(GOC_NOALLOC_MAX_NODES == (long long)GOC_NOALLOC_MAX_BLOCKS * GOC_NOALLOC_NODES_PER_BLOCK,
+              "node limit of goc_mass_noalloc");
+
+static __device__ __align__(256) double g_noalloc_scratch[GOC_NOALLOC_MAX_BLOCKS + 1];
+
+namespace {
+
+// Per block: the sum over its (up to 2048) nodes of sum_a f, written to
+// partial[blockIdx.x] in a fixed order (no atomics, nothing to clear).
+template <class S>
+__global__ void mass_partial_kernel(const StepParams p, double *partial) {
+    __shared__ double red[256];
+    const long long N = (long long)p.nx * p.ny;
+    const S *f = static_cast<const S *>(p.fin);
+    double acc = 0.0;
+    for (int k = 0; k < GOC_NOALLOC_NODES_PER_BLOCK / 256; k++) {
+        const long long n = (long long)blockIdx.x * GOC_NOALLOC_NODES_PER_BLOCK + k * 256 + threadIdx.x;
+        if (n >= N) break;
+        const int j = (int)(n / p.nx), i = (int)(n - (long long)j * p.nx);
+        const long long idx = (long long)j * p.pitch + i;
+        double s = 0.0;
+        for (int a = 0; a < 9; a++) s += (double)Store<S>::ld(f + a * p.plane + idx) * p.sf;
+        acc += s + (double)p.ax1.h[i] * (double)p.ax2.h[j] * p.rho0;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// One block: fixed-order sum of nblocks partials into partial[GOC_NOALLOC_MAX_BLOCKS].
+__global__ void mass_final_kernel(double *partial, int nblocks) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) acc += partial[b];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[GOC_NOALLOC_MAX_BLOCKS] = red[0];
+}
+
+// Device address of the scratch array, looked up once per device (the first
+// call on a device does this set-up; make that call before any stream capture).
+double *noalloc_scratch(goc_status *st) {
+    static double *addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        *st = fail(GOC_ECUDA, "goc_mass_noalloc: no usable current device");
+        return nullptr;
+    }
+    if (!addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            *st = fail(GOC_ECUDA, "goc_mass_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return nullptr;
+        }
+        addr[dev] = static_cast<double *>(ptr);
+    }
+    *st = GOC_OK;
+    return addr[dev];
+}
+
+}  // namespace
+
+extern "C" goc_status goc_mass_noalloc(goc_lattice *L, double *mass) {
+    if (!L || !mass) return fail(GOC_EINVAL, "goc_mass_noalloc: lattice and mass are required");
+    const long long N = (long long)L->nx * L->ny;
+    const long long blocks = (N + GOC_NOALLOC_NODES_PER_BLOCK - 1) / GOC_NOALLOC_NODES_PER_BLOCK;
+    if (blocks > GOC_NOALLOC_MAX_BLOCKS)
+        return fail(GOC_EINVAL, "goc_mass_noalloc: the lattice has %lld nodes; at most %lld are supported",
+                    N, (long long)GOC_NOALLOC_MAX_BLOCKS * GOC_NOALLOC_NODES_PER_BLOCK);
+    int cur_dev = -1;
+    cudaGetDevice(&cur_dev);
+    if (cur_dev != L->device) CU(cudaSetDevice(L->device));
+    goc_status st;
+    double *scratch = noalloc_scratch(&st);
+    if (!scratch) return st;
+    StepParams p = params_for(L, L->cur, nullptr);
+    switch (L->storage) {
+        case GOC_FP16_DEV: mass_partial_kernel<__half><<<(unsigned)blocks, 256, 0, L->stream>>>(p, scratch); break;
+        case GOC_BF16_DEV: mass_partial_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, L->stream>>>(p, scratch); break;
+        default: mass_partial_kernel<float><<<(unsigned)blocks, 256, 0, L->stream>>>(p, scratch); break;
+    }
+    CU(cudaGetLastError());
+    mass_final_kernel<<<1, 256, 0, L->stream>>>(scratch, (int)blocks);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(mass, scratch + GOC_NOALLOC_MAX_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    CU(cudaStreamSynchronize(L->stream));
+    return GOC_OK;
+}
