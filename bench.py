@@ -252,6 +252,80 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """cfg4: 64 lattices (seed 7) advanced together by the persistent batched
+    kernel vs one lattice at a time with its own launches; FP32 and 16-bit."""
+    import torch
+
+    import paper_2607_15362_b300 as goc
+    from paper_2607_15362_b300.serve import lattice_spec
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    probs = gi.cfg4_batch(steps=args.batch_steps)
+    specs = [lattice_spec(p) for p in probs]
+    nodes = sum(p.nodes for p in probs)
+    out = {}
+    for storage in ("fp32", args.storage if args.storage != "fp32" else "fp16"):
+        b = goc.Batch(200 << 30, len(probs), storage=storage, stream=stream.cuda_stream)
+        for sp in specs:
+            b.add(sp)
+        b.step(64)                                   # warm-up: rebuild, graph capture
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(args.batch_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"batched_{storage}_mlups"] = round(nodes * args.batch_steps / ms / 1e3, 1)
+        used, _, _ = b.usage()
+        out[f"batched_{storage}_device_gb"] = round(used / 1e9, 3)
+        b.close()
+    # sequential: each lattice alone, same number of steps
+    total_ms = 0.0
+    for sp in specs:
+        lat = goc.Lattice(sp, stream=stream.cuda_stream)
+        lat.step(64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(args.batch_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        lat.close()
+    out["sequential_fp32_mlups"] = round(nodes * args.batch_steps / total_ms / 1e3, 1)
+    line = {"metric": METRIC, "workload": "cfg4 batch of 64 lattices (seed 7)", "lattices": len(probs),
+            "nodes": nodes, "steps_each": args.batch_steps, "unit": "MLUPS", **out,
+            "speedup_batched_vs_sequential": round(out["batched_fp32_mlups"] / out["sequential_fp32_mlups"], 3)}
+    print(json.dumps(line))
+
+
+def run_serve(args):
+    """cfg5: the first requests of the seed-11 Poisson trace served with
+    continuous batching vs one solve at a time; p50/p99 latency and
+    aggregate MLUPS."""
+    import torch
+
+    from paper_2607_15362_b300.serve import Server, requests_from_trace, run_sequential
+
+    torch.cuda.set_device(0)
+    trace = gi.cfg5_stream()[: args.requests]
+    reqs = requests_from_trace(trace, storage=args.storage)
+    offered = sum(r.problem.nodes * r.budget for r in reqs) / max(trace[-1]["arrival_s"], 1e-9) / 1e6
+    srv = Server(150 * (1 << 30) // 1, max_slots=256, chunk=args.chunk if args.chunk != 1000 else 500,
+                 storage=args.storage)
+    res_b, sum_b = srv.run(reqs, max_wall_s=args.serve_seconds)
+    srv.close()
+    res_s, sum_s = run_sequential(reqs, max_wall_s=args.serve_seconds)
+    line = {"metric": METRIC, "workload": f"cfg5 serving trace (seed 11), first {len(reqs)} requests",
+            "unit": "MLUPS", "offered_mlups": round(offered, 1),
+            "batched": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in sum_b.items()},
+            "sequential": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in sum_s.items()}}
+    print(json.dumps(line))
+
+
 def cpu_baseline(prob, spec_lib, budget_s: float = 15.0):
     """FP64 oracle, as it stands, on this host's cores: a bounded number of
     time steps of the same 512^2 cavity, scaled to MLUPS."""
@@ -313,9 +387,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "batch", "serve"])
+    ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -239,6 +239,16 @@ goc_status goc_batch_remove(goc_batch *b, int slot);
  * time step (work items = (lattice, tile) over all lattices). */
 goc_status goc_batch_step(goc_batch *b, long long nsteps);
 
+/* Mark a slot for residual checks (on != 0): the last two steps of every
+ * later goc_batch_step of >= 2 steps record that lattice's successive fields
+ * and reduce R = ||U^n - U^(n-1)|| / ||U^n|| (Sec. 7.3) and the B residual
+ * on the device.  Allocates the lattice's two snapshot buffers on first use. */
+goc_status goc_batch_check(goc_batch *b, int slot, int on);
+
+/* Residuals from the last goc_batch_step of a checked slot.  Synchronises the
+ * batch stream.  Returns GOC_EDIVERGED if that lattice has diverged. */
+goc_status goc_batch_residual(goc_batch *b, int slot, double *residual_u, double *residual_b);
+
 /* Access one resident lattice (owned by the batch; do not destroy). */
 goc_status goc_batch_lattice(goc_batch *b, int slot, goc_lattice **lat);
 

@@ -62,6 +62,8 @@ SIGNATURES = {
     "goc_batch_remove": (c_int, [c_void_p, c_int]),
     "goc_batch_step": (c_int, [c_void_p, c_ll]),
     "goc_batch_lattice": (c_int, [c_void_p, c_int, P(c_void_p)]),
+    "goc_batch_check": (c_int, [c_void_p, c_int, c_int]),
+    "goc_batch_residual": (c_int, [c_void_p, c_int, P(c_double), P(c_double)]),
     "goc_batch_usage": (c_int, [c_void_p, P(c_ll), P(c_ll), P(c_int)]),
     "goc_mass_noalloc": (c_int, [c_void_p, P(c_double)]),
     "goc_last_error": (ctypes.c_char_p, []),

@@ -80,6 +80,7 @@ struct goc_lattice {
     bool owns_stream = false;
     bool in_batch = false;                       // stepped only through goc_batch_step
     bool fresh = false;                          // buffer holds f^0 (pre-collision): next step reads in place
+    bool res_pending = false;                    // residual sums of a batch step wait in red[4..7]
     CUtensorMap tmf[2], tmF[2], tmg[2];          // TMA descriptors of both buffers
     bool tma_ok = false;
 };
@@ -847,14 +848,18 @@ struct goc_batch {
     // per storage group: params[2][n], tile offsets[n+1]
     struct Group {
         int storage = 0, n = 0, total = 0, grid = 0;
-        StepParams *d_params = nullptr;   // [3][n]: parity 0, parity 1, first step after a rebuild
+        StepParams *d_params = nullptr;   // [7][n]: parity 0, parity 1, first step after a rebuild,
+                                          // then parity p with snapshot u: 3 + 2 p + u
         int *d_off = nullptr;
         int stage_bytes = 0;
+        int mhd = 0;
         std::vector<int> members;
-    } groups[3];
+    } groups[6];                  // index 2 * storage + (MIE on)
     long long phase = 0;
     bool first_pending = false;   // next launch uses the first-step parameters (fresh members read in place)
     cudaGraphExec_t graph = nullptr;
+    std::vector<char> check;      // per slot: record successive fields for the residual
+    bool any_check = false;
 };
 
 namespace {
@@ -884,66 +889,62 @@ void free_groups(goc_batch *B) {
     B->graph = nullptr;
 }
 
-template <class S>
-int persistent_grid(int total, int stage_bytes) {
+template <class S, bool MHD>
+int persistent_grid(int total, int *stage_bytes) {
     using T = Tiling<S>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(batch_step_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * T::STAGE_MHD);
-        attr = true;
+    const int stage = MHD ? T::STAGE_MHD : T::STAGE_NSE;
+    *stage_bytes = stage;
+    static int cached = -1;
+    if (cached < 0) {
+        cudaFuncSetAttribute(batch_step_kernel<S, MHD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * stage);
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S, MHD>, NT, 2 * (size_t)stage);
+        cached = std::max(1, sms * std::max(1, per));
     }
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S>, NT, 2 * (size_t)stage_bytes);
-    int g = std::max(1, sms * std::max(1, per));
-    return std::min(total, g);
-}
-
-template <class S>
-int stage_bytes_for(bool any_mhd) {
-    using T = Tiling<S>;
-    return any_mhd ? T::STAGE_MHD : T::STAGE_NSE;
+    return std::min(total, cached);
 }
 
 goc_status rebuild(goc_batch *B) {
     free_groups(B);
-    for (int s = 0; s < 3; s++) B->groups[s].storage = s;
+    for (int s = 0; s < 6; s++) {
+        B->groups[s].storage = s / 2;
+        B->groups[s].mhd = s % 2;
+    }
     for (int k = 0; k < (int)B->slots.size(); k++)
-        if (B->slots[k]) B->groups[B->slots[k]->storage].members.push_back(k);
+        if (B->slots[k]) B->groups[2 * B->slots[k]->storage + (B->slots[k]->mhd.enabled ? 1 : 0)].members.push_back(k);
     for (auto &g : B->groups) {
         g.n = (int)g.members.size();
         if (!g.n) continue;
-        std::vector<StepParams> hp(3 * g.n);
+        std::vector<StepParams> hp(7 * g.n);
         std::vector<int> off(g.n + 1, 0);
         for (int m = 0; m < g.n; m++) {
-            goc_lattice *L = B->slots[g.members[m]];
+            const int slot = g.members[m];
+            goc_lattice *L = B->slots[slot];
             hp[m] = params_for(L, L->cur, nullptr);
             hp[g.n + m] = params_for(L, L->cur ^ 1, nullptr);
             hp[2 * g.n + m] = hp[m];
             hp[2 * g.n + m].nopull = L->fresh ? 1 : 0;
+            for (int par = 0; par < 2; par++)
+                for (int u = 0; u < 2; u++)
+                    hp[(3 + 2 * par + u) * g.n + m] =
+                        params_for(L, L->cur ^ par, B->check[slot] ? L->uout[u] : nullptr);
             off[m + 1] = off[m] + ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
         }
         g.total = off[g.n];
-        bool any_mhd = false;
-        for (int m = 0; m < g.n; m++) any_mhd = any_mhd || B->slots[g.members[m]]->mhd.enabled;
         CU(cudaMalloc(&g.d_params, hp.size() * sizeof(StepParams)));
         CU(cudaMalloc(&g.d_off, off.size() * sizeof(int)));
         CU(cudaMemcpyAsync(g.d_params, hp.data(), hp.size() * sizeof(StepParams), cudaMemcpyHostToDevice, B->stream));
         CU(cudaMemcpyAsync(g.d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream));
-        switch (g.storage) {
-            case GOC_FP16_DEV:
-                g.stage_bytes = stage_bytes_for<__half>(any_mhd);
-                g.grid = persistent_grid<__half>(g.total, g.stage_bytes);
-                break;
-            case GOC_BF16_DEV:
-                g.stage_bytes = stage_bytes_for<__nv_bfloat16>(any_mhd);
-                g.grid = persistent_grid<__nv_bfloat16>(g.total, g.stage_bytes);
-                break;
-            default:
-                g.stage_bytes = stage_bytes_for<float>(any_mhd);
-                g.grid = persistent_grid<float>(g.total, g.stage_bytes);
-                break;
+        const int key = 2 * g.storage + g.mhd;
+        switch (key) {
+            case 2: g.grid = persistent_grid<__half, false>(g.total, &g.stage_bytes); break;
+            case 3: g.grid = persistent_grid<__half, true>(g.total, &g.stage_bytes); break;
+            case 4: g.grid = persistent_grid<__nv_bfloat16, false>(g.total, &g.stage_bytes); break;
+            case 5: g.grid = persistent_grid<__nv_bfloat16, true>(g.total, &g.stage_bytes); break;
+            case 1: g.grid = persistent_grid<float, true>(g.total, &g.stage_bytes); break;
+            default: g.grid = persistent_grid<float, false>(g.total, &g.stage_bytes); break;
         }
     }
     CU(cudaStreamSynchronize(B->stream));
@@ -953,21 +954,20 @@ goc_status rebuild(goc_batch *B) {
     return GOC_OK;
 }
 
-goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first = false) {
+goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first = false, int snapshot = -1) {
     for (auto &g : B->groups) {
         if (!g.n) continue;
-        const StepParams *p = g.d_params + (first ? 2 : ((B->phase + s) & 1)) * g.n;
+        const int par = (int)((B->phase + s) & 1);
+        const int which = first ? 2 : (snapshot >= 0 ? 3 + 2 * par + snapshot : par);
+        const StepParams *p = g.d_params + which * g.n;
         const size_t smem = 2 * (size_t)g.stage_bytes;
-        switch (g.storage) {
-            case GOC_FP16_DEV:
-                batch_step_kernel<__half><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n, g.stage_bytes);
-                break;
-            case GOC_BF16_DEV:
-                batch_step_kernel<__nv_bfloat16><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n, g.stage_bytes);
-                break;
-            default:
-                batch_step_kernel<float><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n, g.stage_bytes);
-                break;
+        switch (2 * g.storage + g.mhd) {
+            case 2: batch_step_kernel<__half, false><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
+            case 3: batch_step_kernel<__half, true><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
+            case 4: batch_step_kernel<__nv_bfloat16, false><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
+            case 5: batch_step_kernel<__nv_bfloat16, true><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
+            case 1: batch_step_kernel<float, true><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
+            default: batch_step_kernel<float, false><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
         }
         CU(cudaGetLastError());
     }
@@ -994,6 +994,7 @@ goc_status goc_batch_create(long long hbm_budget_bytes, int max_lattices, const 
     cudaGetDevice(&B->device);
     B->slots.assign(max_lattices, nullptr);
     B->bytes.assign(max_lattices, 0);
+    B->check.assign(max_lattices, 0);
     *out = B;
     return GOC_OK;
 }
@@ -1046,6 +1047,9 @@ goc_status goc_batch_remove(goc_batch *B, int slot) {
     free_lattice(B->slots[slot]);
     B->slots[slot] = nullptr;
     B->bytes[slot] = 0;
+    B->check[slot] = 0;
+    B->any_check = false;
+    for (char c : B->check) B->any_check = B->any_check || c;
     B->dirty = true;
     return GOC_OK;
 }
@@ -1074,7 +1078,9 @@ goc_status goc_batch_step(goc_batch *B, long long nsteps) {
             }
         if (--nsteps == 0) return GOC_OK;
     }
-    long long left = nsteps;
+    // with residual checks the last two steps record successive fields
+    const int tail = (B->any_check && nsteps >= 2) ? 2 : 0;
+    long long left = nsteps - tail;
     auto single = [&]() -> goc_status {
         goc_status st = batch_launch(B, B->stream, 0);
         B->phase += 1;
@@ -1115,11 +1121,69 @@ goc_status goc_batch_step(goc_batch *B, long long nsteps) {
         if (st != GOC_OK) return st;
         left--;
     }
+    for (int u = 0; u < tail; u++) {
+        goc_status st = batch_launch(B, B->stream, 0, false, u);
+        if (st != GOC_OK) return st;
+        B->phase += 1;
+    }
     for (auto *L : B->slots)
         if (L) {
             L->steps += nsteps;
             L->cur ^= (int)(nsteps & 1);
         }
+    if (tail) {   // residual sums of the checked lattices (read by goc_batch_residual)
+        for (int k = 0; k < B->max_lat; k++) {
+            goc_lattice *L = B->slots[k];
+            if (!L || !B->check[k]) continue;
+            CU(cudaMemsetAsync(L->red + 4, 0, 4 * sizeof(double), B->stream));
+            residual_kernel<<<148, 256, 0, B->stream>>>(L->uout[0], L->uout[1], L->plane, L->nx, L->ny, L->pitch,
+                                                        L->red + 4);
+            CU(cudaGetLastError());
+            L->res_pending = true;
+        }
+    }
+    return GOC_OK;
+}
+
+goc_status goc_batch_check(goc_batch *B, int slot, int on) {
+    if (!B || slot < 0 || slot >= B->max_lat || !B->slots[slot]) return fail(GOC_EINVAL, "no lattice in slot %d", slot);
+    goc_lattice *L = B->slots[slot];
+    if (on && !L->uout[0]) {
+        for (int b = 0; b < 2; b++) {
+            cudaError_t e = cudaMalloc(&L->uout[b], 4 * L->plane * sizeof(float));
+            if (e != cudaSuccess) return fail(GOC_ENOMEM, "residual buffers: %s", cudaGetErrorString(e));
+            L->device_bytes += 4 * L->plane * sizeof(float);
+            B->used += 4 * L->plane * sizeof(float);
+            B->bytes[slot] += 4 * L->plane * sizeof(float);
+        }
+    }
+    B->check[slot] = on ? 1 : 0;
+    B->any_check = false;
+    for (char c : B->check) B->any_check = B->any_check || c;
+    B->dirty = true;
+    return GOC_OK;
+}
+
+goc_status goc_batch_residual(goc_batch *B, int slot, double *residual_u, double *residual_b) {
+    if (!B || slot < 0 || slot >= B->max_lat || !B->slots[slot]) return fail(GOC_EINVAL, "no lattice in slot %d", slot);
+    goc_lattice *L = B->slots[slot];
+    if (L->res_pending) {
+        double h[4];
+        int flag = 0;
+        CU(cudaMemcpyAsync(h, L->red + 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
+        CU(cudaMemcpyAsync(&flag, L->flag, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+        CU(cudaStreamSynchronize(B->stream));
+        L->res_u = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+        L->res_b = (L->mhd.enabled && h[3] > 0) ? std::sqrt(h[2] / h[3]) : 0.0;
+        L->res_pending = false;
+        if (flag || !std::isfinite(L->res_u) || !std::isfinite(L->res_b)) {
+            if (residual_u) *residual_u = L->res_u;
+            if (residual_b) *residual_b = L->res_b;
+            return fail(GOC_EDIVERGED, "lattice in slot %d diverged", slot);
+        }
+    }
+    if (residual_u) *residual_u = L->res_u;
+    if (residual_b) *residual_b = L->res_b;
     return GOC_OK;
 }
 

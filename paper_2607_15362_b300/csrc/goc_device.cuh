@@ -76,20 +76,26 @@ struct StepParams {
 // ---- storage formats (ld: global read-only path, lds: shared memory) -------
 template <class S> struct Store;
 template <> struct Store<float> {
+    static constexpr bool scaled = false;   // FP32 is stored unscaled
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ float lds(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <> struct Store<__half> {
+    static constexpr bool scaled = true;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
+    static constexpr bool scaled = true;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
+
+// value * scale for 16-bit storage, value unchanged for FP32
+template <class S> __device__ __forceinline__ float scl(float v, float s) { return Store<S>::scaled ? v * s : v; }
 
 __device__ __forceinline__ int wrapi(int k, int n) {
     k %= n;

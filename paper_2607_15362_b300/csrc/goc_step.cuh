@@ -32,11 +32,19 @@
 // the paper's Eq. GOC-LBEcentralmoment, reorganised for FP32.
 #pragma once
 
+#include <cstddef>
+
 #include "goc_device.cuh"
 
 namespace goc {
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
+#ifndef GOC_TILE_ROWS
+#define GOC_TILE_ROWS 8        // tile height (rows); the tile width is one warp
+#endif
+#ifndef GOC_MIN_BLOCKS
+#define GOC_MIN_BLOCKS 3       // resident blocks per SM asked of the register allocator (measured best)
+#endif
+constexpr int TX = 32, TY = GOC_TILE_ROWS, NT = TX * TY;
 constexpr int MH = 2;                        // halo of the field arrays (one-sided stencils)
 constexpr int HYS = 3;                       // halo rows of the staged tile (fields halo + pull)
 template <class S> struct Tiling {
@@ -98,13 +106,13 @@ template <class S> struct SrcGlobal {      // direct (read-only path) global loa
     int pitch;
     float sf, sF, sg;
     __device__ __forceinline__ float fv(int a, int i, int j) const {
-        return Store<S>::ld(f + a * plane + (long long)j * pitch + i) * sf;
+        return scl<S>(Store<S>::ld(f + a * plane + (long long)j * pitch + i), sf);
     }
     __device__ __forceinline__ float Fv(int c, int i, int j) const {
-        return Store<S>::ld(F + c * plane + (long long)j * pitch + i) * sF;
+        return scl<S>(Store<S>::ld(F + c * plane + (long long)j * pitch + i), sF);
     }
     __device__ __forceinline__ float gv(int k, int i, int j) const {
-        return Store<S>::ld(g + k * plane + (long long)j * pitch + i) * sg;
+        return scl<S>(Store<S>::ld(g + k * plane + (long long)j * pitch + i), sg);
     }
 };
 template <class S> struct SrcSmem {        // the TMA-staged tile
@@ -113,13 +121,13 @@ template <class S> struct SrcSmem {        // the TMA-staged tile
     int ox, oy, oyg;                        // lattice coordinates of staged element (0, 0)
     float sf, sF, sg;
     __device__ __forceinline__ float fv(int a, int i, int j) const {
-        return Store<S>::lds(f + (a * T::BY + (j - oy)) * T::BX + (i - ox)) * sf;
+        return scl<S>(Store<S>::lds(f + (a * T::BY + (j - oy)) * T::BX + (i - ox)), sf);
     }
     __device__ __forceinline__ float Fv(int c, int i, int j) const {
-        return Store<S>::lds(F + (c * T::BY + (j - oy)) * T::BX + (i - ox)) * sF;
+        return scl<S>(Store<S>::lds(F + (c * T::BY + (j - oy)) * T::BX + (i - ox)), sF);
     }
     __device__ __forceinline__ float gv(int k, int i, int j) const {
-        return Store<S>::lds(g + (k * T::BYG + (j - oyg)) * T::BX + (i - ox)) * sg;
+        return scl<S>(Store<S>::lds(g + (k * T::BYG + (j - oyg)) * T::BX + (i - ox)), sg);
     }
 };
 
@@ -336,7 +344,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
                 const float W = a == 0 ? p.W0 : p.W1;
                 const float G = W * (H * dBc[c] + g1(a) * x1 + g2(a) * x2);
                 const float gt = gd[c][a] - (gd[c][a] - G) * p.itaum;
-                Store<S>::st(gout + (c * 5 + a) * p.plane + idx, gt * p.isg);
+                Store<S>::st(gout + (c * 5 + a) * p.plane + idx, scl<S>(gt, p.isg));
             }
         }
     }
@@ -447,10 +455,10 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
     o[8] = d[8] + 0.25f * (-R11 - R21 + R12 + R22);
     S *fout = static_cast<S *>(p.fout);
 #pragma unroll
-    for (int a = 0; a < 9; a++) Store<S>::st(fout + a * p.plane + idx, o[a] * p.isf);
+    for (int a = 0; a < 9; a++) Store<S>::st(fout + a * p.plane + idx, scl<S>(o[a], p.isf));
     S *Fout = static_cast<S *>(p.Fout);
-    Store<S>::st(Fout + idx, F1dev * p.isF);
-    Store<S>::st(Fout + p.plane + idx, F2dev * p.isF);
+    Store<S>::st(Fout + idx, scl<S>(F1dev, p.isF));
+    Store<S>::st(Fout + p.plane + idx, scl<S>(F2dev, p.isF));
 
     if (p.uout) {
         p.uout[idx] = U1;
@@ -596,7 +604,7 @@ __device__ __forceinline__ void run_tile(const StepParams &p, int kind, int i0, 
 // Single lattice: persistent blocks stride over the tiles; TMA staging in two
 // dynamic shared-memory stages.
 template <class S, bool MHD>
-__global__ void __launch_bounds__(NT, 2) step_kernel(const __grid_constant__ StepParams p) {
+__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
     using T = Tiling<S>;
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -653,19 +661,28 @@ __device__ __forceinline__ int find_lattice(const int *tile_off, int nlat, int t
     return lo;
 }
 
-template <class S>
-__global__ void __launch_bounds__(NT, 2) batch_step_kernel(const StepParams *__restrict__ params,
-                                                           const int *__restrict__ tile_off, int nlat, int stage_bytes) {
+template <class S, bool MHD>
+__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const StepParams *__restrict__ params,
+                                                                        const int *__restrict__ tile_off, int nlat) {
+    using T = Tiling<S>;
+    constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ FieldSmem sm;
     __shared__ int s_item[2][3];   // per stage: lattice, i0, j0 of the staged item
+    __shared__ __align__(16) unsigned char s_par[(offsetof(StepParams, tm_f) + 15) / 16 * 16];
+    __shared__ int s_k;            // lattice whose parameters are in s_par
     const int total = tile_off[nlat];
+    // contiguous range of work items per block: neighbouring tiles of one lattice
+    const int per = (total + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per, t_end = min(total, t_begin + per);
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const int tid = threadIdx.y * TX + threadIdx.x;
     if (leader) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
+        s_k = -1;
     }
     auto prefetch = [&](int t, int st) {
         const int k = find_lattice(tile_off, nlat, t);
@@ -678,18 +695,24 @@ __global__ void __launch_bounds__(NT, 2) batch_step_kernel(const StepParams *__r
         s_item[st][2] = j0;
         if (tile_kind<S>(q, i0, j0) != 2) {
             fence_proxy_async();
-            issue_tile<S>(q, i0, j0, dyn + st * stage_bytes, &bars[st], q.gin != nullptr);
+            issue_tile<S>(q, i0, j0, dyn + st * STAGE, &bars[st], MHD);
         }
     };
-    if (leader && (int)blockIdx.x < total) prefetch(blockIdx.x, 0);
+    if (leader && t_begin < t_end) prefetch(t_begin, 0);
     __syncthreads();
     uint32_t ph0 = 0, ph1 = 0;
     int stage = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int tn = t + gridDim.x;
-        if (leader && tn < total) prefetch(tn, stage ^ 1);
+    for (int t = t_begin; t < t_end; t++) {
+        if (leader && t + 1 < t_end) prefetch(t + 1, stage ^ 1);
         const int k = s_item[stage][0], i0 = s_item[stage][1], j0 = s_item[stage][2];
-        const StepParams &p = params[k];
+        if (k != s_k) {   // parameters (up to the TMA descriptors) of a new lattice into shared memory
+            const uint4 *src = reinterpret_cast<const uint4 *>(&params[k]);
+            uint4 *dst = reinterpret_cast<uint4 *>(s_par);
+            for (int w = tid; w < (int)(sizeof(s_par) / 16); w += NT) dst[w] = src[w];
+            __syncthreads();
+            if (leader) s_k = k;
+        }
+        const StepParams &p = *reinterpret_cast<const StepParams *>(s_par);
         const int kind = tile_kind<S>(p, i0, j0);
         if (kind != 2) {
             uint32_t &ph = stage ? ph1 : ph0;
@@ -697,8 +720,7 @@ __global__ void __launch_bounds__(NT, 2) batch_step_kernel(const StepParams *__r
             if (!__syncthreads_and(ok)) return;   // the whole block leaves together on a timeout
             ph ^= 1;
         }
-        if (p.gin) run_tile<S, true>(p, kind, i0, j0, dyn + stage * stage_bytes, sm);
-        else run_tile<S, false>(p, kind, i0, j0, dyn + stage * stage_bytes, sm);
+        run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm);
         __syncthreads();   // stage, field arrays and s_item are reused
         stage ^= 1;
     }

@@ -225,6 +225,15 @@ class Batch:
     def step(self, n: int = 1):
         check(lib().goc_batch_step(self._h, int(n)))
 
+    def check(self, slot: int, on: bool = True):
+        """Record the residual of this slot at the end of every batch step."""
+        check(lib().goc_batch_check(self._h, int(slot), int(bool(on))))
+
+    def residual(self, slot: int):
+        ru, rb = ctypes.c_double(), ctypes.c_double()
+        check(lib().goc_batch_residual(self._h, int(slot), ctypes.byref(ru), ctypes.byref(rb)))
+        return ru.value, rb.value
+
     def lattice(self, slot: int) -> Lattice:
         out = ctypes.c_void_p()
         check(lib().goc_batch_lattice(self._h, int(slot), ctypes.byref(out)))
