@@ -162,10 +162,10 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     size_t smem = 0;
     if (L->mhd.enabled) {
         const int grid = step_grid<S, true>(ntiles, &smem);
-        step_kernel<S, true><<<grid, dim3(TX, TY), smem, L->stream>>>(p);
+        step_kernel<S, true><<<grid, dim3(TX, TYT), smem, L->stream>>>(p);
     } else {
         const int grid = step_grid<S, false>(ntiles, &smem);
-        step_kernel<S, false><<<grid, dim3(TX, TY), smem, L->stream>>>(p);
+        step_kernel<S, false><<<grid, dim3(TX, TYT), smem, L->stream>>>(p);
     }
     CU(cudaGetLastError());
     return GOC_OK;
@@ -577,6 +577,12 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     p.fext1 = (float)L->flow.fext[0];
     p.fext2 = (float)L->flow.fext[1];
     p.gi = L->flow.gi_correction ? 1.f : 0.f;
+    p.zc = (float)(L->zeta / L->cs2);
+    p.nc = (float)(L->nu / L->cs2);
+    p.zmn = (float)(L->zeta - L->nu);
+    p.A3 = (float)(2.0 * L->zeta + L->nu);
+    p.A4 = (float)(L->zeta + 2.0 * L->nu);
+    p.gic = (float)((L->flow.gi_correction ? 1.0 : 0.0) / L->cs2);
     for (int s = 0; s < 4; s++) {
         p.uw[s] = grid->bc[s] == GOC_BC_WALL ? (float)grid->wall_u[s] : 0.f;
         p.hwn[s] = (float)L->hw[s];
@@ -962,12 +968,12 @@ goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first =
         const StepParams *p = g.d_params + which * g.n;
         const size_t smem = 2 * (size_t)g.stage_bytes;
         switch (2 * g.storage + g.mhd) {
-            case 2: batch_step_kernel<__half, false><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
-            case 3: batch_step_kernel<__half, true><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
-            case 4: batch_step_kernel<__nv_bfloat16, false><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
-            case 5: batch_step_kernel<__nv_bfloat16, true><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
-            case 1: batch_step_kernel<float, true><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
-            default: batch_step_kernel<float, false><<<g.grid, dim3(TX, TY), smem, st>>>(p, g.d_off, g.n); break;
+            case 2: batch_step_kernel<__half, false><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
+            case 3: batch_step_kernel<__half, true><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
+            case 4: batch_step_kernel<__nv_bfloat16, false><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
+            case 5: batch_step_kernel<__nv_bfloat16, true><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
+            case 1: batch_step_kernel<float, true><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
+            default: batch_step_kernel<float, false><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
         }
         CU(cudaGetLastError());
     }

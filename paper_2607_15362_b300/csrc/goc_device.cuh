@@ -53,6 +53,8 @@ struct StepParams {
     float om[9];
     float fext1, fext2;
     float gi;                  // 1: full correction coefficients, 0: cubic terms dropped
+    // combinations of zeta, nu and 1/cs2 in the correction coefficients (Eqs. 83, 85)
+    float zc, nc, zmn, A3, A4, gic;   // zeta/cs2, nu/cs2, zeta-nu, 2zeta+nu, zeta+2nu, gi/cs2
     float uw[4];               // tangential wall velocity per side
     float hwn[4];              // wall-normal metric factor at each wall (W/E: h1, S/N: h2)
     int moving;                // any moving wall

@@ -35,6 +35,7 @@
 #include <cstddef>
 
 #include "goc_device.cuh"
+#include "goc_vec.cuh"
 
 namespace goc {
 
@@ -44,7 +45,14 @@ namespace goc {
 #ifndef GOC_MIN_BLOCKS
 #define GOC_MIN_BLOCKS 3       // resident blocks per SM asked of the register allocator (measured best)
 #endif
-constexpr int TX = 32, TY = GOC_TILE_ROWS, NT = TX * TY;
+#ifndef GOC_ROWS_PER_THREAD
+#define GOC_ROWS_PER_THREAD 1  // nodes per thread (rows ty + r TY/RPT); 2 runs the collision on packed f32x2 (measured slower)
+#endif
+constexpr int TX = 32, TY = GOC_TILE_ROWS, RPT = GOC_ROWS_PER_THREAD, TYT = TY / RPT, NT = TX * TYT;
+static_assert(TY % RPT == 0, "tile rows must be a multiple of the rows per thread");
+template <int R> struct VecOf;
+template <> struct VecOf<1> { using type = float; };
+template <> struct VecOf<2> { using type = float2; };
 constexpr int MH = 2;                        // halo of the field arrays (one-sided stencils)
 constexpr int HYS = 3;                       // halo rows of the staged tile (fields halo + pull)
 template <class S> struct Tiling {
@@ -271,238 +279,358 @@ struct FieldSmem {
     float rho[TY + 2 * MH][TX + 2 * MH], u1[TY + 2 * MH][TX + 2 * MH], u2[TY + 2 * MH][TX + 2 * MH];
 };
 
-// Phase 2 for node (i, j) = (i0 + tx, j0 + ty).
-template <class S, bool MHD, bool CHECKS, class Src>
-__device__ __forceinline__ void node_update(const StepParams &p, const Src &src, int i, int j, int tx, int ty,
-                                            const FieldSmem &sm, const float (&d)[9], float F1p, float F2p,
-                                            float h1, float h2, float ih1, float ih2) {
-    const int ex = tx + MH, ey = ty + MH;
-    const float t11 = p.ax1.th[i], t22 = p.ax2.th[j];
-    const float H = h1 * h2, iH = ih1 * ih2;
-    const float drho = sm.rho[ey][ex], U1 = sm.u1[ey][ex], U2 = sm.u2[ey][ex];
-    const float rho = p.rho0 + drho;
-
-    // normal derivatives (second-order finite differences)
-    float dU1, dr1, dU2, dr2;
-    if (CHECKS) {
-        dU1 = dfd(sm.u1[ey][ex - 2], sm.u1[ey][ex - 1], U1, sm.u1[ey][ex + 1], sm.u1[ey][ex + 2], i, p.nx, p.per_x);
-        dr1 = dfd(sm.rho[ey][ex - 2], sm.rho[ey][ex - 1], drho, sm.rho[ey][ex + 1], sm.rho[ey][ex + 2], i, p.nx, p.per_x);
-        dU2 = dfd(sm.u2[ey - 2][ex], sm.u2[ey - 1][ex], U2, sm.u2[ey + 1][ex], sm.u2[ey + 2][ex], j, p.ny, p.per_y);
-        dr2 = dfd(sm.rho[ey - 2][ex], sm.rho[ey - 1][ex], drho, sm.rho[ey + 1][ex], sm.rho[ey + 2][ex], j, p.ny, p.per_y);
-    } else {
-        dU1 = 0.5f * (sm.u1[ey][ex + 1] - sm.u1[ey][ex - 1]);
-        dr1 = 0.5f * (sm.rho[ey][ex + 1] - sm.rho[ey][ex - 1]);
-        dU2 = 0.5f * (sm.u2[ey + 1][ex] - sm.u2[ey - 1][ex]);
-        dr2 = 0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex]);
+// Phase 2 for the R = Lanes<V>::R nodes (i, j[r]) of one thread, r = 0..R-1
+// (one node with V = float, two with V = float2: every arithmetic step below
+// runs once for both).  ty[r] is the node's row within the tile, own[r] whether
+// it is a lattice node this thread updates.
+template <class S, bool MHD, bool CHECKS, class V, class Src>
+__device__ __forceinline__ void node_update(const StepParams &p, const Src &src, int i, int tx,
+                                            const int (&j)[Lanes<V>::R], const int (&ty)[Lanes<V>::R],
+                                            const bool (&own)[Lanes<V>::R], const FieldSmem &sm,
+                                            const float (&dn)[Lanes<V>::R][9], const float (&F1pn)[Lanes<V>::R],
+                                            const float (&F2pn)[Lanes<V>::R], float h1, float ih1,
+                                            const float (&h2n)[Lanes<V>::R], const float (&ih2n)[Lanes<V>::R]) {
+    constexpr int R = Lanes<V>::R;
+    const int ex = tx + MH;
+    float t_[8][R];   // per lane: drho, U1, U2, dU1, dr1, dU2, dr2, theta22
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int ey = ty[r] + MH;
+        const float drho = sm.rho[ey][ex], U1 = sm.u1[ey][ex], U2 = sm.u2[ey][ex];
+        t_[0][r] = drho;
+        t_[1][r] = U1;
+        t_[2][r] = U2;
+        if (CHECKS) {
+            t_[3][r] = dfd(sm.u1[ey][ex - 2], sm.u1[ey][ex - 1], U1, sm.u1[ey][ex + 1], sm.u1[ey][ex + 2], i, p.nx, p.per_x);
+            t_[4][r] = dfd(sm.rho[ey][ex - 2], sm.rho[ey][ex - 1], drho, sm.rho[ey][ex + 1], sm.rho[ey][ex + 2], i, p.nx, p.per_x);
+            t_[5][r] = dfd(sm.u2[ey - 2][ex], sm.u2[ey - 1][ex], U2, sm.u2[ey + 1][ex], sm.u2[ey + 2][ex], j[r], p.ny, p.per_y);
+            t_[6][r] = dfd(sm.rho[ey - 2][ex], sm.rho[ey - 1][ex], drho, sm.rho[ey + 1][ex], sm.rho[ey + 2][ex], j[r], p.ny, p.per_y);
+        } else {
+            t_[3][r] = 0.5f * (sm.u1[ey][ex + 1] - sm.u1[ey][ex - 1]);
+            t_[4][r] = 0.5f * (sm.rho[ey][ex + 1] - sm.rho[ey][ex - 1]);
+            t_[5][r] = 0.5f * (sm.u2[ey + 1][ex] - sm.u2[ey - 1][ex]);
+            t_[6][r] = 0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex]);
+        }
+        t_[7][r] = p.ax2.th[own[r] ? j[r] : j[0]];
     }
-
-    const long long idx = (long long)j * p.pitch + i;
-    float FL1 = 0.f, FL2 = 0.f, B1 = 0.f, B2 = 0.f;
+    const V drho = pack<V>(t_[0]), U1 = pack<V>(t_[1]), U2 = pack<V>(t_[2]);
+    const V dU1 = pack<V>(t_[3]), dr1 = pack<V>(t_[4]), dU2 = pack<V>(t_[5]), dr2 = pack<V>(t_[6]);
+    const V t22 = pack<V>(t_[7]);
+    const V h2 = pack<V>(h2n), ih2 = pack<V>(ih2n), F1p = pack<V>(F1pn), F2p = pack<V>(F2pn);
+    const float t11 = p.ax1.th[i];
+    V d[9];
+#pragma unroll
+    for (int a = 0; a < 9; a++) {
+        float t[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) t[r] = dn[r][a];
+        d[a] = pack<V>(t);
+    }
+    const V rho = drho + p.rho0;
+    const V H = h2 * h1, iH = ih2 * ih1;
+    const float cs2 = p.cs2;
+    long long idx[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) idx[r] = (long long)j[r] * p.pitch + i;
+    V FL1 = bc<V>(0.f), FL2 = bc<V>(0.f), B1 = bc<V>(0.f), B2 = bc<V>(0.f);
 
     // ---- MIE (Appendix G): local dB, J3, Lorentz force, SRT collision -------
     if constexpr (MHD) {
         S *gout = static_cast<S *>(p.gout);
-        float gd[2][5], Bc[2], dBc[2], dB1[2], dB2[2], A1[2], A2[2];
+        V gd[2][5], dBc[2], dB1[2], dB2[2];
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            pull_mie<CHECKS>(p, src, i, j, h1, h2, c, gd[c]);
-            float s = gd[c][0] + gd[c][1] + gd[c][2] + gd[c][3] + gd[c][4];
-            dBc[c] = s * iH;                    // h1 h2 B = sum g (Eq. 13_C, Y = 0); sum g_ref- = H B_rest
-            Bc[c] = p.brest[c] + dBc[c];
+            float t[R][5];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                if (own[r]) pull_mie<CHECKS>(p, src, i, j[r], h1, h2n[r], c, t[r]);
+                else {
+#pragma unroll
+                    for (int a = 0; a < 5; a++) t[r][a] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 5; a++) {
+                float u_[R];
+#pragma unroll
+                for (int r = 0; r < R; r++) u_[r] = t[r][a];
+                gd[c][a] = pack<V>(u_);
+            }
+            // h1 h2 B = sum g (Eq. 13_C, Y = 0); sum g_ref- = H B_rest
+            dBc[c] = (gd[c][0] + gd[c][1] + gd[c][2] + gd[c][3] + gd[c][4]) * iH;
         }
-        B1 = Bc[0];
-        B2 = Bc[1];
-        const float U[2] = {U1, U2};
+        B1 = dBc[0] + p.brest[0];
+        B2 = dBc[1] + p.brest[1];
+        // A_cd = U_d B_c - B_d U_c (Eq. 2_C): A_11 = A_22 = 0, A_21 = -A_12
+        const V A12 = U1 * B2 - B1 * U2;
+        const V A1[2] = {bc<V>(0.f), A12}, A2[2] = {bc<V>(0.f) - A12, bc<V>(0.f)};
+        // Eqs. gradB1/gradB2 with Lambda^(1) = sum e (g - g^eq(0)) (Eqs.
+        // firstvelmomenttensor1/2); the rest-state moment M of g_ref- cancels
+        // against the B_rest part of the curvature term.
+        const V k1 = rcpv(fmav(h2 * ih1, p.taum - 0.5f, H * 0.5f) * p.csm2);
+        const V k2 = rcpv(fmav(h1 * ih2, p.taum - 0.5f, H * 0.5f) * p.csm2);
+        const V m1 = H * (0.5f * p.csm2 * h1 * t11), m2 = H * h2 * t22 * (0.5f * p.csm2);
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            A1[c] = U1 * Bc[c] - Bc[0] * U[c];   // A_c1 (Eq. 2_C)
-            A2[c] = U2 * Bc[c] - Bc[1] * U[c];   // A_c2
-            // Eqs. gradB1/gradB2 with Lambda^(1) = sum e (g - g^eq(0)) (Eqs.
-            // firstvelmomenttensor1/2); the rest-state moment M of g_ref- cancels
-            // against the B_rest part of the curvature term.
-            const float L1 = (gd[c][1] - gd[c][3]) - h2 * A1[c] + 0.5f * p.csm2 * h1 * H * t11 * dBc[c];
-            const float L2 = (gd[c][2] - gd[c][4]) - h1 * A2[c] + 0.5f * p.csm2 * H * h2 * t22 * dBc[c];
-            dB1[c] = -L1 * __frcp_rn(p.csm2 * (0.5f * H + (p.taum - 0.5f) * h2 * ih1));
-            dB2[c] = -L2 * __frcp_rn(p.csm2 * (0.5f * H + (p.taum - 0.5f) * h1 * ih2));
+            const V L1 = fmav(m1, dBc[c], (gd[c][1] - gd[c][3]) - h2 * A1[c]);
+            const V L2 = fmav(m2, dBc[c], (gd[c][2] - gd[c][4]) - A2[c] * h1);
+            dB1[c] = bc<V>(0.f) - L1 * k1;
+            dB2[c] = bc<V>(0.f) - L2 * k2;
         }
         // current density (Eq. currentdensity-GOC) and Lorentz force (Eq. Lorentzforce-GOC)
-        const float J3 = p.imum * iH * (h2 * dB1[1] - h1 * dB2[0]);
-        FL1 = -J3 * B2;
+        const V J3 = iH * (h2 * dB1[1] - dB2[0] * h1) * p.imum;
+        FL1 = bc<V>(0.f) - J3 * B2;
         FL2 = J3 * B1;
         // SRT collision (Eq. 12_C, S = 0 on straight grids) with g^eq of
         // Eq. EDF-MIE-base plus the correction of Eq. 42_C.  Relative to the
-        // references: s = d - (d - G)/tau_m, G = g^eq - g_ref- without the
+        // references: s = d (1 - 1/tau_m) + G/tau_m, G = g^eq - g_ref- without the
         // B_rest curvature part, which cancels with the change g_ref- -> g_ref+.
+        const V e1c = (H - h2 * ih1) * p.eta, e2c = (H - h1 * ih2) * p.eta;
+        const V m1e = H * (p.eta * h1 * t11), m2e = H * h2 * t22 * p.eta;
+        const float keep = 1.f - p.itaum, w0 = p.W0 * p.itaum, w1 = p.W1 * p.itaum;
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            const float lc1 = p.eta * (H - h2 * ih1) * dB1[c] + p.eta * h1 * H * t11 * dBc[c];
-            const float lc2 = p.eta * (H - h1 * ih2) * dB2[c] + p.eta * H * h2 * t22 * dBc[c];
-            const float x1 = (h2 * A1[c] + lc1) * p.icsm2;
-            const float x2 = (h1 * A2[c] + lc2) * p.icsm2;
+            const V x1 = fmav(h2, A1[c], fmav(e1c, dB1[c], m1e * dBc[c])) * p.icsm2;
+            const V x2 = fmav(h1, A2[c], fmav(e2c, dB2[c], m2e * dBc[c])) * p.icsm2;
+            const V base = H * dBc[c];
+            const V G[5] = {base * w0, (base + x1) * w1, (base + x2) * w1, (base - x1) * w1, (base - x2) * w1};
 #pragma unroll
             for (int a = 0; a < 5; a++) {
-                const float W = a == 0 ? p.W0 : p.W1;
-                const float G = W * (H * dBc[c] + g1(a) * x1 + g2(a) * x2);
-                const float gt = gd[c][a] - (gd[c][a] - G) * p.itaum;
-                Store<S>::st(gout + (c * 5 + a) * p.plane + idx, scl<S>(gt, p.isg));
+                const V gt = fmav(gd[c][a], keep, G[a]);
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                    if (own[r]) Store<S>::st(gout + (c * 5 + a) * p.plane + idx[r], scl<S>(lane(gt, r), p.isg));
             }
         }
     }
 
     // ---- stresses and effective force (straight grid, Appendix B (i)) -------
-    const float zeta = p.zeta, nu = p.nu, cs2 = p.cs2;
-    const float tau11 = rho * ((zeta + nu) * ih1 * dU1 + (zeta - nu) * ih2 * dU2);
-    const float tau22 = rho * ((zeta + nu) * ih2 * dU2 + (zeta - nu) * ih1 * dU1);
+    const float zeta = p.zeta, nu = p.nu;
+    const V g1d = dU1 * ih1, g2d = dU2 * ih2;             // dU1/(h1 dxi1), dU2/(h2 dxi2)
+    const V tau11 = rho * fmav(g1d, zeta + nu, g2d * (zeta - nu));
+    const V tau22 = rho * fmav(g2d, zeta + nu, g1d * (zeta - nu));
     // F = F_rest + F_dev, F_rest = -(h2, h1) rho0 cs2 (theta11, theta22) is the
     // geometric force of the rest state; only F_dev is stored.
-    const float F1dev = h2 * (p.fext1 + FL1 - drho * cs2 * t11 + (tau11 - rho * U1 * U1) * t11);
-    const float F2dev = h1 * (p.fext2 + FL2 - drho * cs2 * t22 + (tau22 - rho * U2 * U2) * t22);
-    const float F1r = -h2 * p.rho0 * cs2 * t11, F2r = -h1 * p.rho0 * cs2 * t22;
-    const float F1 = F1dev + F1r;
-    const float F2 = F2dev + F2r;
+    const V F1dev = h2 * fmav(tau11 - rho * (U1 * U1) - drho * cs2, t11, FL1 + p.fext1);
+    const V F2dev = fmav(tau22 - rho * (U2 * U2) - drho * cs2, t22, FL2 + p.fext2) * h1;
+    const V F1r = h2 * (-p.rho0 * cs2 * t11), F2r = t22 * (-p.rho0 * cs2 * h1);
+    const V F1 = F1dev + F1r;
+    const V F2 = F2dev + F2r;
 
-    // ---- correction coefficients (Eqs. 83, 85; theta12 = theta21 = 0) ------
-    const float r = h2 * ih1, s = h1 * ih2;               // h2/h1, h1/h2
-    const float ics2 = p.ics2;
-    const float a1 = p.gi * U1 * U1 * ics2, a2 = p.gi * U2 * U2 * ics2;
-    const float r1 = r * ih1, s2 = s * ih2;               // h2/h1^2, h1/h2^2
-    const float D31 = rho * (2.f * zeta - (zeta + nu) * r1 - (zeta - nu) * ih2
-                             - zeta * (2.f - h2 * ics2 + (3.f * a1 + 1.f) * r1));
-    const float D32 = rho * (2.f * zeta - (zeta + nu) * s2 - (zeta - nu) * ih1
-                             - zeta * (2.f - h1 * ics2 + (3.f * a2 + 1.f) * s2));
-    const float D33 = -zeta * ((3.f - a1) * r1 - h2 * ics2 - a2 * ih2) * U1;
-    const float D34 = -zeta * ((3.f - a2) * s2 - h1 * ics2 - a1 * ih1) * U2;
-    const float C3 = rho * zeta * (2.f * U1 * (a1 + 1.f) * r * t11 + 2.f * U2 * (a2 + 1.f) * s * t22);
-    const float D41 = rho * (2.f * nu - (zeta + nu) * r1 + (zeta - nu) * ih2
-                             - nu * (2.f - h2 * ics2 + (3.f * a1 + 1.f) * r1));
-    const float D42 = rho * (-2.f * nu + (zeta + nu) * s2 - (zeta - nu) * ih1
-                             - nu * (-2.f + h1 * ics2 - (3.f * a2 + 1.f) * s2));
-    const float D43 = -nu * ((3.f - a1) * r1 - h2 * ics2 + a2 * ih2) * U1;
-    const float D44 = -nu * (-(3.f - a2) * s2 + h1 * ics2 - a1 * ih1) * U2;
-    const float C4 = rho * nu * (2.f * U1 * (a1 + 1.f) * r * t11 - 2.f * U2 * (a2 + 1.f) * s * t22);
-    const float n3 = D31 * dU1 + D32 * dU2 + D33 * dr1 + D34 * dr2 + C3;
-    const float n4 = D41 * dU1 + D42 * dU2 + D43 * dr1 + D44 * dr2 + C4;
+    // ---- normal-gradient corrections (Eqs. 82-85; theta12 = theta21 = 0) -----
+    // The coefficients D3k, D4k, C3, C4 regrouped: with a1 = gi U1^2/cs2,
+    // a2 = gi U2^2/cs2, r1 = h2/h1^2, s2 = h1/h2^2,
+    //   D31 = rho [zeta h2/cs2 - (zeta-nu)/h2 - r1 (2 zeta + nu + 3 zeta a1)],
+    //   D41 = rho [nu h2/cs2 + (zeta-nu)/h2 - r1 (zeta + 2 nu + 3 nu a1)],
+    //   D33 = -zeta U1 (X1 - a2/h2), D43 = -nu U1 (X1 + a2/h2), X1 = (3 - a1) r1 - h2/cs2,
+    // and the mirror images for D32, D42, D34, D44.
+    const V r = h2 * ih1, s = ih2 * h1;                   // h2/h1, h1/h2
+    const V r1 = r * ih1, s2 = s * ih2;                   // h2/h1^2, h1/h2^2
+    const V uu = U1 * U1, vv = U2 * U2, uv = U1 * U2;
+    const V a1 = uu * p.gic, a2 = vv * p.gic;
+    V n3, n4;
+    {
+        const float zmn = p.zmn;
+        const V P31 = fmav(h2, p.zc, ih2 * (-zmn)) - r1 * fmav(a1, 3.f * zeta, p.A3);
+        const V P32 = bc<V>(p.zc * h1 - zmn * ih1) - s2 * fmav(a2, 3.f * zeta, p.A3);
+        const V P41 = fmav(h2, p.nc, ih2 * zmn) - r1 * fmav(a1, 3.f * nu, p.A4);
+        const V P42 = s2 * fmav(a2, 3.f * nu, p.A4) - (p.nc * h1 + zmn * ih1);
+        const V X1 = fmav(3.f - a1, r1, h2 * (-p.ics2)), X2 = fmav(3.f - a2, s2, bc<V>(-h1 * p.ics2));
+        const V b2 = a2 * ih2, b1 = a1 * ih1;
+        const V Y1 = U1 * (a1 + 1.f) * r * (2.f * t11), Y2 = U2 * (a2 + 1.f) * s * t22 * 2.f;
+        const V q3 = fmav(Y1 + Y2, zeta, fmav(P31, dU1, P32 * dU2));
+        const V q4 = fmav(Y1 - Y2, nu, fmav(P41, dU1, P42 * dU2));
+        n3 = rho * q3 - U1 * (X1 - b2) * dr1 * zeta - U2 * (X2 - b1) * dr2 * zeta;
+        n4 = rho * q4 - U1 * (X1 + b2) * dr1 * nu + U2 * (X2 + b1) * dr2 * nu;
+    }
 
-    // ---- central moments of the deviations: c = F(U) P d -------------------
-    const float k00 = d[0] + d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7] + d[8];
-    const float k10 = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
-    const float k01 = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
-    const float k20 = d[1] + d[3] + d[5] + d[6] + d[7] + d[8];
-    const float k02 = d[2] + d[4] + d[5] + d[6] + d[7] + d[8];
-    const float k11 = d[5] - d[6] + d[7] - d[8];
-    const float k21 = d[5] + d[6] - d[7] - d[8];
-    const float k12 = d[5] - d[6] - d[7] + d[8];
-    const float k22 = d[5] + d[6] + d[7] + d[8];
-    const float u = U1, v = U2, uu = u * u, vv = v * v, uv = u * v;
-    // first raw moments of f - f_rest (f_ref- carries -F_rest/2 of momentum)
-    const float K10 = k10 - 0.5f * F1r, K01 = k01 - 0.5f * F2r;
-    const float c20 = k20 - 2.f * u * K10 + uu * k00;
-    const float c02 = k02 - 2.f * v * K01 + vv * k00;
-    const float c11 = k11 - v * K10 - u * K01 + uv * k00;
-    const float c21 = k21 - 2.f * u * k11 + uu * K01 - v * k20 + 2.f * uv * K10 - uu * v * k00;
-    const float c12 = k12 - 2.f * v * k11 + vv * K10 - u * k02 + 2.f * uv * K01 - u * vv * k00;
-    const float c22 = k22 - 2.f * u * k12 + uu * k02 - 2.f * v * k21 + 4.f * uv * k11
-                      - 2.f * uu * v * K01 + vv * k20 - 2.f * u * vv * K10 + uu * vv * k00;
+    // ---- central moments c = F(U) P (f - f_rest) -----------------------------
+    // f - f_rest = d + (f_ref- - f_rest), the latter -F_rest/4 (e . unit) on
+    // links 1..4.  Central moments about (U1, U2) by two passes of the 1D
+    // transform (values at e = -1, 0, +1 -> moments of orders 0, 1, 2 about the
+    // velocity component): first along xi1 within each row of equal e2, then
+    // along xi2 for each xi1 order.
+    const V u = U1, v = U2;
+    const V nu_ = bc<V>(0.f) - u, nv_ = bc<V>(0.f) - v;
+    V k0[3], k1[3], k2[3];                                // per row e2 = -1, 0, +1
+    {
+        const V q1 = F1r * 0.25f, q2 = F2r * 0.25f;
+        const V fm[3] = {d[7], d[3] + q1, d[6]};
+        const V f0[3] = {d[4] + q2, d[0], d[2] - q2};
+        const V fp[3] = {d[8], d[1] - q1, d[5]};
+#pragma unroll
+        for (int y = 0; y < 3; y++) {
+            const V sm_ = fp[y] + fm[y], tm_ = fp[y] - fm[y];
+            k0[y] = sm_ + f0[y];
+            k1[y] = fmav(nu_, k0[y], tm_);
+            k2[y] = fmav(nu_, tm_ + k1[y], sm_);
+        }
+    }
+    V c[3][3];                                            // c[m][n]: order m along xi1, n along xi2
+    {
+        const V *kk[3] = {k0, k1, k2};
+#pragma unroll
+        for (int m = 0; m < 3; m++) {
+            const V sm_ = kk[m][2] + kk[m][0], tm_ = kk[m][2] - kk[m][0];
+            c[m][0] = sm_ + kk[m][1];
+            c[m][1] = fmav(nv_, c[m][0], tm_);
+            c[m][2] = fmav(nv_, tm_ + c[m][1], sm_);
+        }
+    }
+    const V c20 = c[2][0], c02 = c[0][2], c11 = c[1][1], c21 = c[2][1], c12 = c[1][2], c22 = c[2][2];
 
     // ---- n^eq - n in the combined basis (rest parts cancelled) ---------------
-    const float a0 = H * p.rho0, b0 = r * p.rho0 * cs2, c0 = s * p.rho0 * cs2;
-    const float hm1 = h1 - 1.f, hm2 = h2 - 1.f;
-    const float q20 = r * hm1 * hm1, q02 = s * hm2 * hm2, q11 = hm1 * hm2;
-    const float q21 = -hm2 * hm1 * hm1 * ih1, q12 = -hm1 * hm2 * hm2 * ih2;
-    const float e2s = (r + s) * cs2 * drho + q20 * rho * uu + q02 * rho * vv + n3 - (c20 + c02) - (uu + vv) * a0;
-    const float e2d = (r - s) * cs2 * drho + q20 * rho * uu - q02 * rho * vv + n4 - (c20 - c02) - (uu - vv) * a0;
-    const float e11 = q11 * rho * uv - c11 - uv * a0;
-    const float e21 = q21 * rho * uu * v + (1.f - h2) * rho * cs2 * v * ih1 - c21 + v * b0 + uu * v * a0;
-    const float e12 = q12 * rho * u * vv + (1.f - h1) * rho * cs2 * u * ih2 - c12 + u * c0 + u * vv * a0;
-    const float e22 = cs2 * cs2 * drho - c22 - vv * b0 - uu * c0 - uu * vv * a0;
+    const V a0 = H * p.rho0, b0 = r * (p.rho0 * cs2), c0 = s * (p.rho0 * cs2);
+    const float hm1 = h1 - 1.f;
+    const V hm2 = h2 - 1.f;
+    const V q20 = r * (hm1 * hm1), q02 = s * hm2 * hm2, q11 = hm2 * hm1;
+    const V q21 = hm2 * (-hm1 * hm1 * ih1), q12 = hm2 * hm2 * ih2 * (-hm1);
+    const V rq20 = rho * q20 * uu, rq02 = rho * q02 * vv;
+    const V csd = drho * cs2;
+    const V e2s = fmav(r + s, csd, rq20 + rq02 + n3) - (c20 + c02) - (uu + vv) * a0;
+    const V e2d = fmav(r - s, csd, rq20 - rq02 + n4) - (c20 - c02) - (uu - vv) * a0;
+    const V e11 = (rho * q11 - a0) * uv - c11;
+    const V e21 = fmav(v, b0 + (uu * a0), (rho * q21 * uu + rho * (1.f - h2) * ih1 * cs2) * v) - c21;
+    const V e12 = fmav(u, c0 + (vv * a0), (rho * q12 * vv + rho * (1.f - h1) * ih2 * cs2) * u) - c12;
+    const V e22 = csd * cs2 - c22 - vv * b0 - uu * c0 - uu * vv * a0;
 
     // ---- sources (Eq. cmsourcesGOC) and relaxation ---------------------------
-    const float w1 = ih1 - 1.f, w2 = ih2 - 1.f;
-    const float s2s = 2.f * (w1 * F1 * u + w2 * F2 * v);
-    const float s2d = 2.f * (w1 * F1 * u - w2 * F2 * v);
-    const float s11 = w2 * F1 * v + w1 * F2 * u;
+    const float w1 = ih1 - 1.f;
+    const V w2 = ih2 - 1.f;
+    const V fu = F1 * u * w1, fv = F2 * v * w2;
+    const V s2s = (fu + fv) * 2.f;
+    const V s2d = (fu - fv) * 2.f;
+    const V s11 = fmav(w2 * F1, v, F2 * u * w1);
     const float *om = p.om;
     // k10^eq - k10 = F^{n-1}/2 exactly (definition of U), likewise k01.
     // D10d excludes F_rest, which the change of reference f_ref- -> f_ref+ absorbs.
-    const float D10d = om[1] * 0.5f * F1p + (1.f - 0.5f * om[1]) * F1dev;
-    const float D01d = om[2] * 0.5f * F2p + (1.f - 0.5f * om[2]) * F2dev;
-    const float D10 = D10d + F1r, D01 = D01d + F2r;
-    const float D2s = om[3] * e2s + (1.f - 0.5f * om[3]) * s2s;
-    const float D2d = om[4] * e2d + (1.f - 0.5f * om[4]) * s2d;
-    const float D20 = 0.5f * (D2s + D2d), D02 = 0.5f * (D2s - D2d);
-    const float D11 = om[5] * e11 + (1.f - 0.5f * om[5]) * s11;
-    const float D21 = om[6] * e21, D12 = om[7] * e12, D22 = om[8] * e22;
+    const V D10d = fmav(F1p, 0.5f * om[1], F1dev * (1.f - 0.5f * om[1]));
+    const V D01d = fmav(F2p, 0.5f * om[2], F2dev * (1.f - 0.5f * om[2]));
+    const V D2s = fmav(e2s, om[3], s2s * (1.f - 0.5f * om[3]));
+    const V D2d = fmav(e2d, om[4], s2d * (1.f - 0.5f * om[4]));
+    const V D20 = (D2s + D2d) * 0.5f, D02 = (D2s - D2d) * 0.5f;
+    const V D11 = fmav(e11, om[5], s11 * (1.f - 0.5f * om[5]));
+    const V D21 = e21 * om[6], D12 = e12 * om[7], D22 = e22 * om[8];
 
-    // ---- back to raw moments with F(-U) (Delta k00 = 0) ----------------------
-    const float R20 = D20 + 2.f * u * D10;
-    const float R02 = D02 + 2.f * v * D01;
-    const float R11 = D11 + v * D10 + u * D01;
-    const float R21 = D21 + 2.f * u * D11 + uu * D01 + v * D20 + 2.f * uv * D10;
-    const float R12 = D12 + 2.f * v * D11 + vv * D10 + u * D02 + 2.f * uv * D01;
-    const float R22 = D22 + 2.f * u * D12 + uu * D02 + 2.f * v * D21 + 4.f * uv * D11
-                      + 2.f * uu * v * D01 + vv * D20 + 2.f * u * vv * D10;
-
-    // ---- P^-1 and store ------------------------------------------------------
-    float o[9];
-    o[0] = d[0] - R20 - R02 + R22;
-    o[1] = d[1] + 0.5f * (D10d + R20 - R12 - R22);
-    o[2] = d[2] + 0.5f * (D01d + R02 - R21 - R22);
-    o[3] = d[3] + 0.5f * (-D10d + R20 + R12 - R22);
-    o[4] = d[4] + 0.5f * (-D01d + R02 + R21 - R22);
-    o[5] = d[5] + 0.25f * (R11 + R21 + R12 + R22);
-    o[6] = d[6] + 0.25f * (-R11 + R21 - R12 + R22);
-    o[7] = d[7] + 0.25f * (R11 - R21 - R12 + R22);
-    o[8] = d[8] + 0.25f * (-R11 - R21 + R12 + R22);
-    S *fout = static_cast<S *>(p.fout);
+    // ---- back to populations: o = d + P^-1 F(-U) Delta - (f_ref+ - f_ref-) ----
+    // f_ref+ - f_ref- has raw moments r = (0, F1r, F2r, 0, ...); it is taken off
+    // in central-moment space, Delta - F(U) r, whose terms are all small (first
+    // moments D10d, D01d, higher ones shifted by O(U F_rest)).  The inverse
+    // transform runs the 1D passes in reverse order: along xi2, then xi1; for
+    // central moments (c0, c1, c2) about w, the raw moments are m1 = c1 + w c0,
+    // m2 = c2 + 2 w c1 + w^2 c0 and the values at e = 0, +1, -1 are c0 - m2,
+    // (m1 + m2)/2, (m2 - m1)/2.
+    V o[9];
+    {
+        const V uv2 = uv * 2.f;
+        const V g[3][3] = {
+            {bc<V>(0.f), D01d, fmav(v * 2.f, F2r, D02)},
+            {D10d, fmav(v, F1r, fmav(u, F2r, D11)), D12 - vv * F1r - uv2 * F2r},
+            {fmav(u * 2.f, F1r, D20), D21 - uu * F2r - uv2 * F1r, fmav(uv2, fmav(u, F2r, v * F1r), D22)}};
+        V r0[3], rp[3], rn[3];                            // per xi1 order m: rows e2 = 0, +1, -1
 #pragma unroll
-    for (int a = 0; a < 9; a++) Store<S>::st(fout + a * p.plane + idx, scl<S>(o[a], p.isf));
+        for (int m = 0; m < 3; m++) {
+            const V m1 = fmav(v, g[m][0], g[m][1]);
+            const V m2 = fmav(v, g[m][1] + m1, g[m][2]);
+            r0[m] = g[m][0] - m2;
+            rp[m] = (m1 + m2) * 0.5f;
+            rn[m] = (m2 - m1) * 0.5f;
+        }
+        // rows e2 = 0 (links 3, 0, 1), +1 (6, 2, 5), -1 (7, 4, 8)
+        const V *rows[3] = {r0, rp, rn};
+        V o0[3], op[3], on[3];                            // values at e1 = 0, +1, -1 per row
+#pragma unroll
+        for (int y = 0; y < 3; y++) {
+            const V m1 = fmav(u, rows[y][0], rows[y][1]);
+            const V m2 = fmav(u, rows[y][1] + m1, rows[y][2]);
+            o0[y] = rows[y][0] - m2;
+            op[y] = (m1 + m2) * 0.5f;
+            on[y] = (m2 - m1) * 0.5f;
+        }
+        o[0] = d[0] + o0[0];
+        o[1] = d[1] + op[0];
+        o[3] = d[3] + on[0];
+        o[2] = d[2] + o0[1];
+        o[5] = d[5] + op[1];
+        o[6] = d[6] + on[1];
+        o[4] = d[4] + o0[2];
+        o[8] = d[8] + op[2];
+        o[7] = d[7] + on[2];
+    }
+    S *fout = static_cast<S *>(p.fout);
     S *Fout = static_cast<S *>(p.Fout);
-    Store<S>::st(Fout + idx, scl<S>(F1dev, p.isF));
-    Store<S>::st(Fout + p.plane + idx, scl<S>(F2dev, p.isF));
-
-    if (p.uout) {
-        p.uout[idx] = U1;
-        p.uout[p.plane + idx] = U2;
-        p.uout[2 * p.plane + idx] = B1;
-        p.uout[3 * p.plane + idx] = B2;
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        if (!own[q]) continue;
+#pragma unroll
+        for (int a = 0; a < 9; a++) Store<S>::st(fout + a * p.plane + idx[q], scl<S>(lane(o[a], q), p.isf));
+        Store<S>::st(Fout + idx[q], scl<S>(lane(F1dev, q), p.isF));
+        Store<S>::st(Fout + p.plane + idx[q], scl<S>(lane(F2dev, q), p.isF));
+        if (p.uout) {
+            p.uout[idx[q]] = lane(U1, q);
+            p.uout[p.plane + idx[q]] = lane(U2, q);
+            p.uout[2 * p.plane + idx[q]] = lane(B1, q);
+            p.uout[3 * p.plane + idx[q]] = lane(B2, q);
+        }
     }
     if (p.flag) {   // divergence flag: one atomic per warp at most
-        const bool bad = !(rho > 0.f && fabsf(U1) + fabsf(U2) < 1e30f);
-        const unsigned m = __activemask();
-        if (__any_sync(m, bad) && (threadIdx.x & 31) == (__ffs(m) - 1) && *((volatile int *)p.flag) == 0)
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const float rq = lane(rho, q), uq = fabsf(lane(U1, q)) + fabsf(lane(U2, q));
+            bad = bad || (own[q] && !(rq > 0.f && uq < 1e30f));
+        }
+        const unsigned mk = __activemask();
+        if (__any_sync(mk, bad) && (threadIdx.x & 31) == (__ffs(mk) - 1) && *((volatile int *)p.flag) == 0)
             atomicExch(p.flag, 1);
     }
 }
 
 // One tile of one lattice from a given source; KIND 0: interior (no boundary
 // logic, fields halo 1), 1: near a boundary (fields halo 2 where inside).
-// Every thread pulls its own node into registers (kept across the barrier for
-// the collision); the ring of halo nodes around the tile is shared out over the
-// threads.  Contains a block barrier: every thread of the block must call it.
+// Each thread pulls its RPT nodes (column i0 + tx, rows ty + r TYT) into
+// registers (kept across the barrier for the collision); the ring of halo
+// nodes around the tile is shared out over the threads.  Contains a block
+// barrier: every thread of the block must call it.
 template <class S, bool MHD, int KIND, class Src>
 __device__ __forceinline__ void tile_compute(const StepParams &p, const Src &src, int i0, int j0, FieldSmem &sm) {
     constexpr bool CHECKS = KIND != 0;
     constexpr int W = KIND == 0 ? 1 : MH;                 // halo width of the fields
     constexpr int BAND = W * (TX + 2 * W);                // nodes in the top (or bottom) band
     constexpr int RING = 2 * BAND + 2 * W * TY;
+    constexpr int R = RPT;
+    using V = typename VecOf<R>::type;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool own = i < p.nx && j < p.ny;
-    float d[9], F1p = 0.f, F2p = 0.f, h1 = 1.f, h2 = 1.f, ih1 = 1.f, ih2 = 1.f;
-    {   // own node
+    const int tx = threadIdx.x;
+    const int i = i0 + tx;
+    const bool inx = i < p.nx;
+    float h1 = 1.f, ih1 = 1.f;
+    if (inx) {
+        h1 = p.ax1.h[i];
+        ih1 = p.ax1.ih[i];
+    }
+    int j[R], ty[R];
+    bool own[R];
+    float d[R][9], F1p[R], F2p[R], h2[R], ih2[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {   // own nodes
+        ty[r] = threadIdx.y + r * TYT;
+        j[r] = j0 + ty[r];
+        own[r] = inx && j[r] < p.ny;
         float drho = 0.f, U1 = 0.f, U2 = 0.f;
-        if (own) {
-            h1 = p.ax1.h[i];
-            h2 = p.ax2.h[j];
-            ih1 = p.ax1.ih[i];
-            ih2 = p.ax2.ih[j];
-            pull_node<CHECKS>(p, src, i, j, h1, h2, d);
-            F1p = src.Fv(0, i, j);
-            F2p = src.Fv(1, i, j);
-            fields_from(p, d, F1p, F2p, ih1, ih2, drho, U1, U2);
+        F1p[r] = F2p[r] = 0.f;
+        h2[r] = ih2[r] = 1.f;
+#pragma unroll
+        for (int a = 0; a < 9; a++) d[r][a] = 0.f;
+        if (own[r]) {
+            h2[r] = p.ax2.h[j[r]];
+            ih2[r] = p.ax2.ih[j[r]];
+            pull_node<CHECKS>(p, src, i, j[r], h1, h2[r], d[r]);
+            F1p[r] = src.Fv(0, i, j[r]);
+            F2p[r] = src.Fv(1, i, j[r]);
+            fields_from(p, d[r], F1p[r], F2p[r], ih1, ih2[r], drho, U1, U2);
         } else if (CHECKS) {   // ragged tile: past the last node of a periodic axis sits the wrapped node
-            int ii = i, jj = j;
+            int ii = i, jj = j[r];
             bool in = true;
             if (ii >= p.nx) {
                 if (p.per_x) ii = wrapi(ii, p.nx); else in = false;
@@ -516,20 +644,20 @@ __device__ __forceinline__ void tile_compute(const StepParams &p, const Src &src
                 fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), p.ax1.ih[ii], p.ax2.ih[jj], drho, U1, U2);
             }
         }
-        sm.rho[ty + MH][tx + MH] = drho;
-        sm.u1[ty + MH][tx + MH] = U1;
-        sm.u2[ty + MH][tx + MH] = U2;
+        sm.rho[ty[r] + MH][tx + MH] = drho;
+        sm.u1[ty[r] + MH][tx + MH] = U1;
+        sm.u2[ty[r] + MH][tx + MH] = U2;
     }
     // halo ring: top band, bottom band, left band, right band
-    for (int r = tid; r < RING; r += NT) {
+    for (int q = tid; q < RING; q += NT) {
         int x, y;
-        if (r < 2 * BAND) {
-            const int b = r < BAND ? r : r - BAND;
+        if (q < 2 * BAND) {
+            const int b = q < BAND ? q : q - BAND;
             const int row = b / (TX + 2 * W);
             x = b - row * (TX + 2 * W) - W;
-            y = r < BAND ? row - W : TY + row;
+            y = q < BAND ? row - W : TY + row;
         } else {
-            const int b = r - 2 * BAND;
+            const int b = q - 2 * BAND;
             const int side = b / (W * TY), bb = b - side * (W * TY);
             const int col = bb / TY;
             y = bb - col * TY;
@@ -556,7 +684,10 @@ __device__ __forceinline__ void tile_compute(const StepParams &p, const Src &src
         sm.u2[y + MH][x + MH] = U2;
     }
     __syncthreads();
-    if (own) node_update<S, MHD, CHECKS>(p, src, i, j, tx, ty, sm, d, F1p, F2p, h1, h2, ih1, ih2);
+    bool any = false;
+#pragma unroll
+    for (int r = 0; r < R; r++) any = any || own[r];
+    if (any) node_update<S, MHD, CHECKS, V>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
 }
 
 // Kind of a tile: 0 interior (all pull sources of the tile and its fields
