@@ -37,7 +37,8 @@ import goc_inputs as gi  # noqa: E402
 
 METRIC = "MLUPS & % of HBM peak (FP32 vs FP16 store); batched p50/p99 solve latency"
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_cavity512_fp32.txt")
-KERNEL_SOURCES = ["paper_2607_15362_b300/csrc/goc_step.cuh", "paper_2607_15362_b300/csrc/goc_device.cuh"]
+KERNEL_SOURCES = ["paper_2607_15362_b300/csrc/goc_step.cuh", "paper_2607_15362_b300/csrc/goc_device.cuh",
+                  "paper_2607_15362_b300/csrc/goc_vec.cuh"]
 
 
 def kernel_hash() -> str:

@@ -109,6 +109,9 @@ typedef struct {
     void *cuda_stream;      /* cudaStream_t for all work of this lattice; NULL = default stream */
     int device;             /* CUDA device ordinal; < 0 = current device */
     int check_every;        /* goc_run_until: steps between residual checks; 0 -> 100 */
+    int rounding;           /* FP16/BF16 storage: 0 = stochastic rounding of every stored value
+                               (unbiased, so increments below half a unit in the last place
+                               are kept on average), 1 = round to nearest; ignored for FP32 */
 } goc_exec;
 
 /* ---- lifecycle --------------------------------------------------------- */

@@ -83,6 +83,7 @@ struct goc_lattice {
     bool res_pending = false;                    // residual sums of a batch step wait in red[4..7]
     CUtensorMap tmf[2], tmF[2], tmg[2];          // TMA descriptors of both buffers
     bool tma_ok = false;
+    int rounding = 0;                            // goc_exec.rounding
 };
 
 namespace {
@@ -180,6 +181,9 @@ StepParams params_for(goc_lattice *L, int src, float *uout) {
     p.gin = L->g[src];
     p.gout = L->g[src ^ 1];
     p.uout = uout;
+    p.sr = (L->storage != GOC_FP32 && L->rounding == 0) ? 1 : 0;
+    p.seed_rd = reinterpret_cast<const unsigned *>(L->flag + 2 + src);
+    p.seed_wr = reinterpret_cast<unsigned *>(L->flag + 2 + (src ^ 1));
     p.use_tma = L->tma_ok ? 1 : 0;
     if (L->tma_ok) {
         p.tm_f = L->tmf[src];
@@ -371,6 +375,8 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
     L->steps = 0;
     L->res_u = L->res_b = 0.0;
     L->fresh = true;
+    if (cudaMemsetAsync(L->flag + 2, 0, 2 * sizeof(int), L->stream) != cudaSuccess)   // step counters
+        return fail(GOC_ECUDA, "memset failed");
     return GOC_OK;
 }
 
@@ -460,6 +466,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         L->storage = exec->storage;
         L->stream = (cudaStream_t)exec->cuda_stream;
         L->check_every = exec->check_every > 0 ? exec->check_every : 100;
+        L->rounding = exec->rounding;
         if (exec->device >= 0) {
             cudaError_t e = cudaSetDevice(exec->device);
             if (e != cudaSuccess) {
@@ -491,7 +498,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     TRY(dalloc(L, &L->tab2, 7 * (size_t)L->ny * sizeof(float)));
     TRY(dalloc(L, &L->m1, 2 * (size_t)(L->nx + 2) * sizeof(double)));
     TRY(dalloc(L, &L->m2, 2 * (size_t)(L->ny + 2) * sizeof(double)));
-    TRY(dalloc(L, &L->flag, sizeof(int)));
+    TRY(dalloc(L, &L->flag, 4 * sizeof(int)));   // [0] status, [1] spare, [2..3] step counters of the two parities
     TRY(dalloc(L, &L->red, 8 * sizeof(double)));
     // metric (FP64), q, cs2 (Eq. GOC-LBE_CFL)
     TRY(compute_metric(grid, map, L->stream, L->m1, L->m2, L->red));
@@ -630,7 +637,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     if (std::getenv("GOC_DISABLE_TMA")) L->tma_ok = false;
     TRY(run_init(L, nullptr, nullptr, nullptr, nullptr, nullptr));
     {
-        cudaError_t e = cudaMemsetAsync(L->flag, 0, sizeof(int), L->stream);
+        cudaError_t e = cudaMemsetAsync(L->flag, 0, 4 * sizeof(int), L->stream);
         if (e != cudaSuccess) {
             free_lattice(L);
             return fail(GOC_ECUDA, "memset failed");
@@ -830,6 +837,8 @@ goc_status goc_set_state(goc_lattice *L, const void *buf, size_t bytes) {
     CU(cudaMemcpyAsync(L->f[L->cur], c + 64, nf, cudaMemcpyHostToDevice, L->stream));
     CU(cudaMemcpyAsync(L->F[L->cur], c + 64 + nf, nF, cudaMemcpyHostToDevice, L->stream));
     if (ng) CU(cudaMemcpyAsync(L->g[L->cur], c + 64 + nf + nF, ng, cudaMemcpyHostToDevice, L->stream));
+    const unsigned step = (unsigned)hdr[5];   // the stochastic-rounding stream continues from the saved step
+    CU(cudaMemcpyAsync(L->flag + 2 + L->cur, &step, sizeof(unsigned), cudaMemcpyHostToDevice, L->stream));
     CU(cudaStreamSynchronize(L->stream));
     L->steps = hdr[5];
     L->fresh = hdr[7] != 0;
@@ -846,6 +855,7 @@ struct goc_batch {
     long long budget = 0, used = 0;
     int max_lat = 0;
     int storage = GOC_FP32;
+    int rounding = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
     std::vector<goc_lattice *> slots;
@@ -994,6 +1004,7 @@ goc_status goc_batch_create(long long hbm_budget_bytes, int max_lattices, const 
     B->max_lat = max_lattices;
     if (exec) {
         B->storage = exec->storage;
+        B->rounding = exec->rounding;
         B->stream = (cudaStream_t)exec->cuda_stream;
         if (exec->device >= 0) cudaSetDevice(exec->device);
     }
@@ -1034,6 +1045,7 @@ goc_status goc_batch_add(goc_batch *B, const goc_grid *grid, const goc_map *map,
     ex.storage = storage;
     ex.cuda_stream = B->stream;
     ex.device = -1;
+    ex.rounding = B->rounding;
     goc_lattice *L = nullptr;
     goc_status st = goc_create(grid, map, flow, mhd, &ex, &L);
     if (st != GOC_OK) return st;

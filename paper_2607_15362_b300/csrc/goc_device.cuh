@@ -68,6 +68,12 @@ struct StepParams {
     // optional outputs
     float *uout;               // [4][plane]: U1, U2, B1, B2 of this step's time level (may be null)
     int *flag;                 // status flag (may be null): 1 divergence, 2 a TMA wait timed out
+    // stochastic rounding of 16-bit stores: the step index of this launch is
+    // read from *seed_rd and seed_rd + 1 written to *seed_wr (the counter the
+    // launch of the other buffer parity reads)
+    int sr;
+    const unsigned *seed_rd;
+    unsigned *seed_wr;
     // TMA descriptors of the input buffers (3D: [planes][ny][nx])
     int use_tma;
     CUtensorMap tm_f;          // box [9][TY + 2 HYS][TX + 2 HXS]
@@ -82,22 +88,59 @@ template <> struct Store<float> {
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ float lds(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ void st_sr(float *p, float v, uint32_t &) { *p = v; }
 };
+// Stochastic rounding (st_sr): u, uniform in [0, 2^k) with k the number of
+// FP32 significand bits the format drops (13 for FP16, 16 for BF16), is added
+// to the magnitude bits and the sum truncated toward zero, which rounds away
+// from zero with probability equal to the dropped fraction (IEEE formats are
+// sign-magnitude, so the same holds for negative values).  The random stream
+// is a 32-bit LCG (multiplier 747796405, increment 2891336453) whose high bits
+// are used.
+__device__ __forceinline__ uint32_t lcg_next(uint32_t &r) {
+    r = r * 747796405u + 2891336453u;
+    return r;
+}
 template <> struct Store<__half> {
     static constexpr bool scaled = true;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void st_sr(__half *p, float v, uint32_t &r) {
+        *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (lcg_next(r) >> 19)));
+    }
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr bool scaled = true;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, uint32_t &r) {
+        *p = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (lcg_next(r) >> 16)));
+    }
 };
 
 // value * scale for 16-bit storage, value unchanged for FP32
 template <class S> __device__ __forceinline__ float scl(float v, float s) { return Store<S>::scaled ? v * s : v; }
+
+// Seed of a node's random stream: the 32-bit finaliser of MurmurHash3 applied
+// to a mix of the node index and the step index.
+__device__ __forceinline__ uint32_t node_seed(uint32_t idx, uint32_t step) {
+    uint32_t h = idx * 0x9E3779B1u ^ (step * 0x85EBCA77u + 0x27D4EB2Fu);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// store of one value: stochastic rounding for 16-bit storage when asked for
+template <class S>
+__device__ __forceinline__ void put(S *p, float v, bool sr, uint32_t &r) {
+    if (Store<S>::scaled && sr) Store<S>::st_sr(p, v, r);
+    else Store<S>::st(p, v);
+}
 
 __device__ __forceinline__ int wrapi(int k, int n) {
     k %= n;

@@ -332,6 +332,14 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
     long long idx[R];
 #pragma unroll
     for (int r = 0; r < R; r++) idx[r] = (long long)j[r] * p.pitch + i;
+    // random streams of the stochastic rounding (16-bit storage), one per node
+    const bool sr = Store<S>::scaled && p.sr;
+    uint32_t rng[R];
+    {
+        const uint32_t step = sr ? *p.seed_rd : 0u;
+#pragma unroll
+        for (int r = 0; r < R; r++) rng[r] = sr ? node_seed((uint32_t)idx[r], step) : 0u;
+    }
     V FL1 = bc<V>(0.f), FL2 = bc<V>(0.f), B1 = bc<V>(0.f), B2 = bc<V>(0.f);
 
     // ---- MIE (Appendix G): local dB, J3, Lorentz force, SRT collision -------
@@ -399,7 +407,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
                 const V gt = fmav(gd[c][a], keep, G[a]);
 #pragma unroll
                 for (int r = 0; r < R; r++)
-                    if (own[r]) Store<S>::st(gout + (c * 5 + a) * p.plane + idx[r], scl<S>(lane(gt, r), p.isg));
+                    if (own[r]) put<S>(gout + (c * 5 + a) * p.plane + idx[r], scl<S>(lane(gt, r), p.isg), sr, rng[r]);
             }
         }
     }
@@ -563,9 +571,9 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
     for (int q = 0; q < R; q++) {
         if (!own[q]) continue;
 #pragma unroll
-        for (int a = 0; a < 9; a++) Store<S>::st(fout + a * p.plane + idx[q], scl<S>(lane(o[a], q), p.isf));
-        Store<S>::st(Fout + idx[q], scl<S>(lane(F1dev, q), p.isF));
-        Store<S>::st(Fout + p.plane + idx[q], scl<S>(lane(F2dev, q), p.isF));
+        for (int a = 0; a < 9; a++) put<S>(fout + a * p.plane + idx[q], scl<S>(lane(o[a], q), p.isf), sr, rng[q]);
+        put<S>(Fout + idx[q], scl<S>(lane(F1dev, q), p.isF), sr, rng[q]);
+        put<S>(Fout + p.plane + idx[q], scl<S>(lane(F2dev, q), p.isF), sr, rng[q]);
         if (p.uout) {
             p.uout[idx[q]] = lane(U1, q);
             p.uout[p.plane + idx[q]] = lane(U2, q);
@@ -747,6 +755,7 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_c
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
+        if (Store<S>::scaled && p.sr && blockIdx.x == 0) *p.seed_wr = *p.seed_rd + 1u;   // next step's index
     }
     __syncthreads();
     int t = blockIdx.x;
@@ -844,6 +853,7 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const St
             if (leader) s_k = k;
         }
         const StepParams &p = *reinterpret_cast<const StepParams *>(s_par);
+        if (Store<S>::scaled && p.sr && leader && i0 == 0 && j0 == 0) *p.seed_wr = *p.seed_rd + 1u;
         const int kind = tile_kind<S>(p, i0, j0);
         if (kind != 2) {
             uint32_t &ph = stage ? ph1 : ph0;

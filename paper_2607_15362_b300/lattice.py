@@ -66,12 +66,16 @@ def metric_info(spec: dict):
     return q.value, cs2.value
 
 
-def _exec(storage: str, stream, check_every: int) -> GocExec:
+ROUNDING = {"stochastic": 0, "nearest": 1}
+
+
+def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic") -> GocExec:
     e = GocExec()
     e.storage = _abi.STORAGE[storage]
     e.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
     e.device = -1
     e.check_every = int(check_every)
+    e.rounding = ROUNDING[rounding]
     return e
 
 
@@ -79,7 +83,7 @@ class Lattice:
     """One lattice owned by libgoc."""
 
     def __init__(self, spec: dict, storage: str = "fp32", stream=None, check_every: int = 100,
-                 _handle=None, _owner=None):
+                 rounding: str = "stochastic", _handle=None, _owner=None):
         self.spec = spec
         self.nx, self.ny = int(spec["nx"]), int(spec["ny"])
         self.storage = storage
@@ -88,7 +92,7 @@ class Lattice:
             self._h = _handle
         else:
             g, m, f, h = structs_from_spec(spec)
-            e = _exec(storage, stream, check_every)
+            e = _exec(storage, stream, check_every, rounding)
             out = ctypes.c_void_p()
             check(lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f),
                                    ctypes.byref(h), ctypes.byref(e), ctypes.byref(out)))
@@ -183,8 +187,9 @@ class Batch:
     """Many independent lattices advanced together (one persistent launch
     per time step, captured in CUDA graphs)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_lattices: int, storage: str = "fp32", stream=None):
-        e = _exec(storage, stream, 100)
+    def __init__(self, hbm_budget_bytes: int, max_lattices: int, storage: str = "fp32", stream=None,
+                 rounding: str = "stochastic"):
+        e = _exec(storage, stream, 100, rounding)
         out = ctypes.c_void_p()
         check(lib().goc_batch_create(int(hbm_budget_bytes), int(max_lattices), ctypes.byref(e), ctypes.byref(out)))
         self._h = out

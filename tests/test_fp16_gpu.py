@@ -1,0 +1,92 @@
+"""16-bit population storage (scaled deviations, FP32 arithmetic) against the
+FP64 oracle, with stochastic and with nearest rounding of the stored values.
+
+Round to nearest loses every per-step change smaller than half a unit in the
+last place of FP16 (11 significant bits), which stalls slowly evolving flows;
+stochastic rounding keeps those changes on average.  Tolerances are about
+twice the errors measured on a B300 (FP16 stochastic: cfg1 8.7e-4, cavity
+4.7e-4, Hartmann strip U 2.3e-3 / B1 4.2e-3 after 2000 steps; round to nearest:
+6.8e-3, 8.5e-4, 1.9e-2 / 6.6e-2).
+"""
+import numpy as np
+import pytest
+
+import goc_inputs as gi
+import oracle
+import paper_2607_15362_b300 as goc
+
+pytestmark = pytest.mark.gpu
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def spec_of(prob):
+    return prob.lattice_spec(oracle.build_metric(prob.lattice_spec(1.0)).cs2())
+
+
+CAVITY = gi.Problem("cavity", 64, 48, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
+                    {"Re": 100.0, "u_lid": 0.05, "mach_matched": True})
+HARTMANN_STRIP = gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
+                            {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0})
+
+
+@pytest.mark.parametrize("name,prob,tol_u,tol_b", [
+    ("cfg1", gi.cfg1_poiseuille(), 2e-3, None),
+    ("cavity", CAVITY, 1.5e-3, None),
+    ("hartmann strip", HARTMANN_STRIP, 5e-3, 1e-2),
+])
+def test_fp16_stochastic_rounding_matches_the_oracle(gpu, name, prob, tol_u, tol_b):
+    spec = spec_of(prob)
+    steps = 2000
+    o = oracle.Oracle(spec, threads=8)
+    o.step(steps)
+    fo = o.fields()
+    L = goc.Lattice(spec, storage="fp16", rounding="stochastic")
+    L.step(steps)
+    fg = L.moments()
+    L.close()
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= tol_u
+    if tol_b is not None:
+        assert relerr(fg[3], fo[3]) <= tol_b
+
+
+def test_stochastic_rounding_beats_nearest_on_a_slow_flow(gpu):
+    """cfg1 after 2000 steps: the body force builds the profile by increments
+    far below FP16 resolution; nearest rounding stalls, stochastic does not."""
+    p = gi.cfg1_poiseuille()
+    spec = spec_of(p)
+    o = oracle.Oracle(spec, threads=8)
+    o.step(2000)
+    uo = o.fields()[1]
+    err = {}
+    for rd in ("nearest", "stochastic"):
+        L = goc.Lattice(spec, storage="fp16", rounding=rd)
+        L.step(2000)
+        err[rd] = relerr(L.moments()[1], uo)
+        L.close()
+    assert err["stochastic"] < 0.3 * err["nearest"]
+
+
+def test_stochastic_rounding_is_reproducible_and_checkpointable(gpu):
+    """The random bits are a function of (node, step): two runs agree bitwise,
+    and a run restored from a checkpoint continues the same stream."""
+    spec = spec_of(CAVITY)
+    runs = []
+    for _ in range(2):
+        L = goc.Lattice(spec, storage="fp16")
+        L.step(300)
+        runs.append(L.get_state())
+        L.close()
+    assert runs[0] == runs[1]
+    A = goc.Lattice(spec, storage="fp16")
+    A.step(150)
+    st = A.get_state()
+    A.step(150)
+    B = goc.Lattice(spec, storage="fp16")
+    B.set_state(st)
+    B.step(150)
+    assert A.get_state() == B.get_state()
+    A.close()
+    B.close()
