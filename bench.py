@@ -329,6 +329,108 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def _centrelines(prob, fields, u_lid):
+    """Velocity profiles of a square cavity along its two centrelines, at the
+    physical node positions, normalised by the side and the lid speed:
+    u1 on x = L/2 against y/L, u2 on y = L/2 against x/L.  With an even node
+    count and a symmetric map the centreline lies half-way between the two
+    middle columns (rows), whose average is taken."""
+    import numpy as np
+
+    def positions(m, n):
+        eta = (np.arange(n) + 0.5) / n
+        if m.get("kind", "uniform") == "uniform":
+            return eta
+        b = float(m["beta"])
+        return 0.5 * (1.0 + np.tanh(b * (2.0 * eta - 1.0)) / np.tanh(b))
+
+    n = prob.nx
+    assert n == prob.ny and n % 2 == 0
+    y = positions(prob.map2, n)
+    x = positions(prob.map1, n)
+    u = 0.5 * (fields[1][:, n // 2 - 1] + fields[1][:, n // 2]) / u_lid
+    v = 0.5 * (fields[2][n // 2 - 1, :] + fields[2][n // 2, :]) / u_lid
+    return y, u, x, v
+
+
+def run_accuracy(args):
+    """Matched accuracy: the GOC cavity (512^2, tanh beta = 2) against the
+    standard uniform-grid LBM at several sizes, all at the same Reynolds and
+    Mach numbers and the same dimensionless time t* = t u_lid / L, each
+    compared on the centreline profiles with a uniform 2048^2 run of the
+    standard scheme (FP32) as the reference."""
+    import numpy as np
+    import torch
+
+    import paper_2607_15362_b300 as goc
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    tstar = args.tstar
+
+    def run(prob, scheme):
+        if scheme == "standard":
+            spec = prob.lattice_spec(1.0 / 3.0)
+        else:
+            _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
+            spec = prob.lattice_spec(cs2)
+        u_lid = spec["walls"]["N"]["u"]
+        steps = int(round(tstar * prob.nx / u_lid))
+        lat = goc.Lattice(spec, scheme=scheme, stream=stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        fields = lat.moments()
+        lat.close()
+        return {"n": prob.nx, "steps": steps, "seconds": ms / 1e3, "mlups": prob.nodes * steps / ms / 1e3,
+                "profiles": _centrelines(prob, fields, u_lid)}
+
+    ref = run(gi.cfg2_uniform_comparator(n=args.ref_n), "standard")
+    ry, ru, rx, rv = ref["profiles"]
+
+    def err(r):
+        y, u, x, v = r["profiles"]
+        # reference interpolated to the nodes, closed by the wall values (u = 1 at the lid)
+        uref = np.interp(y, np.concatenate([[0.0], ry, [1.0]]), np.concatenate([[0.0], ru, [1.0]]))
+        vref = np.interp(x, np.concatenate([[0.0], rx, [1.0]]), np.concatenate([[0.0], rv, [0.0]]))
+        return float(np.sqrt((np.sum((u - uref) ** 2) + np.sum((v - vref) ** 2))
+                             / (np.sum(uref ** 2) + np.sum(vref ** 2))))
+
+    rows = []
+    goc_r = run(gi.cfg2_cavity(n=512), "goc")
+    rows.append({"scheme": "goc tanh beta=2", **{k: goc_r[k] for k in ("n", "steps", "seconds", "mlups")},
+                 "centreline_rel_err": err(goc_r)})
+    for n in args.uniform_sizes:
+        r = run(gi.cfg2_uniform_comparator(n=n), "standard")
+        rows.append({"scheme": "standard uniform", **{k: r[k] for k in ("n", "steps", "seconds", "mlups")},
+                     "centreline_rel_err": err(r)})
+    for r in rows:
+        r["seconds"] = round(r["seconds"], 3)
+        r["mlups"] = round(r["mlups"], 1)
+        r["centreline_rel_err"] = float(f"{r['centreline_rel_err']:.4g}")
+    # uniform size and time at the GOC error (log-log interpolation between measured sizes)
+    uni = sorted([r for r in rows if r["scheme"] == "standard uniform"], key=lambda r: r["n"])
+    target = rows[0]["centreline_rel_err"]
+    match = None
+    for a, b in zip(uni, uni[1:]):
+        ea, eb = a["centreline_rel_err"], b["centreline_rel_err"]
+        if (ea - target) * (eb - target) <= 0 and ea != eb:
+            w = (np.log(target) - np.log(ea)) / (np.log(eb) - np.log(ea))
+            n = float(np.exp(np.log(a["n"]) + w * (np.log(b["n"]) - np.log(a["n"]))))
+            t = float(np.exp(np.log(a["seconds"]) + w * (np.log(b["seconds"]) - np.log(a["seconds"]))))
+            match = {"uniform_n": round(n, 1), "uniform_seconds": round(t, 3),
+                     "goc_seconds": rows[0]["seconds"], "goc_speedup_at_matched_accuracy": round(t / rows[0]["seconds"], 3)}
+            break
+    line = {"metric": METRIC, "workload": f"cfg2 cavity matched accuracy at t* = {tstar}", "unit": "MLUPS",
+            "reference": {"scheme": "standard uniform FP32", "n": ref["n"], "steps": ref["steps"],
+                          "mlups": round(ref["mlups"], 1)},
+            "runs": rows, "matched": match}
+    print(json.dumps(line))
+
+
 def cpu_baseline(prob, spec_lib, budget_s: float = 15.0):
     """FP64 oracle, as it stands, on this host's cores: a bounded number of
     time steps of the same 512^2 cavity, scaled to MLUPS."""
@@ -392,7 +494,10 @@ def main():
     ap.add_argument("--cavity-n", type=int, default=512, help="cavity side (512 is the benchmark workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "batch", "serve"])
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "batch", "serve", "accuracy"])
+    ap.add_argument("--tstar", type=float, default=5.0, help="accuracy workload: dimensionless time t u_lid / L")
+    ap.add_argument("--ref-n", type=int, default=2048, help="accuracy workload: reference grid side")
+    ap.add_argument("--uniform-sizes", type=int, nargs="+", default=[256, 384, 512, 768, 1024])
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -403,6 +508,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "accuracy":
+        run_accuracy(args)
     else:
         run_ours(args)
 

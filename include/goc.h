@@ -112,6 +112,11 @@ typedef struct {
     int rounding;           /* FP16/BF16 storage: 0 = stochastic rounding of every stored value
                                (unbiased, so increments below half a unit in the last place
                                are kept on average), 1 = round to nearest; ignored for FP32 */
+    int scheme;             /* 0 = the GOC-LBM step (default); 1 = the standard uniform-grid
+                               central-moment LBM (the comparator: the GOC step at h1 = h2 = 1,
+                               local collision, no stored force); scheme 1 requires uniform
+                               maps on both axes, gi_correction = 0 and no MIE (else
+                               GOC_EINVAL); lattices added by goc_batch_add use scheme 0 */
 } goc_exec;
 
 /* ---- lifecycle --------------------------------------------------------- */

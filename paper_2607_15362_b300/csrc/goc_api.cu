@@ -14,6 +14,7 @@
 #include "../../include/goc.h"
 #include "goc_aux.cuh"
 #include "goc_device.cuh"
+#include "goc_std.cuh"
 #include "goc_step.cuh"
 
 using namespace goc;
@@ -84,6 +85,7 @@ struct goc_lattice {
     CUtensorMap tmf[2], tmF[2], tmg[2];          // TMA descriptors of both buffers
     bool tma_ok = false;
     int rounding = 0;                            // goc_exec.rounding
+    int scheme = 0;                              // goc_exec.scheme
 };
 
 namespace {
@@ -158,7 +160,16 @@ int step_grid(int ntiles, size_t *smem) {
 }
 
 template <class S>
+goc_status launch_std_t(goc_lattice *L, const StepParams &p) {
+    dim3 grid((L->nx + STD_BX - 1) / STD_BX, (L->ny + STD_BY - 1) / STD_BY), block(STD_BX, STD_BY);
+    std_step_kernel<S><<<grid, block, 0, L->stream>>>(p);
+    CU(cudaGetLastError());
+    return GOC_OK;
+}
+
+template <class S>
 goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
+    if (L->scheme == 1) return launch_std_t<S>(L, p);
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
     if (L->mhd.enabled) {
@@ -446,6 +457,14 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     if (!(flow->rho0 > 0.0)) return fail(GOC_EINVAL, "rho0 must be > 0");
     if (flow->nu <= 0.0 && !(flow->tau > 0.5)) return fail(GOC_EINVAL, "need nu > 0 or tau > 1/2");
     if (exec && (exec->storage < 0 || exec->storage > 2)) return fail(GOC_EINVAL, "unknown storage %d", exec->storage);
+    if (exec && (exec->scheme < 0 || exec->scheme > 1)) return fail(GOC_EINVAL, "unknown scheme %d", exec->scheme);
+    if (exec && exec->scheme == 1) {
+        const bool uni = map && (map->kind[0] == GOC_MAP_UNIFORM || (map->kind[0] == GOC_MAP_TANH2 && map->beta[0] == 0.0)) &&
+                         (map->kind[1] == GOC_MAP_UNIFORM || (map->kind[1] == GOC_MAP_TANH2 && map->beta[1] == 0.0));
+        if (!uni) return fail(GOC_EINVAL, "the standard uniform-grid scheme needs uniform maps on both axes");
+        if (flow->gi_correction) return fail(GOC_EINVAL, "the standard uniform-grid scheme needs gi_correction = 0");
+        if (mhd && mhd->enabled) return fail(GOC_EINVAL, "the standard uniform-grid scheme has no MIE");
+    }
     goc_lattice *L = new (std::nothrow) goc_lattice();
     if (!L) return fail(GOC_ENOMEM, "host allocation failed");
     L->grid = *grid;
@@ -467,6 +486,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         L->stream = (cudaStream_t)exec->cuda_stream;
         L->check_every = exec->check_every > 0 ? exec->check_every : 100;
         L->rounding = exec->rounding;
+        L->scheme = exec->scheme;
         if (exec->device >= 0) {
             cudaError_t e = cudaSetDevice(exec->device);
             if (e != cudaSuccess) {
@@ -584,6 +604,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     p.fext1 = (float)L->flow.fext[0];
     p.fext2 = (float)L->flow.fext[1];
     p.gi = L->flow.gi_correction ? 1.f : 0.f;
+    p.constF = L->scheme == 1 ? 1 : 0;
     p.zc = (float)(L->zeta / L->cs2);
     p.nc = (float)(L->nu / L->cs2);
     p.zmn = (float)(L->zeta - L->nu);
@@ -703,6 +724,7 @@ goc_status goc_footprint(const goc_lattice *L, long long *nodes, long long *byte
 double goc_bytes_per_node(const goc_lattice *L) {
     if (!L) return 0.0;
     const double es = (double)elem_size(L->storage);
+    if (L->scheme == 1) return 2.0 * 9.0 * es;          // populations only, read + write
     double b = 2.0 * (9.0 + 2.0) * es;                  // populations + stored force, read + write
     if (L->mhd.enabled) b += 2.0 * 10.0 * es;           // MIE populations
     b += 4.0 * 7.0 * (1.0 / L->ny + 1.0 / L->nx);       // per-axis tables amortised over the lattice

@@ -221,7 +221,10 @@ __global__ void moments_kernel(const StepParams p, double *out) {
     float d[9];
     pull_node<true>(p, src, i, j, h1, h2, d);
     float drho, U1, U2;
-    fields_from(p, d, src.Fv(0, i, j), src.Fv(1, i, j), p.ax1.ih[i], p.ax2.ih[j], drho, U1, U2);   // F - F_rest of the previous step
+    // F - F_rest of the previous step (the body force, or zero before the first step, without a stored force)
+    const float F1p = p.constF ? (p.nopull ? 0.f : p.fext1) : src.Fv(0, i, j);
+    const float F2p = p.constF ? (p.nopull ? 0.f : p.fext2) : src.Fv(1, i, j);
+    fields_from(p, d, F1p, F2p, p.ax1.ih[i], p.ax2.ih[j], drho, U1, U2);
     const long long N = (long long)p.nx * p.ny, n = (long long)j * p.nx + i;
     out[n] = (double)p.rho0 + (double)drho;
     out[N + n] = U1;

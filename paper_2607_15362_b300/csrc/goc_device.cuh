@@ -72,6 +72,7 @@ struct StepParams {
     // read from *seed_rd and seed_rd + 1 written to *seed_wr (the counter the
     // launch of the other buffer parity reads)
     int sr;
+    int constF;                // 1: no stored force; the force of every step is the body force
     const unsigned *seed_rd;
     unsigned *seed_wr;
     // TMA descriptors of the input buffers (3D: [planes][ny][nx])

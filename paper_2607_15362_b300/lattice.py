@@ -67,15 +67,17 @@ def metric_info(spec: dict):
 
 
 ROUNDING = {"stochastic": 0, "nearest": 1}
+SCHEMES = {"goc": 0, "standard": 1}
 
 
-def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic") -> GocExec:
+def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", scheme: str = "goc") -> GocExec:
     e = GocExec()
     e.storage = _abi.STORAGE[storage]
     e.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
     e.device = -1
     e.check_every = int(check_every)
     e.rounding = ROUNDING[rounding]
+    e.scheme = SCHEMES[scheme]
     return e
 
 
@@ -83,7 +85,9 @@ class Lattice:
     """One lattice owned by libgoc."""
 
     def __init__(self, spec: dict, storage: str = "fp32", stream=None, check_every: int = 100,
-                 rounding: str = "stochastic", _handle=None, _owner=None):
+                 rounding: str = "stochastic", scheme: str = "goc", _handle=None, _owner=None):
+        """scheme "standard": the uniform-grid central-moment LBM comparator
+        (uniform maps, spec["gi"] = 0, no MIE)."""
         self.spec = spec
         self.nx, self.ny = int(spec["nx"]), int(spec["ny"])
         self.storage = storage
@@ -92,7 +96,7 @@ class Lattice:
             self._h = _handle
         else:
             g, m, f, h = structs_from_spec(spec)
-            e = _exec(storage, stream, check_every, rounding)
+            e = _exec(storage, stream, check_every, rounding, scheme)
             out = ctypes.c_void_p()
             check(lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f),
                                    ctypes.byref(h), ctypes.byref(e), ctypes.byref(out)))

@@ -64,3 +64,25 @@ def test_errors_are_reported_without_a_device_call():
     assert b"3 nodes" in lib.goc_last_error()
     assert lib.goc_step(None, 1) == _abi.GOC_EINVAL
     lib.goc_destroy(None)
+
+
+def test_standard_scheme_rejects_stretched_maps_without_a_gpu():
+    """goc_create validates scheme 1 before touching the device."""
+    import goc_inputs as gi
+    from paper_2607_15362_b300.lattice import structs_from_spec, _exec
+
+    prob = gi.Problem("cavity", 16, 16, {"kind": "tanh2", "beta": 1.5}, {"kind": "uniform"}, {"Re": 10.0, "u_lid": 0.05})
+    spec = prob.lattice_spec(0.01)
+    spec["gi"] = 0
+    g, m, f, h = structs_from_spec(spec)
+    e = _exec("fp32", None, 100, "stochastic", "standard")
+    out = ctypes.c_void_p()
+    st = _abi.lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f), ctypes.byref(h),
+                               ctypes.byref(e), ctypes.byref(out))
+    assert st == _abi.GOC_EINVAL and not out.value
+    assert b"uniform maps" in _abi.lib().goc_last_error()
+    spec2 = gi.Problem("cavity", 16, 16, {"kind": "uniform"}, {"kind": "uniform"}, {"Re": 10.0, "u_lid": 0.05}).lattice_spec(1 / 3)
+    g, m, f, h = structs_from_spec(spec2)          # gi defaults to 1
+    st = _abi.lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f), ctypes.byref(h),
+                               ctypes.byref(e), ctypes.byref(out))
+    assert st == _abi.GOC_EINVAL and b"gi_correction" in _abi.lib().goc_last_error()
