@@ -16,10 +16,34 @@
 #include "goc_device.cuh"
 #include "goc_std.cuh"
 #include "goc_step.cuh"
+#include "goc_strip.cuh"
 
 using namespace goc;
 
 namespace {
+
+// Kernel launch with programmatic stream serialisation (the kernel may start
+// while its predecessor drains; it waits in griddepcontrol.wait before
+// touching data).  GOC_DISABLE_PDL=1 launches plainly.
+bool pdl_enabled() {
+    static const int on = std::getenv("GOC_DISABLE_PDL") ? 0 : 1;
+    return on != 0;
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 
 thread_local std::string g_err;
 
@@ -86,6 +110,7 @@ struct goc_lattice {
     bool tma_ok = false;
     int rounding = 0;                            // goc_exec.rounding
     int scheme = 0;                              // goc_exec.scheme
+    int strip_h = 0;                             // > 0: step by warp strips of this many rows, else by tiles
 };
 
 namespace {
@@ -162,22 +187,33 @@ int step_grid(int ntiles, size_t *smem) {
 template <class S>
 goc_status launch_std_t(goc_lattice *L, const StepParams &p) {
     dim3 grid((L->nx + STD_BX - 1) / STD_BX, (L->ny + STD_BY - 1) / STD_BY), block(STD_BX, STD_BY);
-    std_step_kernel<S><<<grid, block, 0, L->stream>>>(p);
-    CU(cudaGetLastError());
+    CU(launch_pdl(std_step_kernel<S>, grid, block, 0, L->stream, p));
+    return GOC_OK;
+}
+
+template <class S>
+goc_status launch_strip_t(goc_lattice *L, const StepParams &p0) {
+    StepParams p = p0;
+    p.strip_h = L->strip_h;
+    const long long warps = (long long)strips_x(L->nx) * ((L->ny + L->strip_h - 1) / L->strip_h);
+    const unsigned blocks = (unsigned)((warps * 32 + STRIP_NT - 1) / STRIP_NT);
+    if (L->mhd.enabled) CU(launch_pdl(strip_kernel<S, true>, dim3(blocks), dim3(STRIP_NT), 0, L->stream, p));
+    else CU(launch_pdl(strip_kernel<S, false>, dim3(blocks), dim3(STRIP_NT), 0, L->stream, p));
     return GOC_OK;
 }
 
 template <class S>
 goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     if (L->scheme == 1) return launch_std_t<S>(L, p);
+    if (L->strip_h > 0) return launch_strip_t<S>(L, p);
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
     if (L->mhd.enabled) {
         const int grid = step_grid<S, true>(ntiles, &smem);
-        step_kernel<S, true><<<grid, dim3(TX, TYT), smem, L->stream>>>(p);
+        CU(launch_pdl(step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     } else {
         const int grid = step_grid<S, false>(ntiles, &smem);
-        step_kernel<S, false><<<grid, dim3(TX, TYT), smem, L->stream>>>(p);
+        CU(launch_pdl(step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     }
     CU(cudaGetLastError());
     return GOC_OK;
@@ -487,6 +523,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         L->check_every = exec->check_every > 0 ? exec->check_every : 100;
         L->rounding = exec->rounding;
         L->scheme = exec->scheme;
+        if (const char *e = std::getenv("GOC_STRIP_ROWS")) L->strip_h = std::max(0, std::atoi(e));
         if (exec->device >= 0) {
             cudaError_t e = cudaSetDevice(exec->device);
             if (e != cudaSuccess) {
@@ -999,14 +1036,18 @@ goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first =
         const int which = first ? 2 : (snapshot >= 0 ? 3 + 2 * par + snapshot : par);
         const StepParams *p = g.d_params + which * g.n;
         const size_t smem = 2 * (size_t)g.stage_bytes;
+        const dim3 gd(g.grid), bd(TX, TYT);
+        const int *off = g.d_off;
+        cudaError_t e;
         switch (2 * g.storage + g.mhd) {
-            case 2: batch_step_kernel<__half, false><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
-            case 3: batch_step_kernel<__half, true><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
-            case 4: batch_step_kernel<__nv_bfloat16, false><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
-            case 5: batch_step_kernel<__nv_bfloat16, true><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
-            case 1: batch_step_kernel<float, true><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
-            default: batch_step_kernel<float, false><<<g.grid, dim3(TX, TYT), smem, st>>>(p, g.d_off, g.n); break;
+            case 2: e = launch_pdl(batch_step_kernel<__half, false>, gd, bd, smem, st, p, off, g.n); break;
+            case 3: e = launch_pdl(batch_step_kernel<__half, true>, gd, bd, smem, st, p, off, g.n); break;
+            case 4: e = launch_pdl(batch_step_kernel<__nv_bfloat16, false>, gd, bd, smem, st, p, off, g.n); break;
+            case 5: e = launch_pdl(batch_step_kernel<__nv_bfloat16, true>, gd, bd, smem, st, p, off, g.n); break;
+            case 1: e = launch_pdl(batch_step_kernel<float, true>, gd, bd, smem, st, p, off, g.n); break;
+            default: e = launch_pdl(batch_step_kernel<float, false>, gd, bd, smem, st, p, off, g.n); break;
         }
+        CU(e);
         CU(cudaGetLastError());
     }
     return GOC_OK;

@@ -73,6 +73,7 @@ struct StepParams {
     // launch of the other buffer parity reads)
     int sr;
     int constF;                // 1: no stored force; the force of every step is the body force
+    int strip_h;               // rows per warp strip (strip kernel)
     const unsigned *seed_rd;
     unsigned *seed_wr;
     // TMA descriptors of the input buffers (3D: [planes][ny][nx])
@@ -142,6 +143,16 @@ __device__ __forceinline__ void put(S *p, float v, bool sr, uint32_t &r) {
     if (Store<S>::scaled && sr) Store<S>::st_sr(p, v, r);
     else Store<S>::st(p, v);
 }
+
+// Programmatic dependent launch: a step kernel launched with programmatic
+// stream serialisation may start while the previous step drains; it lets its
+// own successor be scheduled (launch_dependents) and waits for the previous
+// grid's completion and memory (wait) before touching any population.  Both
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ int wrapi(int k, int n) {
     k %= n;

@@ -177,6 +177,8 @@ template <class S>
 __global__ void __launch_bounds__(STD_BX *STD_BY) std_step_kernel(const __grid_constant__ StepParams p) {
     const int i0 = blockIdx.x * STD_BX, j0 = blockIdx.y * STD_BY;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    griddep_launch_dependents();
+    griddep_wait();
     if (Store<S>::scaled && p.sr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
         *p.seed_wr = *p.seed_rd + 1u;
     if (i >= p.nx || j >= p.ny) return;

@@ -281,41 +281,24 @@ struct FieldSmem {
 
 // Phase 2 for the R = Lanes<V>::R nodes (i, j[r]) of one thread, r = 0..R-1
 // (one node with V = float, two with V = float2: every arithmetic step below
-// runs once for both).  ty[r] is the node's row within the tile, own[r] whether
-// it is a lattice node this thread updates.
+// runs once for both): the MIE, stresses, forces and the central-moment
+// collision from the pulled deviations dn, the stored force of the previous
+// step, the fields and their normal derivatives fl[k][r] (k: drho, U1, U2,
+// dU1/dxi1, drho/dxi1, dU2/dxi2, drho/dxi2), and the stores.  own[r]: whether
+// node r is a lattice node this thread updates.
 template <class S, bool MHD, bool CHECKS, class V, class Src>
-__device__ __forceinline__ void node_update(const StepParams &p, const Src &src, int i, int tx,
-                                            const int (&j)[Lanes<V>::R], const int (&ty)[Lanes<V>::R],
-                                            const bool (&own)[Lanes<V>::R], const FieldSmem &sm,
-                                            const float (&dn)[Lanes<V>::R][9], const float (&F1pn)[Lanes<V>::R],
-                                            const float (&F2pn)[Lanes<V>::R], float h1, float ih1,
-                                            const float (&h2n)[Lanes<V>::R], const float (&ih2n)[Lanes<V>::R]) {
+__device__ __forceinline__ void collide(const StepParams &p, const Src &src, int i, const int (&j)[Lanes<V>::R],
+                                        const bool (&own)[Lanes<V>::R], const float (&dn)[Lanes<V>::R][9],
+                                        const float (&F1pn)[Lanes<V>::R], const float (&F2pn)[Lanes<V>::R], float h1,
+                                        float ih1, const float (&h2n)[Lanes<V>::R], const float (&ih2n)[Lanes<V>::R],
+                                        const float (&fl)[7][Lanes<V>::R]) {
     constexpr int R = Lanes<V>::R;
-    const int ex = tx + MH;
-    float t_[8][R];   // per lane: drho, U1, U2, dU1, dr1, dU2, dr2, theta22
+    float th_[R];
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int ey = ty[r] + MH;
-        const float drho = sm.rho[ey][ex], U1 = sm.u1[ey][ex], U2 = sm.u2[ey][ex];
-        t_[0][r] = drho;
-        t_[1][r] = U1;
-        t_[2][r] = U2;
-        if (CHECKS) {
-            t_[3][r] = dfd(sm.u1[ey][ex - 2], sm.u1[ey][ex - 1], U1, sm.u1[ey][ex + 1], sm.u1[ey][ex + 2], i, p.nx, p.per_x);
-            t_[4][r] = dfd(sm.rho[ey][ex - 2], sm.rho[ey][ex - 1], drho, sm.rho[ey][ex + 1], sm.rho[ey][ex + 2], i, p.nx, p.per_x);
-            t_[5][r] = dfd(sm.u2[ey - 2][ex], sm.u2[ey - 1][ex], U2, sm.u2[ey + 1][ex], sm.u2[ey + 2][ex], j[r], p.ny, p.per_y);
-            t_[6][r] = dfd(sm.rho[ey - 2][ex], sm.rho[ey - 1][ex], drho, sm.rho[ey + 1][ex], sm.rho[ey + 2][ex], j[r], p.ny, p.per_y);
-        } else {
-            t_[3][r] = 0.5f * (sm.u1[ey][ex + 1] - sm.u1[ey][ex - 1]);
-            t_[4][r] = 0.5f * (sm.rho[ey][ex + 1] - sm.rho[ey][ex - 1]);
-            t_[5][r] = 0.5f * (sm.u2[ey + 1][ex] - sm.u2[ey - 1][ex]);
-            t_[6][r] = 0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex]);
-        }
-        t_[7][r] = p.ax2.th[own[r] ? j[r] : j[0]];
-    }
-    const V drho = pack<V>(t_[0]), U1 = pack<V>(t_[1]), U2 = pack<V>(t_[2]);
-    const V dU1 = pack<V>(t_[3]), dr1 = pack<V>(t_[4]), dU2 = pack<V>(t_[5]), dr2 = pack<V>(t_[6]);
-    const V t22 = pack<V>(t_[7]);
+    for (int r = 0; r < R; r++) th_[r] = p.ax2.th[own[r] ? j[r] : j[0]];
+    const V drho = pack<V>(fl[0]), U1 = pack<V>(fl[1]), U2 = pack<V>(fl[2]);
+    const V dU1 = pack<V>(fl[3]), dr1 = pack<V>(fl[4]), dU2 = pack<V>(fl[5]), dr2 = pack<V>(fl[6]);
+    const V t22 = pack<V>(th_);
     const V h2 = pack<V>(h2n), ih2 = pack<V>(ih2n), F1p = pack<V>(F1pn), F2p = pack<V>(F2pn);
     const float t11 = p.ax1.th[i];
     V d[9];
@@ -594,6 +577,41 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
     }
 }
 
+// Normal derivatives of the fields from the tile's field arrays (second
+// order: central, one-sided at the first and last node of a wall axis), then
+// the collision.
+template <class S, bool MHD, bool CHECKS, class V, class Src>
+__device__ __forceinline__ void node_update(const StepParams &p, const Src &src, int i, int tx,
+                                            const int (&j)[Lanes<V>::R], const int (&ty)[Lanes<V>::R],
+                                            const bool (&own)[Lanes<V>::R], const FieldSmem &sm,
+                                            const float (&dn)[Lanes<V>::R][9], const float (&F1pn)[Lanes<V>::R],
+                                            const float (&F2pn)[Lanes<V>::R], float h1, float ih1,
+                                            const float (&h2n)[Lanes<V>::R], const float (&ih2n)[Lanes<V>::R]) {
+    constexpr int R = Lanes<V>::R;
+    const int ex = tx + MH;
+    float fl[7][R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int ey = ty[r] + MH;
+        const float drho = sm.rho[ey][ex], U1 = sm.u1[ey][ex], U2 = sm.u2[ey][ex];
+        fl[0][r] = drho;
+        fl[1][r] = U1;
+        fl[2][r] = U2;
+        if (CHECKS) {
+            fl[3][r] = dfd(sm.u1[ey][ex - 2], sm.u1[ey][ex - 1], U1, sm.u1[ey][ex + 1], sm.u1[ey][ex + 2], i, p.nx, p.per_x);
+            fl[4][r] = dfd(sm.rho[ey][ex - 2], sm.rho[ey][ex - 1], drho, sm.rho[ey][ex + 1], sm.rho[ey][ex + 2], i, p.nx, p.per_x);
+            fl[5][r] = dfd(sm.u2[ey - 2][ex], sm.u2[ey - 1][ex], U2, sm.u2[ey + 1][ex], sm.u2[ey + 2][ex], j[r], p.ny, p.per_y);
+            fl[6][r] = dfd(sm.rho[ey - 2][ex], sm.rho[ey - 1][ex], drho, sm.rho[ey + 1][ex], sm.rho[ey + 2][ex], j[r], p.ny, p.per_y);
+        } else {
+            fl[3][r] = 0.5f * (sm.u1[ey][ex + 1] - sm.u1[ey][ex - 1]);
+            fl[4][r] = 0.5f * (sm.rho[ey][ex + 1] - sm.rho[ey][ex - 1]);
+            fl[5][r] = 0.5f * (sm.u2[ey + 1][ex] - sm.u2[ey - 1][ex]);
+            fl[6][r] = 0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex]);
+        }
+    }
+    collide<S, MHD, CHECKS, V>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl);
+}
+
 // One tile of one lattice from a given source; KIND 0: interior (no boundary
 // logic, fields halo 1), 1: near a boundary (fields halo 2 where inside).
 // Each thread pulls its RPT nodes (column i0 + tx, rows ty + r TYT) into
@@ -755,8 +773,10 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_c
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
-        if (Store<S>::scaled && p.sr && blockIdx.x == 0) *p.seed_wr = *p.seed_rd + 1u;   // next step's index
     }
+    griddep_launch_dependents();
+    griddep_wait();   // the previous step is complete: its populations may be read and overwritten
+    if (leader && Store<S>::scaled && p.sr && blockIdx.x == 0) *p.seed_wr = *p.seed_rd + 1u;   // next step's index
     __syncthreads();
     int t = blockIdx.x;
     if (leader && t < ntiles) {
@@ -818,19 +838,32 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const St
     const int t_begin = blockIdx.x * per, t_end = min(total, t_begin + per);
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     const int tid = threadIdx.y * TX + threadIdx.x;
+    // the leader walks the lattices of its contiguous item range in order:
+    // lattice lk holds items [lbeg, lend), ntx tiles per row
+    int lk = 0, lbeg = 0, lend = 0, ntx = 1;
     if (leader) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
         s_k = -1;
+        if (t_begin < t_end) {
+            lk = find_lattice(tile_off, nlat, t_begin);
+            lbeg = tile_off[lk];
+            lend = tile_off[lk + 1];
+            ntx = (params[lk].nx + TX - 1) / TX;
+        }
     }
     auto prefetch = [&](int t, int st) {
-        const int k = find_lattice(tile_off, nlat, t);
-        const StepParams &q = params[k];
-        const int local = t - tile_off[k];
-        const int ntx = (q.nx + TX - 1) / TX;
+        while (t >= lend) {
+            lk++;
+            lbeg = lend;
+            lend = tile_off[lk + 1];
+            ntx = (params[lk].nx + TX - 1) / TX;
+        }
+        const StepParams &q = params[lk];
+        const int local = t - lbeg;
         const int i0 = (local % ntx) * TX, j0 = (local / ntx) * TY;
-        s_item[st][0] = k;
+        s_item[st][0] = lk;
         s_item[st][1] = i0;
         s_item[st][2] = j0;
         if (tile_kind<S>(q, i0, j0) != 2) {
@@ -838,6 +871,8 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const St
             issue_tile<S>(q, i0, j0, dyn + st * STAGE, &bars[st], MHD);
         }
     };
+    griddep_launch_dependents();
+    griddep_wait();   // the previous step of every member is complete
     if (leader && t_begin < t_end) prefetch(t_begin, 0);
     __syncthreads();
     uint32_t ph0 = 0, ph1 = 0;
