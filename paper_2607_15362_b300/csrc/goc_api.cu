@@ -920,16 +920,19 @@ struct goc_batch {
     std::vector<goc_lattice *> slots;
     std::vector<long long> bytes;
     bool dirty = true;
-    // per storage group: params[2][n], tile offsets[n+1]
+    // Members are grouped by storage type and MIE on/off (one kernel each), and
+    // each group is cut into sets whose state fits in L2 together; within a
+    // graph chunk each set runs all its steps before the next set starts, so a
+    // set's populations stay L2-resident for the whole chunk.
     struct Group {
-        int storage = 0, n = 0, total = 0, grid = 0;
-        StepParams *d_params = nullptr;   // [7][n]: parity 0, parity 1, first step after a rebuild,
-                                          // then parity p with snapshot u: 3 + 2 p + u
-        int *d_off = nullptr;
-        int stage_bytes = 0;
-        int mhd = 0;
-        std::vector<int> members;
-    } groups[6];                  // index 2 * storage + (MIE on)
+        int storage = 0, mhd = 0, n = 0, total = 0, grid = 0, stage_bytes = 0;
+        std::vector<int> members;      // at most kBatchMax slots
+        std::vector<BatchArgs> args;   // launch arguments: parity 0, parity 1, first step after a rebuild,
+                                       // then parity p with snapshot u: 3 + 2 p + u
+        CUtensorMap *maps = nullptr;   // device [2 parities][n][3]
+        int *ctr = nullptr;            // device [2]: work-item counters by step parity
+    };
+    std::vector<Group> groups;
     long long phase = 0;
     bool first_pending = false;   // next launch uses the first-step parameters (fresh members read in place)
     cudaGraphExec_t graph = nullptr;
@@ -953,15 +956,24 @@ long long estimate_bytes(const goc_grid *grid, const goc_mhd *mhd, int storage) 
 
 void free_groups(goc_batch *B) {
     for (auto &g : B->groups) {
-        if (g.d_params) cudaFree(g.d_params);
-        if (g.d_off) cudaFree(g.d_off);
-        g.d_params = nullptr;
-        g.d_off = nullptr;
-        g.n = g.total = 0;
-        g.members.clear();
+        if (g.maps) cudaFree(g.maps);
+        if (g.ctr) cudaFree(g.ctr);
     }
+    B->groups.clear();
     if (B->graph) cudaGraphExecDestroy(B->graph);
     B->graph = nullptr;
+}
+
+// bytes of lattice state per set: one set per kernel type, or with
+// GOC_BATCH_L2_SETS=1 sets of three quarters of the L2 size (measured slower on
+// the 64-lattice batch: the step is instruction-bound, and smaller launches
+// add tails)
+long long l2_set_bytes(int device) {
+    const char *e = std::getenv("GOC_BATCH_L2_SETS");
+    if (!e || std::atoi(e) == 0) return (1LL << 62);
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+    return l2 > 0 ? 3LL * l2 / 4 : (1LL << 62);
 }
 
 template <class S, bool MHD>
@@ -983,43 +995,81 @@ int persistent_grid(int total, int *stage_bytes) {
 
 goc_status rebuild(goc_batch *B) {
     free_groups(B);
-    for (int s = 0; s < 6; s++) {
-        B->groups[s].storage = s / 2;
-        B->groups[s].mhd = s % 2;
+    const long long cap = l2_set_bytes(B->device);
+    for (int key = 0; key < 6; key++) {   // kernel type 2 * storage + (MIE on); launches of <= kBatchMax lattices
+        long long used = 0;
+        for (int k = 0; k < (int)B->slots.size(); k++) {
+            goc_lattice *L = B->slots[k];
+            if (!L || 2 * L->storage + (L->mhd.enabled ? 1 : 0) != key) continue;
+            if (B->groups.empty() || 2 * B->groups.back().storage + B->groups.back().mhd != key ||
+                (int)B->groups.back().members.size() == kBatchMax ||
+                (used + B->bytes[k] > cap && !B->groups.back().members.empty())) {
+                goc_batch::Group g;
+                g.storage = key / 2;
+                g.mhd = key % 2;
+                B->groups.push_back(std::move(g));
+                used = 0;
+            }
+            B->groups.back().members.push_back(k);
+            used += B->bytes[k];
+        }
     }
-    for (int k = 0; k < (int)B->slots.size(); k++)
-        if (B->slots[k]) B->groups[2 * B->slots[k]->storage + (B->slots[k]->mhd.enabled ? 1 : 0)].members.push_back(k);
     for (auto &g : B->groups) {
         g.n = (int)g.members.size();
-        if (!g.n) continue;
-        std::vector<StepParams> hp(7 * g.n);
-        std::vector<int> off(g.n + 1, 0);
+        std::vector<int> tiles(g.n);
+        g.total = 0;
+        for (int m = 0; m < g.n; m++) {
+            const goc_lattice *L = B->slots[g.members[m]];
+            tiles[m] = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
+            g.total += tiles[m];
+        }
+        int capacity = 0;   // resident blocks of this kernel on the device
+        switch (2 * g.storage + g.mhd) {
+            case 2: capacity = persistent_grid<__half, false>(1 << 30, &g.stage_bytes); break;
+            case 3: capacity = persistent_grid<__half, true>(1 << 30, &g.stage_bytes); break;
+            case 4: capacity = persistent_grid<__nv_bfloat16, false>(1 << 30, &g.stage_bytes); break;
+            case 5: capacity = persistent_grid<__nv_bfloat16, true>(1 << 30, &g.stage_bytes); break;
+            case 1: capacity = persistent_grid<float, true>(1 << 30, &g.stage_bytes); break;
+            default: capacity = persistent_grid<float, false>(1 << 30, &g.stage_bytes); break;
+        }
+        g.grid = std::min(g.total, capacity);   // persistent blocks taking tiles from the counter
+        g.args.assign(7, BatchArgs{});
+        CU(cudaMalloc(&g.ctr, 2 * sizeof(int)));
+        CU(cudaMemsetAsync(g.ctr, 0, 2 * sizeof(int), B->stream));
+        for (int v = 0; v < 7; v++) {
+            auto &a = g.args[v];
+            a.n = g.n;
+            a.toff[0] = 0;
+            for (int m = 0; m < g.n; m++) a.toff[m + 1] = a.toff[m] + tiles[m];
+            a.parity = v == 1 ? 1 : (v >= 3 ? (v - 3) / 2 : 0);
+            a.ctr = g.ctr;
+        }
+        std::vector<CUtensorMap> hm(2 * 3 * g.n);
+        for (int m = 0; m < g.n; m++) {
+            const goc_lattice *L = B->slots[g.members[m]];
+            for (int par = 0; par < 2; par++) {
+                const int src = L->cur ^ par;
+                hm[(par * g.n + m) * 3 + 0] = L->tmf[src];
+                hm[(par * g.n + m) * 3 + 1] = L->tmF[src];
+                hm[(par * g.n + m) * 3 + 2] = L->mhd.enabled ? L->tmg[src] : L->tmf[src];
+            }
+        }
+        CU(cudaMalloc(&g.maps, hm.size() * sizeof(CUtensorMap)));
+        CU(cudaMemcpyAsync(g.maps, hm.data(), hm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, B->stream));
+        for (int v = 0; v < 7; v++) {   // variant v reads the buffers of parity 0 (v = 0, 2), 1 (v = 1), or 3 + 2 p + u
+            const int par = v == 1 ? 1 : (v >= 3 ? (v - 3) / 2 : 0);
+            g.args[v].maps = g.maps + par * 3 * g.n;
+        }
         for (int m = 0; m < g.n; m++) {
             const int slot = g.members[m];
             goc_lattice *L = B->slots[slot];
-            hp[m] = params_for(L, L->cur, nullptr);
-            hp[g.n + m] = params_for(L, L->cur ^ 1, nullptr);
-            hp[2 * g.n + m] = hp[m];
-            hp[2 * g.n + m].nopull = L->fresh ? 1 : 0;
+            g.args[0].p[m] = params_for(L, L->cur, nullptr);
+            g.args[1].p[m] = params_for(L, L->cur ^ 1, nullptr);
+            g.args[2].p[m] = g.args[0].p[m];
+            g.args[2].p[m].nopull = L->fresh ? 1 : 0;
             for (int par = 0; par < 2; par++)
                 for (int u = 0; u < 2; u++)
-                    hp[(3 + 2 * par + u) * g.n + m] =
-                        params_for(L, L->cur ^ par, B->check[slot] ? L->uout[u] : nullptr);
-            off[m + 1] = off[m] + ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
-        }
-        g.total = off[g.n];
-        CU(cudaMalloc(&g.d_params, hp.size() * sizeof(StepParams)));
-        CU(cudaMalloc(&g.d_off, off.size() * sizeof(int)));
-        CU(cudaMemcpyAsync(g.d_params, hp.data(), hp.size() * sizeof(StepParams), cudaMemcpyHostToDevice, B->stream));
-        CU(cudaMemcpyAsync(g.d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream));
-        const int key = 2 * g.storage + g.mhd;
-        switch (key) {
-            case 2: g.grid = persistent_grid<__half, false>(g.total, &g.stage_bytes); break;
-            case 3: g.grid = persistent_grid<__half, true>(g.total, &g.stage_bytes); break;
-            case 4: g.grid = persistent_grid<__nv_bfloat16, false>(g.total, &g.stage_bytes); break;
-            case 5: g.grid = persistent_grid<__nv_bfloat16, true>(g.total, &g.stage_bytes); break;
-            case 1: g.grid = persistent_grid<float, true>(g.total, &g.stage_bytes); break;
-            default: g.grid = persistent_grid<float, false>(g.total, &g.stage_bytes); break;
+                    g.args[3 + 2 * par + u].p[m] = params_for(L, L->cur ^ par, B->check[slot] ? L->uout[u] : nullptr);
         }
     }
     CU(cudaStreamSynchronize(B->stream));
@@ -1029,23 +1079,25 @@ goc_status rebuild(goc_batch *B) {
     return GOC_OK;
 }
 
-goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first = false, int snapshot = -1) {
-    for (auto &g : B->groups) {
+goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first = false, int snapshot = -1,
+                        int only = -1) {
+    for (int gi = 0; gi < (int)B->groups.size(); gi++) {
+        if (only >= 0 && gi != only) continue;
+        auto &g = B->groups[gi];
         if (!g.n) continue;
         const int par = (int)((B->phase + s) & 1);
         const int which = first ? 2 : (snapshot >= 0 ? 3 + 2 * par + snapshot : par);
-        const StepParams *p = g.d_params + which * g.n;
+        const BatchArgs &a = g.args[which];
         const size_t smem = 2 * (size_t)g.stage_bytes;
         const dim3 gd(g.grid), bd(TX, TYT);
-        const int *off = g.d_off;
         cudaError_t e;
         switch (2 * g.storage + g.mhd) {
-            case 2: e = launch_pdl(batch_step_kernel<__half, false>, gd, bd, smem, st, p, off, g.n); break;
-            case 3: e = launch_pdl(batch_step_kernel<__half, true>, gd, bd, smem, st, p, off, g.n); break;
-            case 4: e = launch_pdl(batch_step_kernel<__nv_bfloat16, false>, gd, bd, smem, st, p, off, g.n); break;
-            case 5: e = launch_pdl(batch_step_kernel<__nv_bfloat16, true>, gd, bd, smem, st, p, off, g.n); break;
-            case 1: e = launch_pdl(batch_step_kernel<float, true>, gd, bd, smem, st, p, off, g.n); break;
-            default: e = launch_pdl(batch_step_kernel<float, false>, gd, bd, smem, st, p, off, g.n); break;
+            case 2: e = launch_pdl(batch_step_kernel<__half, false>, gd, bd, smem, st, a); break;
+            case 3: e = launch_pdl(batch_step_kernel<__half, true>, gd, bd, smem, st, a); break;
+            case 4: e = launch_pdl(batch_step_kernel<__nv_bfloat16, false>, gd, bd, smem, st, a); break;
+            case 5: e = launch_pdl(batch_step_kernel<__nv_bfloat16, true>, gd, bd, smem, st, a); break;
+            case 1: e = launch_pdl(batch_step_kernel<float, true>, gd, bd, smem, st, a); break;
+            default: e = launch_pdl(batch_step_kernel<float, false>, gd, bd, smem, st, a); break;
         }
         CU(e);
         CU(cudaGetLastError());
@@ -1179,7 +1231,9 @@ goc_status goc_batch_step(goc_batch *B, long long nsteps) {
             cudaGraph_t gr;
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             goc_status st = GOC_OK;
-            for (int k = 0; k < kBatchGraphSteps && st == GOC_OK && e == cudaSuccess; k++) st = batch_launch(B, cs, k);
+            // set-major order: each L2-sized set advances all steps of the chunk in turn
+            for (int gi = 0; gi < (int)B->groups.size() && st == GOC_OK && e == cudaSuccess; gi++)
+                for (int k = 0; k < kBatchGraphSteps && st == GOC_OK; k++) st = batch_launch(B, cs, k, false, -1, gi);
             if (e == cudaSuccess) e = cudaStreamEndCapture(cs, &gr);
             cudaStreamDestroy(cs);
             if (st != GOC_OK) return st;

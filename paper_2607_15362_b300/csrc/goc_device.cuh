@@ -83,14 +83,16 @@ struct StepParams {
     CUtensorMap tm_g;          // box [10][TY + 2][TX + 2 HXS]
 };
 
-// ---- storage formats (ld: global read-only path, lds: shared memory) -------
+// ---- storage formats (ld: global read-only path, lds: shared memory, st:
+// global store -- st.global, so the compiler knows a store cannot alias shared
+// memory) ---------------------------------------------------------------------
 template <class S> struct Store;
 template <> struct Store<float> {
     static constexpr bool scaled = false;   // FP32 is stored unscaled
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ float lds(const float *p) { return *p; }
-    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
-    static __device__ __forceinline__ void st_sr(float *p, float v, uint32_t &) { *p = v; }
+    static __device__ __forceinline__ void st(float *p, float v) { __stcg(p, v); }
+    static __device__ __forceinline__ void st_sr(float *p, float v, uint32_t &) { __stcg(p, v); }
 };
 // Stochastic rounding (st_sr): u, uniform in [0, 2^k) with k the number of
 // FP32 significand bits the format drops (13 for FP16, 16 for BF16), is added
@@ -107,18 +109,18 @@ template <> struct Store<__half> {
     static constexpr bool scaled = true;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }
-    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void st(__half *p, float v) { __stcg(p, __float2half_rn(v)); }
     static __device__ __forceinline__ void st_sr(__half *p, float v, uint32_t &r) {
-        *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (lcg_next(r) >> 19)));
+        __stcg(p, __float2half_rz(__uint_as_float(__float_as_uint(v) + (lcg_next(r) >> 19))));
     }
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr bool scaled = true;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { __stcg(p, __float2bfloat16_rn(v)); }
     static __device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, uint32_t &r) {
-        *p = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (lcg_next(r) >> 16)));
+        __stcg(p, __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (lcg_next(r) >> 16))));
     }
 };
 

@@ -158,10 +158,10 @@ __device__ __forceinline__ void std_node(const StepParams &p, int i, int j) {
 #pragma unroll
     for (int a = 0; a < 9; a++) put<S>(fout + a * p.plane + idx, scl<S>(o[a], p.isf), sr, rng);
     if (p.uout) {
-        p.uout[idx] = u;
-        p.uout[p.plane + idx] = v;
-        p.uout[2 * p.plane + idx] = 0.f;
-        p.uout[3 * p.plane + idx] = 0.f;
+        __stcg(p.uout + idx, u);
+        __stcg(p.uout + p.plane + idx, v);
+        __stcg(p.uout + 2 * p.plane + idx, 0.f);
+        __stcg(p.uout + 3 * p.plane + idx, 0.f);
     }
     if (p.flag) {
         const bool bad = !(rho > 0.f && fabsf(u) + fabsf(v) < 1e30f);

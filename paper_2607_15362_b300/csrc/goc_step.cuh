@@ -558,10 +558,10 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         put<S>(Fout + idx[q], scl<S>(lane(F1dev, q), p.isF), sr, rng[q]);
         put<S>(Fout + p.plane + idx[q], scl<S>(lane(F2dev, q), p.isF), sr, rng[q]);
         if (p.uout) {
-            p.uout[idx[q]] = lane(U1, q);
-            p.uout[p.plane + idx[q]] = lane(U2, q);
-            p.uout[2 * p.plane + idx[q]] = lane(B1, q);
-            p.uout[3 * p.plane + idx[q]] = lane(B2, q);
+            __stcg(p.uout + idx[q], lane(U1, q));
+            __stcg(p.uout + p.plane + idx[q], lane(U2, q));
+            __stcg(p.uout + 2 * p.plane + idx[q], lane(B1, q));
+            __stcg(p.uout + 3 * p.plane + idx[q], lane(B2, q));
         }
     }
     if (p.flag) {   // divergence flag: one atomic per warp at most
@@ -730,15 +730,24 @@ __device__ __forceinline__ int tile_kind(const StepParams &p, int i0, int j0) {
     return 1;
 }
 
+// The three tensor maps of a lattice's input buffers (populations, force, MIE).
+struct TileMaps {
+    const CUtensorMap *f, *F, *g;
+};
+
 template <class S>
-__device__ __forceinline__ void issue_tile(const StepParams &p, int i0, int j0, unsigned char *stage, uint64_t *bar,
+__device__ __forceinline__ void issue_tile(const TileMaps &m, int i0, int j0, unsigned char *stage, uint64_t *bar,
                                            bool mhd) {
     using T = Tiling<S>;
     const uint32_t bytes = T::F_BYTES + T::FF_BYTES + (mhd ? T::G_BYTES : 0);
     mbar_expect_tx(bar, bytes);
-    tma_load_3d(stage, &p.tm_f, i0 - T::HXS, j0 - HYS, 0, bar);
-    tma_load_3d(stage + T::OFF_FF, &p.tm_F, i0 - T::HXS, j0 - HYS, 0, bar);
-    if (mhd) tma_load_3d(stage + T::OFF_G, &p.tm_g, i0 - T::HXS, j0 - 1, 0, bar);
+    tma_load_3d(stage, m.f, i0 - T::HXS, j0 - HYS, 0, bar);
+    tma_load_3d(stage + T::OFF_FF, m.F, i0 - T::HXS, j0 - HYS, 0, bar);
+    if (mhd) tma_load_3d(stage + T::OFF_G, m.g, i0 - T::HXS, j0 - 1, 0, bar);
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *m) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
 template <class S, bool MHD>
@@ -758,40 +767,32 @@ __device__ __forceinline__ void run_tile(const StepParams &p, int kind, int i0, 
     }
 }
 
-// Single lattice: persistent blocks stride over the tiles; TMA staging in two
-// dynamic shared-memory stages.
+// The tiles first, first + stride, ... of one lattice, processed by one block
+// with TMA staging in two dynamic shared-memory stages: the copy of the next
+// tile is issued before the current one is computed.  Every thread of the
+// block calls it; the barriers must be initialised.
+// m: the TMA descriptors of the input buffers (a tensor map must sit in
+// parameter, constant or global memory).
 template <class S, bool MHD>
-__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
+__device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMaps &m, int first, int stride,
+                                              unsigned char *dyn, uint64_t *bars, FieldSmem &sm, bool leader) {
     using T = Tiling<S>;
-    extern __shared__ __align__(128) unsigned char dyn[];
-    __shared__ __align__(8) uint64_t bars[2];
-    __shared__ FieldSmem sm;
     constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
     const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY, ntiles = ntx * nty;
-    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-    if (leader) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_mbar_init();
-    }
-    griddep_launch_dependents();
-    griddep_wait();   // the previous step is complete: its populations may be read and overwritten
-    if (leader && Store<S>::scaled && p.sr && blockIdx.x == 0) *p.seed_wr = *p.seed_rd + 1u;   // next step's index
-    __syncthreads();
-    int t = blockIdx.x;
+    int t = first;
     if (leader && t < ntiles) {
         const int i0 = (t % ntx) * TX, j0 = (t / ntx) * TY;
-        if (tile_kind<S>(p, i0, j0) != 2) issue_tile<S>(p, i0, j0, dyn, &bars[0], MHD);
+        if (tile_kind<S>(p, i0, j0) != 2) issue_tile<S>(m, i0, j0, dyn, &bars[0], MHD);
     }
     uint32_t ph0 = 0, ph1 = 0;
     int stage = 0;
-    for (; t < ntiles; t += gridDim.x) {
-        const int tn = t + gridDim.x;
+    for (; t < ntiles; t += stride) {
+        const int tn = t + stride;
         if (leader && tn < ntiles) {
             const int i0n = (tn % ntx) * TX, j0n = (tn / ntx) * TY;
             if (tile_kind<S>(p, i0n, j0n) != 2) {
                 fence_proxy_async();   // generic reads of that stage (previous tile) precede the async writes
-                issue_tile<S>(p, i0n, j0n, dyn + (stage ^ 1) * STAGE, &bars[stage ^ 1], MHD);
+                issue_tile<S>(m, i0n, j0n, dyn + (stage ^ 1) * STAGE, &bars[stage ^ 1], MHD);
             }
         }
         const int i0 = (t % ntx) * TX, j0 = (t / ntx) * TY;
@@ -808,87 +809,103 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_c
     }
 }
 
-// Many lattices in one launch: work item t in [0, total) is a tile of the
-// lattice k with tile_off[k] <= t < tile_off[k+1]; a persistent grid strides
-// over the items.  Lattices with and without the MIE may be mixed (the stage
-// is sized for the MIE when any member has it).
-__device__ __forceinline__ int find_lattice(const int *tile_off, int nlat, int t) {
-    int lo = 0, hi = nlat - 1;   // last k with tile_off[k] <= t
+// Single lattice: persistent blocks stride over the tiles.
+template <class S, bool MHD>
+__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ FieldSmem sm;
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    if (leader) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    griddep_launch_dependents();
+    griddep_wait();   // the previous step is complete: its populations may be read and overwritten
+    if (leader && Store<S>::scaled && p.sr && blockIdx.x == 0) *p.seed_wr = *p.seed_rd + 1u;   // next step's index
+    __syncthreads();
+    const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
+    lattice_tiles<S, MHD>(p, m, blockIdx.x, gridDim.x, dyn, bars, sm, leader);
+}
+
+// Many lattices in one launch.  Their parameters travel in the kernel
+// parameter space (up to kBatchMax lattices, 28 KB); the tensor maps sit in a
+// global array.  Work items are the tiles of all member lattices (item t of
+// lattice k for toff[k] <= t < toff[k+1]), handed out dynamically: the block
+// leader takes the next item from a global counter while the current one is
+// computed (its TMA copy goes into the other stage), so tiles of unequal cost
+// (wall tiles, tiles on periodic seams read from global memory) balance out
+// over the blocks.  The counter of a step is ctr[parity]; each launch zeroes
+// the other one for the next step.
+constexpr int kBatchMax = 32;
+struct BatchArgs {
+    int n;                          // lattices in this launch
+    int toff[kBatchMax + 1];        // first item of each lattice; toff[n] = items
+    int parity;                     // this step's counter
+    int *ctr;                       // [2] item counters in global memory
+    const CUtensorMap *maps;        // [n][3] tensor maps of the input buffers, in global memory
+    StepParams p[kBatchMax];        // (their tm_* members are not used)
+};
+
+__device__ __forceinline__ int batch_lattice(const BatchArgs &a, int t) {
+    int lo = 0, hi = a.n - 1;       // last k with toff[k] <= t
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.toff[mid] <= t) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
 template <class S, bool MHD>
-__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const StepParams *__restrict__ params,
-                                                                        const int *__restrict__ tile_off, int nlat) {
+__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const __grid_constant__ BatchArgs a) {
     using T = Tiling<S>;
     constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ FieldSmem sm;
-    __shared__ int s_item[2][3];   // per stage: lattice, i0, j0 of the staged item
-    __shared__ __align__(16) unsigned char s_par[(offsetof(StepParams, tm_f) + 15) / 16 * 16];
-    __shared__ int s_k;            // lattice whose parameters are in s_par
-    const int total = tile_off[nlat];
-    // contiguous range of work items per block: neighbouring tiles of one lattice
-    const int per = (total + gridDim.x - 1) / gridDim.x;
-    const int t_begin = blockIdx.x * per, t_end = min(total, t_begin + per);
+    __shared__ int s_item[2];
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    // the leader walks the lattices of its contiguous item range in order:
-    // lattice lk holds items [lbeg, lend), ntx tiles per row
-    int lk = 0, lbeg = 0, lend = 0, ntx = 1;
+    const int items = a.toff[a.n];
     if (leader) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
-        s_k = -1;
-        if (t_begin < t_end) {
-            lk = find_lattice(tile_off, nlat, t_begin);
-            lbeg = tile_off[lk];
-            lend = tile_off[lk + 1];
-            ntx = (params[lk].nx + TX - 1) / TX;
-        }
     }
-    auto prefetch = [&](int t, int st) {
-        while (t >= lend) {
-            lk++;
-            lbeg = lend;
-            lend = tile_off[lk + 1];
-            ntx = (params[lk].nx + TX - 1) / TX;
-        }
-        const StepParams &q = params[lk];
-        const int local = t - lbeg;
-        const int i0 = (local % ntx) * TX, j0 = (local / ntx) * TY;
-        s_item[st][0] = lk;
-        s_item[st][1] = i0;
-        s_item[st][2] = j0;
-        if (tile_kind<S>(q, i0, j0) != 2) {
-            fence_proxy_async();
-            issue_tile<S>(q, i0, j0, dyn + st * STAGE, &bars[st], MHD);
-        }
-    };
     griddep_launch_dependents();
     griddep_wait();   // the previous step of every member is complete
-    if (leader && t_begin < t_end) prefetch(t_begin, 0);
+    // take item t and start its copy into stage st (leader only)
+    auto take = [&](int st) {
+        const int t = atomicAdd(&a.ctr[a.parity], 1);
+        s_item[st] = t;
+        if (t < items) {
+            const int k = batch_lattice(a, t);
+            const StepParams &q = a.p[k];
+            const int ntx = (q.nx + TX - 1) / TX, local = t - a.toff[k];
+            const int i0 = (local % ntx) * TX, j0 = (local / ntx) * TY;
+            if (tile_kind<S>(q, i0, j0) != 2) {
+                const TileMaps m{a.maps + 3 * k, a.maps + 3 * k + 1, a.maps + 3 * k + 2};
+                fence_proxy_async();   // generic reads of that stage precede the async writes
+                issue_tile<S>(m, i0, j0, dyn + st * STAGE, &bars[st], MHD);
+            }
+        }
+    };
+    if (leader) {
+        if (blockIdx.x == 0) a.ctr[a.parity ^ 1] = 0;   // the next step's counter
+        take(0);
+    }
     __syncthreads();
     uint32_t ph0 = 0, ph1 = 0;
     int stage = 0;
-    for (int t = t_begin; t < t_end; t++) {
-        if (leader && t + 1 < t_end) prefetch(t + 1, stage ^ 1);
-        const int k = s_item[stage][0], i0 = s_item[stage][1], j0 = s_item[stage][2];
-        if (k != s_k) {   // parameters (up to the TMA descriptors) of a new lattice into shared memory
-            const uint4 *src = reinterpret_cast<const uint4 *>(&params[k]);
-            uint4 *dst = reinterpret_cast<uint4 *>(s_par);
-            for (int w = tid; w < (int)(sizeof(s_par) / 16); w += NT) dst[w] = src[w];
-            __syncthreads();
-            if (leader) s_k = k;
-        }
-        const StepParams &p = *reinterpret_cast<const StepParams *>(s_par);
-        if (Store<S>::scaled && p.sr && leader && i0 == 0 && j0 == 0) *p.seed_wr = *p.seed_rd + 1u;
+    for (;;) {
+        const int t = s_item[stage];
+        if (t >= items) break;   // uniform: every thread reads the same shared value
+        if (leader) take(stage ^ 1);
+        const int k = batch_lattice(a, t);
+        const StepParams &p = a.p[k];
+        const int ntx = (p.nx + TX - 1) / TX, local = t - a.toff[k];
+        const int i0 = (local % ntx) * TX, j0 = (local / ntx) * TY;
+        if (leader && local == 0 && Store<S>::scaled && p.sr) *p.seed_wr = *p.seed_rd + 1u;
         const int kind = tile_kind<S>(p, i0, j0);
         if (kind != 2) {
             uint32_t &ph = stage ? ph1 : ph0;
@@ -897,7 +914,7 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const St
             ph ^= 1;
         }
         run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm);
-        __syncthreads();   // stage, field arrays and s_item are reused
+        __syncthreads();   // the stage, the field arrays and s_item are reused
         stage ^= 1;
     }
 }
