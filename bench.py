@@ -242,7 +242,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": src, "bytes_per_node": bpn,
-                         "kernel": "goc::step_kernel<float,false>", "launch_us": round(launch_s * 1e6, 3)},
+                         "kernel": "goc::step_kernel<float,false>", "launch_us": round(launch_s * 1e6, 3),
+                         "launch_config": lat.launch_config},
             "cpu_baseline": cpu,
             "gpu_launches": args.steps * chunk,
             "clocks": clocks,

@@ -117,6 +117,12 @@ typedef struct {
                                local collision, no stored force); scheme 1 requires uniform
                                maps on both axes, gi_correction = 0 and no MIE (else
                                GOC_EINVAL); lattices added by goc_batch_add use scheme 0 */
+    int fixed_launch;       /* 0 = the launch autotuner picks the tile order (dynamic queue or
+                               static) and programmatic dependent launch on or off, by timing
+                               each choice on 16 steps of the first goc_step call of at least
+                               72 steps (choices are cached per lattice size, storage and MIE;
+                               every choice gives bitwise the same populations);
+                               1 = fixed: dynamic tile queue, dependent launch on */
 } goc_exec;
 
 /* ---- lifecycle --------------------------------------------------------- */
@@ -142,6 +148,16 @@ goc_status goc_init_fields(goc_lattice *lat, const double *rho, const double *u1
 
 /* NULL-safe.  Synchronises the stream and frees all device memory. */
 void goc_destroy(goc_lattice *lat);
+
+/* The launch configuration in use: *dynamic_tiles = 1 for the dynamic tile
+ * queue (0: static tile order), *pdl = 1 for programmatic dependent launch,
+ * *tuned = 1 once chosen (by the autotuner or fixed).  Any output may be NULL.
+ * No counterpart in the paper: a property of this implementation. */
+goc_status goc_launch_config(const goc_lattice *lat, int *dynamic_tiles, int *pdl, int *tuned);
+
+/* Set the launch configuration (dynamic_tiles, pdl: 0 or 1) and turn the
+ * autotuner off for this lattice.  Takes effect from the next step. */
+goc_status goc_set_launch_config(goc_lattice *lat, int dynamic_tiles, int pdl);
 
 /* ---- the hot loop ------------------------------------------------------ */
 

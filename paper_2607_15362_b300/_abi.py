@@ -32,7 +32,7 @@ class GocMhd(ctypes.Structure):
 
 class GocExec(ctypes.Structure):
     _fields_ = [("storage", c_int), ("cuda_stream", c_void_p), ("device", c_int), ("check_every", c_int),
-                ("rounding", c_int), ("scheme", c_int)]
+                ("rounding", c_int), ("scheme", c_int), ("fixed_launch", c_int)]
 
 
 GOC_OK, GOC_EINVAL, GOC_ENOMEM, GOC_ECUDA, GOC_EDIVERGED, GOC_ETIMEOUT, GOC_EBUSY, GOC_EUNSUPPORTED = \
@@ -67,6 +67,8 @@ SIGNATURES = {
     "goc_batch_residual": (c_int, [c_void_p, c_int, P(c_double), P(c_double)]),
     "goc_batch_usage": (c_int, [c_void_p, P(c_ll), P(c_ll), P(c_int)]),
     "goc_mass_noalloc": (c_int, [c_void_p, P(c_double)]),
+    "goc_launch_config": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
+    "goc_set_launch_config": (c_int, [c_void_p, c_int, c_int]),
     "goc_last_error": (ctypes.c_char_p, []),
 }
 

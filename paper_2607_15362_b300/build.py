@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgoc.so")
 SOURCES = ["goc_api.cu"]
-DEPS = ["goc_api.cu", "goc_step.cuh", "goc_aux.cuh", "goc_device.cuh", "goc_vec.cuh", "goc_std.cuh", "goc_strip.cuh"]
+DEPS = ["goc_api.cu", "goc_step.cuh", "goc_aux.cuh", "goc_device.cuh", "goc_vec.cuh", "goc_std.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 

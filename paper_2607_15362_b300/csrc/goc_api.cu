@@ -7,6 +7,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <array>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -16,7 +19,6 @@
 #include "goc_device.cuh"
 #include "goc_std.cuh"
 #include "goc_step.cuh"
-#include "goc_strip.cuh"
 
 using namespace goc;
 
@@ -30,7 +32,8 @@ bool pdl_enabled() {
     return on != 0;
 }
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -38,7 +41,7 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    attr[0].val.programmaticStreamSerializationAllowed = (pdl && pdl_enabled()) ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, args...);
@@ -110,7 +113,10 @@ struct goc_lattice {
     bool tma_ok = false;
     int rounding = 0;                            // goc_exec.rounding
     int scheme = 0;                              // goc_exec.scheme
-    int strip_h = 0;                             // > 0: step by warp strips of this many rows, else by tiles
+    // launch configuration (results are bitwise the same under every choice):
+    // tile queue (dynamic) or static tile order, programmatic dependent launch
+    int cfg_dynamic = 1, cfg_pdl = 1;
+    bool tuned = false;                          // chosen by the launch autotuner (or fixed)
 };
 
 namespace {
@@ -187,33 +193,21 @@ int step_grid(int ntiles, size_t *smem) {
 template <class S>
 goc_status launch_std_t(goc_lattice *L, const StepParams &p) {
     dim3 grid((L->nx + STD_BX - 1) / STD_BX, (L->ny + STD_BY - 1) / STD_BY), block(STD_BX, STD_BY);
-    CU(launch_pdl(std_step_kernel<S>, grid, block, 0, L->stream, p));
-    return GOC_OK;
-}
-
-template <class S>
-goc_status launch_strip_t(goc_lattice *L, const StepParams &p0) {
-    StepParams p = p0;
-    p.strip_h = L->strip_h;
-    const long long warps = (long long)strips_x(L->nx) * ((L->ny + L->strip_h - 1) / L->strip_h);
-    const unsigned blocks = (unsigned)((warps * 32 + STRIP_NT - 1) / STRIP_NT);
-    if (L->mhd.enabled) CU(launch_pdl(strip_kernel<S, true>, dim3(blocks), dim3(STRIP_NT), 0, L->stream, p));
-    else CU(launch_pdl(strip_kernel<S, false>, dim3(blocks), dim3(STRIP_NT), 0, L->stream, p));
+    CU(launch_pdl(L->cfg_pdl != 0, std_step_kernel<S>, grid, block, 0, L->stream, p));
     return GOC_OK;
 }
 
 template <class S>
 goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     if (L->scheme == 1) return launch_std_t<S>(L, p);
-    if (L->strip_h > 0) return launch_strip_t<S>(L, p);
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
     if (L->mhd.enabled) {
         const int grid = step_grid<S, true>(ntiles, &smem);
-        CU(launch_pdl(step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        CU(launch_pdl(L->cfg_pdl != 0, step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     } else {
         const int grid = step_grid<S, false>(ntiles, &smem);
-        CU(launch_pdl(step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        CU(launch_pdl(L->cfg_pdl != 0, step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     }
     CU(cudaGetLastError());
     return GOC_OK;
@@ -231,6 +225,9 @@ StepParams params_for(goc_lattice *L, int src, float *uout) {
     p.sr = (L->storage != GOC_FP32 && L->rounding == 0) ? 1 : 0;
     p.seed_rd = reinterpret_cast<const unsigned *>(L->flag + 2 + src);
     p.seed_wr = reinterpret_cast<unsigned *>(L->flag + 2 + (src ^ 1));
+    static const bool static_tiles = std::getenv("GOC_STATIC_TILES") != nullptr;
+    p.tctr = (static_tiles || !L->cfg_dynamic) ? nullptr : L->flag + 4 + src;
+    p.tctr_next = L->flag + 4 + (src ^ 1);
     p.use_tma = L->tma_ok ? 1 : 0;
     if (L->tma_ok) {
         p.tm_f = L->tmf[src];
@@ -253,6 +250,70 @@ goc_status launch_one(goc_lattice *L, float *uout) {
     L->cur ^= 1;
     L->steps++;
     L->fresh = false;
+    return GOC_OK;
+}
+
+// ---- launch autotuner ------------------------------------------------------
+// Candidates: tile queue or static order x dependent launch on or off (the
+// standard scheme has no tiles: dependent launch only).  Each runs 2 + 16
+// real steps of the lattice; the 16 are timed with CUDA events.
+constexpr long long kTuneWarm = 2, kTuneSteps = 16;
+std::mutex g_tune_mu;
+std::map<std::array<int, 5>, std::pair<int, int>> g_tune_cache;
+
+goc_status autotune(goc_lattice *L, long long *nsteps) {
+    if (L->tuned) return GOC_OK;
+    const std::array<int, 5> key = {L->nx, L->ny, L->storage, L->mhd.enabled ? 1 : 0, L->scheme};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            L->cfg_dynamic = it->second.first;
+            L->cfg_pdl = it->second.second;
+            L->tuned = true;
+            return GOC_OK;
+        }
+    }
+    const int ncand = L->scheme == 1 ? 2 : 4;
+    if (*nsteps < ncand * (kTuneWarm + kTuneSteps)) return GOC_OK;   // tune on a longer call
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bd = 1, bp = 1;
+    goc_status st = GOC_OK;
+    for (int c = 0; c < ncand && st == GOC_OK; c++) {
+        L->cfg_pdl = (c & 1) ? 0 : 1;
+        L->cfg_dynamic = (c & 2) ? 0 : 1;
+        for (long long s = 0; s < kTuneWarm && st == GOC_OK; s++) st = launch_one(L, nullptr);
+        cudaEventRecord(e0, L->stream);
+        for (long long s = 0; s < kTuneSteps && st == GOC_OK; s++) st = launch_one(L, nullptr);
+        cudaEventRecord(e1, L->stream);
+        if (st != GOC_OK) break;
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = fail(GOC_ECUDA, "autotuner timing failed");
+            break;
+        }
+        *nsteps -= kTuneWarm + kTuneSteps;
+        if (ms < best) {
+            best = ms;
+            bd = L->cfg_dynamic;
+            bp = L->cfg_pdl;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GOC_OK) return st;
+    L->cfg_dynamic = bd;
+    L->cfg_pdl = bp;
+    L->tuned = true;
+    if (L->graph) {   // captured under another configuration
+        cudaGraphExecDestroy(L->graph);
+        L->graph = nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {bd, bp};
     return GOC_OK;
 }
 
@@ -523,7 +584,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         L->check_every = exec->check_every > 0 ? exec->check_every : 100;
         L->rounding = exec->rounding;
         L->scheme = exec->scheme;
-        if (const char *e = std::getenv("GOC_STRIP_ROWS")) L->strip_h = std::max(0, std::atoi(e));
+        L->tuned = exec->fixed_launch != 0;
         if (exec->device >= 0) {
             cudaError_t e = cudaSetDevice(exec->device);
             if (e != cudaSuccess) {
@@ -555,7 +616,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     TRY(dalloc(L, &L->tab2, 7 * (size_t)L->ny * sizeof(float)));
     TRY(dalloc(L, &L->m1, 2 * (size_t)(L->nx + 2) * sizeof(double)));
     TRY(dalloc(L, &L->m2, 2 * (size_t)(L->ny + 2) * sizeof(double)));
-    TRY(dalloc(L, &L->flag, 4 * sizeof(int)));   // [0] status, [1] spare, [2..3] step counters of the two parities
+    TRY(dalloc(L, &L->flag, 8 * sizeof(int)));   // [0] status, [1] spare, [2..3] step counters, [4..5] tile queues of the two parities
     TRY(dalloc(L, &L->red, 8 * sizeof(double)));
     // metric (FP64), q, cs2 (Eq. GOC-LBE_CFL)
     TRY(compute_metric(grid, map, L->stream, L->m1, L->m2, L->red));
@@ -695,7 +756,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     if (std::getenv("GOC_DISABLE_TMA")) L->tma_ok = false;
     TRY(run_init(L, nullptr, nullptr, nullptr, nullptr, nullptr));
     {
-        cudaError_t e = cudaMemsetAsync(L->flag, 0, 4 * sizeof(int), L->stream);
+        cudaError_t e = cudaMemsetAsync(L->flag, 0, 8 * sizeof(int), L->stream);
         if (e != cudaSuccess) {
             free_lattice(L);
             return fail(GOC_ECUDA, "memset failed");
@@ -722,6 +783,10 @@ goc_status goc_step(goc_lattice *L, long long nsteps) {
         goc_status st = launch_one(L, nullptr);
         if (st != GOC_OK) return st;
         nsteps--;
+    }
+    {
+        goc_status st = autotune(L, &nsteps);
+        if (st != GOC_OK) return st;
     }
     if (nsteps > kGraphSteps) {
         goc_status st = ensure_graph(L);
@@ -750,6 +815,28 @@ goc_status goc_sync(goc_lattice *L) {
 }
 
 long long goc_steps_done(const goc_lattice *L) { return L ? L->steps : -1; }
+
+goc_status goc_launch_config(const goc_lattice *L, int *dynamic_tiles, int *pdl, int *tuned) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (dynamic_tiles) *dynamic_tiles = L->cfg_dynamic;
+    if (pdl) *pdl = L->cfg_pdl;
+    if (tuned) *tuned = L->tuned ? 1 : 0;
+    return GOC_OK;
+}
+
+goc_status goc_set_launch_config(goc_lattice *L, int dynamic_tiles, int pdl) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if ((dynamic_tiles != 0 && dynamic_tiles != 1) || (pdl != 0 && pdl != 1))
+        return fail(GOC_EINVAL, "dynamic_tiles and pdl must be 0 or 1");
+    L->cfg_dynamic = dynamic_tiles;
+    L->cfg_pdl = pdl;
+    L->tuned = true;
+    if (L->graph) {   // captured under another configuration
+        cudaGraphExecDestroy(L->graph);
+        L->graph = nullptr;
+    }
+    return GOC_OK;
+}
 
 goc_status goc_footprint(const goc_lattice *L, long long *nodes, long long *bytes) {
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
@@ -1092,12 +1179,12 @@ goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first =
         const dim3 gd(g.grid), bd(TX, TYT);
         cudaError_t e;
         switch (2 * g.storage + g.mhd) {
-            case 2: e = launch_pdl(batch_step_kernel<__half, false>, gd, bd, smem, st, a); break;
-            case 3: e = launch_pdl(batch_step_kernel<__half, true>, gd, bd, smem, st, a); break;
-            case 4: e = launch_pdl(batch_step_kernel<__nv_bfloat16, false>, gd, bd, smem, st, a); break;
-            case 5: e = launch_pdl(batch_step_kernel<__nv_bfloat16, true>, gd, bd, smem, st, a); break;
-            case 1: e = launch_pdl(batch_step_kernel<float, true>, gd, bd, smem, st, a); break;
-            default: e = launch_pdl(batch_step_kernel<float, false>, gd, bd, smem, st, a); break;
+            case 2: e = launch_pdl(true, batch_step_kernel<__half, false>, gd, bd, smem, st, a); break;
+            case 3: e = launch_pdl(true, batch_step_kernel<__half, true>, gd, bd, smem, st, a); break;
+            case 4: e = launch_pdl(true, batch_step_kernel<__nv_bfloat16, false>, gd, bd, smem, st, a); break;
+            case 5: e = launch_pdl(true, batch_step_kernel<__nv_bfloat16, true>, gd, bd, smem, st, a); break;
+            case 1: e = launch_pdl(true, batch_step_kernel<float, true>, gd, bd, smem, st, a); break;
+            default: e = launch_pdl(true, batch_step_kernel<float, false>, gd, bd, smem, st, a); break;
         }
         CU(e);
         CU(cudaGetLastError());

@@ -73,7 +73,11 @@ struct StepParams {
     // launch of the other buffer parity reads)
     int sr;
     int constF;                // 1: no stored force; the force of every step is the body force
-    int strip_h;               // rows per warp strip (strip kernel)
+    // tile queue of the single-lattice step kernel: this launch takes tiles from
+    // *tctr and zeroes *tctr_next for the launch of the other buffer parity
+    // (tctr == null: static order, block b takes tiles b, b + grid, ...)
+    int *tctr;
+    int *tctr_next;
     const unsigned *seed_rd;
     unsigned *seed_wr;
     // TMA descriptors of the input buffers (3D: [planes][ny][nx])

@@ -767,34 +767,37 @@ __device__ __forceinline__ void run_tile(const StepParams &p, int kind, int i0, 
     }
 }
 
-// The tiles first, first + stride, ... of one lattice, processed by one block
-// with TMA staging in two dynamic shared-memory stages: the copy of the next
-// tile is issued before the current one is computed.  Every thread of the
-// block calls it; the barriers must be initialised.
-// m: the TMA descriptors of the input buffers (a tensor map must sit in
-// parameter, constant or global memory).
+// The tiles of one lattice processed by one block with TMA staging in two
+// dynamic shared-memory stages: the copy of the next tile is issued before
+// the current one is computed.  Block b starts with tile first = b; the next
+// tile is stride + the counter's next value (dynamic order, with ctr) or
+// t + stride (static order).  Every thread of the block calls it; the barriers
+// must be initialised.
 template <class S, bool MHD>
-__device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMaps &m, int first, int stride,
-                                              unsigned char *dyn, uint64_t *bars, FieldSmem &sm, bool leader) {
+__device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMaps &m, int *ctr, int first, int stride,
+                                              unsigned char *dyn, uint64_t *bars, FieldSmem &sm, int *s_item,
+                                              bool leader) {
     using T = Tiling<S>;
     constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
     const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY, ntiles = ntx * nty;
-    int t = first;
-    if (leader && t < ntiles) {
-        const int i0 = (t % ntx) * TX, j0 = (t / ntx) * TY;
-        if (tile_kind<S>(p, i0, j0) != 2) issue_tile<S>(m, i0, j0, dyn, &bars[0], MHD);
-    }
-    uint32_t ph0 = 0, ph1 = 0;
-    int stage = 0;
-    for (; t < ntiles; t += stride) {
-        const int tn = t + stride;
-        if (leader && tn < ntiles) {
-            const int i0n = (tn % ntx) * TX, j0n = (tn / ntx) * TY;
-            if (tile_kind<S>(p, i0n, j0n) != 2) {
+    auto take = [&](int st, int t) {   // leader: record item t for stage st and start its copy
+        s_item[st] = t;
+        if (t < ntiles) {
+            const int i0 = (t % ntx) * TX, j0 = (t / ntx) * TY;
+            if (tile_kind<S>(p, i0, j0) != 2) {
                 fence_proxy_async();   // generic reads of that stage (previous tile) precede the async writes
-                issue_tile<S>(m, i0n, j0n, dyn + (stage ^ 1) * STAGE, &bars[stage ^ 1], MHD);
+                issue_tile<S>(m, i0, j0, dyn + st * STAGE, &bars[st], MHD);
             }
         }
+    };
+    if (leader) take(0, first);
+    __syncthreads();
+    uint32_t ph0 = 0, ph1 = 0;
+    int stage = 0;
+    for (;;) {
+        const int t = s_item[stage];
+        if (t >= ntiles) break;   // uniform: every thread reads the same shared value
+        if (leader) take(stage ^ 1, ctr ? stride + atomicAdd(ctr, 1) : t + stride);
         const int i0 = (t % ntx) * TX, j0 = (t / ntx) * TY;
         const int kind = tile_kind<S>(p, i0, j0);
         if (kind != 2) {
@@ -804,17 +807,18 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
             ph ^= 1;
         }
         run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm);
-        __syncthreads();   // the stage and the field arrays are reused by the next tile
+        __syncthreads();   // the stage, the field arrays and s_item are reused by the next tile
         stage ^= 1;
     }
 }
 
-// Single lattice: persistent blocks stride over the tiles.
+// Single lattice: persistent blocks take tiles from the lattice's queue.
 template <class S, bool MHD>
 __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ FieldSmem sm;
+    __shared__ int s_item[2];
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     if (leader) {
         mbar_init(&bars[0], 1);
@@ -823,10 +827,12 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_c
     }
     griddep_launch_dependents();
     griddep_wait();   // the previous step is complete: its populations may be read and overwritten
-    if (leader && Store<S>::scaled && p.sr && blockIdx.x == 0) *p.seed_wr = *p.seed_rd + 1u;   // next step's index
-    __syncthreads();
+    if (leader && blockIdx.x == 0) {
+        if (Store<S>::scaled && p.sr) *p.seed_wr = *p.seed_rd + 1u;   // next step's index
+        if (p.tctr) *p.tctr_next = 0;                                  // next step's tile queue
+    }
     const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
-    lattice_tiles<S, MHD>(p, m, blockIdx.x, gridDim.x, dyn, bars, sm, leader);
+    lattice_tiles<S, MHD>(p, m, p.tctr, blockIdx.x, gridDim.x, dyn, bars, sm, s_item, leader);
 }
 
 // Many lattices in one launch.  Their parameters travel in the kernel
@@ -836,8 +842,9 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_c
 // leader takes the next item from a global counter while the current one is
 // computed (its TMA copy goes into the other stage), so tiles of unequal cost
 // (wall tiles, tiles on periodic seams read from global memory) balance out
-// over the blocks.  The counter of a step is ctr[parity]; each launch zeroes
-// the other one for the next step.
+// over the blocks.  Block b starts with item b; the counter of a step,
+// ctr[parity], hands out the items from gridDim.x on; each launch zeroes the
+// other counter for the next step.
 constexpr int kBatchMax = 32;
 struct BatchArgs {
     int n;                          // lattices in this launch
@@ -874,9 +881,9 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const __
     }
     griddep_launch_dependents();
     griddep_wait();   // the previous step of every member is complete
-    // take item t and start its copy into stage st (leader only)
-    auto take = [&](int st) {
-        const int t = atomicAdd(&a.ctr[a.parity], 1);
+    // record item t for stage st and start its copy (leader only); block b
+    // starts with item b, later items come from the counter
+    auto take = [&](int st, int t) {
         s_item[st] = t;
         if (t < items) {
             const int k = batch_lattice(a, t);
@@ -892,7 +899,7 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const __
     };
     if (leader) {
         if (blockIdx.x == 0) a.ctr[a.parity ^ 1] = 0;   // the next step's counter
-        take(0);
+        take(0, blockIdx.x);
     }
     __syncthreads();
     uint32_t ph0 = 0, ph1 = 0;
@@ -900,7 +907,7 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const __
     for (;;) {
         const int t = s_item[stage];
         if (t >= items) break;   // uniform: every thread reads the same shared value
-        if (leader) take(stage ^ 1);
+        if (leader) take(stage ^ 1, (int)gridDim.x + atomicAdd(&a.ctr[a.parity], 1));
         const int k = batch_lattice(a, t);
         const StepParams &p = a.p[k];
         const int ntx = (p.nx + TX - 1) / TX, local = t - a.toff[k];

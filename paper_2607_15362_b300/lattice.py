@@ -70,7 +70,8 @@ ROUNDING = {"stochastic": 0, "nearest": 1}
 SCHEMES = {"goc": 0, "standard": 1}
 
 
-def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", scheme: str = "goc") -> GocExec:
+def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", scheme: str = "goc",
+          fixed_launch: bool = False) -> GocExec:
     e = GocExec()
     e.storage = _abi.STORAGE[storage]
     e.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
@@ -78,6 +79,7 @@ def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", 
     e.check_every = int(check_every)
     e.rounding = ROUNDING[rounding]
     e.scheme = SCHEMES[scheme]
+    e.fixed_launch = 1 if fixed_launch else 0
     return e
 
 
@@ -85,7 +87,8 @@ class Lattice:
     """One lattice owned by libgoc."""
 
     def __init__(self, spec: dict, storage: str = "fp32", stream=None, check_every: int = 100,
-                 rounding: str = "stochastic", scheme: str = "goc", _handle=None, _owner=None):
+                 rounding: str = "stochastic", scheme: str = "goc", fixed_launch: bool = False,
+                 _handle=None, _owner=None):
         """scheme "standard": the uniform-grid central-moment LBM comparator
         (uniform maps, spec["gi"] = 0, no MIE)."""
         self.spec = spec
@@ -96,7 +99,7 @@ class Lattice:
             self._h = _handle
         else:
             g, m, f, h = structs_from_spec(spec)
-            e = _exec(storage, stream, check_every, rounding, scheme)
+            e = _exec(storage, stream, check_every, rounding, scheme, fixed_launch)
             out = ctypes.c_void_p()
             check(lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f),
                                    ctypes.byref(h), ctypes.byref(e), ctypes.byref(out)))
@@ -170,6 +173,15 @@ class Lattice:
         n, b = ctypes.c_longlong(), ctypes.c_longlong()
         check(lib().goc_footprint(self._h, ctypes.byref(n), ctypes.byref(b)))
         return n.value, b.value
+
+    @property
+    def launch_config(self) -> dict:
+        d, p, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().goc_launch_config(self._h, ctypes.byref(d), ctypes.byref(p), ctypes.byref(t)))
+        return {"dynamic_tiles": bool(d.value), "pdl": bool(p.value), "tuned": bool(t.value)}
+
+    def set_launch_config(self, dynamic_tiles: bool, pdl: bool):
+        check(lib().goc_set_launch_config(self._h, int(dynamic_tiles), int(pdl)))
 
     @property
     def bytes_per_node(self) -> float:

@@ -200,3 +200,29 @@ def test_interior_tiles_match_the_oracle(gpu, kind):
     assert np.abs(fg[0] - fo[0]).max() <= 1e-6
     if prob.mhd:
         assert relerr(fg[3], fo[3]) <= 1e-5
+
+
+def test_launch_configurations_give_bitwise_identical_populations(gpu):
+    """Tile queue vs static tile order and dependent launch on or off change
+    only which block computes which tile and when: the populations agree
+    bitwise (on a cavity with interior, wall and ragged tiles, and on a
+    periodic channel whose seam tiles read global memory)."""
+    for prob in (gi.Problem("cavity", 200, 90, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
+                            {"Re": 100.0, "u_lid": 0.05}),
+                 gi.Problem("hartmann", 70, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
+                            {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0})):
+        spec = prob.lattice_spec(cs2_of(prob))
+        states = []
+        for dyn, pdl in ((True, True), (False, True), (True, False), (False, False)):
+            L = goc.Lattice(spec)
+            L.set_launch_config(dyn, pdl)
+            L.step(150)
+            assert L.launch_config == {"dynamic_tiles": dyn, "pdl": pdl, "tuned": True}
+            states.append(L.get_state())
+            L.close()
+        assert all(s == states[0] for s in states[1:])
+        A = goc.Lattice(spec)            # autotuned on its first long call
+        A.step(150)
+        assert A.launch_config["tuned"]
+        assert A.get_state() == states[0]
+        A.close()
