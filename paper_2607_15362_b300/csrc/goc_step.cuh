@@ -43,7 +43,11 @@ namespace goc {
 #define GOC_TILE_ROWS 8        // tile height (rows); the tile width is one warp
 #endif
 #ifndef GOC_MIN_BLOCKS
-#define GOC_MIN_BLOCKS 3       // resident blocks per SM asked of the register allocator (measured best)
+#define GOC_MIN_BLOCKS 4       // resident blocks per SM asked of the register allocator, NSE kernels (64
+                               // registers; measured best: 124.9 vs 139.7 us at 2048^2 with 3 blocks)
+#endif
+#ifndef GOC_MIN_BLOCKS_MHD
+#define GOC_MIN_BLOCKS_MHD 2   // with the MIE two stages of 41 KB leave room for two blocks per SM
 #endif
 #ifndef GOC_ROWS_PER_THREAD
 #define GOC_ROWS_PER_THREAD 1  // nodes per thread (rows ty + r TY/RPT); 2 runs the collision on packed f32x2 (measured slower)
@@ -250,6 +254,14 @@ __device__ __forceinline__ void pull_mie(const StepParams &p, const Src &src, in
     }
 }
 
+// Hardware reciprocal (rcp.approx: relative error below 2^-22, no refinement):
+// rho is near rho0, far from zero, infinities and denormals.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // rho and U (Eq. GOChydrodynamicfields) from pre-collision deviations d and the
 // previous step's F - F_rest: the -F_rest/2 momentum of f_ref- and the +F_rest/2
 // of the force shift cancel, leaving U1 = (sum d e1 + (F1 - F1_rest)/2)/(rho h2).
@@ -261,7 +273,7 @@ __device__ __forceinline__ void fields_from(const StepParams &p, const float d[9
     const float k10 = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
     const float k01 = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
     drho = k00 * (ih1 * ih2);
-    const float irho = __frcp_rn(p.rho0 + drho);
+    const float irho = rcp_approx(p.rho0 + drho);
     U1 = (k10 + 0.5f * F1p) * irho * ih2;
     U2 = (k01 + 0.5f * F2p) * irho * ih1;
 }
@@ -775,31 +787,35 @@ __device__ __forceinline__ void run_tile(const StepParams &p, int kind, int i0, 
 // must be initialised.
 template <class S, bool MHD>
 __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMaps &m, int *ctr, int first, int stride,
-                                              unsigned char *dyn, uint64_t *bars, FieldSmem &sm, int *s_item,
+                                              unsigned char *dyn, uint64_t *bars, FieldSmem &sm, int4 *s_item,
                                               bool leader) {
     using T = Tiling<S>;
     constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
     const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY, ntiles = ntx * nty;
-    auto take = [&](int st, int t) {   // leader: record item t for stage st and start its copy
-        s_item[st] = t;
+    // leader: record item t for stage st as (t, i0, j0, kind) and start its copy
+    auto take = [&](int st, int t) {
+        int4 it = make_int4(t, 0, 0, 0);
         if (t < ntiles) {
-            const int i0 = (t % ntx) * TX, j0 = (t / ntx) * TY;
-            if (tile_kind<S>(p, i0, j0) != 2) {
+            it.y = (t % ntx) * TX;
+            it.z = (t / ntx) * TY;
+            it.w = tile_kind<S>(p, it.y, it.z);
+            if (it.w != 2) {
                 fence_proxy_async();   // generic reads of that stage (previous tile) precede the async writes
-                issue_tile<S>(m, i0, j0, dyn + st * STAGE, &bars[st], MHD);
+                issue_tile<S>(m, it.y, it.z, dyn + st * STAGE, &bars[st], MHD);
             }
         }
+        s_item[st] = it;
     };
     if (leader) take(0, first);
     __syncthreads();
     uint32_t ph0 = 0, ph1 = 0;
     int stage = 0;
     for (;;) {
-        const int t = s_item[stage];
+        const int4 it = s_item[stage];
+        const int t = it.x;
         if (t >= ntiles) break;   // uniform: every thread reads the same shared value
         if (leader) take(stage ^ 1, ctr ? stride + atomicAdd(ctr, 1) : t + stride);
-        const int i0 = (t % ntx) * TX, j0 = (t / ntx) * TY;
-        const int kind = tile_kind<S>(p, i0, j0);
+        const int i0 = it.y, j0 = it.z, kind = it.w;
         if (kind != 2) {
             uint32_t &ph = stage ? ph1 : ph0;
             const bool ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
@@ -814,11 +830,11 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
 
 // Single lattice: persistent blocks take tiles from the lattice's queue.
 template <class S, bool MHD>
-__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
+__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ FieldSmem sm;
-    __shared__ int s_item[2];
+    __shared__ int4 s_item[2];
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     if (leader) {
         mbar_init(&bars[0], 1);
@@ -865,13 +881,13 @@ __device__ __forceinline__ int batch_lattice(const BatchArgs &a, int t) {
 }
 
 template <class S, bool MHD>
-__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) batch_step_kernel(const __grid_constant__ BatchArgs a) {
     using T = Tiling<S>;
     constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ FieldSmem sm;
-    __shared__ int s_item[2];
+    __shared__ int4 s_item[2];   // per stage: item, i0, j0, 4 lattice + tile kind
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     const int items = a.toff[a.n];
     if (leader) {
@@ -884,18 +900,23 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const __
     // record item t for stage st and start its copy (leader only); block b
     // starts with item b, later items come from the counter
     auto take = [&](int st, int t) {
-        s_item[st] = t;
+        int4 it = make_int4(t, 0, 0, 0);
         if (t < items) {
             const int k = batch_lattice(a, t);
             const StepParams &q = a.p[k];
             const int ntx = (q.nx + TX - 1) / TX, local = t - a.toff[k];
-            const int i0 = (local % ntx) * TX, j0 = (local / ntx) * TY;
-            if (tile_kind<S>(q, i0, j0) != 2) {
+            it.y = (local % ntx) * TX;
+            it.z = (local / ntx) * TY;
+            const int kind = tile_kind<S>(q, it.y, it.z);
+            it.w = 4 * k + kind;
+            if (kind != 2) {
                 const TileMaps m{a.maps + 3 * k, a.maps + 3 * k + 1, a.maps + 3 * k + 2};
                 fence_proxy_async();   // generic reads of that stage precede the async writes
-                issue_tile<S>(m, i0, j0, dyn + st * STAGE, &bars[st], MHD);
+                issue_tile<S>(m, it.y, it.z, dyn + st * STAGE, &bars[st], MHD);
             }
+            if (local == 0 && Store<S>::scaled && q.sr) *q.seed_wr = *q.seed_rd + 1u;
         }
+        s_item[st] = it;
     };
     if (leader) {
         if (blockIdx.x == 0) a.ctr[a.parity ^ 1] = 0;   // the next step's counter
@@ -905,15 +926,11 @@ __global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) batch_step_kernel(const __
     uint32_t ph0 = 0, ph1 = 0;
     int stage = 0;
     for (;;) {
-        const int t = s_item[stage];
-        if (t >= items) break;   // uniform: every thread reads the same shared value
+        const int4 it = s_item[stage];
+        if (it.x >= items) break;   // uniform: every thread reads the same shared value
         if (leader) take(stage ^ 1, (int)gridDim.x + atomicAdd(&a.ctr[a.parity], 1));
-        const int k = batch_lattice(a, t);
+        const int k = it.w >> 2, kind = it.w & 3, i0 = it.y, j0 = it.z;
         const StepParams &p = a.p[k];
-        const int ntx = (p.nx + TX - 1) / TX, local = t - a.toff[k];
-        const int i0 = (local % ntx) * TX, j0 = (local / ntx) * TY;
-        if (leader && local == 0 && Store<S>::scaled && p.sr) *p.seed_wr = *p.seed_rd + 1u;
-        const int kind = tile_kind<S>(p, i0, j0);
         if (kind != 2) {
             uint32_t &ph = stage ? ph1 : ph0;
             const bool ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
