@@ -123,13 +123,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def setup_dist():
+def setup_dist(backend: str = "nccl"):
+    """Ranks from the torchrun environment; a process group when there are
+    several (NCCL on the GPUs; the host-side tests use gloo)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
+        dist.init_process_group(backend, init_method="env://")
     return world, rank, local
 
 
@@ -139,14 +141,21 @@ def barrier(world):
         dist.barrier()
 
 
-def allmax(world, x: float) -> float:
+def allmax(world, x: float, device: str = "cuda") -> float:
+    """Maximum of x over the ranks (the job's time is the slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, ms_max: float) -> float:
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time (units per second / 1e6)."""
+    return world * units_per_rank / (ms_max * 1e-3) / 1e6
 
 
 def run_ours(args):
@@ -190,7 +199,7 @@ def run_ours(args):
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms_total = allmax(world, sum(ms_steps))
     ms_per_step = ms_total / args.steps
-    mlups = world * nodes * chunk * args.steps / (ms_total * 1e-3) / 1e6
+    mlups = job_rate(world, nodes * chunk * args.steps, ms_total)
 
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
