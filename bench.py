@@ -167,7 +167,7 @@ def run_ours(args):
     world, rank, local = setup_dist()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    prob = gi.cfg2_cavity(n=args.cavity_n)
+    prob = gi.lid_cavity(n=args.cavity_n)
     _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
     spec = prob.lattice_spec(cs2)
     lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream)
@@ -266,7 +266,7 @@ def run_ours(args):
 
 
 def run_batch(args):
-    """cfg4: 64 lattices (seed 7) advanced together by the persistent batched
+    """64 lattices (seed 7) advanced together by the persistent batched
     kernel vs one lattice at a time with its own launches; FP32 and 16-bit."""
     import torch
 
@@ -275,7 +275,7 @@ def run_batch(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    probs = gi.cfg4_batch(steps=args.batch_steps)
+    probs = gi.batch_lattices(steps=args.batch_steps)
     specs = [lattice_spec(p) for p in probs]
     nodes = sum(p.nodes for p in probs)
     out = {}
@@ -309,14 +309,14 @@ def run_batch(args):
         total_ms += e0.elapsed_time(e1)
         lat.close()
     out["sequential_fp32_mlups"] = round(nodes * args.batch_steps / total_ms / 1e3, 1)
-    line = {"metric": METRIC, "workload": "cfg4 batch of 64 lattices (seed 7)", "lattices": len(probs),
+    line = {"metric": METRIC, "workload": "batch of 64 stretched-grid lattices (seed 7)", "lattices": len(probs),
             "nodes": nodes, "steps_each": args.batch_steps, "unit": "MLUPS", **out,
             "speedup_batched_vs_sequential": round(out["batched_fp32_mlups"] / out["sequential_fp32_mlups"], 3)}
     print(json.dumps(line))
 
 
 def run_serve(args):
-    """cfg5: the first requests of the seed-11 Poisson trace served with
+    """The first requests of the seed-11 Poisson trace served with
     continuous batching vs one solve at a time; p50/p99 latency and
     aggregate MLUPS."""
     import torch
@@ -324,7 +324,7 @@ def run_serve(args):
     from paper_2607_15362_b300.serve import Server, requests_from_trace, run_sequential
 
     torch.cuda.set_device(0)
-    trace = gi.cfg5_stream()[: args.requests]
+    trace = gi.serving_trace()[: args.requests]
     reqs = requests_from_trace(trace, storage=args.storage)
     offered = sum(r.problem.nodes * r.budget for r in reqs) / max(trace[-1]["arrival_s"], 1e-9) / 1e6
     srv = Server(150 * (1 << 30) // 1, max_slots=256, chunk=args.chunk if args.chunk != 1000 else 500,
@@ -332,7 +332,7 @@ def run_serve(args):
     res_b, sum_b = srv.run(reqs, max_wall_s=args.serve_seconds)
     srv.close()
     res_s, sum_s = run_sequential(reqs, max_wall_s=args.serve_seconds)
-    line = {"metric": METRIC, "workload": f"cfg5 serving trace (seed 11), first {len(reqs)} requests",
+    line = {"metric": METRIC, "workload": f"serving trace (seed 11), first {len(reqs)} requests",
             "unit": "MLUPS", "offered_mlups": round(offered, 1),
             "batched": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in sum_b.items()},
             "sequential": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in sum_s.items()}}
@@ -398,7 +398,7 @@ def run_accuracy(args):
         return {"n": prob.nx, "steps": steps, "seconds": ms / 1e3, "mlups": prob.nodes * steps / ms / 1e3,
                 "profiles": _centrelines(prob, fields, u_lid)}
 
-    ref = run(gi.cfg2_uniform_comparator(n=args.ref_n), "standard")
+    ref = run(gi.uniform_cavity(n=args.ref_n), "standard")
     ry, ru, rx, rv = ref["profiles"]
 
     def err(r):
@@ -410,11 +410,11 @@ def run_accuracy(args):
                              / (np.sum(uref ** 2) + np.sum(vref ** 2))))
 
     rows = []
-    goc_r = run(gi.cfg2_cavity(n=512), "goc")
+    goc_r = run(gi.lid_cavity(n=512), "goc")
     rows.append({"scheme": "goc tanh beta=2", **{k: goc_r[k] for k in ("n", "steps", "seconds", "mlups")},
                  "centreline_rel_err": err(goc_r)})
     for n in args.uniform_sizes:
-        r = run(gi.cfg2_uniform_comparator(n=n), "standard")
+        r = run(gi.uniform_cavity(n=n), "standard")
         rows.append({"scheme": "standard uniform", **{k: r[k] for k in ("n", "steps", "seconds", "mlups")},
                      "centreline_rel_err": err(r)})
     for r in rows:
@@ -434,11 +434,119 @@ def run_accuracy(args):
             match = {"uniform_n": round(n, 1), "uniform_seconds": round(t, 3),
                      "goc_seconds": rows[0]["seconds"], "goc_speedup_at_matched_accuracy": round(t / rows[0]["seconds"], 3)}
             break
-    line = {"metric": METRIC, "workload": f"cfg2 cavity matched accuracy at t* = {tstar}", "unit": "MLUPS",
+    line = {"metric": METRIC, "workload": f"512^2 cavity matched accuracy at t* = {tstar}", "unit": "MLUPS",
             "reference": {"scheme": "standard uniform FP32", "n": ref["n"], "steps": ref["steps"],
                           "mlups": round(ref["mlups"], 1)},
             "runs": rows, "matched": match}
     print(json.dumps(line))
+
+
+def _hartmann_analytic(spec, ny, positions):
+    """u_x and B_x of the Hartmann flow (Sec. 7.4) at physical positions y in
+    [0, ny] of a channel of half-width H = ny/2."""
+    import numpy as np
+    d = spec["derived"]
+    Ha = float(spec.get("_Ha"))
+    ys = positions / d["H"] - 1.0
+    Ur = d["H"] ** 2 * d["Fx"] / d["nu"]
+    Br = d["H"] ** 2 * d["Fx"] / math.sqrt(d["nu"] * d["eta"])
+    ua = Ur / (Ha * math.tanh(Ha)) * (1 - np.cosh(Ha * ys) / math.cosh(Ha))
+    ba = Br * (-ys / Ha + np.sinh(Ha * ys) / (Ha * math.tanh(Ha) * math.cosh(Ha)))
+    return ua, ba
+
+
+def run_accuracy_mhd(args):
+    """Matched accuracy for the Hartmann channel (Ha = 100, Re = 100, Pm = 1,
+    256 periodic columns), scored by the column-mean u_x, B_x against the
+    analytic profiles of Sec. 7.4.
+
+    The GOC grid (wall-normal tanh beta = 3, 1024 rows) has c_s^2 = q^2/3 =
+    3.0e-4, so nu = eta = 1.5e-4 and the Alfven crossing time 2 H^2/(Ha nu)
+    is 3.5e7 steps: from rest it needs about 1e8 steps.  It therefore starts
+    from the analytic profiles and runs until its own discrete steady state
+    (residual 1e-9, no new smallest residual over 20 checks, or the step
+    cap), which measures its discretisation error.  The uniform grids (the
+    same library with h = 1 and the cubic terms dropped: the standard
+    central-moment D2Q9 + D2Q5 scheme, c_s^2 = 1/3) run from rest for four
+    crossing times.  The matched uniform size is interpolated (or
+    extrapolated with the measured order) in log-log."""
+    import numpy as np
+    import torch
+
+    import paper_2607_15362_b300 as goc
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    Ha, Re = 100.0, 100.0
+
+    def run(ny, stretched):
+        if stretched:
+            prob = gi.Problem("hartmann", args.mhd_nx, ny, {"kind": "uniform"}, {"kind": "tanh2", "beta": 3.0},
+                              {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0})
+            _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
+            eta = (np.arange(ny) + 0.5) / ny
+            y = 0.5 * ny * (1.0 + np.tanh(3.0 * (2.0 * eta - 1.0)) / np.tanh(3.0))
+        else:
+            prob = gi.Problem("hartmann", args.mhd_nx, ny, {"kind": "uniform"}, {"kind": "uniform"},
+                              {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0, "gi": 0})
+            cs2 = 1.0 / 3.0
+            y = np.arange(ny) + 0.5
+        spec = prob.lattice_spec(cs2)
+        spec["_Ha"] = Ha
+        d = spec["derived"]
+        crossing = 2.0 * d["H"] ** 2 / (Ha * d["nu"])
+        ua, ba = _hartmann_analytic(spec, ny, y)
+        lat = goc.Lattice(spec, stream=stream.cuda_stream, check_every=5000 if stretched else 500,
+                          plateau_checks=20 if stretched else 0)
+        if stretched:
+            shape = (ny, args.mhd_nx)
+            lat.init_fields(u1=np.broadcast_to(ua[:, None], shape).copy(),
+                            b1=np.broadcast_to(ba[:, None], shape).copy())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if stretched:
+            steps, res = lat.run_until(1e-9, args.mhd_goc_max_steps)
+        else:
+            steps = int(4 * crossing)
+            lat.step(steps)
+            lat.sync()
+            res = None
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        f = lat.moments()
+        lat.close()
+        u, b = f[1].mean(axis=1), f[3].mean(axis=1)
+        eu = float(np.linalg.norm(u - ua) / np.linalg.norm(ua))
+        eb = float(np.linalg.norm(b - ba) / np.linalg.norm(ba))
+        row = {"grid": "goc tanh beta=3" if stretched else "uniform", "ny": ny,
+               "start": "analytic" if stretched else "rest", "steps": int(steps),
+               "crossing_steps": round(crossing), "seconds": round(wall, 3),
+               "mlups": round(args.mhd_nx * ny * steps / wall / 1e6, 1),
+               "err_u": float(f"{eu:.4g}"), "err_b": float(f"{eb:.4g}"), "err": float(f"{max(eu, eb):.4g}")}
+        if res is not None:
+            row["residual"] = float(f"{res:.3g}")
+        return row
+
+    rows = [run(args.mhd_goc_ny, True)]
+    for ny in args.mhd_uniform_ny:
+        rows.append(run(ny, False))
+    uni = sorted(rows[1:], key=lambda r: r["ny"])
+    target = rows[0]["err"]
+    match = None
+    for a, b in zip(uni, uni[1:]):
+        ea, eb = a["err"], b["err"]
+        if (ea - target) * (eb - target) <= 0 and ea != eb:
+            w = (np.log(target) - np.log(ea)) / (np.log(eb) - np.log(ea))
+            match = {"uniform_ny": round(float(np.exp(np.log(a["ny"]) + w * (np.log(b["ny"]) - np.log(a["ny"])))), 1),
+                     "how": "interpolated"}
+            break
+    if match is None and len(uni) >= 2 and uni[-1]["err"] < uni[-2]["err"]:
+        a, b = uni[-2], uni[-1]
+        order = np.log(a["err"] / b["err"]) / np.log(b["ny"] / a["ny"])
+        ny = b["ny"] * (b["err"] / target) ** (1.0 / order)
+        match = {"uniform_ny": round(float(ny), 1), "how": f"extrapolated with the measured order {order:.2f}"}
+    print(json.dumps({"metric": METRIC, "workload": f"Hartmann channel {args.mhd_nx} columns, Ha = 100, Re = 100: "
+                      "matched accuracy", "runs": rows, "matched": match}))
 
 
 def cpu_baseline(prob, spec_lib, budget_s: float = 15.0):
@@ -465,7 +573,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    prob = gi.cfg2_cavity()
+    prob = gi.lid_cavity()
     cores = os.cpu_count() or 1
     cs2 = oracle.build_metric(prob.lattice_spec(1.0)).cs2()
     o = oracle.Oracle(prob.lattice_spec(cs2), threads=cores)
@@ -504,7 +612,11 @@ def main():
     ap.add_argument("--cavity-n", type=int, default=512, help="cavity side (512 is the benchmark workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "batch", "serve", "accuracy"])
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "batch", "serve", "accuracy", "accuracy_mhd"])
+    ap.add_argument("--mhd-nx", type=int, default=256)
+    ap.add_argument("--mhd-goc-ny", type=int, default=1024)
+    ap.add_argument("--mhd-goc-max-steps", type=int, default=1000000)
+    ap.add_argument("--mhd-uniform-ny", type=int, nargs="+", default=[512, 1024, 2048])
     ap.add_argument("--tstar", type=float, default=5.0, help="accuracy workload: dimensionless time t u_lid / L")
     ap.add_argument("--ref-n", type=int, default=2048, help="accuracy workload: reference grid side")
     ap.add_argument("--uniform-sizes", type=int, nargs="+", default=[256, 384, 512, 768, 1024])
@@ -520,6 +632,8 @@ def main():
         run_serve(args)
     elif args.workload == "accuracy":
         run_accuracy(args)
+    elif args.workload == "accuracy_mhd":
+        run_accuracy_mhd(args)
     else:
         run_ours(args)
 

@@ -132,14 +132,14 @@ def _node_positions(m: dict, n: int) -> np.ndarray:
 
 # ---- the benchmark configurations -------------------------------------------
 
-def cfg1_poiseuille(nx: int = 32, ny: int = 64, beta: float = 1.5) -> Problem:
+def poiseuille_channel(nx: int = 32, ny: int = 64, beta: float = 1.5) -> Problem:
     """Plain GOC-LBM Poiseuille channel: 32 x 64, wall-normal tanh map
     beta = 1.5, Re = 10, tau = 0.8, body-force driven, 2000 steps from rest."""
     return Problem("poiseuille", nx, ny, {"kind": "uniform"}, {"kind": "tanh2", "beta": beta},
-                   {"Re": 10.0, "tau": 0.8}, steps=2000, name="cfg1_poiseuille_32x64")
+                   {"Re": 10.0, "tau": 0.8}, steps=2000, name="poiseuille_channel_32x64")
 
 
-def cfg2_cavity(n: int = 512, beta: float = 2.0, Re: float = 1000.0, u_lid: float = 0.05,
+def lid_cavity(n: int = 512, beta: float = 2.0, Re: float = 1000.0, u_lid: float = 0.05,
                 steps: int = 20000, mach_matched: bool = True) -> Problem:
     """Lid-driven cavity 512 x 512, tanh clustering to all four walls (beta = 2),
     Re = 1000, 20000 steps.  The lid speed 0.05 is taken at the Mach number it
@@ -148,28 +148,28 @@ def cfg2_cavity(n: int = 512, beta: float = 2.0, Re: float = 1000.0, u_lid: floa
     it is Mach 0.58 on this grid and the FP64 oracle diverges near step 850."""
     return Problem("cavity", n, n, {"kind": "tanh2", "beta": beta}, {"kind": "tanh2", "beta": beta},
                    {"Re": Re, "u_lid": u_lid, "mach_matched": mach_matched}, steps=steps,
-                   name=f"cfg2_cavity_{n}x{n}")
+                   name=f"lid_cavity_{n}x{n}")
 
 
-def cfg2_uniform_comparator(n: int = 1024, Re: float = 1000.0, u_lid: float = 0.05,
+def uniform_cavity(n: int = 1024, Re: float = 1000.0, u_lid: float = 0.05,
                             steps: int = 20000) -> Problem:
     """The matched-accuracy baseline: the same cavity on a uniform 1024^2 grid
     (c_s^2 = 1/3, lid 0.05 = Mach 0.087), run by the standard uniform-grid
     central-moment LBM, i.e. without the cubic correction terms (gi = 0)."""
     return Problem("cavity", n, n, {"kind": "uniform"}, {"kind": "uniform"},
-                   {"Re": Re, "u_lid": u_lid, "gi": 0}, steps=steps, name=f"cfg2_uniform_{n}x{n}")
+                   {"Re": Re, "u_lid": u_lid, "gi": 0}, steps=steps, name=f"uniform_cavity_{n}x{n}")
 
 
-def cfg3_hartmann(nx: int = 256, ny: int = 1024, beta: float = 3.0, Ha: float = 100.0,
+def hartmann_channel(nx: int = 256, ny: int = 1024, beta: float = 3.0, Ha: float = 100.0,
                   Re: float = 100.0) -> Problem:
     """Coupled MHD Hartmann channel 256 x 1024, wall-normal tanh beta = 3,
     Ha = 100, Re = 100, magnetic Prandtl number 1 (tau = tau_m)."""
     return Problem("hartmann", nx, ny, {"kind": "uniform"}, {"kind": "tanh2", "beta": beta},
                    {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0}, steps=0,
-                   name=f"cfg3_hartmann_{nx}x{ny}")
+                   name=f"hartmann_channel_{nx}x{ny}")
 
 
-def cfg4_batch(seed: int = 7, count: int = 64, steps: int = 5000) -> list[Problem]:
+def batch_lattices(seed: int = 7, count: int = 64, steps: int = 5000) -> list[Problem]:
     """64 independent stretched-grid lattices: long side log-uniform in
     [128, 2048], aspect uniform in [1, 4], beta uniform in [0.5, 3], Re
     log-uniform in [100, 2000]; half cavities, half channels (Poiseuille or
@@ -204,7 +204,7 @@ def cfg4_batch(seed: int = 7, count: int = 64, steps: int = 5000) -> list[Proble
     return out
 
 
-def cfg5_stream(seed: int = 11, count: int = 2000, rate_hz: float = 200.0,
+def serving_trace(seed: int = 11, count: int = 2000, rate_hz: float = 200.0,
                 side_range=(64, 2048)) -> list[dict]:
     """Serving trace: Poisson arrivals (rate 200/s), NSE : NSE+MIE = 1 : 1,
     cavity : channel = 1 : 1 among NSE, square sides log-uniform in [64, 2048],

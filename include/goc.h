@@ -123,6 +123,9 @@ typedef struct {
                                72 steps (choices are cached per lattice size, storage and MIE;
                                every choice gives bitwise the same populations);
                                1 = fixed: dynamic tile queue, dependent launch on */
+    int plateau_checks;     /* goc_run_until also stops once this many successive checks bring
+                               no new smallest residual (the FP32/FP16 rounding floor lies above
+                               the tolerance); 0 = never */
 } goc_exec;
 
 /* ---- lifecycle --------------------------------------------------------- */
@@ -169,8 +172,9 @@ goc_status goc_step(goc_lattice *lat, long long nsteps);
 
 /* Step until the residual R = ||U^n - U^(n-1)||_2 / ||U^n||_2 (max with the
  * B residual when the MIE is on; Sec. 7.3) falls below tol, checking every
- * exec.check_every steps, or max_steps is reached.  *done (may be NULL)
- * receives the steps taken, *residual (may be NULL) the last residual.
+ * exec.check_every steps, or max_steps is reached, or (exec.plateau_checks > 0)
+ * that many checks in a row found no new smallest residual.  *done (may be
+ * NULL) receives the steps taken, *residual (may be NULL) the last residual.
  * Synchronises.  Returns GOC_EDIVERGED on NaN. */
 goc_status goc_run_until(goc_lattice *lat, double tol, long long max_steps,
                          long long *done, double *residual);

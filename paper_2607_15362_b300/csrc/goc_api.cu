@@ -117,6 +117,7 @@ struct goc_lattice {
     // tile queue (dynamic) or static tile order, programmatic dependent launch
     int cfg_dynamic = 1, cfg_pdl = 1;
     bool tuned = false;                          // chosen by the launch autotuner (or fixed)
+    int plateau_checks = 0;                      // goc_exec.plateau_checks
 };
 
 namespace {
@@ -585,6 +586,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         L->rounding = exec->rounding;
         L->scheme = exec->scheme;
         L->tuned = exec->fixed_launch != 0;
+        L->plateau_checks = std::max(0, exec->plateau_checks);
         if (exec->device >= 0) {
             cudaError_t e = cudaSetDevice(exec->device);
             if (e != cudaSuccess) {
@@ -909,8 +911,8 @@ goc_status goc_run_until(goc_lattice *L, double tol, long long max_steps, long l
         }
     }
     long long taken = 0;
-    double R = 1e300;
-    int h_flag = 0;
+    double R = 1e300, best = 1e300;
+    int h_flag = 0, stall = 0;
     const int K = std::max(2, L->check_every);
     while (taken < max_steps) {
         long long chunk = std::min<long long>(K, max_steps - taken);
@@ -936,6 +938,12 @@ goc_status goc_run_until(goc_lattice *L, double tol, long long max_steps, long l
                 return fail(GOC_EDIVERGED, "lattice diverged after %lld steps", L->steps);
             }
             if (R < tol) break;
+            if (R < best) {
+                best = R;
+                stall = 0;
+            } else if (L->plateau_checks > 0 && ++stall >= L->plateau_checks) {
+                break;   // rounding floor above the tolerance
+            }
         } else {
             goc_status st = goc_step(L, chunk);
             if (st != GOC_OK) return st;

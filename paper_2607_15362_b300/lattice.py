@@ -71,7 +71,7 @@ SCHEMES = {"goc": 0, "standard": 1}
 
 
 def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", scheme: str = "goc",
-          fixed_launch: bool = False) -> GocExec:
+          fixed_launch: bool = False, plateau_checks: int = 0) -> GocExec:
     e = GocExec()
     e.storage = _abi.STORAGE[storage]
     e.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
@@ -80,6 +80,7 @@ def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", 
     e.rounding = ROUNDING[rounding]
     e.scheme = SCHEMES[scheme]
     e.fixed_launch = 1 if fixed_launch else 0
+    e.plateau_checks = int(plateau_checks)
     return e
 
 
@@ -88,7 +89,7 @@ class Lattice:
 
     def __init__(self, spec: dict, storage: str = "fp32", stream=None, check_every: int = 100,
                  rounding: str = "stochastic", scheme: str = "goc", fixed_launch: bool = False,
-                 _handle=None, _owner=None):
+                 plateau_checks: int = 0, _handle=None, _owner=None):
         """scheme "standard": the uniform-grid central-moment LBM comparator
         (uniform maps, spec["gi"] = 0, no MIE)."""
         self.spec = spec
@@ -99,7 +100,7 @@ class Lattice:
             self._h = _handle
         else:
             g, m, f, h = structs_from_spec(spec)
-            e = _exec(storage, stream, check_every, rounding, scheme, fixed_launch)
+            e = _exec(storage, stream, check_every, rounding, scheme, fixed_launch, plateau_checks)
             out = ctypes.c_void_p()
             check(lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f),
                                    ctypes.byref(h), ctypes.byref(e), ctypes.byref(out)))

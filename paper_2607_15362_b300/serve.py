@@ -189,6 +189,6 @@ def run_sequential(requests: list[Request], time_scale: float = 1.0, keep_fields
 
 
 def requests_from_trace(trace: list[dict], storage: str = "fp32") -> list[Request]:
-    """Requests from goc_inputs.cfg5_stream entries."""
+    """Requests from goc_inputs.serving_trace entries."""
     return [Request(k, t["arrival_s"], t["problem"], int(t["budget"]), t["tol"], storage)
             for k, t in enumerate(trace)]

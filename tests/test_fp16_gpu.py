@@ -4,7 +4,7 @@ FP64 oracle, with stochastic and with nearest rounding of the stored values.
 Round to nearest loses every per-step change smaller than half a unit in the
 last place of FP16 (11 significant bits), which stalls slowly evolving flows;
 stochastic rounding keeps those changes on average.  Tolerances are about
-twice the errors measured on a B300 (FP16 stochastic: cfg1 8.7e-4, cavity
+twice the errors measured on a B300 (FP16 stochastic: Poiseuille 8.7e-4, cavity
 4.7e-4, Hartmann strip U 2.3e-3 / B1 4.2e-3 after 2000 steps; round to nearest:
 6.8e-3, 8.5e-4, 1.9e-2 / 6.6e-2).
 """
@@ -33,7 +33,7 @@ HARTMANN_STRIP = gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "ta
 
 
 @pytest.mark.parametrize("name,prob,tol_u,tol_b", [
-    ("cfg1", gi.cfg1_poiseuille(), 2e-3, None),
+    ("poiseuille", gi.poiseuille_channel(), 2e-3, None),
     ("cavity", CAVITY, 1.5e-3, None),
     ("hartmann strip", HARTMANN_STRIP, 5e-3, 1e-2),
 ])
@@ -53,9 +53,9 @@ def test_fp16_stochastic_rounding_matches_the_oracle(gpu, name, prob, tol_u, tol
 
 
 def test_stochastic_rounding_beats_nearest_on_a_slow_flow(gpu):
-    """cfg1 after 2000 steps: the body force builds the profile by increments
+    """The 32 x 64 Poiseuille channel after 2000 steps: the body force builds the profile by increments
     far below FP16 resolution; nearest rounding stalls, stochastic does not."""
-    p = gi.cfg1_poiseuille()
+    p = gi.poiseuille_channel()
     spec = spec_of(p)
     o = oracle.Oracle(spec, threads=8)
     o.step(2000)

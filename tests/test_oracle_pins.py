@@ -52,7 +52,7 @@ def test_tanh_map_spans_the_domain_and_cs_rule():
     n = 64
     assert map_position("tanh2", n, np.array([0.0]), beta=1.5)[0] == pytest.approx(0.0, abs=1e-12)
     assert map_position("tanh2", n, np.array([float(n)]), beta=1.5)[0] == pytest.approx(n, rel=1e-14)
-    spec = gi.cfg1_poiseuille().lattice_spec(1.0)
+    spec = gi.poiseuille_channel().lattice_spec(1.0)
     m = oracle.build_metric(spec)
     h_first = 1.5 / math.tanh(1.5) / math.cosh(1.5 * (1 / 64 - 1)) ** 2
     assert m.q() == pytest.approx(min(1.0, h_first), rel=1e-14)
@@ -169,7 +169,7 @@ def test_mass_is_conserved_on_a_stretched_periodic_grid():
 
 
 def test_mass_is_conserved_with_bounce_back_and_a_moving_lid():
-    p = gi.cfg2_cavity(n=12, beta=1.2, Re=50.0, u_lid=0.03)
+    p = gi.lid_cavity(n=12, beta=1.2, Re=50.0, u_lid=0.03)
     o = oracle.Oracle(p.lattice_spec(oracle.build_metric(p.lattice_spec(1.0)).cs2()))
     m0 = o.state()[0].sum()
     o.step(2000)
@@ -316,11 +316,11 @@ def test_transposed_problem_gives_the_transposed_solution():
 
 
 # ---------------------------------------------------------- analytic flows --
-def test_cfg1_poiseuille_follows_the_transient_analytic_series():
-    """cfg1 after 2000 steps from rest against the series solution of the
+def test_poiseuille_channel_follows_the_transient_analytic_series():
+    """The 32 x 64 Poiseuille channel after 2000 steps from rest against the series solution of the
     body-force channel (steady profile of Sec. 7.1 minus its decaying sine
     modes)."""
-    p = gi.cfg1_poiseuille()
+    p = gi.poiseuille_channel()
     cs2 = oracle.build_metric(p.lattice_spec(1.0)).cs2()
     spec = p.lattice_spec(cs2)
     o = oracle.Oracle(spec, threads=4)

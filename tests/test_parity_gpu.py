@@ -28,7 +28,7 @@ def cs2_of(problem):
 
 
 def test_library_cs_rule_matches_the_oracle(gpu):
-    for p in (gi.cfg1_poiseuille(), gi.cfg2_cavity(), gi.cfg3_hartmann()):
+    for p in (gi.poiseuille_channel(), gi.lid_cavity(), gi.hartmann_channel()):
         spec = p.lattice_spec(1.0)
         q, cs2 = goc.metric_info(spec)
         m = oracle.build_metric(spec)
@@ -36,10 +36,10 @@ def test_library_cs_rule_matches_the_oracle(gpu):
         assert cs2 == pytest.approx(m.cs2(), rel=1e-14)
 
 
-def test_cfg1_poiseuille_fp32_matches_the_oracle(gpu):
-    """cfg1 (32 x 64, tanh beta = 1.5, Re = 10): FP32 velocity relative L2
+def test_poiseuille_channel_fp32_matches_the_oracle(gpu):
+    """Poiseuille channel (32 x 64, tanh beta = 1.5, Re = 10): FP32 velocity relative L2
     <= 1e-5 after 1000 and after 2000 steps."""
-    p = gi.cfg1_poiseuille()
+    p = gi.poiseuille_channel()
     spec = p.lattice_spec(cs2_of(p))
     o = oracle.Oracle(spec, threads=8)
     L = goc.Lattice(spec)
@@ -106,7 +106,7 @@ def test_mass_is_conserved_on_the_gpu(gpu):
 
 
 def test_checkpoint_restore_is_bitwise(gpu):
-    p = gi.cfg1_poiseuille()
+    p = gi.poiseuille_channel()
     spec = p.lattice_spec(cs2_of(p))
     a = goc.Lattice(spec)
     a.step(150)
@@ -122,7 +122,7 @@ def test_checkpoint_restore_is_bitwise(gpu):
 
 def _mixed_specs():
     out = []
-    for prob in (gi.cfg1_poiseuille(),
+    for prob in (gi.poiseuille_channel(),
                  gi.Problem("cavity", 37, 29, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
                             {"Re": 100.0, "u_lid": 0.05}),
                  gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
@@ -161,7 +161,7 @@ def test_batch_admission_respects_the_hbm_budget(gpu):
     specs = _mixed_specs()
     batch = goc.Batch(hbm_budget_bytes=200_000, max_lattices=8)
     assert batch.try_add(specs[0]) is not None      # 32 x 64 fits
-    assert batch.try_add(gi.cfg2_cavity().lattice_spec(0.007)) is None   # 512^2 does not
+    assert batch.try_add(gi.lid_cavity().lattice_spec(0.007)) is None   # 512^2 does not
     batch.close()
 
 

@@ -81,7 +81,7 @@ def test_standard_equals_the_goc_kernel_at_unit_metric(gpu):
 
 
 def test_standard_scheme_moves_fewer_bytes(gpu):
-    prob = gi.cfg2_uniform_comparator(n=64)
+    prob = gi.uniform_cavity(n=64)
     spec = uniform_spec(prob)
     A = goc.Lattice(spec, scheme="standard")
     assert A.bytes_per_node == 72.0

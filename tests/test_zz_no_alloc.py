@@ -28,7 +28,7 @@ def _lattice(prob, storage="fp32"):
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 def test_noalloc_mass_matches_diagnostics_twice(gpu, storage):
-    for prob in (gi.cfg1_poiseuille(),
+    for prob in (gi.poiseuille_channel(),
                  gi.Problem("cavity", 300, 211, {"kind": "tanh2", "beta": 1.5}, {"kind": "tanh2", "beta": 1.5},
                             {"Re": 400.0, "u_lid": 0.05, "mach_matched": True})):
         lat = _lattice(prob, storage)
