@@ -629,9 +629,12 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
 // Each thread pulls its RPT nodes (column i0 + tx, rows ty + r TYT) into
 // registers (kept across the barrier for the collision); the ring of halo
 // nodes around the tile is shared out over the threads.  Contains a block
-// barrier: every thread of the block must call it.
+// barrier: every thread of the block must call it.  ok: this thread's wait
+// for the staged copy succeeded; false (returned by every thread) when any
+// thread's wait failed -- the block then leaves.
 template <class S, bool MHD, int KIND, class Src>
-__device__ __forceinline__ void tile_compute(const StepParams &p, const Src &src, int i0, int j0, FieldSmem &sm) {
+__device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src, int i0, int j0, FieldSmem &sm,
+                                             bool ok) {
     constexpr bool CHECKS = KIND != 0;
     constexpr int W = KIND == 0 ? 1 : MH;                 // halo width of the fields
     constexpr int BAND = W * (TX + 2 * W);                // nodes in the top (or bottom) band
@@ -686,8 +689,9 @@ __device__ __forceinline__ void tile_compute(const StepParams &p, const Src &src
         sm.u1[ty[r] + MH][tx + MH] = U1;
         sm.u2[ty[r] + MH][tx + MH] = U2;
     }
-    // halo ring: top band, bottom band, left band, right band
-    for (int q = tid; q < RING; q += NT) {
+    // halo ring: top band, bottom band, left band, right band (taken from the
+    // last warp down: warp 0 also stages the next tile)
+    for (int q = NT - 1 - tid; q < RING; q += NT) {
         int x, y;
         if (q < 2 * BAND) {
             const int b = q < BAND ? q : q - BAND;
@@ -721,11 +725,12 @@ __device__ __forceinline__ void tile_compute(const StepParams &p, const Src &src
         sm.u1[y + MH][x + MH] = U1;
         sm.u2[y + MH][x + MH] = U2;
     }
-    __syncthreads();
+    if (!__syncthreads_and(ok)) return false;
     bool any = false;
 #pragma unroll
     for (int r = 0; r < R; r++) any = any || own[r];
     if (any) node_update<S, MHD, CHECKS, V>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
+    return true;
 }
 
 // Kind of a tile: 0 interior (all pull sources of the tile and its fields
@@ -763,20 +768,19 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *m) {
 }
 
 template <class S, bool MHD>
-__device__ __forceinline__ void run_tile(const StepParams &p, int kind, int i0, int j0, const unsigned char *stage,
-                                         FieldSmem &sm) {
+__device__ __forceinline__ bool run_tile(const StepParams &p, int kind, int i0, int j0, const unsigned char *stage,
+                                         FieldSmem &sm, bool ok) {
     using T = Tiling<S>;
     if (kind == 2) {
         SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                          p.plane, p.pitch, p.sf, p.sF, p.sg};
-        tile_compute<S, MHD, 1>(p, src, i0, j0, sm);
-    } else {
-        SrcSmem<S> src{reinterpret_cast<const S *>(stage), reinterpret_cast<const S *>(stage + T::OFF_FF),
-                       reinterpret_cast<const S *>(stage + T::OFF_G), i0 - T::HXS, j0 - HYS, j0 - 1,
-                       p.sf, p.sF, p.sg};
-        if (kind == 0) tile_compute<S, MHD, 0>(p, src, i0, j0, sm);
-        else tile_compute<S, MHD, 1>(p, src, i0, j0, sm);
+        return tile_compute<S, MHD, 1>(p, src, i0, j0, sm, ok);
     }
+    SrcSmem<S> src{reinterpret_cast<const S *>(stage), reinterpret_cast<const S *>(stage + T::OFF_FF),
+                   reinterpret_cast<const S *>(stage + T::OFF_G), i0 - T::HXS, j0 - HYS, j0 - 1,
+                   p.sf, p.sF, p.sg};
+    if (kind == 0) return tile_compute<S, MHD, 0>(p, src, i0, j0, sm, ok);
+    return tile_compute<S, MHD, 1>(p, src, i0, j0, sm, ok);
 }
 
 // The tiles of one lattice processed by one block with TMA staging in two
@@ -806,7 +810,16 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
         }
         s_item[st] = it;
     };
-    if (leader) take(0, first);
+    // leader, dynamic queue, NSE: the counter value of the item after the
+    // next one is fetched one tile ahead, so the atomic's round trip overlaps
+    // a tile.  With the MIE (fewer, longer tiles per block) the reservation
+    // would hold back an item a faster block could take.
+    constexpr bool AHEAD = !MHD;
+    int pend = 0;
+    if (leader) {
+        if (ctr && AHEAD) pend = atomicAdd(ctr, 1);
+        take(0, first);
+    }
     __syncthreads();
     uint32_t ph0 = 0, ph1 = 0;
     int stage = 0;
@@ -814,15 +827,27 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
         const int4 it = s_item[stage];
         const int t = it.x;
         if (t >= ntiles) break;   // uniform: every thread reads the same shared value
-        if (leader) take(stage ^ 1, ctr ? stride + atomicAdd(ctr, 1) : t + stride);
+        if (leader) {
+            int nt = t + stride;
+            if (ctr && AHEAD) {
+                nt = stride + pend;
+                pend = atomicAdd(ctr, 1);
+            } else if (ctr) {
+                nt = stride + atomicAdd(ctr, 1);
+            }
+            take(stage ^ 1, nt);
+        }
         const int i0 = it.y, j0 = it.z, kind = it.w;
+        bool ok = true;   // every thread waits for the copy itself; the fields barrier gathers the outcome
         if (kind != 2) {
             uint32_t &ph = stage ? ph1 : ph0;
-            const bool ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
-            if (!__syncthreads_and(ok)) return;   // the whole block leaves together on a timeout
+            ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
             ph ^= 1;
         }
-        run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm);
+        if (MHD) {   // with the MIE the block gathers after the copy (measured faster there)
+            if (!__syncthreads_and(ok)) return;
+        }
+        if (!run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
         __syncthreads();   // the stage, the field arrays and s_item are reused by the next tile
         stage ^= 1;
     }
@@ -918,8 +943,11 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
         }
         s_item[st] = it;
     };
+    constexpr bool AHEAD = !MHD;   // as in the single-lattice kernel
+    int pend = 0;   // leader: counter value of the item after the next one (fetched one tile ahead)
     if (leader) {
         if (blockIdx.x == 0) a.ctr[a.parity ^ 1] = 0;   // the next step's counter
+        if (AHEAD) pend = atomicAdd(&a.ctr[a.parity], 1);
         take(0, blockIdx.x);
     }
     __syncthreads();
@@ -928,16 +956,28 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
     for (;;) {
         const int4 it = s_item[stage];
         if (it.x >= items) break;   // uniform: every thread reads the same shared value
-        if (leader) take(stage ^ 1, (int)gridDim.x + atomicAdd(&a.ctr[a.parity], 1));
+        if (leader) {
+            int nt;
+            if (AHEAD) {
+                nt = (int)gridDim.x + pend;
+                pend = atomicAdd(&a.ctr[a.parity], 1);
+            } else {
+                nt = (int)gridDim.x + atomicAdd(&a.ctr[a.parity], 1);
+            }
+            take(stage ^ 1, nt);
+        }
         const int k = it.w >> 2, kind = it.w & 3, i0 = it.y, j0 = it.z;
         const StepParams &p = a.p[k];
+        bool ok = true;   // every thread waits for the copy itself; the fields barrier gathers the outcome
         if (kind != 2) {
             uint32_t &ph = stage ? ph1 : ph0;
-            const bool ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
-            if (!__syncthreads_and(ok)) return;   // the whole block leaves together on a timeout
+            ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
             ph ^= 1;
         }
-        run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm);
+        if (MHD) {
+            if (!__syncthreads_and(ok)) return;
+        }
+        if (!run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
         __syncthreads();   // the stage, the field arrays and s_item are reused
         stage ^= 1;
     }
