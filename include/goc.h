@@ -59,8 +59,17 @@ typedef enum { GOC_BC_PERIODIC = 0, GOC_BC_WALL = 1 } goc_bc;
  *           Eq. metriccoefficient (Sec. 6.1): x = (N/2)[1 + tanh(beta(2 eta-1))/tanh beta].
  *  SINE     periodic stretching x = xi + (a N/2pi) sin(2 pi xi/N) (|a| < 1).
  *  ROBERTS  Roberts boundary-layer map, Eq. y_Roberts / Eq. h2_Roberts
- *           (Sec. 6.2), lambda = (gamma+1)/(gamma-1). */
-typedef enum { GOC_MAP_UNIFORM = 0, GOC_MAP_TANH2 = 1, GOC_MAP_SINE = 2, GOC_MAP_ROBERTS = 3 } goc_map_kind;
+ *           (Sec. 6.2), lambda = (gamma+1)/(gamma-1).
+ *  TANH1    clustering at the wall xi = 0 only, Eq. hypertanh_transformation /
+ *           Eq. metriccoefficientB (Sec. 6.3) with the prefactor N (the printed
+ *           N/2 maps onto half the domain): x = N[1 - tanh(beta(1 - eta))/tanh beta].
+ *  SINH     clustering around an interior point x_c = yc N, Eq. Holst_transformation,
+ *           Eq. B_Holst, Eq. h_2_Holst (Sec. 6.4):
+ *           x = x_c [1 + sinh(mu(eta - B))/sinh(mu B)].
+ * Wall maps (TANH2 with beta > 0, ROBERTS, TANH1, SINH) need a wall axis; SINE a
+ * periodic one. */
+typedef enum { GOC_MAP_UNIFORM = 0, GOC_MAP_TANH2 = 1, GOC_MAP_SINE = 2, GOC_MAP_ROBERTS = 3,
+               GOC_MAP_TANH1 = 4, GOC_MAP_SINH = 5 } goc_map_kind;
 
 typedef struct {
     int nx, ny;             /* nodes along xi1, xi2; >= 3 along a wall axis, >= 1 otherwise */
@@ -73,10 +82,12 @@ typedef struct {
 
 typedef struct {
     int kind[2];            /* goc_map_kind for xi1, xi2 */
-    double beta[2];         /* TANH2 clustering parameter (0 = uniform) */
+    double beta[2];         /* TANH2 clustering parameter (0 = uniform); TANH1 (> 0) */
     double a[2];            /* SINE amplitude */
     double gamma[2];        /* ROBERTS gamma (> 1) */
     double alpha[2];        /* ROBERTS alpha (0 or 1/2) */
+    double mu[2];           /* SINH clustering strength (> 0) */
+    double yc[2];           /* SINH clustering point as a fraction of the axis length, in (0, 1) */
 } goc_map;
 
 typedef struct {

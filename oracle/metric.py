@@ -30,6 +30,19 @@ Maps (Sec. 6):
   Sec. 6.2) with lambda = (gamma + 1)/(gamma - 1) (the printed
   (gamma+1)/(gamma+1) is garbled; only this reading gives y(0) = 0 and the
   printed h2).  Cell-centred nodes as above with L = N.
+* ``tanh1``: clustering at the wall xi = 0 only (Eq. hypertanh_transformation,
+  Eq. metriccoefficientB, Sec. 6.3).  The printed prefactor L_y/2 would map
+  onto [0, L/2]; the printed h2 and theta22 belong to the prefactor L, so
+  x = N [1 - tanh(beta (1 - eta)) / tanh(beta)],
+  h = (beta / tanh beta) sech^2(beta (1 - eta)),
+  theta = (2 tanh(beta) / N) tanh(beta (1 - eta)) / sech^2(beta (1 - eta)).
+* ``sinh``: clustering around an interior point x_c = yc N (Eq.
+  Holst_transformation, Eq. B_Holst, Eq. h_2_Holst, Sec. 6.4), the printed
+  "sinh ]" read as sinh[...]:
+  B = ln[(1 + (e^mu - 1) yc) / (1 + (e^-mu - 1) yc)] / (2 mu),
+  x = x_c [1 + sinh(mu (eta - B)) / sinh(mu B)],
+  h = (x_c / N) mu cosh(mu (eta - B)) / sinh(mu B),
+  theta = (sinh(mu B) / x_c) tanh(mu (eta - B)) sech(mu (eta - B)).
 
 Periodic axes place nodes at eta_i = i / N.
 """
@@ -45,8 +58,14 @@ def _eta(n: int, periodic: bool) -> np.ndarray:
     return j / n if periodic else (j + 0.5) / n
 
 
+def _holst_b(mu: float, yc: float) -> float:
+    """B of the interior map (Eq. B_Holst) for x_c / L = yc."""
+    return math.log((1.0 + (math.exp(mu) - 1.0) * yc) / (1.0 + (math.exp(-mu) - 1.0) * yc)) / (2.0 * mu)
+
+
 def map_position(kind: str, n: int, xi: np.ndarray, *, beta: float = 0.0,
-                 a: float = 0.0, gamma: float = 0.0, alpha: float = 0.5) -> np.ndarray:
+                 a: float = 0.0, gamma: float = 0.0, alpha: float = 0.5,
+                 mu: float = 0.0, yc: float = 0.5) -> np.ndarray:
     """Physical coordinate x(xi) of the named map, xi in [0, n] (lattice units)."""
     xi = np.asarray(xi, dtype=np.float64)
     if kind == "uniform" or (kind == "tanh2" and beta == 0.0):
@@ -61,11 +80,17 @@ def map_position(kind: str, n: int, xi: np.ndarray, *, beta: float = 0.0,
         s = (xi / n - alpha) / (1.0 - alpha)
         ls = lam ** s
         return n * ((gamma + 2 * alpha) * ls - gamma + 2 * alpha) / ((2 * alpha + 1) * (1 + ls))
+    if kind == "tanh1":
+        return n * (1.0 - np.tanh(beta * (1.0 - xi / n)) / math.tanh(beta))
+    if kind == "sinh":
+        B = _holst_b(mu, yc)
+        return yc * n * (1.0 + np.sinh(mu * (xi / n - B)) / math.sinh(mu * B))
     raise ValueError(f"unknown map {kind!r}")
 
 
 def map_metric(kind: str, n: int, xi: np.ndarray, *, beta: float = 0.0,
-               a: float = 0.0, gamma: float = 0.0, alpha: float = 0.5):
+               a: float = 0.0, gamma: float = 0.0, alpha: float = 0.5,
+               mu: float = 0.0, yc: float = 0.5):
     """Analytic (h, theta) of the named map at the points xi."""
     xi = np.asarray(xi, dtype=np.float64)
     if kind == "uniform" or (kind == "tanh2" and beta == 0.0):
@@ -87,6 +112,18 @@ def map_metric(kind: str, n: int, xi: np.ndarray, *, beta: float = 0.0,
         ls = lam ** s
         h = (2.0 * gamma / (2 * alpha + 1)) * math.log(lam) / (1.0 - alpha) * ls / (1.0 + ls) ** 2
         theta = (1.0 / n) * ((1.0 + 2 * alpha) / (2.0 * gamma)) * (1.0 / ls - ls)
+        return h, theta
+    if kind == "tanh1":
+        arg = beta * (1.0 - xi / n)
+        sech2 = 1.0 / np.cosh(arg) ** 2
+        h = beta / math.tanh(beta) * sech2
+        theta = (2.0 * math.tanh(beta) / n) * np.tanh(arg) / sech2
+        return h, theta
+    if kind == "sinh":
+        B = _holst_b(mu, yc)
+        arg = mu * (xi / n - B)
+        h = yc * mu * np.cosh(arg) / math.sinh(mu * B)
+        theta = math.sinh(mu * B) / (yc * n) * np.tanh(arg) / np.cosh(arg)
         return h, theta
     raise ValueError(f"unknown map {kind!r}")
 

@@ -368,10 +368,16 @@ goc_status validate(const goc_grid *grid, const goc_map *map) {
     if (grid->bc[2] == GOC_BC_WALL && grid->ny < 3) return fail(GOC_EINVAL, "a wall axis needs >= 3 nodes");
     for (int a = 0; a < 2; a++) {
         int k = map->kind[a];
-        if (k < 0 || k > 3) return fail(GOC_EINVAL, "map kind[%d] = %d unknown", a, k);
+        if (k < 0 || k > 5) return fail(GOC_EINVAL, "map kind[%d] = %d unknown", a, k);
         int per = grid->bc[a == 0 ? 0 : 2] == GOC_BC_PERIODIC;
-        if ((k == GOC_MAP_TANH2 || k == GOC_MAP_ROBERTS) && per && !(k == GOC_MAP_TANH2 && map->beta[a] == 0.0))
-            return fail(GOC_EINVAL, "axis %d: wall-clustering map on a periodic axis", a);
+        const bool wall_map = k == GOC_MAP_ROBERTS || k == GOC_MAP_TANH1 || k == GOC_MAP_SINH ||
+                              (k == GOC_MAP_TANH2 && map->beta[a] != 0.0);
+        if (wall_map && per) return fail(GOC_EINVAL, "axis %d: wall-clustering map on a periodic axis", a);
+        if (k == GOC_MAP_TANH1 && !(map->beta[a] > 0.0)) return fail(GOC_EINVAL, "one-wall tanh beta must be > 0");
+        if (k == GOC_MAP_SINH && !(map->mu[a] > 0.0 && map->mu[a] <= 50.0))
+            return fail(GOC_EINVAL, "interior-map mu must be in (0, 50]");
+        if (k == GOC_MAP_SINH && !(map->yc[a] > 0.0 && map->yc[a] < 1.0))
+            return fail(GOC_EINVAL, "interior-map yc must be in (0, 1)");
         if (k == GOC_MAP_SINE && !per) return fail(GOC_EINVAL, "axis %d: sine map needs a periodic axis", a);
         if (k == GOC_MAP_SINE && !(std::fabs(map->a[a]) < 1.0)) return fail(GOC_EINVAL, "sine amplitude must be < 1");
         if (k == GOC_MAP_TANH2 && !(map->beta[a] >= 0.0)) return fail(GOC_EINVAL, "beta must be >= 0");
@@ -391,6 +397,8 @@ MapParams map_params(const goc_grid *grid, const goc_map *map, int axis) {
     m.a = map->a[axis];
     m.gamma = map->gamma[axis];
     m.alpha = map->alpha[axis];
+    m.mu = map->mu[axis];
+    m.yc = map->yc[axis];
     return m;
 }
 

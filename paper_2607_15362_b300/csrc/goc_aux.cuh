@@ -11,9 +11,9 @@ namespace goc {
 // Eq. curvaturematrix).  Entries 0..n-1 are the nodes, n and n+1 the walls
 // at xi = 0 and xi = n.
 struct MapParams {
-    int kind;          // 0 uniform, 1 tanh2, 2 sine, 3 roberts
+    int kind;          // 0 uniform, 1 tanh2, 2 sine, 3 roberts, 4 tanh1 (one wall), 5 sinh (interior)
     int n, periodic;
-    double beta, a, gamma, alpha;
+    double beta, a, gamma, alpha, mu, yc;
 };
 
 __device__ void map_h_theta(const MapParams &m, double xi, double &h, double &th) {
@@ -31,6 +31,17 @@ __device__ void map_h_theta(const MapParams &m, double xi, double &h, double &th
         const double ph = 2.0 * 3.14159265358979323846 * xi / n;
         h = 1.0 + m.a * cos(ph);
         th = -m.a * (2.0 * 3.14159265358979323846 / n) * sin(ph) / (h * h);
+    } else if (m.kind == 4) {   // one wall (Eq. metriccoefficientB), clustered at xi = 0
+        const double arg = m.beta * (1.0 - xi / n);
+        const double ch = cosh(arg);
+        const double sech2 = 1.0 / (ch * ch);
+        h = m.beta / tanh(m.beta) * sech2;
+        th = (2.0 * tanh(m.beta) / n) * tanh(arg) / sech2;
+    } else if (m.kind == 5) {   // interior point (Eq. B_Holst, Eq. h_2_Holst)
+        const double B = log((1.0 + (exp(m.mu) - 1.0) * m.yc) / (1.0 + (exp(-m.mu) - 1.0) * m.yc)) / (2.0 * m.mu);
+        const double arg = m.mu * (xi / n - B), smb = sinh(m.mu * B), ch = cosh(arg);
+        h = m.yc * m.mu * ch / smb;
+        th = smb / (m.yc * n) * tanh(arg) / ch;
     } else {                    // Roberts (Eq. h2_Roberts), lambda = (gamma+1)/(gamma-1)
         const double lam = (m.gamma + 1.0) / (m.gamma - 1.0);
         const double s = (xi / n - m.alpha) / (1.0 - m.alpha);

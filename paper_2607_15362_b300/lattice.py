@@ -37,6 +37,8 @@ def structs_from_spec(spec: dict):
         m.a[ax] = float(mp.get("a", 0.0))
         m.gamma[ax] = float(mp.get("gamma", 0.0))
         m.alpha[ax] = float(mp.get("alpha", 0.5))
+        m.mu[ax] = float(mp.get("mu", 0.0))
+        m.yc[ax] = float(mp.get("yc", 0.5))
     f = GocFlow()
     f.rho0 = float(spec.get("rho0", 1.0))
     f.tau = float(spec.get("tau", 1.0)) if spec.get("tau") is not None else 1.0

@@ -31,7 +31,9 @@ def _periodic_spec(nx=6, ny=5, **kw):
 
 # ---------------------------------------------------------------- metric ---
 @pytest.mark.parametrize("kind,kw", [("tanh2", {"beta": 1.5}), ("tanh2", {"beta": 3.0}),
-                                     ("sine", {"a": 0.4}), ("roberts", {"gamma": 1.06, "alpha": 0.5})])
+                                     ("sine", {"a": 0.4}), ("roberts", {"gamma": 1.06, "alpha": 0.5}),
+                                     ("roberts", {"gamma": 1.2, "alpha": 0.0}), ("tanh1", {"beta": 2.0}),
+                                     ("sinh", {"mu": 4.0, "yc": 0.3}), ("sinh", {"mu": 2.5, "yc": 0.6})])
 def test_metric_matches_finite_differences_of_the_map(kind, kw):
     """h = dx/dxi (Eq. metricfactor) and theta = h'/h^2 (Eq. curvaturematrix)
     against centred finite differences of the map itself (Sec. 6)."""
@@ -44,6 +46,33 @@ def test_metric_matches_finite_differences_of_the_map(kind, kw):
     hp, _ = map_metric(kind, n, xi + eps, **kw)
     hm, _ = map_metric(kind, n, xi - eps, **kw)
     np.testing.assert_allclose(th, (hp - hm) / (2 * eps) / h ** 2, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind,kw,dense", [("tanh2", {"beta": 2.0}, "both"), ("roberts", {"gamma": 1.05, "alpha": 0.5}, "both"),
+                                           ("roberts", {"gamma": 1.1, "alpha": 0.0}, "end"),
+                                           ("tanh1", {"beta": 2.0}, "start"), ("sinh", {"mu": 4.0, "yc": 0.3}, 0.3)])
+def test_wall_maps_span_the_domain_and_cluster_where_stated(kind, kw, dense):
+    """Every wall map sends xi = 0 and xi = N to the walls y = 0 and y = N, is
+    increasing, and is finest where Sec. 6 says: at both walls (tanh2,
+    Roberts alpha = 1/2), at y = L only (Roberts alpha = 0), at y = 0 only
+    (one-wall tanh, Sec. 6.3), around y_c (interior map, Sec. 6.4)."""
+    n = 80
+    ends = map_position(kind, n, np.array([0.0, float(n)]), **kw)
+    assert ends[0] == pytest.approx(0.0, abs=1e-11)
+    assert ends[1] == pytest.approx(n, rel=1e-12)
+    xi = (np.arange(n) + 0.5)
+    y = map_position(kind, n, xi, **kw)
+    assert np.all(np.diff(y) > 0)
+    h, _ = map_metric(kind, n, xi, **kw)
+    k = int(np.argmin(h))
+    if dense == "both":
+        assert k in (0, n - 1) and h[0] == pytest.approx(h[-1], rel=1e-12)
+    elif dense == "start":
+        assert k == 0 and h[-1] > 2 * h[0]
+    elif dense == "end":
+        assert k == n - 1 and h[0] > 2 * h[-1]
+    else:
+        assert abs(y[k] - dense * n) <= 1.0 and h[0] > 2 * h[k] and h[-1] > 2 * h[k]
 
 
 def test_tanh_map_spans_the_domain_and_cs_rule():
@@ -336,13 +365,14 @@ def test_poiseuille_channel_follows_the_transient_analytic_series():
         assert np.linalg.norm(u1[:, i] - ut) / np.linalg.norm(ut) < 2e-3
 
 
-def _steady_poiseuille_error(ny, beta=1.5, tau=0.8):
-    p = gi.Problem("poiseuille", 1, ny, {"kind": "uniform"}, {"kind": "tanh2", "beta": beta},
-                   {"Re": 10.0, "tau": tau})
+def _steady_poiseuille_error(ny, beta=1.5, tau=0.8, map2=None):
+    map2 = map2 or {"kind": "tanh2", "beta": beta}
+    p = gi.Problem("poiseuille", 1, ny, {"kind": "uniform"}, map2, {"Re": 10.0, "tau": tau})
     cs2 = oracle.build_metric(p.lattice_spec(1.0)).cs2()
     spec = p.lattice_spec(cs2)
     d = spec["derived"]
-    s = map_position("tanh2", ny, np.arange(ny) + 0.5, beta=beta) / d["H"]
+    mp = dict(map2)
+    s = map_position(mp.pop("kind"), ny, np.arange(ny) + 0.5, **mp) / d["H"]
     ua = 4 * d["U"] * s * (1 - s)
     spec["init"] = {"u1": np.repeat(ua[:, None], 1, axis=1), "u2": 0.0}
     o = oracle.Oracle(spec)
@@ -356,6 +386,49 @@ def test_steady_poiseuille_converges_at_second_order():
     orders = [math.log2(e[k] / e[k + 1]) for k in range(2)]
     assert e[-1] < 2e-3
     assert min(orders) > 1.8, (e, orders)
+
+
+@pytest.mark.parametrize("map2", [{"kind": "tanh1", "beta": 1.0}, {"kind": "sinh", "mu": 3.0, "yc": 0.4}])
+def test_steady_poiseuille_converges_on_the_one_wall_and_interior_maps(map2):
+    """The body-force channel on the one-wall tanh map (Sec. 6.3) and the
+    interior-point map (Sec. 6.4): the steady profile of Sec. 7.1 is reached
+    with second-order convergence."""
+    e = [_steady_poiseuille_error(n, map2=map2) for n in (16, 32, 64)]
+    orders = [math.log2(e[k] / e[k + 1]) for k in range(2)]
+    assert e[-1] < 2e-3
+    assert min(orders) > 1.8, (e, orders)
+
+
+def _couette_errors(ny, U=0.02, tau=1.0, fracs=(0.01, 0.05, 0.2)):
+    """Relative L2 distance of the shear-driven channel started from rest to
+    the series solution of Sec. 7.2 at the times t = f H^2 / nu."""
+    m2 = {"kind": "roberts", "gamma": 1.06, "alpha": 0.5}
+    p = gi.Problem("couette", 1, ny, {"kind": "uniform"}, m2, {"tau": tau, "u_wall": U})
+    cs2 = oracle.build_metric(p.lattice_spec(1.0)).cs2()
+    o = oracle.Oracle(p.lattice_spec(cs2))
+    nu, H = cs2 * (tau - 0.5), float(ny)
+    y = map_position("roberts", ny, np.arange(ny) + 0.5, gamma=1.06, alpha=0.5)
+    errs = []
+    for f in fracs:
+        o.step(int(round(f * H * H / nu)) - o.steps_done)
+        _, u1, *_ = o.fields()
+        t = o.steps_done
+        ua = U * y / H
+        for n in range(1, 4000):
+            ua -= 2 * U / (math.pi * n) * math.exp(-(n * math.pi) ** 2 * nu * t / H ** 2) * np.sin(n * math.pi * (1 - y / H))
+        errs.append(np.linalg.norm(u1[:, 0] - ua) / np.linalg.norm(ua))
+    return np.array(errs)
+
+
+def test_transient_couette_follows_the_series_at_second_order():
+    """Transient Couette flow (Sec. 7.2): fluid at rest, top wall moving at U
+    = 0.02 (momentum-augmented bounce-back with the wall metric factor, Eq.
+    101), Roberts clustering gamma = 1.06 at both walls, tau = 1.  Against
+    the printed series solution at three times the error is small and falls
+    at second order from 25 to 50 rows (the paper's grid has 50)."""
+    e25, e50 = _couette_errors(25), _couette_errors(50)
+    assert np.all(e50 < 4e-3), e50
+    assert np.all(np.log2(e25 / e50) > 1.7), (e25, e50)
 
 
 def _tg_rate(n, a):

@@ -52,6 +52,51 @@ def test_poiseuille_channel_fp32_matches_the_oracle(gpu):
         assert np.abs(rg - ro).max() <= 1e-6
 
 
+def test_library_metric_of_every_wall_map_matches_the_oracle(gpu):
+    """q and c_s^2 from the library's FP64 metric kernel for the one-wall
+    tanh map (Sec. 6.3), the interior-point map (Sec. 6.4) and the Roberts
+    map on either axis, against the oracle's numpy metric."""
+    maps = [{"kind": "tanh1", "beta": 2.0}, {"kind": "sinh", "mu": 4.0, "yc": 0.3},
+            {"kind": "roberts", "gamma": 1.05, "alpha": 0.5}, {"kind": "roberts", "gamma": 1.2, "alpha": 0.0}]
+    for m in maps:
+        for prob in (gi.Problem("poiseuille", 8, 77, {"kind": "uniform"}, m, {"Re": 10.0, "tau": 0.8}),
+                     gi.Problem("cavity", 77, 40, m, {"kind": "tanh2", "beta": 0.5}, {"Re": 10.0, "u_lid": 0.01})):
+            spec = prob.lattice_spec(1.0)
+            q, cs2 = goc.metric_info(spec)
+            mo = oracle.build_metric(spec)
+            assert q == pytest.approx(mo.q(), rel=1e-13)
+            assert cs2 == pytest.approx(mo.cs2(), rel=1e-13)
+
+
+@pytest.mark.parametrize("map2", [{"kind": "tanh1", "beta": 1.5}, {"kind": "sinh", "mu": 4.0, "yc": 0.3}])
+def test_one_wall_and_interior_maps_fp32_match_the_oracle(gpu, map2):
+    """Body-force channel (37 x 70) on the one-wall tanh map and on the
+    interior-point map: FP32 velocity relative L2 <= 1e-5 after 1000 steps."""
+    prob = gi.Problem("poiseuille", 37, 70, {"kind": "uniform"}, map2, {"Re": 10.0, "tau": 0.8})
+    spec = prob.lattice_spec(cs2_of(prob))
+    o, L, fo, fg = run_pair(spec, 1000)
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+
+
+def test_transient_couette_fp32_matches_the_oracle(gpu):
+    """Shear-driven channel of Sec. 7.2 on its 6 x 50 grid (Roberts gamma =
+    1.06, tau = 1, top wall at U = 0.02, from rest): FP32 velocity relative
+    L2 <= 1e-5 against the oracle after 3125 and 15625 steps (t = 0.01 and
+    0.05 H^2/nu)."""
+    prob = gi.Problem("couette", 6, 50, {"kind": "uniform"}, {"kind": "roberts", "gamma": 1.06, "alpha": 0.5},
+                      {"tau": 1.0, "u_wall": 0.02})
+    spec = prob.lattice_spec(cs2_of(prob))
+    o = oracle.Oracle(spec, threads=8)
+    L = goc.Lattice(spec)
+    for n in (3125, 12500):
+        o.step(n)
+        L.step(n)
+        fo, fg = o.fields(), L.moments()
+        assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+        assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+
+
 @pytest.mark.parametrize("nx,ny", [(16, 12), (37, 29), (64, 48)])
 def test_cavity_fp32_matches_the_oracle_on_ragged_tiles(gpu, nx, ny):
     """Walls on all sides, moving lid, tanh clustering on both axes; sizes that
