@@ -26,6 +26,11 @@
  *   Step 4: m~ = F(-U) m~^c.   Step 5: f~ = P^-1 m~.
  *   Step 6: streaming with boundary conditions (half-way bounce-back,
  *     momentum-augmented moving wall, Eq. 101/103; MIE anti-bounce-back).
+ *   Alternative Steps 1-5 (Appendix F, orc_set_srt): the SRT collision in
+ *     velocity space, f~ = f + (f^eq - f)/tau + (1 - 1/(2 tau)) S with f^eq and S
+ *     from the raw moments of Eq. 14D / Eq. 14D-source through the printed
+ *     expansions of Q^-1 (Eq. feqGOCLBE, Eq. SGOCLBE); stresses and force as
+ *     above with zeta = nu.
  *   App. G Steps 1-3: local dB (Eqs. gradB1/gradB2), equilibria
  *     (Eq. EDF-MIE-base + Eq. 42_C), SRT collision (Eq. 12_C) with source
  *     S = -W Y (Eq. 8a_C); current density (Eq. currentdensity-GOC).
@@ -86,6 +91,7 @@ typedef struct {
     int gi;               /* 1: full corrections of Eqs. 83/85; 0: cubic GI terms dropped */
     int q3_printed;       /* 1: use the printed q21/q12 signs */
     int mhd;
+    int srt;              /* 1: the SRT collision in velocity space (Appendix F) */
     double csm2, taum, eta, mum;
     /* state */
     double *f, *ft;       /* populations (post-streaming) and post-collision */
@@ -352,6 +358,65 @@ static void raw_equilibria(const orc_t *o, double rho, double U1, double U2,
     m[8] = rho * cs2 * cs2 + rho * cs2 * (U1 * U1 + U2 * U2) + rho * U1 * U1 * U2 * U2;
 }
 
+/* ---- SRT GOC-LBM (Appendix F, "GOC-LBM Based on Collisions in Velocity
+ * Space and SRT") ---------------------------------------------------------- */
+
+/* Raw-moment equilibria of Eq. 14D in the bare order: the base equilibria
+ * with the bare second-moment corrections G_j (Eq. 5D) and H_j (Eq. 6D),
+ * written for zeta = nu.  Readings: H_2 carries h1/h2^2 (the printed h1/h1^2
+ * is garbled: H_2 = (D_32 - D_42)/2); the density-gradient coefficients are
+ * taken from the appendix's definition G_j = (D_3j + D_4j)/2, H_j = (D_3j -
+ * D_4j)/2, which keeps the U^2/c_s^2 parts of D_33, D_43, D_34, D_44: G_3 =
+ * -nu[(3 - U1^2/cs2) h2/h1^2 - h2/cs2] U1, G_4 = nu (U1^2/cs2) U2/h1, H_3 =
+ * nu (U2^2/cs2) U1/h2, H_4 = -nu[(3 - U2^2/cs2) h1/h2^2 - h1/cs2] U2 (its
+ * simplified forms drop these cubic parts and print G_4 = H_3 = 0).  gi = 0
+ * drops the U^2/c_s^2 terms as everywhere else. */
+static void srt_equilibria(const orc_t *o, double rho, double U1, double U2,
+                           double h1, double h2, double t11, double t12, double t21, double t22,
+                           double dU1, double dU2, double dr1, double dr2, double *m) {
+    double cs2 = o->cs2, nu = o->nu;
+    double gi = o->gi ? 1.0 : 0.0;
+    double a1 = gi * U1 * U1 / cs2, a2 = gi * U2 * U2 / cs2;
+    double tc11 = 2 * rho * nu * U2 * t12, tc22 = 2 * rho * nu * U1 * t21;
+    double G1 = rho * nu * (h2 / cs2 - 3 * (1 + a1) * h2 / (h1 * h1));
+    double G3 = -nu * ((3 - a1) * h2 / (h1 * h1) - h2 / cs2) * U1;
+    double G4 = nu * a1 * U2 / h1;
+    double G5 = -h2 / h1 * tc11
+                - rho * nu * (-2 * U1 * (a1 + 1) * h2 / h1 * t11
+                              + U1 * ((3 + a1) * h2 / h1 - h1 * h2 / cs2) * t21
+                              + 2 * U2 * h2 / h1 * t12);
+    double H2 = rho * nu * (h1 / cs2 - 3 * (1 + a2) * h1 / (h2 * h2));
+    double H3 = nu * a2 * U1 / h2;
+    double H4 = -nu * ((3 - a2) * h1 / (h2 * h2) - h1 / cs2) * U2;
+    double H5 = -h1 / h2 * tc22
+                - rho * nu * (-2 * U2 * (a2 + 1) * h1 / h2 * t22
+                              + U2 * ((3 + a2) * h1 / h2 - h1 * h2 / cs2) * t12
+                              + 2 * U1 * h1 / h2 * t21);
+    m[0] = rho * h1 * h2;
+    m[1] = rho * U1 * h2;
+    m[2] = rho * U2 * h1;
+    m[3] = h2 / h1 * rho * (U1 * U1 + cs2) + G1 * dU1 + G3 * dr1 + G4 * dr2 + G5;   /* G2 = 0 */
+    m[4] = h1 / h2 * rho * (U2 * U2 + cs2) + H2 * dU2 + H3 * dr1 + H4 * dr2 + H5;   /* H1 = 0 */
+    m[5] = rho * U1 * U2;
+    m[6] = rho * U2 / h1 * (cs2 + U1 * U1);
+    m[7] = rho * U1 / h2 * (cs2 + U2 * U2);
+    m[8] = rho * cs2 * cs2 + rho * cs2 * (U1 * U1 + U2 * U2) + rho * U1 * U1 * U2 * U2;
+}
+
+/* Raw moments (bare order k00, k10, k01, k20, k02, k11, k21, k12, k22) to
+ * populations: the expansions of Q^-1 printed as Eq. feqGOCLBE / Eq. SGOCLBE. */
+static void srt_to_populations(const double *k, double *f) {
+    f[0] = k[0] - k[3] - k[4] + k[8];
+    f[1] = 0.5 * (k[1] + k[3] - k[7] - k[8]);
+    f[2] = 0.5 * (k[2] + k[4] - k[6] - k[8]);
+    f[3] = 0.5 * (-k[1] + k[3] + k[7] - k[8]);
+    f[4] = 0.5 * (-k[2] + k[4] + k[6] - k[8]);
+    f[5] = 0.25 * (k[5] + k[6] + k[7] + k[8]);
+    f[6] = 0.25 * (-k[5] + k[6] - k[7] + k[8]);
+    f[7] = 0.25 * (k[5] - k[6] - k[7] + k[8]);
+    f[8] = 0.25 * (-k[5] - k[6] + k[7] + k[8]);
+}
+
 /* ---- macroscopic fields ------------------------------------------------- */
 static void update_fields(orc_t *o) {
     int N = o->N;
@@ -480,6 +545,27 @@ static void nse_node(orc_t *o, int n) {
                    / (1.0 + c5 * (t12 * U2 + t21 * U1));
     double F1 = Ft1 + 2 * h2 * t12 * tau12;
     double F2 = Ft2 + 2 * h1 * t21 * tau12;
+    if (o->srt) {
+        /* Appendix F Step 1: f~ = f + (f^eq - f)/tau + (1 - 1/(2 tau)) S with
+         * f^eq = Q^-1 m^eq (Eq. 14D) and S = Q^-1 Psi (Eq. 14D-source; sigma11
+         * read as F1 U2/h2 + F2 U1/h1, the value of Eq. GOCmomentsources, the
+         * printed factor 2 on F1 U2/h2 being garbled) */
+        double meq[9], psi[9] = {0}, fe[9], sv[9];
+        srt_equilibria(o, rho, U1, U2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2, meq);
+        psi[1] = F1;
+        psi[2] = F2;
+        psi[3] = 2 * F1 * U1 / h1;
+        psi[4] = 2 * F2 * U2 / h2;
+        psi[5] = F1 * U2 / h2 + F2 * U1 / h1;
+        srt_to_populations(meq, fe);
+        srt_to_populations(psi, sv);
+        double w = om[4];
+        for (int a = 0; a < 9; a++)
+            o->ft[(size_t)a * N + n] = f[a] + w * (fe[a] - f[a]) + (1 - 0.5 * w) * sv[a];
+        o->F1[n] = F1;
+        o->F2[n] = F2;
+        return;
+    }
     /* Step 3e: central-moment sources (Eq. cmsourcesGOC), bare order */
     double sig[9] = {0};
     sig[1] = F1; sig[2] = F2;
@@ -709,6 +795,18 @@ void orc_corrections(const orc_t *o, double rho, double U1, double U2, double h1
                      double dU1, double dU2, double dr1, double dr2, double *n34) {
     corrections(o, rho, U1, U2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2, &n34[0], &n34[1]);
 }
+
+/* SRT collision (Appendix F) on or off; the caller passes zeta = nu and all
+ * rates 1/tau at creation. */
+void orc_set_srt(orc_t *o, int on) { o->srt = on ? 1 : 0; }
+
+void orc_srt_equilibria(const orc_t *o, double rho, double U1, double U2, double h1, double h2,
+                        double t11, double t12, double t21, double t22,
+                        double dU1, double dU2, double dr1, double dr2, double *m) {
+    srt_equilibria(o, rho, U1, U2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2, m);
+}
+
+void orc_srt_to_populations(const double *k, double *f) { srt_to_populations(k, f); }
 
 /* Per-node diagnostics of the last orc_step's MIE part (J3, Lorentz force). */
 void orc_mie_diag(const orc_t *o, double *J3, double *FL1, double *FL2) {

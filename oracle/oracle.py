@@ -16,6 +16,9 @@ A problem is described by a plain dict ``spec`` (see ``goc_inputs``):
     omega_free        omega0,1,2,6,7,8 (default 1, preparatory step (d))
     fext              (F_ext,1, F_ext,2)
     gi                1: full correction coefficients (default); 0: cubic terms dropped
+    collision         "cm" (default): central-moment MRT of Appendix E; "srt": the
+                      single-relaxation-time GOC-LBM in velocity space of Appendix F
+                      (one rate 1/tau for every moment, zeta = nu)
     mhd               None or {"tau_m" | "eta", "mu_m"}
     rho0              reference density (default 1)
 
@@ -77,6 +80,9 @@ def _load():
             lib.orc_raw_equilibria.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 7 + [_D]
             lib.orc_corrections.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 13 + [_D]
             lib.orc_mie_diag.argtypes = [ctypes.c_void_p] + [_D] * 3
+            lib.orc_set_srt.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.orc_srt_equilibria.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 13 + [_D]
+            lib.orc_srt_to_populations.argtypes = [_D, _D]
             lib.orc_threads.argtypes = [ctypes.c_void_p]
             lib.orc_threads.restype = ctypes.c_int
             _lib = lib
@@ -109,6 +115,9 @@ def derived_parameters(spec: dict, metric: Metric) -> dict:
     om[4] = om[5] = 1.0 / tau
     for k, v in (spec.get("omega_set") or {}).items():   # explicit per-moment rates
         om[int(k)] = float(v)
+    if spec.get("collision", "cm") == "srt":   # Appendix F: one rate, zeta = nu
+        om = [1.0 / tau] * 9
+        zeta = nu
     out = {"cs2": cs2, "nu": nu, "zeta": zeta, "tau": tau, "omega": om}
     mhd = spec.get("mhd")
     if mhd:
@@ -166,6 +175,10 @@ class Oracle:
             1 if mhd else 0, par.get("csm2", 0.0), par.get("tau_m", 1.0), par.get("mu_m", 1.0),
             _p(bwall), int(threads))
         self._lib = lib
+        coll = spec.get("collision", "cm")
+        if coll not in ("cm", "srt"):
+            raise ValueError(f"unknown collision {coll!r}")
+        lib.orc_set_srt(self._h, 1 if coll == "srt" else 0)
         self.steps_done = 0
         self.initialize()
 
@@ -251,6 +264,18 @@ class Oracle:
     def raw_equilibria(self, rho, u1, u2, h1, h2, n3=0.0, n4=0.0):
         out = np.zeros(9)
         self._lib.orc_raw_equilibria(self._h, rho, u1, u2, h1, h2, n3, n4, _p(out))
+        return out
+
+    def srt_equilibria(self, rho, u1, u2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2):
+        out = np.zeros(9)
+        self._lib.orc_srt_equilibria(self._h, rho, u1, u2, h1, h2, t11, t12, t21, t22,
+                                     dU1, dU2, dr1, dr2, _p(out))
+        return out
+
+    def srt_to_populations(self, k):
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        out = np.zeros(9)
+        self._lib.orc_srt_to_populations(_p(k), _p(out))
         return out
 
     def corrections(self, rho, u1, u2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2):
