@@ -127,7 +127,12 @@ typedef struct {
                                central-moment LBM (the comparator: the GOC step at h1 = h2 = 1,
                                local collision, no stored force); scheme 1 requires uniform
                                maps on both axes, gi_correction = 0 and no MIE (else
-                               GOC_EINVAL); lattices added by goc_batch_add use scheme 0 */
+                               GOC_EINVAL); 2 = the GOC-LBM with the single-relaxation-time
+                               collision in velocity space of Appendix F (one rate 1/tau for
+                               every moment, zeta = nu; tau_zeta and omega_free are ignored;
+                               any map, MIE allowed; it diverges on clustered grids at
+                               tau < 1 where the central-moment step does not); lattices
+                               added by goc_batch_add use scheme 0 */
     int fixed_launch;       /* 0 = the launch autotuner picks the tile order (dynamic queue or
                                static) and programmatic dependent launch on or off, by timing
                                each choice on 16 steps of the first goc_step call of at least

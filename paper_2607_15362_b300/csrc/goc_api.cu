@@ -174,18 +174,18 @@ bool encode_lattice_maps(goc_lattice *L) {
 }
 
 // Dynamic shared memory of a step kernel and its persistent grid size.
-template <class S, bool MHD>
+template <class S, bool MHD, bool SRT = false>
 int step_grid(int ntiles, size_t *smem) {
     using T = Tiling<S>;
     const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
     *smem = bytes;
     static int cached = -1;
     if (cached < 0) {
-        cudaFuncSetAttribute(step_kernel<S, MHD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cudaFuncSetAttribute(step_kernel<S, MHD, SRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD>, NT, bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD, SRT>, NT, bytes);
         cached = std::max(1, sms * std::max(1, per));
     }
     return std::min(ntiles, cached);
@@ -203,12 +203,21 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     if (L->scheme == 1) return launch_std_t<S>(L, p);
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
-    if (L->mhd.enabled) {
+    const bool pdl = L->cfg_pdl != 0;
+    if (L->scheme == 2) {   // SRT collision (Appendix F)
+        if (L->mhd.enabled) {
+            const int grid = step_grid<S, true, true>(ntiles, &smem);
+            CU(launch_pdl(pdl, step_kernel<S, true, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        } else {
+            const int grid = step_grid<S, false, true>(ntiles, &smem);
+            CU(launch_pdl(pdl, step_kernel<S, false, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        }
+    } else if (L->mhd.enabled) {
         const int grid = step_grid<S, true>(ntiles, &smem);
-        CU(launch_pdl(L->cfg_pdl != 0, step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        CU(launch_pdl(pdl, step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     } else {
         const int grid = step_grid<S, false>(ntiles, &smem);
-        CU(launch_pdl(L->cfg_pdl != 0, step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        CU(launch_pdl(pdl, step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     }
     CU(cudaGetLastError());
     return GOC_OK;
@@ -563,7 +572,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     if (!(flow->rho0 > 0.0)) return fail(GOC_EINVAL, "rho0 must be > 0");
     if (flow->nu <= 0.0 && !(flow->tau > 0.5)) return fail(GOC_EINVAL, "need nu > 0 or tau > 1/2");
     if (exec && (exec->storage < 0 || exec->storage > 2)) return fail(GOC_EINVAL, "unknown storage %d", exec->storage);
-    if (exec && (exec->scheme < 0 || exec->scheme > 1)) return fail(GOC_EINVAL, "unknown scheme %d", exec->scheme);
+    if (exec && (exec->scheme < 0 || exec->scheme > 2)) return fail(GOC_EINVAL, "unknown scheme %d", exec->scheme);
     if (exec && exec->scheme == 1) {
         const bool uni = map && (map->kind[0] == GOC_MAP_UNIFORM || (map->kind[0] == GOC_MAP_TANH2 && map->beta[0] == 0.0)) &&
                          (map->kind[1] == GOC_MAP_UNIFORM || (map->kind[1] == GOC_MAP_TANH2 && map->beta[1] == 0.0));
@@ -650,7 +659,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         L->tau = L->flow.tau;
         L->nu = L->cs2 * (L->tau - 0.5);
     }
-    L->zeta = L->cs2 * (L->flow.tau_zeta - 0.5);
+    L->zeta = L->scheme == 2 ? L->nu : L->cs2 * (L->flow.tau_zeta - 0.5);   // SRT: zeta = nu
     if (L->mhd.enabled) {
         L->csm2 = L->cs2;   // c_sm = c_s (Eq. GOC-LBE_CFL-MIE)
         if (L->mhd.eta > 0.0) {
@@ -709,6 +718,8 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     for (int k = 0; k < 9; k++) p.om[k] = (float)L->flow.omega_free;
     p.om[3] = (float)(1.0 / L->flow.tau_zeta);
     p.om[4] = p.om[5] = (float)(1.0 / L->tau);
+    if (L->scheme == 2)   // SRT: one rate for every moment
+        for (int k = 0; k < 9; k++) p.om[k] = (float)(1.0 / L->tau);
     p.fext1 = (float)L->flow.fext[0];
     p.fext2 = (float)L->flow.fext[1];
     p.gi = L->flow.gi_correction ? 1.f : 0.f;

@@ -291,6 +291,90 @@ struct FieldSmem {
     float rho[TY + 2 * MH][TX + 2 * MH], u1[TY + 2 * MH][TX + 2 * MH], u2[TY + 2 * MH][TX + 2 * MH];
 };
 
+// The SRT collision of Appendix F (f~ = f + (f^eq - f)/tau + (1 - 1/(2 tau)) S,
+// one rate w = 1/tau for every moment) in the storage variables.  Because the
+// rate is the same for all moments, the update is done on raw moments: m =
+// moments of f - f_rest (two passes of the 1D transform about zero velocity),
+// Delta = w (m^eq - m) + (1 - w/2) Psi with m^eq - m_rest of Eq. 14D (the
+// bare corrections of Eqs. 5D/6D are (n3 +- n4)/2 of Eqs. 82-85 at zeta =
+// nu) and Psi of Eq. 14D-source; the change of reference f_ref- -> f_ref+ is
+// taken off the first moments (which leaves w F^{n-1}/2 + (1 - w/2) F_dev
+// there, as in the central-moment path); o = d + Q^-1 Delta.
+template <class V>
+__device__ __forceinline__ void srt_relax(const StepParams &p, const V (&d)[9], V (&o)[9], V rho, V drho, V U1,
+                                          V U2, V ih2, float ih1, V r, V s, V uu, V vv, V uv, V n3, V n4, V F1,
+                                          V F2, V F1dev, V F2dev, V F1p, V F2p, V F1r, V F2r) {
+    const float w = p.om[4], ks = 1.f - 0.5f * w, cs2 = p.cs2;
+    // populations of f - f_rest by rows e2 = -1, 0, +1 at e1 = -1, 0, +1
+    const V q1 = F1r * 0.25f, q2 = F2r * 0.25f;
+    const V fm[3] = {d[7], d[3] + q1, d[6]};
+    const V f0[3] = {d[4] + q2, d[0], d[2] - q2};
+    const V fp[3] = {d[8], d[1] - q1, d[5]};
+    V k0[3], k1[3], k2[3];                                // per row: orders 0, 1, 2 along xi1
+#pragma unroll
+    for (int y = 0; y < 3; y++) {
+        const V sm_ = fp[y] + fm[y];
+        k0[y] = sm_ + f0[y];
+        k1[y] = fp[y] - fm[y];
+        k2[y] = sm_;
+    }
+    V m[3][3];                                            // m[a][b]: order a along xi1, b along xi2
+    {
+        const V *kk[3] = {k0, k1, k2};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const V sm_ = kk[a][2] + kk[a][0];
+            m[a][0] = sm_ + kk[a][1];
+            m[a][1] = kk[a][2] - kk[a][0];
+            m[a][2] = sm_;
+        }
+    }
+    // m^eq - m_rest (Eq. 14D; m_rest = (H rho0, 0, 0, r rho0 cs2, s rho0 cs2, 0, 0, 0, rho0 cs2^2))
+    const V csd = drho * cs2;
+    const V E20 = fmav(r, fmav(rho, uu, csd), (n3 + n4) * 0.5f);
+    const V E02 = fmav(s, fmav(rho, vv, csd), (n3 - n4) * 0.5f);
+    const V E11 = rho * uv;
+    const V E21 = rho * U2 * (uu + cs2) * ih1;
+    const V E12 = rho * U1 * (vv + cs2) * ih2;
+    const V E22 = fmav(csd, bc<V>(cs2), rho * fmav(uu, vv, (uu + vv) * cs2));
+    V g[3][3];
+    g[0][0] = bc<V>(0.f);
+    g[1][0] = fmav(F1p, 0.5f * w, F1dev * ks);
+    g[0][1] = fmav(F2p, 0.5f * w, F2dev * ks);
+    g[2][0] = fmav(E20 - m[2][0], w, F1 * U1 * (2.f * ks * ih1));
+    g[0][2] = fmav(E02 - m[0][2], w, F2 * U2 * ih2 * (2.f * ks));
+    g[1][1] = fmav(E11 - m[1][1], w, fmav(F1 * U2, ih2, F2 * U1 * ih1) * ks);
+    g[2][1] = (E21 - m[2][1]) * w;
+    g[1][2] = (E12 - m[1][2]) * w;
+    g[2][2] = (E22 - m[2][2]) * w;
+    // Q^-1: along xi2, then xi1; for raw moments (c0, c1, c2) the values at
+    // e = 0, +1, -1 are c0 - c2, (c1 + c2)/2, (c2 - c1)/2
+    V r0[3], rp[3], rn[3];                                // per xi1 order: rows e2 = 0, +1, -1
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        r0[a] = g[a][0] - g[a][2];
+        rp[a] = (g[a][1] + g[a][2]) * 0.5f;
+        rn[a] = (g[a][2] - g[a][1]) * 0.5f;
+    }
+    const V *rows[3] = {r0, rp, rn};
+    V o0[3], op[3], on[3];
+#pragma unroll
+    for (int y = 0; y < 3; y++) {
+        o0[y] = rows[y][0] - rows[y][2];
+        op[y] = (rows[y][1] + rows[y][2]) * 0.5f;
+        on[y] = (rows[y][2] - rows[y][1]) * 0.5f;
+    }
+    o[0] = d[0] + o0[0];
+    o[1] = d[1] + op[0];
+    o[3] = d[3] + on[0];
+    o[2] = d[2] + o0[1];
+    o[5] = d[5] + op[1];
+    o[6] = d[6] + on[1];
+    o[4] = d[4] + o0[2];
+    o[8] = d[8] + op[2];
+    o[7] = d[7] + on[2];
+}
+
 // Phase 2 for the R = Lanes<V>::R nodes (i, j[r]) of one thread, r = 0..R-1
 // (one node with V = float, two with V = float2: every arithmetic step below
 // runs once for both): the MIE, stresses, forces and the central-moment
@@ -298,7 +382,7 @@ struct FieldSmem {
 // step, the fields and their normal derivatives fl[k][r] (k: drho, U1, U2,
 // dU1/dxi1, drho/dxi1, dU2/dxi2, drho/dxi2), and the stores.  own[r]: whether
 // node r is a lattice node this thread updates.
-template <class S, bool MHD, bool CHECKS, class V, class Src>
+template <class S, bool MHD, bool CHECKS, class V, bool SRT, class Src>
 __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int i, const int (&j)[Lanes<V>::R],
                                         const bool (&own)[Lanes<V>::R], const float (&dn)[Lanes<V>::R][9],
                                         const float (&F1pn)[Lanes<V>::R], const float (&F2pn)[Lanes<V>::R], float h1,
@@ -447,6 +531,11 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         n4 = rho * q4 - U1 * (X1 + b2) * dr1 * nu + U2 * (X2 + b1) * dr2 * nu;
     }
 
+    V o[9];
+    if constexpr (SRT) {
+        srt_relax<V>(p, d, o, rho, drho, U1, U2, ih2, ih1, r, s, uu, vv, uv, n3, n4, F1, F2, F1dev, F2dev, F1p,
+                     F2p, F1r, F2r);
+    } else {
     // ---- central moments c = F(U) P (f - f_rest) -----------------------------
     // f - f_rest = d + (f_ref- - f_rest), the latter -F_rest/4 (e . unit) on
     // links 1..4.  Central moments about (U1, U2) by two passes of the 1D
@@ -523,7 +612,6 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     // central moments (c0, c1, c2) about w, the raw moments are m1 = c1 + w c0,
     // m2 = c2 + 2 w c1 + w^2 c0 and the values at e = 0, +1, -1 are c0 - m2,
     // (m1 + m2)/2, (m2 - m1)/2.
-    V o[9];
     {
         const V uv2 = uv * 2.f;
         const V g[3][3] = {
@@ -560,6 +648,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         o[8] = d[8] + op[2];
         o[7] = d[7] + on[2];
     }
+    }   // central-moment path
     S *fout = static_cast<S *>(p.fout);
     S *Fout = static_cast<S *>(p.Fout);
 #pragma unroll
@@ -592,7 +681,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
 // Normal derivatives of the fields from the tile's field arrays (second
 // order: central, one-sided at the first and last node of a wall axis), then
 // the collision.
-template <class S, bool MHD, bool CHECKS, class V, class Src>
+template <class S, bool MHD, bool CHECKS, class V, bool SRT, class Src>
 __device__ __forceinline__ void node_update(const StepParams &p, const Src &src, int i, int tx,
                                             const int (&j)[Lanes<V>::R], const int (&ty)[Lanes<V>::R],
                                             const bool (&own)[Lanes<V>::R], const FieldSmem &sm,
@@ -621,7 +710,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
             fl[6][r] = 0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex]);
         }
     }
-    collide<S, MHD, CHECKS, V>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl);
+    collide<S, MHD, CHECKS, V, SRT>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl);
 }
 
 // One tile of one lattice from a given source; KIND 0: interior (no boundary
@@ -632,7 +721,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
 // barrier: every thread of the block must call it.  ok: this thread's wait
 // for the staged copy succeeded; false (returned by every thread) when any
 // thread's wait failed -- the block then leaves.
-template <class S, bool MHD, int KIND, class Src>
+template <class S, bool MHD, int KIND, bool SRT, class Src>
 __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src, int i0, int j0, FieldSmem &sm,
                                              bool ok) {
     constexpr bool CHECKS = KIND != 0;
@@ -729,7 +818,7 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
     bool any = false;
 #pragma unroll
     for (int r = 0; r < R; r++) any = any || own[r];
-    if (any) node_update<S, MHD, CHECKS, V>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
+    if (any) node_update<S, MHD, CHECKS, V, SRT>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
     return true;
 }
 
@@ -767,20 +856,20 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
-template <class S, bool MHD>
+template <class S, bool MHD, bool SRT = false>
 __device__ __forceinline__ bool run_tile(const StepParams &p, int kind, int i0, int j0, const unsigned char *stage,
                                          FieldSmem &sm, bool ok) {
     using T = Tiling<S>;
     if (kind == 2) {
         SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                          p.plane, p.pitch, p.sf, p.sF, p.sg};
-        return tile_compute<S, MHD, 1>(p, src, i0, j0, sm, ok);
+        return tile_compute<S, MHD, 1, SRT>(p, src, i0, j0, sm, ok);
     }
     SrcSmem<S> src{reinterpret_cast<const S *>(stage), reinterpret_cast<const S *>(stage + T::OFF_FF),
                    reinterpret_cast<const S *>(stage + T::OFF_G), i0 - T::HXS, j0 - HYS, j0 - 1,
                    p.sf, p.sF, p.sg};
-    if (kind == 0) return tile_compute<S, MHD, 0>(p, src, i0, j0, sm, ok);
-    return tile_compute<S, MHD, 1>(p, src, i0, j0, sm, ok);
+    if (kind == 0) return tile_compute<S, MHD, 0, SRT>(p, src, i0, j0, sm, ok);
+    return tile_compute<S, MHD, 1, SRT>(p, src, i0, j0, sm, ok);
 }
 
 // The tiles of one lattice processed by one block with TMA staging in two
@@ -789,7 +878,7 @@ __device__ __forceinline__ bool run_tile(const StepParams &p, int kind, int i0, 
 // tile is stride + the counter's next value (dynamic order, with ctr) or
 // t + stride (static order).  Every thread of the block calls it; the barriers
 // must be initialised.
-template <class S, bool MHD>
+template <class S, bool MHD, bool SRT>
 __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMaps &m, int *ctr, int first, int stride,
                                               unsigned char *dyn, uint64_t *bars, FieldSmem &sm, int4 *s_item,
                                               bool leader) {
@@ -847,14 +936,15 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
         if (MHD) {   // with the MIE the block gathers after the copy (measured faster there)
             if (!__syncthreads_and(ok)) return;
         }
-        if (!run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
+        if (!run_tile<S, MHD, SRT>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
         __syncthreads();   // the stage, the field arrays and s_item are reused by the next tile
         stage ^= 1;
     }
 }
 
 // Single lattice: persistent blocks take tiles from the lattice's queue.
-template <class S, bool MHD>
+// SRT: the collision of Appendix F instead of the central-moment one.
+template <class S, bool MHD, bool SRT = false>
 __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -873,7 +963,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
         if (p.tctr) *p.tctr_next = 0;                                  // next step's tile queue
     }
     const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
-    lattice_tiles<S, MHD>(p, m, p.tctr, blockIdx.x, gridDim.x, dyn, bars, sm, s_item, leader);
+    lattice_tiles<S, MHD, SRT>(p, m, p.tctr, blockIdx.x, gridDim.x, dyn, bars, sm, s_item, leader);
 }
 
 // Many lattices in one launch.  Their parameters travel in the kernel
