@@ -271,3 +271,42 @@ def test_launch_configurations_give_bitwise_identical_populations(gpu):
         assert A.launch_config["tuned"]
         assert A.get_state() == states[0]
         A.close()
+
+
+# ---- SRT collision of Appendix F (goc_exec.scheme = 2) ------------------------
+def _srt_pair(prob, steps_list):
+    spec = prob.lattice_spec(cs2_of(prob))
+    spec["collision"] = "srt"
+    o = oracle.Oracle(spec, threads=8)
+    L = goc.Lattice(spec, scheme="goc_srt")
+    out = []
+    for n in steps_list:
+        o.step(n)
+        L.step(n)
+        out.append((o.fields(), L.moments()))
+    L.close()
+    return out
+
+
+@pytest.mark.parametrize("name", ["poiseuille_roberts", "couette", "cavity", "hartmann"])
+def test_srt_fp32_matches_the_oracle(gpu, name):
+    """The SRT GOC-LBM (Appendix F) in the library against the oracle's SRT:
+    body-force channel on the paper's Roberts grid (gamma = 1.06, tau = 1),
+    the shear-driven channel of Sec. 7.2 (6 x 50), a cavity with ragged tiles,
+    and a Hartmann strip with the MIE; FP32 velocity (and induced field)
+    relative L2 <= 1e-5."""
+    probs = {
+        "poiseuille_roberts": gi.Problem("poiseuille", 8, 48, {"kind": "uniform"},
+                                         {"kind": "roberts", "gamma": 1.06, "alpha": 0.5}, {"Re": 20.0, "tau": 1.0}),
+        "couette": gi.Problem("couette", 6, 50, {"kind": "uniform"}, {"kind": "roberts", "gamma": 1.06, "alpha": 0.5},
+                              {"tau": 1.0, "u_wall": 0.02}),
+        "cavity": gi.Problem("cavity", 37, 29, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
+                             {"Re": 10.0, "u_lid": 0.05}),
+        "hartmann": gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
+                               {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0}),
+    }
+    for fo, fg in _srt_pair(probs[name], (1000, 1000)):
+        assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+        assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+        if name == "hartmann":
+            assert relerr(fg[3], fo[3]) <= 1e-5
