@@ -131,8 +131,9 @@ typedef struct {
                                collision in velocity space of Appendix F (one rate 1/tau for
                                every moment, zeta = nu; tau_zeta and omega_free are ignored;
                                any map, MIE allowed; it diverges on clustered grids at
-                               tau < 1 where the central-moment step does not); lattices
-                               added by goc_batch_add use scheme 0 */
+                               tau < 1 where the central-moment step does not); 3 = the GOC-LBM
+                               with the raw-moment MRT collision of Appendix D (rates as for
+                               scheme 0); lattices added by goc_batch_add use scheme 0 */
     int fixed_launch;       /* 0 = the launch autotuner picks the tile order (dynamic queue or
                                static) and programmatic dependent launch on or off, by timing
                                each choice on 16 steps of the first goc_step call of at least

@@ -26,7 +26,11 @@
  *   Step 4: m~ = F(-U) m~^c.   Step 5: f~ = P^-1 m~.
  *   Step 6: streaming with boundary conditions (half-way bounce-back,
  *     momentum-augmented moving wall, Eq. 101/103; MIE anti-bounce-back).
- *   Alternative Steps 1-5 (Appendix F, orc_set_srt): the SRT collision in
+ *   Alternative Steps 1-5 (Appendix D, orc_set_collision 2): the raw-moment
+ *     MRT -- relaxation of m = P f in the combined basis towards Eq.
+ *     GOCmomentequilibria with the same corrections, sources of Eq.
+ *     GOCmomentsources, f~ = P^-1 m~ through the printed expansion.
+ *   Alternative Steps 1-5 (Appendix F, orc_set_collision 1): the SRT collision in
  *     velocity space, f~ = f + (f^eq - f)/tau + (1 - 1/(2 tau)) S with f^eq and S
  *     from the raw moments of Eq. 14D / Eq. 14D-source through the printed
  *     expansions of Q^-1 (Eq. feqGOCLBE, Eq. SGOCLBE); stresses and force as
@@ -92,6 +96,7 @@ typedef struct {
     int q3_printed;       /* 1: use the printed q21/q12 signs */
     int mhd;
     int srt;              /* 1: the SRT collision in velocity space (Appendix F) */
+    int raw;              /* 1: the raw-moment MRT collision (Appendix D) */
     double csm2, taum, eta, mum;
     /* state */
     double *f, *ft;       /* populations (post-streaming) and post-collision */
@@ -545,6 +550,33 @@ static void nse_node(orc_t *o, int n) {
                    / (1.0 + c5 * (t12 * U2 + t21 * U1));
     double F1 = Ft1 + 2 * h2 * t12 * tau12;
     double F2 = Ft2 + 2 * h1 * t21 * tau12;
+    if (o->raw) {
+        /* Appendix D Step 2e-h: raw sources (Eq. GOCmomentsources), base
+         * equilibria (Eq. GOCmomentequilibria) with n3, n4 (Eqs. 82-85) on the
+         * combined k2s, k2d, relaxation of the nine moments in the combined
+         * basis, split back; Step 3: f~ = P^-1 m~ (its printed expansion) */
+        double n3, n4, meq[9], sg[9] = {0};
+        corrections(o, rho, U1, U2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2, &n3, &n4);
+        raw_equilibria(o, rho, U1, U2, h1, h2, n3, n4, meq);
+        sg[1] = F1;
+        sg[2] = F2;
+        sg[3] = 2 * F1 * U1 / h1;
+        sg[4] = 2 * F2 * U2 / h2;
+        sg[5] = F1 * U2 / h2 + F2 * U1 / h1;
+        double nb[9], nq[9], ns[9], nt[9], mt[9], ft[9];
+        for (int k = 0; k < 9; k++) { nb[k] = m[k]; nq[k] = meq[k]; ns[k] = sg[k]; }
+        nb[3] = m[3] + m[4]; nb[4] = m[3] - m[4];
+        nq[3] = meq[3] + meq[4]; nq[4] = meq[3] - meq[4];
+        ns[3] = sg[3] + sg[4]; ns[4] = sg[3] - sg[4];
+        for (int k = 0; k < 9; k++) nt[k] = nb[k] + om[k] * (nq[k] - nb[k]) + (1 - 0.5 * om[k]) * ns[k];
+        for (int k = 0; k < 9; k++) mt[k] = nt[k];
+        mt[3] = 0.5 * (nt[3] + nt[4]); mt[4] = 0.5 * (nt[3] - nt[4]);
+        srt_to_populations(mt, ft);
+        for (int a = 0; a < 9; a++) o->ft[(size_t)a * N + n] = ft[a];
+        o->F1[n] = F1;
+        o->F2[n] = F2;
+        return;
+    }
     if (o->srt) {
         /* Appendix F Step 1: f~ = f + (f^eq - f)/tau + (1 - 1/(2 tau)) S with
          * f^eq = Q^-1 m^eq (Eq. 14D) and S = Q^-1 Psi (Eq. 14D-source; sigma11
@@ -796,9 +828,13 @@ void orc_corrections(const orc_t *o, double rho, double U1, double U2, double h1
     corrections(o, rho, U1, U2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2, &n34[0], &n34[1]);
 }
 
-/* SRT collision (Appendix F) on or off; the caller passes zeta = nu and all
- * rates 1/tau at creation. */
-void orc_set_srt(orc_t *o, int on) { o->srt = on ? 1 : 0; }
+/* Collision: 0 central-moment MRT (Appendix E), 1 SRT (Appendix F; the caller
+ * passes zeta = nu and all rates 1/tau at creation), 2 raw-moment MRT
+ * (Appendix D). */
+void orc_set_collision(orc_t *o, int kind) {
+    o->srt = kind == 1;
+    o->raw = kind == 2;
+}
 
 void orc_srt_equilibria(const orc_t *o, double rho, double U1, double U2, double h1, double h2,
                         double t11, double t12, double t21, double t22,

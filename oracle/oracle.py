@@ -18,7 +18,8 @@ A problem is described by a plain dict ``spec`` (see ``goc_inputs``):
     gi                1: full correction coefficients (default); 0: cubic terms dropped
     collision         "cm" (default): central-moment MRT of Appendix E; "srt": the
                       single-relaxation-time GOC-LBM in velocity space of Appendix F
-                      (one rate 1/tau for every moment, zeta = nu)
+                      (one rate 1/tau for every moment, zeta = nu); "raw": the
+                      raw-moment MRT of Appendix D (rates as for "cm")
     mhd               None or {"tau_m" | "eta", "mu_m"}
     rho0              reference density (default 1)
 
@@ -80,7 +81,7 @@ def _load():
             lib.orc_raw_equilibria.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 7 + [_D]
             lib.orc_corrections.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 13 + [_D]
             lib.orc_mie_diag.argtypes = [ctypes.c_void_p] + [_D] * 3
-            lib.orc_set_srt.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.orc_set_collision.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_srt_equilibria.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 13 + [_D]
             lib.orc_srt_to_populations.argtypes = [_D, _D]
             lib.orc_threads.argtypes = [ctypes.c_void_p]
@@ -176,9 +177,10 @@ class Oracle:
             _p(bwall), int(threads))
         self._lib = lib
         coll = spec.get("collision", "cm")
-        if coll not in ("cm", "srt"):
+        kinds = {"cm": 0, "srt": 1, "raw": 2}
+        if coll not in kinds:
             raise ValueError(f"unknown collision {coll!r}")
-        lib.orc_set_srt(self._h, 1 if coll == "srt" else 0)
+        lib.orc_set_collision(self._h, kinds[coll])
         self.steps_done = 0
         self.initialize()
 

@@ -204,7 +204,7 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
     const bool pdl = L->cfg_pdl != 0;
-    if (L->scheme == 2) {   // SRT collision (Appendix F)
+    if (L->scheme == 2 || L->scheme == 3) {   // collision on raw moments (Appendix F SRT, Appendix D MRT)
         if (L->mhd.enabled) {
             const int grid = step_grid<S, true, true>(ntiles, &smem);
             CU(launch_pdl(pdl, step_kernel<S, true, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
@@ -572,7 +572,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     if (!(flow->rho0 > 0.0)) return fail(GOC_EINVAL, "rho0 must be > 0");
     if (flow->nu <= 0.0 && !(flow->tau > 0.5)) return fail(GOC_EINVAL, "need nu > 0 or tau > 1/2");
     if (exec && (exec->storage < 0 || exec->storage > 2)) return fail(GOC_EINVAL, "unknown storage %d", exec->storage);
-    if (exec && (exec->scheme < 0 || exec->scheme > 2)) return fail(GOC_EINVAL, "unknown scheme %d", exec->scheme);
+    if (exec && (exec->scheme < 0 || exec->scheme > 3)) return fail(GOC_EINVAL, "unknown scheme %d", exec->scheme);
     if (exec && exec->scheme == 1) {
         const bool uni = map && (map->kind[0] == GOC_MAP_UNIFORM || (map->kind[0] == GOC_MAP_TANH2 && map->beta[0] == 0.0)) &&
                          (map->kind[1] == GOC_MAP_UNIFORM || (map->kind[1] == GOC_MAP_TANH2 && map->beta[1] == 0.0));

@@ -291,20 +291,23 @@ struct FieldSmem {
     float rho[TY + 2 * MH][TX + 2 * MH], u1[TY + 2 * MH][TX + 2 * MH], u2[TY + 2 * MH][TX + 2 * MH];
 };
 
-// The SRT collision of Appendix F (f~ = f + (f^eq - f)/tau + (1 - 1/(2 tau)) S,
-// one rate w = 1/tau for every moment) in the storage variables.  Because the
-// rate is the same for all moments, the update is done on raw moments: m =
-// moments of f - f_rest (two passes of the 1D transform about zero velocity),
-// Delta = w (m^eq - m) + (1 - w/2) Psi with m^eq - m_rest of Eq. 14D (the
-// bare corrections of Eqs. 5D/6D are (n3 +- n4)/2 of Eqs. 82-85 at zeta =
-// nu) and Psi of Eq. 14D-source; the change of reference f_ref- -> f_ref+ is
-// taken off the first moments (which leaves w F^{n-1}/2 + (1 - w/2) F_dev
-// there, as in the central-moment path); o = d + Q^-1 Delta.
+// Collision on raw moments in the storage variables: the raw-moment MRT of
+// Appendix D (Steps 1-3: m = P f, relaxation of k00, k10, k01, k2s, k2d,
+// k11, k21, k12, k22 with omega_0..8 towards Eq. GOCmomentequilibria with the
+// corrections n3, n4 of Eqs. 82-85 on k2s, k2d, sources of Eq.
+// GOCmomentsources, f~ = P^-1 m~), and, with every rate 1/tau and zeta = nu,
+// the SRT of Appendix F (f~ = f + (f^eq - f)/tau + (1 - 1/(2 tau)) S, the same
+// update written in velocity space: its Eq. 14D equilibria are these with
+// the bare corrections (n3 +- n4)/2).  m = moments of f - f_rest (two passes
+// of the 1D transform about zero velocity), Delta = omega (m^eq - m) + (1 -
+// omega/2) Psi per moment with m^eq - m_rest, the change of reference f_ref-
+// -> f_ref+ taken off the first moments (which leaves omega F^{n-1}/2 + (1 -
+// omega/2) F_dev there, as in the central-moment path); o = d + P^-1 Delta.
 template <class V>
-__device__ __forceinline__ void srt_relax(const StepParams &p, const V (&d)[9], V (&o)[9], V rho, V drho, V U1,
+__device__ __forceinline__ void raw_relax(const StepParams &p, const V (&d)[9], V (&o)[9], V rho, V drho, V U1,
                                           V U2, V ih2, float ih1, V r, V s, V uu, V vv, V uv, V n3, V n4, V F1,
                                           V F2, V F1dev, V F2dev, V F1p, V F2p, V F1r, V F2r) {
-    const float w = p.om[4], ks = 1.f - 0.5f * w, cs2 = p.cs2;
+    const float *om = p.om, cs2 = p.cs2;
     // populations of f - f_rest by rows e2 = -1, 0, +1 at e1 = -1, 0, +1
     const V q1 = F1r * 0.25f, q2 = F2r * 0.25f;
     const V fm[3] = {d[7], d[3] + q1, d[6]};
@@ -339,15 +342,21 @@ __device__ __forceinline__ void srt_relax(const StepParams &p, const V (&d)[9], 
     const V E22 = fmav(csd, bc<V>(cs2), rho * fmav(uu, vv, (uu + vv) * cs2));
     V g[3][3];
     g[0][0] = bc<V>(0.f);
-    g[1][0] = fmav(F1p, 0.5f * w, F1dev * ks);
-    g[0][1] = fmav(F2p, 0.5f * w, F2dev * ks);
-    g[2][0] = fmav(E20 - m[2][0], w, F1 * U1 * (2.f * ks * ih1));
-    g[0][2] = fmav(E02 - m[0][2], w, F2 * U2 * ih2 * (2.f * ks));
-    g[1][1] = fmav(E11 - m[1][1], w, fmav(F1 * U2, ih2, F2 * U1 * ih1) * ks);
-    g[2][1] = (E21 - m[2][1]) * w;
-    g[1][2] = (E12 - m[1][2]) * w;
-    g[2][2] = (E22 - m[2][2]) * w;
-    // Q^-1: along xi2, then xi1; for raw moments (c0, c1, c2) the values at
+    g[1][0] = fmav(F1p, 0.5f * om[1], F1dev * (1.f - 0.5f * om[1]));
+    g[0][1] = fmav(F2p, 0.5f * om[2], F2dev * (1.f - 0.5f * om[2]));
+    {   // combined second-order diagonal moments k2s, k2d (rates omega_3, omega_4)
+        const V a20 = E20 - m[2][0], a02 = E02 - m[0][2];
+        const V s20 = F1 * U1 * (2.f * ih1), s02 = F2 * U2 * ih2 * 2.f;
+        const V D2s = fmav(a20 + a02, om[3], (s20 + s02) * (1.f - 0.5f * om[3]));
+        const V D2d = fmav(a20 - a02, om[4], (s20 - s02) * (1.f - 0.5f * om[4]));
+        g[2][0] = (D2s + D2d) * 0.5f;
+        g[0][2] = (D2s - D2d) * 0.5f;
+    }
+    g[1][1] = fmav(E11 - m[1][1], om[5], fmav(F1 * U2, ih2, F2 * U1 * ih1) * (1.f - 0.5f * om[5]));
+    g[2][1] = (E21 - m[2][1]) * om[6];
+    g[1][2] = (E12 - m[1][2]) * om[7];
+    g[2][2] = (E22 - m[2][2]) * om[8];
+    // P^-1: along xi2, then xi1; for raw moments (c0, c1, c2) the values at
     // e = 0, +1, -1 are c0 - c2, (c1 + c2)/2, (c2 - c1)/2
     V r0[3], rp[3], rn[3];                                // per xi1 order: rows e2 = 0, +1, -1
 #pragma unroll
@@ -533,7 +542,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
 
     V o[9];
     if constexpr (SRT) {
-        srt_relax<V>(p, d, o, rho, drho, U1, U2, ih2, ih1, r, s, uu, vv, uv, n3, n4, F1, F2, F1dev, F2dev, F1p,
+        raw_relax<V>(p, d, o, rho, drho, U1, U2, ih2, ih1, r, s, uu, vv, uv, n3, n4, F1, F2, F1dev, F2dev, F1p,
                      F2p, F1r, F2r);
     } else {
     // ---- central moments c = F(U) P (f - f_rest) -----------------------------
@@ -943,7 +952,8 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
 }
 
 // Single lattice: persistent blocks take tiles from the lattice's queue.
-// SRT: the collision of Appendix F instead of the central-moment one.
+// SRT (raw): the collision on raw moments -- Appendix D's raw-moment MRT, or
+// Appendix F's SRT when every rate is 1/tau -- instead of the central-moment one.
 template <class S, bool MHD, bool SRT = false>
 __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
     extern __shared__ __align__(128) unsigned char dyn[];

@@ -69,7 +69,7 @@ def metric_info(spec: dict):
 
 
 ROUNDING = {"stochastic": 0, "nearest": 1}
-SCHEMES = {"goc": 0, "standard": 1, "goc_srt": 2}
+SCHEMES = {"goc": 0, "standard": 1, "goc_srt": 2, "goc_raw": 3}
 
 
 def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", scheme: str = "goc",

@@ -605,3 +605,55 @@ def test_srt_transient_couette_follows_the_series_at_second_order():
     e25, e50 = _couette_errors(25, collision="srt"), _couette_errors(50, collision="srt")
     assert np.all(e50 < 4e-3), e50
     assert np.all(np.log2(e25 / e50) > 1.7), (e25, e50)
+
+
+# --------------------------------------- raw-moment MRT GOC-LBM (Appendix D) --
+def test_raw_moment_mrt_with_one_rate_is_the_srt_scheme():
+    """Appendix D's raw-moment MRT with every rate 1/tau and zeta = nu is the
+    same update as Appendix F's SRT in velocity space (two printed algorithms:
+    relaxation of P f in the combined basis vs. f + (f^eq - f)/tau + ...), on
+    a stretched periodic grid with a random field."""
+    u1, u2 = gi.random_periodic_fields(9, 7, seed=6, amp=0.03)
+    tau = 0.9
+    common = dict(init={"u1": u1, "u2": u2}, tau=tau, fext=(2e-6, -1e-6))
+    a = oracle.Oracle(_periodic_spec(nx=9, ny=7, collision="srt", **common))
+    b = oracle.Oracle(_periodic_spec(nx=9, ny=7, collision="raw", tau_zeta=tau, omega_free=1.0 / tau, **common))
+    assert b.par["zeta"] == pytest.approx(b.par["nu"], rel=1e-14)
+    a.step(40)
+    b.step(40)
+    np.testing.assert_allclose(b.state()[0], a.state()[0], rtol=1e-13, atol=1e-16)
+
+
+def test_raw_moment_mrt_conserves_mass_and_follows_poiseuille_at_second_order():
+    """Raw-moment MRT (free rates 1, tau = 0.8 as in Sec. 7.1, Roberts gamma =
+    1.06): mass on a stretched periodic grid to 1e-12, steady Poiseuille at
+    second order."""
+    u1, u2 = gi.random_periodic_fields(12, 10, seed=4, amp=0.03)
+    o = oracle.Oracle(_periodic_spec(nx=12, ny=10, collision="raw", init={"u1": u1, "u2": u2}))
+    m = o.metric
+    mass0 = (o.fields()[0] * m.h1 * m.h2).sum()
+    o.step(3000)
+    assert abs((o.fields()[0] * m.h1 * m.h2).sum() - mass0) / mass0 < 1e-12
+    m2 = {"kind": "roberts", "gamma": 1.06, "alpha": 0.5}
+    errs = []
+    for ny in (12, 24, 48):
+        p = gi.Problem("poiseuille", 1, ny, {"kind": "uniform"}, m2, {"Re": 20.0, "tau": 0.8})
+        cs2 = oracle.build_metric(p.lattice_spec(1.0)).cs2()
+        spec = p.lattice_spec(cs2)
+        spec["collision"] = "raw"
+        d = spec["derived"]
+        s = map_position("roberts", ny, np.arange(ny) + 0.5, gamma=1.06, alpha=0.5) / d["H"]
+        ua = 4 * d["U"] * s * (1 - s)
+        spec["init"] = {"u1": ua[:, None].copy(), "u2": 0.0}
+        oo = oracle.Oracle(spec)
+        oo.step(int(2.0 * d["H"] ** 2 / d["nu"]))
+        errs.append(np.linalg.norm(oo.fields()[1][:, 0] - ua) / np.linalg.norm(ua))
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert errs[-1] < 5e-3
+    assert min(orders) > 1.8, (errs, orders)
+
+
+def test_raw_moment_mrt_transient_couette_follows_the_series_at_second_order():
+    e25, e50 = _couette_errors(25, collision="raw"), _couette_errors(50, collision="raw")
+    assert np.all(e50 < 4e-3), e50
+    assert np.all(np.log2(e25 / e50) > 1.7), (e25, e50)

@@ -273,12 +273,13 @@ def test_launch_configurations_give_bitwise_identical_populations(gpu):
         A.close()
 
 
-# ---- SRT collision of Appendix F (goc_exec.scheme = 2) ------------------------
-def _srt_pair(prob, steps_list):
+# ---- collisions on raw moments: SRT of Appendix F (goc_exec.scheme = 2) and
+# raw-moment MRT of Appendix D (scheme 3) --------------------------------------
+def _srt_pair(prob, steps_list, collision="srt"):
     spec = prob.lattice_spec(cs2_of(prob))
-    spec["collision"] = "srt"
+    spec["collision"] = collision
     o = oracle.Oracle(spec, threads=8)
-    L = goc.Lattice(spec, scheme="goc_srt")
+    L = goc.Lattice(spec, scheme={"srt": "goc_srt", "raw": "goc_raw"}[collision])
     out = []
     for n in steps_list:
         o.step(n)
@@ -288,9 +289,11 @@ def _srt_pair(prob, steps_list):
     return out
 
 
+@pytest.mark.parametrize("collision", ["srt", "raw"])
 @pytest.mark.parametrize("name", ["poiseuille_roberts", "couette", "cavity", "hartmann"])
-def test_srt_fp32_matches_the_oracle(gpu, name):
-    """The SRT GOC-LBM (Appendix F) in the library against the oracle's SRT:
+def test_srt_fp32_matches_the_oracle(gpu, name, collision):
+    """The SRT GOC-LBM (Appendix F) and the raw-moment MRT (Appendix D) in the
+    library against the oracle's:
     body-force channel on the paper's Roberts grid (gamma = 1.06, tau = 1),
     the shear-driven channel of Sec. 7.2 (6 x 50), a cavity with ragged tiles,
     and a Hartmann strip with the MIE; FP32 velocity (and induced field)
@@ -305,7 +308,7 @@ def test_srt_fp32_matches_the_oracle(gpu, name):
         "hartmann": gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
                                {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0}),
     }
-    for fo, fg in _srt_pair(probs[name], (1000, 1000)):
+    for fo, fg in _srt_pair(probs[name], (1000, 1000), collision):
         assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
         assert np.abs(fg[0] - fo[0]).max() <= 1e-6
         if name == "hartmann":
