@@ -24,7 +24,7 @@ import numpy as np
 
 @dataclass
 class Problem:
-    kind: str                     # "poiseuille" | "cavity" | "hartmann" | "taylor_green" | "couette"
+    kind: str                     # "poiseuille" | "cavity" | "hartmann" | "taylor_green" | "couette" | "taylor_couette"
     nx: int
     ny: int
     map1: dict
@@ -44,6 +44,8 @@ class Problem:
             w = {"W": {"u": 0.0}, "E": {"u": 0.0}, "S": {"u": 0.0}, "N": {"u": self.params["u_lid"]}}
         elif k == "taylor_green":
             w = {"W": None, "E": None, "S": None, "N": None}
+        elif k == "taylor_couette":   # radial walls (xi1) move along xi2; azimuth periodic
+            w = {"W": {"u": self.params["u_in"]}, "E": {"u": self.params["u_out"]}, "S": None, "N": None}
         else:
             raise ValueError(k)
         if k == "hartmann":
@@ -91,6 +93,10 @@ class Problem:
         elif k == "taylor_green":
             spec.update(tau=float(p["tau"]), fext=(0.0, 0.0))
             spec["init"] = taylor_green_init(self, float(p["u0"]))
+        elif k == "taylor_couette":   # Re = U0 (R2 - R1)/nu, R2 - R1 = nx lattice units (Sec. 8.2)
+            nu = float(p["U0"]) * self.nx / float(p["Re"])
+            spec.update(nu=nu, fext=(0.0, 0.0))
+            spec["derived"] = {"nu": nu}
         elif k == "hartmann":
             tau = float(p.get("tau", 1.0))
             taum = float(p.get("tau_m", 1.0))
@@ -260,3 +266,20 @@ def random_periodic_fields(nx: int, ny: int, seed: int, amp: float = 0.02):
         u1 += c1 * np.sin(kx * x + ky * y + p1)
         u2 += c2 * np.cos(kx * x - ky * y + p2)
     return u1, u2
+
+
+def taylor_couette(n1: int = 256, n2: int = 6, r_in: float = 32.0, sectors: float = 60.0, Re: float = 50.0,
+                   U0: float = 0.01, u_in: float = 1.0, u_out: float = 1.5) -> Problem:
+    """Taylor-Couette flow in an annular sector (Sec. 8): inner radius r_in,
+    outer r_in + n1, 2 pi / sectors of the circle on n2 periodic azimuthal
+    nodes; wall speeds u_in U0 (inner) and u_out U0 (outer)."""
+    m1 = {"kind": "annulus", "r_in": r_in, "r_out": r_in + n1, "sectors": sectors}
+    return Problem("taylor_couette", n1, n2, m1, {"kind": "uniform"},
+                   {"Re": Re, "U0": U0, "u_in": u_in * U0, "u_out": u_out * U0}, name=f"taylor_couette_{n1}x{n2}")
+
+
+def taylor_couette_profile(r: np.ndarray, r1: float, r2: float, u1: float, u2: float) -> np.ndarray:
+    """Azimuthal velocity of circular Couette flow between cylinders of radii
+    r1 < r2 with wall speeds u1 = Omega1 r1, u2 = Omega2 r2 (Sec. 8.2)."""
+    o1, o2, e2 = u1 / r1, u2 / r2, (r1 / r2) ** 2
+    return ((o2 - o1 * e2) * r + r1 * r1 * (o1 - o2) / r) / (1.0 - e2)

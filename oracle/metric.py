@@ -45,6 +45,15 @@ Maps (Sec. 6):
   theta = (sinh(mu B) / x_c) tanh(mu (eta - B)) sech(mu (eta - B)).
 
 Periodic axes place nodes at eta_i = i / N.
+
+Curvilinear grid (Sec. 8.1): the annular sector between circles of radii a
+and R_o spanning 2 pi / N_theta, by the conformal map Z = a exp(pi W / N_theta)
+(Eq. 2_annularsector) scaled to the lattice (Eq. 5_annularsector) with
+cell-centred radial nodes (walls at xi1 = 0 and N1) and periodic azimuthal
+nodes xi2 = j:
+  r = a exp(ln(R_o/a) xi1/N1),  phi = (pi/N_theta)(2 xi2/N2 - 1),
+  h1 = r ln(R_o/a)/N1,  h2 = 2 pi r/(N_theta N2),
+  theta11 = theta21 = 1/r,  theta12 = theta22 = 0.
 """
 from __future__ import annotations
 
@@ -171,3 +180,41 @@ class Metric:
     def cs2(self) -> float:
         """c_s^2 = q^2 / 3 (Eq. GOC-LBE_CFL)."""
         return self.q() ** 2 / 3.0
+
+
+def annulus_position(xi1, xi2, n1: int, n2: int, r_in: float, r_out: float, sectors: float):
+    """Cartesian (x1, x2) of the annular-sector map at lattice coordinates."""
+    r = r_in * np.exp(math.log(r_out / r_in) * np.asarray(xi1, dtype=np.float64) / n1)
+    phi = math.pi / sectors * (2.0 * np.asarray(xi2, dtype=np.float64) / n2 - 1.0)
+    return r * np.cos(phi), r * np.sin(phi)
+
+
+def annulus_metric(n1: int, n2: int, r_in: float, r_out: float, sectors: float) -> "Metric":
+    """Metric of the annular sector (Eq. h1, h2, theta of Sec. 8.1) as a
+    Metric: radial axis xi1 with walls, azimuthal axis xi2 periodic."""
+    lam = math.log(r_out / r_in)
+
+    def radial(xi1):
+        r = r_in * np.exp(lam * np.asarray(xi1, dtype=np.float64) / n1)
+        return r, r * lam / n1, 2.0 * math.pi * r / (sectors * n2), 1.0 / r
+
+    m = Metric.__new__(Metric)
+    m.nx, m.ny = n1, n2
+    r, h1, h2, th = radial(np.arange(n1) + 0.5)
+    m.h1_axis, m.h2_axis = h1, h2
+    m.radius = r
+    shape = (n2, n1)
+    m.h1 = np.broadcast_to(h1[None, :], shape).copy()
+    m.h2 = np.broadcast_to(h2[None, :], shape).copy()
+    m.t11 = np.broadcast_to(th[None, :], shape).copy()
+    m.t21 = np.broadcast_to(th[None, :], shape).copy()
+    m.t12 = np.zeros(shape)
+    m.t22 = np.zeros(shape)
+    _, hw1, hw2, _ = radial(np.array([0.0, float(n1)]))
+    m.wall = {
+        "W": (np.full(n2, hw1[0]), np.full(n2, hw2[0])),
+        "E": (np.full(n2, hw1[1]), np.full(n2, hw2[1])),
+        "S": (h1.copy(), h2.copy()),
+        "N": (h1.copy(), h2.copy()),
+    }
+    return m

@@ -34,7 +34,7 @@ import threading
 
 import numpy as np
 
-from .metric import Metric
+from .metric import Metric, annulus_metric
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "goc_oracle.c")
@@ -132,6 +132,10 @@ def derived_parameters(spec: dict, metric: Metric) -> dict:
 
 
 def build_metric(spec: dict) -> Metric:
+    m1 = spec.get("map1", {"kind": "uniform"})
+    if m1.get("kind") == "annulus":   # curvilinear annular sector (Sec. 8.1)
+        return annulus_metric(int(spec["nx"]), int(spec["ny"]), float(m1["r_in"]), float(m1["r_out"]),
+                              float(m1["sectors"]))
     walls = spec["walls"]
     per1 = walls.get("W") is None
     per2 = walls.get("S") is None

@@ -657,3 +657,84 @@ def test_raw_moment_mrt_transient_couette_follows_the_series_at_second_order():
     e25, e50 = _couette_errors(25, collision="raw"), _couette_errors(50, collision="raw")
     assert np.all(e50 < 4e-3), e50
     assert np.all(np.log2(e25 / e50) > 1.7), (e25, e50)
+
+
+# ------------------------------------- curvilinear grid: annular sector (Sec. 8) --
+def test_annulus_metric_matches_finite_differences_of_the_conformal_map():
+    """h1 = |dx/dxi1|, h2 = |dx/dxi2| of the map of Eq. 2_annularsector scaled by
+    Eq. 5_annularsector, the grid lines are orthogonal, and theta_ij =
+    (1/(h_i h_j)) dh_i/dxi_j (Eq. curvaturematrix) gives theta11 = theta21 =
+    1/r, theta12 = theta22 = 0, all by finite differences of the map itself."""
+    from oracle.metric import annulus_metric, annulus_position
+    n1, n2, a, ro, nt = 40, 6, 5.0, 45.0, 60.0
+    m = annulus_metric(n1, n2, a, ro, nt)
+    pos = lambda s1, s2: np.array(annulus_position(s1, s2, n1, n2, a, ro, nt))
+    eps, dl = 1e-4, 1e-2
+
+    def tangent(s1, s2, k):
+        e = (eps, 0.0) if k == 1 else (0.0, eps)
+        return (pos(s1 + e[0], s2 + e[1]) - pos(s1 - e[0], s2 - e[1])) / (2 * eps)
+
+    def h(s1, s2, k):
+        return np.linalg.norm(tangent(s1, s2, k))
+
+    for i in (0, 7, 23, 39):
+        x1, x2 = i + 0.5, 2.0
+        g1, g2 = tangent(x1, x2, 1), tangent(x1, x2, 2)
+        assert abs(g1 @ g2) < 1e-7 * np.linalg.norm(g1) * np.linalg.norm(g2)
+        assert h(x1, x2, 1) == pytest.approx(m.h1[0, i], rel=1e-7)
+        assert h(x1, x2, 2) == pytest.approx(m.h2[0, i], rel=1e-7)
+        H1, H2 = m.h1[0, i], m.h2[0, i]
+        t11 = (h(x1 + dl, x2, 1) - h(x1 - dl, x2, 1)) / (2 * dl) / H1 ** 2
+        t21 = (h(x1 + dl, x2, 2) - h(x1 - dl, x2, 2)) / (2 * dl) / (H1 * H2)
+        t12 = (h(x1, x2 + dl, 1) - h(x1, x2 - dl, 1)) / (2 * dl) / (H1 * H2)
+        t22 = (h(x1, x2 + dl, 2) - h(x1, x2 - dl, 2)) / (2 * dl) / H2 ** 2
+        assert t11 == pytest.approx(m.t11[0, i], rel=1e-5)
+        assert t21 == pytest.approx(m.t21[0, i], rel=1e-5)
+        assert abs(t12) < 1e-4 * m.t11[0, i] and abs(t22) < 1e-4 * m.t11[0, i]
+        assert m.t11[0, i] == pytest.approx(1.0 / (a * math.exp(math.log(ro / a) * x1 / n1)), rel=1e-12)
+    assert np.all(m.t12 == 0) and np.all(m.t22 == 0)
+
+
+def _taylor_couette_error(n1, tau=1.0, threads=4):
+    """Steady azimuthal profile on the annular sector (radius ratio 9, h1, h2
+    as on the paper's 256 x 6 grid with 60 sectors) against Sec. 8.2's
+    analytic solution; inner wall U0, outer 1.5 U0, diffusive scaling (tau
+    fixed, U0 = 0.01 * 16 / n1)."""
+    a = n1 / 8.0
+    sectors = 360.0 * n1 / (256.0 * 6.0)
+    p0 = gi.taylor_couette(n1=n1, n2=6, r_in=a, sectors=sectors)
+    m = oracle.build_metric(p0.lattice_spec(1.0))
+    cs2 = m.cs2()
+    U0 = 0.01 * 16.0 / n1
+    p = gi.taylor_couette(n1=n1, n2=6, r_in=a, sectors=sectors, Re=U0 * n1 / (cs2 * (tau - 0.5)), U0=U0)
+    spec = p.lattice_spec(cs2)
+    ua = gi.taylor_couette_profile(m.radius, a, a + n1, U0, 1.5 * U0)
+    spec["init"] = {"u1": 0.0, "u2": np.broadcast_to(ua[None, :], (6, n1)).copy()}
+    o = oracle.Oracle(spec, threads=threads)
+    o.step(int(1.0 * n1 * n1 / spec["nu"]))
+    rho, u1, u2, *_ = o.fields()
+    return np.linalg.norm(u2[0] - ua) / np.linalg.norm(ua), np.abs(u1).max() / np.abs(ua).max()
+
+
+def test_taylor_couette_on_the_annulus_converges_at_second_order():
+    """Sec. 8.2 on the curvilinear grid: every curvature term is active
+    (theta11 = theta21 = 1/r in the effective force, tau^c, the local shear
+    stress of Appendix A and the corrections).  The steady u_theta(r)
+    approaches the analytic solution at second order in the radial nodes and
+    the radial velocity vanishes."""
+    res = [_taylor_couette_error(n) for n in (12, 24, 48)]
+    e = [x[0] for x in res]
+    orders = [math.log2(e[k] / e[k + 1]) for k in range(2)]
+    assert e[-1] < 1e-3, e
+    assert min(orders) > 1.8, (e, orders)
+    assert all(x[1] < 1e-3 for x in res), res
+
+
+def test_mass_is_conserved_on_the_annulus_with_moving_walls():
+    p = gi.taylor_couette(n1=24, n2=6, r_in=3.0, sectors=360.0 * 24 / (256.0 * 6.0), Re=10.0)
+    m = oracle.build_metric(p.lattice_spec(1.0))
+    o = oracle.Oracle(p.lattice_spec(m.cs2()))
+    mass0 = (o.fields()[0] * m.h1 * m.h2).sum()
+    o.step(4000)
+    assert abs((o.fields()[0] * m.h1 * m.h2).sum() - mass0) / mass0 < 1e-12
