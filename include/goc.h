@@ -66,10 +66,18 @@ typedef enum { GOC_BC_PERIODIC = 0, GOC_BC_WALL = 1 } goc_bc;
  *  SINH     clustering around an interior point x_c = yc N, Eq. Holst_transformation,
  *           Eq. B_Holst, Eq. h_2_Holst (Sec. 6.4):
  *           x = x_c [1 + sinh(mu(eta - B))/sinh(mu B)].
+ *  ANNULUS  (xi1 only) the curvilinear annular sector of Sec. 8.1 between radii
+ *           r_inner and r_outer spanning 2 pi / sectors of the circle, by the
+ *           conformal map of Eq. 2_annularsector scaled to the lattice (Eq.
+ *           5_annularsector) with cell-centred radial nodes:
+ *           r = r_inner exp(ln(r_outer/r_inner) xi1/nx), h1 = r ln(r_outer/r_inner)/nx,
+ *           h2 = 2 pi r/(sectors ny), theta11 = theta21 = 1/r, theta12 = theta22 = 0.
+ *           Needs W/E walls, periodic S/N, kind[1] = UNIFORM, scheme 0, no MIE;
+ *           not for batches.  Wall speeds (wall_u[W], wall_u[E]) are azimuthal.
  * Wall maps (TANH2 with beta > 0, ROBERTS, TANH1, SINH) need a wall axis; SINE a
  * periodic one. */
 typedef enum { GOC_MAP_UNIFORM = 0, GOC_MAP_TANH2 = 1, GOC_MAP_SINE = 2, GOC_MAP_ROBERTS = 3,
-               GOC_MAP_TANH1 = 4, GOC_MAP_SINH = 5 } goc_map_kind;
+               GOC_MAP_TANH1 = 4, GOC_MAP_SINH = 5, GOC_MAP_ANNULUS = 6 } goc_map_kind;
 
 typedef struct {
     int nx, ny;             /* nodes along xi1, xi2; >= 3 along a wall axis, >= 1 otherwise */
@@ -88,6 +96,8 @@ typedef struct {
     double alpha[2];        /* ROBERTS alpha (0 or 1/2) */
     double mu[2];           /* SINH clustering strength (> 0) */
     double yc[2];           /* SINH clustering point as a fraction of the axis length, in (0, 1) */
+    double r_inner, r_outer;  /* ANNULUS radii, 0 < r_inner < r_outer */
+    double sectors;           /* ANNULUS: the sector spans 2 pi / sectors (> 0) */
 } goc_map;
 
 typedef struct {

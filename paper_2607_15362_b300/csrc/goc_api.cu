@@ -174,18 +174,18 @@ bool encode_lattice_maps(goc_lattice *L) {
 }
 
 // Dynamic shared memory of a step kernel and its persistent grid size.
-template <class S, bool MHD, bool SRT = false>
+template <class S, bool MHD, bool SRT = false, bool CURV = false>
 int step_grid(int ntiles, size_t *smem) {
     using T = Tiling<S>;
     const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
     *smem = bytes;
     static int cached = -1;
     if (cached < 0) {
-        cudaFuncSetAttribute(step_kernel<S, MHD, SRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cudaFuncSetAttribute(step_kernel<S, MHD, SRT, CURV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD, SRT>, NT, bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD, SRT, CURV>, NT, bytes);
         cached = std::max(1, sms * std::max(1, per));
     }
     return std::min(ntiles, cached);
@@ -204,7 +204,10 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
     const bool pdl = L->cfg_pdl != 0;
-    if (L->scheme == 2 || L->scheme == 3) {   // collision on raw moments (Appendix F SRT, Appendix D MRT)
+    if (L->sp.curv) {   // curvilinear column metric (central-moment collision, no MIE)
+        const int grid = step_grid<S, false, false, true>(ntiles, &smem);
+        CU(launch_pdl(pdl, step_kernel<S, false, false, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+    } else if (L->scheme == 2 || L->scheme == 3) {   // collision on raw moments (Appendix F SRT, Appendix D MRT)
         if (L->mhd.enabled) {
             const int grid = step_grid<S, true, true>(ntiles, &smem);
             CU(launch_pdl(pdl, step_kernel<S, true, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
@@ -377,8 +380,16 @@ goc_status validate(const goc_grid *grid, const goc_map *map) {
     if (grid->bc[2] == GOC_BC_WALL && grid->ny < 3) return fail(GOC_EINVAL, "a wall axis needs >= 3 nodes");
     for (int a = 0; a < 2; a++) {
         int k = map->kind[a];
-        if (k < 0 || k > 5) return fail(GOC_EINVAL, "map kind[%d] = %d unknown", a, k);
+        if (k < 0 || k > 6) return fail(GOC_EINVAL, "map kind[%d] = %d unknown", a, k);
         int per = grid->bc[a == 0 ? 0 : 2] == GOC_BC_PERIODIC;
+        if (k == GOC_MAP_ANNULUS) {
+            if (a != 0) return fail(GOC_EINVAL, "the annulus map is a xi1 (radial) map");
+            if (per || grid->bc[2] != GOC_BC_PERIODIC || map->kind[1] != GOC_MAP_UNIFORM)
+                return fail(GOC_EINVAL, "the annulus needs W/E walls, periodic S/N and a uniform xi2 map");
+            if (!(map->r_inner > 0.0 && map->r_outer > map->r_inner && map->sectors > 0.0))
+                return fail(GOC_EINVAL, "the annulus needs 0 < r_inner < r_outer and sectors > 0");
+            continue;
+        }
         const bool wall_map = k == GOC_MAP_ROBERTS || k == GOC_MAP_TANH1 || k == GOC_MAP_SINH ||
                               (k == GOC_MAP_TANH2 && map->beta[a] != 0.0);
         if (wall_map && per) return fail(GOC_EINVAL, "axis %d: wall-clustering map on a periodic axis", a);
@@ -408,16 +419,27 @@ MapParams map_params(const goc_grid *grid, const goc_map *map, int axis) {
     m.alpha = map->alpha[axis];
     m.mu = map->mu[axis];
     m.yc = map->yc[axis];
+    m.r_in = map->r_inner;
+    m.r_out = map->r_outer;
+    m.sectors = map->sectors;
+    m.n2 = grid->ny;
     return m;
 }
 
 // FP64 metric of both axes on the device: d1, d2 = [2][n+2] (h, theta); q.
+// Annulus: d1 = [4][n1+2] (h1, theta11, h2, theta21 over xi1) and q is the
+// smallest of h1 and h2 over the nodes.
 goc_status compute_metric(const goc_grid *grid, const goc_map *map, cudaStream_t st,
                           double *d1, double *d2, double *qdev) {
     MapParams a = map_params(grid, map, 0), b = map_params(grid, map, 1);
-    metric_axis_kernel<<<(a.n + 2 + 127) / 128, 128, 0, st>>>(a, d1, d1 + a.n + 2);
     metric_axis_kernel<<<(b.n + 2 + 127) / 128, 128, 0, st>>>(b, d2, d2 + b.n + 2);
-    min_h_kernel<<<1, 256, 0, st>>>(d1, a.n, d2, b.n, qdev);
+    if (a.kind == GOC_MAP_ANNULUS) {
+        annulus_metric_kernel<<<(a.n + 2 + 127) / 128, 128, 0, st>>>(a, d1);
+        min_h_kernel<<<1, 256, 0, st>>>(d1, a.n, d1 + 2 * (a.n + 2), a.n, qdev);
+    } else {
+        metric_axis_kernel<<<(a.n + 2 + 127) / 128, 128, 0, st>>>(a, d1, d1 + a.n + 2);
+        min_h_kernel<<<1, 256, 0, st>>>(d1, a.n, d2, b.n, qdev);
+    }
     CU(cudaGetLastError());
     return GOC_OK;
 }
@@ -471,6 +493,8 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
     q.sp.Fout = L->F[L->cur];
     q.sp.gout = L->g[L->cur];
     q.h1d = L->m1;
+    q.h2x = L->sp.curv ? L->m1 + 2 * (L->nx + 2) : nullptr;
+    q.t21x = L->sp.curv ? L->m1 + 3 * (L->nx + 2) : nullptr;
     q.t1d = L->m1 + L->nx + 2;
     q.h2d = L->m2;
     q.t2d = L->m2 + L->ny + 2;
@@ -550,10 +574,10 @@ goc_status goc_metric_info(const goc_grid *grid, const goc_map *map, double *q, 
     if (st != GOC_OK) return st;
     double *d = nullptr;
     size_t n1 = grid->nx + 2, n2 = grid->ny + 2;
-    CU(cudaMalloc(&d, (2 * n1 + 2 * n2 + 1) * sizeof(double)));
-    st = compute_metric(grid, map, 0, d, d + 2 * n1, d + 2 * n1 + 2 * n2);
+    CU(cudaMalloc(&d, (4 * n1 + 2 * n2 + 1) * sizeof(double)));
+    st = compute_metric(grid, map, 0, d, d + 4 * n1, d + 4 * n1 + 2 * n2);
     double qh = 0;
-    cudaError_t e = cudaMemcpy(&qh, d + 2 * n1 + 2 * n2, sizeof(double), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(&qh, d + 4 * n1 + 2 * n2, sizeof(double), cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (st != GOC_OK) return st;
     if (e != cudaSuccess) return fail(GOC_ECUDA, "metric copy failed: %s", cudaGetErrorString(e));
@@ -579,6 +603,10 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         if (!uni) return fail(GOC_EINVAL, "the standard uniform-grid scheme needs uniform maps on both axes");
         if (flow->gi_correction) return fail(GOC_EINVAL, "the standard uniform-grid scheme needs gi_correction = 0");
         if (mhd && mhd->enabled) return fail(GOC_EINVAL, "the standard uniform-grid scheme has no MIE");
+    }
+    if (map->kind[0] == GOC_MAP_ANNULUS) {
+        if (mhd && mhd->enabled) return fail(GOC_EUNSUPPORTED, "the annulus runs without the MIE");
+        if (exec && exec->scheme != 0) return fail(GOC_EUNSUPPORTED, "the annulus runs the central-moment scheme (0)");
     }
     goc_lattice *L = new (std::nothrow) goc_lattice();
     if (!L) return fail(GOC_ENOMEM, "host allocation failed");
@@ -631,9 +659,10 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         TRY(dalloc(L, &L->F[b], 2 * L->plane * es));
         if (L->mhd.enabled) TRY(dalloc(L, &L->g[b], 10 * L->plane * es));
     }
-    TRY(dalloc(L, &L->tab1, 7 * (size_t)L->nx * sizeof(float)));
+    const bool curv = map->kind[0] == GOC_MAP_ANNULUS;
+    TRY(dalloc(L, &L->tab1, (curv ? 8 : 7) * (size_t)L->nx * sizeof(float)));
     TRY(dalloc(L, &L->tab2, 7 * (size_t)L->ny * sizeof(float)));
-    TRY(dalloc(L, &L->m1, 2 * (size_t)(L->nx + 2) * sizeof(double)));
+    TRY(dalloc(L, &L->m1, (curv ? 4 : 2) * (size_t)(L->nx + 2) * sizeof(double)));
     TRY(dalloc(L, &L->m2, 2 * (size_t)(L->ny + 2) * sizeof(double)));
     TRY(dalloc(L, &L->flag, 8 * sizeof(int)));   // [0] status, [1] spare, [2..3] step counters, [4..5] tile queues of the two parities
     TRY(dalloc(L, &L->red, 8 * sizeof(double)));
@@ -677,8 +706,11 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     L->hw[3] = hw2[1];
     const double rho0cs2 = L->flow.rho0 * L->cs2;
     const int per_x = grid->bc[0] == GOC_BC_PERIODIC, per_y = grid->bc[2] == GOC_BC_PERIODIC;
-    axis_tables_kernel<<<(L->nx + 127) / 128, 128, 0, L->stream>>>(L->m1, L->m1 + L->nx + 2, L->nx, per_x, rho0cs2,
-                                                                   L->cs2, L->tab1);
+    if (curv)
+        annulus_tables_kernel<<<(L->nx + 127) / 128, 128, 0, L->stream>>>(L->m1, L->nx, rho0cs2, L->tab1);
+    else
+        axis_tables_kernel<<<(L->nx + 127) / 128, 128, 0, L->stream>>>(L->m1, L->m1 + L->nx + 2, L->nx, per_x,
+                                                                       rho0cs2, L->cs2, L->tab1);
     axis_tables_kernel<<<(L->ny + 127) / 128, 128, 0, L->stream>>>(L->m2, L->m2 + L->ny + 2, L->ny, per_y, rho0cs2,
                                                                    L->cs2, L->tab2);
     {
@@ -710,6 +742,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     };
     p.ax1 = axis(L->tab1, L->nx);
     p.ax2 = axis(L->tab2, L->ny);
+    p.curv = curv ? 1 : 0;   // the xi1 table then holds h2, 1/h2, theta21 in rows 5-7
     p.rho0 = (float)L->flow.rho0;
     p.cs2 = (float)L->cs2;
     p.ics2 = (float)(1.0 / L->cs2);
@@ -1259,6 +1292,7 @@ goc_status goc_batch_add(goc_batch *B, const goc_grid *grid, const goc_map *map,
     if (!B || !slot) return fail(GOC_EINVAL, "batch and slot are required");
     *slot = -1;
     if (!grid) return fail(GOC_EINVAL, "grid is required");
+    if (map && map->kind[0] == GOC_MAP_ANNULUS) return fail(GOC_EUNSUPPORTED, "annulus lattices are not batched");
     int free_slot = -1;
     for (int k = 0; k < B->max_lat; k++)
         if (!B->slots[k]) {

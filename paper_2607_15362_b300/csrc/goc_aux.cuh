@@ -11,9 +11,11 @@ namespace goc {
 // Eq. curvaturematrix).  Entries 0..n-1 are the nodes, n and n+1 the walls
 // at xi = 0 and xi = n.
 struct MapParams {
-    int kind;          // 0 uniform, 1 tanh2, 2 sine, 3 roberts, 4 tanh1 (one wall), 5 sinh (interior)
+    int kind;          // 0 uniform, 1 tanh2, 2 sine, 3 roberts, 4 tanh1 (one wall), 5 sinh (interior), 6 annulus
     int n, periodic;
     double beta, a, gamma, alpha, mu, yc;
+    double r_in, r_out, sectors;   // annulus (xi1 axis)
+    int n2;                        // annulus: nodes along xi2
 };
 
 __device__ void map_h_theta(const MapParams &m, double xi, double &h, double &th) {
@@ -63,6 +65,21 @@ __global__ void metric_axis_kernel(MapParams m, double *h, double *th) {
     th[k] = tv;
 }
 
+// Annular sector (Sec. 8.1, Eq. 2_annularsector / 5_annularsector): rows
+// h1, theta11, h2, theta21 as functions of xi1, each [n + 2] (nodes, then the
+// walls xi1 = 0 and n); r = r_in exp(ln(r_out/r_in) xi1/n).
+__global__ void annulus_metric_kernel(MapParams m, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m.n + 2) return;
+    const double xi = k < m.n ? (double)k + 0.5 : (k == m.n ? 0.0 : (double)m.n);
+    const double lam = log(m.r_out / m.r_in), r = m.r_in * exp(lam * xi / m.n);
+    const int w = m.n + 2;
+    out[k] = r * lam / m.n;
+    out[w + k] = 1.0 / r;
+    out[2 * w + k] = 2.0 * 3.14159265358979323846 * r / (m.sectors * m.n2);
+    out[3 * w + k] = 1.0 / r;
+}
+
 // q = min over the nodes of both axes (Eq. GOC-LBE_CFL): one block.
 __global__ void min_h_kernel(const double *h1, int n1, const double *h2, int n2, double *q) {
     __shared__ double red[32];
@@ -106,12 +123,38 @@ __global__ void axis_tables_kernel(const double *h, const double *th, int n, int
     out[6 * n + k] = has_p ? (float)(W1 * (h[kp] - h[k]) - 0.25 * csm2 * (htp + ht)) : 0.f;
 }
 
+// FP32 tables of the curvilinear column metric ([10][n], layout of Axis): h1,
+// 1/h1, theta11, the full pull corrections of links 1 and 3,
+//   rm[k] = f_ref+,1(k-1) - f_ref-,1(k) = rho0 cs2 (r(k-1) - r(k))/2 + (Fr(k-1) + Fr(k))/4,
+//   rp[k] = f_ref+,3(k+1) - f_ref-,3(k) = rho0 cs2 (r(k+1) - r(k))/2 - (Fr(k+1) + Fr(k))/4,
+// with r = h2/h1 and the rest-state force Fr = h2 (theta21 - theta11) rho0 cs2
+// (Eq. bodyforce1 at U = 0), then h2, 1/h2, theta21 in the rows the MIE
+// corrections take on straight grids ([8][n]).
+// The xi1 axis has walls, so k - 1 / k + 1 beyond them are never pulled from.
+__global__ void annulus_tables_kernel(const double *m, int n, double rho0cs2, float *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int w = n + 2;
+    const double *h1 = m, *t11 = m + w, *h2 = m + 2 * w, *t21 = m + 3 * w;
+    auto rr = [&](int q) { return h2[q] / h1[q]; };
+    auto fr = [&](int q) { return h2[q] * (t21[q] - t11[q]) * rho0cs2; };
+    out[0 * n + k] = (float)h1[k];
+    out[1 * n + k] = (float)(1.0 / h1[k]);
+    out[2 * n + k] = (float)t11[k];
+    out[3 * n + k] = k > 0 ? (float)(0.5 * rho0cs2 * (rr(k - 1) - rr(k)) + 0.25 * (fr(k - 1) + fr(k))) : 0.f;
+    out[4 * n + k] = k < n - 1 ? (float)(0.5 * rho0cs2 * (rr(k + 1) - rr(k)) - 0.25 * (fr(k + 1) + fr(k))) : 0.f;
+    out[5 * n + k] = (float)h2[k];
+    out[6 * n + k] = (float)(1.0 / h2[k]);
+    out[7 * n + k] = (float)t21[k];
+}
+
 // ---- initial state (Appendix C.1): f = P^-1 m^eq,eff(rho, U), gradients by
 // the same second-order differences as the step; g = g^eq(0) + g^corr.
 // FP64 arithmetic (one-off).  Fields are [ny][nx] doubles on the device.
 struct InitParams {
     StepParams sp;
     const double *h1d, *h2d, *t1d, *t2d;   // FP64 node metric per axis
+    const double *h2x, *t21x;              // curvilinear column metric: h2, theta21 over xi1 (else null)
     double cs2, nu, zeta, rho0, csm2, eta;
     int gi, mhd;
     const double *rho, *u1, *u2, *b1, *b2;
@@ -137,7 +180,9 @@ __global__ void init_kernel(const InitParams q) {
     const int j = blockIdx.y;
     if (i >= p.nx || j >= p.ny) return;
     const long long n = (long long)j * p.nx + i, idx = (long long)j * p.pitch + i;
-    const double h1 = q.h1d[i], h2 = q.h2d[j], t11 = q.t1d[i], t22 = q.t2d[j];
+    const bool curv = q.h2x != nullptr;
+    const double h1 = q.h1d[i], h2 = curv ? q.h2x[i] : q.h2d[j], t11 = q.t1d[i], t22 = curv ? 0.0 : q.t2d[j];
+    const double t21 = curv ? q.t21x[i] : 0.0;   // theta12 = 0 on both grid families
     const double rho = q.rho[n], U1 = q.u1[n], U2 = q.u2[n];
     const double dU1 = dfd64(q.u1, i, j, p.nx, p.ny, 0, p.per_x);
     const double dU2 = dfd64(q.u2, i, j, p.nx, p.ny, 1, p.per_y);
@@ -146,21 +191,26 @@ __global__ void init_kernel(const InitParams q) {
     const double cs2 = q.cs2, nu = q.nu, ze = q.zeta;
     const double gi = q.gi ? 1.0 : 0.0;
     const double a1 = gi * U1 * U1 / cs2, a2 = gi * U2 * U2 / cs2;
-    // Eqs. 83 / 85 on a straight grid (theta12 = theta21 = 0)
+    // Eqs. 83 / 85 with theta12 = 0 (theta21 on the curvilinear column metric)
+    const double tc11 = rho * (ze - nu) * U1 * t21, tc22 = rho * (ze + nu) * U1 * t21;   // Eq. tauc
     const double D31 = rho * (2 * ze - (ze + nu) * h2 / (h1 * h1) - (ze - nu) / h2
                               - ze * (2 - h2 / cs2 + (3 * a1 + 1) * h2 / (h1 * h1)));
     const double D32 = rho * (2 * ze - (ze + nu) * h1 / (h2 * h2) - (ze - nu) / h1
                               - ze * (2 - h1 / cs2 + (3 * a2 + 1) * h1 / (h2 * h2)));
     const double D33 = -ze * ((3 - a1) * h2 / (h1 * h1) - h2 / cs2 - a2 / h2) * U1;
     const double D34 = -ze * ((3 - a2) * h1 / (h2 * h2) - h1 / cs2 - a1 / h1) * U2;
-    const double C3 = rho * ze * (2 * U1 * (a1 + 1) * h2 / h1 * t11 + 2 * U2 * (a2 + 1) * h1 / h2 * t22);
+    const double C3 = rho * ze * (2 * U1 * (a1 + 1) * h2 / h1 * t11 + 2 * U2 * (a2 + 1) * h1 / h2 * t22)
+                      - (h2 / h1 * tc11 + h1 / h2 * tc22)
+                      - rho * ze * U1 * ((3 + a1) * h2 / h1 + 2 * h1 / h2 - h1 * h2 / cs2) * t21;
     const double D41 = rho * (2 * nu - (ze + nu) * h2 / (h1 * h1) + (ze - nu) / h2
                               - nu * (2 - h2 / cs2 + (3 * a1 + 1) * h2 / (h1 * h1)));
     const double D42 = rho * (-2 * nu + (ze + nu) * h1 / (h2 * h2) - (ze - nu) / h1
                               - nu * (-2 + h1 / cs2 - (3 * a2 + 1) * h1 / (h2 * h2)));
     const double D43 = -nu * ((3 - a1) * h2 / (h1 * h1) - h2 / cs2 + a2 / h2) * U1;
     const double D44 = -nu * (-(3 - a2) * h1 / (h2 * h2) + h1 / cs2 - a1 / h1) * U2;
-    const double C4 = rho * nu * (2 * U1 * (a1 + 1) * h2 / h1 * t11 - 2 * U2 * (a2 + 1) * h1 / h2 * t22);
+    const double C4 = rho * nu * (2 * U1 * (a1 + 1) * h2 / h1 * t11 - 2 * U2 * (a2 + 1) * h1 / h2 * t22)
+                      - (h2 / h1 * tc11 - h1 / h2 * tc22)
+                      - rho * nu * U1 * ((3 + a1) * h2 / h1 - 2 * h1 / h2 - h1 * h2 / cs2) * t21;
     const double n3 = D31 * dU1 + D32 * dU2 + D33 * dr1 + D34 * dr2 + C3;
     const double n4 = D41 * dU1 + D42 * dU2 + D43 * dr1 + D44 * dr2 + C4;
     // m^eq,eff - m_rest(rho0), bare order (Eq. GOCmomentequilibria)
@@ -187,7 +237,7 @@ __global__ void init_kernel(const InitParams q) {
     d[7] = 0.25 * (m5 - m6 - m7 + m8);
     d[8] = 0.25 * (-m5 - m6 + m7 + m8);
     // pre-collision reference f_ref- = f_rest - F_rest/4 on links 1, 3 (xi1) and 2, 4 (xi2)
-    const double F1r = -h2 * q.rho0 * cs2 * t11, F2r = -h1 * q.rho0 * cs2 * t22;
+    const double F1r = h2 * q.rho0 * cs2 * (t21 - t11), F2r = -h1 * q.rho0 * cs2 * t22;
     d[1] += 0.25 * F1r;
     d[3] -= 0.25 * F1r;
     d[2] += 0.25 * F2r;
@@ -195,8 +245,8 @@ __global__ void init_kernel(const InitParams q) {
     S *fout = static_cast<S *>(p.fout);
     for (int a = 0; a < 9; a++) Store<S>::st(fout + a * p.plane + idx, (float)(d[a] * p.isf));
     S *Fout = static_cast<S *>(p.Fout);   // F^{-1} = 0, i.e. F_dev = -F_rest
-    Store<S>::st(Fout + idx, (float)(h2 * q.rho0 * cs2 * t11 * p.isF));
-    Store<S>::st(Fout + p.plane + idx, (float)(h1 * q.rho0 * cs2 * t22 * p.isF));
+    Store<S>::st(Fout + idx, (float)(-F1r * p.isF));
+    Store<S>::st(Fout + p.plane + idx, (float)(-F2r * p.isF));
     if (!q.mhd) return;
     S *gout = static_cast<S *>(p.gout);
     const double B[2] = {q.b1[n], q.b2[n]}, U[2] = {U1, U2};
@@ -228,14 +278,15 @@ __global__ void moments_kernel(const StepParams p, double *out) {
     if (i >= p.nx || j >= p.ny) return;
     const SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                            p.plane, p.pitch, p.sf, p.sF, p.sg};
-    const float h1 = p.ax1.h[i], h2 = p.ax2.h[j];
+    const float h1 = p.ax1.h[i], h2 = p.curv ? curv_h2(p.ax1, i) : p.ax2.h[j];
     float d[9];
-    pull_node<true>(p, src, i, j, h1, h2, d);
+    if (p.curv) pull_node<true, true>(p, src, i, j, h1, h2, d);
+    else pull_node<true>(p, src, i, j, h1, h2, d);
     float drho, U1, U2;
     // F - F_rest of the previous step (the body force, or zero before the first step, without a stored force)
     const float F1p = p.constF ? (p.nopull ? 0.f : p.fext1) : src.Fv(0, i, j);
     const float F2p = p.constF ? (p.nopull ? 0.f : p.fext2) : src.Fv(1, i, j);
-    fields_from(p, d, F1p, F2p, p.ax1.ih[i], p.ax2.ih[j], drho, U1, U2);
+    fields_from(p, d, F1p, F2p, p.ax1.ih[i], p.curv ? curv_ih2(p.ax1, i) : p.ax2.ih[j], drho, U1, U2);
     const long long N = (long long)p.nx * p.ny, n = (long long)j * p.nx + i;
     out[n] = (double)p.rho0 + (double)drho;
     out[N + n] = U1;
@@ -291,7 +342,7 @@ __global__ void mass_kernel(const StepParams p, double *out) {
         const long long idx = (long long)j * p.pitch + i;
         double s = 0.0;
         for (int a = 0; a < 9; a++) s += (double)Store<S>::ld(f + a * p.plane + idx) * p.sf;
-        acc[0] += s + (double)p.ax1.h[i] * (double)p.ax2.h[j] * p.rho0;
+        acc[0] += s + (double)p.ax1.h[i] * (double)(p.curv ? curv_h2(p.ax1, i) : p.ax2.h[j]) * p.rho0;
     }
     block_add<1>(acc, out);
 }

@@ -33,13 +33,22 @@ struct Axis {
     const float *rp;   // rest-state pull correction, source k+1: 0.5 rho0 cs2 (1/h(k+1) - 1/h(k))
     const float *dm;   // MIE pull corrections, source k-1: W1 (h(k-1) - h(k)) + csm2 (h^2 theta(k-1) + h^2 theta(k))/4
     const float *dp;   //                      source k+1: W1 (h(k+1) - h(k)) - csm2 (h^2 theta(k+1) + h^2 theta(k))/4
+    // Curvilinear column metric (annular sector; xi1 axis, no MIE): rm/rp hold
+    // the full pull corrections of links 1/3 (not per unit h2), and the rows
+    // dm, dp, dp + n hold h2, 1/h2 and theta21 as functions of xi1.
 };
+
+// the curvilinear column metric of node column i (see Axis)
+__device__ __forceinline__ float curv_h2(const Axis &a, int i) { return a.dm[i]; }
+__device__ __forceinline__ float curv_ih2(const Axis &a, int i) { return a.dp[i]; }
+__device__ __forceinline__ float curv_t21(const Axis &a, int n, int i) { return a.dp[n + i]; }
 
 // Everything one step needs, passed by value.
 struct StepParams {
     int nx, ny, pitch;         // pitch in elements (multiple of 32)
     long long plane;           // ny * pitch
     int per_x, per_y;          // periodic axes
+    int curv;                  // 1: curvilinear column metric (h1, h2, theta11, theta21 functions of xi1)
     int nopull;                // 1: the input buffer holds pre-collision populations (the
                                // initial state f^0 of Appendix C.1): read them in place
     const void *fin;           // [9][plane] stored post-collision deviations (input)

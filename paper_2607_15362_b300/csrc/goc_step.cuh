@@ -153,7 +153,7 @@ template <class S> struct SrcSmem {        // the TMA-staged tile
 // e2 rho_w cs2 u / (2 h1_w) across a W/E wall (rho_w: this node's density at
 // the time of the outgoing population).  CHECKS = false: every source is
 // inside the lattice (interior tile).
-template <bool CHECKS, class Src>
+template <bool CHECKS, bool CURV = false, class Src>
 __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, int i, int j, float h1, float h2,
                                           float d[9]) {
     if (p.nopull) {
@@ -178,8 +178,8 @@ __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, i
         float v;
         if (!ox && !oy) {
             v = src.fv(a, si, sj);
-            if (a == 1) v += h2 * p.ax1.rm[i];
-            if (a == 3) v += h2 * p.ax1.rp[i];
+            if (a == 1) v += CURV ? p.ax1.rm[i] : h2 * p.ax1.rm[i];   // curvilinear: full corrections
+            if (a == 3) v += CURV ? p.ax1.rp[i] : h2 * p.ax1.rp[i];
             if (a == 2) v += h1 * p.ax2.rm[j];
             if (a == 4) v += h1 * p.ax2.rp[j];
         } else {
@@ -391,7 +391,7 @@ __device__ __forceinline__ void raw_relax(const StepParams &p, const V (&d)[9], 
 // step, the fields and their normal derivatives fl[k][r] (k: drho, U1, U2,
 // dU1/dxi1, drho/dxi1, dU2/dxi2, drho/dxi2), and the stores.  own[r]: whether
 // node r is a lattice node this thread updates.
-template <class S, bool MHD, bool CHECKS, class V, bool SRT, class Src>
+template <class S, bool MHD, bool CHECKS, class V, bool SRT, bool CURV, class Src>
 __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int i, const int (&j)[Lanes<V>::R],
                                         const bool (&own)[Lanes<V>::R], const float (&dn)[Lanes<V>::R][9],
                                         const float (&F1pn)[Lanes<V>::R], const float (&F2pn)[Lanes<V>::R], float h1,
@@ -400,7 +400,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     constexpr int R = Lanes<V>::R;
     float th_[R];
 #pragma unroll
-    for (int r = 0; r < R; r++) th_[r] = p.ax2.th[own[r] ? j[r] : j[0]];
+    for (int r = 0; r < R; r++) th_[r] = CURV ? 0.f : p.ax2.th[own[r] ? j[r] : j[0]];   // theta22
     const V drho = pack<V>(fl[0]), U1 = pack<V>(fl[1]), U2 = pack<V>(fl[2]);
     const V dU1 = pack<V>(fl[3]), dr1 = pack<V>(fl[4]), dU2 = pack<V>(fl[5]), dr2 = pack<V>(fl[6]);
     const V t22 = pack<V>(th_);
@@ -503,13 +503,38 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     // ---- stresses and effective force (straight grid, Appendix B (i)) -------
     const float zeta = p.zeta, nu = p.nu;
     const V g1d = dU1 * ih1, g2d = dU2 * ih2;             // dU1/(h1 dxi1), dU2/(h2 dxi2)
-    const V tau11 = rho * fmav(g1d, zeta + nu, g2d * (zeta - nu));
-    const V tau22 = rho * fmav(g2d, zeta + nu, g1d * (zeta - nu));
+    V tau11 = rho * fmav(g1d, zeta + nu, g2d * (zeta - nu));
+    V tau22 = rho * fmav(g2d, zeta + nu, g1d * (zeta - nu));
     // F = F_rest + F_dev, F_rest = -(h2, h1) rho0 cs2 (theta11, theta22) is the
     // geometric force of the rest state; only F_dev is stored.
-    const V F1dev = h2 * fmav(tau11 - rho * (U1 * U1) - drho * cs2, t11, FL1 + p.fext1);
-    const V F2dev = fmav(tau22 - rho * (U2 * U2) - drho * cs2, t22, FL2 + p.fext2) * h1;
-    const V F1r = h2 * (-p.rho0 * cs2 * t11), F2r = t22 * (-p.rho0 * cs2 * h1);
+    V F1dev, F2dev, F1r, F2r, tc11 = bc<V>(0.f), tc22 = bc<V>(0.f);
+    float t21 = 0.f;
+    if constexpr (CURV) {
+        // curvilinear column metric (theta12 = theta22 = 0, theta21 != 0):
+        // tau^c (Eq. tauc), the full effective force (Eqs. bodyforce1/2) and
+        // the local shear stress of Appendix A; F_rest = (h2 (theta21 -
+        // theta11) rho0 cs2, 0)
+        t21 = curv_t21(p.ax1, p.nx, i);
+        tc11 = rho * U1 * ((zeta - nu) * t21);
+        tc22 = rho * U1 * ((zeta + nu) * t21);
+        tau11 = tau11 + tc11;
+        tau22 = tau22 + tc22;
+        const V csd_ = drho * cs2;
+        F1dev = h2 * (fmav(tau11 - rho * (U1 * U1) - csd_, t11, FL1 + p.fext1) - (tau22 - rho * (U2 * U2) - csd_) * t21);
+        F1r = h2 * ((t21 - t11) * p.rho0 * cs2);
+        F2r = bc<V>(0.f);
+        const V Ft2 = h1 * (FL2 + p.fext2 - rho * U1 * U2 * (2.f * t21));
+        const V k11 = d[5] - d[6] + d[7] - d[8];          // raw k11 of f (f_ref- has none)
+        const float c5 = 1.f - 0.5f * p.om[5];
+        const V tau12 = (bc<V>(0.f) - c5) * (k11 + ((F1dev + F1r) * U2 * ih2 + Ft2 * U1 * ih1) * 0.5f - rho * U1 * U2) *
+                        rcpv(fmav(U1, c5 * t21, bc<V>(1.f)));
+        F2dev = fmav(tau12, 2.f * t21 * h1, Ft2);
+    } else {
+        F1dev = h2 * fmav(tau11 - rho * (U1 * U1) - drho * cs2, t11, FL1 + p.fext1);
+        F2dev = fmav(tau22 - rho * (U2 * U2) - drho * cs2, t22, FL2 + p.fext2) * h1;
+        F1r = h2 * (-p.rho0 * cs2 * t11);
+        F2r = t22 * (-p.rho0 * cs2 * h1);
+    }
     const V F1 = F1dev + F1r;
     const V F2 = F2dev + F2r;
 
@@ -538,6 +563,11 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         const V q4 = fmav(Y1 - Y2, nu, fmav(P41, dU1, P42 * dU2));
         n3 = rho * q3 - U1 * (X1 - b2) * dr1 * zeta - U2 * (X2 - b1) * dr2 * zeta;
         n4 = rho * q4 - U1 * (X1 + b2) * dr1 * nu + U2 * (X2 + b1) * dr2 * nu;
+        if constexpr (CURV) {   // theta21 parts of C3, C4 (theta12 = 0)
+            const V Hc = H * p.ics2, a13 = fmav(a1, r, 3.f * r);   // (3 + a1) h2/h1
+            n3 = n3 - fmav(r, tc11, s * tc22) - rho * U1 * (t21 * zeta) * (a13 + s * 2.f - Hc);
+            n4 = n4 - (r * tc11 - s * tc22) - rho * U1 * (t21 * nu) * (a13 - s * 2.f - Hc);
+        }
     }
 
     V o[9];
@@ -690,7 +720,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
 // Normal derivatives of the fields from the tile's field arrays (second
 // order: central, one-sided at the first and last node of a wall axis), then
 // the collision.
-template <class S, bool MHD, bool CHECKS, class V, bool SRT, class Src>
+template <class S, bool MHD, bool CHECKS, class V, bool SRT, bool CURV, class Src>
 __device__ __forceinline__ void node_update(const StepParams &p, const Src &src, int i, int tx,
                                             const int (&j)[Lanes<V>::R], const int (&ty)[Lanes<V>::R],
                                             const bool (&own)[Lanes<V>::R], const FieldSmem &sm,
@@ -719,7 +749,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
             fl[6][r] = 0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex]);
         }
     }
-    collide<S, MHD, CHECKS, V, SRT>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl);
+    collide<S, MHD, CHECKS, V, SRT, CURV>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl);
 }
 
 // One tile of one lattice from a given source; KIND 0: interior (no boundary
@@ -730,7 +760,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
 // barrier: every thread of the block must call it.  ok: this thread's wait
 // for the staged copy succeeded; false (returned by every thread) when any
 // thread's wait failed -- the block then leaves.
-template <class S, bool MHD, int KIND, bool SRT, class Src>
+template <class S, bool MHD, int KIND, bool SRT, bool CURV, class Src>
 __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src, int i0, int j0, FieldSmem &sm,
                                              bool ok) {
     constexpr bool CHECKS = KIND != 0;
@@ -762,9 +792,9 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
 #pragma unroll
         for (int a = 0; a < 9; a++) d[r][a] = 0.f;
         if (own[r]) {
-            h2[r] = p.ax2.h[j[r]];
-            ih2[r] = p.ax2.ih[j[r]];
-            pull_node<CHECKS>(p, src, i, j[r], h1, h2[r], d[r]);
+            h2[r] = CURV ? curv_h2(p.ax1, i) : p.ax2.h[j[r]];
+            ih2[r] = CURV ? curv_ih2(p.ax1, i) : p.ax2.ih[j[r]];
+            pull_node<CHECKS, CURV>(p, src, i, j[r], h1, h2[r], d[r]);
             F1p[r] = src.Fv(0, i, j[r]);
             F2p[r] = src.Fv(1, i, j[r]);
             fields_from(p, d[r], F1p[r], F2p[r], ih1, ih2[r], drho, U1, U2);
@@ -779,8 +809,9 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
             }
             if (in) {
                 float dd[9];
-                pull_node<CHECKS>(p, src, ii, jj, p.ax1.h[ii], p.ax2.h[jj], dd);
-                fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), p.ax1.ih[ii], p.ax2.ih[jj], drho, U1, U2);
+                pull_node<CHECKS, CURV>(p, src, ii, jj, p.ax1.h[ii], CURV ? curv_h2(p.ax1, ii) : p.ax2.h[jj], dd);
+                fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), p.ax1.ih[ii],
+                            CURV ? curv_ih2(p.ax1, ii) : p.ax2.ih[jj], drho, U1, U2);
             }
         }
         sm.rho[ty[r] + MH][tx + MH] = drho;
@@ -816,8 +847,9 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
         float drho = 0.f, U1 = 0.f, U2 = 0.f;
         if (in) {
             float dd[9];
-            pull_node<CHECKS>(p, src, ii, jj, p.ax1.h[ii], p.ax2.h[jj], dd);
-            fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), p.ax1.ih[ii], p.ax2.ih[jj], drho, U1, U2);
+            pull_node<CHECKS, CURV>(p, src, ii, jj, p.ax1.h[ii], CURV ? curv_h2(p.ax1, ii) : p.ax2.h[jj], dd);
+            fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), p.ax1.ih[ii], CURV ? curv_ih2(p.ax1, ii) : p.ax2.ih[jj],
+                        drho, U1, U2);
         }
         sm.rho[y + MH][x + MH] = drho;
         sm.u1[y + MH][x + MH] = U1;
@@ -827,7 +859,7 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
     bool any = false;
 #pragma unroll
     for (int r = 0; r < R; r++) any = any || own[r];
-    if (any) node_update<S, MHD, CHECKS, V, SRT>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
+    if (any) node_update<S, MHD, CHECKS, V, SRT, CURV>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
     return true;
 }
 
@@ -865,20 +897,20 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
-template <class S, bool MHD, bool SRT = false>
+template <class S, bool MHD, bool SRT = false, bool CURV = false>
 __device__ __forceinline__ bool run_tile(const StepParams &p, int kind, int i0, int j0, const unsigned char *stage,
                                          FieldSmem &sm, bool ok) {
     using T = Tiling<S>;
     if (kind == 2) {
         SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                          p.plane, p.pitch, p.sf, p.sF, p.sg};
-        return tile_compute<S, MHD, 1, SRT>(p, src, i0, j0, sm, ok);
+        return tile_compute<S, MHD, 1, SRT, CURV>(p, src, i0, j0, sm, ok);
     }
     SrcSmem<S> src{reinterpret_cast<const S *>(stage), reinterpret_cast<const S *>(stage + T::OFF_FF),
                    reinterpret_cast<const S *>(stage + T::OFF_G), i0 - T::HXS, j0 - HYS, j0 - 1,
                    p.sf, p.sF, p.sg};
-    if (kind == 0) return tile_compute<S, MHD, 0, SRT>(p, src, i0, j0, sm, ok);
-    return tile_compute<S, MHD, 1, SRT>(p, src, i0, j0, sm, ok);
+    if (kind == 0) return tile_compute<S, MHD, 0, SRT, CURV>(p, src, i0, j0, sm, ok);
+    return tile_compute<S, MHD, 1, SRT, CURV>(p, src, i0, j0, sm, ok);
 }
 
 // The tiles of one lattice processed by one block with TMA staging in two
@@ -887,7 +919,7 @@ __device__ __forceinline__ bool run_tile(const StepParams &p, int kind, int i0, 
 // tile is stride + the counter's next value (dynamic order, with ctr) or
 // t + stride (static order).  Every thread of the block calls it; the barriers
 // must be initialised.
-template <class S, bool MHD, bool SRT>
+template <class S, bool MHD, bool SRT, bool CURV>
 __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMaps &m, int *ctr, int first, int stride,
                                               unsigned char *dyn, uint64_t *bars, FieldSmem &sm, int4 *s_item,
                                               bool leader) {
@@ -945,7 +977,7 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
         if (MHD) {   // with the MIE the block gathers after the copy (measured faster there)
             if (!__syncthreads_and(ok)) return;
         }
-        if (!run_tile<S, MHD, SRT>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
+        if (!run_tile<S, MHD, SRT, CURV>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
         __syncthreads();   // the stage, the field arrays and s_item are reused by the next tile
         stage ^= 1;
     }
@@ -954,7 +986,10 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
 // Single lattice: persistent blocks take tiles from the lattice's queue.
 // SRT (raw): the collision on raw moments -- Appendix D's raw-moment MRT, or
 // Appendix F's SRT when every rate is 1/tau -- instead of the central-moment one.
-template <class S, bool MHD, bool SRT = false>
+// CURV: the curvilinear column metric (annular sector; h1, h2, theta11,
+// theta21 functions of xi1) with the theta21 terms of the force, tau^c, the
+// corrections and the local shear stress (Appendix A).
+template <class S, bool MHD, bool SRT = false, bool CURV = false>
 __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -973,7 +1008,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
         if (p.tctr) *p.tctr_next = 0;                                  // next step's tile queue
     }
     const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
-    lattice_tiles<S, MHD, SRT>(p, m, p.tctr, blockIdx.x, gridDim.x, dyn, bars, sm, s_item, leader);
+    lattice_tiles<S, MHD, SRT, CURV>(p, m, p.tctr, blockIdx.x, gridDim.x, dyn, bars, sm, s_item, leader);
 }
 
 // Many lattices in one launch.  Their parameters travel in the kernel

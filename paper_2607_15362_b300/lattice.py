@@ -39,6 +39,8 @@ def structs_from_spec(spec: dict):
         m.alpha[ax] = float(mp.get("alpha", 0.5))
         m.mu[ax] = float(mp.get("mu", 0.0))
         m.yc[ax] = float(mp.get("yc", 0.5))
+        if mp.get("kind") == "annulus":
+            m.r_inner, m.r_outer, m.sectors = float(mp["r_in"]), float(mp["r_out"]), float(mp["sectors"])
     f = GocFlow()
     f.rho0 = float(spec.get("rho0", 1.0))
     f.tau = float(spec.get("tau", 1.0)) if spec.get("tau") is not None else 1.0
