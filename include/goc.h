@@ -172,7 +172,10 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
 /* Re-initialise from host fields (each [ny][nx] doubles, NULL = default:
  * rho0, 0, 0, b_init): f = P^-1 m^eq,eff(rho, U) with finite-difference
  * gradients (Appendix C.1), g = g^eq(B, U) + g^corr, stored force F = 0.
- * Resets the step counter.  Synchronises the stream. */
+ * The fields are copied straight from the caller's buffers (page-locked
+ * buffers copy fastest) into a device staging area of 5 nx ny doubles that
+ * the lattice keeps (it is also the goc_moments buffer).  Resets the step
+ * counter.  Synchronises the stream. */
 goc_status goc_init_fields(goc_lattice *lat, const double *rho, const double *u1,
                            const double *u2, const double *b1, const double *b2);
 

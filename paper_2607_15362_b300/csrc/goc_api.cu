@@ -470,21 +470,34 @@ goc_status dalloc(goc_lattice *L, T **p, size_t bytes) {
 }
 
 goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const double *u2,
-                    const double *b1, const double *b2) {
+                    const double *b1, const double *b2, bool persistent_staging = false) {
     const long long N = (long long)L->nx * L->ny;
-    std::vector<double> host(5 * N);
-    for (long long n = 0; n < N; n++) {
-        host[n] = rho ? rho[n] : L->flow.rho0;
-        host[N + n] = u1 ? u1[n] : 0.0;
-        host[2 * N + n] = u2 ? u2[n] : 0.0;
-        host[3 * N + n] = b1 ? b1[n] : L->mhd.b_init[0];
-        host[4 * N + n] = b2 ? b2[n] : L->mhd.b_init[1];
-    }
+    // staging of the five FP64 fields on the device: the moments buffer (kept
+    // for later calls) when asked, else a temporary allocation
     double *dev = nullptr;
-    CU(cudaMalloc(&dev, 5 * N * sizeof(double)));
-    cudaError_t e = cudaMemcpyAsync(dev, host.data(), 5 * N * sizeof(double), cudaMemcpyHostToDevice, L->stream);
+    bool temporary = false;
+    if (persistent_staging) {
+        if (!L->mom) {
+            CU(cudaMalloc(&L->mom, 5 * N * sizeof(double)));
+            L->device_bytes += 5 * N * sizeof(double);
+        }
+        dev = L->mom;
+    } else {
+        CU(cudaMalloc(&dev, 5 * N * sizeof(double)));
+        temporary = true;
+    }
+    const double *src[5] = {rho, u1, u2, b1, b2};
+    const double dflt[5] = {L->flow.rho0, 0.0, 0.0, L->mhd.b_init[0], L->mhd.b_init[1]};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 5 && e == cudaSuccess; k++) {
+        if (src[k]) e = cudaMemcpyAsync(dev + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, L->stream);
+        else {
+            fill_kernel<<<(unsigned)std::min<long long>((N + 255) / 256, 4096), 256, 0, L->stream>>>(dev + k * N, N, dflt[k]);
+            e = cudaGetLastError();
+        }
+    }
     if (e != cudaSuccess) {
-        cudaFree(dev);
+        if (temporary) cudaFree(dev);
         return fail(GOC_ECUDA, "init copy failed: %s", cudaGetErrorString(e));
     }
     InitParams q;
@@ -519,7 +532,7 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
     }
     e = cudaGetLastError();
     cudaError_t e2 = cudaStreamSynchronize(L->stream);
-    cudaFree(dev);
+    if (temporary) cudaFree(dev);
     if (e != cudaSuccess || e2 != cudaSuccess)
         return fail(GOC_ECUDA, "init kernel failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     L->steps = 0;
@@ -824,7 +837,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
 goc_status goc_init_fields(goc_lattice *L, const double *rho, const double *u1, const double *u2,
                            const double *b1, const double *b2) {
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
-    return run_init(L, rho, u1, u2, b1, b2);
+    return run_init(L, rho, u1, u2, b1, b2, true);
 }
 
 void goc_destroy(goc_lattice *L) { free_lattice(L); }

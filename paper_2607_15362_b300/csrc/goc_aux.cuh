@@ -148,6 +148,11 @@ __global__ void annulus_tables_kernel(const double *m, int n, double rho0cs2, fl
     out[7 * n + k] = (float)t21[k];
 }
 
+__global__ void fill_kernel(double *p, long long n, double v) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        p[k] = v;
+}
+
 // ---- initial state (Appendix C.1): f = P^-1 m^eq,eff(rho, U), gradients by
 // the same second-order differences as the step; g = g^eq(0) + g^corr.
 // FP64 arithmetic (one-off).  Fields are [ny][nx] doubles on the device.

@@ -152,8 +152,15 @@ class Lattice:
         check(lib().goc_run_until(self._h, float(tol), int(max_steps), ctypes.byref(done), ctypes.byref(res)))
         return done.value, res.value
 
-    def moments(self, cartesian: bool = False):
-        out = [np.zeros((self.ny, self.nx)) for _ in range(5)]
+    def moments(self, cartesian: bool = False, out=None):
+        """(rho, U1, U2, B1, B2) as [ny, nx] float64 arrays.  out: five
+        C-contiguous float64 arrays (or None entries to skip a field) to fill
+        instead of new ones, e.g. page-locked buffers."""
+        if out is None:
+            out = [np.zeros((self.ny, self.nx)) for _ in range(5)]
+        for a in out:
+            if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous or a.size != self.nx * self.ny):
+                raise ValueError("out arrays must be C-contiguous float64 of nx * ny elements")
         check(lib().goc_moments(self._h, int(cartesian), *[_dptr(a) for a in out]))
         return tuple(out)
 
