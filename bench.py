@@ -57,9 +57,9 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0}, "fallback"
 
 
-def profile_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
+def _profile_value(key: str):
+    """A number from the committed ncu summary of the step kernel, if it was
+    taken on the current kernel source."""
     try:
         txt = open(PROFILE).read()
     except OSError:
@@ -68,9 +68,14 @@ def profile_traffic():
     if vals.get("kernel_source_hash", "").strip() != kernel_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the step kernel (ncu)."""
+    return _profile_value("dram_bytes_per_launch")
 
 
 class ClockSampler:
@@ -230,6 +235,18 @@ def run_ours(args):
     peak = float(peaks.get("hbm_gbs", 6400.0))
     traffic = profile_traffic()
     clocks = clk.summary()
+    # instruction-issue view of the same kernel: warp instructions per node
+    # (ncu, current source) x node updates per second against one warp
+    # instruction per scheduler per cycle at the SM clock seen under load
+    issue = None
+    ipn = _profile_value("warp_instructions_per_node")
+    if ipn and clocks and clocks.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        ach = ipn * nodes / launch_s
+        pk = sms * 4 * clocks["sm_mhz"] * 1e6
+        issue = {"achieved": float(f"{ach:.4g}"), "peak": float(f"{pk:.4g}"), "unit": "warp instructions/s",
+                 "frac": round(ach / pk, 4), "warp_instructions_per_node": ipn,
+                 "peak_source": f"{sms} SMs x 4 schedulers x 1 warp instruction per cycle at {clocks['sm_mhz']:.0f} MHz"}
 
     # ---- CPU baseline: the FP64 oracle on this host (rank 0 only) ----------
     cpu = None
@@ -255,7 +272,7 @@ def run_ours(args):
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": src, "bytes_per_node": bpn,
                          "kernel": "goc::step_kernel<float,false>", "launch_us": round(launch_s * 1e6, 3),
-                         "launch_config": lat.launch_config},
+                         "launch_config": lat.launch_config, "issue": issue},
             "cpu_baseline": cpu,
             "gpu_launches": args.steps * chunk,
             "clocks": clocks,
