@@ -587,6 +587,44 @@ def cpu_baseline(prob, spec_lib, budget_s: float = 15.0):
             "kind": "oracle", "sample": f"{n} time steps of the {prob.nx}x{prob.ny} cavity after 1 warm-up step"}
 
 
+def run_oracle_timing(args):
+    """The FP64 oracle on this host, single-threaded and on all cores, on the
+    Poiseuille channel (32 x 64), the 512^2 cavity, an x-invariant strip of
+    the Hartmann channel (4 x 1024) and the 8 smallest lattices of the batch;
+    each a bounded number of steps (about args.cpu_seconds per entry)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    probs = [("poiseuille_channel_32x64", gi.poiseuille_channel()), ("lid_cavity_512x512", gi.lid_cavity()),
+             ("hartmann_strip_4x1024", gi.hartmann_channel(nx=4))]
+    batch = sorted(gi.batch_lattices(), key=lambda p: p.nodes)[:8]
+    rows = []
+
+    def time_one(prob, threads, budget):
+        cs2 = oracle.build_metric(prob.lattice_spec(1.0)).cs2()
+        o = oracle.Oracle(prob.lattice_spec(cs2), threads=threads)
+        t0 = time.perf_counter()
+        o.step(1)
+        one = max(time.perf_counter() - t0, 1e-4)
+        n = max(1, min(1000, int(budget / one)))
+        t0 = time.perf_counter()
+        o.step(n)
+        return prob.nodes * n, time.perf_counter() - t0, n, o.threads
+
+    for name, prob in probs:
+        for threads in (1, cores):
+            upd, dt, n, used = time_one(prob, threads, args.cpu_seconds / 4)
+            rows.append({"workload": name, "threads": used, "steps": n, "mlups": round(upd / dt / 1e6, 3)})
+    for threads in (1, cores):
+        upd = dt = 0.0
+        for prob in batch:
+            u, d, n, used = time_one(prob, threads, args.cpu_seconds / 16)
+            upd += u
+            dt += d
+        rows.append({"workload": "batch_8_smallest_lattices", "threads": used, "mlups": round(upd / dt / 1e6, 3)})
+    print(json.dumps({"metric": METRIC, "workload": "oracle timing on the host cores", "unit": "MLUPS",
+                      "cores": cores, "build": "gcc -O3 -march=native -fopenmp, no fast-math", "runs": rows}))
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -632,7 +670,8 @@ def main():
     ap.add_argument("--cavity-n", type=int, default=512, help="cavity side (512 is the benchmark workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "batch", "serve", "accuracy", "accuracy_mhd"])
+    ap.add_argument("--workload", default="cavity",
+                    choices=["cavity", "batch", "serve", "accuracy", "accuracy_mhd", "oracle_timing"])
     ap.add_argument("--mhd-nx", type=int, default=256)
     ap.add_argument("--mhd-goc-ny", type=int, default=1024)
     ap.add_argument("--mhd-goc-max-steps", type=int, default=1000000)
@@ -654,6 +693,8 @@ def main():
         run_accuracy(args)
     elif args.workload == "accuracy_mhd":
         run_accuracy_mhd(args)
+    elif args.workload == "oracle_timing":
+        run_oracle_timing(args)
     else:
         run_ours(args)
 
