@@ -446,7 +446,7 @@ goc_status compute_metric(const goc_grid *grid, const goc_map *map, cudaStream_t
 
 void free_lattice(goc_lattice *L) {
     if (!L) return;
-    if (L->stream || true) cudaStreamSynchronize(L->stream);
+    cudaStreamSynchronize(L->stream);
     if (L->graph) cudaGraphExecDestroy(L->graph);
     void *ptrs[] = {L->f[0], L->f[1], L->F[0], L->F[1], L->g[0], L->g[1], L->tab1, L->tab2,
                     L->m1, L->m2, L->uout[0], L->uout[1], L->flag, L->red, L->mom};
