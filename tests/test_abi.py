@@ -86,3 +86,36 @@ def test_standard_scheme_rejects_stretched_maps_without_a_gpu():
     st = _abi.lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f), ctypes.byref(h),
                                ctypes.byref(e), ctypes.byref(out))
     assert st == _abi.GOC_EINVAL and b"gi_correction" in _abi.lib().goc_last_error()
+
+
+@pytest.mark.parametrize("map1,map2,walls,needle", [
+    ({"kind": "tanh1", "beta": 0.0}, {"kind": "uniform"}, "WE", b"one-wall tanh beta"),
+    ({"kind": "sinh", "mu": 3.0, "yc": 1.2}, {"kind": "uniform"}, "WE", b"yc"),
+    ({"kind": "sinh", "mu": 0.0, "yc": 0.5}, {"kind": "uniform"}, "WE", b"mu"),
+    ({"kind": "tanh1", "beta": 2.0}, {"kind": "uniform"}, "", b"periodic axis"),
+    ({"kind": "uniform"}, {"kind": "annulus", "r_in": 2.0, "r_out": 10.0, "sectors": 6.0}, "WE", b"xi1 (radial)"),
+    ({"kind": "annulus", "r_in": 2.0, "r_out": 10.0, "sectors": 6.0}, {"kind": "uniform"}, "WESN", b"periodic S/N"),
+    ({"kind": "annulus", "r_in": 10.0, "r_out": 2.0, "sectors": 6.0}, {"kind": "uniform"}, "WE", b"r_inner < r_outer"),
+])
+def test_map_parameters_are_validated_without_a_gpu(map1, map2, walls, needle):
+    """goc_metric_info rejects bad map parameters (one-wall tanh, interior
+    point, annulus) on the host, before any device call."""
+    w = {s: ({"u": 0.0} if s in walls else None) for s in "WESN"}
+    spec = {"nx": 12, "ny": 10, "map1": map1, "map2": map2, "walls": w}
+    g, m, f, h = goc.structs_from_spec(spec)
+    q, cs2 = ctypes.c_double(), ctypes.c_double()
+    st = _abi.lib().goc_metric_info(ctypes.byref(g), ctypes.byref(m), ctypes.byref(q), ctypes.byref(cs2))
+    assert st == _abi.GOC_EINVAL
+    assert needle in _abi.lib().goc_last_error()
+
+
+def test_oversized_lattices_are_rejected_without_a_gpu():
+    """nx * ny above 2^31 or ny above 65535 (the launch grid limit of the
+    one-off kernels) is refused with a message, before any allocation."""
+    for nx, ny in ((70000, 70000), (8, 70000)):
+        spec = {"nx": nx, "ny": ny, "walls": {"W": None, "E": None, "S": None, "N": None}}
+        g, m, f, h = goc.structs_from_spec(spec)
+        q, cs2 = ctypes.c_double(), ctypes.c_double()
+        st = _abi.lib().goc_metric_info(ctypes.byref(g), ctypes.byref(m), ctypes.byref(q), ctypes.byref(cs2))
+        assert st == _abi.GOC_EINVAL
+        assert b"too large" in _abi.lib().goc_last_error()

@@ -1,5 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -356,3 +357,73 @@ def test_taylor_couette_on_the_annulus_reaches_the_analytic_profile(gpu):
     assert np.abs(u1).max() < 1e-3 * ua.max()
     assert abs(L.mass() - mass0) / mass0 < 1e-5
     L.close()
+
+
+def test_degenerate_single_column_and_zero_steps(gpu):
+    """A channel one node wide (every x pull wraps to the node itself) matches
+    the oracle; goc_step(0) changes nothing; a negative count is refused."""
+    prob = gi.Problem("poiseuille", 1, 40, {"kind": "uniform"}, {"kind": "roberts", "gamma": 1.06, "alpha": 0.5},
+                      {"Re": 20.0, "tau": 0.8})
+    spec = prob.lattice_spec(cs2_of(prob))
+    o, L, fo, fg = run_pair(spec, 3000)
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    before = L.get_state()
+    L.step(0)
+    assert L.get_state() == before
+    with pytest.raises(goc.GocError):
+        L.step(-1)
+    L.close()
+
+
+# ---- full-size workloads in the launch configuration the benchmark times -------
+def test_full_size_cavity_in_the_benchmark_configuration_matches_the_oracle(gpu):
+    """The 512 x 512 clustered cavity of the benchmark, stepped as bench.py
+    steps it (autotuned launch configuration, captured graph chunks), against
+    the oracle on the whole lattice after 300 steps: FP32 velocity relative
+    L2 <= 1e-5."""
+    prob = gi.lid_cavity()
+    spec = prob.lattice_spec(cs2_of(prob))
+    o = oracle.Oracle(spec, threads=os.cpu_count() or 1)
+    L = goc.Lattice(spec)
+    L.step(300)
+    assert L.launch_config["tuned"]
+    o.step(300)
+    fo, fg = o.fields(), L.moments()
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+    L.close()
+
+
+def test_full_size_hartmann_channel_matches_the_oracle(gpu):
+    """The 256 x 1024 Hartmann channel (tanh beta = 3, Ha = 100) with the MIE,
+    200 steps from rest, against the oracle on the whole lattice."""
+    prob = gi.hartmann_channel()
+    spec = prob.lattice_spec(cs2_of(prob))
+    o = oracle.Oracle(spec, threads=os.cpu_count() or 1)
+    L = goc.Lattice(spec)
+    L.step(200)
+    o.step(200)
+    fo, fg = o.fields(), L.moments()
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    assert relerr(fg[3], fo[3]) <= 1e-5
+    L.close()
+
+
+def test_full_size_batch_matches_individual_lattices_on_a_sample(gpu):
+    """The 64-lattice batch of seed 7 (19.8 M nodes) stepped together for 40
+    steps gives bitwise the populations of each lattice stepped alone, checked
+    on 6 lattices spread over the size range (both kinds, with and without
+    the MIE)."""
+    probs = gi.batch_lattices()
+    specs = [p.lattice_spec(cs2_of(p)) for p in probs]
+    batch = goc.Batch(hbm_budget_bytes=8 << 30, max_lattices=64)
+    slots = [batch.add(s) for s in specs]
+    batch.step(40)
+    order = sorted(range(len(probs)), key=lambda k: probs[k].nodes)
+    for k in [order[0], order[12], order[25], order[38], order[51], order[-1]]:
+        alone = goc.Lattice(specs[k])
+        alone.step(40)
+        for x, y in zip(batch.lattice(slots[k]).moments(), alone.moments()):
+            np.testing.assert_array_equal(x, y)
+        alone.close()
+    batch.close()
