@@ -396,22 +396,27 @@ def test_full_size_cavity_in_the_benchmark_configuration_matches_the_oracle(gpu)
 
 def test_full_size_hartmann_channel_matches_the_oracle(gpu):
     """The 256 x 1024 Hartmann channel (tanh beta = 3, Ha = 100) with the MIE,
-    200 steps from rest, against the oracle on the whole lattice."""
+    200 steps from rest, against the oracle on the whole lattice: velocity
+    relative L2 <= 1e-5; the induced field B1, still a tiny early transient
+    that shares its stored values with the O(B0) reference state, within
+    1e-6 B0 at every node (as B2)."""
     prob = gi.hartmann_channel()
     spec = prob.lattice_spec(cs2_of(prob))
+    B0 = spec["derived"]["B0"]
     o = oracle.Oracle(spec, threads=os.cpu_count() or 1)
     L = goc.Lattice(spec)
     L.step(200)
     o.step(200)
     fo, fg = o.fields(), L.moments()
     assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
-    assert relerr(fg[3], fo[3]) <= 1e-5
+    assert np.abs(fg[3] - fo[3]).max() <= 1e-6 * B0, (np.abs(fg[3] - fo[3]).max() / B0, relerr(fg[3], fo[3]))
+    assert np.abs(fg[4] - fo[4]).max() <= 1e-6 * B0
     L.close()
 
 
 def test_full_size_batch_matches_individual_lattices_on_a_sample(gpu):
     """The 64-lattice batch of seed 7 (19.8 M nodes) stepped together for 40
-    steps gives bitwise the populations of each lattice stepped alone, checked
+    steps gives bitwise the fields of each lattice stepped alone, checked
     on 6 lattices spread over the size range (both kinds, with and without
     the MIE)."""
     probs = gi.batch_lattices()
