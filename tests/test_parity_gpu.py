@@ -396,20 +396,31 @@ def test_full_size_cavity_in_the_benchmark_configuration_matches_the_oracle(gpu)
 
 def test_full_size_hartmann_channel_matches_the_oracle(gpu):
     """The 256 x 1024 Hartmann channel (tanh beta = 3, Ha = 100) with the MIE,
-    200 steps from rest, against the oracle on the whole lattice: velocity
-    relative L2 <= 1e-5; the induced field B1, still a tiny early transient
-    that shares its stored values with the O(B0) reference state, within
-    1e-6 B0 at every node (as B2)."""
+    started from the analytic u_x, B_x of Sec. 7.4 (from rest the flow is
+    still near the FP32 floor after any affordable number of steps: the
+    time step is tied to the smallest cell), 200 steps, against the oracle
+    on the whole lattice: velocity and induced field relative L2 <= 1e-5,
+    B2 within 1e-6 B0."""
+    from oracle.metric import map_position
     prob = gi.hartmann_channel()
     spec = prob.lattice_spec(cs2_of(prob))
-    B0 = spec["derived"]["B0"]
+    d = spec["derived"]
+    Ha, H, B0 = 100.0, d["H"], d["B0"]
+    ys = map_position("tanh2", prob.ny, np.arange(prob.ny) + 0.5, beta=3.0) / H - 1.0
+    Ur, Br = H * H * d["Fx"] / d["nu"], H * H * d["Fx"] / math.sqrt(d["nu"] * d["eta"])
+    ua = Ur / (Ha * math.tanh(Ha)) * (1 - np.cosh(Ha * ys) / math.cosh(Ha))
+    ba = Br * (-ys / Ha + np.sinh(Ha * ys) / (Ha * math.tanh(Ha) * math.cosh(Ha)))
+    u1 = np.repeat(ua[:, None], prob.nx, axis=1)
+    b1 = np.repeat(ba[:, None], prob.nx, axis=1)
     o = oracle.Oracle(spec, threads=os.cpu_count() or 1)
+    o.initialize(u1=u1, b1=b1)
     L = goc.Lattice(spec)
+    L.init_fields(u1=u1, b1=b1)
     L.step(200)
     o.step(200)
     fo, fg = o.fields(), L.moments()
     assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
-    assert np.abs(fg[3] - fo[3]).max() <= 1e-6 * B0, (np.abs(fg[3] - fo[3]).max() / B0, relerr(fg[3], fo[3]))
+    assert relerr(fg[3], fo[3]) <= 1e-5
     assert np.abs(fg[4] - fo[4]).max() <= 1e-6 * B0
     L.close()
 
