@@ -43,7 +43,7 @@ typedef enum {
     GOC_EDIVERGED = -4,    /* NaN/Inf or non-positive density detected */
     GOC_ETIMEOUT = -5,     /* a bounded device-side wait ran out */
     GOC_EBUSY = -6,        /* batch is full / HBM budget exhausted */
-    GOC_EUNSUPPORTED = -7  /* valid request that this build does not support */
+    GOC_EUNSUPPORTED = -7  /* valid request that the library does not support (message says which) */
 } goc_status;
 
 /* Opaque handle of one lattice; owned by the library. */
