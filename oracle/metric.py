@@ -218,3 +218,22 @@ def annulus_metric(n1: int, n2: int, r_in: float, r_out: float, sectors: float) 
         "N": (h1.copy(), h2.copy()),
     }
     return m
+
+
+def table_metric(nx: int, ny: int, table: dict) -> "Metric":
+    """Metric given node by node (a general orthogonal grid): table holds
+    [ny, nx] arrays h1, h2, t11, t12, t21, t22 (theta_ij of Eq.
+    curvaturematrix) and "wall": {"W", "E": (h1, h2) over j, "S", "N": (h1,
+    h2) over i} at the wall points (used by moving walls; any values on
+    periodic sides)."""
+    m = Metric.__new__(Metric)
+    m.nx, m.ny = nx, ny
+    for k in ("h1", "h2", "t11", "t12", "t21", "t22"):
+        a = np.ascontiguousarray(np.asarray(table[k], dtype=np.float64))
+        if a.shape != (ny, nx):
+            raise ValueError(f"{k}: shape {a.shape}, want {(ny, nx)}")
+        setattr(m, k, a.copy())
+    m.h1_axis, m.h2_axis = m.h1[0].copy(), m.h2[:, 0].copy()
+    m.wall = {w: (np.asarray(table["wall"][w][0], dtype=np.float64).copy(),
+                  np.asarray(table["wall"][w][1], dtype=np.float64).copy()) for w in ("W", "E", "S", "N")}
+    return m

@@ -34,7 +34,7 @@ import threading
 
 import numpy as np
 
-from .metric import Metric, annulus_metric
+from .metric import Metric, annulus_metric, table_metric
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "goc_oracle.c")
@@ -133,6 +133,8 @@ def derived_parameters(spec: dict, metric: Metric) -> dict:
 
 def build_metric(spec: dict) -> Metric:
     m1 = spec.get("map1", {"kind": "uniform"})
+    if m1.get("kind") == "table":     # metric given node by node (general orthogonal grid)
+        return table_metric(int(spec["nx"]), int(spec["ny"]), spec["metric"])
     if m1.get("kind") == "annulus":   # curvilinear annular sector (Sec. 8.1)
         return annulus_metric(int(spec["nx"]), int(spec["ny"]), float(m1["r_in"]), float(m1["r_out"]),
                               float(m1["sectors"]))

@@ -738,3 +738,33 @@ def test_mass_is_conserved_on_the_annulus_with_moving_walls():
     mass0 = (o.fields()[0] * m.h1 * m.h2).sum()
     o.step(4000)
     assert abs((o.fields()[0] * m.h1 * m.h2).sum() - mass0) / mass0 < 1e-12
+
+
+def _transposed_table(m):
+    """The metric of a grid with xi1 and xi2 exchanged, as a node table."""
+    return {"h1": m.h2.T, "h2": m.h1.T, "t11": m.t22.T, "t12": m.t21.T, "t21": m.t12.T, "t22": m.t11.T,
+            "wall": {"W": (m.wall["S"][1], m.wall["S"][0]), "E": (m.wall["N"][1], m.wall["N"][0]),
+                     "S": (m.wall["W"][1], m.wall["W"][0]), "N": (m.wall["E"][1], m.wall["E"][0])}}
+
+
+def test_transposed_annulus_gives_the_transposed_solution():
+    """The annular sector with the radial direction along xi2 (a node table:
+    theta12 = theta22 = 1/r, theta11 = theta21 = 0) must give the transposed
+    fields of the annulus along xi1: pins the theta12 terms of the force,
+    tau^c, the local shear stress and the corrections against the theta21
+    terms, which the Taylor-Couette pin fixes."""
+    p = gi.taylor_couette(n1=20, n2=5, r_in=3.0, sectors=360.0 * 20 / (256.0 * 6.0), Re=10.0)
+    m = oracle.build_metric(p.lattice_spec(1.0))
+    a = p.lattice_spec(m.cs2())
+    b = dict(a)
+    b.update(nx=a["ny"], ny=a["nx"], map1={"kind": "table"}, map2={"kind": "uniform"}, metric=_transposed_table(m),
+             walls={"S": a["walls"]["W"], "N": a["walls"]["E"], "W": None, "E": None})
+    oa, ob = oracle.Oracle(a), oracle.Oracle(b)
+    assert ob.par["cs2"] == pytest.approx(oa.par["cs2"], rel=1e-15)
+    oa.step(300)
+    ob.step(300)
+    ra, ua, va, *_ = oa.fields()
+    rb, ub, vb, *_ = ob.fields()
+    np.testing.assert_allclose(ra, rb.T, rtol=1e-13)
+    np.testing.assert_allclose(ua, vb.T, atol=1e-13 * np.abs(va).max())
+    np.testing.assert_allclose(va, ub.T, rtol=1e-11, atol=1e-14 * np.abs(va).max())
