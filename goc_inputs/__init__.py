@@ -32,6 +32,7 @@ class Problem:
     params: dict = field(default_factory=dict)
     steps: int = 0
     name: str = ""
+    metric: dict | None = None    # node table of a general orthogonal grid (map1 kind "table")
 
     # ---- geometry ------------------------------------------------------
     def walls(self) -> dict:
@@ -70,6 +71,8 @@ class Problem:
         spec = {"nx": self.nx, "ny": self.ny, "map1": dict(self.map1), "map2": dict(self.map2),
                 "walls": self.walls(), "rho0": 1.0, "gi": int(p.get("gi", 1)),
                 "tau_zeta": float(p.get("tau_zeta", 1.0))}
+        if self.metric is not None:
+            spec["metric"] = self.metric
         k = self.kind
         if k == "poiseuille":
             tau = float(p["tau"])
@@ -283,3 +286,32 @@ def taylor_couette_profile(r: np.ndarray, r1: float, r2: float, u1: float, u2: f
     r1 < r2 with wall speeds u1 = Omega1 r1, u2 = Omega2 r2 (Sec. 8.2)."""
     o1, o2, e2 = u1 / r1, u2 / r2, (r1 / r2) ** 2
     return ((o2 - o1 * e2) * r + r1 * r1 * (o1 - o2) / r) / (1.0 - e2)
+
+
+def spiral_grid(nx: int, ny: int, c: float, phi: float) -> dict:
+    """Node table of the orthogonal grid of the conformal map
+    z = exp(a (w - w0)) / a, w = xi1 + i xi2, a = c e^{i phi}, w0 the lattice
+    centre: h1 = h2 = h = exp(c (cos(phi) (xi1 - nx/2) - sin(phi) (xi2 - ny/2))),
+    so theta11 = theta21 = c cos(phi)/h and theta12 = theta22 = -c sin(phi)/h
+    (theta_ij = dh_i/dxi_j / (h_i h_j)); the lines of constant xi are
+    logarithmic spirals.  Nodes at xi = (i + 1/2, j + 1/2), walls at xi1 = 0,
+    nx and xi2 = 0, ny."""
+    def h(x1, x2):
+        return np.exp(c * (math.cos(phi) * (x1 - nx / 2.0) - math.sin(phi) * (x2 - ny / 2.0)))
+
+    x1 = (np.arange(nx) + 0.5)[None, :]
+    x2 = (np.arange(ny) + 0.5)[:, None]
+    hn = h(x1, x2)
+    ta, tb = c * math.cos(phi) / hn, -c * math.sin(phi) / hn
+    i_, j_ = np.arange(nx) + 0.5, np.arange(ny) + 0.5
+    wall = {"W": (h(0.0, j_),) * 2, "E": (h(float(nx), j_),) * 2, "S": (h(i_, 0.0),) * 2, "N": (h(i_, float(ny)),) * 2}
+    return {"h1": hn, "h2": hn.copy(), "t11": ta, "t12": tb, "t21": ta.copy(), "t22": tb.copy(), "wall": wall}
+
+
+def spiral_cavity(nx: int = 40, ny: int = 37, c: float | None = None, phi: float = 0.6, Re: float = 50.0,
+                  u_lid: float = 0.05) -> Problem:
+    """Lid-driven cavity on the logarithmic-spiral grid (every theta_ij
+    non-zero): walls on all sides, the N wall moving along xi1."""
+    c = 1.0 / math.hypot(nx, ny) if c is None else c
+    return Problem("cavity", nx, ny, {"kind": "table"}, {"kind": "uniform"}, {"Re": Re, "u_lid": u_lid},
+                   metric=spiral_grid(nx, ny, c, phi))

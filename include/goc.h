@@ -74,10 +74,18 @@ typedef enum { GOC_BC_PERIODIC = 0, GOC_BC_WALL = 1 } goc_bc;
  *           h2 = 2 pi r/(sectors ny), theta11 = theta21 = 1/r, theta12 = theta22 = 0.
  *           Needs W/E walls, periodic S/N, kind[1] = UNIFORM, scheme 0, no MIE;
  *           not for batches.  Wall speeds (wall_u[W], wall_u[E]) are azimuthal.
+ *  TABLE    (kind[0]; kind[1] ignored) a general orthogonal grid given node by
+ *           node: `table` holds six [ny][nx] planes h1, h2, theta11, theta12,
+ *           theta21, theta22 (Eq. metricfactor, Eq. curvaturematrix) and
+ *           `wall_table` the wall-normal metric factor along each wall: h1 at
+ *           the W wall over j, h1 at E over j, h2 at S over i, h2 at N over i
+ *           (2 ny + 2 nx values; used by moving walls, any value on periodic
+ *           sides).  Both are host arrays read during goc_create only; every
+ *           h > 0.  Scheme 0, no MIE, not for batches.
  * Wall maps (TANH2 with beta > 0, ROBERTS, TANH1, SINH) need a wall axis; SINE a
  * periodic one. */
 typedef enum { GOC_MAP_UNIFORM = 0, GOC_MAP_TANH2 = 1, GOC_MAP_SINE = 2, GOC_MAP_ROBERTS = 3,
-               GOC_MAP_TANH1 = 4, GOC_MAP_SINH = 5, GOC_MAP_ANNULUS = 6 } goc_map_kind;
+               GOC_MAP_TANH1 = 4, GOC_MAP_SINH = 5, GOC_MAP_ANNULUS = 6, GOC_MAP_TABLE = 7 } goc_map_kind;
 
 typedef struct {
     int nx, ny;             /* nodes along xi1, xi2; >= 3 along a wall axis, >= 1 otherwise */
@@ -98,6 +106,8 @@ typedef struct {
     double yc[2];           /* SINH clustering point as a fraction of the axis length, in (0, 1) */
     double r_inner, r_outer;  /* ANNULUS radii, 0 < r_inner < r_outer */
     double sectors;           /* ANNULUS: the sector spans 2 pi / sectors (> 0) */
+    const double *table;      /* TABLE: [6][ny][nx] h1, h2, theta11, theta12, theta21, theta22 */
+    const double *wall_table; /* TABLE: [2 ny + 2 nx] wall-normal metric at W, E, S, N */
 } goc_map;
 
 typedef struct {

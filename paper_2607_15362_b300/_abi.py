@@ -18,7 +18,8 @@ class GocGrid(ctypes.Structure):
 class GocMap(ctypes.Structure):
     _fields_ = [("kind", c_int * 2), ("beta", c_double * 2), ("a", c_double * 2),
                 ("gamma", c_double * 2), ("alpha", c_double * 2), ("mu", c_double * 2), ("yc", c_double * 2),
-                ("r_inner", c_double), ("r_outer", c_double), ("sectors", c_double)]
+                ("r_inner", c_double), ("r_outer", c_double), ("sectors", c_double),
+                ("table", c_void_p), ("wall_table", c_void_p)]
 
 
 class GocFlow(ctypes.Structure):
@@ -39,7 +40,7 @@ class GocExec(ctypes.Structure):
 GOC_OK, GOC_EINVAL, GOC_ENOMEM, GOC_ECUDA, GOC_EDIVERGED, GOC_ETIMEOUT, GOC_EBUSY, GOC_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
-MAPS = {"uniform": 0, "tanh2": 1, "sine": 2, "roberts": 3, "tanh1": 4, "sinh": 5, "annulus": 6}
+MAPS = {"uniform": 0, "tanh2": 1, "sine": 2, "roberts": 3, "tanh1": 4, "sinh": 5, "annulus": 6, "table": 7}
 
 # name -> (restype, argtypes); every entry point of include/goc.h
 SIGNATURES = {

@@ -91,6 +91,8 @@ struct goc_lattice {
     void *g[2] = {nullptr, nullptr};
     float *tab1 = nullptr, *tab2 = nullptr;      // [7][nx], [7][ny]
     double *m1 = nullptr, *m2 = nullptr;         // FP64 h, theta per axis: [2][n+2]
+    float *gm = nullptr;                         // node-table metric: [10][plane] + [4][max(nx, ny)]
+    double *gtab = nullptr;                      // node-table metric in FP64: [6][ny][nx] (initial state)
     float *uout[2] = {nullptr, nullptr};
     int *flag = nullptr;
     double *red = nullptr;                       // 8 doubles
@@ -174,18 +176,18 @@ bool encode_lattice_maps(goc_lattice *L) {
 }
 
 // Dynamic shared memory of a step kernel and its persistent grid size.
-template <class S, bool MHD, bool SRT = false, bool CURV = false>
+template <class S, bool MHD, bool SRT = false, int GEOM = 0>
 int step_grid(int ntiles, size_t *smem) {
     using T = Tiling<S>;
     const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
     *smem = bytes;
     static int cached = -1;
     if (cached < 0) {
-        cudaFuncSetAttribute(step_kernel<S, MHD, SRT, CURV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cudaFuncSetAttribute(step_kernel<S, MHD, SRT, GEOM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD, SRT, CURV>, NT, bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD, SRT, GEOM>, NT, bytes);
         cached = std::max(1, sms * std::max(1, per));
     }
     return std::min(ntiles, cached);
@@ -204,9 +206,12 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
     const bool pdl = L->cfg_pdl != 0;
-    if (L->sp.curv) {   // curvilinear column metric (central-moment collision, no MIE)
-        const int grid = step_grid<S, false, false, true>(ntiles, &smem);
-        CU(launch_pdl(pdl, step_kernel<S, false, false, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+    if (L->sp.curv == 2) {   // node-table metric (central-moment collision, no MIE)
+        const int grid = step_grid<S, false, false, 2>(ntiles, &smem);
+        CU(launch_pdl(pdl, step_kernel<S, false, false, 2>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+    } else if (L->sp.curv) {   // curvilinear column metric (central-moment collision, no MIE)
+        const int grid = step_grid<S, false, false, 1>(ntiles, &smem);
+        CU(launch_pdl(pdl, step_kernel<S, false, false, 1>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     } else if (L->scheme == 2 || L->scheme == 3) {   // collision on raw moments (Appendix F SRT, Appendix D MRT)
         if (L->mhd.enabled) {
             const int grid = step_grid<S, true, true>(ntiles, &smem);
@@ -378,9 +383,27 @@ goc_status validate(const goc_grid *grid, const goc_map *map) {
         return fail(GOC_EINVAL, "opposite sides must both be periodic or both walls");
     if (grid->bc[0] == GOC_BC_WALL && grid->nx < 3) return fail(GOC_EINVAL, "a wall axis needs >= 3 nodes");
     if (grid->bc[2] == GOC_BC_WALL && grid->ny < 3) return fail(GOC_EINVAL, "a wall axis needs >= 3 nodes");
+    if (map->kind[0] == GOC_MAP_TABLE) {   // general orthogonal grid given node by node
+        if (!map->table || !map->wall_table) return fail(GOC_EINVAL, "the TABLE map needs table and wall_table");
+        const long long N = (long long)grid->nx * grid->ny;
+        for (long long n = 0; n < 2 * N; n++)
+            if (!(map->table[n] > 0.0 && std::isfinite(map->table[n])))
+                return fail(GOC_EINVAL, "TABLE: h1, h2 must be finite and > 0 at every node");
+        for (long long n = 2 * N; n < 6 * N; n++)
+            if (!std::isfinite(map->table[n])) return fail(GOC_EINVAL, "TABLE: theta must be finite");
+        for (int s = 0; s < 4; s++) {   // wall-normal metric of the wall sides
+            if (grid->bc[s] != GOC_BC_WALL) continue;
+            const int off = s < 2 ? s * grid->ny : 2 * grid->ny + (s - 2) * grid->nx, n = s < 2 ? grid->ny : grid->nx;
+            for (int k = 0; k < n; k++)
+                if (!(map->wall_table[off + k] > 0.0 && std::isfinite(map->wall_table[off + k])))
+                    return fail(GOC_EINVAL, "TABLE: wall_table must be finite and > 0 along the walls");
+        }
+        return GOC_OK;
+    }
     for (int a = 0; a < 2; a++) {
         int k = map->kind[a];
-        if (k < 0 || k > 6) return fail(GOC_EINVAL, "map kind[%d] = %d unknown", a, k);
+        if (k == GOC_MAP_TABLE) return fail(GOC_EINVAL, "the TABLE map is given as kind[0]");
+        if (k < 0 || k > 7) return fail(GOC_EINVAL, "map kind[%d] = %d unknown", a, k);
         int per = grid->bc[a == 0 ? 0 : 2] == GOC_BC_PERIODIC;
         if (k == GOC_MAP_ANNULUS) {
             if (a != 0) return fail(GOC_EINVAL, "the annulus map is a xi1 (radial) map");
@@ -449,7 +472,7 @@ void free_lattice(goc_lattice *L) {
     cudaStreamSynchronize(L->stream);
     if (L->graph) cudaGraphExecDestroy(L->graph);
     void *ptrs[] = {L->f[0], L->f[1], L->F[0], L->F[1], L->g[0], L->g[1], L->tab1, L->tab2,
-                    L->m1, L->m2, L->uout[0], L->uout[1], L->flag, L->red, L->mom};
+                    L->m1, L->m2, L->gm, L->gtab, L->uout[0], L->uout[1], L->flag, L->red, L->mom};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (L->owns_stream && L->stream) cudaStreamDestroy(L->stream);
@@ -506,8 +529,9 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
     q.sp.Fout = L->F[L->cur];
     q.sp.gout = L->g[L->cur];
     q.h1d = L->m1;
-    q.h2x = L->sp.curv ? L->m1 + 2 * (L->nx + 2) : nullptr;
-    q.t21x = L->sp.curv ? L->m1 + 3 * (L->nx + 2) : nullptr;
+    q.h2x = L->sp.curv == 1 ? L->m1 + 2 * (L->nx + 2) : nullptr;
+    q.t21x = L->sp.curv == 1 ? L->m1 + 3 * (L->nx + 2) : nullptr;
+    q.gtab = L->gtab;
     q.t1d = L->m1 + L->nx + 2;
     q.h2d = L->m2;
     q.t2d = L->m2 + L->ny + 2;
@@ -582,9 +606,23 @@ extern "C" {
 
 const char *goc_last_error(void) { return g_err.c_str(); }
 
+// Node-table metric: q = the smallest h1, h2 over the nodes (host table).
+double table_q(const goc_grid *grid, const goc_map *map) {
+    const long long N = (long long)grid->nx * grid->ny;
+    double q = map->table[0];
+    for (long long n = 0; n < 2 * N; n++) q = std::min(q, map->table[n]);
+    return q;
+}
+
 goc_status goc_metric_info(const goc_grid *grid, const goc_map *map, double *q, double *cs2) {
     goc_status st = validate(grid, map);
     if (st != GOC_OK) return st;
+    if (map->kind[0] == GOC_MAP_TABLE) {
+        const double qh = table_q(grid, map);
+        if (q) *q = qh;
+        if (cs2) *cs2 = qh * qh / 3.0;
+        return GOC_OK;
+    }
     double *d = nullptr;
     size_t n1 = grid->nx + 2, n2 = grid->ny + 2;
     CU(cudaMalloc(&d, (4 * n1 + 2 * n2 + 1) * sizeof(double)));
@@ -617,9 +655,10 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         if (flow->gi_correction) return fail(GOC_EINVAL, "the standard uniform-grid scheme needs gi_correction = 0");
         if (mhd && mhd->enabled) return fail(GOC_EINVAL, "the standard uniform-grid scheme has no MIE");
     }
-    if (map->kind[0] == GOC_MAP_ANNULUS) {
-        if (mhd && mhd->enabled) return fail(GOC_EUNSUPPORTED, "the annulus runs without the MIE");
-        if (exec && exec->scheme != 0) return fail(GOC_EUNSUPPORTED, "the annulus runs the central-moment scheme (0)");
+    if (map->kind[0] == GOC_MAP_ANNULUS || map->kind[0] == GOC_MAP_TABLE) {
+        const char *what = map->kind[0] == GOC_MAP_ANNULUS ? "the annulus" : "the TABLE map";
+        if (mhd && mhd->enabled) return fail(GOC_EUNSUPPORTED, "%s runs without the MIE", what);
+        if (exec && exec->scheme != 0) return fail(GOC_EUNSUPPORTED, "%s runs the central-moment scheme (0)", what);
     }
     goc_lattice *L = new (std::nothrow) goc_lattice();
     if (!L) return fail(GOC_ENOMEM, "host allocation failed");
@@ -679,8 +718,12 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     TRY(dalloc(L, &L->m2, 2 * (size_t)(L->ny + 2) * sizeof(double)));
     TRY(dalloc(L, &L->flag, 8 * sizeof(int)));   // [0] status, [1] spare, [2..3] step counters, [4..5] tile queues of the two parities
     TRY(dalloc(L, &L->red, 8 * sizeof(double)));
-    // metric (FP64), q, cs2 (Eq. GOC-LBE_CFL)
-    TRY(compute_metric(grid, map, L->stream, L->m1, L->m2, L->red));
+    // metric (FP64), q, cs2 (Eq. GOC-LBE_CFL); a node table fills the axis
+    // tables with a uniform metric (unused by its step kernel)
+    const bool table = map->kind[0] == GOC_MAP_TABLE;
+    goc_map uni_map = *map;
+    if (table) uni_map.kind[0] = uni_map.kind[1] = GOC_MAP_UNIFORM;
+    TRY(compute_metric(grid, table ? &uni_map : map, L->stream, L->m1, L->m2, L->red));
     double hw1[2], hw2[2], qh;
     {
         cudaError_t e = cudaMemcpyAsync(&qh, L->red, sizeof(double), cudaMemcpyDeviceToHost, L->stream);
@@ -692,6 +735,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
             return fail(GOC_ECUDA, "metric readback failed: %s", cudaGetErrorString(e));
         }
     }
+    if (table) qh = table_q(grid, map);
     L->q = qh;
     L->cs2 = qh * qh / 3.0;
     if (L->flow.nu > 0.0) {
@@ -726,6 +770,37 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
                                                                        rho0cs2, L->cs2, L->tab1);
     axis_tables_kernel<<<(L->ny + 127) / 128, 128, 0, L->stream>>>(L->m2, L->m2 + L->ny + 2, L->ny, per_y, rho0cs2,
                                                                    L->cs2, L->tab2);
+    if (table) {   // node-table metric: FP64 copy for the initial state, FP32 planes + walls for the step
+        const long long N = (long long)L->nx * L->ny;
+        const int wmax = std::max(L->nx, L->ny);
+        TRY(dalloc(L, &L->gtab, 6 * N * sizeof(double)));
+        TRY(dalloc(L, &L->gm, (10 * L->plane + 4 * (long long)wmax) * sizeof(float)));
+        std::vector<float> walls(4 * (size_t)wmax, 1.f);
+        for (int k = 0; k < L->ny; k++) {
+            walls[k] = (float)map->wall_table[k];                           // W: h1 over j
+            walls[wmax + k] = (float)map->wall_table[L->ny + k];            // E
+        }
+        for (int k = 0; k < L->nx; k++) {
+            walls[2 * wmax + k] = (float)map->wall_table[2 * L->ny + k];         // S: h2 over i
+            walls[3 * wmax + k] = (float)map->wall_table[2 * L->ny + L->nx + k];  // N
+        }
+        cudaError_t e = cudaMemsetAsync(L->gm, 0, 10 * L->plane * sizeof(float), L->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(L->gtab, map->table, 6 * N * sizeof(double), cudaMemcpyHostToDevice, L->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(L->gm + 10 * L->plane, walls.data(), walls.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, L->stream);
+        if (e == cudaSuccess) {
+            table_metric_kernel<<<dim3((L->nx + 127) / 128, L->ny), 128, 0, L->stream>>>(
+                L->gtab, L->nx, L->ny, L->pitch, L->plane, per_x, per_y, rho0cs2, L->gm);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);   // the host arrays may go after return
+        if (e != cudaSuccess) {
+            free_lattice(L);
+            return fail(GOC_ECUDA, "node-table upload failed: %s", cudaGetErrorString(e));
+        }
+    }
     {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -755,7 +830,8 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     };
     p.ax1 = axis(L->tab1, L->nx);
     p.ax2 = axis(L->tab2, L->ny);
-    p.curv = curv ? 1 : 0;   // the xi1 table then holds h2, 1/h2, theta21 in rows 5-7
+    p.curv = table ? 2 : curv ? 1 : 0;   // 1: the xi1 table then holds h2, 1/h2, theta21 in rows 5-7
+    p.gm = L->gm;
     p.rho0 = (float)L->flow.rho0;
     p.cs2 = (float)L->cs2;
     p.ics2 = (float)(1.0 / L->cs2);
@@ -1306,6 +1382,7 @@ goc_status goc_batch_add(goc_batch *B, const goc_grid *grid, const goc_map *map,
     *slot = -1;
     if (!grid) return fail(GOC_EINVAL, "grid is required");
     if (map && map->kind[0] == GOC_MAP_ANNULUS) return fail(GOC_EUNSUPPORTED, "annulus lattices are not batched");
+    if (map && map->kind[0] == GOC_MAP_TABLE) return fail(GOC_EUNSUPPORTED, "TABLE lattices are not batched");
     int free_slot = -1;
     for (int k = 0; k < B->max_lat; k++)
         if (!B->slots[k]) {

@@ -153,6 +153,35 @@ __global__ void fill_kernel(double *p, long long n, double v) {
         p[k] = v;
 }
 
+// FP32 node-table metric for the step kernel (StepParams.gm) from the FP64
+// table [6][ny][nx] (h1, h2, theta11, theta12, theta21, theta22): the six
+// planes, then the full pull corrections of links 1..4 into each node,
+//   link 1 (source i-1): rho0 cs2 (r(src) - r)/2 + (Fr1(src) + Fr1)/4,
+//   link 3 (source i+1): rho0 cs2 (r(src) - r)/2 - (Fr1(src) + Fr1)/4,
+//   link 2 (source j-1): rho0 cs2 (s(src) - s)/2 + (Fr2(src) + Fr2)/4,
+//   link 4 (source j+1): rho0 cs2 (s(src) - s)/2 - (Fr2(src) + Fr2)/4,
+// r = h2/h1, s = h1/h2, Fr = (h2 (theta21 - theta11), h1 (theta12 - theta22))
+// rho0 cs2 (Eq. bodyforce1/2 at U = 0); 0 where the source lies beyond a wall.
+__global__ void table_metric_kernel(const double *tab, int nx, int ny, int pitch, long long plane, int per_x,
+                                    int per_y, double rho0cs2, float *gm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx || j >= ny) return;
+    const long long N = (long long)nx * ny;
+    auto at = [&](int k, int ii, int jj) { return tab[k * N + (long long)jj * nx + ii]; };
+    auto r_ = [&](int ii, int jj) { return at(1, ii, jj) / at(0, ii, jj); };
+    auto s_ = [&](int ii, int jj) { return at(0, ii, jj) / at(1, ii, jj); };
+    auto f1 = [&](int ii, int jj) { return at(1, ii, jj) * (at(4, ii, jj) - at(2, ii, jj)) * rho0cs2; };
+    auto f2 = [&](int ii, int jj) { return at(0, ii, jj) * (at(3, ii, jj) - at(5, ii, jj)) * rho0cs2; };
+    const long long o = (long long)j * pitch + i;
+    for (int k = 0; k < 6; k++) gm[k * plane + o] = (float)at(k, i, j);
+    const int im = per_x ? (i - 1 + nx) % nx : i - 1, ip = per_x ? (i + 1) % nx : i + 1;
+    const int jm = per_y ? (j - 1 + ny) % ny : j - 1, jp = per_y ? (j + 1) % ny : j + 1;
+    gm[6 * plane + o] = im >= 0 ? (float)(0.5 * rho0cs2 * (r_(im, j) - r_(i, j)) + 0.25 * (f1(im, j) + f1(i, j))) : 0.f;
+    gm[7 * plane + o] = jm >= 0 ? (float)(0.5 * rho0cs2 * (s_(i, jm) - s_(i, j)) + 0.25 * (f2(i, jm) + f2(i, j))) : 0.f;
+    gm[8 * plane + o] = ip < nx ? (float)(0.5 * rho0cs2 * (r_(ip, j) - r_(i, j)) - 0.25 * (f1(ip, j) + f1(i, j))) : 0.f;
+    gm[9 * plane + o] = jp < ny ? (float)(0.5 * rho0cs2 * (s_(i, jp) - s_(i, j)) - 0.25 * (f2(i, jp) + f2(i, j))) : 0.f;
+}
+
 // ---- initial state (Appendix C.1): f = P^-1 m^eq,eff(rho, U), gradients by
 // the same second-order differences as the step; g = g^eq(0) + g^corr.
 // FP64 arithmetic (one-off).  Fields are [ny][nx] doubles on the device.
@@ -160,6 +189,7 @@ struct InitParams {
     StepParams sp;
     const double *h1d, *h2d, *t1d, *t2d;   // FP64 node metric per axis
     const double *h2x, *t21x;              // curvilinear column metric: h2, theta21 over xi1 (else null)
+    const double *gtab;                    // node table [6][ny][nx] (else null)
     double cs2, nu, zeta, rho0, csm2, eta;
     int gi, mhd;
     const double *rho, *u1, *u2, *b1, *b2;
@@ -186,8 +216,17 @@ __global__ void init_kernel(const InitParams q) {
     if (i >= p.nx || j >= p.ny) return;
     const long long n = (long long)j * p.nx + i, idx = (long long)j * p.pitch + i;
     const bool curv = q.h2x != nullptr;
-    const double h1 = q.h1d[i], h2 = curv ? q.h2x[i] : q.h2d[j], t11 = q.t1d[i], t22 = curv ? 0.0 : q.t2d[j];
-    const double t21 = curv ? q.t21x[i] : 0.0;   // theta12 = 0 on both grid families
+    double h1 = q.h1d[i], h2 = curv ? q.h2x[i] : q.h2d[j], t11 = q.t1d[i], t22 = curv ? 0.0 : q.t2d[j];
+    double t21 = curv ? q.t21x[i] : 0.0, t12 = 0.0;
+    if (q.gtab) {   // node table
+        const long long NN = (long long)p.nx * p.ny;
+        h1 = q.gtab[n];
+        h2 = q.gtab[NN + n];
+        t11 = q.gtab[2 * NN + n];
+        t12 = q.gtab[3 * NN + n];
+        t21 = q.gtab[4 * NN + n];
+        t22 = q.gtab[5 * NN + n];
+    }
     const double rho = q.rho[n], U1 = q.u1[n], U2 = q.u2[n];
     const double dU1 = dfd64(q.u1, i, j, p.nx, p.ny, 0, p.per_x);
     const double dU2 = dfd64(q.u2, i, j, p.nx, p.ny, 1, p.per_y);
@@ -196,8 +235,9 @@ __global__ void init_kernel(const InitParams q) {
     const double cs2 = q.cs2, nu = q.nu, ze = q.zeta;
     const double gi = q.gi ? 1.0 : 0.0;
     const double a1 = gi * U1 * U1 / cs2, a2 = gi * U2 * U2 / cs2;
-    // Eqs. 83 / 85 with theta12 = 0 (theta21 on the curvilinear column metric)
-    const double tc11 = rho * (ze - nu) * U1 * t21, tc22 = rho * (ze + nu) * U1 * t21;   // Eq. tauc
+    // Eqs. 83 / 85 (theta12, theta21 on curvilinear grids)
+    const double tc11 = rho * (ze + nu) * U2 * t12 + rho * (ze - nu) * U1 * t21;   // Eq. tauc
+    const double tc22 = rho * (ze + nu) * U1 * t21 + rho * (ze - nu) * U2 * t12;
     const double D31 = rho * (2 * ze - (ze + nu) * h2 / (h1 * h1) - (ze - nu) / h2
                               - ze * (2 - h2 / cs2 + (3 * a1 + 1) * h2 / (h1 * h1)));
     const double D32 = rho * (2 * ze - (ze + nu) * h1 / (h2 * h2) - (ze - nu) / h1
@@ -206,7 +246,8 @@ __global__ void init_kernel(const InitParams q) {
     const double D34 = -ze * ((3 - a2) * h1 / (h2 * h2) - h1 / cs2 - a1 / h1) * U2;
     const double C3 = rho * ze * (2 * U1 * (a1 + 1) * h2 / h1 * t11 + 2 * U2 * (a2 + 1) * h1 / h2 * t22)
                       - (h2 / h1 * tc11 + h1 / h2 * tc22)
-                      - rho * ze * U1 * ((3 + a1) * h2 / h1 + 2 * h1 / h2 - h1 * h2 / cs2) * t21;
+                      - rho * ze * U1 * ((3 + a1) * h2 / h1 + 2 * h1 / h2 - h1 * h2 / cs2) * t21
+                      - rho * ze * U2 * ((3 + a2) * h1 / h2 + 2 * h2 / h1 - h1 * h2 / cs2) * t12;
     const double D41 = rho * (2 * nu - (ze + nu) * h2 / (h1 * h1) + (ze - nu) / h2
                               - nu * (2 - h2 / cs2 + (3 * a1 + 1) * h2 / (h1 * h1)));
     const double D42 = rho * (-2 * nu + (ze + nu) * h1 / (h2 * h2) - (ze - nu) / h1
@@ -215,7 +256,8 @@ __global__ void init_kernel(const InitParams q) {
     const double D44 = -nu * (-(3 - a2) * h1 / (h2 * h2) + h1 / cs2 - a1 / h1) * U2;
     const double C4 = rho * nu * (2 * U1 * (a1 + 1) * h2 / h1 * t11 - 2 * U2 * (a2 + 1) * h1 / h2 * t22)
                       - (h2 / h1 * tc11 - h1 / h2 * tc22)
-                      - rho * nu * U1 * ((3 + a1) * h2 / h1 - 2 * h1 / h2 - h1 * h2 / cs2) * t21;
+                      - rho * nu * U1 * ((3 + a1) * h2 / h1 - 2 * h1 / h2 - h1 * h2 / cs2) * t21
+                      - rho * nu * U2 * (-(3 + a2) * h1 / h2 + 2 * h2 / h1 + h1 * h2 / cs2) * t12;
     const double n3 = D31 * dU1 + D32 * dU2 + D33 * dr1 + D34 * dr2 + C3;
     const double n4 = D41 * dU1 + D42 * dU2 + D43 * dr1 + D44 * dr2 + C4;
     // m^eq,eff - m_rest(rho0), bare order (Eq. GOCmomentequilibria)
@@ -242,7 +284,7 @@ __global__ void init_kernel(const InitParams q) {
     d[7] = 0.25 * (m5 - m6 - m7 + m8);
     d[8] = 0.25 * (-m5 - m6 + m7 + m8);
     // pre-collision reference f_ref- = f_rest - F_rest/4 on links 1, 3 (xi1) and 2, 4 (xi2)
-    const double F1r = h2 * q.rho0 * cs2 * (t21 - t11), F2r = -h1 * q.rho0 * cs2 * t22;
+    const double F1r = h2 * q.rho0 * cs2 * (t21 - t11), F2r = h1 * q.rho0 * cs2 * (t12 - t22);
     d[1] += 0.25 * F1r;
     d[3] -= 0.25 * F1r;
     d[2] += 0.25 * F2r;
@@ -283,15 +325,23 @@ __global__ void moments_kernel(const StepParams p, double *out) {
     if (i >= p.nx || j >= p.ny) return;
     const SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                            p.plane, p.pitch, p.sf, p.sF, p.sg};
-    const float h1 = p.ax1.h[i], h2 = p.curv ? curv_h2(p.ax1, i) : p.ax2.h[j];
+    float h1, h2, ih1, ih2;
     float d[9];
-    if (p.curv) pull_node<true, true>(p, src, i, j, h1, h2, d);
-    else pull_node<true>(p, src, i, j, h1, h2, d);
+    if (p.curv == 2) {
+        node_metric<2>(p, i, j, h1, h2, ih1, ih2);
+        pull_node<true, 2>(p, src, i, j, h1, h2, d);
+    } else if (p.curv) {
+        node_metric<1>(p, i, j, h1, h2, ih1, ih2);
+        pull_node<true, 1>(p, src, i, j, h1, h2, d);
+    } else {
+        node_metric<0>(p, i, j, h1, h2, ih1, ih2);
+        pull_node<true>(p, src, i, j, h1, h2, d);
+    }
     float drho, U1, U2;
     // F - F_rest of the previous step (the body force, or zero before the first step, without a stored force)
     const float F1p = p.constF ? (p.nopull ? 0.f : p.fext1) : src.Fv(0, i, j);
     const float F2p = p.constF ? (p.nopull ? 0.f : p.fext2) : src.Fv(1, i, j);
-    fields_from(p, d, F1p, F2p, p.ax1.ih[i], p.curv ? curv_ih2(p.ax1, i) : p.ax2.ih[j], drho, U1, U2);
+    fields_from(p, d, F1p, F2p, ih1, ih2, drho, U1, U2);
     const long long N = (long long)p.nx * p.ny, n = (long long)j * p.nx + i;
     out[n] = (double)p.rho0 + (double)drho;
     out[N + n] = U1;
@@ -347,7 +397,10 @@ __global__ void mass_kernel(const StepParams p, double *out) {
         const long long idx = (long long)j * p.pitch + i;
         double s = 0.0;
         for (int a = 0; a < 9; a++) s += (double)Store<S>::ld(f + a * p.plane + idx) * p.sf;
-        acc[0] += s + (double)p.ax1.h[i] * (double)(p.curv ? curv_h2(p.ax1, i) : p.ax2.h[j]) * p.rho0;
+        double hh;
+        if (p.curv == 2) hh = (double)gm_at(p.gm, p.plane, p.pitch, 0, i, j) * gm_at(p.gm, p.plane, p.pitch, 1, i, j);
+        else hh = (double)p.ax1.h[i] * (double)(p.curv ? curv_h2(p.ax1, i) : p.ax2.h[j]);
+        acc[0] += s + hh * p.rho0;
     }
     block_add<1>(acc, out);
 }

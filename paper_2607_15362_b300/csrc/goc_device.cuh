@@ -38,6 +38,15 @@ struct Axis {
     // dm, dp, dp + n hold h2, 1/h2 and theta21 as functions of xi1.
 };
 
+// the node-by-node metric (StepParams.gm): plane k at node (i, j), and the
+// wall-normal metric factor at position k along wall `side`
+__device__ __forceinline__ float gm_at(const float *gm, long long plane, int pitch, int k, int i, int j) {
+    return gm[k * plane + (long long)j * pitch + i];
+}
+__device__ __forceinline__ float gm_wall(const float *gm, long long plane, int nx, int ny, int side, int k) {
+    return gm[10 * plane + (long long)side * (nx > ny ? nx : ny) + k];
+}
+
 // the curvilinear column metric of node column i (see Axis)
 __device__ __forceinline__ float curv_h2(const Axis &a, int i) { return a.dm[i]; }
 __device__ __forceinline__ float curv_ih2(const Axis &a, int i) { return a.dp[i]; }
@@ -48,7 +57,12 @@ struct StepParams {
     int nx, ny, pitch;         // pitch in elements (multiple of 32)
     long long plane;           // ny * pitch
     int per_x, per_y;          // periodic axes
-    int curv;                  // 1: curvilinear column metric (h1, h2, theta11, theta21 functions of xi1)
+    int curv;                  // 1: curvilinear column metric (h1, h2, theta11, theta21 functions of xi1);
+                               // 2: metric given node by node (gm)
+    // node-by-node metric (curv = 2): FP32 planes [10][plane] h1, h2, theta11,
+    // theta12, theta21, theta22 and the pull corrections of links 1..4 (into
+    // the node), then [4][max(nx, ny)] the wall-normal metric along W, E, S, N
+    const float *gm;
     int nopull;                // 1: the input buffer holds pre-collision populations (the
                                // initial state f^0 of Appendix C.1): read them in place
     const void *fin;           // [9][plane] stored post-collision deviations (input)

@@ -153,7 +153,7 @@ template <class S> struct SrcSmem {        // the TMA-staged tile
 // e2 rho_w cs2 u / (2 h1_w) across a W/E wall (rho_w: this node's density at
 // the time of the outgoing population).  CHECKS = false: every source is
 // inside the lattice (interior tile).
-template <bool CHECKS, bool CURV = false, class Src>
+template <bool CHECKS, int GEOM = 0, class Src>
 __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, int i, int j, float h1, float h2,
                                           float d[9]) {
     if (p.nopull) {
@@ -178,10 +178,14 @@ __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, i
         float v;
         if (!ox && !oy) {
             v = src.fv(a, si, sj);
-            if (a == 1) v += CURV ? p.ax1.rm[i] : h2 * p.ax1.rm[i];   // curvilinear: full corrections
-            if (a == 3) v += CURV ? p.ax1.rp[i] : h2 * p.ax1.rp[i];
-            if (a == 2) v += h1 * p.ax2.rm[j];
-            if (a == 4) v += h1 * p.ax2.rp[j];
+            if (GEOM == 2) {   // node table: full corrections per node and link
+                if (a >= 1 && a <= 4) v += gm_at(p.gm, p.plane, p.pitch, 5 + a, i, j);
+            } else {
+                if (a == 1) v += GEOM ? p.ax1.rm[i] : h2 * p.ax1.rm[i];   // curvilinear: full corrections
+                if (a == 3) v += GEOM ? p.ax1.rp[i] : h2 * p.ax1.rp[i];
+                if (a == 2) v += h1 * p.ax2.rm[j];
+                if (a == 4) v += h1 * p.ax2.rp[j];
+            }
         } else {
             v = src.fv(opp(a), i, j);
             if (p.moving && (e1(a) != 0 && e2(a) != 0)) {
@@ -196,8 +200,10 @@ __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, i
                         rhow = p.rho0 + s / (h1 * h2);
                         rhow_ready = true;
                     }
-                    if (uy != 0.f) v += e1(a) * rhow * p.cs2 * uy / (2.f * p.hwn[sy]);
-                    if (ux != 0.f) v += e2(a) * rhow * p.cs2 * ux / (2.f * p.hwn[sx]);
+                    const float hy = GEOM == 2 ? gm_wall(p.gm, p.plane, p.nx, p.ny, sy, i) : p.hwn[sy];
+                    const float hx = GEOM == 2 ? gm_wall(p.gm, p.plane, p.nx, p.ny, sx, j) : p.hwn[sx];
+                    if (uy != 0.f) v += e1(a) * rhow * p.cs2 * uy / (2.f * hy);
+                    if (ux != 0.f) v += e2(a) * rhow * p.cs2 * ux / (2.f * hx);
                 }
             }
         }
@@ -251,6 +257,25 @@ __device__ __forceinline__ void pull_mie(const StepParams &p, const Src &src, in
             v = -src.gv(c * 5 + gopp(a), i, j) + 2.f * p.W1 * (hw * p.bw[side][c] - H * br) + eM;
         }
         d[a] = v;
+    }
+}
+
+// Metric factors (and their inverses) of node (i, j) for the grid kinds:
+// GEOM 0 straight (h1(xi1), h2(xi2)), 1 curvilinear column (h1, h2 of xi1),
+// 2 node table.
+template <int GEOM>
+__device__ __forceinline__ void node_metric(const StepParams &p, int i, int j, float &h1, float &h2, float &ih1,
+                                            float &ih2) {
+    if (GEOM == 2) {
+        h1 = gm_at(p.gm, p.plane, p.pitch, 0, i, j);
+        h2 = gm_at(p.gm, p.plane, p.pitch, 1, i, j);
+        ih1 = 1.f / h1;
+        ih2 = 1.f / h2;
+    } else {
+        h1 = p.ax1.h[i];
+        ih1 = p.ax1.ih[i];
+        h2 = GEOM == 1 ? curv_h2(p.ax1, i) : p.ax2.h[j];
+        ih2 = GEOM == 1 ? curv_ih2(p.ax1, i) : p.ax2.ih[j];
     }
 }
 
@@ -391,7 +416,7 @@ __device__ __forceinline__ void raw_relax(const StepParams &p, const V (&d)[9], 
 // step, the fields and their normal derivatives fl[k][r] (k: drho, U1, U2,
 // dU1/dxi1, drho/dxi1, dU2/dxi2, drho/dxi2), and the stores.  own[r]: whether
 // node r is a lattice node this thread updates.
-template <class S, bool MHD, bool CHECKS, class V, bool SRT, bool CURV, class Src>
+template <class S, bool MHD, bool CHECKS, class V, bool SRT, int GEOM, class Src>
 __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int i, const int (&j)[Lanes<V>::R],
                                         const bool (&own)[Lanes<V>::R], const float (&dn)[Lanes<V>::R][9],
                                         const float (&F1pn)[Lanes<V>::R], const float (&F2pn)[Lanes<V>::R], float h1,
@@ -400,12 +425,15 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     constexpr int R = Lanes<V>::R;
     float th_[R];
 #pragma unroll
-    for (int r = 0; r < R; r++) th_[r] = CURV ? 0.f : p.ax2.th[own[r] ? j[r] : j[0]];   // theta22
+    for (int r = 0; r < R; r++)   // theta22
+        th_[r] = GEOM == 2 ? gm_at(p.gm, p.plane, p.pitch, 5, i, own[r] ? j[r] : j[0])
+                           : (GEOM ? 0.f : p.ax2.th[own[r] ? j[r] : j[0]]);
     const V drho = pack<V>(fl[0]), U1 = pack<V>(fl[1]), U2 = pack<V>(fl[2]);
     const V dU1 = pack<V>(fl[3]), dr1 = pack<V>(fl[4]), dU2 = pack<V>(fl[5]), dr2 = pack<V>(fl[6]);
     const V t22 = pack<V>(th_);
     const V h2 = pack<V>(h2n), ih2 = pack<V>(ih2n), F1p = pack<V>(F1pn), F2p = pack<V>(F2pn);
-    const float t11 = p.ax1.th[i];
+    static_assert(GEOM != 2 || R == 1, "the node-table metric runs one node per thread");
+    const float t11 = GEOM == 2 ? gm_at(p.gm, p.plane, p.pitch, 2, i, j[0]) : p.ax1.th[i];
     V d[9];
 #pragma unroll
     for (int a = 0; a < 9; a++) {
@@ -508,27 +536,36 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     // F = F_rest + F_dev, F_rest = -(h2, h1) rho0 cs2 (theta11, theta22) is the
     // geometric force of the rest state; only F_dev is stored.
     V F1dev, F2dev, F1r, F2r, tc11 = bc<V>(0.f), tc22 = bc<V>(0.f);
-    float t21 = 0.f;
-    if constexpr (CURV) {
-        // curvilinear column metric (theta12 = theta22 = 0, theta21 != 0):
-        // tau^c (Eq. tauc), the full effective force (Eqs. bodyforce1/2) and
-        // the local shear stress of Appendix A; F_rest = (h2 (theta21 -
-        // theta11) rho0 cs2, 0)
-        t21 = curv_t21(p.ax1, p.nx, i);
-        tc11 = rho * U1 * ((zeta - nu) * t21);
-        tc22 = rho * U1 * ((zeta + nu) * t21);
+    float t21 = 0.f, t12 = 0.f;
+    if constexpr (GEOM) {
+        // curvilinear grids (theta12, theta21; the column metric has theta12 =
+        // theta22 = 0): tau^c (Eq. tauc), the full effective force (Eqs.
+        // bodyforce1/2) and the local shear stress of Appendix A; F_rest =
+        // (h2 (theta21 - theta11), h1 (theta12 - theta22)) rho0 cs2
+        if (GEOM == 2) {
+            t12 = gm_at(p.gm, p.plane, p.pitch, 3, i, j[0]);
+            t21 = gm_at(p.gm, p.plane, p.pitch, 4, i, j[0]);
+        } else {
+            t21 = curv_t21(p.ax1, p.nx, i);
+        }
+        tc11 = rho * fmav(U2, (zeta + nu) * t12, U1 * ((zeta - nu) * t21));
+        tc22 = rho * fmav(U1, (zeta + nu) * t21, U2 * ((zeta - nu) * t12));
         tau11 = tau11 + tc11;
         tau22 = tau22 + tc22;
         const V csd_ = drho * cs2;
-        F1dev = h2 * (fmav(tau11 - rho * (U1 * U1) - csd_, t11, FL1 + p.fext1) - (tau22 - rho * (U2 * U2) - csd_) * t21);
+        const V A1 = tau11 - rho * (U1 * U1) - csd_, A2 = tau22 - rho * (U2 * U2) - csd_;
+        const V ruv2 = rho * U1 * U2 * 2.f;
+        const V Ft1d = h2 * (fmav(A1, t11, FL1 + p.fext1) - A2 * t21 - ruv2 * t12);
+        const V Ft2d = h1 * (fmav(A2, t22, FL2 + p.fext2) - A1 * t12 - ruv2 * t21);
         F1r = h2 * ((t21 - t11) * p.rho0 * cs2);
-        F2r = bc<V>(0.f);
-        const V Ft2 = h1 * (FL2 + p.fext2 - rho * U1 * U2 * (2.f * t21));
+        F2r = h1 * (t12 - t22) * (p.rho0 * cs2);
         const V k11 = d[5] - d[6] + d[7] - d[8];          // raw k11 of f (f_ref- has none)
         const float c5 = 1.f - 0.5f * p.om[5];
-        const V tau12 = (bc<V>(0.f) - c5) * (k11 + ((F1dev + F1r) * U2 * ih2 + Ft2 * U1 * ih1) * 0.5f - rho * U1 * U2) *
-                        rcpv(fmav(U1, c5 * t21, bc<V>(1.f)));
-        F2dev = fmav(tau12, 2.f * t21 * h1, Ft2);
+        const V tau12 = (bc<V>(0.f) - c5) *
+                        (k11 + ((Ft1d + F1r) * U2 * ih2 + (Ft2d + F2r) * U1 * ih1) * 0.5f - rho * U1 * U2) *
+                        rcpv(fmav(U1, c5 * t21, fmav(U2, c5 * t12, bc<V>(1.f))));
+        F1dev = fmav(tau12, 2.f * t12 * h2, Ft1d);
+        F2dev = fmav(tau12, 2.f * t21 * h1, Ft2d);
     } else {
         F1dev = h2 * fmav(tau11 - rho * (U1 * U1) - drho * cs2, t11, FL1 + p.fext1);
         F2dev = fmav(tau22 - rho * (U2 * U2) - drho * cs2, t22, FL2 + p.fext2) * h1;
@@ -563,10 +600,12 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         const V q4 = fmav(Y1 - Y2, nu, fmav(P41, dU1, P42 * dU2));
         n3 = rho * q3 - U1 * (X1 - b2) * dr1 * zeta - U2 * (X2 - b1) * dr2 * zeta;
         n4 = rho * q4 - U1 * (X1 + b2) * dr1 * nu + U2 * (X2 + b1) * dr2 * nu;
-        if constexpr (CURV) {   // theta21 parts of C3, C4 (theta12 = 0)
-            const V Hc = H * p.ics2, a13 = fmav(a1, r, 3.f * r);   // (3 + a1) h2/h1
-            n3 = n3 - fmav(r, tc11, s * tc22) - rho * U1 * (t21 * zeta) * (a13 + s * 2.f - Hc);
-            n4 = n4 - (r * tc11 - s * tc22) - rho * U1 * (t21 * nu) * (a13 - s * 2.f - Hc);
+        if constexpr (GEOM) {   // tau^c and the theta21, theta12 parts of C3, C4
+            const V Hc = H * p.ics2, a13 = fmav(a1, r, 3.f * r), a23 = fmav(a2, s, 3.f * s);   // (3 + a) h2/h1, h1/h2
+            n3 = n3 - fmav(r, tc11, s * tc22) - rho * U1 * (t21 * zeta) * (a13 + s * 2.f - Hc)
+                 - rho * U2 * (t12 * zeta) * (a23 + r * 2.f - Hc);
+            n4 = n4 - (r * tc11 - s * tc22) - rho * U1 * (t21 * nu) * (a13 - s * 2.f - Hc)
+                 - rho * U2 * (t12 * nu) * (r * 2.f + Hc - a23);
         }
     }
 
@@ -720,7 +759,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
 // Normal derivatives of the fields from the tile's field arrays (second
 // order: central, one-sided at the first and last node of a wall axis), then
 // the collision.
-template <class S, bool MHD, bool CHECKS, class V, bool SRT, bool CURV, class Src>
+template <class S, bool MHD, bool CHECKS, class V, bool SRT, int GEOM, class Src>
 __device__ __forceinline__ void node_update(const StepParams &p, const Src &src, int i, int tx,
                                             const int (&j)[Lanes<V>::R], const int (&ty)[Lanes<V>::R],
                                             const bool (&own)[Lanes<V>::R], const FieldSmem &sm,
@@ -749,7 +788,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
             fl[6][r] = 0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex]);
         }
     }
-    collide<S, MHD, CHECKS, V, SRT, CURV>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl);
+    collide<S, MHD, CHECKS, V, SRT, GEOM>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl);
 }
 
 // One tile of one lattice from a given source; KIND 0: interior (no boundary
@@ -760,7 +799,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
 // barrier: every thread of the block must call it.  ok: this thread's wait
 // for the staged copy succeeded; false (returned by every thread) when any
 // thread's wait failed -- the block then leaves.
-template <class S, bool MHD, int KIND, bool SRT, bool CURV, class Src>
+template <class S, bool MHD, int KIND, bool SRT, int GEOM, class Src>
 __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src, int i0, int j0, FieldSmem &sm,
                                              bool ok) {
     constexpr bool CHECKS = KIND != 0;
@@ -774,7 +813,7 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
     const int i = i0 + tx;
     const bool inx = i < p.nx;
     float h1 = 1.f, ih1 = 1.f;
-    if (inx) {
+    if (inx && GEOM != 2) {
         h1 = p.ax1.h[i];
         ih1 = p.ax1.ih[i];
     }
@@ -792,9 +831,8 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
 #pragma unroll
         for (int a = 0; a < 9; a++) d[r][a] = 0.f;
         if (own[r]) {
-            h2[r] = CURV ? curv_h2(p.ax1, i) : p.ax2.h[j[r]];
-            ih2[r] = CURV ? curv_ih2(p.ax1, i) : p.ax2.ih[j[r]];
-            pull_node<CHECKS, CURV>(p, src, i, j[r], h1, h2[r], d[r]);
+            node_metric<GEOM>(p, i, j[r], h1, h2[r], ih1, ih2[r]);   // (GEOM 2 runs one node per thread)
+            pull_node<CHECKS, GEOM>(p, src, i, j[r], h1, h2[r], d[r]);
             F1p[r] = src.Fv(0, i, j[r]);
             F2p[r] = src.Fv(1, i, j[r]);
             fields_from(p, d[r], F1p[r], F2p[r], ih1, ih2[r], drho, U1, U2);
@@ -808,10 +846,10 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
                 if (p.per_y) jj = wrapi(jj, p.ny); else in = false;
             }
             if (in) {
-                float dd[9];
-                pull_node<CHECKS, CURV>(p, src, ii, jj, p.ax1.h[ii], CURV ? curv_h2(p.ax1, ii) : p.ax2.h[jj], dd);
-                fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), p.ax1.ih[ii],
-                            CURV ? curv_ih2(p.ax1, ii) : p.ax2.ih[jj], drho, U1, U2);
+                float dd[9], g1, g2, ig1, ig2;
+                node_metric<GEOM>(p, ii, jj, g1, g2, ig1, ig2);
+                pull_node<CHECKS, GEOM>(p, src, ii, jj, g1, g2, dd);
+                fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), ig1, ig2, drho, U1, U2);
             }
         }
         sm.rho[ty[r] + MH][tx + MH] = drho;
@@ -846,10 +884,10 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
         }
         float drho = 0.f, U1 = 0.f, U2 = 0.f;
         if (in) {
-            float dd[9];
-            pull_node<CHECKS, CURV>(p, src, ii, jj, p.ax1.h[ii], CURV ? curv_h2(p.ax1, ii) : p.ax2.h[jj], dd);
-            fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), p.ax1.ih[ii], CURV ? curv_ih2(p.ax1, ii) : p.ax2.ih[jj],
-                        drho, U1, U2);
+            float dd[9], g1, g2, ig1, ig2;
+            node_metric<GEOM>(p, ii, jj, g1, g2, ig1, ig2);
+            pull_node<CHECKS, GEOM>(p, src, ii, jj, g1, g2, dd);
+            fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), ig1, ig2, drho, U1, U2);
         }
         sm.rho[y + MH][x + MH] = drho;
         sm.u1[y + MH][x + MH] = U1;
@@ -859,7 +897,7 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
     bool any = false;
 #pragma unroll
     for (int r = 0; r < R; r++) any = any || own[r];
-    if (any) node_update<S, MHD, CHECKS, V, SRT, CURV>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
+    if (any) node_update<S, MHD, CHECKS, V, SRT, GEOM>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
     return true;
 }
 
@@ -897,20 +935,20 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
-template <class S, bool MHD, bool SRT = false, bool CURV = false>
+template <class S, bool MHD, bool SRT = false, int GEOM = 0>
 __device__ __forceinline__ bool run_tile(const StepParams &p, int kind, int i0, int j0, const unsigned char *stage,
                                          FieldSmem &sm, bool ok) {
     using T = Tiling<S>;
     if (kind == 2) {
         SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                          p.plane, p.pitch, p.sf, p.sF, p.sg};
-        return tile_compute<S, MHD, 1, SRT, CURV>(p, src, i0, j0, sm, ok);
+        return tile_compute<S, MHD, 1, SRT, GEOM>(p, src, i0, j0, sm, ok);
     }
     SrcSmem<S> src{reinterpret_cast<const S *>(stage), reinterpret_cast<const S *>(stage + T::OFF_FF),
                    reinterpret_cast<const S *>(stage + T::OFF_G), i0 - T::HXS, j0 - HYS, j0 - 1,
                    p.sf, p.sF, p.sg};
-    if (kind == 0) return tile_compute<S, MHD, 0, SRT, CURV>(p, src, i0, j0, sm, ok);
-    return tile_compute<S, MHD, 1, SRT, CURV>(p, src, i0, j0, sm, ok);
+    if (kind == 0) return tile_compute<S, MHD, 0, SRT, GEOM>(p, src, i0, j0, sm, ok);
+    return tile_compute<S, MHD, 1, SRT, GEOM>(p, src, i0, j0, sm, ok);
 }
 
 // The tiles of one lattice processed by one block with TMA staging in two
@@ -919,7 +957,7 @@ __device__ __forceinline__ bool run_tile(const StepParams &p, int kind, int i0, 
 // tile is stride + the counter's next value (dynamic order, with ctr) or
 // t + stride (static order).  Every thread of the block calls it; the barriers
 // must be initialised.
-template <class S, bool MHD, bool SRT, bool CURV>
+template <class S, bool MHD, bool SRT, int GEOM>
 __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMaps &m, int *ctr, int first, int stride,
                                               unsigned char *dyn, uint64_t *bars, FieldSmem &sm, int4 *s_item,
                                               bool leader) {
@@ -977,7 +1015,7 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
         if (MHD) {   // with the MIE the block gathers after the copy (measured faster there)
             if (!__syncthreads_and(ok)) return;
         }
-        if (!run_tile<S, MHD, SRT, CURV>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
+        if (!run_tile<S, MHD, SRT, GEOM>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
         __syncthreads();   // the stage, the field arrays and s_item are reused by the next tile
         stage ^= 1;
     }
@@ -986,10 +1024,11 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
 // Single lattice: persistent blocks take tiles from the lattice's queue.
 // SRT (raw): the collision on raw moments -- Appendix D's raw-moment MRT, or
 // Appendix F's SRT when every rate is 1/tau -- instead of the central-moment one.
-// CURV: the curvilinear column metric (annular sector; h1, h2, theta11,
-// theta21 functions of xi1) with the theta21 terms of the force, tau^c, the
-// corrections and the local shear stress (Appendix A).
-template <class S, bool MHD, bool SRT = false, bool CURV = false>
+// GEOM: 1 the curvilinear column metric (annular sector; h1, h2, theta11,
+// theta21 functions of xi1), 2 the metric given node by node (general
+// orthogonal grids), with the theta21 / theta12 terms of the force, tau^c,
+// the corrections and the local shear stress (Appendix A).
+template <class S, bool MHD, bool SRT = false, int GEOM = 0>
 __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -1008,7 +1047,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
         if (p.tctr) *p.tctr_next = 0;                                  // next step's tile queue
     }
     const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
-    lattice_tiles<S, MHD, SRT, CURV>(p, m, p.tctr, blockIdx.x, gridDim.x, dyn, bars, sm, s_item, leader);
+    lattice_tiles<S, MHD, SRT, GEOM>(p, m, p.tctr, blockIdx.x, gridDim.x, dyn, bars, sm, s_item, leader);
 }
 
 // Many lattices in one launch.  Their parameters travel in the kernel

@@ -41,6 +41,18 @@ def structs_from_spec(spec: dict):
         m.yc[ax] = float(mp.get("yc", 0.5))
         if mp.get("kind") == "annulus":
             m.r_inner, m.r_outer, m.sectors = float(mp["r_in"]), float(mp["r_out"]), float(mp["sectors"])
+        if mp.get("kind") == "table" and ax == 0:   # general grid: spec["metric"] as in oracle.metric.table_metric
+            t = spec["metric"]
+            tab = np.ascontiguousarray(np.stack([np.asarray(t[k], dtype=np.float64).reshape(g.ny, g.nx)
+                                                 for k in ("h1", "h2", "t11", "t12", "t21", "t22")]))
+            wall = t["wall"]
+            wt = np.ascontiguousarray(np.concatenate([np.asarray(wall["W"][0], dtype=np.float64),
+                                                      np.asarray(wall["E"][0], dtype=np.float64),
+                                                      np.asarray(wall["S"][1], dtype=np.float64),
+                                                      np.asarray(wall["N"][1], dtype=np.float64)]))
+            m.table = tab.ctypes.data
+            m.wall_table = wt.ctypes.data
+            m._keep = (tab, wt)   # alive as long as the struct
     f = GocFlow()
     f.rho0 = float(spec.get("rho0", 1.0))
     f.tau = float(spec.get("tau", 1.0)) if spec.get("tau") is not None else 1.0

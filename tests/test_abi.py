@@ -119,3 +119,31 @@ def test_oversized_lattices_are_rejected_without_a_gpu():
         st = _abi.lib().goc_metric_info(ctypes.byref(g), ctypes.byref(m), ctypes.byref(q), ctypes.byref(cs2))
         assert st == _abi.GOC_EINVAL
         assert b"too large" in _abi.lib().goc_last_error()
+
+
+def test_node_table_map_is_validated_and_sized_on_the_host():
+    """A TABLE map needs both host arrays, h1, h2 > 0 at every node and along
+    the wall sides; goc_metric_info then returns q = the smallest h without a
+    device call."""
+    import numpy as np
+    import goc_inputs as gi
+    p = gi.spiral_cavity(12, 10)
+    spec = p.lattice_spec(0.1)
+    g, m, f, h = goc.structs_from_spec(spec)
+    q, cs2 = ctypes.c_double(), ctypes.c_double()
+    assert _abi.lib().goc_metric_info(ctypes.byref(g), ctypes.byref(m), ctypes.byref(q), ctypes.byref(cs2)) == 0
+    assert q.value == pytest.approx(float(np.min(p.metric["h1"])), rel=1e-15)
+    assert cs2.value == pytest.approx(q.value ** 2 / 3, rel=1e-15)
+    bad = dict(p.metric, h2=p.metric["h2"].copy())
+    bad["h2"][3, 4] = 0.0
+    spec["metric"] = bad
+    g, m, f, h = goc.structs_from_spec(spec)
+    assert _abi.lib().goc_metric_info(ctypes.byref(g), ctypes.byref(m), ctypes.byref(q), ctypes.byref(cs2)) == _abi.GOC_EINVAL
+    assert b"h1, h2" in _abi.lib().goc_last_error()
+    m.table = None
+    assert _abi.lib().goc_metric_info(ctypes.byref(g), ctypes.byref(m), ctypes.byref(q), ctypes.byref(cs2)) == _abi.GOC_EINVAL
+    assert b"needs table" in _abi.lib().goc_last_error()
+    g, m, f, h = goc.structs_from_spec({"nx": 12, "ny": 10, "map2": {"kind": "table"},
+                                        "walls": {"W": None, "E": None, "S": None, "N": None}})
+    assert _abi.lib().goc_metric_info(ctypes.byref(g), ctypes.byref(m), ctypes.byref(q), ctypes.byref(cs2)) == _abi.GOC_EINVAL
+    assert b"kind[0]" in _abi.lib().goc_last_error()
