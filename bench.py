@@ -37,6 +37,7 @@ import goc_inputs as gi  # noqa: E402
 
 METRIC = "MLUPS & % of HBM peak (FP32 vs FP16 store); batched p50/p99 solve latency"
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_cavity512_fp32.txt")
+PROFILE_SPIRAL = os.path.join(ROOT, "profiles", "step_kernel_spiral512_fp32_table.txt")
 KERNEL_SOURCES = ["paper_2607_15362_b300/csrc/goc_step.cuh", "paper_2607_15362_b300/csrc/goc_device.cuh",
                   "paper_2607_15362_b300/csrc/goc_vec.cuh"]
 
@@ -57,11 +58,11 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0}, "fallback"
 
 
-def _profile_value(key: str):
-    """A number from the committed ncu summary of the step kernel, if it was
+def _profile_value(key: str, path: str = PROFILE):
+    """A number from a committed ncu summary of the step kernel, if it was
     taken on the current kernel source."""
     try:
-        txt = open(PROFILE).read()
+        txt = open(path).read()
     except OSError:
         return None
     vals = dict(line.split("=", 1) for line in txt.splitlines() if "=" in line and not line.startswith("#"))
@@ -73,9 +74,9 @@ def _profile_value(key: str):
         return None
 
 
-def profile_traffic():
+def profile_traffic(path: str = PROFILE):
     """DRAM bytes per launch of the step kernel (ncu)."""
-    return _profile_value("dram_bytes_per_launch")
+    return _profile_value("dram_bytes_per_launch", path)
 
 
 class ClockSampler:
@@ -172,7 +173,11 @@ def run_ours(args):
     world, rank, local = setup_dist()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    prob = gi.lid_cavity(n=args.cavity_n)
+    spiral = args.grid == "spiral"
+    if spiral:   # the same cavity on a general orthogonal grid given node by node
+        prob = gi.spiral_cavity(args.cavity_n, args.cavity_n, Re=1000.0, u_lid=0.05, mach_matched=True)
+    else:
+        prob = gi.lid_cavity(n=args.cavity_n)
     _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
     spec = prob.lattice_spec(cs2)
     lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream)
@@ -233,13 +238,15 @@ def run_ours(args):
     launch_s = ms_per_step * 1e-3 / chunk
     achieved = bpn * nodes / launch_s / 1e9
     peak = float(peaks.get("hbm_gbs", 6400.0))
-    traffic = profile_traffic()
+    prof = PROFILE_SPIRAL if spiral else PROFILE
+    captured = args.cavity_n == 512 and args.storage == "fp32"   # the captures are of FP32 512^2 launches
+    traffic = profile_traffic(prof) if captured else None
     clocks = clk.summary()
     # instruction-issue view of the same kernel: warp instructions per node
     # (ncu, current source) x node updates per second against one warp
     # instruction per scheduler per cycle at the SM clock seen under load
     issue = None
-    ipn = _profile_value("warp_instructions_per_node")
+    ipn = _profile_value("warp_instructions_per_node", prof) if captured else None
     if ipn and clocks and clocks.get("sm_mhz"):
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         ach = ipn * nodes / launch_s
@@ -261,7 +268,9 @@ def run_ours(args):
             "dtype": "f32" if args.storage == "fp32" else f"f32 arithmetic, {args.storage} storage",
             "data": "synthetic (lid-driven cavity from rest, seeded parameters)",
             "config": {"workload": prob.name + f"_{args.storage}", "nodes": nodes,
-                       "lb_steps_per_bench_step": chunk, "map": "tanh beta=2 on both axes",
+                       "lb_steps_per_bench_step": chunk,
+                       "map": ("logarithmic spiral given node by node (every theta_ij non-zero)" if spiral
+                               else "tanh beta=2 on both axes"),
                        "Re": 1000, "u_lid": round(spec["walls"]["N"]["u"], 6), "lid_mach": 0.087, "storage": args.storage,
                        "parallelism": f"replicas x{world}" if world > 1 else "single lattice",
                        "l2": f"flushed between timed steps (256 MiB write); lattice ({nodes * bpn / 1e6:.0f} MB) "
@@ -271,7 +280,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": src, "bytes_per_node": bpn,
-                         "kernel": "goc::step_kernel<float,false>", "launch_us": round(launch_s * 1e6, 3),
+                         "kernel": "goc::step_kernel<float,0,0,2>" if spiral else "goc::step_kernel<float,0,0,0>",
+                         "launch_us": round(launch_s * 1e6, 3),
                          "launch_config": lat.launch_config, "issue": issue},
             "cpu_baseline": cpu,
             "gpu_launches": args.steps * chunk,
@@ -668,6 +678,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     ap.add_argument("--cavity-n", type=int, default=512, help="cavity side (512 is the benchmark workload)")
+    ap.add_argument("--grid", default="tanh", choices=["tanh", "spiral"],
+                    help="cavity grid: tanh map on both axes (the benchmark), or a logarithmic-spiral node table")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
     ap.add_argument("--workload", default="cavity",

@@ -309,9 +309,12 @@ def spiral_grid(nx: int, ny: int, c: float, phi: float) -> dict:
 
 
 def spiral_cavity(nx: int = 40, ny: int = 37, c: float | None = None, phi: float = 0.6, Re: float = 50.0,
-                  u_lid: float = 0.05) -> Problem:
+                  u_lid: float = 0.05, mach_matched: bool = False) -> Problem:
     """Lid-driven cavity on the logarithmic-spiral grid (every theta_ij
-    non-zero): walls on all sides, the N wall moving along xi1."""
+    non-zero): walls on all sides, the N wall moving along xi1
+    (mach_matched: the lid at the Mach number u_lid has on a standard
+    lattice)."""
     c = 1.0 / math.hypot(nx, ny) if c is None else c
-    return Problem("cavity", nx, ny, {"kind": "table"}, {"kind": "uniform"}, {"Re": Re, "u_lid": u_lid},
-                   metric=spiral_grid(nx, ny, c, phi))
+    return Problem("cavity", nx, ny, {"kind": "table"}, {"kind": "uniform"},
+                   {"Re": Re, "u_lid": u_lid, "mach_matched": mach_matched},
+                   metric=spiral_grid(nx, ny, c, phi), name=f"spiral_cavity_{nx}x{ny}")

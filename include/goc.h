@@ -272,7 +272,9 @@ long long goc_steps_done(const goc_lattice *lat);
 goc_status goc_footprint(const goc_lattice *lat, long long *nodes, long long *device_bytes);
 
 /* Algorithmic HBM bytes one node update moves (populations and stored force
- * read and written once, plus the per-node share of the metric tables). */
+ * read and written once, plus the per-node share of the metric tables: the
+ * per-axis tables amortised over the other axis, or the 10 FP32 values per
+ * node of a TABLE map). */
 double goc_bytes_per_node(const goc_lattice *lat);
 
 /* ---- checkpoint / resume ----------------------------------------------- */

@@ -994,7 +994,8 @@ double goc_bytes_per_node(const goc_lattice *L) {
     if (L->scheme == 1) return 2.0 * 9.0 * es;          // populations only, read + write
     double b = 2.0 * (9.0 + 2.0) * es;                  // populations + stored force, read + write
     if (L->mhd.enabled) b += 2.0 * 10.0 * es;           // MIE populations
-    b += 4.0 * 7.0 * (1.0 / L->ny + 1.0 / L->nx);       // per-axis tables amortised over the lattice
+    if (L->sp.curv == 2) return b + 4.0 * 10.0;         // node-table metric: 10 FP32 values per node
+    b += 4.0 * (L->sp.curv ? 8.0 : 7.0) / L->ny + 4.0 * 7.0 / L->nx;   // per-axis tables amortised over the lattice
     return b;
 }
 
