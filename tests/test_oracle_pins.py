@@ -821,3 +821,91 @@ def test_reflected_spiral_grid_gives_the_reflected_solution():
     np.testing.assert_allclose(ra, rb[::-1], rtol=1e-13)
     np.testing.assert_allclose(ua, ub[::-1], atol=1e-12 * scale)
     np.testing.assert_allclose(va, -vb[::-1], atol=1e-12 * scale)
+
+
+# ---- MIE on the curvilinear grid (Appendix G with theta21, source Y) -----------
+def _annulus_mie(n1, rot, b_in=0.02, b_out=0.01, steps_per_diffusion=1.0):
+    """Kinematic MIE on the annular sector: rigid rotation U2 = Omega r (the
+    Taylor-Couette solution for wall speeds Omega R1, Omega R2), walls
+    imposing B = (b_in, 0) and (b_out, 0), mu_m = 1e8 so that the Lorentz
+    force is negligible.  Returns the oracle's fields after n1^2/eta steps
+    from (B1 linear in xi1, B2 = 0) and the steady solution of Eq. 5_C."""
+    a = n1 / 8.0
+    p = gi.taylor_couette(n1=n1, n2=6, r_in=a, sectors=360.0 * n1 / (256.0 * 6.0), Re=10.0, u_in=1.0, u_out=1.0)
+    m = oracle.build_metric(p.lattice_spec(1.0))
+    spec = p.lattice_spec(m.cs2())
+    r_in, r_out = a, a + n1
+    lam = math.log(r_out / r_in) / n1                  # r = R1 exp(lam xi1), h1 = lam r
+    om = rot * 0.16 / n1 / r_out
+    spec["walls"]["W"] = {"u": om * r_in, "B": (b_in, 0.0)}
+    spec["walls"]["E"] = {"u": om * r_out, "B": (b_out, 0.0)}
+    spec["mhd"] = {"tau_m": 1.0, "mu_m": 1e8}
+    x = np.arange(n1) + 0.5
+    b1a = b_in + (b_out - b_in) * x / n1
+    spec["init"] = {"u1": 0.0, "u2": np.broadcast_to(om * m.radius[None, :], (6, n1)).copy()}
+    o = oracle.Oracle(spec)
+    o.initialize(b1=np.broadcast_to(b1a[None, :], (6, n1)).copy(), b2=np.zeros((6, n1)))
+    eta = o.par["eta"]
+    # Eq. 5_C at steady state with h2/h1 constant on this grid: B1'' = 0, and
+    # eta (h2/h1) B2'' = d/dxi1(h2 A21) + Y2 with A21 = -B1 U2, Y2 = h1 h2 A21 theta21,
+    # i.e. B2'' = -(lam Omega/eta) r^2 (3 lam B1 + B1'); solved on a fine grid.
+    X = np.linspace(0.0, n1, 8001)
+    s = (b_out - b_in) / n1
+    rhs = -(lam * om / eta) * (r_in * np.exp(lam * X)) ** 2 * (3 * lam * (b_in + s * X) + s)
+    hX = X[1] - X[0]
+    k = len(X) - 2
+    lap = (np.diag(-2.0 * np.ones(k)) + np.diag(np.ones(k - 1), 1) + np.diag(np.ones(k - 1), -1)) / hX ** 2
+    b2a = np.interp(x, X, np.concatenate([[0.0], np.linalg.solve(lap, rhs[1:-1]), [0.0]]))
+    o.step(int(steps_per_diffusion * n1 * n1 / eta))
+    return o.fields(), b1a, b2a, om * m.radius
+
+
+def test_curvilinear_mie_reaches_the_steady_solution_of_its_equation():
+    """Sec. 8's annular sector with the MIE of Appendix G (theta21 = 1/r in
+    the gradient formula, the g^corr terms, J3 and the source Y of Eq. 6ab_C
+    as printed): B1 relaxes to the solution of Eq. 5_C (linear in xi1, since
+    h2/h1 is constant) and B2, driven by the rotation through the advection
+    tensor A and the source Y, to the solution of its ODE -- both at second
+    order in the radial nodes.  A Y of the opposite sign leaves B2 75% off."""
+    errs = []
+    for n1 in (16, 32):
+        f, b1a, b2a, ua = _annulus_mie(n1, rot=1.0)
+        rho, u1, u2, b1, b2 = f[:5]
+        assert np.linalg.norm(u2[0] - ua) / np.linalg.norm(ua) < 1e-3
+        assert np.abs(b1 - b1[0]).max() < 1e-12 and np.abs(b2 - b2[0]).max() < 1e-12   # azimuthally uniform
+        errs.append((np.linalg.norm(b1[0] - b1a) / np.linalg.norm(b1a),
+                     np.linalg.norm(b2[0] - b2a) / np.linalg.norm(b2a)))
+    (e1a, e2a), (e1b, e2b) = errs
+    assert e1b < 3e-3 and e2b < 1e-2, errs
+    assert math.log2(e1a / e1b) > 1.8 and math.log2(e2a / e2b) > 1.8, errs
+
+
+def test_transposed_annulus_with_the_mie_gives_the_transposed_solution():
+    """The annulus with its radial direction along xi2 (theta12 in place of
+    theta21) and the MIE: B1 and B2 exchange roles, so the fields are the
+    transposed ones with the components swapped.  Pins the theta12 terms of
+    the gradient formula, g^corr, J3, Y and the B solve against the theta21
+    ones (pinned above)."""
+    n1 = 20
+    p = gi.taylor_couette(n1=n1, n2=5, r_in=3.0, sectors=360.0 * n1 / (256.0 * 6.0), Re=10.0, u_in=1.0, u_out=1.5)
+    m = oracle.build_metric(p.lattice_spec(1.0))
+    a = p.lattice_spec(m.cs2())
+    a["walls"]["W"] = dict(a["walls"]["W"], B=(0.02, 0.005))
+    a["walls"]["E"] = dict(a["walls"]["E"], B=(0.01, -0.004))
+    a["mhd"] = {"tau_m": 0.9, "mu_m": 2.0}
+    b = dict(a)
+    b.update(nx=a["ny"], ny=a["nx"], map1={"kind": "table"}, map2={"kind": "uniform"}, metric=_transposed_table(m),
+             walls={"S": dict(a["walls"]["W"], B=(0.005, 0.02)), "N": dict(a["walls"]["E"], B=(-0.004, 0.01)),
+                    "W": None, "E": None})
+    oa, ob = oracle.Oracle(a), oracle.Oracle(b)
+    oa.step(400)
+    ob.step(400)
+    ra, ua, va, b1a, b2a = oa.fields()[:5]
+    rb, ub, vb, b1b, b2b = ob.fields()[:5]
+    sb = max(np.abs(b1a).max(), np.abs(b2a).max())
+    assert np.abs(b2a).max() > 1e-3
+    np.testing.assert_allclose(ra, rb.T, rtol=1e-13)
+    np.testing.assert_allclose(va, ub.T, rtol=1e-11, atol=1e-13 * np.abs(va).max())
+    np.testing.assert_allclose(ua, vb.T, atol=1e-12 * np.abs(va).max())
+    np.testing.assert_allclose(b1a, b2b.T, atol=1e-12 * sb)
+    np.testing.assert_allclose(b2a, b1b.T, atol=1e-12 * sb)
