@@ -72,16 +72,21 @@ typedef enum { GOC_BC_PERIODIC = 0, GOC_BC_WALL = 1 } goc_bc;
  *           5_annularsector) with cell-centred radial nodes:
  *           r = r_inner exp(ln(r_outer/r_inner) xi1/nx), h1 = r ln(r_outer/r_inner)/nx,
  *           h2 = 2 pi r/(sectors ny), theta11 = theta21 = 1/r, theta12 = theta22 = 0.
- *           Needs W/E walls, periodic S/N, kind[1] = UNIFORM, scheme 0, no MIE;
- *           not for batches.  Wall speeds (wall_u[W], wall_u[E]) are azimuthal.
+ *           Needs W/E walls, periodic S/N, kind[1] = UNIFORM, scheme 0; not for
+ *           batches.  Wall speeds (wall_u[W], wall_u[E]) are azimuthal.  With the
+ *           MIE, Appendix G's curvature terms (theta21 in the local gradient
+ *           formula, g^corr and J3, the source Y of Eq. 6ab_C) are active and
+ *           the MIE populations are stored without a reference field.
  *  TABLE    (kind[0]; kind[1] ignored) a general orthogonal grid given node by
  *           node: `table` holds six [ny][nx] planes h1, h2, theta11, theta12,
  *           theta21, theta22 (Eq. metricfactor, Eq. curvaturematrix) and
- *           `wall_table` the wall-normal metric factor along each wall: h1 at
- *           the W wall over j, h1 at E over j, h2 at S over i, h2 at N over i
- *           (2 ny + 2 nx values; used by moving walls, any value on periodic
- *           sides).  Both are host arrays read during goc_create only; every
- *           h > 0.  Scheme 0, no MIE, not for batches.
+ *           `wall_table` the metric factors at the wall points: first the
+ *           wall-normal one (h1 at the W wall over j, h1 at E over j, h2 at S
+ *           over i, h2 at N over i: 2 ny + 2 nx values), then the tangential
+ *           one in the same order (h2 at W and E, h1 at S and N).  Moving walls
+ *           use the normal factor, the MIE wall condition h1 h2; any values on
+ *           periodic sides.  Both are host arrays read during goc_create only;
+ *           every h > 0.  Scheme 0, not for batches; the MIE as for ANNULUS.
  * Wall maps (TANH2 with beta > 0, ROBERTS, TANH1, SINH) need a wall axis; SINE a
  * periodic one. */
 typedef enum { GOC_MAP_UNIFORM = 0, GOC_MAP_TANH2 = 1, GOC_MAP_SINE = 2, GOC_MAP_ROBERTS = 3,
@@ -107,7 +112,7 @@ typedef struct {
     double r_inner, r_outer;  /* ANNULUS radii, 0 < r_inner < r_outer */
     double sectors;           /* ANNULUS: the sector spans 2 pi / sectors (> 0) */
     const double *table;      /* TABLE: [6][ny][nx] h1, h2, theta11, theta12, theta21, theta22 */
-    const double *wall_table; /* TABLE: [2 ny + 2 nx] wall-normal metric at W, E, S, N */
+    const double *wall_table; /* TABLE: [2][2 ny + 2 nx] wall-normal, then tangential metric at W, E, S, N */
 } goc_map;
 
 typedef struct {

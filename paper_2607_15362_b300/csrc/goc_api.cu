@@ -206,10 +206,16 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
     const bool pdl = L->cfg_pdl != 0;
-    if (L->sp.curv == 2) {   // node-table metric (central-moment collision, no MIE)
+    if (L->sp.curv == 2 && L->mhd.enabled) {   // node-table metric (central-moment collision)
+        const int grid = step_grid<S, true, false, 2>(ntiles, &smem);
+        CU(launch_pdl(pdl, step_kernel<S, true, false, 2>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+    } else if (L->sp.curv == 2) {
         const int grid = step_grid<S, false, false, 2>(ntiles, &smem);
         CU(launch_pdl(pdl, step_kernel<S, false, false, 2>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
-    } else if (L->sp.curv) {   // curvilinear column metric (central-moment collision, no MIE)
+    } else if (L->sp.curv && L->mhd.enabled) {   // curvilinear column metric (central-moment collision)
+        const int grid = step_grid<S, true, false, 1>(ntiles, &smem);
+        CU(launch_pdl(pdl, step_kernel<S, true, false, 1>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+    } else if (L->sp.curv) {
         const int grid = step_grid<S, false, false, 1>(ntiles, &smem);
         CU(launch_pdl(pdl, step_kernel<S, false, false, 1>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     } else if (L->scheme == 2 || L->scheme == 3) {   // collision on raw moments (Appendix F SRT, Appendix D MRT)
@@ -391,12 +397,16 @@ goc_status validate(const goc_grid *grid, const goc_map *map) {
                 return fail(GOC_EINVAL, "TABLE: h1, h2 must be finite and > 0 at every node");
         for (long long n = 2 * N; n < 6 * N; n++)
             if (!std::isfinite(map->table[n])) return fail(GOC_EINVAL, "TABLE: theta must be finite");
-        for (int s = 0; s < 4; s++) {   // wall-normal metric of the wall sides
+        const int nw = 2 * grid->ny + 2 * grid->nx;
+        for (int s = 0; s < 4; s++) {   // wall-normal and tangential metric of the wall sides
             if (grid->bc[s] != GOC_BC_WALL) continue;
             const int off = s < 2 ? s * grid->ny : 2 * grid->ny + (s - 2) * grid->nx, n = s < 2 ? grid->ny : grid->nx;
-            for (int k = 0; k < n; k++)
-                if (!(map->wall_table[off + k] > 0.0 && std::isfinite(map->wall_table[off + k])))
-                    return fail(GOC_EINVAL, "TABLE: wall_table must be finite and > 0 along the walls");
+            for (int t = 0; t < 2; t++)
+                for (int k = 0; k < n; k++) {
+                    const double v = map->wall_table[t * nw + off + k];
+                    if (!(v > 0.0 && std::isfinite(v)))
+                        return fail(GOC_EINVAL, "TABLE: wall_table must be finite and > 0 along the walls");
+                }
         }
         return GOC_OK;
     }
@@ -657,7 +667,6 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     }
     if (map->kind[0] == GOC_MAP_ANNULUS || map->kind[0] == GOC_MAP_TABLE) {
         const char *what = map->kind[0] == GOC_MAP_ANNULUS ? "the annulus" : "the TABLE map";
-        if (mhd && mhd->enabled) return fail(GOC_EUNSUPPORTED, "%s runs without the MIE", what);
         if (exec && exec->scheme != 0) return fail(GOC_EUNSUPPORTED, "%s runs the central-moment scheme (0)", what);
     }
     goc_lattice *L = new (std::nothrow) goc_lattice();
@@ -724,11 +733,14 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     goc_map uni_map = *map;
     if (table) uni_map.kind[0] = uni_map.kind[1] = GOC_MAP_UNIFORM;
     TRY(compute_metric(grid, table ? &uni_map : map, L->stream, L->m1, L->m2, L->red));
-    double hw1[2], hw2[2], qh;
+    double hw1[2], hw2[2], qh, hwt1[2] = {1.0, 1.0};
     {
         cudaError_t e = cudaMemcpyAsync(&qh, L->red, sizeof(double), cudaMemcpyDeviceToHost, L->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hw1, L->m1 + L->nx, 2 * sizeof(double), cudaMemcpyDeviceToHost, L->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hw2, L->m2 + L->ny, 2 * sizeof(double), cudaMemcpyDeviceToHost, L->stream);
+        if (e == cudaSuccess && curv)   // annulus: h2 at the radial walls (tangential factor)
+            e = cudaMemcpyAsync(hwt1, L->m1 + 2 * (L->nx + 2) + L->nx, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                L->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
         if (e != cudaSuccess) {
             free_lattice(L);
@@ -774,15 +786,20 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         const long long N = (long long)L->nx * L->ny;
         const int wmax = std::max(L->nx, L->ny);
         TRY(dalloc(L, &L->gtab, 6 * N * sizeof(double)));
-        TRY(dalloc(L, &L->gm, (10 * L->plane + 4 * (long long)wmax) * sizeof(float)));
-        std::vector<float> walls(4 * (size_t)wmax, 1.f);
-        for (int k = 0; k < L->ny; k++) {
-            walls[k] = (float)map->wall_table[k];                           // W: h1 over j
-            walls[wmax + k] = (float)map->wall_table[L->ny + k];            // E
-        }
-        for (int k = 0; k < L->nx; k++) {
-            walls[2 * wmax + k] = (float)map->wall_table[2 * L->ny + k];         // S: h2 over i
-            walls[3 * wmax + k] = (float)map->wall_table[2 * L->ny + L->nx + k];  // N
+        TRY(dalloc(L, &L->gm, (10 * L->plane + 8 * (long long)wmax) * sizeof(float)));
+        std::vector<float> walls(8 * (size_t)wmax, 1.f);
+        const int nw = 2 * L->ny + 2 * L->nx;
+        for (int t = 0; t < 2; t++) {   // t = 0: wall-normal factor, 1: tangential
+            const double *w = map->wall_table + t * nw;
+            float *o = walls.data() + 4 * t * (size_t)wmax;
+            for (int k = 0; k < L->ny; k++) {
+                o[k] = (float)w[k];                       // W (over j)
+                o[wmax + k] = (float)w[L->ny + k];        // E
+            }
+            for (int k = 0; k < L->nx; k++) {
+                o[2 * wmax + k] = (float)w[2 * L->ny + k];            // S (over i)
+                o[3 * wmax + k] = (float)w[2 * L->ny + L->nx + k];    // N
+            }
         }
         cudaError_t e = cudaMemsetAsync(L->gm, 0, 10 * L->plane * sizeof(float), L->stream);
         if (e == cudaSuccess)
@@ -856,8 +873,11 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         p.uw[s] = grid->bc[s] == GOC_BC_WALL ? (float)grid->wall_u[s] : 0.f;
         p.hwn[s] = (float)L->hw[s];
         if (p.uw[s] != 0.f) p.moving = 1;
-        p.bw[s][0] = (float)grid->wall_b[s][0];
-        p.bw[s][1] = (float)grid->wall_b[s][1];
+        // the column metric's MIE wall condition takes h1 h2 at the wall: its
+        // tangential factor h2 (constant along the radial walls) is folded in here
+        const double ht = (curv && s < 2) ? hwt1[s] : 1.0;
+        p.bw[s][0] = (float)(ht * grid->wall_b[s][0]);
+        p.bw[s][1] = (float)(ht * grid->wall_b[s][1]);
     }
     // storage scales (1 for FP32; for 16-bit a per-lattice velocity scale)
     p.sf = p.isf = p.sF = p.isF = p.sg = p.isg = 1.f;
@@ -882,9 +902,15 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         p.imum = (float)(1.0 / L->mhd.mu_m);
         p.W0 = (float)(1.0 - 2.0 * L->csm2);
         p.W1 = (float)(0.5 * L->csm2);
-        p.brest[0] = (float)L->mhd.b_init[0];
-        p.brest[1] = (float)L->mhd.b_init[1];
+        // storage reference field: the initial uniform field on straight grids;
+        // curvilinear grids store g itself (B_rest = 0)
+        p.brest[0] = p.curv ? 0.f : (float)L->mhd.b_init[0];
+        p.brest[1] = p.curv ? 0.f : (float)L->mhd.b_init[1];
         double bmax = std::max(std::fabs(L->mhd.b_init[0]), std::fabs(L->mhd.b_init[1]));
+        if (p.curv)
+            for (int s = 0; s < 4; s++)
+                if (grid->bc[s] == GOC_BC_WALL)
+                    bmax = std::max(bmax, std::max(std::fabs(grid->wall_b[s][0]), std::fabs(grid->wall_b[s][1])));
         if (L->storage != GOC_FP32 && bmax > 0) {
             p.sg = (float)(bmax / 256.0);
             p.isg = (float)(256.0 / bmax);

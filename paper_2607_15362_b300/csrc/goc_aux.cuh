@@ -302,10 +302,11 @@ __global__ void init_kernel(const InitParams q) {
         const double dB1 = dfd64(Bf[c], i, j, p.nx, p.ny, 0, p.per_x);
         const double dB2 = dfd64(Bf[c], i, j, p.nx, p.ny, 1, p.per_y);
         const double A1 = U1 * B[c] - B[0] * U[c], A2 = U2 * B[c] - B[1] * U[c];
-        const double lc1 = q.eta * (H - h2 / h1) * dB1 + q.eta * h1 * H * t11 * B[c];
-        const double lc2 = q.eta * (H - h1 / h2) * dB2 + q.eta * H * h2 * t22 * B[c];
+        // Eq. 42_C (theta21, theta12 on curvilinear grids)
+        const double lc1 = q.eta * (H - h2 / h1) * dB1 + q.eta * h1 * H * (t11 + t21) * B[c];
+        const double lc2 = q.eta * (H - h1 / h2) * dB2 + q.eta * H * h2 * (t22 + t12) * B[c];
         // relative to the pre-collision reference g_ref- = W H B_rest - e.M/2 with
-        // M = csm2/2 (h1 H theta11, H h2 theta22) B_rest
+        // M = csm2/2 (h1 H theta11, H h2 theta22) B_rest (B_rest = 0 on curvilinear grids)
         const double M1 = 0.5 * q.csm2 * h1 * H * t11 * p.brest[c], M2 = 0.5 * q.csm2 * H * h2 * t22 * p.brest[c];
         for (int a = 0; a < 5; a++) {
             const double W = a == 0 ? 1.0 - 2.0 * q.csm2 : 0.5 * q.csm2;
@@ -348,11 +349,26 @@ __global__ void moments_kernel(const StepParams p, double *out) {
     out[2 * N + n] = U2;
     double B1 = 0.0, B2 = 0.0;
     if constexpr (MHD) {
-        float gd[5];
-        pull_mie<true>(p, src, i, j, h1, h2, 0, gd);
-        B1 = (double)p.brest[0] + (double)((gd[0] + gd[1] + gd[2] + gd[3] + gd[4]) / (h1 * h2));
-        pull_mie<true>(p, src, i, j, h1, h2, 1, gd);
-        B2 = (double)p.brest[1] + (double)((gd[0] + gd[1] + gd[2] + gd[3] + gd[4]) / (h1 * h2));
+        float gd[2][5];
+        for (int c = 0; c < 2; c++) {
+            if (p.curv == 2) pull_mie<true, 2>(p, src, i, j, h1, h2, c, gd[c]);
+            else if (p.curv) pull_mie<true, 1>(p, src, i, j, h1, h2, c, gd[c]);
+            else pull_mie<true>(p, src, i, j, h1, h2, c, gd[c]);
+        }
+        const float s0 = (gd[0][0] + gd[0][1] + gd[0][2] + gd[0][3] + gd[0][4]) / (h1 * h2);
+        const float s1 = (gd[1][0] + gd[1][1] + gd[1][2] + gd[1][3] + gd[1][4]) / (h1 * h2);
+        if (p.curv) {   // h1 h2 B = sum g - Y/2 (Eq. 13_C, Eq. 6ab_C), as in the step kernel
+            const float t12 = p.curv == 2 ? gm_at(p.gm, p.plane, p.pitch, 3, i, j) : 0.f;
+            const float t21 = p.curv == 2 ? gm_at(p.gm, p.plane, p.pitch, 4, i, j) : curv_t21(p.ax1, p.nx, i);
+            const float a11 = 1.f + 0.5f * t12 * U2, a12 = -0.5f * t12 * U1;
+            const float a21 = -0.5f * t21 * U2, a22 = 1.f + 0.5f * t21 * U1;
+            const float det = a11 * a22 - a12 * a21;
+            B1 = (double)((s0 * a22 - a12 * s1) / det);
+            B2 = (double)((a11 * s1 - a21 * s0) / det);
+        } else {
+            B1 = (double)p.brest[0] + (double)s0;
+            B2 = (double)p.brest[1] + (double)s1;
+        }
     }
     out[3 * N + n] = B1;
     out[4 * N + n] = B2;

@@ -39,7 +39,8 @@ struct Axis {
 };
 
 // the node-by-node metric (StepParams.gm): plane k at node (i, j), and the
-// wall-normal metric factor at position k along wall `side`
+// wall metric at position k along wall `side` (0-3: the wall-normal factor at
+// W, E, S, N; 4-7: the tangential one)
 __device__ __forceinline__ float gm_at(const float *gm, long long plane, int pitch, int k, int i, int j) {
     return gm[k * plane + (long long)j * pitch + i];
 }
@@ -61,7 +62,8 @@ struct StepParams {
                                // 2: metric given node by node (gm)
     // node-by-node metric (curv = 2): FP32 planes [10][plane] h1, h2, theta11,
     // theta12, theta21, theta22 and the pull corrections of links 1..4 (into
-    // the node), then [4][max(nx, ny)] the wall-normal metric along W, E, S, N
+    // the node), then [8][max(nx, ny)] the wall-normal metric along W, E, S, N
+    // and the tangential one
     const float *gm;
     int nopull;                // 1: the input buffer holds pre-collision populations (the
                                // initial state f^0 of Appendix C.1): read them in place

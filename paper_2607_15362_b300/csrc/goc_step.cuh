@@ -220,7 +220,7 @@ __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, i
 // anti-bounce-back g_a = -g~_abar + 2 W_a h_wall B_wall,c (Appendix G,
 // boundary conditions), h_wall = h1,wall h2,wall, which in these variables is
 // -s_abar + 2 W_a (h_wall B_wall - H B_rest) + e_a.M.
-template <bool CHECKS, class Src>
+template <bool CHECKS, int GEOM = 0, class Src>
 __device__ __forceinline__ void pull_mie(const StepParams &p, const Src &src, int i, int j, float h1, float h2,
                                          int c, float d[5]) {
     const float H = h1 * h2;
@@ -245,10 +245,21 @@ __device__ __forceinline__ void pull_mie(const StepParams &p, const Src &src, in
         float v;
         if (!ox && !oy) {
             v = src.gv(c * 5 + a, si, sj);
-            if (a == 1) v += br * h2 * p.ax1.dm[i];
-            if (a == 3) v += br * h2 * p.ax1.dp[i];
-            if (a == 2) v += br * h1 * p.ax2.dm[j];
-            if (a == 4) v += br * h1 * p.ax2.dp[j];
+            if (GEOM == 0) {   // curvilinear grids store g itself (B_rest = 0)
+                if (a == 1) v += br * h2 * p.ax1.dm[i];
+                if (a == 3) v += br * h2 * p.ax1.dp[i];
+                if (a == 2) v += br * h1 * p.ax2.dm[j];
+                if (a == 4) v += br * h1 * p.ax2.dp[j];
+            }
+        } else if (GEOM) {   // h_wall = h1 h2 at the wall point
+            // (the column metric has bw premultiplied by the tangential factor,
+            // which is constant along its radial walls)
+            const int side = oy ? (g2(a) > 0 ? SIDE_S : SIDE_N) : (g1(a) > 0 ? SIDE_W : SIDE_E);
+            const int k = oy ? i : j;
+            const float hw = GEOM == 2 ? gm_wall(p.gm, p.plane, p.nx, p.ny, side, k) *
+                                             gm_wall(p.gm, p.plane, p.nx, p.ny, 4 + side, k)
+                                       : p.hwn[side];
+            v = -src.gv(c * 5 + gopp(a), i, j) + 2.f * p.W1 * hw * p.bw[side][c];
         } else {
             int side = oy ? (g2(a) > 0 ? SIDE_S : SIDE_N) : (g1(a) > 0 ? SIDE_W : SIDE_E);
             float hw = oy ? h1 * p.hwn[side] : p.hwn[side] * h2;
@@ -457,6 +468,14 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         for (int r = 0; r < R; r++) rng[r] = sr ? node_seed((uint32_t)idx[r], step) : 0u;
     }
     V FL1 = bc<V>(0.f), FL2 = bc<V>(0.f), B1 = bc<V>(0.f), B2 = bc<V>(0.f);
+    // theta12, theta21 of curvilinear grids (the column metric has theta12 = 0)
+    float t21 = 0.f, t12 = 0.f;
+    if constexpr (GEOM == 2) {
+        t12 = gm_at(p.gm, p.plane, p.pitch, 3, i, j[0]);
+        t21 = gm_at(p.gm, p.plane, p.pitch, 4, i, j[0]);
+    } else if constexpr (GEOM == 1) {
+        t21 = curv_t21(p.ax1, p.nx, i);
+    }
 
     // ---- MIE (Appendix G): local dB, J3, Lorentz force, SRT collision -------
     if constexpr (MHD) {
@@ -467,7 +486,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
             float t[R][5];
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                if (own[r]) pull_mie<CHECKS>(p, src, i, j[r], h1, h2n[r], c, t[r]);
+                if (own[r]) pull_mie<CHECKS, GEOM>(p, src, i, j[r], h1, h2n[r], c, t[r]);
                 else {
 #pragma unroll
                     for (int a = 0; a < 5; a++) t[r][a] = 0.f;
@@ -480,8 +499,19 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
                 for (int r = 0; r < R; r++) u_[r] = t[r][a];
                 gd[c][a] = pack<V>(u_);
             }
-            // h1 h2 B = sum g (Eq. 13_C, Y = 0); sum g_ref- = H B_rest
+            // h1 h2 B = sum g - Y/2 (Eq. 13_C; Y = 0 on straight grids); sum g_ref- = H B_rest
             dBc[c] = (gd[c][0] + gd[c][1] + gd[c][2] + gd[c][3] + gd[c][4]) * iH;
+        }
+        if constexpr (GEOM) {
+            // curvilinear grids (B_rest = 0): Y_1 = H theta12 (U2 B1 - U1 B2),
+            // Y_2 = H theta21 (U1 B2 - U2 B1) (Eq. 6ab_C) are linear in B, so
+            // B = sum g / H - Y / (2 H) is a 2 x 2 solve at the node
+            const V a11 = fmav(U2, 0.5f * t12, bc<V>(1.f)), a12 = U1 * (-0.5f * t12);
+            const V a21 = U2 * (-0.5f * t21), a22 = fmav(U1, 0.5f * t21, bc<V>(1.f));
+            const V idet = rcpv(a11 * a22 - a12 * a21);
+            const V s0 = dBc[0], s1 = dBc[1];
+            dBc[0] = (s0 * a22 - a12 * s1) * idet;
+            dBc[1] = (a11 * s1 - a21 * s0) * idet;
         }
         B1 = dBc[0] + p.brest[0];
         B2 = dBc[1] + p.brest[1];
@@ -493,16 +523,19 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         // against the B_rest part of the curvature term.
         const V k1 = rcpv(fmav(h2 * ih1, p.taum - 0.5f, H * 0.5f) * p.csm2);
         const V k2 = rcpv(fmav(h1 * ih2, p.taum - 0.5f, H * 0.5f) * p.csm2);
-        const V m1 = H * (0.5f * p.csm2 * h1 * t11), m2 = H * h2 * t22 * (0.5f * p.csm2);
+        // (theta11 + theta21, theta22 + theta12 on curvilinear grids)
+        const V m1 = H * (0.5f * p.csm2 * h1 * (GEOM ? t11 + t21 : t11)), m2 = H * h2 * t22 * (0.5f * p.csm2);
+        const V m2c = GEOM ? fmav(H * h2, 0.5f * p.csm2 * t12, m2) : m2;
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             const V L1 = fmav(m1, dBc[c], (gd[c][1] - gd[c][3]) - h2 * A1[c]);
-            const V L2 = fmav(m2, dBc[c], (gd[c][2] - gd[c][4]) - A2[c] * h1);
+            const V L2 = fmav(m2c, dBc[c], (gd[c][2] - gd[c][4]) - A2[c] * h1);
             dB1[c] = bc<V>(0.f) - L1 * k1;
             dB2[c] = bc<V>(0.f) - L2 * k2;
         }
         // current density (Eq. currentdensity-GOC) and Lorentz force (Eq. Lorentzforce-GOC)
-        const V J3 = iH * (h2 * dB1[1] - dB2[0] * h1) * p.imum;
+        V J3 = iH * (h2 * dB1[1] - dB2[0] * h1) * p.imum;
+        if constexpr (GEOM) J3 = fmav(fmav(B2, t21, B1 * (-t12)), p.imum, J3);   // + (B2 theta21 - B1 theta12)/mu
         FL1 = bc<V>(0.f) - J3 * B2;
         FL2 = J3 * B1;
         // SRT collision (Eq. 12_C, S = 0 on straight grids) with g^eq of
@@ -510,14 +543,20 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         // references: s = d (1 - 1/tau_m) + G/tau_m, G = g^eq - g_ref- without the
         // B_rest curvature part, which cancels with the change g_ref- -> g_ref+.
         const V e1c = (H - h2 * ih1) * p.eta, e2c = (H - h1 * ih2) * p.eta;
-        const V m1e = H * (p.eta * h1 * t11), m2e = H * h2 * t22 * p.eta;
+        const V m1e = H * (p.eta * h1 * (GEOM ? t11 + t21 : t11)), m2e = GEOM ? H * h2 * ((t22 + t12) * p.eta) : H * h2 * t22 * p.eta;
         const float keep = 1.f - p.itaum, w0 = p.W0 * p.itaum, w1 = p.W1 * p.itaum;
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             const V x1 = fmav(h2, A1[c], fmav(e1c, dB1[c], m1e * dBc[c])) * p.icsm2;
             const V x2 = fmav(h1, A2[c], fmav(e2c, dB2[c], m2e * dBc[c])) * p.icsm2;
             const V base = H * dBc[c];
-            const V G[5] = {base * w0, (base + x1) * w1, (base + x2) * w1, (base - x1) * w1, (base - x2) * w1};
+            V G[5] = {base * w0, (base + x1) * w1, (base + x2) * w1, (base - x1) * w1, (base - x2) * w1};
+            if constexpr (GEOM) {   // source S_a = -W_a Y_c (Eq. 8a_C), weight (1 - 1/(2 tau_m)) in Eq. 12_C
+                const V ys = (c == 0 ? H * t12 * A2[0] : H * t21 * A1[1]) * (0.5f * p.itaum - 1.f);
+                G[0] = fmav(ys, p.W0, G[0]);
+#pragma unroll
+                for (int a = 1; a < 5; a++) G[a] = fmav(ys, p.W1, G[a]);
+            }
 #pragma unroll
             for (int a = 0; a < 5; a++) {
                 const V gt = fmav(gd[c][a], keep, G[a]);
@@ -536,18 +575,11 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     // F = F_rest + F_dev, F_rest = -(h2, h1) rho0 cs2 (theta11, theta22) is the
     // geometric force of the rest state; only F_dev is stored.
     V F1dev, F2dev, F1r, F2r, tc11 = bc<V>(0.f), tc22 = bc<V>(0.f);
-    float t21 = 0.f, t12 = 0.f;
     if constexpr (GEOM) {
         // curvilinear grids (theta12, theta21; the column metric has theta12 =
         // theta22 = 0): tau^c (Eq. tauc), the full effective force (Eqs.
         // bodyforce1/2) and the local shear stress of Appendix A; F_rest =
         // (h2 (theta21 - theta11), h1 (theta12 - theta22)) rho0 cs2
-        if (GEOM == 2) {
-            t12 = gm_at(p.gm, p.plane, p.pitch, 3, i, j[0]);
-            t21 = gm_at(p.gm, p.plane, p.pitch, 4, i, j[0]);
-        } else {
-            t21 = curv_t21(p.ax1, p.nx, i);
-        }
         tc11 = rho * fmav(U2, (zeta + nu) * t12, U1 * ((zeta - nu) * t21));
         tc22 = rho * fmav(U1, (zeta + nu) * t21, U2 * ((zeta - nu) * t12));
         tau11 = tau11 + tc11;

@@ -45,11 +45,11 @@ def structs_from_spec(spec: dict):
             t = spec["metric"]
             tab = np.ascontiguousarray(np.stack([np.asarray(t[k], dtype=np.float64).reshape(g.ny, g.nx)
                                                  for k in ("h1", "h2", "t11", "t12", "t21", "t22")]))
-            wall = t["wall"]
-            wt = np.ascontiguousarray(np.concatenate([np.asarray(wall["W"][0], dtype=np.float64),
-                                                      np.asarray(wall["E"][0], dtype=np.float64),
-                                                      np.asarray(wall["S"][1], dtype=np.float64),
-                                                      np.asarray(wall["N"][1], dtype=np.float64)]))
+            wall = t["wall"]   # side -> (h1, h2) at the wall points
+            wt = np.ascontiguousarray(np.concatenate(
+                [np.asarray(wall[w][k], dtype=np.float64)
+                 for w, k in (("W", 0), ("E", 0), ("S", 1), ("N", 1),     # wall-normal factor
+                              ("W", 1), ("E", 1), ("S", 0), ("N", 0))]))  # tangential factor
             m.table = tab.ctypes.data
             m.wall_table = wt.ctypes.data
             m._keep = (tab, wt)   # alive as long as the struct
