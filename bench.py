@@ -507,15 +507,24 @@ def run_accuracy_mhd(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    Ha, Re = 100.0, 100.0
+    Ha, Re = args.mhd_ha, args.mhd_re
+    roberts = args.mhd_map == "roberts"
+    goc_name = f"goc roberts gamma={args.mhd_gamma}" if roberts else "goc tanh beta=3"
 
     def run(ny, stretched):
         if stretched:
-            prob = gi.Problem("hartmann", args.mhd_nx, ny, {"kind": "uniform"}, {"kind": "tanh2", "beta": 3.0},
+            eta = (np.arange(ny) + 0.5) / ny   # cell-centred nodes, walls at eta = 0 and 1
+            if roberts:   # Sec. 6.2 with alpha = 1/2 (clustering at both walls), lambda = (gamma+1)/(gamma-1)
+                g = args.mhd_gamma
+                ls = ((g + 1.0) / (g - 1.0)) ** (2.0 * eta - 1.0)
+                y = ny * ((g + 1.0) * ls + 1.0 - g) / (2.0 * (1.0 + ls))
+                map2 = {"kind": "roberts", "gamma": g, "alpha": 0.5}
+            else:
+                y = 0.5 * ny * (1.0 + np.tanh(3.0 * (2.0 * eta - 1.0)) / np.tanh(3.0))
+                map2 = {"kind": "tanh2", "beta": 3.0}
+            prob = gi.Problem("hartmann", args.mhd_nx, ny, {"kind": "uniform"}, map2,
                               {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0})
             _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
-            eta = (np.arange(ny) + 0.5) / ny
-            y = 0.5 * ny * (1.0 + np.tanh(3.0 * (2.0 * eta - 1.0)) / np.tanh(3.0))
         else:
             prob = gi.Problem("hartmann", args.mhd_nx, ny, {"kind": "uniform"}, {"kind": "uniform"},
                               {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0, "gi": 0})
@@ -534,7 +543,12 @@ def run_accuracy_mhd(args):
                             b1=np.broadcast_to(ba[:, None], shape).copy())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if stretched:
+        if stretched and args.mhd_goc_crossings > 0:   # a fixed number of crossing times
+            steps = int(args.mhd_goc_crossings * crossing)
+            lat.step(steps)
+            lat.sync()
+            res = None
+        elif stretched:
             steps, res = lat.run_until(1e-9, args.mhd_goc_max_steps)
         else:
             steps = int(4 * crossing)
@@ -548,11 +562,12 @@ def run_accuracy_mhd(args):
         u, b = f[1].mean(axis=1), f[3].mean(axis=1)
         eu = float(np.linalg.norm(u - ua) / np.linalg.norm(ua))
         eb = float(np.linalg.norm(b - ba) / np.linalg.norm(ba))
-        row = {"grid": "goc tanh beta=3" if stretched else "uniform", "ny": ny,
+        row = {"grid": goc_name if stretched else "uniform", "ny": ny,
                "start": "analytic" if stretched else "rest", "steps": int(steps),
                "crossing_steps": round(crossing), "seconds": round(wall, 3),
                "mlups": round(args.mhd_nx * ny * steps / wall / 1e6, 1),
-               "err_u": float(f"{eu:.4g}"), "err_b": float(f"{eb:.4g}"), "err": float(f"{max(eu, eb):.4g}")}
+               "err_u": float(f"{eu:.4g}"), "err_b": float(f"{eb:.4g}"), "err": float(f"{max(eu, eb):.4g}"),
+               "err_sq": float(f"{max(eu, eb) ** 2:.4g}")}
         if res is not None:
             row["residual"] = float(f"{res:.3g}")
         return row
@@ -575,7 +590,7 @@ def run_accuracy_mhd(args):
         order = np.log(a["err"] / b["err"]) / np.log(b["ny"] / a["ny"])
         ny = b["ny"] * (b["err"] / target) ** (1.0 / order)
         match = {"uniform_ny": round(float(ny), 1), "how": f"extrapolated with the measured order {order:.2f}"}
-    print(json.dumps({"metric": METRIC, "workload": f"Hartmann channel {args.mhd_nx} columns, Ha = 100, Re = 100: "
+    print(json.dumps({"metric": METRIC, "workload": f"Hartmann channel {args.mhd_nx} columns, Ha = {Ha:g}, Re = {Re:g}: "
                       "matched accuracy", "runs": rows, "matched": match}))
 
 
@@ -685,6 +700,13 @@ def main():
     ap.add_argument("--workload", default="cavity",
                     choices=["cavity", "batch", "serve", "accuracy", "accuracy_mhd", "oracle_timing"])
     ap.add_argument("--mhd-nx", type=int, default=256)
+    ap.add_argument("--mhd-ha", type=float, default=100.0)
+    ap.add_argument("--mhd-re", type=float, default=100.0)
+    ap.add_argument("--mhd-map", default="tanh", choices=["tanh", "roberts"],
+                    help="wall-normal map of the GOC Hartmann grid (roberts: the paper's Table 3 grids)")
+    ap.add_argument("--mhd-gamma", type=float, default=1.05)
+    ap.add_argument("--mhd-goc-crossings", type=float, default=0.0,
+                    help="run the GOC grid for this many crossing times instead of to its residual plateau")
     ap.add_argument("--mhd-goc-ny", type=int, default=1024)
     ap.add_argument("--mhd-goc-max-steps", type=int, default=1000000)
     ap.add_argument("--mhd-uniform-ny", type=int, nargs="+", default=[512, 1024, 2048])
