@@ -122,6 +122,32 @@ def test_stretched_periodic_vortex_fp32_matches_the_oracle(gpu):
     assert np.abs(fg[0] - fo[0]).max() <= 1e-6
 
 
+def test_periodic_node_table_matches_the_per_axis_grid(gpu):
+    """The sine-stretched periodic vortex with its metric given node by node
+    (both axes periodic: the node-table corrections wrap across both seams)
+    against the oracle, and against the same problem on the per-axis maps
+    stepped by the library (the same scheme; FP32 rounding apart)."""
+    u1, u2 = gi.random_periodic_fields(40, 24, seed=3, amp=0.03)
+    spec = dict(nx=40, ny=24, map1={"kind": "sine", "a": 0.3}, map2={"kind": "sine", "a": -0.25},
+                walls={"W": None, "E": None, "S": None, "N": None}, tau=0.7, tau_zeta=0.8,
+                fext=(1e-6, -2e-6), init={"u1": u1, "u2": u2})
+    m = oracle.build_metric(spec)
+    one = np.ones(1)
+    tab = dict(spec, map1={"kind": "table"}, map2={"kind": "uniform"},
+               metric={"h1": m.h1, "h2": m.h2, "t11": m.t11, "t12": m.t12, "t21": m.t21, "t22": m.t22,
+                       "wall": {w: (one.repeat(24 if w in "WE" else 40), one.repeat(24 if w in "WE" else 40))
+                                for w in "WESN"}})
+    o, L, fo, fg = run_pair(tab, 500)
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+    L2 = goc.Lattice(spec)
+    L2.step(500)
+    fa = L2.moments()
+    assert relerr(np.stack(fg[1:3]), np.stack(fa[1:3])) <= 1e-5
+    L.close()
+    L2.close()
+
+
 def test_hartmann_strip_fp32_matches_the_oracle(gpu):
     """Coupled NSE + MIE (Appendix G) on a wall-normal tanh grid: FP32 velocity
     and induced field within 1e-5 relative L2 after 1000 steps; the induced
@@ -492,6 +518,24 @@ def test_full_size_cavity_in_the_benchmark_configuration_matches_the_oracle(gpu)
     the oracle on the whole lattice after 300 steps: FP32 velocity relative
     L2 <= 1e-5."""
     prob = gi.lid_cavity()
+    spec = prob.lattice_spec(cs2_of(prob))
+    o = oracle.Oracle(spec, threads=os.cpu_count() or 1)
+    L = goc.Lattice(spec)
+    L.step(300)
+    assert L.launch_config["tuned"]
+    o.step(300)
+    fo, fg = o.fields(), L.moments()
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    assert np.abs(fg[0] - fo[0]).max() <= 1e-6
+    L.close()
+
+
+def test_full_size_spiral_cavity_in_the_benchmark_configuration_matches_the_oracle(gpu):
+    """The 512 x 512 cavity on the logarithmic-spiral node table, as
+    `bench.py --grid spiral` steps it (autotuned launch, graph chunks),
+    against the oracle on the whole lattice after 300 steps: FP32 velocity
+    relative L2 <= 1e-5."""
+    prob = gi.spiral_cavity(512, 512, Re=1000.0, u_lid=0.05, mach_matched=True)
     spec = prob.lattice_spec(cs2_of(prob))
     o = oracle.Oracle(spec, threads=os.cpu_count() or 1)
     L = goc.Lattice(spec)
