@@ -33,9 +33,10 @@ struct Axis {
     const float *rp;   // rest-state pull correction, source k+1: 0.5 rho0 cs2 (1/h(k+1) - 1/h(k))
     const float *dm;   // MIE pull corrections, source k-1: W1 (h(k-1) - h(k)) + csm2 (h^2 theta(k-1) + h^2 theta(k))/4
     const float *dp;   //                      source k+1: W1 (h(k+1) - h(k)) - csm2 (h^2 theta(k+1) + h^2 theta(k))/4
-    // Curvilinear column metric (annular sector; xi1 axis, no MIE): rm/rp hold
-    // the full pull corrections of links 1/3 (not per unit h2), and the rows
-    // dm, dp, dp + n hold h2, 1/h2 and theta21 as functions of xi1.
+    // Curvilinear column metric (annular sector; xi1 axis): rm/rp hold the
+    // full pull corrections of links 1/3 (not per unit h2), and the rows dm,
+    // dp, dp + n hold h2, 1/h2 and theta21 as functions of xi1 (the MIE then
+    // stores its populations without a reference field and needs no dm/dp).
 };
 
 // the node-by-node metric (StepParams.gm): plane k at node (i, j), and the

@@ -1059,7 +1059,8 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
 // GEOM: 1 the curvilinear column metric (annular sector; h1, h2, theta11,
 // theta21 functions of xi1), 2 the metric given node by node (general
 // orthogonal grids), with the theta21 / theta12 terms of the force, tau^c,
-// the corrections and the local shear stress (Appendix A).
+// the corrections and the local shear stress (Appendix A) and, with the MIE,
+// those of the gradient formula, g^corr and J3 and the source Y (Appendix G).
 template <class S, bool MHD, bool SRT = false, int GEOM = 0>
 __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
     extern __shared__ __align__(128) unsigned char dyn[];
