@@ -232,9 +232,11 @@ goc_status goc_sync(goc_lattice *lat);
 /* Macroscopic fields of the current state into caller-owned host arrays
  * ([ny][nx] doubles each; any may be NULL): rho, U1, U2 (with the stored
  * force, Eq. GOChydrodynamicfields), B1, B2 (Eq. 13_C; zero without MIE).
- * cartesian != 0 maps vector components with Eq. vectormapping; on the
- * straight grids of this library the GOC unit vectors coincide with the
- * Cartesian ones, so the values are the same.  Synchronises. */
+ * cartesian != 0 maps vector components with Eq. vectormapping: on the
+ * straight grids the GOC unit vectors coincide with the Cartesian ones (the
+ * values are the same); on the ANNULUS (radial xi1, azimuthal xi2) they are
+ * rotated by the azimuth phi = (pi/sectors)(2 j/ny - 1) of node row j; a
+ * TABLE map carries no coordinates (GOC_EUNSUPPORTED).  Synchronises. */
 goc_status goc_moments(goc_lattice *lat, int cartesian, double *rho, double *u1,
                        double *u2, double *b1, double *b2);
 

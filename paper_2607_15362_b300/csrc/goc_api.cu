@@ -1027,15 +1027,39 @@ double goc_bytes_per_node(const goc_lattice *L) {
 
 goc_status goc_moments(goc_lattice *L, int cartesian, double *rho, double *u1, double *u2,
                        double *b1, double *b2) {
-    (void)cartesian;   // straight grids: GOC unit vectors are the Cartesian ones
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    const bool rotate = cartesian && L->map.kind[0] == GOC_MAP_ANNULUS;
+    if (cartesian && L->map.kind[0] == GOC_MAP_TABLE)
+        return fail(GOC_EUNSUPPORTED, "a TABLE map carries no coordinates: Cartesian components are unavailable");
     goc_status st = moments_to_device(L);
     if (st != GOC_OK) return st;
     const long long N = (long long)L->nx * L->ny;
     double *outs[5] = {rho, u1, u2, b1, b2};
-    for (int k = 0; k < 5; k++)
-        if (outs[k]) CU(cudaMemcpyAsync(outs[k], L->mom + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    // the annulus rotates both components of a vector: fetch the pair whole
+    std::vector<double> tmp;
+    if (rotate) tmp.assign(4 * (size_t)N, 0.0);
+    for (int k = 0; k < 5; k++) {
+        double *dst = outs[k];
+        if (rotate && k >= 1) dst = tmp.data() + (k - 1) * N;
+        if (dst) CU(cudaMemcpyAsync(dst, L->mom + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    }
     CU(cudaStreamSynchronize(L->stream));
+    if (rotate) {   // Eq. vectormapping on the annular sector: xi1 radial, xi2 azimuthal at
+                    // phi = (pi/sectors)(2 xi2/ny - 1), periodic nodes at xi2 = j
+        const double PI = 3.14159265358979323846;
+        for (int j = 0; j < L->ny; j++) {
+            const double phi = PI / L->map.sectors * (2.0 * j / L->ny - 1.0), c = std::cos(phi), s = std::sin(phi);
+            for (int i = 0; i < L->nx; i++) {
+                const long long n = (long long)j * L->nx + i;
+                for (int v = 0; v < 2; v++) {
+                    const double vr = tmp[(2 * v) * N + n], vp = tmp[(2 * v + 1) * N + n];
+                    double *ox = outs[1 + 2 * v], *oy = outs[2 + 2 * v];
+                    if (ox) ox[n] = c * vr - s * vp;
+                    if (oy) oy[n] = s * vr + c * vp;
+                }
+            }
+        }
+    }
     return GOC_OK;
 }
 

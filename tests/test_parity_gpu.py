@@ -495,6 +495,38 @@ def test_mie_on_curvilinear_grids_matches_the_oracle(gpu, case, storage):
     L.close()
 
 
+def test_cartesian_components_on_the_annulus(gpu):
+    """goc_moments(cartesian=1) on the annular sector (Eq. vectormapping)
+    against the oracle's radial and azimuthal components rotated by the
+    azimuth of each node position of the map (Sec. 8.1); a node table, which
+    carries no coordinates, refuses."""
+    from oracle.metric import annulus_position
+    prob = gi.taylor_couette(n1=45, n2=11, r_in=6.0, sectors=9.0, Re=20.0, u_in=1.0, u_out=1.5)
+    m = oracle.build_metric(prob.lattice_spec(1.0))
+    spec = prob.lattice_spec(m.cs2())
+    spec["walls"]["W"] = dict(spec["walls"]["W"], B=(0.02, 0.005))
+    spec["mhd"] = {"tau_m": 0.9, "mu_m": 2.0, "B_init": (0.01, 0.004)}
+    o = oracle.Oracle(spec, threads=8)
+    L = goc.Lattice(spec)
+    o.step(300)
+    L.step(300)
+    x, y = annulus_position(np.arange(45)[None, :] + 0.5, np.arange(11)[:, None], 45, 11, 6.0, 51.0, 9.0)
+    phi = np.arctan2(y, x)
+    c, s_ = np.cos(phi), np.sin(phi)
+    rho, ur, up, br, bp = o.fields()
+    want = [c * ur - s_ * up, s_ * ur + c * up, c * br - s_ * bp, s_ * br + c * bp]
+    got = L.moments(cartesian=True)
+    assert relerr(np.stack(got[1:3]), np.stack(want[:2])) <= 1e-5
+    assert relerr(np.stack(got[3:5]), np.stack(want[2:])) <= 1e-4
+    L.close()
+    t = dict(spec, map1={"kind": "table"}, map2={"kind": "uniform"},
+             metric={"h1": m.h1, "h2": m.h2, "t11": m.t11, "t12": m.t12, "t21": m.t21, "t22": m.t22, "wall": m.wall})
+    L = goc.Lattice(t)
+    with pytest.raises(Exception, match="no coordinates"):
+        L.moments(cartesian=True)
+    L.close()
+
+
 def test_degenerate_single_column_and_zero_steps(gpu):
     """A channel one node wide (every x pull wraps to the node itself) matches
     the oracle; goc_step(0) changes nothing; a negative count is refused."""
