@@ -72,8 +72,8 @@ typedef enum { GOC_BC_PERIODIC = 0, GOC_BC_WALL = 1 } goc_bc;
  *           5_annularsector) with cell-centred radial nodes:
  *           r = r_inner exp(ln(r_outer/r_inner) xi1/nx), h1 = r ln(r_outer/r_inner)/nx,
  *           h2 = 2 pi r/(sectors ny), theta11 = theta21 = 1/r, theta12 = theta22 = 0.
- *           Needs W/E walls, periodic S/N, kind[1] = UNIFORM, scheme 0; not for
- *           batches.  Wall speeds (wall_u[W], wall_u[E]) are azimuthal.  With the
+ *           Needs W/E walls, periodic S/N, kind[1] = UNIFORM; schemes 0, 2, 3;
+ *           not for batches.  Wall speeds (wall_u[W], wall_u[E]) are azimuthal.  With the
  *           MIE, Appendix G's curvature terms (theta21 in the local gradient
  *           formula, g^corr and J3, the source Y of Eq. 6ab_C) are active and
  *           the MIE populations are stored without a reference field.
@@ -86,7 +86,8 @@ typedef enum { GOC_BC_PERIODIC = 0, GOC_BC_WALL = 1 } goc_bc;
  *           one in the same order (h2 at W and E, h1 at S and N).  Moving walls
  *           use the normal factor, the MIE wall condition h1 h2; any values on
  *           periodic sides.  Both are host arrays read during goc_create only;
- *           every h > 0.  Scheme 0, not for batches; the MIE as for ANNULUS.
+ *           every h > 0.  Schemes 0, 2, 3, not for batches; the MIE as for
+ *           ANNULUS.
  * Wall maps (TANH2 with beta > 0, ROBERTS, TANH1, SINH) need a wall axis; SINE a
  * periodic one. */
 typedef enum { GOC_MAP_UNIFORM = 0, GOC_MAP_TANH2 = 1, GOC_MAP_SINE = 2, GOC_MAP_ROBERTS = 3,

@@ -200,24 +200,41 @@ goc_status launch_std_t(goc_lattice *L, const StepParams &p) {
     return GOC_OK;
 }
 
+// Curved grids (GEOM 1, 2): the step kernel for the lattice's collision
+// (central moments, or raw moments for schemes 2 and 3) and MIE setting.
+template <class S, int GEOM>
+cudaError_t launch_geom(goc_lattice *L, const StepParams &p, int ntiles) {
+    size_t smem = 0;
+    const bool pdl = L->cfg_pdl != 0, raw = L->scheme == 2 || L->scheme == 3;
+    const dim3 block(TX, TYT);
+    if (L->mhd.enabled && raw) {
+        const int grid = step_grid<S, true, true, GEOM>(ntiles, &smem);
+        return launch_pdl(pdl, step_kernel<S, true, true, GEOM>, dim3(grid), block, smem, L->stream, p);
+    }
+    if (L->mhd.enabled) {
+        const int grid = step_grid<S, true, false, GEOM>(ntiles, &smem);
+        return launch_pdl(pdl, step_kernel<S, true, false, GEOM>, dim3(grid), block, smem, L->stream, p);
+    }
+    if (raw) {
+        const int grid = step_grid<S, false, true, GEOM>(ntiles, &smem);
+        return launch_pdl(pdl, step_kernel<S, false, true, GEOM>, dim3(grid), block, smem, L->stream, p);
+    }
+    const int grid = step_grid<S, false, false, GEOM>(ntiles, &smem);
+    return launch_pdl(pdl, step_kernel<S, false, false, GEOM>, dim3(grid), block, smem, L->stream, p);
+}
+
 template <class S>
 goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
     if (L->scheme == 1) return launch_std_t<S>(L, p);
     const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
     size_t smem = 0;
     const bool pdl = L->cfg_pdl != 0;
-    if (L->sp.curv == 2 && L->mhd.enabled) {   // node-table metric (central-moment collision)
-        const int grid = step_grid<S, true, false, 2>(ntiles, &smem);
-        CU(launch_pdl(pdl, step_kernel<S, true, false, 2>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
-    } else if (L->sp.curv == 2) {
-        const int grid = step_grid<S, false, false, 2>(ntiles, &smem);
-        CU(launch_pdl(pdl, step_kernel<S, false, false, 2>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
-    } else if (L->sp.curv && L->mhd.enabled) {   // curvilinear column metric (central-moment collision)
-        const int grid = step_grid<S, true, false, 1>(ntiles, &smem);
-        CU(launch_pdl(pdl, step_kernel<S, true, false, 1>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
-    } else if (L->sp.curv) {
-        const int grid = step_grid<S, false, false, 1>(ntiles, &smem);
-        CU(launch_pdl(pdl, step_kernel<S, false, false, 1>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+    if (L->sp.curv == 2) {   // node-table metric
+        const cudaError_t e = launch_geom<S, 2>(L, p, ntiles);
+        CU(e);
+    } else if (L->sp.curv) {   // curvilinear column metric
+        const cudaError_t e = launch_geom<S, 1>(L, p, ntiles);
+        CU(e);
     } else if (L->scheme == 2 || L->scheme == 3) {   // collision on raw moments (Appendix F SRT, Appendix D MRT)
         if (L->mhd.enabled) {
             const int grid = step_grid<S, true, true>(ntiles, &smem);
@@ -664,10 +681,6 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         if (!uni) return fail(GOC_EINVAL, "the standard uniform-grid scheme needs uniform maps on both axes");
         if (flow->gi_correction) return fail(GOC_EINVAL, "the standard uniform-grid scheme needs gi_correction = 0");
         if (mhd && mhd->enabled) return fail(GOC_EINVAL, "the standard uniform-grid scheme has no MIE");
-    }
-    if (map->kind[0] == GOC_MAP_ANNULUS || map->kind[0] == GOC_MAP_TABLE) {
-        const char *what = map->kind[0] == GOC_MAP_ANNULUS ? "the annulus" : "the TABLE map";
-        if (exec && exec->scheme != 0) return fail(GOC_EUNSUPPORTED, "%s runs the central-moment scheme (0)", what);
     }
     goc_lattice *L = new (std::nothrow) goc_lattice();
     if (!L) return fail(GOC_ENOMEM, "host allocation failed");
