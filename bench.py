@@ -471,6 +471,82 @@ def run_accuracy(args):
     print(json.dumps(line))
 
 
+def _vortex_centres(prob, fields):
+    """Centres of the primary vortex (minimum of the stream function) and of
+    the first secondary vortices at the bottom corners (local maxima), in
+    units of the side, from U1 on the physical node positions of the tanh
+    map.  psi(x, y) = integral of u from the bottom wall (u = 0 there) along
+    y; the extremum node is refined by a parabola through its neighbours
+    along each axis."""
+    import numpy as np
+
+    def positions(m, n):
+        eta = (np.arange(n) + 0.5) / n
+        if m.get("kind", "uniform") == "uniform":
+            return eta
+        b = float(m["beta"])
+        return 0.5 * (1.0 + np.tanh(b * (2.0 * eta - 1.0)) / np.tanh(b))
+
+    x, y = positions(prob.map1, prob.nx), positions(prob.map2, prob.ny)
+    u = fields[1]
+    psi = np.empty_like(u)
+    psi[0] = 0.5 * u[0] * y[0]
+    for j in range(1, prob.ny):
+        psi[j] = psi[j - 1] + 0.5 * (u[j] + u[j - 1]) * (y[j] - y[j - 1])
+
+    def refine(c, k, f):
+        if 0 < k < len(c) - 1:
+            x0, x1, x2 = c[k - 1], c[k], c[k + 1]
+            f0, f1, f2 = f[k - 1], f[k], f[k + 1]
+            den = (x0 - x1) * (x0 - x2) * (x1 - x2)
+            a = (x2 * (f1 - f0) + x1 * (f0 - f2) + x0 * (f2 - f1)) / den
+            b = (x2 * x2 * (f0 - f1) + x1 * x1 * (f2 - f0) + x0 * x0 * (f1 - f2)) / den
+            if a != 0:
+                return float(-b / (2 * a))
+        return float(c[k])
+
+    def centre(mask, sign):
+        q = np.where(mask, sign * psi, -np.inf)
+        j, i = np.unravel_index(np.argmax(q), q.shape)
+        return [round(refine(x, i, psi[j]), 4), round(refine(y, j, psi[:, i]), 4)]
+
+    X, Y = np.meshgrid(x, y)
+    return {"primary": centre(np.ones_like(psi, bool), -1.0),
+            "bottom_left": centre((X < 0.3) & (Y < 0.3), 1.0),
+            "bottom_right": centre((X > 0.6) & (Y < 0.4), 1.0)}
+
+
+def run_vortex(args):
+    """The cavity of Sec. 7.3 run to its steady state on the GPU, and the
+    centres of its primary and bottom-corner vortices (the quantities of the
+    paper's Tables 1 and 2)."""
+    import torch
+
+    import paper_2607_15362_b300 as goc
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    prob = gi.lid_cavity(n=args.cavity_n, beta=args.vortex_beta, Re=args.vortex_re)
+    _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
+    spec = prob.lattice_spec(cs2)
+    u_lid = spec["walls"]["N"]["u"]
+    lat = goc.Lattice(spec, stream=stream.cuda_stream, check_every=1000)
+    steps = int(round(args.tstar * prob.nx / u_lid))
+    t0 = time.perf_counter()
+    lat.step(steps)
+    lat.sync()
+    wall = time.perf_counter() - t0
+    fields = lat.moments()
+    lat.close()
+    # the paper's GOC-LBM values (Table 1, Table 2) at Re = 1000, for context
+    printed = {"primary": [0.5314, 0.5646], "bottom_left": [0.0855, 0.0779], "bottom_right": [0.8581, 0.1104]}
+    print(json.dumps({"metric": METRIC, "workload": f"cavity {prob.nx}^2, tanh beta = {args.vortex_beta}, "
+                      f"Re = {args.vortex_re:g}, t* = {args.tstar}: vortex centres",
+                      "steps": steps, "seconds": round(wall, 3), "mlups": round(prob.nodes * steps / wall / 1e6, 1),
+                      "centres": _vortex_centres(prob, fields),
+                      "paper_goc_lbm_re1000": printed if args.vortex_re == 1000.0 else None}))
+
+
 def _hartmann_analytic(spec, ny, positions):
     """u_x and B_x of the Hartmann flow (Sec. 7.4) at physical positions y in
     [0, ny] of a channel of half-width H = ny/2."""
@@ -698,13 +774,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
     ap.add_argument("--workload", default="cavity",
-                    choices=["cavity", "batch", "serve", "accuracy", "accuracy_mhd", "oracle_timing"])
+                    choices=["cavity", "batch", "serve", "accuracy", "accuracy_mhd", "oracle_timing", "vortex"])
     ap.add_argument("--mhd-nx", type=int, default=256)
     ap.add_argument("--mhd-ha", type=float, default=100.0)
     ap.add_argument("--mhd-re", type=float, default=100.0)
     ap.add_argument("--mhd-map", default="tanh", choices=["tanh", "roberts"],
                     help="wall-normal map of the GOC Hartmann grid (roberts: the paper's Table 3 grids)")
     ap.add_argument("--mhd-gamma", type=float, default=1.05)
+    ap.add_argument("--vortex-re", type=float, default=1000.0)
+    ap.add_argument("--vortex-beta", type=float, default=1.2)
     ap.add_argument("--mhd-goc-crossings", type=float, default=0.0,
                     help="run the GOC grid for this many crossing times instead of to its residual plateau")
     ap.add_argument("--mhd-goc-ny", type=int, default=1024)
@@ -729,6 +807,8 @@ def main():
         run_accuracy_mhd(args)
     elif args.workload == "oracle_timing":
         run_oracle_timing(args)
+    elif args.workload == "vortex":
+        run_vortex(args)
     else:
         run_ours(args)
 
