@@ -213,7 +213,11 @@ goc_status goc_set_launch_config(goc_lattice *lat, int dynamic_tiles, int pdl);
 /* Enqueue nsteps time steps (each one fused launch: pull-streaming with
  * boundary conditions, hydrodynamic fields, normal gradients, stresses,
  * effective and Lorentz forces, central-moment collision, MIE collision,
- * store).  Asynchronous; returns launch errors only.  nsteps >= 0. */
+ * store).  Asynchronous: returns launch errors, and the device status word
+ * as a copy taken behind the previous call's work, if it has arrived (no
+ * wait): GOC_EDIVERGED once a step saw NaN/Inf or a non-positive density,
+ * GOC_ECUDA if a staged tile copy did not complete in its bounded wait; the
+ * status is sticky until goc_init_fields or goc_set_state.  nsteps >= 0. */
 goc_status goc_step(goc_lattice *lat, long long nsteps);
 
 /* Step until the residual R = ||U^n - U^(n-1)||_2 / ||U^n||_2 (max with the
@@ -225,7 +229,8 @@ goc_status goc_step(goc_lattice *lat, long long nsteps);
 goc_status goc_run_until(goc_lattice *lat, double tol, long long max_steps,
                          long long *done, double *residual);
 
-/* Block the host until the lattice's stream has drained. */
+/* Block the host until the lattice's stream has drained; then returns the
+ * device status word as goc_step describes (GOC_EDIVERGED, GOC_ECUDA). */
 goc_status goc_sync(goc_lattice *lat);
 
 /* ---- results ----------------------------------------------------------- */
@@ -237,7 +242,9 @@ goc_status goc_sync(goc_lattice *lat);
  * straight grids the GOC unit vectors coincide with the Cartesian ones (the
  * values are the same); on the ANNULUS (radial xi1, azimuthal xi2) they are
  * rotated by the azimuth phi = (pi/sectors)(2 j/ny - 1) of node row j; a
- * TABLE map carries no coordinates (GOC_EUNSUPPORTED).  Synchronises. */
+ * TABLE map carries no coordinates (GOC_EUNSUPPORTED).  Synchronises; the
+ * arrays are filled even when the status word reports a diverged lattice
+ * (then GOC_EDIVERGED is returned). */
 goc_status goc_moments(goc_lattice *lat, int cartesian, double *rho, double *u1,
                        double *u2, double *b1, double *b2);
 

@@ -109,6 +109,8 @@ struct goc_lattice {
     int graph_cur = 0;                           // buffer the captured graph starts from
     bool owns_stream = false;
     bool in_batch = false;                       // stepped only through goc_batch_step
+    int *hflag = nullptr;                        // pinned host copy of flag[0], refreshed after each goc_step
+    cudaEvent_t flag_ev = nullptr;               // completion of that copy
     bool fresh = false;                          // buffer holds f^0 (pre-collision): next step reads in place
     bool res_pending = false;                    // residual sums of a batch step wait in red[4..7]
     CUtensorMap tmf[2], tmF[2], tmg[2];          // TMA descriptors of both buffers
@@ -494,6 +496,20 @@ goc_status compute_metric(const goc_grid *grid, const goc_map *map, cudaStream_t
     return GOC_OK;
 }
 
+// The device status word flag[0]: 1 = NaN/Inf or non-positive density seen
+// by a step, 2 = a staged tile copy did not complete within its bounded wait.
+goc_status flag_status(const goc_lattice *L, int f) {
+    if (f == 1) return fail(GOC_EDIVERGED, "lattice diverged (by step %lld)", L->steps);
+    return fail(GOC_ECUDA, "a staged tile copy did not complete in time (status %d)", f);
+}
+
+// Read flag[0] after the stream has drained (synchronous, 4 bytes).
+goc_status device_status(goc_lattice *L) {
+    int f = 0;
+    CU(cudaMemcpy(&f, L->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    return f ? flag_status(L, f) : GOC_OK;
+}
+
 void free_lattice(goc_lattice *L) {
     if (!L) return;
     cudaStreamSynchronize(L->stream);
@@ -502,6 +518,8 @@ void free_lattice(goc_lattice *L) {
                     L->m1, L->m2, L->gm, L->gtab, L->uout[0], L->uout[1], L->flag, L->red, L->mom};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (L->flag_ev) cudaEventDestroy(L->flag_ev);
+    if (L->hflag) cudaFreeHost(L->hflag);
     if (L->owns_stream && L->stream) cudaStreamDestroy(L->stream);
     delete L;
 }
@@ -589,8 +607,10 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
     L->steps = 0;
     L->res_u = L->res_b = 0.0;
     L->fresh = true;
-    if (cudaMemsetAsync(L->flag + 2, 0, 2 * sizeof(int), L->stream) != cudaSuccess)   // step counters
+    if (cudaMemsetAsync(L->flag + 2, 0, 2 * sizeof(int), L->stream) != cudaSuccess ||   // step counters
+        cudaMemsetAsync(L->flag, 0, sizeof(int), L->stream) != cudaSuccess)             // status word
         return fail(GOC_ECUDA, "memset failed");
+    if (L->hflag) *L->hflag = 0;
     return GOC_OK;
 }
 
@@ -739,6 +759,17 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     TRY(dalloc(L, &L->m1, (curv ? 4 : 2) * (size_t)(L->nx + 2) * sizeof(double)));
     TRY(dalloc(L, &L->m2, 2 * (size_t)(L->ny + 2) * sizeof(double)));
     TRY(dalloc(L, &L->flag, 8 * sizeof(int)));   // [0] status, [1] spare, [2..3] step counters, [4..5] tile queues of the two parities
+    {   // pinned host copy of the status word and the event that marks its arrival
+        cudaError_t e = cudaMallocHost((void **)&L->hflag, sizeof(int));
+        if (e == cudaSuccess) {
+            *L->hflag = 0;
+            e = cudaEventCreateWithFlags(&L->flag_ev, cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            free_lattice(L);
+            return fail(GOC_ECUDA, "status word setup failed: %s", cudaGetErrorString(e));
+        }
+    }
     TRY(dalloc(L, &L->red, 8 * sizeof(double)));
     // metric (FP64), q, cs2 (Eq. GOC-LBE_CFL); a node table fills the axis
     // tables with a uniform metric (unused by its step kernel)
@@ -957,10 +988,24 @@ goc_status goc_init_fields(goc_lattice *L, const double *rho, const double *u1, 
 
 void goc_destroy(goc_lattice *L) { free_lattice(L); }
 
+static goc_status enqueue_steps(goc_lattice *L, long long nsteps);
+
 goc_status goc_step(goc_lattice *L, long long nsteps) {
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
     if (nsteps < 0) return fail(GOC_EINVAL, "nsteps must be >= 0");
     if (L->in_batch) return fail(GOC_EINVAL, "this lattice belongs to a batch: step it with goc_batch_step");
+    // the status word as of the end of the previous call, if its copy has landed (no wait)
+    if (L->flag_ev && cudaEventQuery(L->flag_ev) == cudaSuccess && *L->hflag) return flag_status(L, *L->hflag);
+    goc_status st = enqueue_steps(L, nsteps);
+    if (st != GOC_OK) return st;
+    if (L->flag_ev) {   // refresh the host copy of the status word behind this call's work
+        CU(cudaMemcpyAsync(L->hflag, L->flag, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+        CU(cudaEventRecord(L->flag_ev, L->stream));
+    }
+    return GOC_OK;
+}
+
+static goc_status enqueue_steps(goc_lattice *L, long long nsteps) {
     if (L->fresh && nsteps > 0) {   // first step after initialisation: no streaming of f^0
         goc_status st = launch_one(L, nullptr);
         if (st != GOC_OK) return st;
@@ -993,7 +1038,7 @@ goc_status goc_step(goc_lattice *L, long long nsteps) {
 goc_status goc_sync(goc_lattice *L) {
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
     CU(cudaStreamSynchronize(L->stream));
-    return GOC_OK;
+    return device_status(L);
 }
 
 long long goc_steps_done(const goc_lattice *L) { return L ? L->steps : -1; }
@@ -1057,6 +1102,7 @@ goc_status goc_moments(goc_lattice *L, int cartesian, double *rho, double *u1, d
         if (dst) CU(cudaMemcpyAsync(dst, L->mom + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     }
     CU(cudaStreamSynchronize(L->stream));
+    const goc_status fs = device_status(L);   // the fields are returned either way
     if (rotate) {   // Eq. vectormapping on the annular sector: xi1 radial, xi2 azimuthal at
                     // phi = (pi/sectors)(2 xi2/ny - 1), periodic nodes at xi2 = j
         const double PI = 3.14159265358979323846;
@@ -1073,7 +1119,7 @@ goc_status goc_moments(goc_lattice *L, int cartesian, double *rho, double *u1, d
             }
         }
     }
-    return GOC_OK;
+    return fs;
 }
 
 goc_status goc_moments_device(goc_lattice *L, float *out) {
@@ -1140,7 +1186,7 @@ goc_status goc_run_until(goc_lattice *L, double tol, long long max_steps, long l
             if (h_flag || !std::isfinite(R)) {
                 if (done) *done = taken;
                 if (residual) *residual = R;
-                return fail(GOC_EDIVERGED, "lattice diverged after %lld steps", L->steps);
+                return h_flag ? flag_status(L, h_flag) : fail(GOC_EDIVERGED, "lattice diverged after %lld steps", L->steps);
             }
             if (R < tol) break;
             if (R < best) {
@@ -1198,7 +1244,9 @@ goc_status goc_set_state(goc_lattice *L, const void *buf, size_t bytes) {
     if (ng) CU(cudaMemcpyAsync(L->g[L->cur], c + 64 + nf + nF, ng, cudaMemcpyHostToDevice, L->stream));
     const unsigned step = (unsigned)hdr[5];   // the stochastic-rounding stream continues from the saved step
     CU(cudaMemcpyAsync(L->flag + 2 + L->cur, &step, sizeof(unsigned), cudaMemcpyHostToDevice, L->stream));
+    CU(cudaMemsetAsync(L->flag, 0, sizeof(int), L->stream));   // a restored state starts with a clear status
     CU(cudaStreamSynchronize(L->stream));
+    if (L->hflag) *L->hflag = 0;
     L->steps = hdr[5];
     L->fresh = hdr[7] != 0;
     return GOC_OK;

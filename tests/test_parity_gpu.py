@@ -663,3 +663,28 @@ def test_full_size_batch_matches_individual_lattices_on_a_sample(gpu):
             np.testing.assert_array_equal(x, y)
         alone.close()
     batch.close()
+
+
+def test_divergence_is_reported_and_cleared_by_reinitialisation(gpu):
+    """A lattice driven far past its stability limit (Mach 0.87 lid, tau =
+    0.50007: NaN within 50 steps in the oracle) raises GOC_EDIVERGED from the
+    next synchronising call, from later goc_step calls (sticky), and from
+    goc_moments (which still fills the arrays); re-initialising clears it."""
+    from paper_2607_15362_b300 import _abi
+    p = gi.Problem("cavity", 48, 48, {"kind": "uniform"}, {"kind": "uniform"}, {"Re": 1e6, "u_lid": 0.5})
+    L = goc.Lattice(p.lattice_spec(1.0 / 3.0))
+    L.step(400)
+    with pytest.raises(goc.GocError) as e:
+        L.sync()
+    assert e.value.status == _abi.GOC_EDIVERGED and "diverged" in str(e.value)
+    with pytest.raises(goc.GocError) as e:
+        L.step(10)
+    assert e.value.status == _abi.GOC_EDIVERGED
+    with pytest.raises(goc.GocError):
+        L.moments()
+    L.init_fields()
+    L.step(5)
+    L.sync()
+    rho = L.moments()[0]
+    assert np.isfinite(rho).all()
+    L.close()
