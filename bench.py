@@ -513,7 +513,8 @@ def _vortex_centres(prob, fields):
     X, Y = np.meshgrid(x, y)
     return {"primary": centre(np.ones_like(psi, bool), -1.0),
             "bottom_left": centre((X < 0.3) & (Y < 0.3), 1.0),
-            "bottom_right": centre((X > 0.6) & (Y < 0.4), 1.0)}
+            "bottom_right": centre((X > 0.6) & (Y < 0.4), 1.0),
+            "top_left": centre((X < 0.3) & (Y > 0.7), 1.0)}
 
 
 def run_vortex(args):
@@ -526,7 +527,8 @@ def run_vortex(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    prob = gi.lid_cavity(n=args.cavity_n, beta=args.vortex_beta, Re=args.vortex_re)
+    prob = gi.lid_cavity(n=args.cavity_n, beta=args.vortex_beta, Re=args.vortex_re,
+                         u_lid=args.vortex_mach / math.sqrt(3.0))   # lid at this Mach number
     _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
     spec = prob.lattice_spec(cs2)
     u_lid = spec["walls"]["N"]["u"]
@@ -538,13 +540,18 @@ def run_vortex(args):
     wall = time.perf_counter() - t0
     fields = lat.moments()
     lat.close()
-    # the paper's GOC-LBM values (Table 1, Table 2) at Re = 1000, for context
-    printed = {"primary": [0.5314, 0.5646], "bottom_left": [0.0855, 0.0779], "bottom_right": [0.8581, 0.1104]}
+    # the paper's GOC-LBM values (Table 1, Table 2), for context
+    printed = {1000.0: {"primary": [0.5314, 0.5646], "bottom_left": [0.0855, 0.0779],
+                        "bottom_right": [0.8581, 0.1104], "top_left": None},
+               3200.0: {"primary": [0.5178, 0.5404], "bottom_left": [0.0813, 0.1194],
+                        "bottom_right": [0.8249, 0.0845], "top_left": [0.05318, 0.89824]},
+               5000.0: {"primary": [0.5151, 0.5356], "bottom_left": [0.0726, 0.1383],
+                        "bottom_right": [0.8040, 0.0747], "top_left": [0.0646, 0.9060]}}.get(args.vortex_re)
     print(json.dumps({"metric": METRIC, "workload": f"cavity {prob.nx}^2, tanh beta = {args.vortex_beta}, "
-                      f"Re = {args.vortex_re:g}, t* = {args.tstar}: vortex centres",
+                      f"Re = {args.vortex_re:g}, lid Mach {args.vortex_mach:g}, t* = {args.tstar}: vortex centres",
                       "steps": steps, "seconds": round(wall, 3), "mlups": round(prob.nodes * steps / wall / 1e6, 1),
                       "centres": _vortex_centres(prob, fields),
-                      "paper_goc_lbm_re1000": printed if args.vortex_re == 1000.0 else None}))
+                      "paper_goc_lbm": printed}))
 
 
 def _hartmann_analytic(spec, ny, positions):
@@ -783,6 +790,7 @@ def main():
     ap.add_argument("--mhd-gamma", type=float, default=1.05)
     ap.add_argument("--vortex-re", type=float, default=1000.0)
     ap.add_argument("--vortex-beta", type=float, default=1.2)
+    ap.add_argument("--vortex-mach", type=float, default=0.05 * math.sqrt(3.0))
     ap.add_argument("--mhd-goc-crossings", type=float, default=0.0,
                     help="run the GOC grid for this many crossing times instead of to its residual plateau")
     ap.add_argument("--mhd-goc-ny", type=int, default=1024)
