@@ -216,7 +216,7 @@ goc_status goc_set_launch_config(goc_lattice *lat, int dynamic_tiles, int pdl);
  * store).  Asynchronous: returns launch errors, and the device status word
  * as a copy taken behind the previous call's work, if it has arrived (no
  * wait): GOC_EDIVERGED once a step saw NaN/Inf or a non-positive density,
- * GOC_ECUDA if a staged tile copy did not complete in its bounded wait; the
+ * GOC_ETIMEOUT if a staged tile copy did not complete in its bounded wait; the
  * status is sticky until goc_init_fields or goc_set_state.  nsteps >= 0. */
 goc_status goc_step(goc_lattice *lat, long long nsteps);
 
@@ -230,7 +230,7 @@ goc_status goc_run_until(goc_lattice *lat, double tol, long long max_steps,
                          long long *done, double *residual);
 
 /* Block the host until the lattice's stream has drained; then returns the
- * device status word as goc_step describes (GOC_EDIVERGED, GOC_ECUDA). */
+ * device status word as goc_step describes (GOC_EDIVERGED, GOC_ETIMEOUT). */
 goc_status goc_sync(goc_lattice *lat);
 
 /* ---- results ----------------------------------------------------------- */
@@ -342,6 +342,13 @@ goc_status goc_batch_usage(const goc_batch *b, long long *used, long long *budge
 
 /* ---- errors ------------------------------------------------------------ */
 const char *goc_last_error(void);
+
+/* Failure-detection self-test: one block waits on a device barrier that
+ * nothing completes and gives up after `polls` polls (1 .. 2^26), the way
+ * every device-side wait of the step kernels is bounded.  Returns
+ * GOC_ETIMEOUT when the wait ran out (the expected outcome); the device stays
+ * usable.  GOC_EINVAL for a poll count out of range. */
+goc_status goc_selftest_bounded_wait(long long polls);
 
 #ifdef __cplusplus
 }

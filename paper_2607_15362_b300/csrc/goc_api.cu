@@ -496,11 +496,28 @@ goc_status compute_metric(const goc_grid *grid, const goc_map *map, cudaStream_t
     return GOC_OK;
 }
 
+// Self-test of the bounded device-side wait: one thread waits on an mbarrier
+// that nothing completes, gives up after `polls` polls and records status 2,
+// as the step kernels' waits do; the context stays usable.
+__global__ void wait_selftest_kernel(long long polls, int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    for (long long k = 0; k < polls; k++)
+        if (mbar_try_wait(&bar, 0)) {
+            *status = 0;
+            return;
+        }
+    *status = 2;
+}
+
 // The device status word flag[0]: 1 = NaN/Inf or non-positive density seen
 // by a step, 2 = a staged tile copy did not complete within its bounded wait.
 goc_status flag_status(const goc_lattice *L, int f) {
     if (f == 1) return fail(GOC_EDIVERGED, "lattice diverged (by step %lld)", L->steps);
-    return fail(GOC_ECUDA, "a staged tile copy did not complete in time (status %d)", f);
+    if (f == 2) return fail(GOC_ETIMEOUT, "a staged tile copy did not complete within its bounded wait");
+    return fail(GOC_ECUDA, "unknown device status %d", f);
 }
 
 // Read flag[0] after the stream has drained (synchronous, 4 bytes).
@@ -652,6 +669,22 @@ goc_status moments_to_device(goc_lattice *L) {
 extern "C" {
 
 const char *goc_last_error(void) { return g_err.c_str(); }
+
+goc_status goc_selftest_bounded_wait(long long polls) {
+    if (polls < 1 || polls > (1LL << 26)) return fail(GOC_EINVAL, "polls must be in [1, 2^26]");
+    int *d = nullptr, h = -1;
+    CU(cudaMalloc(&d, sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<1, 32>>>(polls, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(GOC_ECUDA, "wait self-test failed: %s", cudaGetErrorString(e));
+    if (h == 2) return fail(GOC_ETIMEOUT, "the bounded wait ran out after %lld polls", polls);
+    return fail(GOC_ECUDA, "wait self-test: unexpected status %d", h);
+}
 
 // Node-table metric: q = the smallest h1, h2 over the nodes (host table).
 double table_q(const goc_grid *grid, const goc_map *map) {
@@ -1664,6 +1697,7 @@ goc_status goc_batch_residual(goc_batch *B, int slot, double *residual_u, double
         if (flag || !std::isfinite(L->res_u) || !std::isfinite(L->res_b)) {
             if (residual_u) *residual_u = L->res_u;
             if (residual_b) *residual_b = L->res_b;
+            if (flag == 2) return flag_status(L, flag);
             return fail(GOC_EDIVERGED, "lattice in slot %d diverged", slot);
         }
     }

@@ -688,3 +688,20 @@ def test_divergence_is_reported_and_cleared_by_reinitialisation(gpu):
     rho = L.moments()[0]
     assert np.isfinite(rho).all()
     L.close()
+
+
+def test_bounded_device_wait_times_out_and_leaves_the_device_usable(gpu):
+    """The failure-detection self-test: a wait on a device barrier that
+    nothing completes gives up after its poll budget and reports
+    GOC_ETIMEOUT (the bounded-wait status of the step kernels); a lattice
+    then steps normally on the same device."""
+    from paper_2607_15362_b300 import _abi
+    lib = goc.lib()
+    assert lib.goc_selftest_bounded_wait(0) == _abi.GOC_EINVAL
+    assert lib.goc_selftest_bounded_wait(1 << 16) == _abi.GOC_ETIMEOUT
+    assert b"ran out" in lib.goc_last_error()
+    prob = gi.poiseuille_channel()
+    o, L, fo, fg = run_pair(prob.lattice_spec(cs2_of(prob)), 200)
+    L.sync()
+    assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
+    L.close()
