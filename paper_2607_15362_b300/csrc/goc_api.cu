@@ -1,5 +1,6 @@
 // goc_api.cu -- host side of the C ABI declared in include/goc.h.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -21,6 +22,14 @@
 #include "goc_step.cuh"
 
 using namespace goc;
+
+// Named ranges for timeline tools (NVTX; no cost without an attached tool).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 namespace {
 
@@ -719,6 +728,7 @@ goc_status goc_metric_info(const goc_grid *grid, const goc_map *map, double *q, 
 
 goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *flow,
                       const goc_mhd *mhd, const goc_exec *exec, goc_lattice **out) {
+    TraceRange trace_("goc_create");
     if (!out) return fail(GOC_EINVAL, "out is NULL");
     *out = nullptr;
     goc_status st = validate(grid, map);
@@ -1015,6 +1025,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
 
 goc_status goc_init_fields(goc_lattice *L, const double *rho, const double *u1, const double *u2,
                            const double *b1, const double *b2) {
+    TraceRange trace_("goc_init_fields");
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
     return run_init(L, rho, u1, u2, b1, b2, true);
 }
@@ -1024,6 +1035,7 @@ void goc_destroy(goc_lattice *L) { free_lattice(L); }
 static goc_status enqueue_steps(goc_lattice *L, long long nsteps);
 
 goc_status goc_step(goc_lattice *L, long long nsteps) {
+    TraceRange trace_("goc_step");
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
     if (nsteps < 0) return fail(GOC_EINVAL, "nsteps must be >= 0");
     if (L->in_batch) return fail(GOC_EINVAL, "this lattice belongs to a batch: step it with goc_batch_step");
@@ -1118,6 +1130,7 @@ double goc_bytes_per_node(const goc_lattice *L) {
 
 goc_status goc_moments(goc_lattice *L, int cartesian, double *rho, double *u1, double *u2,
                        double *b1, double *b2) {
+    TraceRange trace_("goc_moments");
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
     const bool rotate = cartesian && L->map.kind[0] == GOC_MAP_ANNULUS;
     if (cartesian && L->map.kind[0] == GOC_MAP_TABLE)
@@ -1185,6 +1198,7 @@ goc_status goc_diagnostics(goc_lattice *L, double *mass, double *residual_u, dou
 }
 
 goc_status goc_run_until(goc_lattice *L, double tol, long long max_steps, long long *done, double *residual) {
+    TraceRange trace_("goc_run_until");
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
     if (max_steps < 0) return fail(GOC_EINVAL, "max_steps must be >= 0");
     if (!L->uout[0]) {
@@ -1571,6 +1585,7 @@ goc_status goc_batch_remove(goc_batch *B, int slot) {
 }
 
 goc_status goc_batch_step(goc_batch *B, long long nsteps) {
+    TraceRange trace_("goc_batch_step");
     if (!B) return fail(GOC_EINVAL, "batch is NULL");
     if (nsteps < 0) return fail(GOC_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return GOC_OK;
