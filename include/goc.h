@@ -343,6 +343,15 @@ goc_status goc_batch_usage(const goc_batch *b, long long *used, long long *budge
 /* ---- errors ------------------------------------------------------------ */
 const char *goc_last_error(void);
 
+/* Guard bands (a debug aid in place of a device memory checker): when the
+ * environment variable GOC_GUARD_BANDS is set at goc_create, the padding
+ * columns of every population, force and MIE plane and a 64 KB tail after
+ * each such buffer are filled with a canary byte, which no kernel writes.
+ * goc_check_guards counts the guard bytes that changed (*bad; 0 when no stray
+ * write happened).  Synchronises.  GOC_EINVAL if the lattice has no guards.
+ * goc_set_state rewrites the padding with the saved state's bytes. */
+goc_status goc_check_guards(goc_lattice *lat, long long *bad);
+
 /* Failure-detection self-test: one block waits on a device barrier that
  * nothing completes and gives up after `polls` polls (1 .. 2^26), the way
  * every device-side wait of the step kernels is bounded.  Returns

@@ -70,6 +70,7 @@ SIGNATURES = {
     "goc_batch_usage": (c_int, [c_void_p, P(c_ll), P(c_ll), P(c_int)]),
     "goc_mass_noalloc": (c_int, [c_void_p, P(c_double)]),
     "goc_selftest_bounded_wait": (c_int, [c_ll]),
+    "goc_check_guards": (c_int, [c_void_p, P(c_ll)]),
     "goc_launch_config": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
     "goc_set_launch_config": (c_int, [c_void_p, c_int, c_int]),
     "goc_last_error": (ctypes.c_char_p, []),

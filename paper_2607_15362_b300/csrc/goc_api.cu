@@ -118,6 +118,7 @@ struct goc_lattice {
     int graph_cur = 0;                           // buffer the captured graph starts from
     bool owns_stream = false;
     bool in_batch = false;                       // stepped only through goc_batch_step
+    bool guard = false;                          // guard bands: padding columns and buffer tails hold a canary
     int *hflag = nullptr;                        // pinned host copy of flag[0], refreshed after each goc_step
     cudaEvent_t flag_ev = nullptr;               // completion of that copy
     bool fresh = false;                          // buffer holds f^0 (pre-collision): next step reads in place
@@ -505,6 +506,57 @@ goc_status compute_metric(const goc_grid *grid, const goc_map *map, cudaStream_t
     return GOC_OK;
 }
 
+// Guard bands (debug aid in place of a memory checker): with GOC_GUARD_BANDS
+// set at creation, the padding columns [nx, pitch) of every plane of the
+// population, force and MIE buffers and a tail after each buffer hold the
+// byte 0xA5; no kernel writes there, so goc_check_guards counting other bytes
+// finds stray writes.
+constexpr size_t kGuardTail = 65536;
+constexpr unsigned char kCanary = 0xA5;
+size_t guard_tail(const goc_lattice *L) { return L->guard ? kGuardTail : 0; }
+
+__global__ void guard_kernel(unsigned char *buf, long long rows, long long row_bytes, long long valid_bytes,
+                             long long tail_bytes, int check, unsigned long long *bad) {
+    const long long padw = row_bytes - valid_bytes, pad = rows * padw, total = pad + tail_bytes;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const long long a = k < pad ? (k / padw) * row_bytes + valid_bytes + k % padw : rows * row_bytes + (k - pad);
+        if (check) {
+            if (buf[a] != kCanary) atomicAdd(bad, 1ull);
+        } else {
+            buf[a] = kCanary;
+        }
+    }
+}
+
+// Fill (check = false) or count (check = true, into *bad) the guard bytes of
+// both buffers of every population array of L.
+goc_status guard_pass(goc_lattice *L, bool check, long long *bad) {
+    const long long es = (long long)elem_size(L->storage), row = L->pitch * es, valid = L->nx * es;
+    unsigned long long *d = nullptr;
+    if (check) {
+        CU(cudaMalloc(&d, sizeof(unsigned long long)));
+        CU(cudaMemsetAsync(d, 0, sizeof(unsigned long long), L->stream));
+    }
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+        void *bufs[3] = {L->f[b], L->F[b], L->g[b]};
+        const int planes[3] = {9, 2, 10};
+        for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+            if (!bufs[k]) continue;
+            guard_kernel<<<148, 256, 0, L->stream>>>(static_cast<unsigned char *>(bufs[k]), (long long)planes[k] * L->ny,
+                                                    row, valid, (long long)kGuardTail, check ? 1 : 0, d);
+            e = cudaGetLastError();
+        }
+    }
+    unsigned long long h = 0;
+    if (e == cudaSuccess && check) e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, L->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return fail(GOC_ECUDA, "guard pass failed: %s", cudaGetErrorString(e));
+    if (bad) *bad = (long long)h;
+    return GOC_OK;
+}
+
 // Self-test of the bounded device-side wait: one thread waits on an mbarrier
 // that nothing completes, gives up after `polls` polls and records status 2,
 // as the step kernels' waits do; the context stays usable.
@@ -679,6 +731,12 @@ extern "C" {
 
 const char *goc_last_error(void) { return g_err.c_str(); }
 
+goc_status goc_check_guards(goc_lattice *L, long long *bad) {
+    if (!L || !bad) return fail(GOC_EINVAL, "lattice and bad are required");
+    if (!L->guard) return fail(GOC_EINVAL, "guard bands are off (set GOC_GUARD_BANDS before goc_create)");
+    return guard_pass(L, true, bad);
+}
+
 goc_status goc_selftest_bounded_wait(long long polls) {
     if (polls < 1 || polls > (1LL << 26)) return fail(GOC_EINVAL, "polls must be in [1, 2^26]");
     int *d = nullptr, h = -1;
@@ -780,6 +838,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     cudaGetDevice(&L->device);
     L->nx = grid->nx;
     L->ny = grid->ny;
+    L->guard = std::getenv("GOC_GUARD_BANDS") != nullptr;
     L->pitch = (grid->nx + 31) / 32 * 32;
     L->plane = (long long)L->pitch * L->ny;
     const size_t es = elem_size(L->storage);
@@ -792,9 +851,9 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         }                      \
     } while (0)
     for (int b = 0; b < 2; b++) {
-        TRY(dalloc(L, &L->f[b], 9 * L->plane * es));
-        TRY(dalloc(L, &L->F[b], 2 * L->plane * es));
-        if (L->mhd.enabled) TRY(dalloc(L, &L->g[b], 10 * L->plane * es));
+        TRY(dalloc(L, &L->f[b], 9 * L->plane * es + guard_tail(L)));
+        TRY(dalloc(L, &L->F[b], 2 * L->plane * es + guard_tail(L)));
+        if (L->mhd.enabled) TRY(dalloc(L, &L->g[b], 10 * L->plane * es + guard_tail(L)));
     }
     const bool curv = map->kind[0] == GOC_MAP_ANNULUS;
     TRY(dalloc(L, &L->tab1, (curv ? 8 : 7) * (size_t)L->nx * sizeof(float)));
@@ -1011,6 +1070,7 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     }
     if (std::getenv("GOC_DISABLE_TMA")) L->tma_ok = false;
     TRY(run_init(L, nullptr, nullptr, nullptr, nullptr, nullptr));
+    if (L->guard) TRY(guard_pass(L, false, nullptr));
     {
         cudaError_t e = cudaMemsetAsync(L->flag, 0, 8 * sizeof(int), L->stream);
         if (e != cudaSuccess) {

@@ -705,3 +705,48 @@ def test_bounded_device_wait_times_out_and_leaves_the_device_usable(gpu):
     L.sync()
     assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= 1e-5
     L.close()
+
+
+@pytest.mark.parametrize("case", ["cavity", "hartmann_fp16", "annulus_mhd", "spiral"])
+def test_no_stray_writes_into_guard_bands(gpu, case, monkeypatch):
+    """With GOC_GUARD_BANDS set, the padding columns of every plane and a
+    64 KB tail after every population, force and MIE buffer hold a canary;
+    after stepping (ragged tiles, periodic seams, walls, the MIE, 16-bit
+    storage, node tables) and re-initialising, no guard byte has changed."""
+    import ctypes
+    from paper_2607_15362_b300 import _abi
+    monkeypatch.setenv("GOC_GUARD_BANDS", "1")
+    storage = "fp16" if case.endswith("fp16") else "fp32"
+    if case == "cavity":
+        prob = gi.Problem("cavity", 100, 90, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
+                          {"Re": 30.0, "u_lid": 0.05})
+        spec = prob.lattice_spec(cs2_of(prob))
+    elif case == "hartmann_fp16":
+        prob = gi.Problem("hartmann", 4, 48, {"kind": "uniform"}, {"kind": "tanh2", "beta": 1.5},
+                          {"Ha": 10.0, "Re": 10.0, "tau": 1.0, "tau_m": 1.0})
+        spec = prob.lattice_spec(cs2_of(prob))
+    elif case == "annulus_mhd":
+        prob = gi.taylor_couette(n1=45, n2=11, r_in=6.0, sectors=9.0, Re=20.0, u_in=1.0, u_out=1.5)
+        spec = prob.lattice_spec(cs2_of(prob))
+        spec["walls"]["W"] = dict(spec["walls"]["W"], B=(0.02, 0.005))
+        spec["mhd"] = {"tau_m": 0.9, "mu_m": 2.0, "B_init": (0.01, 0.004)}
+    else:
+        prob = gi.spiral_cavity(40, 37)
+        spec = prob.lattice_spec(cs2_of(prob))
+    L = goc.Lattice(spec, storage=storage)
+    bad = ctypes.c_longlong(-1)
+    _abi.check(goc.lib().goc_check_guards(L._h, ctypes.byref(bad)))
+    assert bad.value == 0
+    L.step(300)
+    L.moments()
+    L.init_fields()
+    L.step(101)
+    _abi.check(goc.lib().goc_check_guards(L._h, ctypes.byref(bad)))
+    assert bad.value == 0
+    if case == "cavity":   # the check sees a changed guard byte: one written through goc_set_state
+        st = bytearray(L.get_state())
+        st[64 + 100 * 4] ^= 0xFF            # first padding byte of row 0 of population plane 0
+        L.set_state(bytes(st))
+        _abi.check(goc.lib().goc_check_guards(L._h, ctypes.byref(bad)))
+        assert bad.value >= 1
+    L.close()
