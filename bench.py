@@ -175,9 +175,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     spiral = args.grid == "spiral"
     if spiral:   # the same cavity on a general orthogonal grid given node by node
-        prob = gi.spiral_cavity(args.cavity_n, args.cavity_n, Re=1000.0, u_lid=0.05, mach_matched=True)
+        prob = gi.spiral_cavity(args.cavity_n, args.cavity_n, Re=args.cavity_re, u_lid=0.05, mach_matched=True)
     else:
-        prob = gi.lid_cavity(n=args.cavity_n)
+        prob = gi.lid_cavity(n=args.cavity_n, Re=args.cavity_re)
     _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
     spec = prob.lattice_spec(cs2)
     lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream)
@@ -271,7 +271,8 @@ def run_ours(args):
                        "lb_steps_per_bench_step": chunk,
                        "map": ("logarithmic spiral given node by node (every theta_ij non-zero)" if spiral
                                else "tanh beta=2 on both axes"),
-                       "Re": 1000, "u_lid": round(spec["walls"]["N"]["u"], 6), "lid_mach": 0.087, "storage": args.storage,
+                       "Re": args.cavity_re, "u_lid": round(spec["walls"]["N"]["u"], 6), "lid_mach": 0.087,
+                       "storage": args.storage,
                        "parallelism": f"replicas x{world}" if world > 1 else "single lattice",
                        "l2": f"flushed between timed steps (256 MiB write); lattice ({nodes * bpn / 1e6:.0f} MB) "
                              + ("is L2-resident within a step" if nodes * bpn < 100e6 else "exceeds L2")},
@@ -776,6 +777,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     ap.add_argument("--cavity-n", type=int, default=512, help="cavity side (512 is the benchmark workload)")
+    ap.add_argument("--cavity-re", type=float, default=1000.0,
+                    help="cavity Reynolds number (1000 is the benchmark workload; with the Mach-matched lid "
+                         "tau - 1/2 grows as n/Re and the step is stable up to tau of about 2)")
     ap.add_argument("--grid", default="tanh", choices=["tanh", "spiral"],
                     help="cavity grid: tanh map on both axes (the benchmark), or a logarithmic-spiral node table")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
