@@ -173,14 +173,23 @@ def run_ours(args):
     world, rank, local = setup_dist()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    spiral = args.grid == "spiral"
+    spiral, annulus = args.grid == "spiral", args.grid == "annulus"
+    n = args.cavity_n
     if spiral:   # the same cavity on a general orthogonal grid given node by node
-        prob = gi.spiral_cavity(args.cavity_n, args.cavity_n, Re=args.cavity_re, u_lid=0.05, mach_matched=True)
+        prob = gi.spiral_cavity(n, n, Re=args.cavity_re, u_lid=0.05, mach_matched=True)
+    elif annulus:   # Taylor-Couette flow in an annular sector, radius ratio 2, h2 = h1 at mid-radius
+        prob = gi.taylor_couette(n1=n, n2=n, r_in=float(n), sectors=2 * math.pi / math.log(2.0), Re=200.0,
+                                 u_in=1.0, u_out=1.5)
     else:
-        prob = gi.lid_cavity(n=args.cavity_n, Re=args.cavity_re)
+        prob = gi.lid_cavity(n=n, Re=args.cavity_re)
     _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
     spec = prob.lattice_spec(cs2)
-    lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream)
+    if args.mie:   # the coupled MIE with an initial uniform field
+        spec["mhd"] = {"tau_m": 0.9, "mu_m": 2.0, "B_init": (0.01, 0.004)}
+    if args.scheme != "goc":
+        spec["collision"] = {"goc_srt": "srt", "goc_raw": "raw"}[args.scheme]   # the same collision for the oracle
+    geom = 2 if spiral else 1 if annulus else 0
+    lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream, scheme=args.scheme)
     nodes = prob.nodes
     chunk = args.chunk
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -239,7 +248,9 @@ def run_ours(args):
     achieved = bpn * nodes / launch_s / 1e9
     peak = float(peaks.get("hbm_gbs", 6400.0))
     prof = PROFILE_SPIRAL if spiral else PROFILE
-    captured = args.cavity_n == 512 and args.storage == "fp32"   # the captures are of FP32 512^2 launches
+    # the captures are of FP32 512^2 launches of the central-moment NSE step on the two cavity grids
+    captured = (args.cavity_n == 512 and args.storage == "fp32" and not annulus and not args.mie
+                and args.scheme == "goc")
     traffic = profile_traffic(prof) if captured else None
     clocks = clk.summary()
     # instruction-issue view of the same kernel: warp instructions per node
@@ -266,12 +277,17 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "fp32" else f"f32 arithmetic, {args.storage} storage",
-            "data": "synthetic (lid-driven cavity from rest, seeded parameters)",
+            "data": ("synthetic (Taylor-Couette flow from rest)" if annulus
+                     else "synthetic (lid-driven cavity from rest, seeded parameters)"),
             "config": {"workload": prob.name + f"_{args.storage}", "nodes": nodes,
                        "lb_steps_per_bench_step": chunk,
                        "map": ("logarithmic spiral given node by node (every theta_ij non-zero)" if spiral
+                               else "annular sector, radius ratio 2 (Sec. 8.1)" if annulus
                                else "tanh beta=2 on both axes"),
-                       "Re": args.cavity_re, "u_lid": round(spec["walls"]["N"]["u"], 6), "lid_mach": 0.087,
+                       "Re": 200.0 if annulus else args.cavity_re,
+                       "u_lid": None if annulus else round(spec["walls"]["N"]["u"], 6),
+                       "lid_mach": None if annulus else 0.087,
+                       "mie": bool(args.mie), "collision": args.scheme,
                        "storage": args.storage,
                        "parallelism": f"replicas x{world}" if world > 1 else "single lattice",
                        "l2": f"flushed between timed steps (256 MiB write); lattice ({nodes * bpn / 1e6:.0f} MB) "
@@ -281,7 +297,9 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": src, "bytes_per_node": bpn,
-                         "kernel": "goc::step_kernel<float,0,0,2>" if spiral else "goc::step_kernel<float,0,0,0>",
+                         "kernel": "goc::step_kernel<{},{},{},{}>".format(
+                             {"fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}[args.storage],
+                             int(bool(args.mie)), int(args.scheme != "goc"), geom),
                          "launch_us": round(launch_s * 1e6, 3),
                          "launch_config": lat.launch_config, "issue": issue},
             "cpu_baseline": cpu,
@@ -680,11 +698,16 @@ def run_accuracy_mhd(args):
 
 def cpu_baseline(prob, spec_lib, budget_s: float = 15.0):
     """FP64 oracle, as it stands, on this host's cores: a bounded number of
-    time steps of the same 512^2 cavity, scaled to MLUPS."""
+    time steps of the same workload (its own c_s^2; the MIE and collision
+    settings of the GPU run), scaled to MLUPS."""
     import oracle
     cores = os.cpu_count() or 1
     cs2 = oracle.build_metric(prob.lattice_spec(1.0)).cs2()
-    o = oracle.Oracle(prob.lattice_spec(cs2), threads=cores)
+    spec = prob.lattice_spec(cs2)
+    for k in ("mhd", "collision"):
+        if k in spec_lib:
+            spec[k] = spec_lib[k]
+    o = oracle.Oracle(spec, threads=cores)
     t0 = time.perf_counter()
     o.step(1)
     one = time.perf_counter() - t0
@@ -693,7 +716,8 @@ def cpu_baseline(prob, spec_lib, budget_s: float = 15.0):
     o.step(n)
     dt = time.perf_counter() - t0
     return {"value": round(prob.nodes * n / dt / 1e6, 3), "unit": "MLUPS", "cores": o.threads,
-            "kind": "oracle", "sample": f"{n} time steps of the {prob.nx}x{prob.ny} cavity after 1 warm-up step"}
+            "kind": "oracle", "sample": f"{n} time steps of {prob.name or prob.kind} ({prob.nx}x{prob.ny}) "
+                                         "after 1 warm-up step"}
 
 
 def run_oracle_timing(args):
@@ -780,8 +804,12 @@ def main():
     ap.add_argument("--cavity-re", type=float, default=1000.0,
                     help="cavity Reynolds number (1000 is the benchmark workload; with the Mach-matched lid "
                          "tau - 1/2 grows as n/Re and the step is stable up to tau of about 2)")
-    ap.add_argument("--grid", default="tanh", choices=["tanh", "spiral"],
-                    help="cavity grid: tanh map on both axes (the benchmark), or a logarithmic-spiral node table")
+    ap.add_argument("--grid", default="tanh", choices=["tanh", "spiral", "annulus"],
+                    help="tanh map on both axes (the benchmark cavity), the cavity on a logarithmic-spiral node "
+                         "table, or Taylor-Couette flow on the annular sector")
+    ap.add_argument("--scheme", default="goc", choices=["goc", "goc_srt", "goc_raw"],
+                    help="collision: central-moment MRT (the benchmark), SRT (Appendix F), raw-moment MRT (Appendix D)")
+    ap.add_argument("--mie", action="store_true", help="couple the MIE (Appendix G)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
     ap.add_argument("--workload", default="cavity",
