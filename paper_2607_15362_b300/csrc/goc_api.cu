@@ -101,7 +101,6 @@ struct goc_lattice {
     float *tab1 = nullptr, *tab2 = nullptr;      // [7][nx], [7][ny]
     double *m1 = nullptr, *m2 = nullptr;         // FP64 h, theta per axis: [2][n+2]
     float *gm = nullptr;                         // node-table metric: [10][plane] + [4][max(nx, ny)]
-    double *gtab = nullptr;                      // node-table metric in FP64: [6][ny][nx] (initial state)
     float *uout[2] = {nullptr, nullptr};
     int *flag = nullptr;
     double *red = nullptr;                       // 8 doubles
@@ -593,7 +592,7 @@ void free_lattice(goc_lattice *L) {
     cudaStreamSynchronize(L->stream);
     if (L->graph) cudaGraphExecDestroy(L->graph);
     void *ptrs[] = {L->f[0], L->f[1], L->F[0], L->F[1], L->g[0], L->g[1], L->tab1, L->tab2,
-                    L->m1, L->m2, L->gm, L->gtab, L->uout[0], L->uout[1], L->flag, L->red, L->mom};
+                    L->m1, L->m2, L->gm, L->uout[0], L->uout[1], L->flag, L->red, L->mom};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (L->flag_ev) cudaEventDestroy(L->flag_ev);
@@ -654,7 +653,6 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
     q.h1d = L->m1;
     q.h2x = L->sp.curv == 1 ? L->m1 + 2 * (L->nx + 2) : nullptr;
     q.t21x = L->sp.curv == 1 ? L->m1 + 3 * (L->nx + 2) : nullptr;
-    q.gtab = L->gtab;
     q.t1d = L->m1 + L->nx + 2;
     q.h2d = L->m2;
     q.t2d = L->m2 + L->ny + 2;
@@ -928,11 +926,21 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
                                                                        rho0cs2, L->cs2, L->tab1);
     axis_tables_kernel<<<(L->ny + 127) / 128, 128, 0, L->stream>>>(L->m2, L->m2 + L->ny + 2, L->ny, per_y, rho0cs2,
                                                                    L->cs2, L->tab2);
-    if (table) {   // node-table metric: FP64 copy for the initial state, FP32 planes + walls for the step
+    if (table) {   // node-table metric: FP32 planes + walls for the step (and the initial state), the
+                   // link corrections formed in FP64 from a temporary device copy of the table
         const long long N = (long long)L->nx * L->ny;
         const int wmax = std::max(L->nx, L->ny);
-        TRY(dalloc(L, &L->gtab, 6 * N * sizeof(double)));
         TRY(dalloc(L, &L->gm, (10 * L->plane + 8 * (long long)wmax) * sizeof(float)));
+        double *gtab = nullptr;
+        {
+            cudaError_t e = cudaMalloc(&gtab, 6 * N * sizeof(double));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                free_lattice(L);
+                return fail(e == cudaErrorMemoryAllocation ? GOC_ENOMEM : GOC_ECUDA, "node-table staging: %s",
+                            cudaGetErrorString(e));
+            }
+        }
         std::vector<float> walls(8 * (size_t)wmax, 1.f);
         const int nw = 2 * L->ny + 2 * L->nx;
         for (int t = 0; t < 2; t++) {   // t = 0: wall-normal factor, 1: tangential
@@ -949,16 +957,18 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         }
         cudaError_t e = cudaMemsetAsync(L->gm, 0, 10 * L->plane * sizeof(float), L->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(L->gtab, map->table, 6 * N * sizeof(double), cudaMemcpyHostToDevice, L->stream);
+            e = cudaMemcpyAsync(gtab, map->table, 6 * N * sizeof(double), cudaMemcpyHostToDevice, L->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(L->gm + 10 * L->plane, walls.data(), walls.size() * sizeof(float),
                                 cudaMemcpyHostToDevice, L->stream);
         if (e == cudaSuccess) {
             table_metric_kernel<<<dim3((L->nx + 127) / 128, L->ny), 128, 0, L->stream>>>(
-                L->gtab, L->nx, L->ny, L->pitch, L->plane, per_x, per_y, rho0cs2, L->gm);
+                gtab, L->nx, L->ny, L->pitch, L->plane, per_x, per_y, rho0cs2, L->gm);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);   // the host arrays may go after return
+        if (e != cudaSuccess) cudaStreamSynchronize(L->stream);
+        cudaFree(gtab);
         if (e != cudaSuccess) {
             free_lattice(L);
             return fail(GOC_ECUDA, "node-table upload failed: %s", cudaGetErrorString(e));

@@ -189,7 +189,6 @@ struct InitParams {
     StepParams sp;
     const double *h1d, *h2d, *t1d, *t2d;   // FP64 node metric per axis
     const double *h2x, *t21x;              // curvilinear column metric: h2, theta21 over xi1 (else null)
-    const double *gtab;                    // node table [6][ny][nx] (else null)
     double cs2, nu, zeta, rho0, csm2, eta;
     int gi, mhd;
     const double *rho, *u1, *u2, *b1, *b2;
@@ -218,14 +217,13 @@ __global__ void init_kernel(const InitParams q) {
     const bool curv = q.h2x != nullptr;
     double h1 = q.h1d[i], h2 = curv ? q.h2x[i] : q.h2d[j], t11 = q.t1d[i], t22 = curv ? 0.0 : q.t2d[j];
     double t21 = curv ? q.t21x[i] : 0.0, t12 = 0.0;
-    if (q.gtab) {   // node table
-        const long long NN = (long long)p.nx * p.ny;
-        h1 = q.gtab[n];
-        h2 = q.gtab[NN + n];
-        t11 = q.gtab[2 * NN + n];
-        t12 = q.gtab[3 * NN + n];
-        t21 = q.gtab[4 * NN + n];
-        t22 = q.gtab[5 * NN + n];
+    if (p.curv == 2) {   // node table: the FP32 planes the step kernel uses
+        h1 = gm_at(p.gm, p.plane, p.pitch, 0, i, j);
+        h2 = gm_at(p.gm, p.plane, p.pitch, 1, i, j);
+        t11 = gm_at(p.gm, p.plane, p.pitch, 2, i, j);
+        t12 = gm_at(p.gm, p.plane, p.pitch, 3, i, j);
+        t21 = gm_at(p.gm, p.plane, p.pitch, 4, i, j);
+        t22 = gm_at(p.gm, p.plane, p.pitch, 5, i, j);
     }
     const double rho = q.rho[n], U1 = q.u1[n], U2 = q.u2[n];
     const double dU1 = dfd64(q.u1, i, j, p.nx, p.ny, 0, p.per_x);
