@@ -22,9 +22,11 @@
  *  - Layout of host field arrays: row-major [ny][nx], node (i, j) at j*nx + i,
  *    i along xi1, j along xi2.  Lattice units: Delta xi = Delta t = 1.
  *  - Geometry: straight orthogonal grids x = x(xi1), y = y(xi2) (Appendix B,
- *    case (i)), so theta12 = theta21 = 0.  Node placement: wall axes are
- *    cell-centred (eta_j = (j + 1/2)/N, walls half a spacing outside the
- *    first and last node, physical length N); periodic axes use eta_i = i/N.
+ *    case (i); theta12 = theta21 = 0) from the per-axis maps, the curvilinear
+ *    annular sector of Sec. 8.1 (ANNULUS), or any orthogonal grid given node
+ *    by node (TABLE).  Node placement: wall axes are cell-centred (eta_j =
+ *    (j + 1/2)/N, walls half a spacing outside the first and last node,
+ *    physical length N); periodic axes use eta_i = i/N.
  */
 #ifndef GOC_H
 #define GOC_H
@@ -132,7 +134,8 @@ typedef struct {
     double tau_m;           /* magnetic relaxation time (used if eta <= 0) */
     double eta;             /* magnetic resistivity eta = csm^2 (tau_m - 1/2); > 0 overrides tau_m */
     double mu_m;            /* magnetic permeability (current density J = curl B / mu_m); 0 -> 1 */
-    double b_init[2];       /* uniform initial field (B1, B2); also the storage reference state */
+    double b_init[2];       /* uniform initial field (B1, B2); on per-axis grids also the storage
+                               reference state */
 } goc_mhd;
 
 /* Population storage in HBM.  All arithmetic is FP32.  Populations are
@@ -174,7 +177,8 @@ typedef struct {
 /* ---- lifecycle --------------------------------------------------------- */
 
 /* q = min(min h1, min h2) and cs^2 = q^2/3 of a grid/map pair (Eq. GOC-LBE_CFL),
- * computed by the library's FP64 metric kernel.  Either output may be NULL. */
+ * computed by the library's FP64 metric kernel (for a TABLE map, from the
+ * table on the host).  Either output may be NULL. */
 goc_status goc_metric_info(const goc_grid *grid, const goc_map *map, double *q, double *cs2);
 
 /* Create a lattice: FP64 metric precompute (preparatory step (a)), cs rule
