@@ -79,6 +79,8 @@ class Problem:
             nu = cs2 * (tau - 0.5)
             H = float(self.ny)
             U = p["Re"] * nu / (0.5 * H)
+            if "mach_max" in p:   # keep the centreline speed subsonic on this lattice
+                U = min(U, float(p["mach_max"]) * math.sqrt(cs2))
             spec.update(tau=tau, fext=(2.0 * nu * U / (0.5 * H) ** 2, 0.0))
             spec["derived"] = {"U": U, "nu": nu, "H": H}
         elif k == "couette":
@@ -91,6 +93,8 @@ class Problem:
                 u = min(u, float(p["lid_cs_fraction"]) * math.sqrt(cs2))
             spec["walls"]["N"]["u"] = u
             nu = u * self.nx / p["Re"]
+            if "tau_max" in p:   # keep tau = 1/2 + nu/cs^2 inside the step's stability range
+                nu = min(nu, cs2 * (float(p["tau_max"]) - 0.5))
             spec.update(nu=nu, fext=(0.0, 0.0))
             spec["derived"] = {"nu": nu, "u_lid": u}
         elif k == "taylor_green":
@@ -109,6 +113,8 @@ class Problem:
             Ha, Re = float(p["Ha"]), float(p["Re"])
             B0 = Ha * math.sqrt(nu * eta) / H          # rho = mu_m = 1
             u0 = Re * nu / H
+            if "mach_max" in p:   # keep the centreline speed subsonic on this lattice
+                u0 = min(u0, float(p["mach_max"]) * math.sqrt(cs2))
             Fx = u0 * nu / (H * H) / ((1.0 - 1.0 / math.cosh(Ha)) / (Ha * math.tanh(Ha)))
             spec.update(tau=tau, fext=(Fx, 0.0), mhd={"tau_m": taum, "mu_m": 1.0, "B_init": (0.0, B0)})
             spec["walls"]["S"]["B"] = (0.0, B0)
@@ -182,7 +188,11 @@ def batch_lattices(seed: int = 7, count: int = 64, steps: int = 5000) -> list[Pr
     """64 independent stretched-grid lattices: long side log-uniform in
     [128, 2048], aspect uniform in [1, 4], beta uniform in [0.5, 3], Re
     log-uniform in [100, 2000]; half cavities, half channels (Poiseuille or
-    Hartmann with probability 1/2, Ha uniform in [10, 200])."""
+    Hartmann with probability 1/2, Ha uniform in [10, 200]).  A cavity's
+    viscosity is capped at tau = 1 (over long runs the clustered-grid step
+    diverged at tau = 1.5), which raises its Reynolds number where n/Re is
+    large; channel speeds are capped at Mach 0.1 on the lattice, which lowers
+    the Reynolds number of small, fast channels."""
     rng = np.random.default_rng(seed)
     kinds = np.array(["cavity"] * (count // 2) + ["channel"] * (count - count // 2))
     rng.shuffle(kinds)
@@ -196,7 +206,7 @@ def batch_lattices(seed: int = 7, count: int = 64, steps: int = 5000) -> list[Pr
         if kind == "cavity":
             out.append(Problem("cavity", L, short, {"kind": "tanh2", "beta": beta},
                                {"kind": "tanh2", "beta": beta},
-                               {"Re": Re, "u_lid": 0.05, "lid_cs_fraction": 0.1},
+                               {"Re": Re, "u_lid": 0.05, "lid_cs_fraction": 0.1, "tau_max": 1.0},
                                steps=steps, name=f"b{k}_cavity_{L}x{short}"))
         else:
             hart = rng.uniform() < 0.5
@@ -204,11 +214,11 @@ def batch_lattices(seed: int = 7, count: int = 64, steps: int = 5000) -> list[Pr
             if hart:
                 out.append(Problem("hartmann", short, L, {"kind": "uniform"},
                                    {"kind": "tanh2", "beta": beta},
-                                   {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0},
+                                   {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0, "mach_max": 0.1},
                                    steps=steps, name=f"b{k}_hartmann_{short}x{L}"))
             else:
                 out.append(Problem("poiseuille", short, L, {"kind": "uniform"},
-                                   {"kind": "tanh2", "beta": beta}, {"Re": Re, "tau": 0.8},
+                                   {"kind": "tanh2", "beta": beta}, {"Re": Re, "tau": 0.8, "mach_max": 0.1},
                                    steps=steps, name=f"b{k}_poiseuille_{short}x{L}"))
     return out
 
@@ -219,7 +229,8 @@ def serving_trace(seed: int = 11, count: int = 2000, rate_hz: float = 200.0,
     cavity : channel = 1 : 1 among NSE, square sides log-uniform in [64, 2048],
     beta uniform in [0.5, 3], Re log-uniform in [100, 2000], Ha uniform in
     [10, 200]; stop at a step budget log-uniform in [1k, 50k] (p = 1/2) or at
-    residual 1e-8 capped at 50k steps."""
+    residual 1e-8 capped at 50k steps.  Cavity viscosities and channel speeds
+    are capped as in batch_lattices."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -237,14 +248,16 @@ def serving_trace(seed: int = 11, count: int = 2000, rate_hz: float = 200.0,
             budget, tol = 50000, 1e-8
         if mhd:
             prob = Problem("hartmann", side, side, {"kind": "uniform"}, {"kind": "tanh2", "beta": beta},
-                           {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0}, name=f"r{k}_hartmann_{side}")
+                           {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0, "mach_max": 0.1},
+                           name=f"r{k}_hartmann_{side}")
         elif rng.uniform() < 0.5:
             prob = Problem("cavity", side, side, {"kind": "tanh2", "beta": beta},
-                           {"kind": "tanh2", "beta": beta}, {"Re": Re, "u_lid": 0.05, "lid_cs_fraction": 0.1},
+                           {"kind": "tanh2", "beta": beta},
+                           {"Re": Re, "u_lid": 0.05, "lid_cs_fraction": 0.1, "tau_max": 1.0},
                            name=f"r{k}_cavity_{side}")
         else:
             prob = Problem("poiseuille", side, side, {"kind": "uniform"}, {"kind": "tanh2", "beta": beta},
-                           {"Re": Re, "tau": 0.8}, name=f"r{k}_poiseuille_{side}")
+                           {"Re": Re, "tau": 0.8, "mach_max": 0.1}, name=f"r{k}_poiseuille_{side}")
         out.append({"arrival_s": t, "problem": prob, "budget": budget, "tol": tol})
     return out
 

@@ -24,6 +24,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from ._abi import GOC_EDIVERGED, GocError
 from .lattice import Batch, Lattice, metric_info
 
 
@@ -66,6 +67,7 @@ def summarize(results: list[Result], wall_s: float) -> dict:
     return {
         "requests": len(results),
         "done": int(sum(r.status == "done" for r in results)),
+        "diverged": int(sum(r.status == "diverged" for r in results)),
         "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
         "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
         "aggregate_mlups": work / wall_s / 1e6 if wall_s > 0 else None,
@@ -141,9 +143,15 @@ class Server:
             for slot, status in done:
                 a = active.pop(slot)
                 r = a["req"]
-                fields = self.batch.lattice(slot).moments() if self.keep_fields else None
-                if not self.keep_fields:
-                    self.batch.lattice(slot).sync()
+                fields = None
+                try:   # a lattice that diverged is reported as such and evicted; the others go on
+                    fields = self.batch.lattice(slot).moments() if self.keep_fields else None
+                    if not self.keep_fields:
+                        self.batch.lattice(slot).sync()
+                except GocError as e:
+                    if e.status != GOC_EDIVERGED:
+                        raise
+                    status, fields = "diverged", None
                 results.append(Result(r.rid, r.arrival_s * time_scale, a["admitted"], now(), a["steps"],
                                       r.problem.nodes, a["residual"], status, fields))
                 self.batch.remove(slot)
@@ -174,16 +182,20 @@ def run_sequential(requests: list[Request], time_scale: float = 1.0, keep_fields
             time.sleep(wait)
         admitted = time.perf_counter() - t0
         lat = Lattice(lattice_spec(r.problem), storage=r.storage, check_every=check_every, stream=stream)
-        residual = None
-        if r.tol is None:
-            lat.step(r.budget)
-            steps = r.budget
-        else:
-            steps, residual = lat.run_until(r.tol, r.budget)
-        fields = lat.moments() if keep_fields else None
-        lat.sync()
+        residual, status, fields, steps = None, "done", None, r.budget
+        try:
+            if r.tol is None:
+                lat.step(r.budget)
+            else:
+                steps, residual = lat.run_until(r.tol, r.budget)
+            fields = lat.moments() if keep_fields else None
+            lat.sync()
+        except GocError as e:
+            if e.status != GOC_EDIVERGED:
+                raise
+            status, fields = "diverged", None
         results.append(Result(r.rid, r.arrival_s * time_scale, admitted, time.perf_counter() - t0, steps,
-                              r.problem.nodes, residual, "done", fields))
+                              r.problem.nodes, residual, status, fields))
         lat.close()
     return results, summarize(results, time.perf_counter() - t0)
 

@@ -93,3 +93,28 @@ def test_first_come_first_served():
     results, _ = srv.run(reqs)
     order = [r.rid for r in sorted(results, key=lambda r: r.admitted_s)]
     assert order == [0, 1, 2]
+
+
+def test_a_diverged_request_is_evicted_and_the_others_finish():
+    """A lattice whose status word reports divergence when its result is
+    collected is recorded as "diverged" and removed; the requests beside it
+    finish with their exact budgets and the memory is released."""
+    from paper_2607_15362_b300._abi import GOC_EDIVERGED, GocError
+
+    class DivergingLattice(FakeLattice):
+        def sync(self):
+            if self.slot == 1:
+                raise GocError(GOC_EDIVERGED, "lattice diverged")
+
+    class DivergingBatch(FakeBatch):
+        def lattice(self, slot):
+            return DivergingLattice(self, slot)
+
+    fb = DivergingBatch(budget=10 ** 9)
+    reqs = [_req(0, 0.0, 16, 500), _req(1, 0.0, 16, 500), _req(2, 0.0, 16, 800)]
+    srv = Server(0, chunk=300, batch=fb, spec_fn=lambda p: {"nx": p.nx, "ny": p.ny})
+    results, summary = srv.run(reqs)
+    by = {r.rid: r for r in results}
+    assert by[1].status == "diverged" and by[0].status == by[2].status == "done"
+    assert by[2].steps == 800 and summary["diverged"] == 1 and summary["done"] == 2
+    assert fb.used == 0
