@@ -164,6 +164,32 @@ def job_rate(world: int, units_per_rank: float, ms_max: float) -> float:
     return world * units_per_rank / (ms_max * 1e-3) / 1e6
 
 
+def _problem(args):
+    """The workload of the main bench line: the clustered cavity (the
+    benchmark), the cavity on a logarithmic-spiral node table, or
+    Taylor-Couette flow in an annular sector (radius ratio 2, h2 = h1 at
+    mid-radius)."""
+    n = args.cavity_n
+    if args.grid == "spiral":
+        return gi.spiral_cavity(n, n, Re=args.cavity_re, u_lid=0.05, mach_matched=True)
+    if args.grid == "annulus":
+        return gi.taylor_couette(n1=n, n2=n, r_in=float(n), sectors=2 * math.pi / math.log(2.0), Re=200.0,
+                                 u_in=1.0, u_out=1.5)
+    return gi.lid_cavity(n=n, Re=args.cavity_re)
+
+
+def _spec(args, prob, cs2):
+    """Lattice spec of the workload for a given c_s^2 (the MIE and collision
+    options included, in the form both the library binding and the oracle
+    read)."""
+    spec = prob.lattice_spec(cs2)
+    if args.mie:   # the coupled MIE with an initial uniform field
+        spec["mhd"] = {"tau_m": 0.9, "mu_m": 2.0, "B_init": (0.01, 0.004)}
+    if args.scheme != "goc":
+        spec["collision"] = {"goc_srt": "srt", "goc_raw": "raw"}[args.scheme]
+    return spec
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -174,20 +200,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     spiral, annulus = args.grid == "spiral", args.grid == "annulus"
-    n = args.cavity_n
-    if spiral:   # the same cavity on a general orthogonal grid given node by node
-        prob = gi.spiral_cavity(n, n, Re=args.cavity_re, u_lid=0.05, mach_matched=True)
-    elif annulus:   # Taylor-Couette flow in an annular sector, radius ratio 2, h2 = h1 at mid-radius
-        prob = gi.taylor_couette(n1=n, n2=n, r_in=float(n), sectors=2 * math.pi / math.log(2.0), Re=200.0,
-                                 u_in=1.0, u_out=1.5)
-    else:
-        prob = gi.lid_cavity(n=n, Re=args.cavity_re)
+    prob = _problem(args)
     _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
-    spec = prob.lattice_spec(cs2)
-    if args.mie:   # the coupled MIE with an initial uniform field
-        spec["mhd"] = {"tau_m": 0.9, "mu_m": 2.0, "B_init": (0.01, 0.004)}
-    if args.scheme != "goc":
-        spec["collision"] = {"goc_srt": "srt", "goc_raw": "raw"}[args.scheme]   # the same collision for the oracle
+    spec = _spec(args, prob, cs2)
     geom = 2 if spiral else 1 if annulus else 0
     lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream, scheme=args.scheme)
     nodes = prob.nodes
@@ -764,10 +779,10 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    prob = gi.lid_cavity()
+    prob = _problem(args)   # the same workload as the main line, stepped by the oracle
     cores = os.cpu_count() or 1
     cs2 = oracle.build_metric(prob.lattice_spec(1.0)).cs2()
-    o = oracle.Oracle(prob.lattice_spec(cs2), threads=cores)
+    o = oracle.Oracle(_spec(args, prob, cs2), threads=cores)
     per_step = max(1, args.ref_steps_per_step)
     for _ in range(args.warmup):
         o.step(per_step)
@@ -781,10 +796,10 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": prob.name + "_fp32", "nodes": prob.nodes,
+        "config": {"workload": prob.name + f"_{args.storage}", "nodes": prob.nodes,
                    "lb_steps_per_bench_step": per_step, "parallelism": "host cores"},
         "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": o.threads, "kind": "oracle",
-                         "sample": f"{per_step} time steps per benchmark step of the {prob.nx}x{prob.ny} cavity"},
+                         "sample": f"{per_step} time steps per benchmark step of {prob.name} ({prob.nx}x{prob.ny})"},
         "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
