@@ -57,6 +57,15 @@
  *     outgoing population; the wall term applies to every link that crosses
  *     a moving wall (corner diagonals included).
  *
+ * Parity unpinned: the terms proportional to U1 theta21 and U2 theta12 in
+ * tau^c (Eq. tauc) and in C3, C4 (Eqs. 83/85).  Every flow with a closed-form
+ * answer available here has them identically zero (Taylor-Couette flow and
+ * its transpose: no radial velocity and theta12 = 0, resp. theta21 = 0; the
+ * fluid at rest on the spiral grid: U = 0).  They are exercised on the
+ * spiral grid, where the reflection pin fixes their index placement, and the
+ * corrections are checked against the paper's second printed form (Eq. 79
+ * with Eqs. 63b/66b), but no independent value fixes their coefficients.
+ *
  * Layout: node n = j*nx + i (i along xi1, j along xi2); populations f[a*N+n];
  * vector populations g[(c*5+a)*N+n] for component c = 0 (B1), 1 (B2).
  */
