@@ -57,14 +57,15 @@
  *     outgoing population; the wall term applies to every link that crosses
  *     a moving wall (corner diagonals included).
  *
- * Parity unpinned: the terms proportional to U1 theta21 and U2 theta12 in
- * tau^c (Eq. tauc) and in C3, C4 (Eqs. 83/85).  Every flow with a closed-form
- * answer available here has them identically zero (Taylor-Couette flow and
- * its transpose: no radial velocity and theta12 = 0, resp. theta21 = 0; the
- * fluid at rest on the spiral grid: U = 0).  They are exercised on the
- * spiral grid, where the reflection pin fixes their index placement, and the
- * corrections are checked against the paper's second printed form (Eq. 79
- * with Eqs. 63b/66b), but no independent value fixes their coefficients.
+ * Weakest pins: the terms proportional to U1 theta21 and U2 theta12 vanish
+ * in every flow with a closed-form answer available here (Taylor-Couette
+ * flow and its transpose have no radial velocity and theta12 = 0, resp.
+ * theta21 = 0).  tau^c (Eq. tauc, one function for the stresses and the
+ * corrections) is pinned against the curvature part of the strain-rate
+ * tensor the paper defines with its NSE in GOC; the other such terms of C3,
+ * C4 (Eqs. 83/85) only against the paper's second printed form of the
+ * corrections (Eq. 79 with Eqs. 63b/66b), and their index placement by the
+ * spiral-grid reflection pin.
  *
  * Layout: node n = j*nx + i (i along xi1, j along xi2); populations f[a*N+n];
  * vector populations g[(c*5+a)*N+n] for component c = 0 (B1), 1 (B2).
@@ -293,6 +294,13 @@ static double d_xi2(const orc_t *o, const double *phi, int i, int j) {
 
 /* ---- equilibria --------------------------------------------------------- */
 
+/* tau^c (Eq. tauc): the curvature part of the normal stresses. */
+static void tau_c(double rho, double ze, double nu, double U1, double U2, double t12, double t21,
+                  double *tc11, double *tc22) {
+    *tc11 = rho * (ze + nu) * U2 * t12 + rho * (ze - nu) * U1 * t21;
+    *tc22 = rho * (ze + nu) * U1 * t21 + rho * (ze - nu) * U2 * t12;
+}
+
 /* Normal-gradient corrections n3^eq(1), n4^eq(1) (Eqs. 82-85, Delta t = 1). */
 static void corrections(const orc_t *o, double rho, double U1, double U2,
                         double h1, double h2, double t11, double t12, double t21, double t22,
@@ -301,9 +309,8 @@ static void corrections(const orc_t *o, double rho, double U1, double U2,
     double cs2 = o->cs2, nu = o->nu, ze = o->zeta;
     double gi = o->gi ? 1.0 : 0.0;
     double a1 = gi * U1 * U1 / cs2, a2 = gi * U2 * U2 / cs2;
-    /* tau^c (Eq. tauc) */
-    double tc11 = rho * (ze + nu) * U2 * t12 + rho * (ze - nu) * U1 * t21;
-    double tc22 = rho * (ze + nu) * U1 * t21 + rho * (ze - nu) * U2 * t12;
+    double tc11, tc22;
+    tau_c(rho, ze, nu, U1, U2, t12, t21, &tc11, &tc22);
     double D31 = rho * (2 * ze - (ze + nu) * h2 / (h1 * h1) - (ze - nu) / h2
                         - ze * (2 - h2 / cs2 + (3 * a1 + 1) * h2 / (h1 * h1)));
     double D32 = rho * (2 * ze - (ze + nu) * h1 / (h2 * h2) - (ze - nu) / h1
@@ -544,8 +551,8 @@ static void nse_node(orc_t *o, int n) {
     matvec9(Fm, m, mc);
     /* Step 3a-d: stresses and effective force */
     double P = rho * cs2;
-    double tc11 = rho * (ze + nu) * U2 * t12 + rho * (ze - nu) * U1 * t21;
-    double tc22 = rho * (ze + nu) * U1 * t21 + rho * (ze - nu) * U2 * t12;
+    double tc11, tc22;
+    tau_c(rho, ze, nu, U1, U2, t12, t21, &tc11, &tc22);
     double tau11 = rho * (ze + nu) / h1 * dU1 + rho * (ze - nu) / h2 * dU2 + tc11;
     double tau22 = rho * (ze + nu) / h2 * dU2 + rho * (ze - nu) / h1 * dU1 + tc22;
     double fx1 = o->fext1 + (o->mhd ? o->FL1[n] : 0.0);

@@ -22,8 +22,12 @@ MUTATIONS = [
      "double Ft2 = h1 * (fx2 + (-t22) * P",
      pins.test_rest_is_exact_and_mass_conserved_on_a_general_orthogonal_grid),
     ("tau_c_coefficients_swapped",
-     "    /* tau^c (Eq. tauc) */\n    double tc11 = rho * (ze + nu) * U2 * t12 + rho * (ze - nu) * U1 * t21;",
-     "    /* tau^c (Eq. tauc) */\n    double tc11 = rho * (ze - nu) * U2 * t12 + rho * (ze + nu) * U1 * t21;",
+     "    *tc11 = rho * (ze + nu) * U2 * t12 + rho * (ze - nu) * U1 * t21;",
+     "    *tc11 = rho * (ze - nu) * U2 * t12 + rho * (ze + nu) * U1 * t21;",
+     pins.test_correction_coefficients_match_the_E3_E4_form),
+    ("tau_c_index_transposed",
+     "    *tc22 = rho * (ze + nu) * U1 * t21 + rho * (ze - nu) * U2 * t12;",
+     "    *tc22 = rho * (ze + nu) * U1 * t12 + rho * (ze - nu) * U2 * t21;",
      pins.test_correction_coefficients_match_the_E3_E4_form),
     ("q21_printed_sign", "    double q21 = (1 - h2) * (h1 - 1) * (h1 - 1) / h1;",
      "    double q21 = -(1 - h2) * (h1 - 1) * (h1 - 1) / h1;",

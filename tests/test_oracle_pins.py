@@ -136,13 +136,27 @@ def test_central_equilibria_are_the_binomial_transform_of_the_raw_ones():
         assert abs(bad[6] - central[6]) > 1e-6 * abs(u * u * v) * abs(h1 - 1) ** 2 * abs(h2 - 1) or abs(u * v) < 1e-3
 
 
+def _strain_curvature(U, theta):
+    """The derivative-free parts of the diagonal strain rates S_11, S_22 from
+    the strain-rate tensor in GOC as the paper defines it after its NSE in
+    GOC: S_ij = 1/2 [(1/h_j) dU_i/dxi_j + (1/h_i) dU_j/dxi_i
+    - (U_(i) theta_ij + U_(j) theta_ji) + 2 U_m theta_(i)m delta_ij]."""
+    return [0.5 * (-(U[i] * theta[i][i] + U[i] * theta[i][i]) + 2 * sum(U[m] * theta[i][m] for m in range(2)))
+            for i in range(2)]
+
+
 def _E3_E4_form(par, rho, U1, U2, h1, h2, t11, t12, t21, t22, dU1, dU2, dr1, dr2):
     """n3^eq(1), n4^eq(1) from Eq. 79a/79b with the deviations E3 (Eq. 63b) and
-    E4 (Eq. 66b); an independent printed form of Eqs. 82-85."""
+    E4 (Eq. 66b); an independent printed form of Eqs. 82-85.  tau^c is not
+    retyped from Eq. tauc: it is the curvature part of the normal stresses
+    rho [(zeta + nu) S_11 + (zeta - nu) S_22] (the coefficients of the
+    derivative terms of Eq. viscousstress_OCC_modified3) with S_ii from the
+    strain-rate tensor in GOC."""
     cs2, nu, ze = par["cs2"], par["nu"], par["zeta"]
     w3, w4 = par["omega"][3], par["omega"][4]
-    tc11 = rho * (ze + nu) * U2 * t12 + rho * (ze - nu) * U1 * t21
-    tc22 = rho * (ze + nu) * U1 * t21 + rho * (ze - nu) * U2 * t12
+    s11c, s22c = _strain_curvature((U1, U2), ((t11, t12), (t21, t22)))
+    tc11 = rho * ((ze + nu) * s11c + (ze - nu) * s22c)
+    tc22 = rho * ((ze + nu) * s22c + (ze - nu) * s11c)
     E3 = (1 / w3) * ((2 * cs2 - h2 + (3 * U1 ** 2 + cs2) * h2 / h1 ** 2) * rho * dU1
                      + (2 * cs2 - h1 + (3 * U2 ** 2 + cs2) * h1 / h2 ** 2) * rho * dU2
                      + ((3 * cs2 - U1 ** 2) * h2 / h1 ** 2 - h2 - U2 ** 2 / h2) * U1 * dr1
