@@ -68,6 +68,7 @@ def summarize(results: list[Result], wall_s: float) -> dict:
         "requests": len(results),
         "done": int(sum(r.status == "done" for r in results)),
         "diverged": int(sum(r.status == "diverged" for r in results)),
+        "cancelled": int(sum(r.status == "cancelled" for r in results)),
         "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
         "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
         "aggregate_mlups": work / wall_s / 1e6 if wall_s > 0 else None,
@@ -83,6 +84,13 @@ class Server:
         self.spec_fn = spec_fn or lattice_spec
         self.chunk = int(chunk)
         self.keep_fields = keep_fields
+        self._cancelled: set[int] = set()
+
+    def cancel(self, rid: int):
+        """Withdraw request rid: if it waits it is dropped, if it runs it is
+        evicted at the next chunk boundary; either way it is reported as
+        "cancelled".  Safe to call from another thread while run() serves."""
+        self._cancelled.add(rid)
 
     def close(self):
         self.batch.close()
@@ -103,6 +111,16 @@ class Server:
             t = now()
             while pending and pending[0].arrival_s * time_scale <= t:
                 waiting.append(pending.popleft())
+            for r in [r for r in waiting if r.rid in self._cancelled]:   # withdrawn before admission
+                waiting.remove(r)
+                results.append(Result(r.rid, r.arrival_s * time_scale, float("nan"), now(), 0,
+                                      r.problem.nodes, None, "cancelled"))
+            for slot in [s_ for s_, a in active.items() if a["req"].rid in self._cancelled]:   # evicted
+                a = active.pop(slot)
+                r = a["req"]
+                results.append(Result(r.rid, r.arrival_s * time_scale, a["admitted"], now(), a["steps"],
+                                      r.problem.nodes, a["residual"], "cancelled"))
+                self.batch.remove(slot)
             while waiting:                                   # first come, first served
                 r = waiting[0]
                 spec = specs.get(r.rid) or self.spec_fn(r.problem)

@@ -118,3 +118,27 @@ def test_a_diverged_request_is_evicted_and_the_others_finish():
     assert by[1].status == "diverged" and by[0].status == by[2].status == "done"
     assert by[2].steps == 800 and summary["diverged"] == 1 and summary["done"] == 2
     assert fb.used == 0
+
+
+def test_a_cancelled_request_is_withdrawn_waiting_or_running():
+    """cancel(rid) drops a waiting request and evicts a running one at the
+    next chunk boundary (its memory released); both are reported as
+    cancelled and the other requests finish with their exact budgets."""
+    fb = FakeBatch(budget=2 * 16 * 16)
+    reqs = [_req(0, 0.0, 16, 3000), _req(1, 0.0, 16, 900), _req(2, 0.0, 16, 600), _req(3, 0.0, 16, 400)]
+    srv = Server(0, chunk=300, batch=fb, spec_fn=lambda p: {"nx": p.nx, "ny": p.ny})
+
+    orig_step = fb.step
+
+    def step(k):   # after the first chunk: cancel request 0 (running) and 3 (waiting)
+        orig_step(k)
+        if len(fb.calls) == 1:
+            srv.cancel(0)
+            srv.cancel(3)
+    fb.step = step
+    results, summary = srv.run(reqs)
+    by = {r.rid: r for r in results}
+    assert by[0].status == "cancelled" and by[0].steps == 300
+    assert by[3].status == "cancelled" and by[3].steps == 0
+    assert by[1].status == by[2].status == "done" and by[1].steps == 900 and by[2].steps == 600
+    assert summary["cancelled"] == 2 and fb.used == 0
