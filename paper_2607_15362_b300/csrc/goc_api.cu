@@ -413,6 +413,16 @@ goc_status validate(const goc_grid *grid, const goc_map *map) {
     for (int s = 0; s < 4; s++)
         if (grid->bc[s] != GOC_BC_PERIODIC && grid->bc[s] != GOC_BC_WALL)
             return fail(GOC_EINVAL, "bc[%d] must be GOC_BC_PERIODIC or GOC_BC_WALL", s);
+    for (int s = 0; s < 4; s++)
+        if (!std::isfinite(grid->wall_u[s]) || !std::isfinite(grid->wall_b[s][0]) || !std::isfinite(grid->wall_b[s][1]))
+            return fail(GOC_EINVAL, "wall speeds and fields must be finite");
+    for (int a = 0; a < 2; a++) {
+        const double mv[] = {map->beta[a], map->a[a], map->gamma[a], map->alpha[a], map->mu[a], map->yc[a]};
+        for (double v : mv)
+            if (!std::isfinite(v)) return fail(GOC_EINVAL, "map parameters must be finite");
+    }
+    if (!std::isfinite(map->r_inner) || !std::isfinite(map->r_outer) || !std::isfinite(map->sectors))
+        return fail(GOC_EINVAL, "map parameters must be finite");
     if (grid->bc[0] != grid->bc[1] || grid->bc[2] != grid->bc[3])
         return fail(GOC_EINVAL, "opposite sides must both be periodic or both walls");
     if (grid->bc[0] == GOC_BC_WALL && grid->nx < 3) return fail(GOC_EINVAL, "a wall axis needs >= 3 nodes");
@@ -790,6 +800,17 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     goc_status st = validate(grid, map);
     if (st != GOC_OK) return st;
     if (!flow) return fail(GOC_EINVAL, "flow is required");
+    {   // every real parameter finite (a NaN passes the range checks below unnoticed)
+        const double fv[] = {flow->rho0, flow->tau, flow->nu, flow->tau_zeta, flow->omega_free, flow->fext[0],
+                             flow->fext[1]};
+        for (double v : fv)
+            if (!std::isfinite(v)) return fail(GOC_EINVAL, "flow parameters must be finite");
+        if (mhd && mhd->enabled) {
+            const double mv[] = {mhd->tau_m, mhd->eta, mhd->mu_m, mhd->b_init[0], mhd->b_init[1]};
+            for (double v : mv)
+                if (!std::isfinite(v)) return fail(GOC_EINVAL, "MIE parameters must be finite");
+        }
+    }
     if (!(flow->rho0 > 0.0)) return fail(GOC_EINVAL, "rho0 must be > 0");
     if (flow->nu <= 0.0 && !(flow->tau > 0.5)) return fail(GOC_EINVAL, "need nu > 0 or tau > 1/2");
     if (exec && (exec->storage < 0 || exec->storage > 2)) return fail(GOC_EINVAL, "unknown storage %d", exec->storage);

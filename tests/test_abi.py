@@ -183,3 +183,29 @@ def test_a_c_program_drives_the_library_like_the_binding(tmp_path):
     assert float(rho.max()) == pytest.approx(rmax, rel=1e-14)
     assert L.mass() == pytest.approx(mass, rel=1e-14)
     L.close()
+
+
+@pytest.mark.parametrize("where", ["nu", "fext", "wall_u", "beta", "b_init"])
+def test_non_finite_parameters_are_refused_on_the_host(where):
+    """A NaN or infinite parameter (a corrupted request) is refused with
+    GOC_EINVAL before any device call, wherever it sits."""
+    spec = {"nx": 16, "ny": 12, "map2": {"kind": "tanh2", "beta": 1.0},
+            "walls": {"W": None, "E": None, "S": {"u": 0.0}, "N": {"u": 0.01}}, "nu": 0.1,
+            "mhd": {"tau_m": 1.0, "B_init": (0.0, 0.01)}}
+    g, m, f, h = goc.structs_from_spec(spec)
+    bad = float("nan")
+    if where == "nu":
+        f.nu = bad
+    elif where == "fext":
+        f.fext[1] = float("inf")
+    elif where == "wall_u":
+        g.wall_u[3] = bad
+    elif where == "beta":
+        m.beta[1] = bad
+    else:
+        h.b_init[0] = bad
+    out = ctypes.c_void_p()
+    st = _abi.lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f), ctypes.byref(h), None,
+                               ctypes.byref(out))
+    assert st == _abi.GOC_EINVAL and not out.value
+    assert b"finite" in _abi.lib().goc_last_error()
