@@ -17,7 +17,13 @@ def _dptr(a):
 
 
 def structs_from_spec(spec: dict):
-    """goc_grid, goc_map, goc_flow, goc_mhd of a lattice spec (see goc_inputs)."""
+    """goc_grid, goc_map, goc_flow, goc_mhd of a lattice spec (see goc_inputs):
+    nx, ny; walls {"W", "E", "S", "N"} -> None (periodic) or {"u": tangential
+    speed, "B": (B1, B2)}; map1, map2 {"kind": uniform | tanh2 | sine | roberts
+    | tanh1 | sinh | annulus | table, with that map's parameters}; for kind
+    "table" (map1), spec["metric"] holds [ny, nx] arrays h1, h2, t11, t12, t21,
+    t22 and "wall": side -> (h1, h2) along that side; rho0, nu or tau,
+    tau_zeta, omega_free, fext, gi; mhd {tau_m or eta, mu_m, B_init}."""
     g = GocGrid()
     g.nx, g.ny = int(spec["nx"]), int(spec["ny"])
     walls = spec["walls"]
