@@ -209,3 +209,20 @@ def test_non_finite_parameters_are_refused_on_the_host(where):
                                ctypes.byref(out))
     assert st == _abi.GOC_EINVAL and not out.value
     assert b"finite" in _abi.lib().goc_last_error()
+
+
+def test_bench_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference (the FP64 oracle on the host cores) prints one
+    JSON line with the contract's keys, on the same workload options as the
+    main line."""
+    import json
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", "--cavity-n", "32", "--ref-steps-per-step", "1", "--grid", "annulus"],
+                         capture_output=True, text=True, check=True, cwd=ROOT).stdout.strip().splitlines()
+    line = json.loads(out[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["config"]["workload"].startswith("taylor_couette")
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
