@@ -430,7 +430,7 @@ def _transposed_table_of(m):
 
 
 @pytest.mark.parametrize("case,storage", [("annulus", "fp32"), ("transposed", "fp32"), ("spiral", "fp32"),
-                                          ("spiral", "fp16")])
+                                          ("spiral", "fp16"), ("spiral", "bf16")])
 def test_node_table_metric_matches_the_oracle(gpu, case, storage):
     """The node-table step kernel (h1, h2, theta_ij and the link corrections
     read per node) against the oracle: the annular sector of Sec. 8 given as a
@@ -438,7 +438,8 @@ def test_node_table_metric_matches_the_oracle(gpu, case, storage):
     radial direction along xi2 (theta12, theta22 in place of theta21,
     theta11; moving S/N walls) and the lid-driven cavity on the
     logarithmic-spiral grid (40 x 37, every theta_ij non-zero).  Velocity
-    relative L2 <= 1e-5 (FP16 storage: 2e-3) after 500 and 1500 steps."""
+    relative L2 <= 1e-5 (FP16 storage: 2e-3; BF16, 8 significant bits: 2e-2)
+    after 500 and 1500 steps."""
     if case == "spiral":
         prob = gi.spiral_cavity(40, 37, phi=0.6)
         m = oracle.build_metric(prob.lattice_spec(1.0))
@@ -461,13 +462,13 @@ def test_node_table_metric_matches_the_oracle(gpu, case, storage):
     assert cs2 == pytest.approx(m.cs2(), rel=1e-14)
     o = oracle.Oracle(spec_o, threads=8)
     L = goc.Lattice(spec_g, storage=storage)
-    tol = 1e-5 if storage == "fp32" else 2e-3
+    tol = {"fp32": 1e-5, "fp16": 2e-3, "bf16": 2e-2}[storage]
     for n in (500, 1000):
         o.step(n)
         L.step(n)
         fo, fg = o.fields(), L.moments()
         assert relerr(np.stack(fg[1:3]), np.stack(fo[1:3])) <= tol, (case, n)
-        assert np.abs(fg[0] - fo[0]).max() <= (1e-6 if storage == "fp32" else 1e-3)
+        assert np.abs(fg[0] - fo[0]).max() <= {"fp32": 1e-6, "fp16": 1e-3, "bf16": 1e-2}[storage]
     if storage == "fp32":
         mo = (fo[0] * m.h1 * m.h2).sum() if not transpose else (fo[0] * m.h1.T * m.h2.T).sum()
         assert L.mass() == pytest.approx(mo, rel=1e-6)
