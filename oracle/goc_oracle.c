@@ -63,9 +63,10 @@
  * theta21 = 0).  tau^c (Eq. tauc, one function for the stresses and the
  * corrections) is pinned against the curvature part of the strain-rate
  * tensor the paper defines with its NSE in GOC; the other such terms of C3,
- * C4 (Eqs. 83/85) only against the paper's second printed form of the
- * corrections (Eq. 79 with Eqs. 63b/66b), and their index placement by the
- * spiral-grid reflection pin.
+ * C4 (Eqs. 83/85) only against the paper's other printed forms of the
+ * corrections (Eq. 79 with Eqs. 63b/66b; at zeta = nu, the SRT coefficients
+ * of Appendix F), and their index placement by the spiral-grid reflection
+ * pin.
  *
  * Layout: node n = j*nx + i (i along xi1, j along xi2); populations f[a*N+n];
  * vector populations g[(c*5+a)*N+n] for component c = 0 (B1), 1 (B2).
