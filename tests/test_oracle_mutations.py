@@ -29,6 +29,9 @@ MUTATIONS = [
      "    *tc22 = rho * (ze + nu) * U1 * t21 + rho * (ze - nu) * U2 * t12;",
      "    *tc22 = rho * (ze + nu) * U1 * t12 + rho * (ze - nu) * U2 * t21;",
      pins.test_correction_coefficients_match_the_E3_E4_form),
+    ("C3_theta21_bracket_swapped", "+ U1 * ((3 + a1) * h2 / h1 + 2 * h1 / h2 - h1 * h2 / cs2) * t21",
+     "+ U1 * ((3 + a1) * h1 / h2 + 2 * h2 / h1 - h1 * h2 / cs2) * t21",
+     pins.test_correction_coefficients_match_the_E3_E4_form),
     ("q21_printed_sign", "    double q21 = (1 - h2) * (h1 - 1) * (h1 - 1) / h1;",
      "    double q21 = -(1 - h2) * (h1 - 1) * (h1 - 1) / h1;",
      pins.test_central_equilibria_are_the_binomial_transform_of_the_raw_ones),
