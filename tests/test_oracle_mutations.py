@@ -18,6 +18,9 @@ MUTATIONS = [
     ("mie_source_sign", "    Y[1] = H * ((U[0] * B[1] - B[0] * U[1]) * t21);",
      "    Y[1] = -H * ((U[0] * B[1] - B[0] * U[1]) * t21);",
      pins.test_curvilinear_mie_reaches_the_steady_solution_of_its_equation),
+    ("mie_gradient_theta21_dropped", "dB1[c] = -(L1 + 0.5 * csm2 * h1 * h1 * h2 * (t11 + t21) * B[c])",
+     "dB1[c] = -(L1 + 0.5 * csm2 * h1 * h1 * h2 * (t11) * B[c])",
+     pins.test_curvilinear_mie_reaches_the_steady_solution_of_its_equation),
     ("rest_force_theta12_dropped", "double Ft2 = h1 * (fx2 + (t12 - t22) * P",
      "double Ft2 = h1 * (fx2 + (-t22) * P",
      pins.test_rest_is_exact_and_mass_conserved_on_a_general_orthogonal_grid),
