@@ -1,0 +1,35 @@
+"""Host-side helpers of bench.py (no GPU)."""
+import numpy as np
+
+import bench
+import goc_inputs as gi
+
+
+def _tanh_positions(beta, n):
+    eta = (np.arange(n) + 0.5) / n
+    return 0.5 * (1.0 + np.tanh(beta * (2.0 * eta - 1.0)) / np.tanh(beta))
+
+
+def test_vortex_centres_are_found_at_a_known_extremum():
+    """A stream function psi = (x - x0)^2 y + (y - y0)^2 - y0^2 (zero on the
+    bottom wall, minimum at (x0, y0)) sampled on the clustered nodes through
+    u = dpsi/dy: the primary centre comes back to 1e-3; a lone local maximum
+    of psi in the bottom-right corner region is found there."""
+    prob = gi.lid_cavity(n=96, beta=1.2)
+    x = _tanh_positions(1.2, 96)
+    X, Y = np.meshgrid(x, x)
+    x0, y0 = 0.5314, 0.5646
+    u = (X - x0) ** 2 + 2 * (Y - y0)
+    c = bench._vortex_centres(prob, [None, u, None])
+    assert abs(c["primary"][0] - x0) < 1e-3 and abs(c["primary"][1] - y0) < 1e-3
+    # a secondary vortex alone: psi a bump (local maximum) centred at (0.86, 0.11)
+    xb, yb, w = 0.86, 0.11, 0.03
+    bump = 1e-3 * np.exp(-((X - xb) ** 2 + (Y - yb) ** 2) / w ** 2)
+    u2 = bump * (-2 * (Y - yb) / w ** 2)
+    c2 = bench._vortex_centres(prob, [None, u2, None])
+    assert abs(c2["bottom_right"][0] - xb) < 0.01 and abs(c2["bottom_right"][1] - yb) < 0.01
+
+
+def test_job_rate_counts_every_rank():
+    """value = node updates of all ranks / the slowest rank's time."""
+    assert bench.job_rate(4, 1e6, 2000.0) == 4 * 1e6 / 2.0 / 1e6
