@@ -403,6 +403,27 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def _wall_positions(m, n):
+    """Physical node positions, as a fraction of the side, of a wall axis
+    with cell-centred nodes (eta = (j + 1/2)/n, walls at 0 and 1) under the
+    uniform map, the two-wall tanh map (Sec. 6.1) or the two-wall Roberts map
+    (Sec. 6.2, alpha = 1/2, lambda = (gamma + 1)/(gamma - 1)): the geometry
+    the accuracy workloads score against."""
+    import numpy as np
+    eta = (np.arange(n) + 0.5) / n
+    kind = m.get("kind", "uniform")
+    if kind == "uniform":
+        return eta
+    if kind == "tanh2":
+        b = float(m["beta"])
+        return 0.5 * (1.0 + np.tanh(b * (2.0 * eta - 1.0)) / np.tanh(b))
+    if kind == "roberts" and float(m.get("alpha", 0.5)) == 0.5:
+        g = float(m["gamma"])
+        ls = ((g + 1.0) / (g - 1.0)) ** (2.0 * eta - 1.0)
+        return ((g + 1.0) * ls + 1.0 - g) / (2.0 * (1.0 + ls))
+    raise ValueError(m)
+
+
 def _centrelines(prob, fields, u_lid):
     """Velocity profiles of a square cavity along its two centrelines, at the
     physical node positions, normalised by the side and the lid speed:
@@ -411,13 +432,7 @@ def _centrelines(prob, fields, u_lid):
     middle columns (rows), whose average is taken."""
     import numpy as np
 
-    def positions(m, n):
-        eta = (np.arange(n) + 0.5) / n
-        if m.get("kind", "uniform") == "uniform":
-            return eta
-        b = float(m["beta"])
-        return 0.5 * (1.0 + np.tanh(b * (2.0 * eta - 1.0)) / np.tanh(b))
-
+    positions = _wall_positions
     n = prob.nx
     assert n == prob.ny and n % 2 == 0
     y = positions(prob.map2, n)
@@ -514,14 +529,7 @@ def _vortex_centres(prob, fields):
     along each axis."""
     import numpy as np
 
-    def positions(m, n):
-        eta = (np.arange(n) + 0.5) / n
-        if m.get("kind", "uniform") == "uniform":
-            return eta
-        b = float(m["beta"])
-        return 0.5 * (1.0 + np.tanh(b * (2.0 * eta - 1.0)) / np.tanh(b))
-
-    x, y = positions(prob.map1, prob.nx), positions(prob.map2, prob.ny)
+    x, y = _wall_positions(prob.map1, prob.nx), _wall_positions(prob.map2, prob.ny)
     u = fields[1]
     psi = np.empty_like(u)
     psi[0] = 0.5 * u[0] * y[0]
@@ -630,15 +638,11 @@ def run_accuracy_mhd(args):
 
     def run(ny, stretched):
         if stretched:
-            eta = (np.arange(ny) + 0.5) / ny   # cell-centred nodes, walls at eta = 0 and 1
-            if roberts:   # Sec. 6.2 with alpha = 1/2 (clustering at both walls), lambda = (gamma+1)/(gamma-1)
-                g = args.mhd_gamma
-                ls = ((g + 1.0) / (g - 1.0)) ** (2.0 * eta - 1.0)
-                y = ny * ((g + 1.0) * ls + 1.0 - g) / (2.0 * (1.0 + ls))
-                map2 = {"kind": "roberts", "gamma": g, "alpha": 0.5}
+            if roberts:   # clustering at both walls
+                map2 = {"kind": "roberts", "gamma": args.mhd_gamma, "alpha": 0.5}
             else:
-                y = 0.5 * ny * (1.0 + np.tanh(3.0 * (2.0 * eta - 1.0)) / np.tanh(3.0))
                 map2 = {"kind": "tanh2", "beta": 3.0}
+            y = ny * _wall_positions(map2, ny)
             prob = gi.Problem("hartmann", args.mhd_nx, ny, {"kind": "uniform"}, map2,
                               {"Ha": Ha, "Re": Re, "tau": 1.0, "tau_m": 1.0})
             _, cs2 = goc.metric_info(prob.lattice_spec(1.0))

@@ -33,3 +33,15 @@ def test_vortex_centres_are_found_at_a_known_extremum():
 def test_job_rate_counts_every_rank():
     """value = node updates of all ranks / the slowest rank's time."""
     assert bench.job_rate(4, 1e6, 2000.0) == 4 * 1e6 / 2.0 / 1e6
+
+
+def test_bench_wall_positions_match_the_maps():
+    """The node positions bench.py scores profiles against are the uniform,
+    tanh and Roberts maps at cell-centred nodes (checked against the
+    oracle's map positions)."""
+    from oracle.metric import map_position
+    for m, n in (({"kind": "uniform"}, 40), ({"kind": "tanh2", "beta": 1.2}, 64), ({"kind": "tanh2", "beta": 3.0}, 50),
+                 ({"kind": "roberts", "gamma": 1.05, "alpha": 0.5}, 270)):
+        kw = {k: v for k, v in m.items() if k != "kind"}
+        want = map_position(m["kind"], n, np.arange(n) + 0.5, **kw) / n
+        np.testing.assert_allclose(bench._wall_positions(m, n), want, rtol=0, atol=1e-13)
