@@ -263,11 +263,11 @@ goc_status goc_diagnostics(goc_lattice *lat, double *mass, double *residual_u,
                            double *residual_b);
 
 /* Total mass sum f of the current state, like goc_diagnostics(mass), for
- * callers that cannot allocate device memory at the time they ask: code
- * running while a CUDA stream capture is active (cudaMalloc is not allowed
- * there), real-time loops that must not stall on the allocator, and
- * applications whose device memory is all handed to their own pool.  This
- * call allocates nothing: its scratch is a fixed array of
+ * callers that cannot allocate device memory at the time they ask:
+ * real-time loops that must not stall on the allocator, and applications
+ * whose device memory is all handed to their own pool at start-up (a
+ * cudaMalloc there fails or fragments that pool).  This call allocates
+ * nothing: its scratch is a fixed array of
  * GOC_NOALLOC_MAX_BLOCKS + 1 doubles (32 KiB) inside the library, held by every
  * GPU that loads the library until the process exits.  The paper has no
  * counterpart; it is a service of this library.
@@ -277,9 +277,12 @@ goc_status goc_diagnostics(goc_lattice *lat, double *mass, double *residual_u,
  *    that first call before any stream capture.
  *  - All calls share the scratch array and it keeps the last call's contents;
  *    calls whose work overlaps on the GPU (other streams or threads) race.
- *  - The sum is taken in a fixed order (deterministic); it agrees with
- *    goc_diagnostics to FP64 rounding.  Synchronises the lattice's stream;
- *    *mass is a host pointer. */
+ *  - Every grid kind (per-axis maps, the annular sector, node tables) and
+ *    every storage format is supported; the sum is taken in a fixed order
+ *    (deterministic) and agrees with goc_diagnostics to FP64 rounding.
+ *  - Runs on the lattice's device and restores the caller's current device
+ *    before returning.  Waits for the lattice's stream (a synchronous
+ *    device-to-host copy of the result); *mass is a host pointer. */
 #define GOC_NOALLOC_MAX_BLOCKS 4096
 #define GOC_NOALLOC_MAX_NODES 8388608LL
 goc_status goc_mass_noalloc(goc_lattice *lat, double *mass);

@@ -1835,10 +1835,9 @@ goc_status goc_batch_usage(const goc_batch *B, long long *used, long long *budge
 // ============================================================================
 // Total mass without allocating device memory.
 //
-// Some callers cannot call cudaMalloc when they need a diagnostic: code that
-// runs while a CUDA stream capture is active (allocation is not permitted
-// there), real-time loops that must not stall on the allocator, and
-// applications that hand all device memory to their own pool at start-up.
+// Some callers cannot call cudaMalloc when they need a diagnostic: real-time
+// loops that must not stall on the allocator, and applications that hand all
+// device memory to their own pool at start-up.
 // goc_mass_noalloc computes what goc_diagnostics(mass) computes, but its
 // scratch (one partial sum per block plus the final sum) lives in the
 // file-scope array below, which every GPU that loads this library holds until
@@ -1868,7 +1867,7 @@ __global__ void mass_partial_kernel(const StepParams p, double *partial) {
         const long long idx = (long long)j * p.pitch + i;
         double s = 0.0;
         for (int a = 0; a < 9; a++) s += (double)Store<S>::ld(f + a * p.plane + idx) * p.sf;
-        acc += s + (double)p.ax1.h[i] * (double)p.ax2.h[j] * p.rho0;
+        acc += s + node_h1h2(p, i, j) * p.rho0;
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -1892,6 +1891,27 @@ __global__ void mass_final_kernel(double *partial, int nblocks) {
     }
     if (threadIdx.x == 0) partial[GOC_NOALLOC_MAX_BLOCKS] = red[0];
 }
+
+// Makes a device current for the lifetime of the guard and restores the
+// caller's current device afterwards.
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        ok_ = prev_ == dev || cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev_ >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev_) cudaSetDevice(prev_);
+    }
+    bool ok() const { return ok_; }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+
+  private:
+    int prev_ = -1;
+    bool ok_ = false;
+};
 
 // Device address of the scratch array, looked up once per device (the first
 // call on a device does this set-up; make that call before any stream capture).
@@ -1925,9 +1945,8 @@ extern "C" goc_status goc_mass_noalloc(goc_lattice *L, double *mass) {
     if (blocks > GOC_NOALLOC_MAX_BLOCKS)
         return fail(GOC_EINVAL, "goc_mass_noalloc: the lattice has %lld nodes; at most %lld are supported",
                     N, (long long)GOC_NOALLOC_MAX_BLOCKS * GOC_NOALLOC_NODES_PER_BLOCK);
-    int cur_dev = -1;
-    cudaGetDevice(&cur_dev);
-    if (cur_dev != L->device) CU(cudaSetDevice(L->device));
+    DeviceGuard guard(L->device);   // the caller's current device is restored on every return
+    if (!guard.ok()) return fail(GOC_ECUDA, "goc_mass_noalloc: cannot make device %d current", L->device);
     goc_status st;
     double *scratch = noalloc_scratch(&st);
     if (!scratch) return st;

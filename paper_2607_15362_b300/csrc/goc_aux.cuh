@@ -398,6 +398,14 @@ __device__ void block_add(double (&v)[K], double *dst) {
     }
 }
 
+// h1 h2 of node (i, j) in FP64 for every grid kind: per-axis tables
+// (straight), the column metric (annular sector: h2 a function of xi1) or the
+// node table.  The rest-state mass of the node is this times rho0.
+__device__ __forceinline__ double node_h1h2(const StepParams &p, int i, int j) {
+    if (p.curv == 2) return (double)gm_at(p.gm, p.plane, p.pitch, 0, i, j) * gm_at(p.gm, p.plane, p.pitch, 1, i, j);
+    return (double)p.ax1.h[i] * (double)(p.curv ? curv_h2(p.ax1, i) : p.ax2.h[j]);
+}
+
 // Total mass sum_nodes sum_a f (= sum h1 h2 rho): post-collision deviations
 // plus h1 h2 rho0 per node (mass is a collision invariant).
 template <class S>
@@ -411,10 +419,7 @@ __global__ void mass_kernel(const StepParams p, double *out) {
         const long long idx = (long long)j * p.pitch + i;
         double s = 0.0;
         for (int a = 0; a < 9; a++) s += (double)Store<S>::ld(f + a * p.plane + idx) * p.sf;
-        double hh;
-        if (p.curv == 2) hh = (double)gm_at(p.gm, p.plane, p.pitch, 0, i, j) * gm_at(p.gm, p.plane, p.pitch, 1, i, j);
-        else hh = (double)p.ax1.h[i] * (double)(p.curv ? curv_h2(p.ax1, i) : p.ax2.h[j]);
-        acc[0] += s + hh * p.rho0;
+        acc[0] += s + node_h1h2(p, i, j) * p.rho0;
     }
     block_add<1>(acc, out);
 }
