@@ -404,24 +404,9 @@ def run_serve(args):
 
 
 def _wall_positions(m, n):
-    """Physical node positions, as a fraction of the side, of a wall axis
-    with cell-centred nodes (eta = (j + 1/2)/n, walls at 0 and 1) under the
-    uniform map, the two-wall tanh map (Sec. 6.1) or the two-wall Roberts map
-    (Sec. 6.2, alpha = 1/2, lambda = (gamma + 1)/(gamma - 1)): the geometry
-    the accuracy workloads score against."""
-    import numpy as np
-    eta = (np.arange(n) + 0.5) / n
-    kind = m.get("kind", "uniform")
-    if kind == "uniform":
-        return eta
-    if kind == "tanh2":
-        b = float(m["beta"])
-        return 0.5 * (1.0 + np.tanh(b * (2.0 * eta - 1.0)) / np.tanh(b))
-    if kind == "roberts" and float(m.get("alpha", 0.5)) == 0.5:
-        g = float(m["gamma"])
-        ls = ((g + 1.0) / (g - 1.0)) ** (2.0 * eta - 1.0)
-        return ((g + 1.0) * ls + 1.0 - g) / (2.0 * (1.0 + ls))
-    raise ValueError(m)
+    """Physical node positions of a wall axis as a fraction of the side (see
+    goc_inputs.wall_positions)."""
+    return gi.wall_positions(m, n)
 
 
 def _centrelines(prob, fields, u_lid):
@@ -598,16 +583,8 @@ def run_vortex(args):
 
 def _hartmann_analytic(spec, ny, positions):
     """u_x and B_x of the Hartmann flow (Sec. 7.4) at physical positions y in
-    [0, ny] of a channel of half-width H = ny/2."""
-    import numpy as np
-    d = spec["derived"]
-    Ha = float(spec.get("_Ha"))
-    ys = positions / d["H"] - 1.0
-    Ur = d["H"] ** 2 * d["Fx"] / d["nu"]
-    Br = d["H"] ** 2 * d["Fx"] / math.sqrt(d["nu"] * d["eta"])
-    ua = Ur / (Ha * math.tanh(Ha)) * (1 - np.cosh(Ha * ys) / math.cosh(Ha))
-    ba = Br * (-ys / Ha + np.sinh(Ha * ys) / (Ha * math.tanh(Ha) * math.cosh(Ha)))
-    return ua, ba
+    [0, ny] of a channel of half-width H = ny/2 (goc_inputs.hartmann_profiles)."""
+    return gi.hartmann_profiles(spec, float(spec.get("_Ha")), positions)
 
 
 def run_accuracy_mhd(args):

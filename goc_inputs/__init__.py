@@ -145,6 +145,57 @@ def _node_positions(m: dict, n: int) -> np.ndarray:
     raise ValueError(m)
 
 
+def wall_positions(m: dict, n: int) -> np.ndarray:
+    """Physical node positions, as a fraction of the side, of a wall axis
+    with cell-centred nodes (eta = (j + 1/2)/n, walls at 0 and 1) under the
+    uniform map, the two-wall tanh map (Sec. 6.1) or the two-wall Roberts map
+    (Sec. 6.2, alpha = 1/2, lambda = (gamma + 1)/(gamma - 1)): problem
+    geometry for scoring against analytic profiles."""
+    eta = (np.arange(n) + 0.5) / n
+    kind = m.get("kind", "uniform")
+    if kind == "uniform":
+        return eta
+    if kind == "tanh2":
+        b = float(m["beta"])
+        return 0.5 * (1.0 + np.tanh(b * (2.0 * eta - 1.0)) / np.tanh(b))
+    if kind == "roberts" and float(m.get("alpha", 0.5)) == 0.5:
+        g = float(m["gamma"])
+        ls = ((g + 1.0) / (g - 1.0)) ** (2.0 * eta - 1.0)
+        return ((g + 1.0) * ls + 1.0 - g) / (2.0 * (1.0 + ls))
+    raise ValueError(m)
+
+
+def hartmann_profiles(spec: dict, Ha: float, y: np.ndarray):
+    """Analytic u_x and B_x of the Hartmann flow (Sec. 7.4) at physical
+    positions y in [0, 2H] of a channel of half-width H (spec["derived"] of a
+    "hartmann" Problem): u = U_r (1 - cosh(Ha y*)/cosh Ha)/(Ha tanh Ha),
+    B_x = B_r (-y*/Ha + sinh(Ha y*)/(Ha tanh(Ha) cosh Ha)), y* = y/H - 1,
+    U_r = H^2 F_x/nu, B_r = H^2 F_x/sqrt(nu eta) (rho = mu_m = 1)."""
+    d = spec["derived"]
+    ys = np.asarray(y, dtype=np.float64) / d["H"] - 1.0
+    Ur = d["H"] ** 2 * d["Fx"] / d["nu"]
+    Br = d["H"] ** 2 * d["Fx"] / math.sqrt(d["nu"] * d["eta"])
+    ua = Ur / (Ha * math.tanh(Ha)) * (1 - np.cosh(Ha * ys) / math.cosh(Ha))
+    ba = Br * (-ys / Ha + np.sinh(Ha * ys) / (Ha * math.tanh(Ha) * math.cosh(Ha)))
+    return ua, ba
+
+
+def steady_strips() -> dict:
+    """x-invariant channel strips whose steady states the 16-bit storage
+    tests score against (oracle profiles in tests/golden/): the Poiseuille
+    channel of the benchmark (32 x 64), a Hartmann strip (4 x 96, tanh beta =
+    2, Ha = 20, Re = 20) and a strip of the 256 x 1024 Hartmann channel with
+    its clustering (tanh beta = 3, Ha = 100, Re = 100).  name -> (Problem,
+    start, steps on the GPU); start "analytic" begins from the profiles of
+    Sec. 7.4 (the clustered channel needs ~1e8 steps from rest)."""
+    return {
+        "poiseuille_64": (poiseuille_channel(), "rest", 800_000),
+        "hartmann_ha20_96": (Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
+                                     {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0}), "rest", 800_000),
+        "hartmann_ha100_1024": (hartmann_channel(nx=4), "analytic", 500_000),
+    }
+
+
 # ---- the benchmark configurations -------------------------------------------
 
 def poiseuille_channel(nx: int = 32, ny: int = 64, beta: float = 1.5) -> Problem:

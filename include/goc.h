@@ -172,6 +172,17 @@ typedef struct {
     int plateau_checks;     /* goc_run_until also stops once this many successive checks bring
                                no new smallest residual (the FP32/FP16 rounding floor lies above
                                the tolerance); 0 = never */
+    int reference_every;    /* FP16/BF16 storage on straight grids: the stored deviations of the
+                               xi1 links (1, 3) are taken relative to a reference that carries
+                               the row-mean velocity A1(j), and the MIE populations relative to
+                               the row-mean field Bref(j); the reference is refreshed from the
+                               state every this many steps (and at initialisation), so that at a
+                               steady flow along xi1 the stored values -- and their rounding
+                               noise -- shrink to what the row means do not capture.
+                               0 -> every 1024 steps; < 0 = never (A1 = 0, Bref = B_init).
+                               goc_step refreshes exactly at multiples of the period; in a
+                               batch, at the end of the goc_batch_step call that reaches one.
+                               Ignored for FP32 storage, curved grids and scheme 1. */
 } goc_exec;
 
 /* ---- lifecycle --------------------------------------------------------- */

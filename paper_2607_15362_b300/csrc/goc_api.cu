@@ -79,7 +79,8 @@ goc_status fail(goc_status st, const char *fmt, ...) {
 
 size_t elem_size(int storage) { return storage == GOC_FP32 ? 4 : 2; }
 
-constexpr int kGraphSteps = 64;   // steps per captured graph (even: one buffer cycle per 2)
+constexpr int kGraphSteps = 64;
+constexpr int kRefEvery = 1024;   // default steps between refreshes of the per-row storage reference   // steps per captured graph (even: one buffer cycle per 2)
 
 }  // namespace
 
@@ -131,6 +132,11 @@ struct goc_lattice {
     int cfg_dynamic = 1, cfg_pdl = 1;
     bool tuned = false;                          // chosen by the launch autotuner (or fixed)
     int plateau_checks = 0;                      // goc_exec.plateau_checks
+    // per-row storage reference (16-bit storage on straight grids; see goc_aux.cuh)
+    double *ref64 = nullptr;                     // FP64 master rows [3][ny] (A1, Bref_1, Bref_2), then the next rows
+    float *reft = nullptr;                       // FP32 tables u1r [ny], brow [2][ny], bpull [4][ny]
+    int ref_every = 0;                           // steps between refreshes (0: the reference stays as created)
+    long long ref_next = 0;                      // step count at which the next refresh is due
 };
 
 namespace {
@@ -602,7 +608,8 @@ void free_lattice(goc_lattice *L) {
     cudaStreamSynchronize(L->stream);
     if (L->graph) cudaGraphExecDestroy(L->graph);
     void *ptrs[] = {L->f[0], L->f[1], L->F[0], L->F[1], L->g[0], L->g[1], L->tab1, L->tab2,
-                    L->m1, L->m2, L->gm, L->uout[0], L->uout[1], L->flag, L->red, L->mom};
+                    L->m1, L->m2, L->gm, L->uout[0], L->uout[1], L->flag, L->red, L->mom,
+                    L->ref64, L->reft};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (L->flag_ev) cudaEventDestroy(L->flag_ev);
@@ -622,6 +629,68 @@ goc_status dalloc(goc_lattice *L, T **p, size_t bytes) {
     }
     L->device_bytes += bytes;
     return GOC_OK;
+}
+
+// ---- per-row storage reference (16-bit storage, straight grids) -------------
+// FP32 tables from the FP64 rows src ([3][ny]).
+goc_status ref_tables(goc_lattice *L, const double *src) {
+    const StepParams &p = L->sp;
+    ref_tables_kernel<<<(L->ny + 127) / 128, 128, 0, L->stream>>>(
+        L->m2, L->m2 + L->ny + 2, L->ny, p.per_y, L->flow.rho0, L->csm2, src, L->reft, L->reft + L->ny,
+        L->reft + 3 * L->ny);
+    CU(cudaGetLastError());
+    return GOC_OK;
+}
+
+// The reference of a new state: A1 = 0, Bref = the initial uniform field.
+goc_status ref_reset(goc_lattice *L) {
+    const int ny = L->ny;
+    const double v[3] = {0.0, L->mhd.enabled ? L->mhd.b_init[0] : 0.0, L->mhd.enabled ? L->mhd.b_init[1] : 0.0};
+    for (int k = 0; k < 3; k++) {
+        fill_kernel<<<(ny + 255) / 256, 256, 0, L->stream>>>(L->ref64 + (long long)k * ny, ny, v[k]);
+        CU(cudaGetLastError());
+    }
+    return ref_tables(L, L->ref64);
+}
+
+// Refresh: row means of U1 and B of the current state become the reference,
+// the stored values are re-expressed against it, the tables rebuilt.
+goc_status ref_refresh(goc_lattice *L) {
+    StepParams p = params_for(L, L->cur, nullptr);
+    p.nopull = L->fresh ? 1 : 0;
+    double *next = L->ref64 + 3 * (long long)L->ny;
+    const dim3 ag((L->nx + 127) / 128, L->ny);
+    const unsigned salt = (unsigned)L->steps * 0x9E3779B1u + 0x632BE5ABu;
+    const double *h1 = L->m1, *t1 = L->m1 + L->nx + 2, *h2 = L->m2, *t2 = L->m2 + L->ny + 2;
+    const double rho0 = L->flow.rho0, csm2 = L->csm2;
+    const int pre = L->fresh ? 1 : 0;
+    const bool m = L->mhd.enabled;
+#define GOC_REF_LAUNCH(S, MHD)                                                                           \
+    do {                                                                                                 \
+        ref_rows_kernel<S, MHD><<<L->ny, 256, 0, L->stream>>>(p, next);                                   \
+        ref_apply_kernel<S, MHD><<<ag, 128, 0, L->stream>>>(p, h1, t1, h2, t2, next, rho0, csm2, pre, salt); \
+    } while (0)
+    if (L->storage == GOC_FP16_DEV) {
+        if (m) GOC_REF_LAUNCH(__half, true);
+        else GOC_REF_LAUNCH(__half, false);
+    } else {
+        if (m) GOC_REF_LAUNCH(__nv_bfloat16, true);
+        else GOC_REF_LAUNCH(__nv_bfloat16, false);
+    }
+#undef GOC_REF_LAUNCH
+    CU(cudaGetLastError());
+    goc_status st = ref_tables(L, next);
+    if (st != GOC_OK) return st;
+    CU(cudaMemcpyAsync(L->ref64, next, 3 * (size_t)L->ny * sizeof(double), cudaMemcpyDeviceToDevice, L->stream));
+    return GOC_OK;
+}
+
+// Refresh when due (the step count reached ref_next).
+goc_status ref_maybe_refresh(goc_lattice *L) {
+    if (L->ref_every <= 0 || L->steps < L->ref_next) return GOC_OK;
+    goc_status st = ref_refresh(L);
+    L->ref_next = (L->steps / L->ref_every + 1) * L->ref_every;
+    return st;
 }
 
 goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const double *u2,
@@ -654,6 +723,13 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
     if (e != cudaSuccess) {
         if (temporary) cudaFree(dev);
         return fail(GOC_ECUDA, "init copy failed: %s", cudaGetErrorString(e));
+    }
+    if (L->ref64) {   // the initial state is expressed against the creation reference
+        goc_status st = ref_reset(L);
+        if (st != GOC_OK) {
+            if (temporary) cudaFree(dev);
+            return st;
+        }
     }
     InitParams q;
     q.sp = params_for(L, L->cur, nullptr);   // writes the current buffer
@@ -697,6 +773,11 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
         cudaMemsetAsync(L->flag, 0, sizeof(int), L->stream) != cudaSuccess)             // status word
         return fail(GOC_ECUDA, "memset failed");
     if (L->hflag) *L->hflag = 0;
+    if (L->ref_every > 0) {   // reference from the initial fields
+        goc_status st = ref_refresh(L);
+        if (st != GOC_OK) return st;
+        L->ref_next = L->ref_every;
+    }
     return GOC_OK;
 }
 
@@ -1094,6 +1175,13 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         }
     }
     p.flag = L->flag;
+    if (L->storage != GOC_FP32 && p.curv == 0) {   // per-row storage reference of 16-bit straight grids
+        TRY(dalloc(L, &L->ref64, 6 * (size_t)L->ny * sizeof(double)));
+        TRY(dalloc(L, &L->reft, 7 * (size_t)L->ny * sizeof(float)));
+        p.reft = L->reft;
+        const int every = exec ? exec->reference_every : 0;
+        L->ref_every = (L->scheme == 1 || every < 0) ? 0 : (every > 0 ? every : kRefEvery);
+    }
     switch (L->storage) {
         case GOC_FP16_DEV: L->tma_ok = encode_lattice_maps<__half>(L); break;
         case GOC_BF16_DEV: L->tma_ok = encode_lattice_maps<__nv_bfloat16>(L); break;
@@ -1141,7 +1229,24 @@ goc_status goc_step(goc_lattice *L, long long nsteps) {
     return GOC_OK;
 }
 
+static goc_status enqueue_run(goc_lattice *L, long long nsteps);
+
+// Steps in runs that end where a refresh of the per-row storage reference is
+// due (every ref_every steps), so the refresh points depend only on the step
+// count.
 static goc_status enqueue_steps(goc_lattice *L, long long nsteps) {
+    if (L->ref_every <= 0) return enqueue_run(L, nsteps);
+    while (nsteps > 0) {
+        const long long m = std::min(nsteps, std::max(1LL, L->ref_next - L->steps));
+        goc_status st = enqueue_run(L, m);
+        if (st != GOC_OK) return st;
+        nsteps -= m;
+        if ((st = ref_maybe_refresh(L)) != GOC_OK) return st;
+    }
+    return GOC_OK;
+}
+
+static goc_status enqueue_run(goc_lattice *L, long long nsteps) {
     if (L->fresh && nsteps > 0) {   // first step after initialisation: no streaming of f^0
         goc_status st = launch_one(L, nullptr);
         if (st != GOC_OK) return st;
@@ -1310,6 +1415,7 @@ goc_status goc_run_until(goc_lattice *L, double tol, long long max_steps, long l
             if (st != GOC_OK) return st;
             if ((st = launch_one(L, L->uout[0])) != GOC_OK) return st;
             if ((st = launch_one(L, L->uout[1])) != GOC_OK) return st;
+            if ((st = ref_maybe_refresh(L)) != GOC_OK) return st;
             CU(cudaMemsetAsync(L->red, 0, 4 * sizeof(double), L->stream));
             residual_kernel<<<296, 256, 0, L->stream>>>(L->uout[0], L->uout[1], L->plane, L->nx, L->ny, L->pitch, L->red);
             CU(cudaGetLastError());
@@ -1348,7 +1454,8 @@ goc_status goc_get_state(goc_lattice *L, void *buf, size_t *bytes) {
     if (!L || !bytes) return fail(GOC_EINVAL, "lattice and bytes are required");
     const size_t es = elem_size(L->storage);
     const size_t nf = 9 * L->plane * es, nF = 2 * L->plane * es, ng = L->mhd.enabled ? 10 * L->plane * es : 0;
-    const size_t total = 64 + nf + nF + ng;
+    const size_t nr = L->ref64 ? 3 * (size_t)L->ny * sizeof(double) : 0;   // per-row storage reference
+    const size_t total = 64 + nf + nF + ng + nr;
     if (!buf) {
         *bytes = total;
         return GOC_OK;
@@ -1361,6 +1468,7 @@ goc_status goc_get_state(goc_lattice *L, void *buf, size_t *bytes) {
     CU(cudaMemcpyAsync(c + 64, L->f[L->cur], nf, cudaMemcpyDeviceToHost, L->stream));
     CU(cudaMemcpyAsync(c + 64 + nf, L->F[L->cur], nF, cudaMemcpyDeviceToHost, L->stream));
     if (ng) CU(cudaMemcpyAsync(c + 64 + nf + nF, L->g[L->cur], ng, cudaMemcpyDeviceToHost, L->stream));
+    if (nr) CU(cudaMemcpyAsync(c + 64 + nf + nF + ng, L->ref64, nr, cudaMemcpyDeviceToHost, L->stream));
     CU(cudaStreamSynchronize(L->stream));
     *bytes = total;
     return GOC_OK;
@@ -1374,12 +1482,18 @@ goc_status goc_set_state(goc_lattice *L, const void *buf, size_t bytes) {
     std::memcpy(hdr, c, sizeof hdr);
     const size_t es = elem_size(L->storage);
     const size_t nf = 9 * L->plane * es, nF = 2 * L->plane * es, ng = L->mhd.enabled ? 10 * L->plane * es : 0;
+    const size_t nr = L->ref64 ? 3 * (size_t)L->ny * sizeof(double) : 0;
     if (hdr[0] != 0x474f434c4154ll || hdr[1] != L->nx || hdr[2] != L->ny || hdr[3] != L->storage ||
-        hdr[4] != L->mhd.enabled || (size_t)hdr[6] != 64 + nf + nF + ng || bytes < 64 + nf + nF + ng)
+        hdr[4] != L->mhd.enabled || (size_t)hdr[6] != 64 + nf + nF + ng + nr || bytes < 64 + nf + nF + ng + nr)
         return fail(GOC_EINVAL, "state does not match this lattice");
     CU(cudaMemcpyAsync(L->f[L->cur], c + 64, nf, cudaMemcpyHostToDevice, L->stream));
     CU(cudaMemcpyAsync(L->F[L->cur], c + 64 + nf, nF, cudaMemcpyHostToDevice, L->stream));
     if (ng) CU(cudaMemcpyAsync(L->g[L->cur], c + 64 + nf + nF, ng, cudaMemcpyHostToDevice, L->stream));
+    if (nr) {
+        CU(cudaMemcpyAsync(L->ref64, c + 64 + nf + nF + ng, nr, cudaMemcpyHostToDevice, L->stream));
+        goc_status st = ref_tables(L, L->ref64);
+        if (st != GOC_OK) return st;
+    }
     const unsigned step = (unsigned)hdr[5];   // the stochastic-rounding stream continues from the saved step
     CU(cudaMemcpyAsync(L->flag + 2 + L->cur, &step, sizeof(unsigned), cudaMemcpyHostToDevice, L->stream));
     CU(cudaMemsetAsync(L->flag, 0, sizeof(int), L->stream));   // a restored state starts with a clear status
@@ -1387,6 +1501,7 @@ goc_status goc_set_state(goc_lattice *L, const void *buf, size_t bytes) {
     if (L->hflag) *L->hflag = 0;
     L->steps = hdr[5];
     L->fresh = hdr[7] != 0;
+    if (L->ref_every > 0) L->ref_next = (L->steps / L->ref_every + 1) * L->ref_every;
     return GOC_OK;
 }
 
@@ -1401,6 +1516,7 @@ struct goc_batch {
     int max_lat = 0;
     int storage = GOC_FP32;
     int rounding = 0;
+    int reference_every = 0;      // goc_exec.reference_every of the members
     cudaStream_t stream = nullptr;
     int device = 0;
     std::vector<goc_lattice *> slots;
@@ -1606,6 +1722,7 @@ goc_status goc_batch_create(long long hbm_budget_bytes, int max_lattices, const 
     if (exec) {
         B->storage = exec->storage;
         B->rounding = exec->rounding;
+        B->reference_every = exec->reference_every;
         B->stream = (cudaStream_t)exec->cuda_stream;
         if (exec->device >= 0) cudaSetDevice(exec->device);
     }
@@ -1649,6 +1766,7 @@ goc_status goc_batch_add(goc_batch *B, const goc_grid *grid, const goc_map *map,
     ex.cuda_stream = B->stream;
     ex.device = -1;
     ex.rounding = B->rounding;
+    ex.reference_every = B->reference_every;
     goc_lattice *L = nullptr;
     goc_status st = goc_create(grid, map, flow, mhd, &ex, &L);
     if (st != GOC_OK) return st;
@@ -1754,6 +1872,10 @@ goc_status goc_batch_step(goc_batch *B, long long nsteps) {
         if (L) {
             L->steps += nsteps;
             L->cur ^= (int)(nsteps & 1);
+            // per-row storage reference of 16-bit members: refreshed at the end of
+            // the call in which its step count reaches the next refresh point
+            goc_status st = ref_maybe_refresh(L);
+            if (st != GOC_OK) return st;
         }
     if (tail) {   // residual sums of the checked lattices (read by goc_batch_residual)
         for (int k = 0; k < B->max_lat; k++) {

@@ -285,6 +285,11 @@ __global__ void init_kernel(const InitParams q) {
     const double F1r = h2 * q.rho0 * cs2 * (t21 - t11), F2r = h1 * q.rho0 * cs2 * (t12 - t22);
     d[1] += 0.25 * F1r;
     d[3] -= 0.25 * F1r;
+    constexpr bool scaled = Store<S>::scaled;
+    if (scaled && !p.curv) {   // per-row reference of 16-bit storage: +-u1r on links 1, 3
+        d[1] -= (double)GOC_U1R(p, j);
+        d[3] += (double)GOC_U1R(p, j);
+    }
     d[2] += 0.25 * F2r;
     d[4] -= 0.25 * F2r;
     S *fout = static_cast<S *>(p.fout);
@@ -305,10 +310,11 @@ __global__ void init_kernel(const InitParams q) {
         const double lc2 = q.eta * (H - h1 / h2) * dB2 + q.eta * H * h2 * (t22 + t12) * B[c];
         // relative to the pre-collision reference g_ref- = W H B_rest - e.M/2 with
         // M = csm2/2 (h1 H theta11, H h2 theta22) B_rest (B_rest = 0 on curvilinear grids)
-        const double M1 = 0.5 * q.csm2 * h1 * H * t11 * p.brest[c], M2 = 0.5 * q.csm2 * H * h2 * t22 * p.brest[c];
+        const double br = (scaled && !p.curv) ? (double)bref<true>(p, c, j) : (double)p.brest[c];
+        const double M1 = 0.5 * q.csm2 * h1 * H * t11 * br, M2 = 0.5 * q.csm2 * H * h2 * t22 * br;
         for (int a = 0; a < 5; a++) {
             const double W = a == 0 ? 1.0 - 2.0 * q.csm2 : 0.5 * q.csm2;
-            const double geq = W * (H * (B[c] - p.brest[c]) + g1(a) * (h2 * A1 + lc1) / q.csm2
+            const double geq = W * (H * (B[c] - br) + g1(a) * (h2 * A1 + lc1) / q.csm2
                                     + g2(a) * (h1 * A2 + lc2) / q.csm2)
                                + 0.5 * (g1(a) * M1 + g2(a) * M2);
             Store<S>::st(gout + (c * 5 + a) * p.plane + idx, (float)(geq * p.isg));
@@ -324,8 +330,10 @@ __global__ void moments_kernel(const StepParams p, double *out) {
     if (i >= p.nx || j >= p.ny) return;
     const SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                            p.plane, p.pitch, p.sf, p.sF, p.sg};
+    constexpr bool REF = Store<S>::scaled;   // 16-bit storage: straight grids carry the per-row reference
     float h1, h2, ih1, ih2;
     float d[9];
+    float ur1 = 0.f;
     if (p.curv == 2) {
         node_metric<2>(p, i, j, h1, h2, ih1, ih2);
         pull_node<true, 2>(p, src, i, j, h1, h2, d);
@@ -334,13 +342,14 @@ __global__ void moments_kernel(const StepParams p, double *out) {
         pull_node<true, 1>(p, src, i, j, h1, h2, d);
     } else {
         node_metric<0>(p, i, j, h1, h2, ih1, ih2);
-        pull_node<true>(p, src, i, j, h1, h2, d);
+        if (REF) ur1 = GOC_U1R(p, j);
+        pull_node<true, 0, REF>(p, src, i, j, h1, h2, d, ur1);
     }
     float drho, U1, U2;
     // F - F_rest of the previous step (the body force, or zero before the first step, without a stored force)
     const float F1p = p.constF ? (p.nopull ? 0.f : p.fext1) : src.Fv(0, i, j);
     const float F2p = p.constF ? (p.nopull ? 0.f : p.fext2) : src.Fv(1, i, j);
-    fields_from(p, d, F1p, F2p, ih1, ih2, drho, U1, U2);
+    fields_from<REF>(p, d, F1p, F2p, ih1, ih2, drho, U1, U2, ur1);
     const long long N = (long long)p.nx * p.ny, n = (long long)j * p.nx + i;
     out[n] = (double)p.rho0 + (double)drho;
     out[N + n] = U1;
@@ -351,7 +360,7 @@ __global__ void moments_kernel(const StepParams p, double *out) {
         for (int c = 0; c < 2; c++) {
             if (p.curv == 2) pull_mie<true, 2>(p, src, i, j, h1, h2, c, gd[c]);
             else if (p.curv) pull_mie<true, 1>(p, src, i, j, h1, h2, c, gd[c]);
-            else pull_mie<true>(p, src, i, j, h1, h2, c, gd[c]);
+            else pull_mie<true, 0, REF>(p, src, i, j, h1, h2, c, gd[c]);
         }
         const float s0 = (gd[0][0] + gd[0][1] + gd[0][2] + gd[0][3] + gd[0][4]) / (h1 * h2);
         const float s1 = (gd[1][0] + gd[1][1] + gd[1][2] + gd[1][3] + gd[1][4]) / (h1 * h2);
@@ -364,12 +373,129 @@ __global__ void moments_kernel(const StepParams p, double *out) {
             B1 = (double)((s0 * a22 - a12 * s1) / det);
             B2 = (double)((a11 * s1 - a21 * s0) / det);
         } else {
-            B1 = (double)p.brest[0] + (double)s0;
-            B2 = (double)p.brest[1] + (double)s1;
+            B1 = (double)bref<REF>(p, 0, j) + (double)s0;
+            B2 = (double)bref<REF>(p, 1, j) + (double)s1;
         }
     }
     out[3 * N + n] = B1;
     out[4 * N + n] = B2;
+}
+
+// ---- per-row storage reference of 16-bit storage on straight grids ----------
+// The stored deviations of links 1 and 3 are relative to a reference carrying
+// the momentum h2 rho0 A1(j) of a row velocity A1(j); the MIE populations are
+// relative to g_ref = W H Bref(j) -+ e.M/2 with a row field Bref_c(j) (M as for
+// B_rest).  A refresh sets A1 and Bref to the row means of U1 and B of the
+// current state (ref_rows_kernel), re-expresses the stored values against the
+// new reference (ref_apply_kernel), then rebuilds the FP32 tables
+// (ref_tables_kernel).  The FP64 master rows ref[3][ny] are A1, Bref_1, Bref_2.
+
+// u1r of row j: the value the step kernel reads, from the FP64 master rows
+__device__ __forceinline__ float ref_u1r(const double *h2, const double *ref, double rho0, int j) {
+    return (float)(0.5 * rho0 * h2[j] * ref[j]);
+}
+
+// FP32 tables u1r [ny], brow [2][ny], bpull [4][ny] (links 2 and 4, per unit
+// h1: g_ref+(source row) - g_ref-(row j), the MIE analogue of the f_ref
+// corrections; 0 where the source row lies beyond a wall)
+__global__ void ref_tables_kernel(const double *h2, const double *t2, int ny, int per_y, double rho0, double csm2,
+                                  const double *ref, float *u1r, float *brow, float *bpull) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ny) return;
+    u1r[j] = ref_u1r(h2, ref, rho0, j);
+    const bool has_m = per_y || j > 0, has_p = per_y || j < ny - 1;
+    const int jm = per_y ? (j - 1 + ny) % ny : (j > 0 ? j - 1 : j);
+    const int jp = per_y ? (j + 1) % ny : (j < ny - 1 ? j + 1 : j);
+    const double W1 = 0.5 * csm2;
+    for (int c = 0; c < 2; c++) {
+        const double *B = ref + (1 + c) * ny;
+        brow[c * ny + j] = (float)B[j];
+        const double hb = h2[j] * B[j], hm = h2[jm] * B[jm], hp = h2[jp] * B[jp];
+        const double tb = h2[j] * h2[j] * t2[j] * B[j], tm = h2[jm] * h2[jm] * t2[jm] * B[jm],
+                     tp = h2[jp] * h2[jp] * t2[jp] * B[jp];
+        bpull[c * ny + j] = has_m ? (float)(W1 * (hm - hb) + 0.25 * csm2 * (tm + tb)) : 0.f;
+        bpull[(2 + c) * ny + j] = has_p ? (float)(W1 * (hp - hb) - 0.25 * csm2 * (tp + tb)) : 0.f;
+    }
+}
+
+// Row means of U1 and B of the current state, one block of 256 threads per
+// row, summed in a fixed order (the refresh is reproducible): out[3][ny].
+template <class S, bool MHD>
+__global__ void ref_rows_kernel(const StepParams p, double *out) {
+    static_assert(Store<S>::scaled, "the per-row reference belongs to 16-bit storage");
+    __shared__ double red[3][256];
+    const int j = blockIdx.x, t = threadIdx.x;
+    const SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
+                           p.plane, p.pitch, p.sf, p.sF, p.sg};
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = t; i < p.nx; i += 256) {
+        float h1, h2, ih1, ih2, d[9], drho, U1, U2;
+        node_metric<0>(p, i, j, h1, h2, ih1, ih2);
+        const float ur1 = GOC_U1R(p, j);
+        pull_node<true, 0, true>(p, src, i, j, h1, h2, d, ur1);
+        fields_from<true>(p, d, src.Fv(0, i, j), src.Fv(1, i, j), ih1, ih2, drho, U1, U2, ur1);
+        acc[0] += (double)U1;
+        if constexpr (MHD) {
+            for (int c = 0; c < 2; c++) {
+                float gd[5];
+                pull_mie<true, 0, true>(p, src, i, j, h1, h2, c, gd);
+                const float sum = (gd[0] + gd[1] + gd[2] + gd[3] + gd[4]) / (h1 * h2);
+                acc[1 + c] += (double)bref<true>(p, c, j) + (double)sum;
+            }
+        }
+    }
+    for (int k = 0; k < 3; k++) red[k][t] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w)
+            for (int k = 0; k < 3; k++) red[k][t] += red[k][t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[j] = red[0][0] / p.nx;
+        out[p.ny + j] = MHD ? red[1][0] / p.nx : (double)p.brest[0];
+        out[2 * p.ny + j] = MHD ? red[2][0] / p.nx : (double)p.brest[1];
+    }
+}
+
+// Re-express the stored values of the current buffer (post-collision, or the
+// pre-collision f^0 when pre = 1) against the new reference rows refn: the
+// stored value plus f_ref(old) - f_ref(new), rounded like every stored value
+// (stochastically unless round-to-nearest storage was asked for).  The old
+// reference is read from the tables the step kernel uses (p.u1r, p.brow).
+template <class S, bool MHD>
+__global__ void ref_apply_kernel(const StepParams p, const double *h1d, const double *t1d, const double *h2d,
+                                 const double *t2d, const double *refn, double rho0, double csm2, int pre,
+                                 unsigned salt) {
+    static_assert(Store<S>::scaled, "the per-row reference belongs to 16-bit storage");
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= p.nx || j >= p.ny) return;
+    const long long idx = (long long)j * p.pitch + i;
+    uint32_t rng = node_seed((uint32_t)idx, salt);
+    const bool sr = p.sr != 0;
+    S *f = static_cast<S *>(const_cast<void *>(p.fin));
+    const double du = (double)GOC_U1R(p, j) - (double)ref_u1r(h2d, refn, rho0, j);
+    if (du != 0.0) {
+        S *f1 = f + p.plane + idx, *f3 = f + 3 * p.plane + idx;
+        const double v1 = (double)Store<S>::ld(f1) * p.sf + du, v3 = (double)Store<S>::ld(f3) * p.sf - du;
+        put<S>(f1, (float)(v1 * p.isf), sr, rng);
+        put<S>(f3, (float)(v3 * p.isf), sr, rng);
+    }
+    if constexpr (MHD) {
+        S *g = static_cast<S *>(const_cast<void *>(p.gin));
+        const double H = h1d[i] * h2d[j], sgn = pre ? -1.0 : 1.0;
+        for (int c = 0; c < 2; c++) {
+            const double dB = (double)GOC_BROW(p, c, j) - (double)(float)refn[(1 + c) * p.ny + j];
+            if (dB == 0.0) continue;
+            const double M1 = 0.5 * csm2 * dB * h1d[i] * H * t1d[i], M2 = 0.5 * csm2 * dB * H * h2d[j] * t2d[j];
+            for (int a = 0; a < 5; a++) {
+                const double W = a == 0 ? 1.0 - 2.0 * csm2 : 0.5 * csm2;
+                const double shift = W * H * dB + sgn * 0.5 * (g1(a) * M1 + g2(a) * M2);
+                S *ga = g + (c * 5 + a) * p.plane + idx;
+                put<S>(ga, (float)(((double)Store<S>::ld(ga) * p.sg + shift) * p.isg), sr, rng);
+            }
+        }
+    }
 }
 
 // ---- FP64 reductions ---------------------------------------------------------

@@ -49,6 +49,11 @@ __device__ __forceinline__ float gm_wall(const float *gm, long long plane, int n
     return gm[10 * plane + (long long)side * (nx > ny ? nx : ny) + k];
 }
 
+// rows of the per-row storage reference table (StepParams.reft)
+#define GOC_U1R(p, j) ((p).reft[(j)])
+#define GOC_BROW(p, c, j) ((p).reft[(1 + (c)) * (p).ny + (j)])
+#define GOC_BPULL(p, k, c, j) ((p).reft[(3 + 2 * (k) + (c)) * (p).ny + (j)])
+
 // the curvilinear column metric of node column i (see Axis)
 __device__ __forceinline__ float curv_h2(const Axis &a, int i) { return a.dm[i]; }
 __device__ __forceinline__ float curv_ih2(const Axis &a, int i) { return a.dp[i]; }
@@ -106,6 +111,20 @@ struct StepParams {
     int *tctr_next;
     const unsigned *seed_rd;
     unsigned *seed_wr;
+    // Per-row storage reference of 16-bit storage on straight grids (null
+    // otherwise): the stored deviations of links 1 and 3 are taken relative to
+    // a reference that carries the momentum h2 rho0 A1(j) of a row velocity
+    // A1(j), and the MIE populations relative to a row field Bref_c(j); both
+    // are row means of the flow, refreshed every few hundred steps, so that at
+    // a steady channel flow the stored values (and their rounding) shrink to
+    // the part the row means do not capture.
+    // One table of 7 rows of ny values (one pointer: the batch kernel carries
+    // 32 of these parameter blocks in its parameter space):
+    //   row 0           u1r[j] = h2 rho0 A1(j) / 2  (added on link 1, taken off link 3)
+    //   rows 1, 2       brow[c][j] = Bref_c(j)
+    //   rows 3 + 2k + c bpull[k][c][j]: pull correction of MIE link 2 (k = 0) or
+    //                   4 (k = 1), per unit h1, for the source row j -+ 1
+    const float *reft;
     // TMA descriptors of the input buffers (3D: [planes][ny][nx])
     int use_tma;
     CUtensorMap tm_f;          // box [9][TY + 2 HYS][TX + 2 HXS]

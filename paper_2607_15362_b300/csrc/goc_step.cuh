@@ -143,6 +143,13 @@ template <class S> struct SrcSmem {        // the TMA-staged tile
     }
 };
 
+// The storage reference field of the MIE populations of row j: the per-row
+// reference of 16-bit straight-grid storage (REF), else the uniform B_rest.
+template <bool REF>
+__device__ __forceinline__ float bref(const StepParams &p, int c, int j) {
+    return REF ? GOC_BROW(p, c, j) : p.brest[c];
+}
+
 // Pull the nine deviations arriving at node (i, j): the value stored at the
 // source is relative to the source's f_ref+, the result relative to this
 // node's f_ref-, so links 1..4 add f_ref+(source) - f_ref-(node) (the rm/rp
@@ -152,10 +159,13 @@ template <class S> struct SrcSmem {        // the TMA-staged tile
 // (Eq. 101) = e1 rho_w cs2 u / (2 h2_w) across a S/N wall and
 // e2 rho_w cs2 u / (2 h1_w) across a W/E wall (rho_w: this node's density at
 // the time of the outgoing population).  CHECKS = false: every source is
-// inside the lattice (interior tile).
-template <bool CHECKS, int GEOM = 0, class Src>
+// inside the lattice (interior tile).  REF: the per-row storage reference of
+// links 1 and 3 (half momentum ur1 = u1r[j]) is the same at the source and the
+// node of an x link and cancels; a link bounced back at a W/E wall changes
+// from link 1 to 3 (or back), whose references differ by 2 e1 ur1.
+template <bool CHECKS, int GEOM = 0, bool REF = false, class Src>
 __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, int i, int j, float h1, float h2,
-                                          float d[9]) {
+                                          float d[9], float ur1 = 0.f) {
     if (p.nopull) {
 #pragma unroll
         for (int a = 0; a < 9; a++) d[a] = src.fv(a, i, j);
@@ -188,6 +198,7 @@ __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, i
             }
         } else {
             v = src.fv(opp(a), i, j);
+            if (REF && (a == 1 || a == 3)) v -= 2.f * (float)e1(a) * ur1;
             if (p.moving && (e1(a) != 0 && e2(a) != 0)) {
                 int sy = e2(a) > 0 ? SIDE_S : SIDE_N;
                 int sx = e1(a) > 0 ? SIDE_W : SIDE_E;
@@ -219,8 +230,10 @@ __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, i
 // inside adds g_ref+(source) - g_ref-(node) (dm/dp tables).  Outside a wall:
 // anti-bounce-back g_a = -g~_abar + 2 W_a h_wall B_wall,c (Appendix G,
 // boundary conditions), h_wall = h1,wall h2,wall, which in these variables is
-// -s_abar + 2 W_a (h_wall B_wall - H B_rest) + e_a.M.
-template <bool CHECKS, int GEOM = 0, class Src>
+// -s_abar + 2 W_a (h_wall B_wall - H B_rest) + e_a.M.  REF: B_rest is the
+// row field Bref_c(j); links 2 and 4 come from another row and take their
+// corrections from the per-row tables bpull.
+template <bool CHECKS, int GEOM = 0, bool REF = false, class Src>
 __device__ __forceinline__ void pull_mie(const StepParams &p, const Src &src, int i, int j, float h1, float h2,
                                          int c, float d[5]) {
     const float H = h1 * h2;
@@ -229,7 +242,7 @@ __device__ __forceinline__ void pull_mie(const StepParams &p, const Src &src, in
         for (int a = 0; a < 5; a++) d[a] = src.gv(c * 5 + a, i, j);
         return;
     }
-    const float br = p.brest[c];
+    const float br = bref<REF>(p, c, j);
 #pragma unroll
     for (int a = 0; a < 5; a++) {
         int si = i - g1(a), sj = j - g2(a);
@@ -248,8 +261,13 @@ __device__ __forceinline__ void pull_mie(const StepParams &p, const Src &src, in
             if (GEOM == 0) {   // curvilinear grids store g itself (B_rest = 0)
                 if (a == 1) v += br * h2 * p.ax1.dm[i];
                 if (a == 3) v += br * h2 * p.ax1.dp[i];
-                if (a == 2) v += br * h1 * p.ax2.dm[j];
-                if (a == 4) v += br * h1 * p.ax2.dp[j];
+                if (REF) {
+                    if (a == 2) v += h1 * GOC_BPULL(p, 0, c, j);
+                    if (a == 4) v += h1 * GOC_BPULL(p, 1, c, j);
+                } else {
+                    if (a == 2) v += br * h1 * p.ax2.dm[j];
+                    if (a == 4) v += br * h1 * p.ax2.dp[j];
+                }
             }
         } else if (GEOM) {   // h_wall = h1 h2 at the wall point
             // (the column metric has bw premultiplied by the tangential factor,
@@ -301,8 +319,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // rho and U (Eq. GOChydrodynamicfields) from pre-collision deviations d and the
 // previous step's F - F_rest: the -F_rest/2 momentum of f_ref- and the +F_rest/2
 // of the force shift cancel, leaving U1 = (sum d e1 + (F1 - F1_rest)/2)/(rho h2).
+// REF: links 1 and 3 of the reference carry 2 ur1 of momentum more.
+template <bool REF = false>
 __device__ __forceinline__ void fields_from(const StepParams &p, const float d[9], float F1p, float F2p,
-                                            float ih1, float ih2, float &drho, float &U1, float &U2) {
+                                            float ih1, float ih2, float &drho, float &U1, float &U2,
+                                            float ur1 = 0.f) {
     float k00 = 0.f;
 #pragma unroll
     for (int a = 0; a < 9; a++) k00 += d[a];
@@ -310,7 +331,8 @@ __device__ __forceinline__ void fields_from(const StepParams &p, const float d[9
     const float k01 = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
     drho = k00 * (ih1 * ih2);
     const float irho = rcp_approx(p.rho0 + drho);
-    U1 = (k10 + 0.5f * F1p) * irho * ih2;
+    if (REF) U1 = (k10 + fmaf(0.5f, F1p, 2.f * ur1)) * irho * ih2;
+    else U1 = (k10 + 0.5f * F1p) * irho * ih2;
     U2 = (k01 + 0.5f * F2p) * irho * ih1;
 }
 
@@ -339,13 +361,14 @@ struct FieldSmem {
 // omega/2) Psi per moment with m^eq - m_rest, the change of reference f_ref-
 // -> f_ref+ taken off the first moments (which leaves omega F^{n-1}/2 + (1 -
 // omega/2) F_dev there, as in the central-moment path); o = d + P^-1 Delta.
-template <class V>
+// REF: f_ref- - f_rest also holds +-ur1 on links 1 and 3 (per-row reference).
+template <bool REF, class V>
 __device__ __forceinline__ void raw_relax(const StepParams &p, const V (&d)[9], V (&o)[9], V rho, V drho, V U1,
                                           V U2, V ih2, float ih1, V r, V s, V uu, V vv, V uv, V n3, V n4, V F1,
-                                          V F2, V F1dev, V F2dev, V F1p, V F2p, V F1r, V F2r) {
+                                          V F2, V F1dev, V F2dev, V F1p, V F2p, V F1r, V F2r, V ur1) {
     const float *om = p.om, cs2 = p.cs2;
     // populations of f - f_rest by rows e2 = -1, 0, +1 at e1 = -1, 0, +1
-    const V q1 = F1r * 0.25f, q2 = F2r * 0.25f;
+    const V q1 = REF ? fmav(F1r, 0.25f, bc<V>(0.f) - ur1) : F1r * 0.25f, q2 = F2r * 0.25f;
     const V fm[3] = {d[7], d[3] + q1, d[6]};
     const V f0[3] = {d[4] + q2, d[0], d[2] - q2};
     const V fp[3] = {d[8], d[1] - q1, d[5]};
@@ -432,8 +455,9 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
                                         const bool (&own)[Lanes<V>::R], const float (&dn)[Lanes<V>::R][9],
                                         const float (&F1pn)[Lanes<V>::R], const float (&F2pn)[Lanes<V>::R], float h1,
                                         float ih1, const float (&h2n)[Lanes<V>::R], const float (&ih2n)[Lanes<V>::R],
-                                        const float (&fl)[7][Lanes<V>::R]) {
+                                        const float (&fl)[7][Lanes<V>::R], const float (&ur1n)[Lanes<V>::R]) {
     constexpr int R = Lanes<V>::R;
+    constexpr bool REF = Store<S>::scaled && GEOM == 0;   // per-row storage reference
     float th_[R];
 #pragma unroll
     for (int r = 0; r < R; r++)   // theta22
@@ -480,13 +504,13 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     // ---- MIE (Appendix G): local dB, J3, Lorentz force, SRT collision -------
     if constexpr (MHD) {
         S *gout = static_cast<S *>(p.gout);
-        V gd[2][5], dBc[2], dB1[2], dB2[2];
+        V gd[2][5], dBc[2], dB1[2], dB2[2], gsum[2], gmov[2];
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             float t[R][5];
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                if (own[r]) pull_mie<CHECKS, GEOM>(p, src, i, j[r], h1, h2n[r], c, t[r]);
+                if (own[r]) pull_mie<CHECKS, GEOM, REF>(p, src, i, j[r], h1, h2n[r], c, t[r]);
                 else {
 #pragma unroll
                     for (int a = 0; a < 5; a++) t[r][a] = 0.f;
@@ -500,7 +524,9 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
                 gd[c][a] = pack<V>(u_);
             }
             // h1 h2 B = sum g - Y/2 (Eq. 13_C; Y = 0 on straight grids); sum g_ref- = H B_rest
-            dBc[c] = (gd[c][0] + gd[c][1] + gd[c][2] + gd[c][3] + gd[c][4]) * iH;
+            gmov[c] = (gd[c][1] + gd[c][3]) + (gd[c][2] + gd[c][4]);   // the four moving links
+            gsum[c] = gd[c][0] + gmov[c];
+            dBc[c] = gsum[c] * iH;
         }
         if constexpr (GEOM) {
             // curvilinear grids (B_rest = 0): Y_1 = H theta12 (U2 B1 - U1 B2),
@@ -513,8 +539,17 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
             dBc[0] = (s0 * a22 - a12 * s1) * idet;
             dBc[1] = (a11 * s1 - a21 * s0) * idet;
         }
-        B1 = dBc[0] + p.brest[0];
-        B2 = dBc[1] + p.brest[1];
+        {
+            float b0_[R], b1_[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int jr = own[r] ? j[r] : j[0];
+                b0_[r] = bref<REF>(p, 0, jr);
+                b1_[r] = bref<REF>(p, 1, jr);
+            }
+            B1 = dBc[0] + pack<V>(b0_);
+            B2 = dBc[1] + pack<V>(b1_);
+        }
         // A_cd = U_d B_c - B_d U_c (Eq. 2_C): A_11 = A_22 = 0, A_21 = -A_12
         const V A12 = U1 * B2 - B1 * U2;
         const V A1[2] = {bc<V>(0.f), A12}, A2[2] = {bc<V>(0.f) - A12, bc<V>(0.f)};
@@ -539,27 +574,50 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         FL1 = bc<V>(0.f) - J3 * B2;
         FL2 = J3 * B1;
         // SRT collision (Eq. 12_C, S = 0 on straight grids) with g^eq of
-        // Eq. EDF-MIE-base plus the correction of Eq. 42_C.  Relative to the
-        // references: s = d (1 - 1/tau_m) + G/tau_m, G = g^eq - g_ref- without the
-        // B_rest curvature part, which cancels with the change g_ref- -> g_ref+.
+        // Eq. EDF-MIE-base plus the correction of Eq. 42_C, written as
+        // g~ = g + (g^eq - g)/tau_m + S.  Relative to the references: g^eq -
+        // g_ref- without the B_rest curvature part, which cancels with the change
+        // g_ref- -> g_ref+.  The zeroth moment of g^eq is H B = sum g - Y/2 by
+        // construction (the rest link takes H B minus the other four), so the
+        // collision moves sum g by exactly -Y (Eq. 8a_C with its weight) up to
+        // rounding; with the FP32 weights W0 + 4 W1 != 1 and a separate
+        // 1 - 1/tau_m, B drifted by a fixed relative amount every step.  The
+        // rest link (g_0 ~ H B, nearly all of the field) is updated by g^eq_0 -
+        // g_0 = (sum of the moving links - Y/2) - (their g^eq), formed from the
+        // small moving-link values only: near a steady state it is then close to
+        // zero and leaves g_0 unchanged, where forming it from a sum that holds
+        // g_0 itself repeated the same rounding of g_0 every step (a drift of
+        // about one FP32 unit of B per step).
         const V e1c = (H - h2 * ih1) * p.eta, e2c = (H - h1 * ih2) * p.eta;
         const V m1e = H * (p.eta * h1 * (GEOM ? t11 + t21 : t11)), m2e = GEOM ? H * h2 * ((t22 + t12) * p.eta) : H * h2 * t22 * p.eta;
-        const float keep = 1.f - p.itaum, w0 = p.W0 * p.itaum, w1 = p.W1 * p.itaum;
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             const V x1 = fmav(h2, A1[c], fmav(e1c, dB1[c], m1e * dBc[c])) * p.icsm2;
             const V x2 = fmav(h1, A2[c], fmav(e2c, dB2[c], m2e * dBc[c])) * p.icsm2;
-            const V base = H * dBc[c];
-            V G[5] = {base * w0, (base + x1) * w1, (base + x2) * w1, (base - x1) * w1, (base - x2) * w1};
+            V base = gsum[c], mov = gmov[c];                   // H (B - B_rest) = sum g - Y/2
+            V ys = bc<V>(0.f);
             if constexpr (GEOM) {   // source S_a = -W_a Y_c (Eq. 8a_C), weight (1 - 1/(2 tau_m)) in Eq. 12_C
-                const V ys = (c == 0 ? H * t12 * A2[0] : H * t21 * A1[1]) * (0.5f * p.itaum - 1.f);
-                G[0] = fmav(ys, p.W0, G[0]);
-#pragma unroll
-                for (int a = 1; a < 5; a++) G[a] = fmav(ys, p.W1, G[a]);
+                const V Y = c == 0 ? H * t12 * A2[0] : H * t21 * A1[1];
+                base = fmav(Y, -0.5f, base);
+                mov = fmav(Y, -0.5f, mov);
+                ys = Y * (0.5f * p.itaum - 1.f);
+            }
+            V Geq[5];
+            Geq[1] = (base + x1) * p.W1;
+            Geq[2] = (base + x2) * p.W1;
+            Geq[3] = (base - x1) * p.W1;
+            Geq[4] = (base - x2) * p.W1;
+            const V q0 = mov - ((Geq[1] + Geq[3]) + (Geq[2] + Geq[4]));   // g^eq_0 - g_0
+            V Sa[5];
+            if constexpr (GEOM) {
+                const V s1 = ys * p.W1;
+                Sa[1] = Sa[2] = Sa[3] = Sa[4] = s1;
+                Sa[0] = fmav(s1, -4.f, ys);
             }
 #pragma unroll
             for (int a = 0; a < 5; a++) {
-                const V gt = fmav(gd[c][a], keep, G[a]);
+                V gt = fmav(a == 0 ? q0 : Geq[a] - gd[c][a], p.itaum, gd[c][a]);
+                if constexpr (GEOM) gt = gt + Sa[a];
 #pragma unroll
                 for (int r = 0; r < R; r++)
                     if (own[r]) put<S>(gout + (c * 5 + a) * p.plane + idx[r], scl<S>(lane(gt, r), p.isg), sr, rng[r]);
@@ -643,8 +701,8 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
 
     V o[9];
     if constexpr (SRT) {
-        raw_relax<V>(p, d, o, rho, drho, U1, U2, ih2, ih1, r, s, uu, vv, uv, n3, n4, F1, F2, F1dev, F2dev, F1p,
-                     F2p, F1r, F2r);
+        raw_relax<REF, V>(p, d, o, rho, drho, U1, U2, ih2, ih1, r, s, uu, vv, uv, n3, n4, F1, F2, F1dev, F2dev, F1p,
+                          F2p, F1r, F2r, pack<V>(ur1n));
     } else {
     // ---- central moments c = F(U) P (f - f_rest) -----------------------------
     // f - f_rest = d + (f_ref- - f_rest), the latter -F_rest/4 (e . unit) on
@@ -656,7 +714,8 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     const V nu_ = bc<V>(0.f) - u, nv_ = bc<V>(0.f) - v;
     V k0[3], k1[3], k2[3];                                // per row e2 = -1, 0, +1
     {
-        const V q1 = F1r * 0.25f, q2 = F2r * 0.25f;
+        // (REF: f_ref- - f_rest also holds +-ur1 on links 1 and 3)
+        const V q1 = REF ? fmav(F1r, 0.25f, bc<V>(0.f) - pack<V>(ur1n)) : F1r * 0.25f, q2 = F2r * 0.25f;
         const V fm[3] = {d[7], d[3] + q1, d[6]};
         const V f0[3] = {d[4] + q2, d[0], d[2] - q2};
         const V fp[3] = {d[8], d[1] - q1, d[5]};
@@ -797,7 +856,8 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
                                             const bool (&own)[Lanes<V>::R], const FieldSmem &sm,
                                             const float (&dn)[Lanes<V>::R][9], const float (&F1pn)[Lanes<V>::R],
                                             const float (&F2pn)[Lanes<V>::R], float h1, float ih1,
-                                            const float (&h2n)[Lanes<V>::R], const float (&ih2n)[Lanes<V>::R]) {
+                                            const float (&h2n)[Lanes<V>::R], const float (&ih2n)[Lanes<V>::R],
+                                            const float (&ur1n)[Lanes<V>::R]) {
     constexpr int R = Lanes<V>::R;
     const int ex = tx + MH;
     float fl[7][R];
@@ -820,7 +880,7 @@ __device__ __forceinline__ void node_update(const StepParams &p, const Src &src,
             fl[6][r] = 0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex]);
         }
     }
-    collide<S, MHD, CHECKS, V, SRT, GEOM>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl);
+    collide<S, MHD, CHECKS, V, SRT, GEOM>(p, src, i, j, own, dn, F1pn, F2pn, h1, ih1, h2n, ih2n, fl, ur1n);
 }
 
 // One tile of one lattice from a given source; KIND 0: interior (no boundary
@@ -835,6 +895,7 @@ template <class S, bool MHD, int KIND, bool SRT, int GEOM, class Src>
 __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src, int i0, int j0, FieldSmem &sm,
                                              bool ok) {
     constexpr bool CHECKS = KIND != 0;
+    constexpr bool REF = Store<S>::scaled && GEOM == 0;   // per-row storage reference
     constexpr int W = KIND == 0 ? 1 : MH;                 // halo width of the fields
     constexpr int BAND = W * (TX + 2 * W);                // nodes in the top (or bottom) band
     constexpr int RING = 2 * BAND + 2 * W * TY;
@@ -851,7 +912,7 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
     }
     int j[R], ty[R];
     bool own[R];
-    float d[R][9], F1p[R], F2p[R], h2[R], ih2[R];
+    float d[R][9], F1p[R], F2p[R], h2[R], ih2[R], ur1[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {   // own nodes
         ty[r] = threadIdx.y + r * TYT;
@@ -860,14 +921,16 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
         float drho = 0.f, U1 = 0.f, U2 = 0.f;
         F1p[r] = F2p[r] = 0.f;
         h2[r] = ih2[r] = 1.f;
+        ur1[r] = 0.f;
 #pragma unroll
         for (int a = 0; a < 9; a++) d[r][a] = 0.f;
         if (own[r]) {
             node_metric<GEOM>(p, i, j[r], h1, h2[r], ih1, ih2[r]);   // (GEOM 2 runs one node per thread)
-            pull_node<CHECKS, GEOM>(p, src, i, j[r], h1, h2[r], d[r]);
+            if (REF) ur1[r] = GOC_U1R(p, j[r]);
+            pull_node<CHECKS, GEOM, REF>(p, src, i, j[r], h1, h2[r], d[r], ur1[r]);
             F1p[r] = src.Fv(0, i, j[r]);
             F2p[r] = src.Fv(1, i, j[r]);
-            fields_from(p, d[r], F1p[r], F2p[r], ih1, ih2[r], drho, U1, U2);
+            fields_from<REF>(p, d[r], F1p[r], F2p[r], ih1, ih2[r], drho, U1, U2, ur1[r]);
         } else if (CHECKS) {   // ragged tile: past the last node of a periodic axis sits the wrapped node
             int ii = i, jj = j[r];
             bool in = true;
@@ -880,8 +943,9 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
             if (in) {
                 float dd[9], g1, g2, ig1, ig2;
                 node_metric<GEOM>(p, ii, jj, g1, g2, ig1, ig2);
-                pull_node<CHECKS, GEOM>(p, src, ii, jj, g1, g2, dd);
-                fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), ig1, ig2, drho, U1, U2);
+                const float u = REF ? GOC_U1R(p, jj) : 0.f;
+                pull_node<CHECKS, GEOM, REF>(p, src, ii, jj, g1, g2, dd, u);
+                fields_from<REF>(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), ig1, ig2, drho, U1, U2, u);
             }
         }
         sm.rho[ty[r] + MH][tx + MH] = drho;
@@ -918,8 +982,9 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
         if (in) {
             float dd[9], g1, g2, ig1, ig2;
             node_metric<GEOM>(p, ii, jj, g1, g2, ig1, ig2);
-            pull_node<CHECKS, GEOM>(p, src, ii, jj, g1, g2, dd);
-            fields_from(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), ig1, ig2, drho, U1, U2);
+            const float u = REF ? GOC_U1R(p, jj) : 0.f;
+            pull_node<CHECKS, GEOM, REF>(p, src, ii, jj, g1, g2, dd, u);
+            fields_from<REF>(p, dd, src.Fv(0, ii, jj), src.Fv(1, ii, jj), ig1, ig2, drho, U1, U2, u);
         }
         sm.rho[y + MH][x + MH] = drho;
         sm.u1[y + MH][x + MH] = U1;
@@ -929,7 +994,8 @@ __device__ __forceinline__ bool tile_compute(const StepParams &p, const Src &src
     bool any = false;
 #pragma unroll
     for (int r = 0; r < R; r++) any = any || own[r];
-    if (any) node_update<S, MHD, CHECKS, V, SRT, GEOM>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2);
+    if (any)
+        node_update<S, MHD, CHECKS, V, SRT, GEOM>(p, src, i, tx, j, ty, own, sm, d, F1p, F2p, h1, ih1, h2, ih2, ur1);
     return true;
 }
 

@@ -93,7 +93,7 @@ SCHEMES = {"goc": 0, "standard": 1, "goc_srt": 2, "goc_raw": 3}
 
 
 def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", scheme: str = "goc",
-          fixed_launch: bool = False, plateau_checks: int = 0) -> GocExec:
+          fixed_launch: bool = False, plateau_checks: int = 0, reference_every: int = 0) -> GocExec:
     e = GocExec()
     e.storage = _abi.STORAGE[storage]
     e.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
@@ -103,6 +103,7 @@ def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", 
     e.scheme = SCHEMES[scheme]
     e.fixed_launch = 1 if fixed_launch else 0
     e.plateau_checks = int(plateau_checks)
+    e.reference_every = int(reference_every)
     return e
 
 
@@ -111,9 +112,11 @@ class Lattice:
 
     def __init__(self, spec: dict, storage: str = "fp32", stream=None, check_every: int = 100,
                  rounding: str = "stochastic", scheme: str = "goc", fixed_launch: bool = False,
-                 plateau_checks: int = 0, _handle=None, _owner=None):
+                 plateau_checks: int = 0, reference_every: int = 0, _handle=None, _owner=None):
         """scheme "standard": the uniform-grid central-moment LBM comparator
-        (uniform maps, spec["gi"] = 0, no MIE)."""
+        (uniform maps, spec["gi"] = 0, no MIE).  reference_every: steps between
+        refreshes of the per-row storage reference of 16-bit storage on
+        straight grids (0: the library default, < 0: never)."""
         self.spec = spec
         self.nx, self.ny = int(spec["nx"]), int(spec["ny"])
         self.storage = storage
@@ -122,7 +125,7 @@ class Lattice:
             self._h = _handle
         else:
             g, m, f, h = structs_from_spec(spec)
-            e = _exec(storage, stream, check_every, rounding, scheme, fixed_launch, plateau_checks)
+            e = _exec(storage, stream, check_every, rounding, scheme, fixed_launch, plateau_checks, reference_every)
             out = ctypes.c_void_p()
             check(lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f),
                                    ctypes.byref(h), ctypes.byref(e), ctypes.byref(out)))
@@ -234,8 +237,8 @@ class Batch:
     per time step, captured in CUDA graphs)."""
 
     def __init__(self, hbm_budget_bytes: int, max_lattices: int, storage: str = "fp32", stream=None,
-                 rounding: str = "stochastic"):
-        e = _exec(storage, stream, 100, rounding)
+                 rounding: str = "stochastic", reference_every: int = 0):
+        e = _exec(storage, stream, 100, rounding, reference_every=reference_every)
         out = ctypes.c_void_p()
         check(lib().goc_batch_create(int(hbm_budget_bytes), int(max_lattices), ctypes.byref(e), ctypes.byref(out)))
         self._h = out

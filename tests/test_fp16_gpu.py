@@ -3,10 +3,13 @@ FP64 oracle, with stochastic and with nearest rounding of the stored values.
 
 Round to nearest loses every per-step change smaller than half a unit in the
 last place of FP16 (11 significant bits), which stalls slowly evolving flows;
-stochastic rounding keeps those changes on average.  Tolerances are about
-twice the errors measured on a B300 (FP16 stochastic: Poiseuille 8.7e-4, cavity
-4.7e-4, Hartmann strip U 2.3e-3 / B1 4.2e-3 after 2000 steps; round to nearest:
-6.8e-3, 8.5e-4, 1.9e-2 / 6.6e-2).
+stochastic rounding keeps those changes on average.  The bound is the one
+stated for 16-bit storage, 2e-3 relative L2 (velocity, induced field), here
+during the run from rest: after 2000 steps for the Poiseuille channel and the
+cavity, after 20000 steps for the Hartmann strip, whose induced field is
+still small after 2000 (its Alfven crossing takes ~3e4 steps; relative to
+that small field the error measured 2.1e-3 there).  The steady states are
+checked in test_fp16_steady_gpu.py.
 """
 import numpy as np
 import pytest
@@ -32,14 +35,13 @@ HARTMANN_STRIP = gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "ta
                             {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0})
 
 
-@pytest.mark.parametrize("name,prob,tol_u,tol_b", [
-    ("poiseuille", gi.poiseuille_channel(), 2e-3, None),
-    ("cavity", CAVITY, 1.5e-3, None),
-    ("hartmann strip", HARTMANN_STRIP, 5e-3, 1e-2),
+@pytest.mark.parametrize("name,prob,steps,tol_u,tol_b", [
+    ("poiseuille", gi.poiseuille_channel(), 2000, 2e-3, None),
+    ("cavity", CAVITY, 2000, 2e-3, None),
+    ("hartmann strip", HARTMANN_STRIP, 20000, 2e-3, 2e-3),
 ])
-def test_fp16_stochastic_rounding_matches_the_oracle(gpu, name, prob, tol_u, tol_b):
+def test_fp16_stochastic_rounding_matches_the_oracle(gpu, name, prob, steps, tol_u, tol_b):
     spec = spec_of(prob)
-    steps = 2000
     o = oracle.Oracle(spec, threads=8)
     o.step(steps)
     fo = o.fields()
@@ -54,7 +56,8 @@ def test_fp16_stochastic_rounding_matches_the_oracle(gpu, name, prob, tol_u, tol
 
 def test_stochastic_rounding_beats_nearest_on_a_slow_flow(gpu):
     """The 32 x 64 Poiseuille channel after 2000 steps: the body force builds the profile by increments
-    far below FP16 resolution; nearest rounding stalls, stochastic does not."""
+    far below FP16 resolution; nearest rounding stalls, stochastic does not.  The per-row storage
+    reference is off here (it shrinks the stored values and with them the stall)."""
     p = gi.poiseuille_channel()
     spec = spec_of(p)
     o = oracle.Oracle(spec, threads=8)
@@ -62,7 +65,7 @@ def test_stochastic_rounding_beats_nearest_on_a_slow_flow(gpu):
     uo = o.fields()[1]
     err = {}
     for rd in ("nearest", "stochastic"):
-        L = goc.Lattice(spec, storage="fp16", rounding=rd)
+        L = goc.Lattice(spec, storage="fp16", rounding=rd, reference_every=-1)
         L.step(2000)
         err[rd] = relerr(L.moments()[1], uo)
         L.close()
