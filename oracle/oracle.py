@@ -149,12 +149,14 @@ class Oracle:
     """One lattice advanced by the FP64 oracle."""
 
     def __init__(self, spec: dict, threads: int | None = None,
-                 q3_printed: bool = False):
+                 q3_printed: bool = False, metric: Metric | None = None):
+        """metric: the node metric to use instead of the one built from the
+        spec's maps (a slab of a larger lattice, see oracle.slab)."""
         lib = _load()
         self.spec = spec
         nx, ny = int(spec["nx"]), int(spec["ny"])
         self.nx, self.ny = nx, ny
-        self.metric = m = build_metric(spec)
+        self.metric = m = build_metric(spec) if metric is None else metric
         self.par = par = derived_parameters(spec, m)
         walls = spec["walls"]
         wall = np.array([0 if walls.get(w) is None else 1 for w in _WALLS], dtype=np.int32)
