@@ -329,6 +329,117 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sharded(args):
+    """One lattice cut into slabs along xi2, one per rank and GPU
+    (goc_create_slab), with one ghost-row exchange per LB step over NCCL
+    (paper_2607_15362_b300.slab.Halo): the clustered cavity n x (n * ranks),
+    so that every GPU holds an n x n slab (weak scaling)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2607_15362_b300 as goc
+    from paper_2607_15362_b300.slab import Halo, rows_of
+
+    world, rank, local = setup_dist()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n = args.cavity_n
+    prob = gi.Problem("cavity", n, n * world, {"kind": "tanh2", "beta": 2.0}, {"kind": "tanh2", "beta": 2.0},
+                      {"Re": args.cavity_re, "u_lid": 0.05, "mach_matched": True},
+                      name=f"lid_cavity_{n}x{n * world}_in_{world}_slabs")
+    _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
+    spec = _spec(args, prob, cs2)
+    r0, r1 = rows_of(rank, world, prob.ny)
+    slab = goc.Slab(spec, r0, r1, storage=args.storage, stream=stream.cuda_stream)
+    halo = Halo(slab, rank, world, False, f"cuda:{local}")
+    halo.exchange(dist)
+    chunk = args.chunk
+    own_nodes = prob.nx * (r1 - r0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_step():
+        for _ in range(chunk):
+            slab.step(1)
+            halo.exchange(dist)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            one_step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(world)
+    ms_total = allmax(world, sum(a.elapsed_time(b) for a, b in ev))
+    ms_per_step = ms_total / args.steps
+    mlups = job_rate(world, own_nodes * chunk * args.steps, ms_total)
+    e2e = None
+    nloc = slab.nx * slab.ny
+    h2d = d2h = 3 * nloc * 8
+    if not args.no_e2e:
+        keep = [torch.full((slab.ny, slab.nx), v, dtype=torch.float64).pin_memory() for v in (1.0, 0, 0, 0, 0, 0)]
+        rho_in, u1_in, u2_in, rho_out, u1_out, u2_out = [t.numpy() for t in keep]
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        for _ in range(args.steps):
+            slab.init_fields(rho=rho_in, u1=u1_in, u2=u2_in)
+            halo.exchange(dist)
+            one_step()
+            slab.moments(out=[rho_out, u1_out, u2_out, None, None])
+        torch.cuda.synchronize()
+        e_wall = allmax(world, time.perf_counter() - e0)
+        e2e = world * own_nodes * chunk * args.steps / e_wall / 1e6
+        del keep
+    peaks, src = measured_peaks()
+    bpn = slab.bytes_per_node
+    launch_s = ms_per_step * 1e-3 / chunk
+    achieved = bpn * own_nodes / launch_s / 1e9
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    # launches per LB step: the step kernel, then per side with a neighbour the
+    # pack and unpack kernels (plus the storage-reference rows and tables of
+    # 16-bit storage)
+    sides = (1 if r0 > 0 else 0) + (1 if r1 < prob.ny else 0)
+    per_step = 1 + 2 * sides + (2 * sides + 1 if args.storage != "fp32" else 0)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "fp32" else f"f32 arithmetic, {args.storage} storage",
+            "data": "synthetic (lid-driven cavity from rest, seeded parameters)",
+            "config": {"workload": prob.name + f"_{args.storage}", "nodes": prob.nodes,
+                       "nodes_per_gpu": own_nodes, "lb_steps_per_bench_step": chunk,
+                       "map": "tanh beta=2 on both axes", "Re": args.cavity_re,
+                       "u_lid": round(spec["walls"]["N"]["u"], 6), "storage": args.storage,
+                       "parallelism": f"slabs along xi2 x{world}, one ghost-row exchange per LB step (NCCL)",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "e2e": ({"value": round(e2e, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+                    if e2e is not None else None),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+                         "bytes_per_node": bpn, "kernel": "goc::step_kernel<float,0,0,0> (per slab)",
+                         "launch_us": round(launch_s * 1e6, 3)},
+            "cpu_baseline": None,
+            "gpu_launches": args.steps * chunk * per_step,
+            "clocks": clk.summary(),
+            "wall_s": round(wall, 3),
+        }
+        print(json.dumps(line))
+    slab.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_batch(args):
     """64 lattices (seed 7) advanced together by the persistent batched
     kernel vs one lattice at a time with its own launches; FP32 and 16-bit."""
@@ -830,6 +941,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several ranks: one independent lattice per rank instead of one lattice in slabs")
+    ap.add_argument("--shard", action="store_true",
+                    help="run the slab path (one lattice in slabs along xi2) even on one rank")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -845,6 +960,9 @@ def main():
         run_oracle_timing(args)
     elif args.workload == "vortex":
         run_vortex(args)
+    elif args.shard or (int(os.environ.get("WORLD_SIZE", "1")) > 1 and not args.replicas and args.grid == "tanh"
+                        and not args.mie and args.scheme == "goc"):
+        run_sharded(args)   # one lattice over all ranks, slabs along xi2
     else:
         run_ours(args)
 

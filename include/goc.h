@@ -360,6 +360,58 @@ goc_status goc_batch_lattice(goc_batch *b, int slot, goc_lattice **lat);
 /* Bytes the batch currently holds on the device and its budget. */
 goc_status goc_batch_usage(const goc_batch *b, long long *used, long long *budget, int *count);
 
+/* ---- one lattice over several GPUs: slabs along xi2 -------------------- */
+/* The lattice is cut into bands of xi2 rows ("slabs", one per GPU), as the
+ * lattice Boltzmann update allows: a node's new populations depend on its
+ * neighbours one row away, and through the second-order normal derivatives of
+ * the fields (Appendix E) on rows two away, so two ghost rows per internal cut
+ * suffice.  A slab is a lattice of its own rows plus two ghost rows on each
+ * side that has a neighbouring slab (both sides on a periodic xi2 axis); it
+ * treats its cuts as walls, which makes only the ghost rows wrong, and after
+ * every step the ghost rows are overwritten with the two rows of the
+ * neighbouring slab nearest the cut (populations, stored force, MIE
+ * populations, and the per-row storage reference of 16-bit storage).  The
+ * owned rows are then bitwise those of the single lattice: the metric is the
+ * global one (q, hence c_s^2, the minimum over the whole lattice, Eq.
+ * GOC-LBE_CFL) and the random streams of stochastic rounding follow global
+ * node indices.  Per-axis maps (straight grids) only. */
+
+/* A slab owning the global rows [row_begin, row_end) of the lattice `grid`
+ * (the whole lattice's grid and map; its nx and W/E sides are the slab's).
+ * Needs row_end - row_begin >= 2, and on a periodic xi2 axis at least 2 rows
+ * left to the other slabs.  The slab's local rows are: ghost_lo ghost rows,
+ * the owned rows, ghost_hi ghost rows (goc_slab_info); goc_moments,
+ * goc_moments_device, goc_get_state and goc_init_fields work on all local
+ * rows, goc_diagnostics' mass on the owned rows (add the slabs' shares).
+ * goc_step takes at most one step per call on a slab, goc_run_until is
+ * GOC_EUNSUPPORTED (the residual is a global sum).  Protocol, per slab: after
+ * creation, after goc_init_fields / goc_set_state and after every
+ * goc_step(slab, 1): goc_slab_pack, send send_lo to the slab below and
+ * send_hi to the slab above, receive theirs, goc_slab_unpack (recv_lo from
+ * the slab below, recv_hi from the one above). */
+goc_status goc_create_slab(const goc_grid *grid, const goc_map *map, const goc_flow *flow,
+                           const goc_mhd *mhd, const goc_exec *exec, int row_begin, int row_end,
+                           goc_lattice **out);
+
+/* Global rows [*row_begin, *row_end) owned and ghost rows below / above (0, ny,
+ * 0, 0 for a whole lattice).  Any pointer may be NULL. */
+goc_status goc_slab_info(const goc_lattice *lat, int *row_begin, int *row_end, int *ghost_lo,
+                         int *ghost_hi);
+
+/* Bytes of one side's ghost-row message (0 for a whole lattice): every plane
+ * of the state, two rows of nx values each, in the storage type, then (16-bit
+ * storage) the FP64 per-row storage reference of those rows. */
+long long goc_slab_halo_bytes(const goc_lattice *lat);
+
+/* Copy the two owned rows nearest each cut into caller-owned DEVICE buffers
+ * of goc_slab_halo_bytes bytes (NULL: that side is skipped; ignored on a side
+ * without a neighbour).  Enqueued on the lattice stream; no sync. */
+goc_status goc_slab_pack(goc_lattice *lat, void *send_lo, void *send_hi);
+
+/* Overwrite the ghost rows from the neighbours' messages (DEVICE buffers as
+ * for goc_slab_pack; NULL skips a side).  Enqueued on the lattice stream. */
+goc_status goc_slab_unpack(goc_lattice *lat, const void *recv_lo, const void *recv_hi);
+
 /* ---- errors ------------------------------------------------------------ */
 const char *goc_last_error(void);
 

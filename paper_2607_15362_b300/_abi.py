@@ -74,6 +74,12 @@ SIGNATURES = {
     "goc_check_guards": (c_int, [c_void_p, P(c_ll)]),
     "goc_launch_config": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
     "goc_set_launch_config": (c_int, [c_void_p, c_int, c_int]),
+    "goc_create_slab": (c_int, [P(GocGrid), P(GocMap), P(GocFlow), P(GocMhd), P(GocExec), c_int, c_int,
+                                P(c_void_p)]),
+    "goc_slab_info": (c_int, [c_void_p] + [P(c_int)] * 4),
+    "goc_slab_halo_bytes": (c_ll, [c_void_p]),
+    "goc_slab_pack": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "goc_slab_unpack": (c_int, [c_void_p, c_void_p, c_void_p]),
     "goc_last_error": (ctypes.c_char_p, []),
 }
 

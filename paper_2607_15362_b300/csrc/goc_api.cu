@@ -80,7 +80,8 @@ goc_status fail(goc_status st, const char *fmt, ...) {
 size_t elem_size(int storage) { return storage == GOC_FP32 ? 4 : 2; }
 
 constexpr int kGraphSteps = 64;
-constexpr int kRefEvery = 1024;   // default steps between refreshes of the per-row storage reference   // steps per captured graph (even: one buffer cycle per 2)
+constexpr int kRefEvery = 1024;
+constexpr int kSlabGhost = 2;     // ghost rows per internal cut of a slab   // default steps between refreshes of the per-row storage reference   // steps per captured graph (even: one buffer cycle per 2)
 
 }  // namespace
 
@@ -137,6 +138,10 @@ struct goc_lattice {
     float *reft = nullptr;                       // FP32 tables u1r [ny], brow [2][ny], bpull [4][ny]
     int ref_every = 0;                           // steps between refreshes (0: the reference stays as created)
     long long ref_next = 0;                      // step count at which the next refresh is due
+    // slab of a larger lattice (goc_create_slab): global rows [slab_r0, slab_r1)
+    // owned, slab_glo / slab_ghi ghost rows below / above them
+    bool slab = false;
+    int slab_r0 = 0, slab_r1 = 0, slab_glo = 0, slab_ghi = 0;
 };
 
 namespace {
@@ -503,6 +508,48 @@ MapParams map_params(const goc_grid *grid, const goc_map *map, int axis) {
     return m;
 }
 
+// Rows of a global xi2 axis metric g = [2][ng + 2] (h, theta at the nodes,
+// then the walls at xi = 0 and ng) for a slab: local row k is global row
+// first + k (wrapped on a periodic axis); the wall entries are the global
+// walls where the slab reaches them, else the slab's edge rows (an internal
+// cut, which only ghost rows see).
+__global__ void slice_axis_kernel(const double *g, int ng, int first, int periodic, int wall_lo, int wall_hi,
+                                  double *out, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n + 2) return;
+    int src;
+    if (k < n) src = periodic ? ((first + k) % ng + ng) % ng : first + k;
+    else if (k == n) src = wall_lo ? ng : first;
+    else src = wall_hi ? ng + 1 : first + n - 1;
+    out[k] = g[src];
+    out[n + 2 + k] = g[ng + 2 + src];
+}
+
+// Two rows [row, row + 2) of every plane of the current buffers (populations,
+// stored force, MIE populations) to or from a message buf[plane][2][nx].
+template <class S>
+__global__ void halo_kernel(const StepParams p, S *buf, int row, int unpack) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y, k = blockIdx.z;
+    if (i >= p.nx) return;
+    S *base = k < 9 ? static_cast<S *>(const_cast<void *>(p.fin)) + k * p.plane
+                    : (k < 11 ? static_cast<S *>(const_cast<void *>(p.Fin)) + (k - 9) * p.plane
+                              : static_cast<S *>(const_cast<void *>(p.gin)) + (k - 11) * p.plane);
+    S *cell = base + (long long)(row + r) * p.pitch + i;
+    S *msg = buf + ((long long)k * 2 + r) * p.nx + i;
+    if (unpack) *cell = *msg;
+    else *msg = *cell;
+}
+
+// The FP64 per-row storage reference rows [3][ny] of rows [row, row + 2) to or
+// from msg[3][2].
+__global__ void halo_ref_kernel(double *ref, int ny, double *msg, int row, int unpack) {
+    const int t = threadIdx.x;
+    if (t >= 6) return;
+    const int c = t / 2, r = t % 2;
+    if (unpack) ref[c * ny + row + r] = msg[t];
+    else msg[t] = ref[c * ny + row + r];
+}
+
 // FP64 metric of both axes on the device: d1, d2 = [2][n+2] (h, theta); q.
 // Annulus: d1 = [4][n1+2] (h1, theta11, h2, theta21 over xi1) and q is the
 // smallest of h1 and h2 over the nodes.
@@ -667,7 +714,7 @@ goc_status ref_refresh(goc_lattice *L) {
     const bool m = L->mhd.enabled;
 #define GOC_REF_LAUNCH(S, MHD)                                                                           \
     do {                                                                                                 \
-        ref_rows_kernel<S, MHD><<<L->ny, 256, 0, L->stream>>>(p, next);                                   \
+        ref_rows_kernel<S, MHD><<<L->ny, 256, 0, L->stream>>>(p, next, pre);                              \
         ref_apply_kernel<S, MHD><<<ag, 128, 0, L->stream>>>(p, h1, t1, h2, t2, next, rho0, csm2, pre, salt); \
     } while (0)
     if (L->storage == GOC_FP16_DEV) {
@@ -873,12 +920,28 @@ goc_status goc_metric_info(const goc_grid *grid, const goc_map *map, double *q, 
     return GOC_OK;
 }
 
+// A slab of a global lattice: its global xi2 extent and the rows it covers.
+struct SlabPlan {
+    const goc_grid *global;
+    int r0, r1, glo, ghi;
+};
+
+static goc_status create_impl(const goc_grid *grid, const goc_map *map, const goc_flow *flow, const goc_mhd *mhd,
+                              const goc_exec *exec, const SlabPlan *slab, goc_lattice **out);
+
 goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *flow,
                       const goc_mhd *mhd, const goc_exec *exec, goc_lattice **out) {
+    return create_impl(grid, map, flow, mhd, exec, nullptr, out);
+}
+
+static goc_status create_impl(const goc_grid *grid, const goc_map *map, const goc_flow *flow, const goc_mhd *mhd,
+                              const goc_exec *exec, const SlabPlan *slab, goc_lattice **out) {
     TraceRange trace_("goc_create");
     if (!out) return fail(GOC_EINVAL, "out is NULL");
     *out = nullptr;
-    goc_status st = validate(grid, map);
+    // (a slab's whole lattice was validated by goc_create_slab; its own xi2
+    // sides are walls whatever the global axis is)
+    goc_status st = slab ? GOC_OK : validate(grid, map);
     if (st != GOC_OK) return st;
     if (!flow) return fail(GOC_EINVAL, "flow is required");
     {   // every real parameter finite (a NaN passes the range checks below unnoticed)
@@ -978,7 +1041,32 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     const bool table = map->kind[0] == GOC_MAP_TABLE;
     goc_map uni_map = *map;
     if (table) uni_map.kind[0] = uni_map.kind[1] = GOC_MAP_UNIFORM;
-    TRY(compute_metric(grid, table ? &uni_map : map, L->stream, L->m1, L->m2, L->red));
+    if (slab) {   // the global xi2 metric and q, then this slab's rows of it
+        const int ng = slab->global->ny;
+        double *m2g = nullptr;
+        if (cudaMalloc(&m2g, 2 * (size_t)(ng + 2) * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            free_lattice(L);
+            return fail(GOC_ENOMEM, "slab metric staging failed");
+        }
+        goc_status ms = compute_metric(slab->global, map, L->stream, L->m1, m2g, L->red);
+        if (ms == GOC_OK) {
+            slice_axis_kernel<<<(L->ny + 2 + 127) / 128, 128, 0, L->stream>>>(
+                m2g, ng, slab->r0 - slab->glo, slab->global->bc[2] == GOC_BC_PERIODIC, slab->glo == 0,
+                slab->ghi == 0, L->m2, L->ny);
+            if (cudaGetLastError() != cudaSuccess) ms = fail(GOC_ECUDA, "slab metric kernel failed");
+        }
+        cudaStreamSynchronize(L->stream);
+        cudaFree(m2g);
+        TRY(ms);
+        L->slab = true;
+        L->slab_r0 = slab->r0;
+        L->slab_r1 = slab->r1;
+        L->slab_glo = slab->glo;
+        L->slab_ghi = slab->ghi;
+    } else {
+        TRY(compute_metric(grid, table ? &uni_map : map, L->stream, L->m1, L->m2, L->red));
+    }
     double hw1[2], hw2[2], qh, hwt1[2] = {1.0, 1.0};
     {
         cudaError_t e = cudaMemcpyAsync(&qh, L->red, sizeof(double), cudaMemcpyDeviceToHost, L->stream);
@@ -1119,6 +1207,9 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
         for (int k = 0; k < 9; k++) p.om[k] = (float)(1.0 / L->tau);
     p.fext1 = (float)L->flow.fext[0];
     p.fext2 = (float)L->flow.fext[1];
+    p.seed_row0 = L->slab ? L->slab_r0 - L->slab_glo : 0;
+    p.own0 = L->slab ? L->slab_glo : 0;
+    p.own1 = L->slab ? L->ny - L->slab_ghi : L->ny;
     p.gi = L->flow.gi_correction ? 1.f : 0.f;
     p.constF = L->scheme == 1 ? 1 : 0;
     p.zc = (float)(L->zeta / L->cs2);
@@ -1140,8 +1231,10 @@ goc_status goc_create(const goc_grid *grid, const goc_map *map, const goc_flow *
     // storage scales (1 for FP32; for 16-bit a per-lattice velocity scale)
     p.sf = p.isf = p.sF = p.isF = p.sg = p.isg = 1.f;
     if (L->storage != GOC_FP32) {
-        double uref = 1e-3 * std::sqrt(L->cs2);
-        for (int s = 0; s < 4; s++) uref = std::max(uref, std::fabs((double)p.uw[s]));
+        double uref = 1e-3 * std::sqrt(L->cs2);   // (a slab takes the whole lattice's walls: one scale for all slabs)
+        for (int s = 0; s < 4; s++)
+            uref = std::max(uref, std::fabs(slab ? (slab->global->bc[s] == GOC_BC_WALL ? (double)(float)slab->global->wall_u[s] : 0.0)
+                                                 : (double)p.uw[s]));
         double hmax = 1.0;   // scale so that |deviation| / s stays well inside the 16-bit range
         double sf = L->flow.rho0 * uref * hmax / 256.0;
         p.sf = (float)sf;
@@ -1218,6 +1311,9 @@ goc_status goc_step(goc_lattice *L, long long nsteps) {
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
     if (nsteps < 0) return fail(GOC_EINVAL, "nsteps must be >= 0");
     if (L->in_batch) return fail(GOC_EINVAL, "this lattice belongs to a batch: step it with goc_batch_step");
+    if (L->slab && nsteps > 1)
+        return fail(GOC_EINVAL, "a slab exchanges its ghost rows after every step: goc_step(slab, 1), then "
+                                "goc_slab_pack / goc_slab_unpack");
     // the status word as of the end of the previous call, if its copy has landed (no wait)
     if (L->flag_ev && cudaEventQuery(L->flag_ev) == cudaSuccess && *L->hflag) return flag_status(L, *L->hflag);
     goc_status st = enqueue_steps(L, nsteps);
@@ -1396,6 +1492,7 @@ goc_status goc_diagnostics(goc_lattice *L, double *mass, double *residual_u, dou
 goc_status goc_run_until(goc_lattice *L, double tol, long long max_steps, long long *done, double *residual) {
     TraceRange trace_("goc_run_until");
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (L->slab) return fail(GOC_EUNSUPPORTED, "goc_run_until needs the whole lattice: a slab's residual is one share of it");
     if (max_steps < 0) return fail(GOC_EINVAL, "max_steps must be >= 0");
     if (!L->uout[0]) {
         for (int b = 0; b < 2; b++) {
@@ -1503,6 +1600,101 @@ goc_status goc_set_state(goc_lattice *L, const void *buf, size_t bytes) {
     L->fresh = hdr[7] != 0;
     if (L->ref_every > 0) L->ref_next = (L->steps / L->ref_every + 1) * L->ref_every;
     return GOC_OK;
+}
+
+
+// ---- slab decomposition of one lattice along xi2 --------------------------
+
+goc_status goc_create_slab(const goc_grid *grid, const goc_map *map, const goc_flow *flow, const goc_mhd *mhd,
+                           const goc_exec *exec, int row_begin, int row_end, goc_lattice **out) {
+    if (!out) return fail(GOC_EINVAL, "out is NULL");
+    *out = nullptr;
+    goc_status st = validate(grid, map);
+    if (st != GOC_OK) return st;
+    if (map->kind[0] == GOC_MAP_ANNULUS || map->kind[0] == GOC_MAP_TABLE)
+        return fail(GOC_EUNSUPPORTED, "slabs take per-axis maps (straight grids)");
+    const bool per = grid->bc[2] == GOC_BC_PERIODIC;
+    if (!(0 <= row_begin && row_begin + kSlabGhost <= row_end && row_end <= grid->ny))
+        return fail(GOC_EINVAL, "slab rows [%d, %d) of %d: need 0 <= begin, end - begin >= %d, end <= ny",
+                    row_begin, row_end, grid->ny, kSlabGhost);
+    if (per && row_end - row_begin > grid->ny - kSlabGhost)
+        return fail(GOC_EINVAL, "on a periodic xi2 axis a slab leaves at least %d rows to its neighbours", kSlabGhost);
+    SlabPlan plan;
+    plan.global = grid;
+    plan.r0 = row_begin;
+    plan.r1 = row_end;
+    plan.glo = (per || row_begin > 0) ? kSlabGhost : 0;
+    plan.ghi = (per || row_end < grid->ny) ? kSlabGhost : 0;
+    goc_grid local = *grid;
+    local.ny = (row_end - row_begin) + plan.glo + plan.ghi;
+    for (int s = 2; s < 4; s++) {   // an internal cut is a wall of the local lattice (only ghost rows see it)
+        const bool cut = s == 2 ? plan.glo > 0 : plan.ghi > 0;
+        if (!cut) continue;
+        local.bc[s] = GOC_BC_WALL;
+        local.wall_u[s] = 0.0;
+        local.wall_b[s][0] = local.wall_b[s][1] = 0.0;
+    }
+    if (per) local.bc[2] = local.bc[3] = GOC_BC_WALL;
+    return create_impl(&local, map, flow, mhd, exec, &plan, out);
+}
+
+goc_status goc_slab_info(const goc_lattice *L, int *row_begin, int *row_end, int *ghost_lo, int *ghost_hi) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (row_begin) *row_begin = L->slab ? L->slab_r0 : 0;
+    if (row_end) *row_end = L->slab ? L->slab_r1 : L->ny;
+    if (ghost_lo) *ghost_lo = L->slab_glo;
+    if (ghost_hi) *ghost_hi = L->slab_ghi;
+    return GOC_OK;
+}
+
+static int slab_planes(const goc_lattice *L) { return 11 + (L->mhd.enabled ? 10 : 0); }
+static size_t slab_plane_bytes(const goc_lattice *L) {
+    return ((size_t)slab_planes(L) * kSlabGhost * L->nx * elem_size(L->storage) + 7) / 8 * 8;
+}
+
+long long goc_slab_halo_bytes(const goc_lattice *L) {
+    if (!L || !L->slab) return 0;
+    return (long long)(slab_plane_bytes(L) + (L->ref64 ? 3 * kSlabGhost * sizeof(double) : 0));
+}
+
+// rows [row, row + 2) of the current state to (unpack = 0) or from (1) msg
+static goc_status slab_move(goc_lattice *L, void *msg, int row, int unpack) {
+    StepParams p = params_for(L, L->cur, nullptr);
+    const dim3 grid((L->nx + 127) / 128, kSlabGhost, slab_planes(L));
+    switch (L->storage) {
+        case GOC_FP16_DEV: halo_kernel<__half><<<grid, 128, 0, L->stream>>>(p, static_cast<__half *>(msg), row, unpack); break;
+        case GOC_BF16_DEV:
+            halo_kernel<__nv_bfloat16><<<grid, 128, 0, L->stream>>>(p, static_cast<__nv_bfloat16 *>(msg), row, unpack);
+            break;
+        default: halo_kernel<float><<<grid, 128, 0, L->stream>>>(p, static_cast<float *>(msg), row, unpack); break;
+    }
+    CU(cudaGetLastError());
+    if (L->ref64) {
+        halo_ref_kernel<<<1, 32, 0, L->stream>>>(L->ref64, L->ny, reinterpret_cast<double *>(static_cast<char *>(msg) +
+                                                                                             slab_plane_bytes(L)),
+                                                 row, unpack);
+        CU(cudaGetLastError());
+    }
+    return GOC_OK;
+}
+
+goc_status goc_slab_pack(goc_lattice *L, void *send_lo, void *send_hi) {
+    if (!L || !L->slab) return fail(GOC_EINVAL, "not a slab");
+    const int own0 = L->slab_glo, own1 = L->ny - L->slab_ghi;
+    goc_status st = GOC_OK;
+    if (send_lo && L->slab_glo) st = slab_move(L, send_lo, own0, 0);
+    if (st == GOC_OK && send_hi && L->slab_ghi) st = slab_move(L, send_hi, own1 - kSlabGhost, 0);
+    return st;
+}
+
+goc_status goc_slab_unpack(goc_lattice *L, const void *recv_lo, const void *recv_hi) {
+    if (!L || !L->slab) return fail(GOC_EINVAL, "not a slab");
+    const int own1 = L->ny - L->slab_ghi;
+    goc_status st = GOC_OK;
+    if (recv_lo && L->slab_glo) st = slab_move(L, const_cast<void *>(recv_lo), 0, 1);
+    if (st == GOC_OK && recv_hi && L->slab_ghi) st = slab_move(L, const_cast<void *>(recv_hi), own1, 1);
+    if (st == GOC_OK && L->ref64) st = ref_tables(L, L->ref64);   // the ghost rows' storage reference changed
+    return st;
 }
 
 }  // extern "C"
@@ -1979,13 +2171,13 @@ namespace {
 template <class S>
 __global__ void mass_partial_kernel(const StepParams p, double *partial) {
     __shared__ double red[256];
-    const long long N = (long long)p.nx * p.ny;
+    const long long N = (long long)p.nx * (p.own1 - p.own0);   // the owned rows
     const S *f = static_cast<const S *>(p.fin);
     double acc = 0.0;
     for (int k = 0; k < GOC_NOALLOC_NODES_PER_BLOCK / 256; k++) {
         const long long n = (long long)blockIdx.x * GOC_NOALLOC_NODES_PER_BLOCK + k * 256 + threadIdx.x;
         if (n >= N) break;
-        const int j = (int)(n / p.nx), i = (int)(n - (long long)j * p.nx);
+        const int j = p.own0 + (int)(n / p.nx), i = (int)(n - (long long)(j - p.own0) * p.nx);
         const long long idx = (long long)j * p.pitch + i;
         double s = 0.0;
         for (int a = 0; a < 9; a++) s += (double)Store<S>::ld(f + a * p.plane + idx) * p.sf;
@@ -2062,7 +2254,7 @@ double *noalloc_scratch(goc_status *st) {
 
 extern "C" goc_status goc_mass_noalloc(goc_lattice *L, double *mass) {
     if (!L || !mass) return fail(GOC_EINVAL, "goc_mass_noalloc: lattice and mass are required");
-    const long long N = (long long)L->nx * L->ny;
+    const long long N = (long long)L->nx * (L->sp.own1 - L->sp.own0);   // owned rows
     const long long blocks = (N + GOC_NOALLOC_NODES_PER_BLOCK - 1) / GOC_NOALLOC_NODES_PER_BLOCK;
     if (blocks > GOC_NOALLOC_MAX_BLOCKS)
         return fail(GOC_EINVAL, "goc_mass_noalloc: the lattice has %lld nodes; at most %lld are supported",

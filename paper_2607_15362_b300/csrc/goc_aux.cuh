@@ -420,27 +420,40 @@ __global__ void ref_tables_kernel(const double *h2, const double *t2, int ny, in
 
 // Row means of U1 and B of the current state, one block of 256 threads per
 // row, summed in a fixed order (the refresh is reproducible): out[3][ny].
+// Each node's values come from its own stored populations and force only (no
+// pulls), so a slab's rows next to a cut need no fresh ghost rows: after a
+// step the stored post-collision populations hold the momentum h2 rho U1 +
+// F1/2 (exactly with omega1 = 1; the reference only has to be close to the
+// flow), i.e. U1 = (sum d e1 + 2 u1r - (F1 - F1_rest)/2) / (rho h2), and the
+// MIE zeroth moment h1 h2 (B - Bref) = sum g (Y = 0 on straight grids); the
+// initial pre-collision state (pre = 1) gives U1 by Eq.
+// GOChydrodynamicfields, with + (F1 - F1_rest)/2.
 template <class S, bool MHD>
-__global__ void ref_rows_kernel(const StepParams p, double *out) {
+__global__ void ref_rows_kernel(const StepParams p, double *out, int pre) {
     static_assert(Store<S>::scaled, "the per-row reference belongs to 16-bit storage");
     __shared__ double red[3][256];
     const int j = blockIdx.x, t = threadIdx.x;
     const SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                            p.plane, p.pitch, p.sf, p.sF, p.sg};
     double acc[3] = {0.0, 0.0, 0.0};
+    const float fs = pre ? 0.5f : -0.5f;
     for (int i = t; i < p.nx; i += 256) {
-        float h1, h2, ih1, ih2, d[9], drho, U1, U2;
+        float h1, h2, ih1, ih2, d[9];
         node_metric<0>(p, i, j, h1, h2, ih1, ih2);
-        const float ur1 = GOC_U1R(p, j);
-        pull_node<true, 0, true>(p, src, i, j, h1, h2, d, ur1);
-        fields_from<true>(p, d, src.Fv(0, i, j), src.Fv(1, i, j), ih1, ih2, drho, U1, U2, ur1);
+#pragma unroll
+        for (int a = 0; a < 9; a++) d[a] = src.fv(a, i, j);
+        float k00 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 9; a++) k00 += d[a];
+        const float k10 = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+        const float rho = p.rho0 + k00 * (ih1 * ih2);
+        const float U1 = (k10 + fmaf(fs, src.Fv(0, i, j), 2.f * GOC_U1R(p, j))) / rho * ih2;
         acc[0] += (double)U1;
         if constexpr (MHD) {
             for (int c = 0; c < 2; c++) {
-                float gd[5];
-                pull_mie<true, 0, true>(p, src, i, j, h1, h2, c, gd);
-                const float sum = (gd[0] + gd[1] + gd[2] + gd[3] + gd[4]) / (h1 * h2);
-                acc[1 + c] += (double)bref<true>(p, c, j) + (double)sum;
+                float sum = 0.f;
+                for (int a = 0; a < 5; a++) sum += src.gv(c * 5 + a, i, j);
+                acc[1 + c] += (double)GOC_BROW(p, c, j) + (double)(sum * (ih1 * ih2));
             }
         }
     }
@@ -471,7 +484,7 @@ __global__ void ref_apply_kernel(const StepParams p, const double *h1d, const do
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= p.nx || j >= p.ny) return;
     const long long idx = (long long)j * p.pitch + i;
-    uint32_t rng = node_seed((uint32_t)idx, salt);
+    uint32_t rng = node_seed((uint32_t)(idx + (long long)p.seed_row0 * p.pitch), salt);
     const bool sr = p.sr != 0;
     S *f = static_cast<S *>(const_cast<void *>(p.fin));
     const double du = (double)GOC_U1R(p, j) - (double)ref_u1r(h2d, refn, rho0, j);
@@ -537,11 +550,11 @@ __device__ __forceinline__ double node_h1h2(const StepParams &p, int i, int j) {
 template <class S>
 __global__ void mass_kernel(const StepParams p, double *out) {
     double acc[1] = {0.0};
-    const long long N = (long long)p.nx * p.ny;
+    const long long N = (long long)p.nx * (p.own1 - p.own0);   // the owned rows
     const S *f = static_cast<const S *>(p.fin);
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(n / p.nx), i = (int)(n - (long long)j * p.nx);
+        const int j = p.own0 + (int)(n / p.nx), i = (int)(n - (long long)(j - p.own0) * p.nx);
         const long long idx = (long long)j * p.pitch + i;
         double s = 0.0;
         for (int a = 0; a < 9; a++) s += (double)Store<S>::ld(f + a * p.plane + idx) * p.sf;

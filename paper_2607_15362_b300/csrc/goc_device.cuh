@@ -66,6 +66,12 @@ struct StepParams {
     int per_x, per_y;          // periodic axes
     int curv;                  // 1: curvilinear column metric (h1, h2, theta11, theta21 functions of xi1);
                                // 2: metric given node by node (gm)
+    // slab of a larger lattice (goc_create_slab): local rows [own0, own1) are
+    // the lattice's own (reductions), seed_row0 is the global row of local row
+    // 0 (random streams of stochastic rounding follow global node indices);
+    // 0, ny, 0 for a whole lattice.  (Placed in alignment gaps: the batch
+    // kernel carries 32 of these blocks in its 32 KB parameter space.)
+    int own0;
     // node-by-node metric (curv = 2): FP32 planes [10][plane] h1, h2, theta11,
     // theta12, theta21, theta22 and the pull corrections of links 1..4 (into
     // the node), then [8][max(nx, ny)] the wall-normal metric along W, E, S, N
@@ -73,6 +79,7 @@ struct StepParams {
     const float *gm;
     int nopull;                // 1: the input buffer holds pre-collision populations (the
                                // initial state f^0 of Appendix C.1): read them in place
+    int seed_row0;
     const void *fin;           // [9][plane] stored post-collision deviations (input)
     void *fout;                // [9][plane] (output)
     const void *Fin;           // [2][plane] stored effective force of the previous step
@@ -127,6 +134,7 @@ struct StepParams {
     const float *reft;
     // TMA descriptors of the input buffers (3D: [planes][ny][nx])
     int use_tma;
+    int own1;                  // end of the owned rows (see own0)
     CUtensorMap tm_f;          // box [9][TY + 2 HYS][TX + 2 HXS]
     CUtensorMap tm_F;          // box [2][TY + 2 HYS][TX + 2 HXS]
     CUtensorMap tm_g;          // box [10][TY + 2][TX + 2 HXS]

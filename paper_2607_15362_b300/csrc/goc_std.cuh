@@ -153,7 +153,7 @@ __device__ __forceinline__ void std_node(const StepParams &p, int i, int j) {
 
     const long long idx = (long long)j * p.pitch + i;
     const bool sr = Store<S>::scaled && p.sr;
-    uint32_t rng = sr ? node_seed((uint32_t)idx, *p.seed_rd) : 0u;
+    uint32_t rng = sr ? node_seed((uint32_t)(idx + (long long)p.seed_row0 * p.pitch), *p.seed_rd) : 0u;
     S *fout = static_cast<S *>(p.fout);
 #pragma unroll
     for (int a = 0; a < 9; a++) put<S>(fout + a * p.plane + idx, scl<S>(o[a], p.isf), sr, rng);

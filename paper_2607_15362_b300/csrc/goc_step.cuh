@@ -489,7 +489,8 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     {
         const uint32_t step = sr ? *p.seed_rd : 0u;
 #pragma unroll
-        for (int r = 0; r < R; r++) rng[r] = sr ? node_seed((uint32_t)idx[r], step) : 0u;
+        for (int r = 0; r < R; r++)
+            rng[r] = sr ? node_seed((uint32_t)(idx[r] + (long long)p.seed_row0 * p.pitch), step) : 0u;
     }
     V FL1 = bc<V>(0.f), FL2 = bc<V>(0.f), B1 = bc<V>(0.f), B2 = bc<V>(0.f);
     // theta12, theta21 of curvilinear grids (the column metric has theta12 = 0)

@@ -232,6 +232,57 @@ class Lattice:
         check(lib().goc_set_state(self._h, buf, len(data)))
 
 
+def _vp(ptr):
+    return ctypes.c_void_p(int(ptr)) if ptr else None
+
+
+class Slab(Lattice):
+    """The slab of the global rows [row_begin, row_end) of the lattice
+    `spec` (goc_create_slab): a Lattice over its local rows -- ghost rows,
+    owned rows, ghost rows -- whose ghost rows are refreshed from the
+    neighbouring slabs after creation and after every step (pack, exchange,
+    unpack; see paper_2607_15362_b300.slab)."""
+
+    def __init__(self, spec: dict, row_begin: int, row_end: int, storage: str = "fp32", stream=None,
+                 rounding: str = "stochastic", scheme: str = "goc", reference_every: int = 0):
+        g, m, f, h = structs_from_spec(spec)
+        e = _exec(storage, stream, 100, rounding, scheme, True, 0, reference_every)
+        out = ctypes.c_void_p()
+        check(lib().goc_create_slab(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f), ctypes.byref(h),
+                                    ctypes.byref(e), int(row_begin), int(row_end), ctypes.byref(out)))
+        r0, r1, lo, hi = (ctypes.c_int() for _ in range(4))
+        check(lib().goc_slab_info(out, ctypes.byref(r0), ctypes.byref(r1), ctypes.byref(lo), ctypes.byref(hi)))
+        self.row_begin, self.row_end, self.ghost_lo, self.ghost_hi = r0.value, r1.value, lo.value, hi.value
+        self.global_ny = int(spec["ny"])
+        local = dict(spec, ny=self.row_end - self.row_begin + self.ghost_lo + self.ghost_hi)
+        local.pop("init", None)
+        super().__init__(local, storage=storage, _handle=out)
+        self.global_spec = spec
+        # global row of every local row (ghost rows of a periodic axis wrap)
+        self.rows = (np.arange(self.ny) + self.row_begin - self.ghost_lo) % self.global_ny
+        self.halo_bytes = int(lib().goc_slab_halo_bytes(out))
+        init = spec.get("init")
+        if init:
+            self.init_fields(**{k: np.asarray(v)[self.rows] for k, v in init.items() if v is not None})
+
+    @property
+    def own(self) -> slice:
+        """Local rows owned by this slab."""
+        return slice(self.ghost_lo, self.ghost_lo + self.row_end - self.row_begin)
+
+    def owned_moments(self, cartesian: bool = False):
+        """(rho, U1, U2, B1, B2) of the owned rows."""
+        return tuple(a[self.own] for a in self.moments(cartesian))
+
+    def pack(self, send_lo, send_hi):
+        """Rows nearest each cut into device buffers (addresses; None skips)."""
+        check(lib().goc_slab_pack(self._h, _vp(send_lo), _vp(send_hi)))
+
+    def unpack(self, recv_lo, recv_hi):
+        """Ghost rows from the neighbours' messages (device addresses; None skips)."""
+        check(lib().goc_slab_unpack(self._h, _vp(recv_lo), _vp(recv_hi)))
+
+
 class Batch:
     """Many independent lattices advanced together (one persistent launch
     per time step, captured in CUDA graphs)."""
