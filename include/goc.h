@@ -223,6 +223,16 @@ goc_status goc_launch_config(const goc_lattice *lat, int *dynamic_tiles, int *pd
  * autotuner off for this lattice.  Takes effect from the next step. */
 goc_status goc_set_launch_config(goc_lattice *lat, int dynamic_tiles, int pdl);
 
+/* Grid of the step kernel: *balanced = 0 launches as many persistent blocks
+ * as fit on the device (or one per tile), 1 the fewest blocks that take the
+ * same number of rounds of tiles, so every block gets an equal share (512
+ * blocks for the 1024 tiles of a 512^2 lattice instead of 592 with 1.73
+ * rounds).  Chosen by the autotuner with the other launch settings; the set
+ * call fixes it (and turns the autotuner off).  Results are bitwise the same
+ * under either.  No counterpart in the paper. */
+goc_status goc_launch_grid(const goc_lattice *lat, int *balanced);
+goc_status goc_set_launch_grid(goc_lattice *lat, int balanced);
+
 /* ---- the hot loop ------------------------------------------------------ */
 
 /* Enqueue nsteps time steps (each one fused launch: pull-streaming with

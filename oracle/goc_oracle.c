@@ -117,6 +117,7 @@ typedef struct {
     double *rho, *U1, *U2, *B1, *B2;
     double *dU1, *dU2, *dr1, *dr2;   /* normal derivatives */
     double *FL1, *FL2, *J3;
+    double *dB;           /* [4][N] dB1/dxi1, dB2/dxi1, dB1/dxi2, dB2/dxi2 of the last step (diagnostic) */
     /* P and P^-1 */
     double P[9][9], Pinv[9][9];
     int nthreads;
@@ -253,6 +254,7 @@ orc_t *orc_create(int nx, int ny,
     o->dU1 = dup(NULL, N); o->dU2 = dup(NULL, N);
     o->dr1 = dup(NULL, N); o->dr2 = dup(NULL, N);
     o->FL1 = dup(NULL, N); o->FL2 = dup(NULL, N); o->J3 = dup(NULL, N);
+    o->dB = dup(NULL, 4 * N);
     /* P from its definition: row k is the monomial e1^MX e2^MY (Eq. Q-momentbasis) */
     for (int k = 0; k < 9; k++)
         for (int a = 0; a < 9; a++) o->P[k][a] = ipow(E1[a], MX[k]) * ipow(E2[a], MY[k]);
@@ -265,7 +267,7 @@ void orc_destroy(orc_t *o) {
     if (!o) return;
     double *ptrs[] = {o->h1, o->h2, o->t11, o->t12, o->t21, o->t22, o->f, o->ft,
                       o->F1, o->F2, o->g, o->gt, o->rho, o->U1, o->U2, o->B1, o->B2,
-                      o->dU1, o->dU2, o->dr1, o->dr2, o->FL1, o->FL2, o->J3};
+                      o->dU1, o->dU2, o->dr1, o->dr2, o->FL1, o->FL2, o->J3, o->dB};
     for (size_t k = 0; k < sizeof ptrs / sizeof ptrs[0]; k++) free(ptrs[k]);
     for (int w = 0; w < 4; w++) { free(o->wh1[w]); free(o->wh2[w]); }
     free(o);
@@ -511,6 +513,10 @@ static void mie_node(orc_t *o, int n) {
                  / (csm2 * (0.5 * H + (taum - 0.5) * h2 / h1));
         dB2[c] = -(L2 + 0.5 * csm2 * h1 * h2 * h2 * (t22 + t12) * B[c])
                  / (csm2 * (0.5 * H + (taum - 0.5) * h1 / h2));
+    }
+    for (int c = 0; c < 2; c++) {   /* kept for the diagnostic accessor only */
+        o->dB[(size_t)c * N + n] = dB1[c];
+        o->dB[(size_t)(2 + c) * N + n] = dB2[c];
     }
     /* current density (Eq. currentdensity-GOC) and Lorentz force (Eq. Lorentzforce-GOC) */
     double J3 = (1.0 / o->mum) / H * (h2 * dB1[1] - h1 * dB2[0] + H * (B[1] * t21 - B[0] * t12));
@@ -867,6 +873,12 @@ void orc_mie_diag(const orc_t *o, double *J3, double *FL1, double *FL2) {
     if (J3) memcpy(J3, o->J3, sizeof(double) * N);
     if (FL1) memcpy(FL1, o->FL1, sizeof(double) * N);
     if (FL2) memcpy(FL2, o->FL2, sizeof(double) * N);
+}
+
+/* The local gradients of B (Eqs. gradB1 / gradB2) the last orc_step used:
+ * [4][ny][nx] dB1/dxi1, dB2/dxi1, dB1/dxi2, dB2/dxi2. */
+void orc_mie_grad(const orc_t *o, double *dB) {
+    if (dB && o->mhd) memcpy(dB, o->dB, sizeof(double) * 4 * o->N);
 }
 
 int orc_threads(const orc_t *o) { return o->nthreads; }

@@ -81,6 +81,7 @@ def _load():
             lib.orc_raw_equilibria.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 7 + [_D]
             lib.orc_corrections.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 13 + [_D]
             lib.orc_mie_diag.argtypes = [ctypes.c_void_p] + [_D] * 3
+            lib.orc_mie_grad.argtypes = [ctypes.c_void_p, _D]
             lib.orc_set_collision.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_srt_equilibria.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 13 + [_D]
             lib.orc_srt_to_populations.argtypes = [_D, _D]
@@ -253,6 +254,13 @@ class Oracle:
         self._lib.orc_mie_diag(self._h, _p(J3), _p(FL1), _p(FL2))
         s = (self.ny, self.nx)
         return J3.reshape(s), FL1.reshape(s), FL2.reshape(s)
+
+    def mie_grad(self):
+        """The local gradients of B of the last step (Eqs. gradB1/gradB2):
+        [4, ny, nx] dB1/dxi1, dB2/dxi1, dB1/dxi2, dB2/dxi2."""
+        out = np.zeros(4 * self.nx * self.ny)
+        self._lib.orc_mie_grad(self._h, _p(out))
+        return out.reshape(4, self.ny, self.nx)
 
     # ---- single-node algebra exposed for pin tests --------------------
     def frame_matrix(self, u, v):

@@ -131,6 +131,7 @@ struct goc_lattice {
     // launch configuration (results are bitwise the same under every choice):
     // tile queue (dynamic) or static tile order, programmatic dependent launch
     int cfg_dynamic = 1, cfg_pdl = 1;
+    int cfg_balanced = 0;                        // grid: the fewest blocks taking the same rounds of tiles
     bool tuned = false;                          // chosen by the launch autotuner (or fixed)
     int plateau_checks = 0;                      // goc_exec.plateau_checks
     // per-row storage reference (16-bit storage on straight grids; see goc_aux.cuh)
@@ -199,7 +200,7 @@ bool encode_lattice_maps(goc_lattice *L) {
 
 // Dynamic shared memory of a step kernel and its persistent grid size.
 template <class S, bool MHD, bool SRT = false, int GEOM = 0>
-int step_grid(int ntiles, size_t *smem) {
+int step_grid(int ntiles, size_t *smem, bool balanced = false) {
     using T = Tiling<S>;
     const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
     *smem = bytes;
@@ -211,6 +212,10 @@ int step_grid(int ntiles, size_t *smem) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD, SRT, GEOM>, NT, bytes);
         cached = std::max(1, sms * std::max(1, per));
+    }
+    if (balanced) {   // the fewest blocks that take the same number of rounds of tiles: equal shares
+        const int rounds = (ntiles + cached - 1) / cached;
+        return (ntiles + rounds - 1) / rounds;
     }
     return std::min(ntiles, cached);
 }
@@ -230,18 +235,18 @@ cudaError_t launch_geom(goc_lattice *L, const StepParams &p, int ntiles) {
     const bool pdl = L->cfg_pdl != 0, raw = L->scheme == 2 || L->scheme == 3;
     const dim3 block(TX, TYT);
     if (L->mhd.enabled && raw) {
-        const int grid = step_grid<S, true, true, GEOM>(ntiles, &smem);
+        const int grid = step_grid<S, true, true, GEOM>(ntiles, &smem, L->cfg_balanced != 0);
         return launch_pdl(pdl, step_kernel<S, true, true, GEOM>, dim3(grid), block, smem, L->stream, p);
     }
     if (L->mhd.enabled) {
-        const int grid = step_grid<S, true, false, GEOM>(ntiles, &smem);
+        const int grid = step_grid<S, true, false, GEOM>(ntiles, &smem, L->cfg_balanced != 0);
         return launch_pdl(pdl, step_kernel<S, true, false, GEOM>, dim3(grid), block, smem, L->stream, p);
     }
     if (raw) {
-        const int grid = step_grid<S, false, true, GEOM>(ntiles, &smem);
+        const int grid = step_grid<S, false, true, GEOM>(ntiles, &smem, L->cfg_balanced != 0);
         return launch_pdl(pdl, step_kernel<S, false, true, GEOM>, dim3(grid), block, smem, L->stream, p);
     }
-    const int grid = step_grid<S, false, false, GEOM>(ntiles, &smem);
+    const int grid = step_grid<S, false, false, GEOM>(ntiles, &smem, L->cfg_balanced != 0);
     return launch_pdl(pdl, step_kernel<S, false, false, GEOM>, dim3(grid), block, smem, L->stream, p);
 }
 
@@ -259,17 +264,17 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
         CU(e);
     } else if (L->scheme == 2 || L->scheme == 3) {   // collision on raw moments (Appendix F SRT, Appendix D MRT)
         if (L->mhd.enabled) {
-            const int grid = step_grid<S, true, true>(ntiles, &smem);
+            const int grid = step_grid<S, true, true>(ntiles, &smem, L->cfg_balanced != 0);
             CU(launch_pdl(pdl, step_kernel<S, true, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
         } else {
-            const int grid = step_grid<S, false, true>(ntiles, &smem);
+            const int grid = step_grid<S, false, true>(ntiles, &smem, L->cfg_balanced != 0);
             CU(launch_pdl(pdl, step_kernel<S, false, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
         }
     } else if (L->mhd.enabled) {
-        const int grid = step_grid<S, true>(ntiles, &smem);
+        const int grid = step_grid<S, true>(ntiles, &smem, L->cfg_balanced != 0);
         CU(launch_pdl(pdl, step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     } else {
-        const int grid = step_grid<S, false>(ntiles, &smem);
+        const int grid = step_grid<S, false>(ntiles, &smem, L->cfg_balanced != 0);
         CU(launch_pdl(pdl, step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     }
     CU(cudaGetLastError());
@@ -322,7 +327,7 @@ goc_status launch_one(goc_lattice *L, float *uout) {
 // real steps of the lattice; the 16 are timed with CUDA events.
 constexpr long long kTuneWarm = 2, kTuneSteps = 16;
 std::mutex g_tune_mu;
-std::map<std::array<int, 5>, std::pair<int, int>> g_tune_cache;
+std::map<std::array<int, 5>, std::array<int, 3>> g_tune_cache;
 
 goc_status autotune(goc_lattice *L, long long *nsteps) {
     if (L->tuned) return GOC_OK;
@@ -331,23 +336,25 @@ goc_status autotune(goc_lattice *L, long long *nsteps) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            L->cfg_dynamic = it->second.first;
-            L->cfg_pdl = it->second.second;
+            L->cfg_dynamic = it->second[0];
+            L->cfg_pdl = it->second[1];
+            L->cfg_balanced = it->second[2];
             L->tuned = true;
             return GOC_OK;
         }
     }
-    const int ncand = L->scheme == 1 ? 2 : 4;
+    const int ncand = L->scheme == 1 ? 2 : 8;
     if (*nsteps < ncand * (kTuneWarm + kTuneSteps)) return GOC_OK;   // tune on a longer call
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bd = 1, bp = 1;
+    int bd = 1, bp = 1, bb = 0;
     goc_status st = GOC_OK;
     for (int c = 0; c < ncand && st == GOC_OK; c++) {
         L->cfg_pdl = (c & 1) ? 0 : 1;
         L->cfg_dynamic = (c & 2) ? 0 : 1;
+        L->cfg_balanced = (c & 4) ? 1 : 0;
         for (long long s = 0; s < kTuneWarm && st == GOC_OK; s++) st = launch_one(L, nullptr);
         cudaEventRecord(e0, L->stream);
         for (long long s = 0; s < kTuneSteps && st == GOC_OK; s++) st = launch_one(L, nullptr);
@@ -363,6 +370,7 @@ goc_status autotune(goc_lattice *L, long long *nsteps) {
             best = ms;
             bd = L->cfg_dynamic;
             bp = L->cfg_pdl;
+            bb = L->cfg_balanced;
         }
     }
     cudaEventDestroy(e0);
@@ -370,13 +378,14 @@ goc_status autotune(goc_lattice *L, long long *nsteps) {
     if (st != GOC_OK) return st;
     L->cfg_dynamic = bd;
     L->cfg_pdl = bp;
+    L->cfg_balanced = bb;
     L->tuned = true;
     if (L->graph) {   // captured under another configuration
         cudaGraphExecDestroy(L->graph);
         L->graph = nullptr;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = {bd, bp};
+    g_tune_cache[key] = {bd, bp, bb};
     return GOC_OK;
 }
 
@@ -1385,6 +1394,24 @@ goc_status goc_launch_config(const goc_lattice *L, int *dynamic_tiles, int *pdl,
     if (dynamic_tiles) *dynamic_tiles = L->cfg_dynamic;
     if (pdl) *pdl = L->cfg_pdl;
     if (tuned) *tuned = L->tuned ? 1 : 0;
+    return GOC_OK;
+}
+
+goc_status goc_launch_grid(const goc_lattice *L, int *balanced) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (balanced) *balanced = L->cfg_balanced;
+    return GOC_OK;
+}
+
+goc_status goc_set_launch_grid(goc_lattice *L, int balanced) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (balanced != 0 && balanced != 1) return fail(GOC_EINVAL, "balanced must be 0 or 1");
+    L->cfg_balanced = balanced;
+    L->tuned = true;
+    if (L->graph) {   // captured under another configuration
+        cudaGraphExecDestroy(L->graph);
+        L->graph = nullptr;
+    }
     return GOC_OK;
 }
 

@@ -835,16 +835,13 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
             __stcg(p.uout + 3 * p.plane + idx[q], lane(B2, q));
         }
     }
-    if (p.flag) {   // divergence flag: one atomic per warp at most
-        bool bad = false;
+    // divergence (non-positive density or non-finite velocity): the thread
+    // that sees it sets the status word unless it is set already (no vote and
+    // nothing kept across tiles: the test costs a compare and a branch)
 #pragma unroll
-        for (int q = 0; q < R; q++) {
-            const float rq = lane(rho, q), uq = fabsf(lane(U1, q)) + fabsf(lane(U2, q));
-            bad = bad || (own[q] && !(rq > 0.f && uq < 1e30f));
-        }
-        const unsigned mk = __activemask();
-        if (__any_sync(mk, bad) && (threadIdx.x & 31) == (__ffs(mk) - 1) && *((volatile int *)p.flag) == 0)
-            atomicExch(p.flag, 1);
+    for (int q = 0; q < R; q++) {
+        const float rq = lane(rho, q), uq = fabsf(lane(U1, q)) + fabsf(lane(U2, q));
+        if (own[q] && !(rq > 0.f && uq < 1e30f) && p.flag && *((volatile int *)p.flag) == 0) atomicExch(p.flag, 1);
     }
 }
 

@@ -209,12 +209,15 @@ class Lattice:
 
     @property
     def launch_config(self) -> dict:
-        d, p, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        d, p, t, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(lib().goc_launch_config(self._h, ctypes.byref(d), ctypes.byref(p), ctypes.byref(t)))
-        return {"dynamic_tiles": bool(d.value), "pdl": bool(p.value), "tuned": bool(t.value)}
+        check(lib().goc_launch_grid(self._h, ctypes.byref(b)))
+        return {"dynamic_tiles": bool(d.value), "pdl": bool(p.value), "balanced_grid": bool(b.value),
+                "tuned": bool(t.value)}
 
-    def set_launch_config(self, dynamic_tiles: bool, pdl: bool):
+    def set_launch_config(self, dynamic_tiles: bool, pdl: bool, balanced_grid: bool = False):
         check(lib().goc_set_launch_config(self._h, int(dynamic_tiles), int(pdl)))
+        check(lib().goc_set_launch_grid(self._h, int(balanced_grid)))
 
     @property
     def bytes_per_node(self) -> float:

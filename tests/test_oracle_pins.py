@@ -871,6 +871,7 @@ def _annulus_mie(n1, rot, b_in=0.02, b_out=0.01, steps_per_diffusion=1.0):
     lap = (np.diag(-2.0 * np.ones(k)) + np.diag(np.ones(k - 1), 1) + np.diag(np.ones(k - 1), -1)) / hX ** 2
     b2a = np.interp(x, X, np.concatenate([[0.0], np.linalg.solve(lap, rhs[1:-1]), [0.0]]))
     o.step(int(steps_per_diffusion * n1 * n1 / eta))
+    _annulus_mie.last = o
     return o.fields(), b1a, b2a, om * m.radius
 
 
@@ -892,6 +893,32 @@ def test_curvilinear_mie_reaches_the_steady_solution_of_its_equation():
     (e1a, e2a), (e1b, e2b) = errs
     assert e1b < 3e-3 and e2b < 1e-2, errs
     assert math.log2(e1a / e1b) > 1.8 and math.log2(e2a / e2b) > 1.8, errs
+
+
+def test_mie_local_gradients_match_finite_differences_of_the_field():
+    """Eqs. gradB1 / gradB2 give dB from the non-equilibrium first moments of
+    g (Lambda^(1)) and the curvature terms, locally: on the steady, smooth
+    field of the annular sector above (theta11 = theta21 = 1/r) they must
+    agree with second-order central differences of the B nodes themselves,
+    the difference shrinking at second order in the radial nodes (a dropped
+    curvature term, a wrong tau_m - 1/2 factor or a transposed h1/h2 ratio
+    leaves an O(1) gap).  The field is uniform along xi2, so the xi2
+    gradients from the moments must vanish there."""
+    errs = []
+    for n1 in (16, 32):
+        f, *_ = _annulus_mie(n1, rot=1.0)
+        b1, b2 = f[3][0], f[4][0]
+        # the oracle's fields and gradients belong to the same (last) step
+        o_grad = _annulus_mie.last.mie_grad()
+        inner = slice(2, n1 - 2)
+        fd = [0.5 * (b[2:] - b[:-2])[1:-1] for b in (b1, b2)]    # d/dxi1 at the inner nodes
+        mom = [o_grad[0][0][inner], o_grad[1][0][inner]]         # dB1/dxi1, dB2/dxi1
+        errs.append([np.linalg.norm(m - d) / np.linalg.norm(d) for m, d in zip(mom, fd)])
+        scale = max(np.abs(o_grad[0]).max(), np.abs(o_grad[1]).max())
+        assert np.abs(o_grad[2:]).max() < 1e-6 * scale   # d/dxi2 of a field uniform along xi2
+    (a1, a2), (c1, c2) = errs
+    assert c1 < 1e-2 and c2 < 2e-2, errs
+    assert math.log2(a1 / c1) > 1.7 and math.log2(a2 / c2) > 1.7, errs
 
 
 def test_transposed_annulus_with_the_mie_gives_the_transposed_solution():

@@ -292,8 +292,9 @@ def test_interior_tiles_match_the_oracle(gpu, kind):
 
 
 def test_launch_configurations_give_bitwise_identical_populations(gpu):
-    """Tile queue vs static tile order and dependent launch on or off change
-    only which block computes which tile and when: the populations agree
+    """Tile queue vs static tile order, dependent launch on or off and the
+    balanced grid change only which block computes which tile and when: the
+    populations agree
     bitwise (on a cavity with interior, wall and ragged tiles, and on a
     periodic channel whose seam tiles read global memory)."""
     for prob in (gi.Problem("cavity", 200, 90, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
@@ -302,11 +303,12 @@ def test_launch_configurations_give_bitwise_identical_populations(gpu):
                             {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0})):
         spec = prob.lattice_spec(cs2_of(prob))
         states = []
-        for dyn, pdl in ((True, True), (False, True), (True, False), (False, False)):
+        for dyn, pdl, bal in ((True, True, False), (False, True, False), (True, False, False),
+                              (False, False, False), (True, True, True), (False, True, True)):
             L = goc.Lattice(spec)
-            L.set_launch_config(dyn, pdl)
+            L.set_launch_config(dyn, pdl, bal)
             L.step(150)
-            assert L.launch_config == {"dynamic_tiles": dyn, "pdl": pdl, "tuned": True}
+            assert L.launch_config == {"dynamic_tiles": dyn, "pdl": pdl, "balanced_grid": bal, "tuned": True}
             states.append(L.get_state())
             L.close()
         assert all(s == states[0] for s in states[1:])
