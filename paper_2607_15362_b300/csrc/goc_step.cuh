@@ -46,8 +46,17 @@ namespace goc {
 #define GOC_MIN_BLOCKS 4       // resident blocks per SM asked of the register allocator, NSE kernels (64
                                // registers; measured best: 124.9 vs 139.7 us at 2048^2 with 3 blocks)
 #endif
+#ifndef GOC_MIE_STAGED
+// 0 (default): the MIE populations are read through L1 and the NSE+MIE kernels
+// run 3 blocks per SM (80 registers, 2 x 25 KB stages); 1: they are staged by
+// TMA with the tile (2 x 41 KB stages, 2 blocks per SM).  Measured (B300,
+// FP32 / FP16 us per step): Hartmann channel 256 x 1024 31.8 / 37.2 against
+// 34.2 / 41.8 staged; 1024^2 cavity with the MIE 70.7 / 71.5 against 70.6 /
+// 76.7; 2048^2 218 / 232 against 208 / 253.
+#define GOC_MIE_STAGED 0
+#endif
 #ifndef GOC_MIN_BLOCKS_MHD
-#define GOC_MIN_BLOCKS_MHD 2   // with the MIE two stages of 41 KB leave room for two blocks per SM
+#define GOC_MIN_BLOCKS_MHD (GOC_MIE_STAGED ? 2 : 3)
 #endif
 #ifndef GOC_ROWS_PER_THREAD
 #define GOC_ROWS_PER_THREAD 1  // nodes per thread (rows ty + r TY/RPT); 2 runs the collision on packed f32x2 (measured slower)
@@ -71,7 +80,7 @@ template <class S> struct Tiling {
     static constexpr int OFF_FF = align128(F_BYTES);
     static constexpr int OFF_G = OFF_FF + align128(FF_BYTES);
     static constexpr int STAGE_NSE = OFF_G;
-    static constexpr int STAGE_MHD = OFF_G + align128(G_BYTES);
+    static constexpr int STAGE_MHD = GOC_MIE_STAGED ? OFF_G + align128(G_BYTES) : OFF_G;
 };
 
 // ---- TMA / mbarrier primitives (inline PTX) ----------------------------------
@@ -132,6 +141,10 @@ template <class S> struct SrcSmem {        // the TMA-staged tile
     const S *f, *F, *g;
     int ox, oy, oyg;                        // lattice coordinates of staged element (0, 0)
     float sf, sF, sg;
+#if !GOC_MIE_STAGED
+    long long plane;                        // g: the MIE populations in global memory
+    int pitch;
+#endif
     __device__ __forceinline__ float fv(int a, int i, int j) const {
         return scl<S>(Store<S>::lds(f + (a * T::BY + (j - oy)) * T::BX + (i - ox)), sf);
     }
@@ -139,7 +152,11 @@ template <class S> struct SrcSmem {        // the TMA-staged tile
         return scl<S>(Store<S>::lds(F + (c * T::BY + (j - oy)) * T::BX + (i - ox)), sF);
     }
     __device__ __forceinline__ float gv(int k, int i, int j) const {
+#if GOC_MIE_STAGED
         return scl<S>(Store<S>::lds(g + (k * T::BYG + (j - oyg)) * T::BX + (i - ox)), sg);
+#else
+        return scl<S>(Store<S>::ld(g + k * plane + (long long)j * pitch + i), sg);
+#endif
     }
 };
 
@@ -1020,11 +1037,11 @@ template <class S>
 __device__ __forceinline__ void issue_tile(const TileMaps &m, int i0, int j0, unsigned char *stage, uint64_t *bar,
                                            bool mhd) {
     using T = Tiling<S>;
-    const uint32_t bytes = T::F_BYTES + T::FF_BYTES + (mhd ? T::G_BYTES : 0);
+    const uint32_t bytes = T::F_BYTES + T::FF_BYTES + (mhd && GOC_MIE_STAGED ? T::G_BYTES : 0);
     mbar_expect_tx(bar, bytes);
     tma_load_3d(stage, m.f, i0 - T::HXS, j0 - HYS, 0, bar);
     tma_load_3d(stage + T::OFF_FF, m.F, i0 - T::HXS, j0 - HYS, 0, bar);
-    if (mhd) tma_load_3d(stage + T::OFF_G, m.g, i0 - T::HXS, j0 - 1, 0, bar);
+    if (mhd && GOC_MIE_STAGED) tma_load_3d(stage + T::OFF_G, m.g, i0 - T::HXS, j0 - 1, 0, bar);
 }
 
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *m) {
@@ -1040,9 +1057,14 @@ __device__ __forceinline__ bool run_tile(const StepParams &p, int kind, int i0, 
                          p.plane, p.pitch, p.sf, p.sF, p.sg};
         return tile_compute<S, MHD, 1, SRT, GEOM>(p, src, i0, j0, sm, ok);
     }
+#if GOC_MIE_STAGED
     SrcSmem<S> src{reinterpret_cast<const S *>(stage), reinterpret_cast<const S *>(stage + T::OFF_FF),
                    reinterpret_cast<const S *>(stage + T::OFF_G), i0 - T::HXS, j0 - HYS, j0 - 1,
                    p.sf, p.sF, p.sg};
+#else
+    SrcSmem<S> src{reinterpret_cast<const S *>(stage), reinterpret_cast<const S *>(stage + T::OFF_FF),
+                   static_cast<const S *>(p.gin), i0 - T::HXS, j0 - HYS, j0 - 1, p.sf, p.sF, p.sg, p.plane, p.pitch};
+#endif
     if (kind == 0) return tile_compute<S, MHD, 0, SRT, GEOM>(p, src, i0, j0, sm, ok);
     return tile_compute<S, MHD, 1, SRT, GEOM>(p, src, i0, j0, sm, ok);
 }
@@ -1176,7 +1198,7 @@ __device__ __forceinline__ int batch_lattice(const BatchArgs &a, int t) {
     return lo;
 }
 
-template <class S, bool MHD>
+template <class S, bool MHD, int GEOM = 0>
 __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) batch_step_kernel(const __grid_constant__ BatchArgs a) {
     using T = Tiling<S>;
     constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
@@ -1248,7 +1270,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
         if (MHD) {
             if (!__syncthreads_and(ok)) return;
         }
-        if (!run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
+        if (!run_tile<S, MHD, false, GEOM>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok)) return;   // the block leaves together
         __syncthreads();   // the stage, the field arrays and s_item are reused
         stage ^= 1;
     }
