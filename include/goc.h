@@ -341,9 +341,10 @@ void goc_batch_destroy(goc_batch *b);
 
 /* Admit a lattice (same arguments as goc_create; exec's stream and storage
  * come from the batch unless exec != NULL).  Returns GOC_EBUSY if the budget
- * or the slot count would be exceeded, GOC_EUNSUPPORTED for an ANNULUS or
- * TABLE map (curved-grid lattices run one per goc_create).  *slot receives
- * the slot id. */
+ * or the slot count would be exceeded.  Every grid kind may join: per-axis
+ * maps, the annular sector and node tables are grouped by kind (one batch
+ * kernel per storage type, MIE on/off and grid kind).  *slot receives the
+ * slot id. */
 goc_status goc_batch_add(goc_batch *b, const goc_grid *grid, const goc_map *map,
                          const goc_flow *flow, const goc_mhd *mhd, int storage, int *slot);
 

@@ -1746,7 +1746,7 @@ struct goc_batch {
     // graph chunk each set runs all its steps before the next set starts, so a
     // set's populations stay L2-resident for the whole chunk.
     struct Group {
-        int storage = 0, mhd = 0, n = 0, total = 0, grid = 0, stage_bytes = 0;
+        int storage = 0, mhd = 0, geom = 0, n = 0, total = 0, grid = 0, stage_bytes = 0;
         std::vector<int> members;      // at most kBatchMax slots
         std::vector<BatchArgs> args;   // launch arguments: parity 0, parity 1, first step after a rebuild,
                                        // then parity p with snapshot u: 3 + 2 p + u
@@ -1765,13 +1765,16 @@ namespace {
 
 constexpr int kBatchGraphSteps = 32;
 
-long long estimate_bytes(const goc_grid *grid, const goc_mhd *mhd, int storage) {
+long long estimate_bytes(const goc_grid *grid, const goc_map *map, const goc_mhd *mhd, int storage) {
     const long long pitch = (grid->nx + 31) / 32 * 32;
     const long long plane = pitch * grid->ny;
     const long long es = (long long)elem_size(storage);
     long long b = 2 * (9 + 2) * plane * es;
     if (mhd && mhd->enabled) b += 2 * 10 * plane * es;
-    b += 7LL * 4 * (grid->nx + grid->ny) + 16LL * (grid->nx + grid->ny + 4) + 128;
+    b += 8LL * 4 * (grid->nx + grid->ny) + 32LL * (grid->nx + grid->ny + 4) + 128;
+    if (map && map->kind[0] == GOC_MAP_TABLE)   // node-table metric planes and wall factors
+        b += (10 * plane + 8LL * std::max(grid->nx, grid->ny)) * 4;
+    if (storage != GOC_FP32) b += 6LL * 8 * grid->ny + 7LL * 4 * grid->ny;   // per-row storage reference
     return b;
 }
 
@@ -1797,37 +1800,67 @@ long long l2_set_bytes(int device) {
     return l2 > 0 ? 3LL * l2 / 4 : (1LL << 62);
 }
 
-template <class S, bool MHD>
-int persistent_grid(int total, int *stage_bytes) {
+template <class S, bool MHD, int GEOM>
+int persistent_grid_t(int total, int *stage_bytes) {
     using T = Tiling<S>;
     const int stage = MHD ? T::STAGE_MHD : T::STAGE_NSE;
     *stage_bytes = stage;
     static int cached = -1;
     if (cached < 0) {
-        cudaFuncSetAttribute(batch_step_kernel<S, MHD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * stage);
+        cudaFuncSetAttribute(batch_step_kernel<S, MHD, GEOM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * stage);
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S, MHD>, NT, 2 * (size_t)stage);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S, MHD, GEOM>, NT, 2 * (size_t)stage);
         cached = std::max(1, sms * std::max(1, per));
     }
     return std::min(total, cached);
 }
 
+// Kernel type of a batch group: storage (3) x MIE (2) x grid kind (straight,
+// annular sector, node table); one batch kernel instantiation each.
+int batch_key(int storage, int mhd, int geom) { return (geom * 3 + storage) * 2 + mhd; }
+
+template <int GEOM>
+int persistent_grid_g(int storage, int mhd, int *stage_bytes) {
+    switch (2 * storage + mhd) {
+        case 2: return persistent_grid_t<__half, false, GEOM>(1 << 30, stage_bytes);
+        case 3: return persistent_grid_t<__half, true, GEOM>(1 << 30, stage_bytes);
+        case 4: return persistent_grid_t<__nv_bfloat16, false, GEOM>(1 << 30, stage_bytes);
+        case 5: return persistent_grid_t<__nv_bfloat16, true, GEOM>(1 << 30, stage_bytes);
+        case 1: return persistent_grid_t<float, true, GEOM>(1 << 30, stage_bytes);
+        default: return persistent_grid_t<float, false, GEOM>(1 << 30, stage_bytes);
+    }
+}
+
+template <int GEOM>
+cudaError_t batch_launch_g(int storage, int mhd, dim3 gd, dim3 bd, size_t smem, cudaStream_t st, const BatchArgs &a) {
+    switch (2 * storage + mhd) {
+        case 2: return launch_pdl(true, batch_step_kernel<__half, false, GEOM>, gd, bd, smem, st, a);
+        case 3: return launch_pdl(true, batch_step_kernel<__half, true, GEOM>, gd, bd, smem, st, a);
+        case 4: return launch_pdl(true, batch_step_kernel<__nv_bfloat16, false, GEOM>, gd, bd, smem, st, a);
+        case 5: return launch_pdl(true, batch_step_kernel<__nv_bfloat16, true, GEOM>, gd, bd, smem, st, a);
+        case 1: return launch_pdl(true, batch_step_kernel<float, true, GEOM>, gd, bd, smem, st, a);
+        default: return launch_pdl(true, batch_step_kernel<float, false, GEOM>, gd, bd, smem, st, a);
+    }
+}
+
 goc_status rebuild(goc_batch *B) {
     free_groups(B);
     const long long cap = l2_set_bytes(B->device);
-    for (int key = 0; key < 6; key++) {   // kernel type 2 * storage + (MIE on); launches of <= kBatchMax lattices
+    for (int key = 0; key < 18; key++) {   // kernel type (batch_key); launches of <= kBatchMax lattices
         long long used = 0;
         for (int k = 0; k < (int)B->slots.size(); k++) {
             goc_lattice *L = B->slots[k];
-            if (!L || 2 * L->storage + (L->mhd.enabled ? 1 : 0) != key) continue;
-            if (B->groups.empty() || 2 * B->groups.back().storage + B->groups.back().mhd != key ||
+            if (!L || batch_key(L->storage, L->mhd.enabled ? 1 : 0, L->sp.curv) != key) continue;
+            if (B->groups.empty() ||
+                batch_key(B->groups.back().storage, B->groups.back().mhd, B->groups.back().geom) != key ||
                 (int)B->groups.back().members.size() == kBatchMax ||
                 (used + B->bytes[k] > cap && !B->groups.back().members.empty())) {
                 goc_batch::Group g;
-                g.storage = key / 2;
                 g.mhd = key % 2;
+                g.storage = (key / 2) % 3;
+                g.geom = key / 6;
                 B->groups.push_back(std::move(g));
                 used = 0;
             }
@@ -1845,14 +1878,9 @@ goc_status rebuild(goc_batch *B) {
             g.total += tiles[m];
         }
         int capacity = 0;   // resident blocks of this kernel on the device
-        switch (2 * g.storage + g.mhd) {
-            case 2: capacity = persistent_grid<__half, false>(1 << 30, &g.stage_bytes); break;
-            case 3: capacity = persistent_grid<__half, true>(1 << 30, &g.stage_bytes); break;
-            case 4: capacity = persistent_grid<__nv_bfloat16, false>(1 << 30, &g.stage_bytes); break;
-            case 5: capacity = persistent_grid<__nv_bfloat16, true>(1 << 30, &g.stage_bytes); break;
-            case 1: capacity = persistent_grid<float, true>(1 << 30, &g.stage_bytes); break;
-            default: capacity = persistent_grid<float, false>(1 << 30, &g.stage_bytes); break;
-        }
+        capacity = g.geom == 2 ? persistent_grid_g<2>(g.storage, g.mhd, &g.stage_bytes)
+                   : g.geom == 1 ? persistent_grid_g<1>(g.storage, g.mhd, &g.stage_bytes)
+                                 : persistent_grid_g<0>(g.storage, g.mhd, &g.stage_bytes);
         g.grid = std::min(g.total, capacity);   // persistent blocks taking tiles from the counter
         g.args.assign(7, BatchArgs{});
         CU(cudaMalloc(&g.ctr, 2 * sizeof(int)));
@@ -1912,14 +1940,9 @@ goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first =
         const size_t smem = 2 * (size_t)g.stage_bytes;
         const dim3 gd(g.grid), bd(TX, TYT);
         cudaError_t e;
-        switch (2 * g.storage + g.mhd) {
-            case 2: e = launch_pdl(true, batch_step_kernel<__half, false>, gd, bd, smem, st, a); break;
-            case 3: e = launch_pdl(true, batch_step_kernel<__half, true>, gd, bd, smem, st, a); break;
-            case 4: e = launch_pdl(true, batch_step_kernel<__nv_bfloat16, false>, gd, bd, smem, st, a); break;
-            case 5: e = launch_pdl(true, batch_step_kernel<__nv_bfloat16, true>, gd, bd, smem, st, a); break;
-            case 1: e = launch_pdl(true, batch_step_kernel<float, true>, gd, bd, smem, st, a); break;
-            default: e = launch_pdl(true, batch_step_kernel<float, false>, gd, bd, smem, st, a); break;
-        }
+        e = g.geom == 2 ? batch_launch_g<2>(g.storage, g.mhd, gd, bd, smem, st, a)
+            : g.geom == 1 ? batch_launch_g<1>(g.storage, g.mhd, gd, bd, smem, st, a)
+                          : batch_launch_g<0>(g.storage, g.mhd, gd, bd, smem, st, a);
         CU(e);
         CU(cudaGetLastError());
     }
@@ -1967,8 +1990,6 @@ goc_status goc_batch_add(goc_batch *B, const goc_grid *grid, const goc_map *map,
     if (!B || !slot) return fail(GOC_EINVAL, "batch and slot are required");
     *slot = -1;
     if (!grid) return fail(GOC_EINVAL, "grid is required");
-    if (map && map->kind[0] == GOC_MAP_ANNULUS) return fail(GOC_EUNSUPPORTED, "annulus lattices are not batched");
-    if (map && map->kind[0] == GOC_MAP_TABLE) return fail(GOC_EUNSUPPORTED, "TABLE lattices are not batched");
     int free_slot = -1;
     for (int k = 0; k < B->max_lat; k++)
         if (!B->slots[k]) {
@@ -1976,7 +1997,7 @@ goc_status goc_batch_add(goc_batch *B, const goc_grid *grid, const goc_map *map,
             break;
         }
     if (free_slot < 0) return fail(GOC_EBUSY, "batch is full (%d lattices)", B->max_lat);
-    const long long need = estimate_bytes(grid, mhd, storage);
+    const long long need = estimate_bytes(grid, map, mhd, storage);
     if (B->used + need > B->budget)
         return fail(GOC_EBUSY, "HBM budget exhausted (%lld + %lld > %lld bytes)", B->used, need, B->budget);
     goc_exec ex;
