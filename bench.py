@@ -285,6 +285,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(prob, spec, budget_s=args.cpu_seconds)
+    extras = None
+    headline = (args.cavity_n == 512 and args.grid == "tanh" and args.storage == "fp32" and not args.mie
+                and args.scheme == "goc")
+    if rank == 0 and world == 1 and headline and not args.no_extras:
+        extras = extra_numbers(args)
 
     if rank == 0:
         line = {
@@ -318,6 +323,7 @@ def run_ours(args):
                          "launch_us": round(launch_s * 1e6, 3),
                          "launch_config": lat.launch_config, "issue": issue},
             "cpu_baseline": cpu,
+            "extras": extras,
             "gpu_launches": args.steps * chunk,
             "clocks": clocks,
             "wall_s": round(wall, 3),
@@ -440,9 +446,10 @@ def run_sharded(args):
         dist.destroy_process_group()
 
 
-def run_batch(args):
+def batch_numbers(steps: int, storage16: str = "fp16") -> dict:
     """64 lattices (seed 7) advanced together by the persistent batched
-    kernel vs one lattice at a time with its own launches; FP32 and 16-bit."""
+    kernel (FP32 and 16-bit storage) vs one lattice at a time with its own
+    launches (FP32): aggregate MLUPS of each."""
     import torch
 
     import paper_2607_15362_b300 as goc
@@ -450,11 +457,11 @@ def run_batch(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    probs = gi.batch_lattices(steps=args.batch_steps)
+    probs = gi.batch_lattices(steps=steps)
     specs = [lattice_spec(p) for p in probs]
     nodes = sum(p.nodes for p in probs)
-    out = {}
-    for storage in ("fp32", args.storage if args.storage != "fp32" else "fp16"):
+    out = {"lattices": len(probs), "nodes": nodes, "steps_each": steps}
+    for storage in ("fp32", storage16):
         b = goc.Batch(200 << 30, len(probs), storage=storage, stream=stream.cuda_stream)
         for sp in specs:
             b.add(sp)
@@ -462,35 +469,38 @@ def run_batch(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        b.step(args.batch_steps)
+        b.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        out[f"batched_{storage}_mlups"] = round(nodes * args.batch_steps / ms / 1e3, 1)
+        out[f"batched_{storage}_mlups"] = round(nodes * steps / ms / 1e3, 1)
         used, _, _ = b.usage()
         out[f"batched_{storage}_device_gb"] = round(used / 1e9, 3)
         b.close()
-    # sequential: each lattice alone, same number of steps
-    total_ms = 0.0
+    total_ms = 0.0   # sequential: each lattice alone, same number of steps
     for sp in specs:
         lat = goc.Lattice(sp, stream=stream.cuda_stream)
         lat.step(64)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        lat.step(args.batch_steps)
+        lat.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
         lat.close()
-    out["sequential_fp32_mlups"] = round(nodes * args.batch_steps / total_ms / 1e3, 1)
-    line = {"metric": METRIC, "workload": "batch of 64 stretched-grid lattices (seed 7)", "lattices": len(probs),
-            "nodes": nodes, "steps_each": args.batch_steps, "unit": "MLUPS", **out,
-            "speedup_batched_vs_sequential": round(out["batched_fp32_mlups"] / out["sequential_fp32_mlups"], 3)}
+    out["sequential_fp32_mlups"] = round(nodes * steps / total_ms / 1e3, 1)
+    out["speedup_batched_vs_sequential"] = round(out["batched_fp32_mlups"] / out["sequential_fp32_mlups"], 3)
+    return out
+
+
+def run_batch(args):
+    line = {"metric": METRIC, "workload": "batch of 64 stretched-grid lattices (seed 7)", "unit": "MLUPS",
+            **batch_numbers(args.batch_steps, args.storage if args.storage != "fp32" else "fp16")}
     print(json.dumps(line))
 
 
-def run_serve(args):
+def serve_numbers(requests: int, storage: str, chunk: int, seconds: float) -> dict:
     """The first requests of the seed-11 Poisson trace served with
     continuous batching vs one solve at a time; p50/p99 latency and
     aggregate MLUPS."""
@@ -499,19 +509,83 @@ def run_serve(args):
     from paper_2607_15362_b300.serve import Server, requests_from_trace, run_sequential
 
     torch.cuda.set_device(0)
-    trace = gi.serving_trace()[: args.requests]
-    reqs = requests_from_trace(trace, storage=args.storage)
+    trace = gi.serving_trace()[:requests]
+    reqs = requests_from_trace(trace, storage=storage)
     offered = sum(r.problem.nodes * r.budget for r in reqs) / max(trace[-1]["arrival_s"], 1e-9) / 1e6
-    srv = Server(150 * (1 << 30) // 1, max_slots=256, chunk=args.chunk if args.chunk != 1000 else 500,
-                 storage=args.storage)
-    res_b, sum_b = srv.run(reqs, max_wall_s=args.serve_seconds)
+    srv = Server(150 * (1 << 30) // 1, max_slots=256, chunk=chunk, storage=storage)
+    res_b, sum_b = srv.run(reqs, max_wall_s=seconds)
     srv.close()
-    res_s, sum_s = run_sequential(reqs, max_wall_s=args.serve_seconds)
-    line = {"metric": METRIC, "workload": f"serving trace (seed 11), first {len(reqs)} requests",
-            "unit": "MLUPS", "offered_mlups": round(offered, 1),
+    res_s, sum_s = run_sequential(reqs, max_wall_s=seconds)
+    return {"workload": f"serving trace (seed 11), first {len(reqs)} requests", "unit": "MLUPS",
+            "offered_mlups": round(offered, 1),
             "batched": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in sum_b.items()},
             "sequential": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in sum_s.items()}}
-    print(json.dumps(line))
+
+
+def run_serve(args):
+    print(json.dumps({"metric": METRIC, **serve_numbers(args.requests, args.storage,
+                                                        args.chunk if args.chunk != 1000 else 500,
+                                                        args.serve_seconds)}))
+
+
+def lattice_rate(spec: dict, storage: str, steps: int, init=None) -> dict:
+    """us per LB step (CUDA events around goc_step after a warm-up call that
+    lets the launch autotuner run), node updates per second and the HBM
+    fraction (algorithmic bytes / time over the measured copy bandwidth)."""
+    import torch
+
+    import paper_2607_15362_b300 as goc
+    stream = torch.cuda.current_stream()
+    lat = goc.Lattice(spec, storage=storage, stream=stream.cuda_stream)
+    if init:
+        lat.init_fields(**init)
+    lat.step(max(200, steps // 4))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    nodes = spec["nx"] * spec["ny"]
+    peaks, _ = measured_peaks()
+    bpn = lat.bytes_per_node
+    lat.close()
+    return {"us_per_step": round(us, 3), "mlups": round(nodes / us, 1),
+            "hbm_frac": round(bpn * nodes / (us * 1e-6) / (float(peaks.get("hbm_gbs", 6400.0)) * 1e9), 4),
+            "bytes_per_node": round(bpn, 2)}
+
+
+def extra_numbers(args) -> dict:
+    """The rest of the metric, measured in the same run as the headline: 16-bit
+    against FP32 storage (the benchmark cavity, and at 2048^2 beyond L2), the
+    coupled MHD Hartmann channel (256 x 1024, tanh beta = 3, Ha = 100), the
+    64-lattice batch against sequential launches, and serving p50/p99."""
+    import paper_2607_15362_b300 as goc
+    t0 = time.perf_counter()
+    out = {}
+    storage = {}
+    for n, re in ((512, 1000.0), (2048, 4000.0)):
+        prob = gi.lid_cavity(n=n, Re=re)
+        _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
+        spec = prob.lattice_spec(cs2)
+        row = {st: lattice_rate(spec, st, 2000 if n == 512 else 400) for st in ("fp32", "fp16", "bf16")}
+        row["fp16_over_fp32"] = round(row["fp16"]["mlups"] / row["fp32"]["mlups"], 3)
+        storage[f"cavity_{n}x{n}" + ("" if n == 512 else f"_Re{re:g}")] = row
+    out["storage"] = storage
+    prob = gi.hartmann_channel()
+    _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
+    spec = prob.lattice_spec(cs2)
+    y = prob.ny * gi.wall_positions(prob.map2, prob.ny)
+    ua, ba = gi.hartmann_profiles(spec, 100.0, y)
+    shape = (prob.ny, prob.nx)
+    import numpy as np
+    init = {"u1": np.broadcast_to(ua[:, None], shape).copy(), "b1": np.broadcast_to(ba[:, None], shape).copy()}
+    out["mie_hartmann_256x1024"] = {st: lattice_rate(spec, st, 2000, init) for st in ("fp32", "fp16")}
+    out["batch"] = batch_numbers(500)
+    out["serve"] = serve_numbers(args.requests, "fp32", 500, args.serve_seconds)
+    out["extras_wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def _wall_positions(m, n):
@@ -941,6 +1015,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra measurements of the main line (storage formats, sizes, MHD, batch, serving)")
     ap.add_argument("--replicas", action="store_true",
                     help="with several ranks: one independent lattice per rank instead of one lattice in slabs")
     ap.add_argument("--shard", action="store_true",
