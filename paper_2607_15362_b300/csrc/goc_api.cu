@@ -20,6 +20,7 @@
 #include "goc_device.cuh"
 #include "goc_std.cuh"
 #include "goc_step.cuh"
+#include "goc_internal.h"
 
 using namespace goc;
 
@@ -33,30 +34,6 @@ struct TraceRange {
 
 namespace {
 
-// Kernel launch with programmatic stream serialisation (the kernel may start
-// while its predecessor drains; it waits in griddepcontrol.wait before
-// touching data).  GOC_DISABLE_PDL=1 launches plainly.
-bool pdl_enabled() {
-    static const int on = std::getenv("GOC_DISABLE_PDL") ? 0 : 1;
-    return on != 0;
-}
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                       Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = (pdl && pdl_enabled()) ? 1 : 0;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
-
 thread_local std::string g_err;
 
 goc_status fail(goc_status st, const char *fmt, ...) {
@@ -69,81 +46,23 @@ goc_status fail(goc_status st, const char *fmt, ...) {
     return st;
 }
 
-#define CU(call)                                                                          \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(GOC_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
-                        __FILE__, __LINE__);                                              \
-    } while (0)
-
 size_t elem_size(int storage) { return storage == GOC_FP32 ? 4 : 2; }
 
-constexpr int kGraphSteps = 64;
-constexpr int kRefEvery = 1024;
-constexpr int kSlabGhost = 2;     // ghost rows per internal cut of a slab   // default steps between refreshes of the per-row storage reference   // steps per captured graph (even: one buffer cycle per 2)
+constexpr int kGraphSteps = 64;  // steps per captured graph (even: one buffer cycle per 2)
+constexpr int kRefEvery = 1024;  // default steps between refreshes of the per-row storage reference
+constexpr int kSlabGhost = 2;     // ghost rows per internal cut of a slab
 
 }  // namespace
 
-struct goc_lattice {
-    goc_grid grid;
-    goc_map map;
-    goc_flow flow;
-    goc_mhd mhd;
-    int storage = GOC_FP32;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    int check_every = 100;
-    int nx = 0, ny = 0, pitch = 0;
-    long long plane = 0;
-    // device memory
-    void *f[2] = {nullptr, nullptr};
-    void *F[2] = {nullptr, nullptr};
-    void *g[2] = {nullptr, nullptr};
-    float *tab1 = nullptr, *tab2 = nullptr;      // [7][nx], [7][ny]
-    double *m1 = nullptr, *m2 = nullptr;         // FP64 h, theta per axis: [2][n+2]
-    float *gm = nullptr;                         // node-table metric: [10][plane] + [4][max(nx, ny)]
-    float *uout[2] = {nullptr, nullptr};
-    int *flag = nullptr;
-    double *red = nullptr;                       // 8 doubles
-    double *mom = nullptr;                       // [5][ny][nx]
-    size_t device_bytes = 0;
-    // parameters
-    double q = 1.0, cs2 = 1.0 / 3.0, nu = 0, zeta = 0, tau = 1, csm2 = 0, taum = 1, eta = 0;
-    double hw[4] = {1, 1, 1, 1};
-    StepParams sp;
-    int cur = 0;
-    long long steps = 0;
-    double res_u = 0.0, res_b = 0.0;
-    cudaGraphExec_t graph = nullptr;
-    int graph_cur = 0;                           // buffer the captured graph starts from
-    bool owns_stream = false;
-    bool in_batch = false;                       // stepped only through goc_batch_step
-    bool guard = false;                          // guard bands: padding columns and buffer tails hold a canary
-    int *hflag = nullptr;                        // pinned host copy of flag[0], refreshed after each goc_step
-    cudaEvent_t flag_ev = nullptr;               // completion of that copy
-    bool fresh = false;                          // buffer holds f^0 (pre-collision): next step reads in place
-    bool res_pending = false;                    // residual sums of a batch step wait in red[4..7]
-    CUtensorMap tmf[2], tmF[2], tmg[2];          // TMA descriptors of both buffers
-    bool tma_ok = false;
-    int rounding = 0;                            // goc_exec.rounding
-    int scheme = 0;                              // goc_exec.scheme
-    // launch configuration (results are bitwise the same under every choice):
-    // tile queue (dynamic) or static tile order, programmatic dependent launch
-    int cfg_dynamic = 1, cfg_pdl = 1;
-    int cfg_balanced = 0;                        // grid: the fewest blocks taking the same rounds of tiles
-    bool tuned = false;                          // chosen by the launch autotuner (or fixed)
-    int plateau_checks = 0;                      // goc_exec.plateau_checks
-    // per-row storage reference (16-bit storage on straight grids; see goc_aux.cuh)
-    double *ref64 = nullptr;                     // FP64 master rows [3][ny] (A1, Bref_1, Bref_2), then the next rows
-    float *reft = nullptr;                       // FP32 tables u1r [ny], brow [2][ny], bpull [4][ny]
-    int ref_every = 0;                           // steps between refreshes (0: the reference stays as created)
-    long long ref_next = 0;                      // step count at which the next refresh is due
-    // slab of a larger lattice (goc_create_slab): global rows [slab_r0, slab_r1)
-    // owned, slab_glo / slab_ghi ghost rows below / above them
-    bool slab = false;
-    int slab_r0 = 0, slab_r1 = 0, slab_glo = 0, slab_ghi = 0;
-};
+goc_status goc_fail(goc_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return fail(st, "%s", buf);
+}
+
 
 namespace {
 
@@ -198,88 +117,6 @@ bool encode_lattice_maps(goc_lattice *L) {
     return ok;
 }
 
-// Dynamic shared memory of a step kernel and its persistent grid size.
-template <class S, bool MHD, bool SRT = false, int GEOM = 0>
-int step_grid(int ntiles, size_t *smem, bool balanced = false) {
-    using T = Tiling<S>;
-    const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
-    *smem = bytes;
-    static int cached = -1;
-    if (cached < 0) {
-        cudaFuncSetAttribute(step_kernel<S, MHD, SRT, GEOM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD, SRT, GEOM>, NT, bytes);
-        cached = std::max(1, sms * std::max(1, per));
-    }
-    if (balanced) {   // the fewest blocks that take the same number of rounds of tiles: equal shares
-        const int rounds = (ntiles + cached - 1) / cached;
-        return (ntiles + rounds - 1) / rounds;
-    }
-    return std::min(ntiles, cached);
-}
-
-template <class S>
-goc_status launch_std_t(goc_lattice *L, const StepParams &p) {
-    dim3 grid((L->nx + STD_BX - 1) / STD_BX, (L->ny + STD_BY - 1) / STD_BY), block(STD_BX, STD_BY);
-    CU(launch_pdl(L->cfg_pdl != 0, std_step_kernel<S>, grid, block, 0, L->stream, p));
-    return GOC_OK;
-}
-
-// Curved grids (GEOM 1, 2): the step kernel for the lattice's collision
-// (central moments, or raw moments for schemes 2 and 3) and MIE setting.
-template <class S, int GEOM>
-cudaError_t launch_geom(goc_lattice *L, const StepParams &p, int ntiles) {
-    size_t smem = 0;
-    const bool pdl = L->cfg_pdl != 0, raw = L->scheme == 2 || L->scheme == 3;
-    const dim3 block(TX, TYT);
-    if (L->mhd.enabled && raw) {
-        const int grid = step_grid<S, true, true, GEOM>(ntiles, &smem, L->cfg_balanced != 0);
-        return launch_pdl(pdl, step_kernel<S, true, true, GEOM>, dim3(grid), block, smem, L->stream, p);
-    }
-    if (L->mhd.enabled) {
-        const int grid = step_grid<S, true, false, GEOM>(ntiles, &smem, L->cfg_balanced != 0);
-        return launch_pdl(pdl, step_kernel<S, true, false, GEOM>, dim3(grid), block, smem, L->stream, p);
-    }
-    if (raw) {
-        const int grid = step_grid<S, false, true, GEOM>(ntiles, &smem, L->cfg_balanced != 0);
-        return launch_pdl(pdl, step_kernel<S, false, true, GEOM>, dim3(grid), block, smem, L->stream, p);
-    }
-    const int grid = step_grid<S, false, false, GEOM>(ntiles, &smem, L->cfg_balanced != 0);
-    return launch_pdl(pdl, step_kernel<S, false, false, GEOM>, dim3(grid), block, smem, L->stream, p);
-}
-
-template <class S>
-goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
-    if (L->scheme == 1) return launch_std_t<S>(L, p);
-    const int ntiles = ((L->nx + TX - 1) / TX) * ((L->ny + TY - 1) / TY);
-    size_t smem = 0;
-    const bool pdl = L->cfg_pdl != 0;
-    if (L->sp.curv == 2) {   // node-table metric
-        const cudaError_t e = launch_geom<S, 2>(L, p, ntiles);
-        CU(e);
-    } else if (L->sp.curv) {   // curvilinear column metric
-        const cudaError_t e = launch_geom<S, 1>(L, p, ntiles);
-        CU(e);
-    } else if (L->scheme == 2 || L->scheme == 3) {   // collision on raw moments (Appendix F SRT, Appendix D MRT)
-        if (L->mhd.enabled) {
-            const int grid = step_grid<S, true, true>(ntiles, &smem, L->cfg_balanced != 0);
-            CU(launch_pdl(pdl, step_kernel<S, true, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
-        } else {
-            const int grid = step_grid<S, false, true>(ntiles, &smem, L->cfg_balanced != 0);
-            CU(launch_pdl(pdl, step_kernel<S, false, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
-        }
-    } else if (L->mhd.enabled) {
-        const int grid = step_grid<S, true>(ntiles, &smem, L->cfg_balanced != 0);
-        CU(launch_pdl(pdl, step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
-    } else {
-        const int grid = step_grid<S, false>(ntiles, &smem, L->cfg_balanced != 0);
-        CU(launch_pdl(pdl, step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
-    }
-    CU(cudaGetLastError());
-    return GOC_OK;
-}
 
 StepParams params_for(goc_lattice *L, int src, float *uout) {
     StepParams p = L->sp;
@@ -1800,50 +1637,10 @@ long long l2_set_bytes(int device) {
     return l2 > 0 ? 3LL * l2 / 4 : (1LL << 62);
 }
 
-template <class S, bool MHD, int GEOM>
-int persistent_grid_t(int total, int *stage_bytes) {
-    using T = Tiling<S>;
-    const int stage = MHD ? T::STAGE_MHD : T::STAGE_NSE;
-    *stage_bytes = stage;
-    static int cached = -1;
-    if (cached < 0) {
-        cudaFuncSetAttribute(batch_step_kernel<S, MHD, GEOM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * stage);
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S, MHD, GEOM>, NT, 2 * (size_t)stage);
-        cached = std::max(1, sms * std::max(1, per));
-    }
-    return std::min(total, cached);
-}
 
 // Kernel type of a batch group: storage (3) x MIE (2) x grid kind (straight,
 // annular sector, node table); one batch kernel instantiation each.
 int batch_key(int storage, int mhd, int geom) { return (geom * 3 + storage) * 2 + mhd; }
-
-template <int GEOM>
-int persistent_grid_g(int storage, int mhd, int *stage_bytes) {
-    switch (2 * storage + mhd) {
-        case 2: return persistent_grid_t<__half, false, GEOM>(1 << 30, stage_bytes);
-        case 3: return persistent_grid_t<__half, true, GEOM>(1 << 30, stage_bytes);
-        case 4: return persistent_grid_t<__nv_bfloat16, false, GEOM>(1 << 30, stage_bytes);
-        case 5: return persistent_grid_t<__nv_bfloat16, true, GEOM>(1 << 30, stage_bytes);
-        case 1: return persistent_grid_t<float, true, GEOM>(1 << 30, stage_bytes);
-        default: return persistent_grid_t<float, false, GEOM>(1 << 30, stage_bytes);
-    }
-}
-
-template <int GEOM>
-cudaError_t batch_launch_g(int storage, int mhd, dim3 gd, dim3 bd, size_t smem, cudaStream_t st, const BatchArgs &a) {
-    switch (2 * storage + mhd) {
-        case 2: return launch_pdl(true, batch_step_kernel<__half, false, GEOM>, gd, bd, smem, st, a);
-        case 3: return launch_pdl(true, batch_step_kernel<__half, true, GEOM>, gd, bd, smem, st, a);
-        case 4: return launch_pdl(true, batch_step_kernel<__nv_bfloat16, false, GEOM>, gd, bd, smem, st, a);
-        case 5: return launch_pdl(true, batch_step_kernel<__nv_bfloat16, true, GEOM>, gd, bd, smem, st, a);
-        case 1: return launch_pdl(true, batch_step_kernel<float, true, GEOM>, gd, bd, smem, st, a);
-        default: return launch_pdl(true, batch_step_kernel<float, false, GEOM>, gd, bd, smem, st, a);
-    }
-}
 
 goc_status rebuild(goc_batch *B) {
     free_groups(B);
@@ -1878,9 +1675,9 @@ goc_status rebuild(goc_batch *B) {
             g.total += tiles[m];
         }
         int capacity = 0;   // resident blocks of this kernel on the device
-        capacity = g.geom == 2 ? persistent_grid_g<2>(g.storage, g.mhd, &g.stage_bytes)
-                   : g.geom == 1 ? persistent_grid_g<1>(g.storage, g.mhd, &g.stage_bytes)
-                                 : persistent_grid_g<0>(g.storage, g.mhd, &g.stage_bytes);
+        capacity = g.storage == GOC_FP16_DEV   ? batch_grid_t<__half>(g.mhd, g.geom, &g.stage_bytes)
+                   : g.storage == GOC_BF16_DEV ? batch_grid_t<__nv_bfloat16>(g.mhd, g.geom, &g.stage_bytes)
+                                               : batch_grid_t<float>(g.mhd, g.geom, &g.stage_bytes);
         g.grid = std::min(g.total, capacity);   // persistent blocks taking tiles from the counter
         g.args.assign(7, BatchArgs{});
         CU(cudaMalloc(&g.ctr, 2 * sizeof(int)));
@@ -1940,9 +1737,9 @@ goc_status batch_launch(goc_batch *B, cudaStream_t st, long long s, bool first =
         const size_t smem = 2 * (size_t)g.stage_bytes;
         const dim3 gd(g.grid), bd(TX, TYT);
         cudaError_t e;
-        e = g.geom == 2 ? batch_launch_g<2>(g.storage, g.mhd, gd, bd, smem, st, a)
-            : g.geom == 1 ? batch_launch_g<1>(g.storage, g.mhd, gd, bd, smem, st, a)
-                          : batch_launch_g<0>(g.storage, g.mhd, gd, bd, smem, st, a);
+        e = g.storage == GOC_FP16_DEV   ? batch_launch_t<__half>(g.mhd, g.geom, gd, bd, smem, st, a)
+            : g.storage == GOC_BF16_DEV ? batch_launch_t<__nv_bfloat16>(g.mhd, g.geom, gd, bd, smem, st, a)
+                                        : batch_launch_t<float>(g.mhd, g.geom, gd, bd, smem, st, a);
         CU(e);
         CU(cudaGetLastError());
     }
