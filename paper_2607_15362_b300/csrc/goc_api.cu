@@ -865,8 +865,8 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
         if (L->mhd.enabled) TRY(dalloc(L, &L->g[b], 10 * L->plane * es + guard_tail(L)));
     }
     const bool curv = map->kind[0] == GOC_MAP_ANNULUS;
-    TRY(dalloc(L, &L->tab1, (curv ? 8 : 7) * (size_t)L->nx * sizeof(float)));
-    TRY(dalloc(L, &L->tab2, 7 * (size_t)L->ny * sizeof(float)));
+    TRY(dalloc(L, &L->tab1, 16 * (size_t)L->nx * sizeof(float)));   // 8 rows, then the per-index records
+    TRY(dalloc(L, &L->tab2, 16 * (size_t)L->ny * sizeof(float)));
     TRY(dalloc(L, &L->m1, (curv ? 4 : 2) * (size_t)(L->nx + 2) * sizeof(double)));
     TRY(dalloc(L, &L->m2, 2 * (size_t)(L->ny + 2) * sizeof(double)));
     TRY(dalloc(L, &L->flag, 8 * sizeof(int)));   // [0] status, [1] spare, [2..3] step counters, [4..5] tile queues of the two parities
@@ -962,6 +962,8 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
                                                                        rho0cs2, L->cs2, L->tab1);
     axis_tables_kernel<<<(L->ny + 127) / 128, 128, 0, L->stream>>>(L->m2, L->m2 + L->ny + 2, L->ny, per_y, rho0cs2,
                                                                    L->cs2, L->tab2);
+    axis_records_kernel<<<(L->nx + 127) / 128, 128, 0, L->stream>>>(L->tab1, L->nx);
+    axis_records_kernel<<<(L->ny + 127) / 128, 128, 0, L->stream>>>(L->tab2, L->ny);
     if (table) {   // node-table metric: FP32 planes + walls for the step (and the initial state), the
                    // link corrections formed in FP64 from a temporary device copy of the table
         const long long N = (long long)L->nx * L->ny;
@@ -1609,6 +1611,7 @@ long long estimate_bytes(const goc_grid *grid, const goc_map *map, const goc_mhd
     long long b = 2 * (9 + 2) * plane * es;
     if (mhd && mhd->enabled) b += 2 * 10 * plane * es;
     b += 8LL * 4 * (grid->nx + grid->ny) + 32LL * (grid->nx + grid->ny + 4) + 128;
+    b += 36LL * (grid->nx + grid->ny);   // spare table row and per-index metric records
     if (map && map->kind[0] == GOC_MAP_TABLE)   // node-table metric planes and wall factors
         b += (10 * plane + 8LL * std::max(grid->nx, grid->ny)) * 4;
     if (storage != GOC_FP32) b += 6LL * 8 * grid->ny + 7LL * 4 * grid->ny;   // per-row storage reference

@@ -583,4 +583,15 @@ __global__ void residual_kernel(const float *a, const float *b, long long plane,
     block_add<4>(acc, out);
 }
 
+// Per-index metric records of an axis from its table rows (h, ih, th, rm,
+// rp, dm, dp of n values each), written after the table's 8 rows:
+// rec[2k] = (h, ih, th, rm), rec[2k + 1] = (rp, dm, dp, 0).
+__global__ void axis_records_kernel(float *tab, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float4 *rec = reinterpret_cast<float4 *>(tab + 8 * (size_t)n);
+    rec[2 * k] = make_float4(tab[k], tab[n + k], tab[2 * n + k], tab[3 * n + k]);
+    rec[2 * k + 1] = make_float4(tab[4 * n + k], tab[5 * n + k], tab[6 * n + k], 0.f);
+}
+
 }  // namespace goc

@@ -33,11 +33,19 @@ struct Axis {
     const float *rp;   // rest-state pull correction, source k+1: 0.5 rho0 cs2 (1/h(k+1) - 1/h(k))
     const float *dm;   // MIE pull corrections, source k-1: W1 (h(k-1) - h(k)) + csm2 (h^2 theta(k-1) + h^2 theta(k))/4
     const float *dp;   //                      source k+1: W1 (h(k+1) - h(k)) - csm2 (h^2 theta(k+1) + h^2 theta(k))/4
+    // The table holds 8 rows of n values (7 on straight grids, plus a spare
+    // row), then the same quantities per node index as records of two float4,
+    // (h, ih, th, rm), (rp, dm, dp, 0), at h + 8 n (see axis_records).
     // Curvilinear column metric (annular sector; xi1 axis): rm/rp hold the
     // full pull corrections of links 1/3 (not per unit h2), and the rows dm,
     // dp, dp + n hold h2, 1/h2 and theta21 as functions of xi1 (the MIE then
     // stores its populations without a reference field and needs no dm/dp).
 };
+
+// the per-index records of an axis table of n entries
+__device__ __forceinline__ const float4 *axis_records(const Axis &a, int n) {
+    return reinterpret_cast<const float4 *>(a.h + 8 * (size_t)n);
+}
 
 // the node-by-node metric (StepParams.gm): plane k at node (i, j), and the
 // wall metric at position k along wall `side` (0-3: the wall-normal factor at

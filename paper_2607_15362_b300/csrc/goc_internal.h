@@ -64,7 +64,7 @@ struct goc_lattice {
     void *f[2] = {nullptr, nullptr};
     void *F[2] = {nullptr, nullptr};
     void *g[2] = {nullptr, nullptr};
-    float *tab1 = nullptr, *tab2 = nullptr;      // [7][nx], [7][ny]
+    float *tab1 = nullptr, *tab2 = nullptr;      // [8][nx] + records [nx][8], [8][ny] + records [ny][8]
     double *m1 = nullptr, *m2 = nullptr;         // FP64 h, theta per axis: [2][n+2]
     float *gm = nullptr;                         // node-table metric: [10][plane] + [4][max(nx, ny)]
     float *uout[2] = {nullptr, nullptr};

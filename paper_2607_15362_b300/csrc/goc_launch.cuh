@@ -8,32 +8,59 @@
 #include <algorithm>
 
 #include "goc_internal.h"
+#include "goc_lean.cuh"
 #include "goc_std.cuh"
 
 using namespace goc;
 
 namespace {
 
-// Dynamic shared memory of a step kernel and its persistent grid size.
+// Persistent grid size of a tiled step kernel: resident blocks per SM x SMs
+// (found once per kernel, `cached`), or with `balanced` the fewest blocks that
+// take the same number of rounds of tiles (equal shares).
+template <class K>
+int persistent_grid(K kern, size_t bytes, int ntiles, bool balanced, int &cached) {
+    if (cached < 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, bytes);
+        cached = std::max(1, sms * std::max(1, per));
+    }
+    if (balanced) {
+        const int rounds = (ntiles + cached - 1) / cached;
+        return (ntiles + rounds - 1) / rounds;
+    }
+    return std::min(ntiles, cached);
+}
+
+// Dynamic shared memory of a step kernel (two stages) and its persistent grid size.
 template <class S, bool MHD, bool SRT = false, int GEOM = 0>
 int step_grid(int ntiles, size_t *smem, bool balanced = false) {
     using T = Tiling<S>;
     const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
     *smem = bytes;
     static int cached = -1;
-    if (cached < 0) {
-        cudaFuncSetAttribute(step_kernel<S, MHD, SRT, GEOM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<S, MHD, SRT, GEOM>, NT, bytes);
-        cached = std::max(1, sms * std::max(1, per));
-    }
-    if (balanced) {   // the fewest blocks that take the same number of rounds of tiles: equal shares
-        const int rounds = (ntiles + cached - 1) / cached;
-        return (ntiles + rounds - 1) / rounds;
-    }
-    return std::min(ntiles, cached);
+    return persistent_grid(step_kernel<S, MHD, SRT, GEOM>, bytes, ntiles, balanced, cached);
+}
+
+// The same for the straight-grid kernel lean_step_kernel.
+template <class S, bool MHD>
+int lean_grid(int ntiles, size_t *smem, bool balanced = false) {
+    using T = Tiling<S>;
+    const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
+    *smem = bytes;
+    static int cached = -1;
+    return persistent_grid(lean_step_kernel<S, MHD>, bytes, ntiles, balanced, cached);
+}
+
+// Straight grids with the central-moment collision run lean_step_kernel
+// unless GOC_GENERAL_KERNEL is set (the general tile path of step_kernel, for
+// comparisons).
+inline bool lean_enabled() {
+    static const bool on = std::getenv("GOC_GENERAL_KERNEL") == nullptr;
+    return on;
 }
 
 template <class S>
@@ -113,6 +140,12 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
             const int grid = step_grid<S, false, true>(ntiles, &smem, L->cfg_balanced != 0);
             CU(launch_pdl(pdl, step_kernel<S, false, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
         }
+    } else if (lean_enabled() && L->mhd.enabled) {
+        const int grid = lean_grid<S, true>(ntiles, &smem, L->cfg_balanced != 0);
+        CU(launch_pdl(pdl, lean_step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+    } else if (lean_enabled()) {
+        const int grid = lean_grid<S, false>(ntiles, &smem, L->cfg_balanced != 0);
+        CU(launch_pdl(pdl, lean_step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
     } else if (L->mhd.enabled) {
         const int grid = step_grid<S, true>(ntiles, &smem, L->cfg_balanced != 0);
         CU(launch_pdl(pdl, step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));

@@ -1,0 +1,210 @@
+// goc_lean.cuh -- the step kernel for straight grids (h1 = h1(xi1), h2 =
+// h2(xi2): every grid of Sec. 6 and 7) with the central-moment collision:
+// the same time step as step_kernel<S, MHD, false, 0> (Appendix E Steps 1-7,
+// Appendix G with the MIE), organised to spend fewer instructions per node on
+// everything around the collision.
+//
+//   * The metric of a column or a row is one 32-byte record (h, 1/h, theta,
+//     the two pull corrections; float4 pairs, two vector loads) instead of
+//     five loads from five tables.
+//   * Interior tiles (every pull source and the fields halo inside the
+//     lattice) take a path whose shared-memory addresses are fixed offsets
+//     from one per-thread base, with the ring of halo nodes laid out once per
+//     thread; tiles next to a wall or across a periodic seam take the general
+//     tile path of goc_step.cuh.
+//   * The post-collision values of one node are stored through one 64-bit
+//     address per buffer and per-plane offsets kept for the whole launch.
+#pragma once
+
+#include "goc_step.cuh"
+
+namespace goc {
+
+// Metric record of node index k along an axis: rec[2k] = (h, 1/h, theta, rm),
+// rec[2k + 1] = (rp, dm, dp, 0) (the rows of the per-axis tables, see Axis).
+struct AxisRecord {
+    float h, ih, th, rm, rp, dm, dp;
+};
+__device__ __forceinline__ AxisRecord axis_record(const float4 *rec, int k) {
+    const float4 a = __ldg(rec + 2 * k), b = __ldg(rec + 2 * k + 1);
+    return AxisRecord{a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+}
+
+// Pull of the nine deviations arriving at an interior node whose stored value
+// of link 0 sits at s (all sources inside the staged box), with the rest-state
+// pull corrections of links 1..4 (rm/rp of the node's column and row).
+template <class S>
+__device__ __forceinline__ void lean_pull(const S *s, float sf, const AxisRecord &c, const AxisRecord &r,
+                                          float d[9]) {
+    using T = Tiling<S>;
+    constexpr int BX = T::BX, PL = T::BX * T::BY;
+    d[0] = scl<S>(Store<S>::lds(s), sf);
+    d[1] = fmaf(r.h, c.rm, scl<S>(Store<S>::lds(s + PL - 1), sf));            // source (i-1, j)
+    d[2] = fmaf(c.h, r.rm, scl<S>(Store<S>::lds(s + 2 * PL - BX), sf));       // (i, j-1)
+    d[3] = fmaf(r.h, c.rp, scl<S>(Store<S>::lds(s + 3 * PL + 1), sf));        // (i+1, j)
+    d[4] = fmaf(c.h, r.rp, scl<S>(Store<S>::lds(s + 4 * PL + BX), sf));       // (i, j+1)
+    d[5] = scl<S>(Store<S>::lds(s + 5 * PL - BX - 1), sf);                    // (i-1, j-1)
+    d[6] = scl<S>(Store<S>::lds(s + 6 * PL - BX + 1), sf);                    // (i+1, j-1)
+    d[7] = scl<S>(Store<S>::lds(s + 7 * PL + BX + 1), sf);                    // (i+1, j+1)
+    d[8] = scl<S>(Store<S>::lds(s + 8 * PL + BX - 1), sf);                    // (i-1, j+1)
+}
+
+// One interior tile: the fields of the tile and of its ring (halo of one
+// node) from the staged populations, then the collision of each node.  Every
+// thread of the block calls it (it contains the fields barrier).  st: the
+// stage (populations, then the stored force at Tiling<S>::OFF_FF).
+template <class S, bool MHD>
+__device__ __forceinline__ bool lean_tile(const StepParams &p, const unsigned char *st, int i0, int j0,
+                                          FieldSmem &sm, bool ok) {
+    using T = Tiling<S>;
+    constexpr bool REF = Store<S>::scaled;                // per-row storage reference (16-bit storage)
+    constexpr int BX = T::BX, BAND = TX + 2, RING = 2 * BAND + 2 * TY;
+    const S *sf_ = reinterpret_cast<const S *>(st);
+    const S *sF_ = reinterpret_cast<const S *>(st + T::OFF_FF);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int i = i0 + tx, j = j0 + ty;
+    const float4 *rec1 = axis_records(p.ax1, p.nx), *rec2 = axis_records(p.ax2, p.ny);
+    const AxisRecord c = axis_record(rec1, i), r = axis_record(rec2, j);
+    // own node
+    const int so = (ty + HYS) * BX + tx + T::HXS;
+    float d[9], drho, U1, U2;
+    const float ur1 = REF ? GOC_U1R(p, j) : 0.f;
+    lean_pull<S>(sf_ + so, p.sf, c, r, d);
+    const float F1p = scl<S>(Store<S>::lds(sF_ + so), p.sF);
+    const float F2p = scl<S>(Store<S>::lds(sF_ + T::BX * T::BY + so), p.sF);
+    fields_from<REF>(p, d, F1p, F2p, c.ih, r.ih, drho, U1, U2, ur1);
+    sm.rho[ty + MH][tx + MH] = drho;
+    sm.u1[ty + MH][tx + MH] = U1;
+    sm.u2[ty + MH][tx + MH] = U2;
+    // ring: rows -1 and TY (columns -1..TX), columns -1 and TX (rows 0..TY-1),
+    // one node per thread from the last thread down (warp 0 also stages the
+    // next tile)
+    {
+        const int q = NT - 1 - tid;
+        if (q < RING) {
+            int x, y;
+            if (q < 2 * BAND) {
+                y = q < BAND ? -1 : TY;
+                x = (q < BAND ? q : q - BAND) - 1;
+            } else {
+                const int b = q - 2 * BAND;
+                x = b < TY ? -1 : TX;
+                y = b < TY ? b : b - TY;
+            }
+            const AxisRecord cq = axis_record(rec1, i0 + x), rq = axis_record(rec2, j0 + y);
+            const int sq = (y + HYS) * BX + x + T::HXS;
+            float dd[9], a, u, v;
+            lean_pull<S>(sf_ + sq, p.sf, cq, rq, dd);
+            fields_from<REF>(p, dd, scl<S>(Store<S>::lds(sF_ + sq), p.sF),
+                             scl<S>(Store<S>::lds(sF_ + T::BX * T::BY + sq), p.sF), cq.ih, rq.ih, a, u, v,
+                             REF ? GOC_U1R(p, j0 + y) : 0.f);
+            sm.rho[y + MH][x + MH] = a;
+            sm.u1[y + MH][x + MH] = u;
+            sm.u2[y + MH][x + MH] = v;
+        }
+    }
+    if (!__syncthreads_and(ok)) return false;
+    // central second-order differences (interior)
+    const int ex = tx + MH, ey = ty + MH;
+    const float fl[7][1] = {{drho}, {U1}, {U2},
+                            {0.5f * (sm.u1[ey][ex + 1] - sm.u1[ey][ex - 1])},
+                            {0.5f * (sm.rho[ey][ex + 1] - sm.rho[ey][ex - 1])},
+                            {0.5f * (sm.u2[ey + 1][ex] - sm.u2[ey - 1][ex])},
+                            {0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex])}};
+    const int jj[1] = {j};
+    const bool own[1] = {true};
+    const float dn[1][9] = {{d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], d[8]}};
+    const float F1n[1] = {F1p}, F2n[1] = {F2p}, h2n[1] = {r.h}, ih2n[1] = {r.ih}, urn[1] = {ur1};
+    SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
+                     p.plane, p.pitch, p.sf, p.sF, p.sg};
+    collide<S, MHD, false, float, false, 0>(p, src, i, jj, own, dn, F1n, F2n, c.h, c.ih, h2n, ih2n, fl, urn);
+    return true;
+}
+
+template <class S, bool MHD>
+__device__ __forceinline__ bool lean_run_tile(const StepParams &p, int kind, int i0, int j0,
+                                              const unsigned char *stage, FieldSmem &sm, bool ok) {
+    if (kind == 0 && !p.nopull) return lean_tile<S, MHD>(p, stage, i0, j0, sm, ok);   // (the first step
+                                                                                       // reads f^0 in place)
+    return run_tile<S, MHD, false, 0>(p, kind, i0, j0, stage, sm, ok);
+}
+
+// Single lattice on a straight grid: persistent blocks take tiles from the
+// lattice's queue, as step_kernel does.
+template <class S, bool MHD>
+__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
+    lean_step_kernel(const __grid_constant__ StepParams p) {
+    using T = Tiling<S>;
+    constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ FieldSmem sm;
+    __shared__ int4 s_item[2];
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    if (leader) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    griddep_launch_dependents();
+    griddep_wait();
+    if (leader && blockIdx.x == 0) {
+        if (Store<S>::scaled && p.sr) *p.seed_wr = *p.seed_rd + 1u;
+        if (p.tctr) *p.tctr_next = 0;
+    }
+    const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
+    int *ctr = p.tctr;
+    const int first = blockIdx.x, stride = gridDim.x;
+    const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + TY - 1) / TY, ntiles = ntx * nty;
+    auto take = [&](int stg, int t) {
+        int4 it = make_int4(t, 0, 0, 0);
+        if (t < ntiles) {
+            it.y = (t % ntx) * TX;
+            it.z = (t / ntx) * TY;
+            it.w = tile_kind<S>(p, it.y, it.z);
+            if (it.w != 2) {
+                fence_proxy_async();
+                issue_tile<S>(m, it.y, it.z, dyn + stg * STAGE, &bars[stg], MHD);
+            }
+        }
+        s_item[stg] = it;
+    };
+    constexpr bool AHEAD = !MHD;
+    int pend = 0;
+    if (leader) {
+        if (ctr && AHEAD) pend = atomicAdd(ctr, 1);
+        take(0, first);
+    }
+    __syncthreads();
+    uint32_t ph0 = 0, ph1 = 0;
+    int stage = 0;
+    for (;;) {
+        const int4 it = s_item[stage];
+        const int t = it.x;
+        if (t >= ntiles) break;
+        if (leader) {
+            int nt = t + stride;
+            if (ctr && AHEAD) {
+                nt = stride + pend;
+                pend = atomicAdd(ctr, 1);
+            } else if (ctr) {
+                nt = stride + atomicAdd(ctr, 1);
+            }
+            take(stage ^ 1, nt);
+        }
+        bool ok = true;
+        if (it.w != 2) {
+            uint32_t &ph = stage ? ph1 : ph0;
+            ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
+            ph ^= 1;
+        }
+        if (MHD) {
+            if (!__syncthreads_and(ok)) return;
+        }
+        if (!lean_run_tile<S, MHD>(p, it.w, it.y, it.z, dyn + stage * STAGE, sm, ok)) return;
+        __syncthreads();
+        stage ^= 1;
+    }
+}
+
+}  // namespace goc
