@@ -204,6 +204,42 @@ __device__ __forceinline__ uint32_t node_seed(uint32_t idx, uint32_t step) {
     return h;
 }
 
+// Two values to a 16-bit format in one conversion, packed as (a << 16) | b:
+// with sr stochastically rounded by the hardware (cvt.rs: random bits 31..16
+// round a, bits 15..0 round b; each rounds away from zero with probability
+// equal to the discarded fraction), else rounded to nearest.
+template <class S> __device__ __forceinline__ uint32_t cvt2(float a, float b, bool sr, uint32_t rbits);
+template <> __device__ __forceinline__ uint32_t cvt2<__half>(float a, float b, bool sr, uint32_t rbits) {
+    uint32_t d;
+    if (sr) asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+    else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(a), "f"(b));
+    return d;
+}
+template <> __device__ __forceinline__ uint32_t cvt2<__nv_bfloat16>(float a, float b, bool sr, uint32_t rbits) {
+    uint32_t d;
+    if (sr) asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+    else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(a), "f"(b));
+    return d;
+}
+// 32 random bits for one cvt2: the high halves of the next two LCG outputs
+// (the low bits of an LCG have short periods)
+__device__ __forceinline__ uint32_t rand_pair_bits(uint32_t &r) {
+    const uint32_t w1 = lcg_next(r), w2 = lcg_next(r);
+    return __byte_perm(w1, w2, 0x3276);   // (w1 & 0xffff0000) | (w2 >> 16)
+}
+// Store the two halves of a cvt2 result (pb may be null: the low half is dropped).
+template <class S> __device__ __forceinline__ void st_pair(S *pa, S *pb, uint32_t d) {
+    asm volatile("st.global.cg.b16 [%0], %1;" ::"l"(pa), "h"((unsigned short)(d >> 16)) : "memory");
+    if (pb) asm volatile("st.global.cg.b16 [%0], %1;" ::"l"(pb), "h"((unsigned short)(d & 0xffffu)) : "memory");
+}
+// a and b (unscaled) stored at pa and pb through one cvt2, the random bits
+// drawn from r when stochastic rounding is on
+template <class S>
+__device__ __forceinline__ void put2(S *pa, S *pb, float a, float b, bool sr, uint32_t &r) {
+    const uint32_t rb = sr ? rand_pair_bits(r) : 0u;
+    st_pair<S>(pa, pb, cvt2<S>(a, b, sr, rb));
+}
+
 // store of one value: stochastic rounding for 16-bit storage when asked for
 template <class S>
 __device__ __forceinline__ void put(S *p, float v, bool sr, uint32_t &r) {

@@ -117,7 +117,8 @@ __device__ __forceinline__ bool lean_tile(const StepParams &p, const unsigned ch
     const float F1n[1] = {F1p}, F2n[1] = {F2p}, h2n[1] = {r.h}, ih2n[1] = {r.ih}, urn[1] = {ur1};
     SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                      p.plane, p.pitch, p.sf, p.sF, p.sg};
-    collide<S, MHD, false, float, false, 0>(p, src, i, jj, own, dn, F1n, F2n, c.h, c.ih, h2n, ih2n, fl, urn);
+    const float th[2] = {c.th, r.th};
+    collide<S, MHD, false, float, false, 0>(p, src, i, jj, own, dn, F1n, F2n, c.h, c.ih, h2n, ih2n, fl, urn, th);
     return true;
 }
 

@@ -472,20 +472,23 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
                                         const bool (&own)[Lanes<V>::R], const float (&dn)[Lanes<V>::R][9],
                                         const float (&F1pn)[Lanes<V>::R], const float (&F2pn)[Lanes<V>::R], float h1,
                                         float ih1, const float (&h2n)[Lanes<V>::R], const float (&ih2n)[Lanes<V>::R],
-                                        const float (&fl)[7][Lanes<V>::R], const float (&ur1n)[Lanes<V>::R]) {
+                                        const float (&fl)[7][Lanes<V>::R], const float (&ur1n)[Lanes<V>::R],
+                                        const float *th_given = nullptr) {
+    // th_given (straight grids, one node per thread): theta11, theta22 of the
+    // node, already loaded by the caller
     constexpr int R = Lanes<V>::R;
     constexpr bool REF = Store<S>::scaled && GEOM == 0;   // per-row storage reference
     float th_[R];
 #pragma unroll
     for (int r = 0; r < R; r++)   // theta22
         th_[r] = GEOM == 2 ? gm_at(p.gm, p.plane, p.pitch, 5, i, own[r] ? j[r] : j[0])
-                           : (GEOM ? 0.f : p.ax2.th[own[r] ? j[r] : j[0]]);
+                           : (GEOM ? 0.f : (th_given ? th_given[1] : p.ax2.th[own[r] ? j[r] : j[0]]));
     const V drho = pack<V>(fl[0]), U1 = pack<V>(fl[1]), U2 = pack<V>(fl[2]);
     const V dU1 = pack<V>(fl[3]), dr1 = pack<V>(fl[4]), dU2 = pack<V>(fl[5]), dr2 = pack<V>(fl[6]);
     const V t22 = pack<V>(th_);
     const V h2 = pack<V>(h2n), ih2 = pack<V>(ih2n), F1p = pack<V>(F1pn), F2p = pack<V>(F2pn);
     static_assert(GEOM != 2 || R == 1, "the node-table metric runs one node per thread");
-    const float t11 = GEOM == 2 ? gm_at(p.gm, p.plane, p.pitch, 2, i, j[0]) : p.ax1.th[i];
+    const float t11 = GEOM == 2 ? gm_at(p.gm, p.plane, p.pitch, 2, i, j[0]) : (th_given ? th_given[0] : p.ax1.th[i]);
     V d[9];
 #pragma unroll
     for (int a = 0; a < 9; a++) {
@@ -632,13 +635,26 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
                 Sa[1] = Sa[2] = Sa[3] = Sa[4] = s1;
                 Sa[0] = fmav(s1, -4.f, ys);
             }
+            V gt[5];
 #pragma unroll
             for (int a = 0; a < 5; a++) {
-                V gt = fmav(a == 0 ? q0 : Geq[a] - gd[c][a], p.itaum, gd[c][a]);
-                if constexpr (GEOM) gt = gt + Sa[a];
+                gt[a] = fmav(a == 0 ? q0 : Geq[a] - gd[c][a], p.itaum, gd[c][a]);
+                if constexpr (GEOM) gt[a] = gt[a] + Sa[a];
+            }
 #pragma unroll
-                for (int r = 0; r < R; r++)
-                    if (own[r]) put<S>(gout + (c * 5 + a) * p.plane + idx[r], scl<S>(lane(gt, r), p.isg), sr, rng[r]);
+            for (int r = 0; r < R; r++) {
+                if (!own[r]) continue;
+                S *go = gout + c * 5 * p.plane + idx[r];
+                if constexpr (Store<S>::scaled) {   // pairs through one conversion each
+                    const float is = p.isg;
+                    const long long pl = p.plane;
+                    put2<S>(go, go + pl, lane(gt[0], r) * is, lane(gt[1], r) * is, sr, rng[r]);
+                    put2<S>(go + 2 * pl, go + 3 * pl, lane(gt[2], r) * is, lane(gt[3], r) * is, sr, rng[r]);
+                    put2<S>(go + 4 * pl, static_cast<S *>(nullptr), lane(gt[4], r) * is, 0.f, sr, rng[r]);
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 5; a++) put<S>(go + a * p.plane, scl<S>(lane(gt[a], r), p.isg), sr, rng[r]);
+                }
             }
         }
     }
@@ -841,10 +857,20 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
 #pragma unroll
     for (int q = 0; q < R; q++) {
         if (!own[q]) continue;
+        if constexpr (Store<S>::scaled) {   // pairs through one conversion each
+            S *fo = fout + idx[q], *Fo = Fout + idx[q];
+            const long long pl = p.plane;
+            const float is = p.isf;
 #pragma unroll
-        for (int a = 0; a < 9; a++) put<S>(fout + a * p.plane + idx[q], scl<S>(lane(o[a], q), p.isf), sr, rng[q]);
-        put<S>(Fout + idx[q], scl<S>(lane(F1dev, q), p.isF), sr, rng[q]);
-        put<S>(Fout + p.plane + idx[q], scl<S>(lane(F2dev, q), p.isF), sr, rng[q]);
+            for (int a = 0; a < 8; a += 2)
+                put2<S>(fo + a * pl, fo + (a + 1) * pl, lane(o[a], q) * is, lane(o[a + 1], q) * is, sr, rng[q]);
+            put2<S>(fo + 8 * pl, Fo, lane(o[8], q) * is, lane(F1dev, q) * p.isF, sr, rng[q]);
+            put2<S>(Fo + pl, static_cast<S *>(nullptr), lane(F2dev, q) * p.isF, 0.f, sr, rng[q]);
+        } else {
+            for (int a = 0; a < 9; a++) put<S>(fout + a * p.plane + idx[q], scl<S>(lane(o[a], q), p.isf), sr, rng[q]);
+            put<S>(Fout + idx[q], scl<S>(lane(F1dev, q), p.isF), sr, rng[q]);
+            put<S>(Fout + p.plane + idx[q], scl<S>(lane(F2dev, q), p.isF), sr, rng[q]);
+        }
         if (p.uout) {
             __stcg(p.uout + idx[q], lane(U1, q));
             __stcg(p.uout + p.plane + idx[q], lane(U2, q));
