@@ -460,6 +460,169 @@ __device__ __forceinline__ void raw_relax(const StepParams &p, const V (&d)[9], 
     o[7] = d[7] + on[2];
 }
 
+// ---- packed FP32 pairs (two lanes, one instruction: sm_100-family f32x2) ----
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float s) { return __fadd2_rn(a, make_float2(s, s)); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fma2(float2 a, float s, float2 c) { return __ffma2_rn(a, make_float2(s, s), c); }
+__device__ __forceinline__ float2 fma2(float s, float2 b, float2 c) { return __ffma2_rn(make_float2(s, s), b, c); }
+// a - b (the product b * (-1) is exact, so this is the rounded difference)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// Central-moment collision of one node on a straight grid (theta12 = theta21
+// = 0): the stresses and effective force (Appendix B (i), Eq.
+// Special1_Force_terms), the corrections of Eqs. 82-85, the central-moment
+// relaxation with sources (Appendix E Steps 1-5) and the return to
+// populations -- the update of the central-moment path of collide() for
+// GEOM 0, with the pairs of quantities its formulas treat alike along xi1 and
+// xi2 (h1 and h2, U1 and U2, the two force components, the coefficient pairs
+// of the corrections, the equilibrium pairs k21/k12 ...) computed together on
+// packed FP32 pairs.  Inputs: pre-collision deviations d (relative to f_ref-),
+// drho, U1, U2 and their normal derivatives, the metric of the node, the
+// stored force of the previous step (F1p, F2p), the Lorentz force (FL1, FL2),
+// the per-row storage reference ur1 (REF).  Outputs: o (relative to f_ref+)
+// and the force deviation F - F_rest.
+template <bool REF>
+__device__ __forceinline__ void collide_straight(const StepParams &p, const float (&d)[9], float drho, float U1,
+                                                 float U2, float dU1, float dr1, float dU2, float dr2, float h1,
+                                                 float ih1, float t11, float h2, float ih2, float t22, float F1p,
+                                                 float F2p, float FL1, float FL2, float ur1, float (&o)[9],
+                                                 float &F1dev, float &F2dev) {
+    const float cs2 = p.cs2, zeta = p.zeta, nu = p.nu;
+    const float rho = drho + p.rho0, csd = drho * cs2;
+    const float2 iM = f2(ih1, ih2), T = f2(t11, t22);
+    const float2 Ms = f2(h2, h1), iMs = f2(ih2, ih1);     // swapped: (h2, h1), (1/h2, 1/h1)
+    const float2 U = f2(U1, U2), Us = f2(U2, U1);
+    // ---- stresses tau11, tau22 and the effective force ------------------------
+    const float2 G = mul2(f2(dU1, dU2), iM);             // (dU1/(h1 dxi1), dU2/(h2 dxi2))
+    const float2 tau = mul2(fma2(G, zeta + nu, mul2(f2(G.y, G.x), zeta - nu)), rho);
+    const float2 UU = mul2(U, U);                         // (uu, vv)
+    const float2 A = add2(fma2(-rho, UU, tau), -csd);     // tau_kk - rho U_k^2 - drho cs2
+    // F = F_rest + F_dev with F_rest = -(h2 theta11, h1 theta22) rho0 cs2, the
+    // geometric force of the rest state; only F_dev is stored
+    const float2 Fdev = mul2(fma2(A, T, f2(FL1 + p.fext1, FL2 + p.fext2)), Ms);
+    const float2 Fr = mul2(mul2(T, -p.rho0 * cs2), Ms);
+    const float2 F = add2(Fdev, Fr);
+    F1dev = Fdev.x;
+    F2dev = Fdev.y;
+    // ---- normal-gradient corrections (Eqs. 82-85 regrouped as in collide) ----
+    const float2 RS = mul2(Ms, iM);                        // (r, s) = (h2/h1, h1/h2)
+    const float2 R12 = mul2(RS, iM);                       // (h2/h1^2, h1/h2^2)
+    const float uv = U1 * U2;
+    const float2 a = mul2(UU, p.gic);                      // (a1, a2)
+    const float2 P3 = sub2(fma2(Ms, p.zc, mul2(iMs, -p.zmn)), mul2(R12, fma2(a, 3.f * zeta, f2(p.A3, p.A3))));
+    const float2 P4 = sub2(fma2(Ms, p.nc, mul2(iMs, p.zmn)), mul2(R12, fma2(a, 3.f * nu, f2(p.A4, p.A4))));   // (P41, -P42)
+    const float2 X = fma2(add2(f2(-a.x, -a.y), 3.f), R12, mul2(Ms, -p.ics2));
+    const float2 B = mul2(a, iM);                          // (b1, b2)
+    const float2 Y = mul2(mul2(mul2(U, add2(a, 1.f)), RS), mul2(T, 2.f));
+    const float2 PD3 = mul2(P3, f2(dU1, dU2)), PD4 = mul2(P4, f2(dU1, dU2));
+    const float q3 = fmaf(Y.x + Y.y, zeta, PD3.x + PD3.y);
+    const float q4 = fmaf(Y.x - Y.y, nu, PD4.x - PD4.y);
+    const float2 V = mul2(U, f2(dr1, dr2));
+    const float2 Bs = f2(B.y, B.x);
+    const float2 W3 = mul2(V, sub2(X, Bs)), W4 = mul2(V, add2(X, Bs));
+    const float n3 = fmaf(-zeta, W3.x + W3.y, rho * q3);
+    const float n4 = fmaf(-nu, W4.x - W4.y, rho * q4);
+    // ---- central moments c = F(U) P (f - f_rest): two passes of the 1D transform
+    const float u = U1, v = U2, nu_ = -u, nv_ = -v;
+    float k0[3], k1[3], k2[3];                            // per row e2 = -1, 0, +1
+    {
+        const float q1 = REF ? fmaf(Fr.x, 0.25f, -ur1) : Fr.x * 0.25f, q2 = Fr.y * 0.25f;
+        const float fm[3] = {d[7], d[3] + q1, d[6]};
+        const float f0[3] = {d[4] + q2, d[0], d[2] - q2};
+        const float fp[3] = {d[8], d[1] - q1, d[5]};
+#pragma unroll
+        for (int y = 0; y < 3; y++) {
+            const float sm_ = fp[y] + fm[y], tm_ = fp[y] - fm[y];
+            k0[y] = sm_ + f0[y];
+            k1[y] = fmaf(nu_, k0[y], tm_);
+            k2[y] = fmaf(nu_, tm_ + k1[y], sm_);
+        }
+    }
+    float c[3][3];                                        // c[m][n]: order m along xi1, n along xi2
+    {
+        const float *kk[3] = {k0, k1, k2};
+#pragma unroll
+        for (int m = 0; m < 3; m++) {
+            const float sm_ = kk[m][2] + kk[m][0], tm_ = kk[m][2] - kk[m][0];
+            c[m][0] = sm_ + kk[m][1];
+            c[m][1] = fmaf(nv_, c[m][0], tm_);
+            c[m][2] = fmaf(nv_, tm_ + c[m][1], sm_);
+        }
+    }
+    // ---- n^eq - n in the combined basis (rest parts cancelled) ---------------
+    const float a0 = h1 * h2 * p.rho0;
+    const float2 BC = mul2(RS, p.rho0 * cs2);             // (b0, c0)
+    const float2 HM = add2(f2(h1, h2), -1.f);              // (h1 - 1, h2 - 1)
+    const float q11 = HM.x * HM.y;
+    const float2 Q2 = mul2(mul2(RS, HM), HM);              // (q20, q02)
+    const float2 Q3 = mul2(mul2(HM, iM), -q11);            // (q21, q12)
+    const float2 E = sub2(fma2(RS, csd, mul2(mul2(Q2, UU), rho)), fma2(UU, a0, f2(c[2][0], c[0][2])));
+    const float e2s = E.x + E.y + n3, e2d = E.x - E.y + n4;
+    const float e11 = fmaf(rho, q11, -a0) * uv - c[1][1];
+    const float2 inner = mul2(fma2(Q3, UU, mul2(mul2(f2(HM.y, HM.x), iM), -cs2)), rho);
+    const float2 E3 = sub2(fma2(Us, fma2(UU, a0, BC), mul2(inner, Us)), f2(c[2][1], c[1][2]));   // (e21, e12)
+    const float e22 = csd * cs2 - c[2][2] - fmaf(UU.y, BC.x, UU.x * BC.y) - UU.x * UU.y * a0;
+    // ---- sources (Eq. cmsourcesGOC) and relaxation ---------------------------
+    const float *om = p.om;
+    const float2 FU = mul2(mul2(F, U), add2(iM, -1.f));   // (F1 U1 (1/h1 - 1), F2 U2 (1/h2 - 1))
+    const float s2s = (FU.x + FU.y) * 2.f, s2d = (FU.x - FU.y) * 2.f;
+    const float s11 = fmaf((ih2 - 1.f) * F.x, v, F.y * u * (ih1 - 1.f));
+    // k10^eq - k10 = F^{n-1}/2 exactly (definition of U), likewise k01; the
+    // first-moment change excludes F_rest, which the change of reference
+    // f_ref- -> f_ref+ absorbs
+    const float2 om12 = f2(om[1], om[2]);
+    const float2 D1 = fma2(f2(F1p, F2p), mul2(om12, 0.5f), mul2(Fdev, fma2(om12, -0.5f, f2(1.f, 1.f))));
+    const float2 D2 = fma2(f2(e2s, e2d), f2(om[3], om[4]),
+                           mul2(f2(s2s, s2d), fma2(f2(om[3], om[4]), -0.5f, f2(1.f, 1.f))));   // (k2s, k2d)
+    const float2 D20 = mul2(f2(D2.x + D2.y, D2.x - D2.y), 0.5f);                               // (D20, D02)
+    const float D11 = fmaf(e11, om[5], s11 * (1.f - 0.5f * om[5]));
+    const float2 D3 = mul2(E3, f2(om[6], om[7]));          // (D21, D12)
+    const float D22 = e22 * om[8];
+    // ---- back to populations: o = d + P^-1 F(-U) Delta - (f_ref+ - f_ref-) ----
+    // (f_ref+ - f_ref- has raw moments (0, F1r, F2r, 0, ...), taken off in
+    // central-moment space as in collide)
+    {
+        const float uv2 = uv * 2.f;
+        const float2 G2 = fma2(mul2(U, 2.f), Fr, D20);                           // (g20, g02)
+        const float2 G3 = fma2(-uv2, Fr, fma2(f2(-UU.x, -UU.y), f2(Fr.y, Fr.x), D3));   // (g21, g12)
+        const float g[3][3] = {{0.f, D1.y, G2.y},
+                               {D1.x, fmaf(v, Fr.x, fmaf(u, Fr.y, D11)), G3.y},
+                               {G2.x, G3.x, fmaf(uv2, fmaf(u, Fr.y, v * Fr.x), D22)}};
+        float r0[3], rp[3], rn[3];                        // per xi1 order m: rows e2 = 0, +1, -1
+#pragma unroll
+        for (int m = 0; m < 3; m++) {
+            const float m1 = fmaf(v, g[m][0], g[m][1]);
+            const float m2 = fmaf(v, g[m][1] + m1, g[m][2]);
+            r0[m] = g[m][0] - m2;
+            rp[m] = (m1 + m2) * 0.5f;
+            rn[m] = (m2 - m1) * 0.5f;
+        }
+        const float *rows[3] = {r0, rp, rn};
+        float o0[3], op[3], on[3];                        // values at e1 = 0, +1, -1 per row
+#pragma unroll
+        for (int y = 0; y < 3; y++) {
+            const float m1 = fmaf(u, rows[y][0], rows[y][1]);
+            const float m2 = fmaf(u, rows[y][1] + m1, rows[y][2]);
+            o0[y] = rows[y][0] - m2;
+            op[y] = (m1 + m2) * 0.5f;
+            on[y] = (m2 - m1) * 0.5f;
+        }
+        o[0] = d[0] + o0[0];
+        o[1] = d[1] + op[0];
+        o[3] = d[3] + on[0];
+        o[2] = d[2] + o0[1];
+        o[5] = d[5] + op[1];
+        o[6] = d[6] + on[1];
+        o[4] = d[4] + o0[2];
+        o[8] = d[8] + op[2];
+        o[7] = d[7] + on[2];
+    }
+}
+
 // Phase 2 for the R = Lanes<V>::R nodes (i, j[r]) of one thread, r = 0..R-1
 // (one node with V = float, two with V = float2: every arithmetic step below
 // runs once for both): the MIE, stresses, forces and the central-moment
@@ -659,6 +822,11 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         }
     }
 
+    V o[9], F1dev, F2dev;
+    if constexpr (GEOM == 0 && !SRT && R == 1) {   // straight grid, central moments, one node per thread
+        collide_straight<REF>(p, d, drho, U1, U2, dU1, dr1, dU2, dr2, h1, ih1, t11, h2, ih2, t22, F1p, F2p, FL1,
+                              FL2, ur1n[0], o, F1dev, F2dev);
+    } else {
     // ---- stresses and effective force (straight grid, Appendix B (i)) -------
     const float zeta = p.zeta, nu = p.nu;
     const V g1d = dU1 * ih1, g2d = dU2 * ih2;             // dU1/(h1 dxi1), dU2/(h2 dxi2)
@@ -666,7 +834,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     V tau22 = rho * fmav(g2d, zeta + nu, g1d * (zeta - nu));
     // F = F_rest + F_dev, F_rest = -(h2, h1) rho0 cs2 (theta11, theta22) is the
     // geometric force of the rest state; only F_dev is stored.
-    V F1dev, F2dev, F1r, F2r, tc11 = bc<V>(0.f), tc22 = bc<V>(0.f);
+    V F1r, F2r, tc11 = bc<V>(0.f), tc22 = bc<V>(0.f);
     if constexpr (GEOM) {
         // curvilinear grids (theta12, theta21; the column metric has theta12 =
         // theta22 = 0): tau^c (Eq. tauc), the full effective force (Eqs.
@@ -733,7 +901,6 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         }
     }
 
-    V o[9];
     if constexpr (SRT) {
         raw_relax<REF, V>(p, d, o, rho, drho, U1, U2, ih2, ih1, r, s, uu, vv, uv, n3, n4, F1, F2, F1dev, F2dev, F1p,
                           F2p, F1r, F2r, pack<V>(ur1n));
@@ -852,6 +1019,7 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
         o[7] = d[7] + on[2];
     }
     }   // central-moment path
+    }   // general collision
     S *fout = static_cast<S *>(p.fout);
     S *Fout = static_cast<S *>(p.Fout);
 #pragma unroll
