@@ -233,6 +233,17 @@ goc_status goc_set_launch_config(goc_lattice *lat, int dynamic_tiles, int pdl);
 goc_status goc_launch_grid(const goc_lattice *lat, int *balanced);
 goc_status goc_set_launch_grid(goc_lattice *lat, int balanced);
 
+/* Tile shape of the step kernel on straight grids with the central-moment
+ * collision: *rows = 8 (tiles of 32 x 8 nodes, one node per thread) or 16
+ * (32 x 16, two nodes per thread, so the per-tile work and the ring of halo
+ * nodes are shared by twice the nodes).  Other lattices always use 8.  Chosen
+ * by the autotuner with the other launch settings; the set call fixes it
+ * (GOC_EINVAL for a height other than 8 or 16, or 16 on a lattice that cannot
+ * use it) and turns the autotuner off.  Results are bitwise the same under
+ * either.  No counterpart in the paper. */
+goc_status goc_tile_height(const goc_lattice *lat, int *rows);
+goc_status goc_set_tile_height(goc_lattice *lat, int rows);
+
 /* ---- the hot loop ------------------------------------------------------ */
 
 /* Enqueue nsteps time steps (each one fused launch: pull-streaming with

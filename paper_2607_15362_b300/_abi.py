@@ -76,6 +76,8 @@ SIGNATURES = {
     "goc_set_launch_config": (c_int, [c_void_p, c_int, c_int]),
     "goc_launch_grid": (c_int, [c_void_p, P(c_int)]),
     "goc_set_launch_grid": (c_int, [c_void_p, c_int]),
+    "goc_tile_height": (c_int, [c_void_p, P(c_int)]),
+    "goc_set_tile_height": (c_int, [c_void_p, c_int]),
     "goc_create_slab": (c_int, [P(GocGrid), P(GocMap), P(GocFlow), P(GocMhd), P(GocExec), c_int, c_int,
                                 P(c_void_p)]),
     "goc_slab_info": (c_int, [c_void_p] + [P(c_int)] * 4),

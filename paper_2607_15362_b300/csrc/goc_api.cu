@@ -111,6 +111,8 @@ bool encode_lattice_maps(goc_lattice *L) {
     for (int b = 0; b < 2; b++) {
         ok = ok && encode_planes(&L->tmf[b], L->storage, L->f[b], L->nx, L->ny, L->pitch, 9, T::BX, T::BY);
         ok = ok && encode_planes(&L->tmF[b], L->storage, L->F[b], L->nx, L->ny, L->pitch, 2, T::BX, T::BY);
+        ok = ok && encode_planes(&L->tmf2[b], L->storage, L->f[b], L->nx, L->ny, L->pitch, 9, T::BX, Tiling2<S>::BY);
+        ok = ok && encode_planes(&L->tmF2[b], L->storage, L->F[b], L->nx, L->ny, L->pitch, 2, T::BX, Tiling2<S>::BY);
         if (L->mhd.enabled)
             ok = ok && encode_planes(&L->tmg[b], L->storage, L->g[b], L->nx, L->ny, L->pitch, 10, T::BX, T::BYG);
     }
@@ -159,12 +161,16 @@ goc_status launch_one(goc_lattice *L, float *uout) {
 }
 
 // ---- launch autotuner ------------------------------------------------------
-// Candidates: tile queue or static order x dependent launch on or off (the
-// standard scheme has no tiles: dependent launch only).  Each runs 2 + 16
-// real steps of the lattice; the 16 are timed with CUDA events.
+// Candidates: tile queue or static order x the balanced grid x dependent
+// launch on or off -- on straight grids with the central-moment collision the
+// tile height (8 or 16 rows) in place of the last, with dependent launch on;
+// the standard scheme has no tiles (dependent launch only).  Each runs 2 + 16 real steps of the lattice; the 16 are timed
+// with CUDA events.  Every candidate gives bitwise the same populations.
 constexpr long long kTuneWarm = 2, kTuneSteps = 16;
 std::mutex g_tune_mu;
-std::map<std::array<int, 5>, std::array<int, 3>> g_tune_cache;
+std::map<std::array<int, 5>, std::array<int, 4>> g_tune_cache;
+
+bool tile_rows_apply(const goc_lattice *L) { return L->scheme == 0 && L->sp.curv == 0; }
 
 goc_status autotune(goc_lattice *L, long long *nsteps) {
     if (L->tuned) return GOC_OK;
@@ -176,20 +182,25 @@ goc_status autotune(goc_lattice *L, long long *nsteps) {
             L->cfg_dynamic = it->second[0];
             L->cfg_pdl = it->second[1];
             L->cfg_balanced = it->second[2];
+            L->cfg_rows = it->second[3];
             L->tuned = true;
             return GOC_OK;
         }
     }
+    // (straight grids with the central-moment collision: the tile height takes
+    // the place of the dependent-launch switch, which measured best on everywhere)
+    const bool rows = tile_rows_apply(L);
     const int ncand = L->scheme == 1 ? 2 : 8;
     if (*nsteps < ncand * (kTuneWarm + kTuneSteps)) return GOC_OK;   // tune on a longer call
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bd = 1, bp = 1, bb = 0;
+    int bd = 1, bp = 1, bb = 0, br = 1;
     goc_status st = GOC_OK;
     for (int c = 0; c < ncand && st == GOC_OK; c++) {
-        L->cfg_pdl = (c & 1) ? 0 : 1;
+        L->cfg_pdl = (c & 1) && !rows ? 0 : 1;
+        L->cfg_rows = (c & 1) && rows ? 2 : 1;
         L->cfg_dynamic = (c & 2) ? 0 : 1;
         L->cfg_balanced = (c & 4) ? 1 : 0;
         for (long long s = 0; s < kTuneWarm && st == GOC_OK; s++) st = launch_one(L, nullptr);
@@ -208,6 +219,7 @@ goc_status autotune(goc_lattice *L, long long *nsteps) {
             bd = L->cfg_dynamic;
             bp = L->cfg_pdl;
             bb = L->cfg_balanced;
+            br = L->cfg_rows;
         }
     }
     cudaEventDestroy(e0);
@@ -216,13 +228,14 @@ goc_status autotune(goc_lattice *L, long long *nsteps) {
     L->cfg_dynamic = bd;
     L->cfg_pdl = bp;
     L->cfg_balanced = bb;
+    L->cfg_rows = br;
     L->tuned = true;
     if (L->graph) {   // captured under another configuration
         cudaGraphExecDestroy(L->graph);
         L->graph = nullptr;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = {bd, bp, bb};
+    g_tune_cache[key] = {bd, bp, bb, br};
     return GOC_OK;
 }
 
@@ -1239,6 +1252,26 @@ goc_status goc_launch_config(const goc_lattice *L, int *dynamic_tiles, int *pdl,
 goc_status goc_launch_grid(const goc_lattice *L, int *balanced) {
     if (!L) return fail(GOC_EINVAL, "lattice is NULL");
     if (balanced) *balanced = L->cfg_balanced;
+    return GOC_OK;
+}
+
+goc_status goc_tile_height(const goc_lattice *L, int *rows) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (rows) *rows = tile_rows_apply(L) ? 8 * L->cfg_rows : TY;
+    return GOC_OK;
+}
+
+goc_status goc_set_tile_height(goc_lattice *L, int rows) {
+    if (!L) return fail(GOC_EINVAL, "lattice is NULL");
+    if (rows != 8 && rows != 16) return fail(GOC_EINVAL, "the tile height must be 8 or 16 rows");
+    if (rows == 16 && !tile_rows_apply(L))
+        return fail(GOC_EINVAL, "16-row tiles are for straight grids with the central-moment collision");
+    L->cfg_rows = rows / 8;
+    L->tuned = true;
+    if (L->graph) {   // captured under another configuration
+        cudaGraphExecDestroy(L->graph);
+        L->graph = nullptr;
+    }
     return GOC_OK;
 }
 

@@ -11,6 +11,7 @@
 #include "../../include/goc.h"
 #include "goc_device.cuh"
 #include "goc_step.cuh"
+#include "goc_lean.cuh"
 
 // Error reporting shared by every translation unit: records the message
 // returned by goc_last_error() and returns st.
@@ -89,6 +90,7 @@ struct goc_lattice {
     bool fresh = false;                          // buffer holds f^0 (pre-collision): next step reads in place
     bool res_pending = false;                    // residual sums of a batch step wait in red[4..7]
     CUtensorMap tmf[2], tmF[2], tmg[2];          // TMA descriptors of both buffers
+    CUtensorMap tmf2[2], tmF2[2];                // the same with the box of 32 x 16 tiles
     bool tma_ok = false;
     int rounding = 0;                            // goc_exec.rounding
     int scheme = 0;                              // goc_exec.scheme
@@ -96,6 +98,7 @@ struct goc_lattice {
     // tile queue (dynamic) or static tile order, programmatic dependent launch
     int cfg_dynamic = 1, cfg_pdl = 1;
     int cfg_balanced = 0;                        // grid: the fewest blocks taking the same rounds of tiles
+    int cfg_rows = 1;                            // straight grids: tiles of 8 (1) or 16 (2) rows
     bool tuned = false;                          // chosen by the launch autotuner (or fixed)
     int plateau_checks = 0;                      // goc_exec.plateau_checks
     // per-row storage reference (16-bit storage on straight grids; see goc_aux.cuh)

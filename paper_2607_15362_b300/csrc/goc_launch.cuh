@@ -55,6 +55,16 @@ int lean_grid(int ntiles, size_t *smem, bool balanced = false) {
     return persistent_grid(lean_step_kernel<S, MHD>, bytes, ntiles, balanced, cached);
 }
 
+// The same for the 32 x 16 tile kernel lean2_step_kernel.
+template <class S, bool MHD>
+int lean2_grid(int ntiles, size_t *smem, bool balanced = false) {
+    using T = Tiling2<S>;
+    const size_t bytes = (size_t)T::NSTAGE * T::STAGE;
+    *smem = bytes;
+    static int cached = -1;
+    return persistent_grid(lean2_step_kernel<S, MHD>, bytes, ntiles, balanced, cached);
+}
+
 // Straight grids with the central-moment collision run lean_step_kernel
 // unless GOC_GENERAL_KERNEL is set (the general tile path of step_kernel, for
 // comparisons).
@@ -139,6 +149,18 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
         } else {
             const int grid = step_grid<S, false, true>(ntiles, &smem, L->cfg_balanced != 0);
             CU(launch_pdl(pdl, step_kernel<S, false, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        }
+    } else if (lean_enabled() && L->cfg_rows == 2 && L->tma_ok) {   // 32 x 16 tiles
+        StepParams q = p;
+        q.tm_f = L->tmf2[L->cur];
+        q.tm_F = L->tmF2[L->cur];
+        const int nt2 = ((L->nx + TX - 1) / TX) * ((L->ny + 2 * TY - 1) / (2 * TY));
+        if (L->mhd.enabled) {
+            const int grid = lean2_grid<S, true>(nt2, &smem, L->cfg_balanced != 0);
+            CU(launch_pdl(pdl, lean2_step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, q));
+        } else {
+            const int grid = lean2_grid<S, false>(nt2, &smem, L->cfg_balanced != 0);
+            CU(launch_pdl(pdl, lean2_step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, q));
         }
     } else if (lean_enabled() && L->mhd.enabled) {
         const int grid = lean_grid<S, true>(ntiles, &smem, L->cfg_balanced != 0);

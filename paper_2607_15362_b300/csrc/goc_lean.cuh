@@ -33,11 +33,11 @@ __device__ __forceinline__ AxisRecord axis_record(const float4 *rec, int k) {
 // Pull of the nine deviations arriving at an interior node whose stored value
 // of link 0 sits at s (all sources inside the staged box), with the rest-state
 // pull corrections of links 1..4 (rm/rp of the node's column and row).
-template <class S>
+template <class S, int BYS = Tiling<S>::BY>
 __device__ __forceinline__ void lean_pull(const S *s, float sf, const AxisRecord &c, const AxisRecord &r,
                                           float d[9]) {
     using T = Tiling<S>;
-    constexpr int BX = T::BX, PL = T::BX * T::BY;
+    constexpr int BX = T::BX, PL = T::BX * BYS;
     d[0] = scl<S>(Store<S>::lds(s), sf);
     d[1] = fmaf(r.h, c.rm, scl<S>(Store<S>::lds(s + PL - 1), sf));            // source (i-1, j)
     d[2] = fmaf(c.h, r.rm, scl<S>(Store<S>::lds(s + 2 * PL - BX), sf));       // (i, j-1)
@@ -205,6 +205,224 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
         if (!lean_run_tile<S, MHD>(p, it.w, it.y, it.z, dyn + stage * STAGE, sm, ok)) return;
         __syncthreads();
         stage ^= 1;
+    }
+}
+
+// ---- 32 x 16 tiles, two rows per thread -------------------------------------
+// The same step on tiles twice as tall: each thread updates the nodes of rows
+// ty and ty + 8 of its column, so the per-tile work (item, copy, barriers,
+// metric records of the column) and the ring of halo nodes are shared by twice
+// the nodes.  Interior tiles are staged by TMA (box [9][22][BX] and [2][22][BX]:
+// 16 rows and a halo of 3); tiles next to a wall or across a periodic seam run
+// as two 32 x 8 tiles of the general path on direct global loads.  FP32 keeps
+// one stage (released after the last read of the tile, then the next copy is
+// issued), 16-bit storage two.
+template <class S> struct Tiling2 {
+    static constexpr int HXS = Tiling<S>::HXS, BX = Tiling<S>::BX, TYL = 2 * TY, BY = TYL + 2 * HYS;
+    static constexpr int align128(int b) { return (b + 127) / 128 * 128; }
+    static constexpr int F_BYTES = 9 * BY * BX * (int)sizeof(S);
+    static constexpr int FF_BYTES = 2 * BY * BX * (int)sizeof(S);
+    static constexpr int OFF_FF = align128(F_BYTES);
+    static constexpr int STAGE = OFF_FF + align128(FF_BYTES);
+    static constexpr int NSTAGE = sizeof(S) == 4 ? 1 : 2;
+};
+struct FieldSmem2 {
+    float rho[2 * TY + 2 * MH][TX + 2 * MH], u1[2 * TY + 2 * MH][TX + 2 * MH], u2[2 * TY + 2 * MH][TX + 2 * MH];
+};
+static_assert(sizeof(FieldSmem2) >= sizeof(FieldSmem), "the general path's field arrays live in FieldSmem2");
+
+// Kind of a 32 x 16 tile: 0 interior (staged), 1 anything else (general path,
+// global loads).
+template <class S>
+__device__ __forceinline__ int tile_kind2(const StepParams &p, int i0, int j0) {
+    using T = Tiling2<S>;
+    if (!p.use_tma) return 1;
+    const bool wx = p.per_x && (i0 - T::HXS < 0 || i0 + TX + T::HXS > p.nx);
+    const bool wy = p.per_y && (j0 - HYS < 0 || j0 + T::TYL + HYS > p.ny);
+    if (wx || wy) return 1;
+    if (i0 >= 2 && i0 + TX + 2 <= p.nx && j0 >= 2 && j0 + T::TYL + 2 <= p.ny) return 0;
+    return 1;
+}
+
+template <class S, bool MHD>
+__device__ __forceinline__ void lean2_collide(const StepParams &p, int i, int j, const AxisRecord &c,
+                                              const AxisRecord &r, const float (&d)[9], float F1p, float F2p,
+                                              float drho, float U1, float U2, const FieldSmem2 &sm, int ex, int ey,
+                                              float ur1) {
+    const float fl[7][1] = {{drho}, {U1}, {U2},
+                            {0.5f * (sm.u1[ey][ex + 1] - sm.u1[ey][ex - 1])},
+                            {0.5f * (sm.rho[ey][ex + 1] - sm.rho[ey][ex - 1])},
+                            {0.5f * (sm.u2[ey + 1][ex] - sm.u2[ey - 1][ex])},
+                            {0.5f * (sm.rho[ey + 1][ex] - sm.rho[ey - 1][ex])}};
+    const int jj[1] = {j};
+    const bool own[1] = {true};
+    const float dn[1][9] = {{d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], d[8]}};
+    const float F1n[1] = {F1p}, F2n[1] = {F2p}, h2n[1] = {r.h}, ih2n[1] = {r.ih}, urn[1] = {ur1};
+    const float th[2] = {c.th, r.th};
+    SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
+                     p.plane, p.pitch, p.sf, p.sF, p.sg};
+    collide<S, MHD, false, float, false, 0>(p, src, i, jj, own, dn, F1n, F2n, c.h, c.ih, h2n, ih2n, fl, urn, th);
+}
+
+// One interior 32 x 16 tile from the stage st.  Every thread of the block
+// calls it (fields barrier inside).  The populations of the upper node are
+// pulled again after the barrier instead of being held through the lower
+// node's collision.
+template <class S, bool MHD>
+__device__ __forceinline__ bool lean2_tile(const StepParams &p, const unsigned char *st, int i0, int j0,
+                                           FieldSmem2 &sm, bool ok) {
+    using T = Tiling2<S>;
+    constexpr bool REF = Store<S>::scaled;
+    constexpr int BX = T::BX, PLF = T::BX * T::BY, TYL = T::TYL, BAND = TX + 2, RING = 2 * BAND + 2 * TYL;
+    const S *sf_ = reinterpret_cast<const S *>(st);
+    const S *sF_ = reinterpret_cast<const S *>(st + T::OFF_FF);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int i = i0 + tx, ja = j0 + ty, jb = ja + TY;
+    const float4 *rec1 = axis_records(p.ax1, p.nx), *rec2 = axis_records(p.ax2, p.ny);
+    const AxisRecord c = axis_record(rec1, i), ra = axis_record(rec2, ja), rb = axis_record(rec2, jb);
+    const int sa = (ty + HYS) * BX + tx + T::HXS, sb = sa + TY * BX;
+    // lower node: pulled, fields, kept; upper node: fields only
+    float d[9], drho, U1, U2;
+    const float ura = REF ? GOC_U1R(p, ja) : 0.f, urb = REF ? GOC_U1R(p, jb) : 0.f;
+    lean_pull<S, T::BY>(sf_ + sa, p.sf, c, ra, d);
+    const float F1p = scl<S>(Store<S>::lds(sF_ + sa), p.sF), F2p = scl<S>(Store<S>::lds(sF_ + PLF + sa), p.sF);
+    fields_from<REF>(p, d, F1p, F2p, c.ih, ra.ih, drho, U1, U2, ura);
+    sm.rho[ty + MH][tx + MH] = drho;
+    sm.u1[ty + MH][tx + MH] = U1;
+    sm.u2[ty + MH][tx + MH] = U2;
+    {
+        float db[9], a, u, v;
+        lean_pull<S, T::BY>(sf_ + sb, p.sf, c, rb, db);
+        fields_from<REF>(p, db, scl<S>(Store<S>::lds(sF_ + sb), p.sF), scl<S>(Store<S>::lds(sF_ + PLF + sb), p.sF),
+                         c.ih, rb.ih, a, u, v, urb);
+        sm.rho[ty + TY + MH][tx + MH] = a;
+        sm.u1[ty + TY + MH][tx + MH] = u;
+        sm.u2[ty + TY + MH][tx + MH] = v;
+    }
+    {   // ring, from the last thread down (warp 0 also stages the next tile)
+        const int q = NT - 1 - tid;
+        if (q < RING) {
+            int x, y;
+            if (q < 2 * BAND) {
+                y = q < BAND ? -1 : TYL;
+                x = (q < BAND ? q : q - BAND) - 1;
+            } else {
+                const int b = q - 2 * BAND;
+                x = b < TYL ? -1 : TX;
+                y = b < TYL ? b : b - TYL;
+            }
+            const AxisRecord cq = axis_record(rec1, i0 + x), rq = axis_record(rec2, j0 + y);
+            const int sq = (y + HYS) * BX + x + T::HXS;
+            float dd[9], a, u, v;
+            lean_pull<S, T::BY>(sf_ + sq, p.sf, cq, rq, dd);
+            fields_from<REF>(p, dd, scl<S>(Store<S>::lds(sF_ + sq), p.sF), scl<S>(Store<S>::lds(sF_ + PLF + sq), p.sF),
+                             cq.ih, rq.ih, a, u, v, REF ? GOC_U1R(p, j0 + y) : 0.f);
+            sm.rho[y + MH][x + MH] = a;
+            sm.u1[y + MH][x + MH] = u;
+            sm.u2[y + MH][x + MH] = v;
+        }
+    }
+    if (!__syncthreads_and(ok)) return false;
+    lean2_collide<S, MHD>(p, i, ja, c, ra, d, F1p, F2p, drho, U1, U2, sm, tx + MH, ty + MH, ura);
+    {   // upper node: pulled again from the stage, its fields from the field arrays
+        float db[9];
+        lean_pull<S, T::BY>(sf_ + sb, p.sf, c, rb, db);
+        const int ey = ty + TY + MH, ex = tx + MH;
+        lean2_collide<S, MHD>(p, i, jb, c, rb, db, scl<S>(Store<S>::lds(sF_ + sb), p.sF),
+                              scl<S>(Store<S>::lds(sF_ + PLF + sb), p.sF), sm.rho[ey][ex], sm.u1[ey][ex],
+                              sm.u2[ey][ex], sm, ex, ey, urb);
+    }
+    return true;
+}
+
+template <class S>
+__device__ __forceinline__ void issue_tile2(const TileMaps &m, int i0, int j0, unsigned char *stage, uint64_t *bar) {
+    using T = Tiling2<S>;
+    mbar_expect_tx(bar, T::F_BYTES + T::FF_BYTES);
+    tma_load_3d(stage, m.f, i0 - T::HXS, j0 - HYS, 0, bar);
+    tma_load_3d(stage + T::OFF_FF, m.F, i0 - T::HXS, j0 - HYS, 0, bar);
+}
+
+// Single lattice on a straight grid, 32 x 16 tiles (p.tm_f / p.tm_F must be
+// the maps with the 22-row box).
+template <class S, bool MHD>
+__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
+    lean2_step_kernel(const __grid_constant__ StepParams p) {
+    using T = Tiling2<S>;
+    constexpr int NS = T::NSTAGE;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ FieldSmem2 sm;
+    __shared__ int4 s_item[2];
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    if (leader) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    griddep_launch_dependents();
+    griddep_wait();
+    if (leader && blockIdx.x == 0) {
+        if (Store<S>::scaled && p.sr) *p.seed_wr = *p.seed_rd + 1u;
+        if (p.tctr) *p.tctr_next = 0;
+    }
+    const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
+    int *ctr = p.tctr;
+    const int stride = gridDim.x;
+    const int ntx = (p.nx + TX - 1) / TX, nty = (p.ny + T::TYL - 1) / T::TYL, ntiles = ntx * nty;
+    auto take = [&](int stg, int t) {
+        int4 it = make_int4(t, 0, 0, 1);
+        if (t < ntiles) {
+            it.y = (t % ntx) * TX;
+            it.z = (t / ntx) * T::TYL;
+            it.w = p.nopull ? 1 : tile_kind2<S>(p, it.y, it.z);   // (the first step reads f^0 in place)
+            if (it.w == 0) {
+                fence_proxy_async();
+                issue_tile2<S>(m, it.y, it.z, dyn + stg * T::STAGE, &bars[stg]);
+            }
+        }
+        s_item[stg] = it;
+    };
+    auto next_index = [&](int t) { return ctr ? stride + atomicAdd(ctr, 1) : t + stride; };
+    if (leader) take(0, blockIdx.x);
+    __syncthreads();
+    uint32_t ph0 = 0, ph1 = 0;
+    int stage = 0;
+    for (;;) {
+        const int4 it = s_item[stage];
+        const int t = it.x;
+        if (t >= ntiles) break;
+        int nt = 0;
+        if (leader) {
+            nt = next_index(t);
+            if (NS == 2) take(stage ^ 1, nt);
+        }
+        bool ok = true;
+        if (it.w == 0) {
+            uint32_t &ph = stage ? ph1 : ph0;
+            ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
+            ph ^= 1;
+            if (MHD) {
+                if (!__syncthreads_and(ok)) return;
+            }
+            if (!lean2_tile<S, MHD>(p, dyn + stage * T::STAGE, it.y, it.z, sm, ok)) return;
+        } else {   // two 32 x 8 tiles of the general path on global loads
+            SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin),
+                             static_cast<const S *>(p.gin), p.plane, p.pitch, p.sf, p.sF, p.sg};
+            FieldSmem &sm1 = *reinterpret_cast<FieldSmem *>(&sm);
+            if (!tile_compute<S, MHD, 1, false, 0>(p, src, it.y, it.z, sm1, true)) return;
+            if (it.z + TY < p.ny) {
+                __syncthreads();   // the field arrays are reused
+                if (!tile_compute<S, MHD, 1, false, 0>(p, src, it.y, it.z + TY, sm1, true)) return;
+            }
+        }
+        __syncthreads();   // the stage, the field arrays and s_item are reused
+        if (NS == 1) {
+            if (leader) take(0, nt);   // the single stage is free: copy the next tile
+            __syncthreads();
+        } else {
+            stage ^= 1;
+        }
     }
 }
 

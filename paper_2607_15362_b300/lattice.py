@@ -209,15 +209,19 @@ class Lattice:
 
     @property
     def launch_config(self) -> dict:
-        d, p, t, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        d, p, t, b, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(lib().goc_launch_config(self._h, ctypes.byref(d), ctypes.byref(p), ctypes.byref(t)))
         check(lib().goc_launch_grid(self._h, ctypes.byref(b)))
+        check(lib().goc_tile_height(self._h, ctypes.byref(r)))
         return {"dynamic_tiles": bool(d.value), "pdl": bool(p.value), "balanced_grid": bool(b.value),
-                "tuned": bool(t.value)}
+                "tile_rows": r.value, "tuned": bool(t.value)}
 
-    def set_launch_config(self, dynamic_tiles: bool, pdl: bool, balanced_grid: bool = False):
+    def set_launch_config(self, dynamic_tiles: bool, pdl: bool, balanced_grid: bool = False, tile_rows: int = 8):
+        """Fix the launch settings (and turn the autotuner off); tile_rows 16
+        is for straight grids with the central-moment collision."""
         check(lib().goc_set_launch_config(self._h, int(dynamic_tiles), int(pdl)))
         check(lib().goc_set_launch_grid(self._h, int(balanced_grid)))
+        check(lib().goc_set_tile_height(self._h, int(tile_rows)))
 
     @property
     def bytes_per_node(self) -> float:

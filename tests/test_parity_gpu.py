@@ -292,23 +292,25 @@ def test_interior_tiles_match_the_oracle(gpu, kind):
 
 
 def test_launch_configurations_give_bitwise_identical_populations(gpu):
-    """Tile queue vs static tile order, dependent launch on or off and the
-    balanced grid change only which block computes which tile and when: the
-    populations agree
-    bitwise (on a cavity with interior, wall and ragged tiles, and on a
-    periodic channel whose seam tiles read global memory)."""
+    """Tile queue vs static tile order, dependent launch on or off, the
+    balanced grid and the tile height (32 x 8 or 32 x 16 nodes) change only
+    which block computes which node and when: the populations agree bitwise
+    (on a cavity with interior, wall and ragged tiles, and on a periodic
+    channel with the MIE whose seam tiles read global memory)."""
     for prob in (gi.Problem("cavity", 200, 90, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
                             {"Re": 100.0, "u_lid": 0.05}),
                  gi.Problem("hartmann", 70, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
                             {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0})):
         spec = prob.lattice_spec(cs2_of(prob))
         states = []
-        for dyn, pdl, bal in ((True, True, False), (False, True, False), (True, False, False),
-                              (False, False, False), (True, True, True), (False, True, True)):
+        for dyn, pdl, bal, rows in ((True, True, False, 8), (False, True, False, 8), (True, False, False, 8),
+                                    (False, False, False, 8), (True, True, True, 8), (False, True, True, 8),
+                                    (True, True, False, 16), (False, True, True, 16), (True, False, False, 16)):
             L = goc.Lattice(spec)
-            L.set_launch_config(dyn, pdl, bal)
+            L.set_launch_config(dyn, pdl, bal, tile_rows=rows)
             L.step(150)
-            assert L.launch_config == {"dynamic_tiles": dyn, "pdl": pdl, "balanced_grid": bal, "tuned": True}
+            assert L.launch_config == {"dynamic_tiles": dyn, "pdl": pdl, "balanced_grid": bal, "tile_rows": rows,
+                                       "tuned": True}
             states.append(L.get_state())
             L.close()
         assert all(s == states[0] for s in states[1:])
@@ -317,6 +319,18 @@ def test_launch_configurations_give_bitwise_identical_populations(gpu):
         assert A.launch_config["tuned"]
         assert A.get_state() == states[0]
         A.close()
+
+
+def test_tall_tiles_are_for_straight_grids_only(gpu):
+    """The 32 x 16 tiles run the straight-grid central-moment kernel; a curved
+    grid reports 8-row tiles and refuses 16."""
+    prob = gi.taylor_couette(n1=45, n2=11, r_in=6.0, sectors=9.0, Re=20.0, u_in=1.0, u_out=1.5)
+    L = goc.Lattice(prob.lattice_spec(cs2_of(prob)))
+    assert L.launch_config["tile_rows"] == 8
+    with pytest.raises(goc.GocError) as e:
+        L.set_launch_config(True, True, False, tile_rows=16)
+    assert "straight grids" in str(e.value)
+    L.close()
 
 
 # ---- collisions on raw moments: SRT of Appendix F (goc_exec.scheme = 2) and
