@@ -36,10 +36,10 @@ sys.path.insert(0, ROOT)
 import goc_inputs as gi  # noqa: E402
 
 METRIC = "MLUPS & % of HBM peak (FP32 vs FP16 store); batched p50/p99 solve latency"
-PROFILE = os.path.join(ROOT, "profiles", "step_kernel_cavity512_fp32.txt")
+PROFILE = os.path.join(ROOT, "profiles", "lean_step_kernel_cavity512_fp32.txt")
 PROFILE_SPIRAL = os.path.join(ROOT, "profiles", "step_kernel_spiral512_fp32_table.txt")
 KERNEL_SOURCES = ["paper_2607_15362_b300/csrc/goc_step.cuh", "paper_2607_15362_b300/csrc/goc_device.cuh",
-                  "paper_2607_15362_b300/csrc/goc_vec.cuh"]
+                  "paper_2607_15362_b300/csrc/goc_vec.cuh", "paper_2607_15362_b300/csrc/goc_lean.cuh"]
 
 
 def kernel_hash() -> str:
@@ -48,6 +48,16 @@ def kernel_hash() -> str:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def step_kernel_name(storage: str, mie: bool, scheme: str, geom: int, tile_rows: int = 8) -> str:
+    """The step kernel a lattice runs: straight grids with the central-moment
+    collision run lean_step_kernel (lean2_step_kernel with 16-row tiles), the
+    others step_kernel."""
+    s = {"fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}[storage]
+    if geom == 0 and scheme == "goc":
+        return "goc::{}<{},{}>".format("lean2_step_kernel" if tile_rows == 16 else "lean_step_kernel", s, int(mie))
+    return "goc::step_kernel<{},{},{},{}>".format(s, int(mie), int(scheme != "goc"), geom)
 
 
 def measured_peaks():
@@ -317,9 +327,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": src, "bytes_per_node": bpn,
-                         "kernel": "goc::step_kernel<{},{},{},{}>".format(
-                             {"fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}[args.storage],
-                             int(bool(args.mie)), int(args.scheme != "goc"), geom),
+                         "kernel": step_kernel_name(args.storage, bool(args.mie), args.scheme, geom,
+                                                    lat.launch_config.get("tile_rows", 8)),
                          "launch_us": round(launch_s * 1e6, 3),
                          "launch_config": lat.launch_config, "issue": issue},
             "cpu_baseline": cpu,
