@@ -314,7 +314,8 @@ goc_status goc_diagnostics(goc_lattice *lat, double *mass, double *residual_u,
  *    (deterministic) and agrees with goc_diagnostics to FP64 rounding.
  *  - Runs on the lattice's device and restores the caller's current device
  *    before returning.  Waits for the lattice's stream (a synchronous
- *    device-to-host copy of the result); *mass is a host pointer. */
+ *    device-to-host copy of the result), so that stream must not be under
+ *    stream capture when this is called; *mass is a host pointer. */
 #define GOC_NOALLOC_MAX_BLOCKS 4096
 #define GOC_NOALLOC_MAX_NODES 8388608LL
 goc_status goc_mass_noalloc(goc_lattice *lat, double *mass);
