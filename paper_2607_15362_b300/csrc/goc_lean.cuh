@@ -133,7 +133,7 @@ __device__ __forceinline__ bool lean_run_tile(const StepParams &p, int kind, int
 // Single lattice on a straight grid: persistent blocks take tiles from the
 // lattice's queue, as step_kernel does.
 template <class S, bool MHD>
-__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
+__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MIN_BLOCKS)
     lean_step_kernel(const __grid_constant__ StepParams p) {
     using T = Tiling<S>;
     constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
@@ -346,7 +346,7 @@ __device__ __forceinline__ void issue_tile2(const TileMaps &m, int i0, int j0, u
 // Single lattice on a straight grid, 32 x 16 tiles (p.tm_f / p.tm_F must be
 // the maps with the 22-row box).
 template <class S, bool MHD>
-__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS)
+__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MIN_BLOCKS)
     lean2_step_kernel(const __grid_constant__ StepParams p) {
     using T = Tiling2<S>;
     constexpr int NS = T::NSTAGE;

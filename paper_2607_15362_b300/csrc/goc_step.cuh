@@ -58,6 +58,13 @@ namespace goc {
 #ifndef GOC_MIN_BLOCKS_MHD
 #define GOC_MIN_BLOCKS_MHD (GOC_MIE_STAGED ? 2 : 3)
 #endif
+#ifndef GOC_MIN_BLOCKS_MHD_STRAIGHT
+// NSE+MIE kernels of straight grids: 4 blocks per SM (64 registers) measured
+// faster than 3 (80 registers, no spills): Hartmann channel 256 x 1024
+// 27.9 against 30.3-31.8 us per step, 2048^2 cavity with the MIE 181 against
+// 207 us (FP32).  The curved-grid MIE kernels, with more terms, keep 3.
+#define GOC_MIN_BLOCKS_MHD_STRAIGHT (GOC_MIE_STAGED ? 2 : 4)
+#endif
 #ifndef GOC_ROWS_PER_THREAD
 #define GOC_ROWS_PER_THREAD 1  // nodes per thread (rows ty + r TY/RPT); 2 runs the collision on packed f32x2 (measured slower)
 #endif
@@ -1342,7 +1349,8 @@ __device__ __forceinline__ void lattice_tiles(const StepParams &p, const TileMap
 // the corrections and the local shear stress (Appendix A) and, with the MIE,
 // those of the gradient formula, g^corr and J3 and the source Y (Appendix G).
 template <class S, bool MHD, bool SRT = false, int GEOM = 0>
-__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) step_kernel(const __grid_constant__ StepParams p) {
+__global__ void __launch_bounds__(NT, MHD ? (GEOM == 0 ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MIN_BLOCKS_MHD) : GOC_MIN_BLOCKS)
+    step_kernel(const __grid_constant__ StepParams p) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ FieldSmem sm;
@@ -1393,7 +1401,8 @@ __device__ __forceinline__ int batch_lattice(const BatchArgs &a, int t) {
 }
 
 template <class S, bool MHD, int GEOM = 0>
-__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD : GOC_MIN_BLOCKS) batch_step_kernel(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(NT, MHD ? (GEOM == 0 ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MIN_BLOCKS_MHD) : GOC_MIN_BLOCKS)
+    batch_step_kernel(const __grid_constant__ BatchArgs a) {
     using T = Tiling<S>;
     constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
     extern __shared__ __align__(128) unsigned char dyn[];
