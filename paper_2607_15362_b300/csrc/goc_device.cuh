@@ -207,18 +207,20 @@ __device__ __forceinline__ uint32_t node_seed(uint32_t idx, uint32_t step) {
 // Two values to a 16-bit format in one conversion, packed as (a << 16) | b:
 // with sr stochastically rounded by the hardware (cvt.rs: random bits 31..16
 // round a, bits 15..0 round b; each rounds away from zero with probability
-// equal to the discarded fraction), else rounded to nearest.
+// equal to the discarded fraction), else rounded to nearest; a value beyond
+// the format's range saturates to its largest finite value (as the truncating
+// conversion of the software rounding does), never to infinity.
 template <class S> __device__ __forceinline__ uint32_t cvt2(float a, float b, bool sr, uint32_t rbits);
 template <> __device__ __forceinline__ uint32_t cvt2<__half>(float a, float b, bool sr, uint32_t rbits) {
     uint32_t d;
-    if (sr) asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
-    else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(a), "f"(b));
+    if (sr) asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+    else asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(a), "f"(b));
     return d;
 }
 template <> __device__ __forceinline__ uint32_t cvt2<__nv_bfloat16>(float a, float b, bool sr, uint32_t rbits) {
     uint32_t d;
-    if (sr) asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
-    else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(a), "f"(b));
+    if (sr) asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+    else asm("cvt.rn.satfinite.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(a), "f"(b));
     return d;
 }
 // 32 random bits for one cvt2: the high halves of the next two LCG outputs
@@ -236,8 +238,12 @@ template <class S> __device__ __forceinline__ void st_pair(S *pa, S *pb, uint32_
 // drawn from r when stochastic rounding is on
 template <class S>
 __device__ __forceinline__ void put2(S *pa, S *pb, float a, float b, bool sr, uint32_t &r) {
-    const uint32_t rb = sr ? rand_pair_bits(r) : 0u;
-    st_pair<S>(pa, pb, cvt2<S>(a, b, sr, rb));
+    if (sr) {
+        st_pair<S>(pa, pb, cvt2<S>(a, b, true, rand_pair_bits(r)));
+    } else {   // round to nearest: the scalar conversions
+        Store<S>::st(pa, a);
+        if (pb) Store<S>::st(pb, b);
+    }
 }
 
 // store of one value: stochastic rounding for 16-bit storage when asked for

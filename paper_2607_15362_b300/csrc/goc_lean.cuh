@@ -53,7 +53,7 @@ __device__ __forceinline__ void lean_pull(const S *s, float sf, const AxisRecord
 // node) from the staged populations, then the collision of each node.  Every
 // thread of the block calls it (it contains the fields barrier).  st: the
 // stage (populations, then the stored force at Tiling<S>::OFF_FF).
-template <class S, bool MHD>
+template <class S, bool MHD, bool SEAM = false>
 __device__ __forceinline__ bool lean_tile(const StepParams &p, const unsigned char *st, int i0, int j0,
                                           FieldSmem &sm, bool ok) {
     using T = Tiling<S>;
@@ -91,7 +91,7 @@ __device__ __forceinline__ bool lean_tile(const StepParams &p, const unsigned ch
                 x = b < TY ? -1 : TX;
                 y = b < TY ? b : b - TY;
             }
-            const AxisRecord cq = axis_record(rec1, i0 + x), rq = axis_record(rec2, j0 + y);
+            const AxisRecord cq = axis_record(rec1, SEAM ? wrapi(i0 + x, p.nx) : i0 + x), rq = axis_record(rec2, j0 + y);
             const int sq = (y + HYS) * BX + x + T::HXS;
             float dd[9], a, u, v;
             lean_pull<S>(sf_ + sq, p.sf, cq, rq, dd);
@@ -118,15 +118,68 @@ __device__ __forceinline__ bool lean_tile(const StepParams &p, const unsigned ch
     SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
                      p.plane, p.pitch, p.sf, p.sF, p.sg};
     const float th[2] = {c.th, r.th};
-    collide<S, MHD, false, float, false, 0>(p, src, i, jj, own, dn, F1n, F2n, c.h, c.ih, h2n, ih2n, fl, urn, th);
+    // (SEAM: the MIE pull wraps across the periodic seam)
+    collide<S, MHD, SEAM, float, false, 0>(p, src, i, jj, own, dn, F1n, F2n, c.h, c.ih, h2n, ih2n, fl, urn, th);
     return true;
+}
+
+// Kind of a tile for the straight-grid kernel: tile_kind's 0 (interior), 1
+// (near a wall), 2 (halo across a periodic seam, global loads), and 3: a full
+// tile whose staged box crosses the periodic seam of xi1 only (inside the
+// lattice and away from walls along xi2, nx a multiple of the tile width).
+// Kind 3 is staged like kind 0 -- the copy fills the columns beyond the seam
+// with zeros -- and those columns are then copied from the other side of the
+// lattice (seam_fill), so the tile takes the interior path.  FP32 storage
+// only: with 16-bit storage the general path on global loads and the interior
+// path round the scaled values differently in the last bit (the compiler
+// fuses different products), and the slabs of one lattice, whose seam tiles
+// near a cut take the general path, must reproduce the lattice bitwise.
+template <class S>
+__device__ __forceinline__ int tile_kind_lean(const StepParams &p, int i0, int j0) {
+    const int k = tile_kind<S>(p, i0, j0);
+    if (Store<S>::scaled || k != 2 || !p.use_tma || p.nopull || !p.per_x || p.nx % TX) return k;
+    const bool wy = p.per_y && (j0 - HYS < 0 || j0 + TY + HYS > p.ny);
+    return !wy && j0 >= 2 && j0 + TY + 2 <= p.ny ? 3 : 2;
+}
+
+// Copy the columns of a kind-3 tile's stage that lie beyond the periodic seam
+// of xi1 (zero-filled by the copy) from the other side of the lattice: per
+// side, Tiling<S>::HXS columns (16 bytes) of each of the 11 planes and each
+// staged row inside the lattice, one 16-byte load and store per segment.
+// Called by every thread after the stage's copy has landed; the caller
+// separates it from the reads with a block barrier.
+template <class S>
+__device__ __forceinline__ void seam_fill(const StepParams &p, unsigned char *st, int i0, int j0) {
+    using T = Tiling<S>;
+    constexpr int SEG = T::HXS, NSEG = 11 * T::BY;
+    static_assert(SEG * sizeof(S) == 16, "a segment is 16 bytes");
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int q = tid; q < 2 * NSEG; q += NT) {
+        const int side = q >= NSEG ? 1 : 0, k = q - side * NSEG;
+        const int plane = k / T::BY, row = k - plane * T::BY;
+        const int bx0 = side ? T::BX - SEG : 0;
+        const int x0 = i0 - T::HXS + bx0, y = j0 - HYS + row;
+        if ((x0 >= 0 && x0 < p.nx) || y < 0 || y >= p.ny) continue;
+        const int xs = x0 < 0 ? x0 + p.nx : x0 - p.nx;
+        const S *src = plane < 9 ? static_cast<const S *>(p.fin) + plane * p.plane
+                                 : static_cast<const S *>(p.Fin) + (plane - 9) * p.plane;
+        src += (long long)y * p.pitch + xs;
+        unsigned char *dst = st + (plane < 9 ? 0 : T::OFF_FF) +
+                             (((plane < 9 ? plane : plane - 9) * T::BY + row) * T::BX + bx0) * (int)sizeof(S);
+        *reinterpret_cast<uint4 *>(dst) = __ldg(reinterpret_cast<const uint4 *>(src));
+    }
 }
 
 template <class S, bool MHD>
 __device__ __forceinline__ bool lean_run_tile(const StepParams &p, int kind, int i0, int j0,
-                                              const unsigned char *stage, FieldSmem &sm, bool ok) {
+                                              unsigned char *stage, FieldSmem &sm, bool ok) {
     if (kind == 0 && !p.nopull) return lean_tile<S, MHD>(p, stage, i0, j0, sm, ok);   // (the first step
                                                                                        // reads f^0 in place)
+    if (kind == 3) {   // (never for the first step: tile_kind_lean)
+        seam_fill<S>(p, stage, i0, j0);
+        __syncthreads();
+        return lean_tile<S, MHD, true>(p, stage, i0, j0, sm, ok);
+    }
     return run_tile<S, MHD, false, 0>(p, kind, i0, j0, stage, sm, ok);
 }
 
@@ -162,7 +215,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MI
         if (t < ntiles) {
             it.y = (t % ntx) * TX;
             it.z = (t / ntx) * TY;
-            it.w = tile_kind<S>(p, it.y, it.z);
+            it.w = tile_kind_lean<S>(p, it.y, it.z);
             if (it.w != 2) {
                 fence_proxy_async();
                 issue_tile<S>(m, it.y, it.z, dyn + stg * STAGE, &bars[stg], MHD);

@@ -56,20 +56,27 @@ def test_fp16_stochastic_rounding_matches_the_oracle(gpu, name, prob, steps, tol
 
 def test_stochastic_rounding_beats_nearest_on_a_slow_flow(gpu):
     """The 32 x 64 Poiseuille channel after 2000 steps: the body force builds the profile by increments
-    far below FP16 resolution; nearest rounding stalls, stochastic does not.  The per-row storage
-    reference is off here (it shrinks the stored values and with them the stall)."""
+    far below FP16 resolution.  Round to nearest drops them systematically, so the mean flow is biased;
+    stochastic rounding keeps them on average.  The per-row storage reference is off here (it shrinks
+    the stored values and with them the effect).  The bias is the robust measure: the relative L2 error
+    of the nearest-rounding run depends on last-bit differences of the arithmetic (measured 1.6e-3 to
+    3.9e-3 on the two tile shapes), its mean deviates by 0.9e-3 to 1.1e-3 of the mean flow in both,
+    the stochastic run's by about 1e-5."""
     p = gi.poiseuille_channel()
     spec = spec_of(p)
     o = oracle.Oracle(spec, threads=8)
     o.step(2000)
     uo = o.fields()[1]
-    err = {}
+    err, bias = {}, {}
     for rd in ("nearest", "stochastic"):
         L = goc.Lattice(spec, storage="fp16", rounding=rd, reference_every=-1)
         L.step(2000)
-        err[rd] = relerr(L.moments()[1], uo)
+        u = L.moments()[1]
+        err[rd] = relerr(u, uo)
+        bias[rd] = float((u - uo).sum() / uo.sum())
         L.close()
-    assert err["stochastic"] < 0.3 * err["nearest"]
+    assert err["stochastic"] <= 2e-3
+    assert abs(bias["stochastic"]) < 0.1 * abs(bias["nearest"])
 
 
 def test_stochastic_rounding_is_reproducible_and_checkpointable(gpu):
