@@ -479,4 +479,89 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MI
     }
 }
 
+// Many lattices in one launch (BatchArgs, goc_step.cuh): the tiles of all
+// members from one work queue; members on straight grids take the interior
+// and seam paths of the straight-grid kernel, the others the general path.
+template <class S, bool MHD, int GEOM = 0>
+__global__ void __launch_bounds__(NT, MHD ? (GEOM == 0 ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MIN_BLOCKS_MHD) : GOC_MIN_BLOCKS)
+    batch_step_kernel(const __grid_constant__ BatchArgs a) {
+    using T = Tiling<S>;
+    constexpr int STAGE = MHD ? T::STAGE_MHD : T::STAGE_NSE;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ FieldSmem sm;
+    __shared__ int4 s_item[2];   // per stage: item, i0, j0, 4 lattice + tile kind
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    const int items = a.toff[a.n];
+    if (leader) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    griddep_launch_dependents();
+    griddep_wait();   // the previous step of every member is complete
+    // record item t for stage st and start its copy (leader only); block b
+    // starts with item b, later items come from the counter
+    auto take = [&](int st, int t) {
+        int4 it = make_int4(t, 0, 0, 0);
+        if (t < items) {
+            const int k = batch_lattice(a, t);
+            const StepParams &q = a.p[k];
+            const int ntx = (q.nx + TX - 1) / TX, local = t - a.toff[k];
+            it.y = (local % ntx) * TX;
+            it.z = (local / ntx) * TY;
+            const int kind = GEOM == 0 ? tile_kind_lean<S>(q, it.y, it.z) : tile_kind<S>(q, it.y, it.z);
+            it.w = 4 * k + kind;
+            if (kind != 2) {
+                const TileMaps m{a.maps + 3 * k, a.maps + 3 * k + 1, a.maps + 3 * k + 2};
+                fence_proxy_async();   // generic reads of that stage precede the async writes
+                issue_tile<S>(m, it.y, it.z, dyn + st * STAGE, &bars[st], MHD);
+            }
+            if (local == 0 && Store<S>::scaled && q.sr) *q.seed_wr = *q.seed_rd + 1u;
+        }
+        s_item[st] = it;
+    };
+    constexpr bool AHEAD = !MHD;   // as in the single-lattice kernel
+    int pend = 0;   // leader: counter value of the item after the next one (fetched one tile ahead)
+    if (leader) {
+        if (blockIdx.x == 0) a.ctr[a.parity ^ 1] = 0;   // the next step's counter
+        if (AHEAD) pend = atomicAdd(&a.ctr[a.parity], 1);
+        take(0, blockIdx.x);
+    }
+    __syncthreads();
+    uint32_t ph0 = 0, ph1 = 0;
+    int stage = 0;
+    for (;;) {
+        const int4 it = s_item[stage];
+        if (it.x >= items) break;   // uniform: every thread reads the same shared value
+        if (leader) {
+            int nt;
+            if (AHEAD) {
+                nt = (int)gridDim.x + pend;
+                pend = atomicAdd(&a.ctr[a.parity], 1);
+            } else {
+                nt = (int)gridDim.x + atomicAdd(&a.ctr[a.parity], 1);
+            }
+            take(stage ^ 1, nt);
+        }
+        const int k = it.w >> 2, kind = it.w & 3, i0 = it.y, j0 = it.z;
+        const StepParams &p = a.p[k];
+        bool ok = true;   // every thread waits for the copy itself; the fields barrier gathers the outcome
+        if (kind != 2) {
+            uint32_t &ph = stage ? ph1 : ph0;
+            ok = mbar_wait_bounded(&bars[stage], ph, p.flag);
+            ph ^= 1;
+        }
+        if (MHD) {
+            if (!__syncthreads_and(ok)) return;
+        }
+        bool done;
+        if constexpr (GEOM == 0) done = lean_run_tile<S, MHD>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok);
+        else done = run_tile<S, MHD, false, GEOM>(p, kind, i0, j0, dyn + stage * STAGE, sm, ok);
+        if (!done) return;   // the block leaves together
+        __syncthreads();   // the stage, the field arrays and s_item are reused
+        stage ^= 1;
+    }
+}
+
 }  // namespace goc
