@@ -46,13 +46,28 @@ int step_grid(int ntiles, size_t *smem, bool balanced = false) {
 }
 
 // The same for the straight-grid kernel lean_step_kernel.
-template <class S, bool MHD>
+template <class S, bool MHD, bool SEAMS>
 int lean_grid(int ntiles, size_t *smem, bool balanced = false) {
     using T = Tiling<S>;
     const size_t bytes = 2 * (size_t)(MHD ? T::STAGE_MHD : T::STAGE_NSE);
     *smem = bytes;
     static int cached = -1;
-    return persistent_grid(lean_step_kernel<S, MHD>, bytes, ntiles, balanced, cached);
+    return persistent_grid(lean_step_kernel<S, MHD, SEAMS>, bytes, ntiles, balanced, cached);
+}
+
+// Launch lean_step_kernel with or without the seam path (kind-3 tiles exist
+// only for FP32 lattices periodic along xi1 whose width is a multiple of 32).
+template <class S, bool MHD>
+cudaError_t launch_lean(goc_lattice *L, const StepParams &p, int ntiles, bool pdl) {
+    size_t smem = 0;
+    if constexpr (!Store<S>::scaled) {
+        if (L->sp.per_x && L->nx % TX == 0) {
+            const int grid = lean_grid<S, MHD, true>(ntiles, &smem, L->cfg_balanced != 0);
+            return launch_pdl(pdl, lean_step_kernel<S, MHD, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p);
+        }
+    }
+    const int grid = lean_grid<S, MHD, false>(ntiles, &smem, L->cfg_balanced != 0);
+    return launch_pdl(pdl, lean_step_kernel<S, MHD, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p);
 }
 
 // The same for the 32 x 16 tile kernel lean2_step_kernel.
@@ -163,11 +178,9 @@ goc_status launch_step_t(goc_lattice *L, const StepParams &p) {
             CU(launch_pdl(pdl, lean2_step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, q));
         }
     } else if (lean_enabled() && L->mhd.enabled) {
-        const int grid = lean_grid<S, true>(ntiles, &smem, L->cfg_balanced != 0);
-        CU(launch_pdl(pdl, lean_step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        CU((launch_lean<S, true>(L, p, ntiles, pdl)));
     } else if (lean_enabled()) {
-        const int grid = lean_grid<S, false>(ntiles, &smem, L->cfg_balanced != 0);
-        CU(launch_pdl(pdl, lean_step_kernel<S, false>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));
+        CU((launch_lean<S, false>(L, p, ntiles, pdl)));
     } else if (L->mhd.enabled) {
         const int grid = step_grid<S, true>(ntiles, &smem, L->cfg_balanced != 0);
         CU(launch_pdl(pdl, step_kernel<S, true>, dim3(grid), dim3(TX, TYT), smem, L->stream, p));

@@ -170,12 +170,12 @@ __device__ __forceinline__ void seam_fill(const StepParams &p, unsigned char *st
     }
 }
 
-template <class S, bool MHD>
+template <class S, bool MHD, bool SEAMS = true>
 __device__ __forceinline__ bool lean_run_tile(const StepParams &p, int kind, int i0, int j0,
                                               unsigned char *stage, FieldSmem &sm, bool ok) {
     if (kind == 0 && !p.nopull) return lean_tile<S, MHD>(p, stage, i0, j0, sm, ok);   // (the first step
                                                                                        // reads f^0 in place)
-    if (kind == 3) {   // (never for the first step: tile_kind_lean)
+    if (SEAMS && kind == 3) {   // (never for the first step: tile_kind_lean)
         seam_fill<S>(p, stage, i0, j0);
         __syncthreads();
         return lean_tile<S, MHD, true>(p, stage, i0, j0, sm, ok);
@@ -184,8 +184,10 @@ __device__ __forceinline__ bool lean_run_tile(const StepParams &p, int kind, int
 }
 
 // Single lattice on a straight grid: persistent blocks take tiles from the
-// lattice's queue, as step_kernel does.
-template <class S, bool MHD>
+// lattice's queue, as step_kernel does.  SEAMS: the lattice has seam tiles of
+// kind 3 (FP32, periodic along xi1, width a multiple of 32); the other
+// lattices run an instantiation without that path.
+template <class S, bool MHD, bool SEAMS>
 __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MIN_BLOCKS)
     lean_step_kernel(const __grid_constant__ StepParams p) {
     using T = Tiling<S>;
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MI
         if (t < ntiles) {
             it.y = (t % ntx) * TX;
             it.z = (t / ntx) * TY;
-            it.w = tile_kind_lean<S>(p, it.y, it.z);
+            it.w = SEAMS ? tile_kind_lean<S>(p, it.y, it.z) : tile_kind<S>(p, it.y, it.z);
             if (it.w != 2) {
                 fence_proxy_async();
                 issue_tile<S>(m, it.y, it.z, dyn + stg * STAGE, &bars[stg], MHD);
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MI
         if (MHD) {
             if (!__syncthreads_and(ok)) return;
         }
-        if (!lean_run_tile<S, MHD>(p, it.w, it.y, it.z, dyn + stage * STAGE, sm, ok)) return;
+        if (!lean_run_tile<S, MHD, SEAMS>(p, it.w, it.y, it.z, dyn + stage * STAGE, sm, ok)) return;
         __syncthreads();
         stage ^= 1;
     }
