@@ -1096,6 +1096,13 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
         for (int s = 0; s < 4; s++)
             uref = std::max(uref, std::fabs(slab ? (slab->global->bc[s] == GOC_BC_WALL ? (double)(float)slab->global->wall_u[s] : 0.0)
                                                  : (double)p.uw[s]));
+        {   // a body force drives flows up to about the Poiseuille centreline speed F n^2 / (8 nu)
+            // across the lattice's extent n (the whole lattice's for a slab)
+            const goc_grid *gg = slab ? slab->global : grid;
+            const double fx = std::max(std::fabs(L->flow.fext[0]), std::fabs(L->flow.fext[1]));
+            const double n = (double)std::max(gg->nx, gg->ny);
+            if (fx > 0.0 && L->nu > 0.0) uref = std::max(uref, fx * n * n / (8.0 * L->nu));
+        }
         double hmax = 1.0;   // scale so that |deviation| / s stays well inside the 16-bit range
         double sf = L->flow.rho0 * uref * hmax / 256.0;
         p.sf = (float)sf;
