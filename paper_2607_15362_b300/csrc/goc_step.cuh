@@ -693,7 +693,71 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
     }
 
     // ---- MIE (Appendix G): local dB, J3, Lorentz force, SRT collision -------
-    if constexpr (MHD) {
+    if constexpr (MHD && GEOM == 0 && R == 1) {
+        // The same MIE update for one node on a straight grid with the two
+        // field components c = 0, 1 as the lanes of packed FP32 pairs (every
+        // formula below is the same for both components).
+        S *gout = static_cast<S *>(p.gout);
+        float t[2][5];
+#pragma unroll
+        for (int c = 0; c < 2; c++) pull_mie<CHECKS, 0, REF>(p, src, i, j[0], h1, h2n[0], c, t[c]);
+        float2 GD[5];
+#pragma unroll
+        for (int a = 0; a < 5; a++) GD[a] = f2(t[0][a], t[1][a]);
+        // h1 h2 B = sum g (Eq. 13_C, Y = 0 on straight grids); sum g_ref- = H B_rest
+        const float2 GMOV = add2(add2(GD[1], GD[3]), add2(GD[2], GD[4]));   // the four moving links
+        const float2 GSUM = add2(GD[0], GMOV);
+        const float2 DBC = mul2(GSUM, iH);
+        B1 = DBC.x + bref<REF>(p, 0, j[0]);
+        B2 = DBC.y + bref<REF>(p, 1, j[0]);
+        // A_cd = U_d B_c - B_d U_c (Eq. 2_C): (A1[0], A1[1]) = (0, A12), (A2[0], A2[1]) = (-A12, 0)
+        const float A12 = U1 * B2 - B1 * U2;
+        const float2 A1 = f2(0.f, A12), A2 = f2(-A12, 0.f);
+        // Eqs. gradB1/gradB2 with Lambda^(1) = sum e (g - g^eq(0))
+        const float k1 = rcpv(fmaf(h2 * ih1, p.taum - 0.5f, H * 0.5f) * p.csm2);
+        const float k2 = rcpv(fmaf(h1 * ih2, p.taum - 0.5f, H * 0.5f) * p.csm2);
+        const float m1 = H * (0.5f * p.csm2 * h1 * t11), m2 = H * h2 * t22 * (0.5f * p.csm2);
+        const float2 DB1 = mul2(fma2(DBC, m1, fma2(A1, -h2, sub2(GD[1], GD[3]))), -k1);
+        const float2 DB2 = mul2(fma2(DBC, m2, fma2(A2, -h1, sub2(GD[2], GD[4]))), -k2);
+        // current density (Eq. currentdensity-GOC) and Lorentz force (Eq. Lorentzforce-GOC)
+        const float J3 = iH * (h2 * DB1.y - DB2.x * h1) * p.imum;
+        FL1 = -J3 * B2;
+        FL2 = J3 * B1;
+        // SRT collision (Eq. 12_C) written as in the general form below
+        const float e1c = (H - h2 * ih1) * p.eta, e2c = (H - h1 * ih2) * p.eta;
+        const float m1e = H * (p.eta * h1 * t11), m2e = H * h2 * t22 * p.eta;
+        const float2 X1 = mul2(fma2(A1, h2, fma2(DB1, e1c, mul2(DBC, m1e))), p.icsm2);
+        const float2 X2 = mul2(fma2(A2, h1, fma2(DB2, e2c, mul2(DBC, m2e))), p.icsm2);
+        float2 Geq[5];
+        Geq[1] = mul2(add2(GSUM, X1), p.W1);
+        Geq[2] = mul2(add2(GSUM, X2), p.W1);
+        Geq[3] = mul2(sub2(GSUM, X1), p.W1);
+        Geq[4] = mul2(sub2(GSUM, X2), p.W1);
+        const float2 Q0 = sub2(GMOV, add2(add2(Geq[1], Geq[3]), add2(Geq[2], Geq[4])));   // g^eq_0 - g_0
+        float2 GT[5];
+        GT[0] = fma2(Q0, p.itaum, GD[0]);
+#pragma unroll
+        for (int a = 1; a < 5; a++) GT[a] = fma2(sub2(Geq[a], GD[a]), p.itaum, GD[a]);
+        if (own[0]) {
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                S *go = gout + c * 5 * p.plane + idx[0];
+                float gt[5];
+#pragma unroll
+                for (int a = 0; a < 5; a++) gt[a] = c ? GT[a].y : GT[a].x;
+                if constexpr (Store<S>::scaled) {   // pairs through one conversion each
+                    const float is = p.isg;
+                    const long long pl = p.plane;
+                    put2<S>(go, go + pl, gt[0] * is, gt[1] * is, sr, rng[0]);
+                    put2<S>(go + 2 * pl, go + 3 * pl, gt[2] * is, gt[3] * is, sr, rng[0]);
+                    put2<S>(go + 4 * pl, static_cast<S *>(nullptr), gt[4] * is, 0.f, sr, rng[0]);
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 5; a++) put<S>(go + a * p.plane, gt[a], sr, rng[0]);
+                }
+            }
+        }
+    } else if constexpr (MHD) {
         S *gout = static_cast<S *>(p.gout);
         V gd[2][5], dBc[2], dB1[2], dB2[2], gsum[2], gmov[2];
 #pragma unroll
