@@ -950,3 +950,50 @@ def test_transposed_annulus_with_the_mie_gives_the_transposed_solution():
     np.testing.assert_allclose(ua, vb.T, atol=1e-12 * np.abs(va).max())
     np.testing.assert_allclose(b1a, b2b.T, atol=1e-12 * sb)
     np.testing.assert_allclose(b2a, b1b.T, atol=1e-12 * sb)
+
+
+def test_spiral_node_table_is_the_metric_of_its_conformal_map():
+    """The logarithmic-spiral node table (goc_inputs.spiral_grid), which feeds
+    both the oracle and the library, against the map it stands for, computed
+    here from the map alone: z(w) = exp(a (w - w0)) / a with w = xi1 + i xi2,
+    a = c e^{i phi}.  h_k = |dr/dxi_k| by central differences of the node
+    positions, the coordinate lines orthogonal (Eq. metricfactor with a
+    diagonal metric), and theta_ij = (dh_i/dxi_j) / (h_i h_j) by central
+    differences of those h (Eq. curvaturematrix), at every node and on the
+    four walls."""
+    nx, ny, c, phi = 24, 21, 1.0 / math.hypot(24, 21), 0.6
+    g = gi.spiral_grid(nx, ny, c, phi)
+    a = c * complex(math.cos(phi), math.sin(phi))
+    w0 = complex(nx / 2.0, ny / 2.0)
+
+    def r(x1, x2):
+        z = np.exp(a * (x1 + 1j * x2 - w0)) / a
+        return np.stack([z.real, z.imag])
+
+    d = 1e-4
+
+    def hk(x1, x2):
+        r1 = (r(x1 + d, x2) - r(x1 - d, x2)) / (2 * d)
+        r2 = (r(x1, x2 + d) - r(x1, x2 - d)) / (2 * d)
+        return np.linalg.norm(r1, axis=0), np.linalg.norm(r2, axis=0), (r1 * r2).sum(axis=0)
+
+    x1 = (np.arange(nx) + 0.5)[None, :] * np.ones((ny, 1))
+    x2 = (np.arange(ny) + 0.5)[:, None] * np.ones((1, nx))
+    h1, h2, dot = hk(x1, x2)
+    np.testing.assert_allclose(g["h1"], h1, rtol=1e-7)
+    np.testing.assert_allclose(g["h2"], h2, rtol=1e-7)
+    assert np.abs(dot).max() <= 1e-8 * (h1 * h2).max()
+    e = 1e-3
+    dh = {(k, m): (hk(x1 + e * (m == 1), x2 + e * (m == 2))[k - 1] - hk(x1 - e * (m == 1), x2 - e * (m == 2))[k - 1]) / (2 * e)
+          for k in (1, 2) for m in (1, 2)}
+    hh = {1: h1, 2: h2}
+    for (k, m), key in (((1, 1), "t11"), ((1, 2), "t12"), ((2, 1), "t21"), ((2, 2), "t22")):
+        theta = dh[(k, m)] / (hh[k] * hh[m])
+        np.testing.assert_allclose(g[key], theta, rtol=1e-5, atol=1e-9)
+    i_, j_ = np.arange(nx) + 0.5, np.arange(ny) + 0.5
+    for side, (p1, p2) in {"W": (np.zeros(ny), j_), "E": (np.full(ny, float(nx)), j_),
+                           "S": (i_, np.zeros(nx)), "N": (i_, np.full(nx, float(ny)))}.items():
+        w1, w2, _ = hk(p1, p2)
+        normal, tangential = (w1, w2) if side in "WE" else (w2, w1)
+        np.testing.assert_allclose(g["wall"][side][0], normal, rtol=1e-7)
+        np.testing.assert_allclose(g["wall"][side][1], tangential, rtol=1e-7)
