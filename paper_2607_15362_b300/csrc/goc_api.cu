@@ -144,7 +144,17 @@ StepParams params_for(goc_lattice *L, int src, float *uout) {
     return p;
 }
 
+// Zero the tile queues of both parities after steps of a batch kernel, which
+// leaves them as they were (called outside graph capture).
+goc_status clean_queues(goc_lattice *L) {
+    if (!L->queues_dirty) return GOC_OK;
+    CU(cudaMemsetAsync(L->flag + 4, 0, 2 * sizeof(int), L->stream));
+    L->queues_dirty = false;
+    return GOC_OK;
+}
+
 goc_status launch_one(goc_lattice *L, float *uout) {
+    if (goc_status st = clean_queues(L); st != GOC_OK) return st;
     StepParams p = params_for(L, L->cur, uout);
     p.nopull = L->fresh ? 1 : 0;
     goc_status st;
@@ -240,6 +250,7 @@ goc_status autotune(goc_lattice *L, long long *nsteps) {
 }
 
 goc_status ensure_graph(goc_lattice *L) {
+    if (goc_status st = clean_queues(L); st != GOC_OK) return st;
     if (L->graph) return GOC_OK;
     // capture kGraphSteps launches on a private stream (the lattice stream may
     // be the legacy default stream, which cannot be captured)
@@ -1895,6 +1906,7 @@ goc_status goc_batch_step(goc_batch *B, long long nsteps) {
                 L->steps += 1;
                 L->cur ^= 1;
                 L->fresh = false;
+                L->queues_dirty = true;
             }
         if (--nsteps == 0) return GOC_OK;
     }
@@ -1952,6 +1964,7 @@ goc_status goc_batch_step(goc_batch *B, long long nsteps) {
         if (L) {
             L->steps += nsteps;
             L->cur ^= (int)(nsteps & 1);
+            L->queues_dirty = true;
             // per-row storage reference of 16-bit members: refreshed at the end of
             // the call in which its step count reaches the next refresh point
             goc_status st = ref_maybe_refresh(L);

@@ -121,7 +121,9 @@ struct StepParams {
     int constF;                // 1: no stored force; the force of every step is the body force
     // tile queue of the single-lattice step kernel: this launch takes tiles from
     // *tctr and zeroes *tctr_next for the launch of the other buffer parity
-    // (tctr == null: static order, block b takes tiles b, b + grid, ...)
+    // (tctr == null: static order, block b takes tiles b, b + grid, ...).
+    // Every launch zeroes tctr_next, whether it takes tiles from a queue or
+    // not, so that a change of tile order between steps finds it clean.
     int *tctr;
     int *tctr_next;
     const unsigned *seed_rd;

@@ -100,6 +100,10 @@ struct goc_lattice {
     int cfg_balanced = 0;                        // grid: the fewest blocks taking the same rounds of tiles
     int cfg_rows = 1;                            // straight grids: tiles of 8 (1) or 16 (2) rows
     bool tuned = false;                          // chosen by the launch autotuner (or fixed)
+    // Each single-lattice step kernel zeroes the tile queue of the other
+    // buffer parity, which the next step uses; steps taken by a batch kernel
+    // do not, and the next single-lattice launch zeroes both first.
+    bool queues_dirty = false;
     int plateau_checks = 0;                      // goc_exec.plateau_checks
     // per-row storage reference (16-bit storage on straight grids; see goc_aux.cuh)
     double *ref64 = nullptr;                     // FP64 master rows [3][ny] (A1, Bref_1, Bref_2), then the next rows

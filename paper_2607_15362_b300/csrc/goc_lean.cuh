@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MI
     griddep_wait();
     if (leader && blockIdx.x == 0) {
         if (Store<S>::scaled && p.sr) *p.seed_wr = *p.seed_rd + 1u;
-        if (p.tctr) *p.tctr_next = 0;
+        if (p.tctr_next) *p.tctr_next = 0;
     }
     const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
     int *ctr = p.tctr;
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MI
     griddep_wait();
     if (leader && blockIdx.x == 0) {
         if (Store<S>::scaled && p.sr) *p.seed_wr = *p.seed_rd + 1u;
-        if (p.tctr) *p.tctr_next = 0;
+        if (p.tctr_next) *p.tctr_next = 0;
     }
     const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
     int *ctr = p.tctr;

@@ -1429,7 +1429,7 @@ __global__ void __launch_bounds__(NT, MHD ? (GEOM == 0 ? GOC_MIN_BLOCKS_MHD_STRA
     griddep_wait();   // the previous step is complete: its populations may be read and overwritten
     if (leader && blockIdx.x == 0) {
         if (Store<S>::scaled && p.sr) *p.seed_wr = *p.seed_rd + 1u;   // next step's index
-        if (p.tctr) *p.tctr_next = 0;                                  // next step's tile queue
+        if (p.tctr_next) *p.tctr_next = 0;                                  // next step's tile queue
     }
     const TileMaps m{&p.tm_f, &p.tm_F, &p.tm_g};
     lattice_tiles<S, MHD, SRT, GEOM>(p, m, p.tctr, blockIdx.x, gridDim.x, dyn, bars, sm, s_item, leader);

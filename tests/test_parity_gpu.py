@@ -356,6 +356,28 @@ def test_launch_configurations_give_bitwise_identical_populations(gpu):
         A.close()
 
 
+def test_tile_queues_survive_changes_of_launch_configuration(gpu):
+    """The tile queues of the two buffer parities stay consistent when the
+    tile order or the tile height changes between steps, each setting for an
+    odd number of steps: the populations equal those of one configuration
+    throughout, bitwise."""
+    prob = gi.Problem("cavity", 200, 90, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
+                      {"Re": 100.0, "u_lid": 0.05})
+    spec = prob.lattice_spec(cs2_of(prob))
+    ref = goc.Lattice(spec)
+    ref.set_launch_config(True, True)
+    ref.step(1 + 7 + 5 + 3 + 9 + 7 + 11)
+    want = ref.get_state()
+    ref.close()
+    L = goc.Lattice(spec)
+    L.step(1)
+    for dyn, rows, n in ((True, 8, 7), (False, 8, 5), (True, 16, 3), (False, 16, 9), (True, 8, 7), (False, 8, 11)):
+        L.set_launch_config(dyn, True, tile_rows=rows)
+        L.step(n)
+    assert L.get_state() == want
+    L.close()
+
+
 def test_tall_tiles_are_for_straight_grids_only(gpu):
     """The 32 x 16 tiles run the straight-grid central-moment kernel; a curved
     grid reports 8-row tiles and refuses 16."""
