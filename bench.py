@@ -214,7 +214,9 @@ def run_ours(args):
     _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
     spec = _spec(args, prob, cs2)
     geom = 2 if spiral else 1 if annulus else 0
-    lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream, scheme=args.scheme)
+    in_place = args.streaming == "in_place"
+    lat = goc.Lattice(spec, storage=args.storage, stream=stream.cuda_stream, scheme=args.scheme,
+                      streaming=args.streaming)
     nodes = prob.nodes
     chunk = args.chunk
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -275,7 +277,7 @@ def run_ours(args):
     prof = PROFILE_SPIRAL if spiral else PROFILE
     # the captures are of FP32 512^2 launches of the central-moment NSE step on the two cavity grids
     captured = (args.cavity_n == 512 and args.storage == "fp32" and not annulus and not args.mie
-                and args.scheme == "goc")
+                and args.scheme == "goc" and not in_place)
     traffic = profile_traffic(prof) if captured else None
     clocks = clk.summary()
     # instruction-issue view of the same kernel: warp instructions per node
@@ -297,7 +299,7 @@ def run_ours(args):
         cpu = cpu_baseline(prob, spec, budget_s=args.cpu_seconds)
     extras = None
     headline = (args.cavity_n == 512 and args.grid == "tanh" and args.storage == "fp32" and not args.mie
-                and args.scheme == "goc")
+                and args.scheme == "goc" and not in_place)
     if rank == 0 and world == 1 and headline and not args.no_extras:
         extras = extra_numbers(args)
 
@@ -319,6 +321,7 @@ def run_ours(args):
                        "lid_mach": None if annulus else 0.087,
                        "mie": bool(args.mie), "collision": args.scheme,
                        "storage": args.storage,
+                       "streaming": args.streaming,
                        "parallelism": f"replicas x{world}" if world > 1 else "single lattice",
                        "l2": f"flushed between timed steps (256 MiB write); lattice ({nodes * bpn / 1e6:.0f} MB) "
                              + ("is L2-resident within a step" if nodes * bpn < 100e6 else "exceeds L2")},
@@ -327,13 +330,14 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": src, "bytes_per_node": bpn,
-                         "kernel": step_kernel_name(args.storage, bool(args.mie), args.scheme, geom,
-                                                    lat.launch_config.get("tile_rows", 8)),
+                         "kernel": ("goc::aa_fields_kernel + goc::aa_collide_kernel (in place)" if in_place
+                                    else step_kernel_name(args.storage, bool(args.mie), args.scheme, geom,
+                                                          lat.launch_config.get("tile_rows", 8))),
                          "launch_us": round(launch_s * 1e6, 3),
                          "launch_config": lat.launch_config, "issue": issue},
             "cpu_baseline": cpu,
             "extras": extras,
-            "gpu_launches": args.steps * chunk,
+            "gpu_launches": args.steps * chunk * (2 if in_place else 1),
             "clocks": clocks,
             "wall_s": round(wall, 3),
         }
@@ -997,6 +1001,8 @@ def main():
     ap.add_argument("--grid", default="tanh", choices=["tanh", "spiral", "annulus"],
                     help="tanh map on both axes (the benchmark cavity), the cavity on a logarithmic-spiral node "
                          "table, or Taylor-Couette flow on the annular sector")
+    ap.add_argument("--streaming", default="two_buffers", choices=["two_buffers", "in_place"],
+                    help="in_place: one population buffer updated in place (FP32, straight grids, no MIE)")
     ap.add_argument("--scheme", default="goc", choices=["goc", "goc_srt", "goc_raw"],
                     help="collision: central-moment MRT (the benchmark), SRT (Appendix F), raw-moment MRT (Appendix D)")
     ap.add_argument("--mie", action="store_true", help="couple the MIE (Appendix G)")

@@ -183,6 +183,16 @@ typedef struct {
                                goc_step refreshes exactly at multiples of the period; in a
                                batch, at the end of the goc_batch_step call that reaches one.
                                Ignored for FP32 storage, curved grids and scheme 1. */
+    int streaming;          /* 0 = two population buffers, read one and write the other (default);
+                               1 = one buffer updated in place: two access patterns alternate
+                               (the post-collision populations kept at their node with the link
+                               reversed, then at the node they stream to), each step a fields
+                               pass and a collision pass.  56 B per node resident instead of
+                               88 B, 156 B moved per step instead of 88 B; the populations
+                               are bitwise those of streaming 0.  FP32 storage, scheme 0, no
+                               MIE, per-axis maps (else GOC_EUNSUPPORTED); not in batches or
+                               slabs; goc_get_state / goc_set_state keep the layout, so a
+                               state moves only between lattices of the same streaming. */
 } goc_exec;
 
 /* ---- lifecycle --------------------------------------------------------- */

@@ -35,7 +35,7 @@ class GocMhd(ctypes.Structure):
 class GocExec(ctypes.Structure):
     _fields_ = [("storage", c_int), ("cuda_stream", c_void_p), ("device", c_int), ("check_every", c_int),
                 ("rounding", c_int), ("scheme", c_int), ("fixed_launch", c_int), ("plateau_checks", c_int),
-                ("reference_every", c_int)]
+                ("reference_every", c_int), ("streaming", c_int)]
 
 
 GOC_OK, GOC_EINVAL, GOC_ENOMEM, GOC_ECUDA, GOC_EDIVERGED, GOC_ETIMEOUT, GOC_EBUSY, GOC_EUNSUPPORTED = \

@@ -13,7 +13,7 @@ LIB = os.path.join(HERE, "libgoc.so")
 # storage type
 SOURCES = ["goc_api.cu", "goc_kernels_f32.cu", "goc_kernels_f16.cu", "goc_kernels_bf16.cu"]
 DEPS = SOURCES + ["goc_step.cuh", "goc_aux.cuh", "goc_device.cuh", "goc_vec.cuh", "goc_std.cuh",
-                  "goc_internal.h", "goc_launch.cuh", "goc_lean.cuh"]
+                  "goc_internal.h", "goc_launch.cuh", "goc_lean.cuh", "goc_aa.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC"]
 

@@ -158,10 +158,14 @@ goc_status launch_one(goc_lattice *L, float *uout) {
     StepParams p = params_for(L, L->cur, uout);
     p.nopull = L->fresh ? 1 : 0;
     goc_status st;
-    switch (L->storage) {
-        case GOC_FP16_DEV: st = launch_step_t<__half>(L, p); break;
-        case GOC_BF16_DEV: st = launch_step_t<__nv_bfloat16>(L, p); break;
-        default: st = launch_step_t<float>(L, p); break;
+    if (L->aa) {
+        st = launch_aa_step(L, p);
+    } else {
+        switch (L->storage) {
+            case GOC_FP16_DEV: st = launch_step_t<__half>(L, p); break;
+            case GOC_BF16_DEV: st = launch_step_t<__nv_bfloat16>(L, p); break;
+            default: st = launch_step_t<float>(L, p); break;
+        }
     }
     if (st != GOC_OK) return st;
     L->cur ^= 1;
@@ -524,9 +528,13 @@ void free_lattice(goc_lattice *L) {
     if (!L) return;
     cudaStreamSynchronize(L->stream);
     if (L->graph) cudaGraphExecDestroy(L->graph);
+    if (L->aa) {   // one buffer, named twice
+        L->f[1] = nullptr;
+        L->F[1] = nullptr;
+    }
     void *ptrs[] = {L->f[0], L->f[1], L->F[0], L->F[1], L->g[0], L->g[1], L->tab1, L->tab2,
                     L->m1, L->m2, L->gm, L->uout[0], L->uout[1], L->flag, L->red, L->mom,
-                    L->ref64, L->reft};
+                    L->ref64, L->reft, L->aa_fld, L->aa_wsum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (L->flag_ev) cudaEventDestroy(L->flag_ev);
@@ -613,6 +621,7 @@ goc_status ref_maybe_refresh(goc_lattice *L) {
 goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const double *u2,
                     const double *b1, const double *b2, bool persistent_staging = false) {
     const long long N = (long long)L->nx * L->ny;
+    if (L->aa) L->cur = 0;   // in place: the parity names the layout, and the first step reads f^0
     // staging of the five FP64 fields on the device: the moments buffer (kept
     // for later calls) when asked, else a temporary allocation
     double *dev = nullptr;
@@ -712,6 +721,7 @@ goc_status moments_to_device(goc_lattice *L) {
     }
     StepParams p = params_for(L, L->cur, nullptr);
     p.nopull = L->fresh ? 1 : 0;
+    if (L->aa) return launch_aa_moments(L, p, L->mom);
     dim3 grid((L->nx + 127) / 128, L->ny), block(128);
     const bool m = L->mhd.enabled;
     switch (L->storage) {
@@ -836,6 +846,14 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
         if (flow->gi_correction) return fail(GOC_EINVAL, "the standard uniform-grid scheme needs gi_correction = 0");
         if (mhd && mhd->enabled) return fail(GOC_EINVAL, "the standard uniform-grid scheme has no MIE");
     }
+    if (exec && (exec->streaming < 0 || exec->streaming > 1))
+        return fail(GOC_EINVAL, "unknown streaming %d", exec->streaming);
+    if (exec && exec->streaming == 1) {
+        const bool straight = map->kind[0] != GOC_MAP_ANNULUS && map->kind[0] != GOC_MAP_TABLE;
+        if (exec->storage != GOC_FP32 || exec->scheme != 0 || (mhd && mhd->enabled) || !straight)
+            return fail(GOC_EUNSUPPORTED,
+                        "in-place streaming needs FP32 storage, scheme 0, no MIE and a straight grid");
+    }
     goc_lattice *L = new (std::nothrow) goc_lattice();
     if (!L) return fail(GOC_ENOMEM, "host allocation failed");
     L->grid = *grid;
@@ -859,6 +877,8 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
         L->rounding = exec->rounding;
         L->scheme = exec->scheme;
         L->tuned = exec->fixed_launch != 0;
+        L->aa = exec->streaming == 1;
+        if (L->aa) L->tuned = true;   // its two launches per step have no tile order to tune
         L->plateau_checks = std::max(0, exec->plateau_checks);
         if (exec->device >= 0) {
             cudaError_t e = cudaSetDevice(exec->device);
@@ -883,10 +903,17 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
             return s_;         \
         }                      \
     } while (0)
-    for (int b = 0; b < 2; b++) {
+    for (int b = 0; b < (L->aa ? 1 : 2); b++) {
         TRY(dalloc(L, &L->f[b], 9 * L->plane * es + guard_tail(L)));
         TRY(dalloc(L, &L->F[b], 2 * L->plane * es + guard_tail(L)));
         if (L->mhd.enabled) TRY(dalloc(L, &L->g[b], 10 * L->plane * es + guard_tail(L)));
+    }
+    if (L->aa) {   // in place: one population and force buffer, the fields of the current step
+        L->f[1] = L->f[0];
+        L->F[1] = L->F[0];
+        L->aa_wn = std::max(L->nx, L->ny);
+        TRY(dalloc(L, &L->aa_fld, 3 * L->plane * sizeof(float)));
+        TRY(dalloc(L, &L->aa_wsum, 4 * (size_t)L->aa_wn * sizeof(float)));
     }
     const bool curv = map->kind[0] == GOC_MAP_ANNULUS;
     TRY(dalloc(L, &L->tab1, 16 * (size_t)L->nx * sizeof(float)));   // 8 rows, then the per-index records
@@ -1330,6 +1357,9 @@ double goc_bytes_per_node(const goc_lattice *L) {
     if (!L) return 0.0;
     const double es = (double)elem_size(L->storage);
     if (L->scheme == 1) return 2.0 * 9.0 * es;          // populations only, read + write
+    if (L->aa)   // fields pass: populations, force read, fields written; collision pass: populations, force
+                 // and fields read, populations and force written
+        return 4.0 * (11.0 + 3.0 + 11.0 + 3.0 + 11.0) + 4.0 * 7.0 / L->ny + 4.0 * 7.0 / L->nx;
     double b = 2.0 * (9.0 + 2.0) * es;                  // populations + stored force, read + write
     if (L->mhd.enabled) b += 2.0 * 10.0 * es;           // MIE populations
     if (L->sp.curv == 2) return b + 4.0 * 10.0;         // node-table metric: 10 FP32 values per node
@@ -1476,8 +1506,11 @@ goc_status goc_get_state(goc_lattice *L, void *buf, size_t *bytes) {
     }
     if (*bytes < total) return fail(GOC_EINVAL, "buffer too small (%zu < %zu)", *bytes, total);
     char *c = static_cast<char *>(buf);
+    // hdr[7]: 1 the state is f^0 (the next step reads it in place); in-place
+    // lattices add 2, and 4 when the populations are in the layout of odd
+    // parity (see goc_aa.cuh)
     long long hdr[8] = {0x474f434c4154ll, L->nx, L->ny, L->storage, L->mhd.enabled, L->steps, (long long)total,
-                        L->fresh ? 1 : 0};
+                        (L->fresh ? 1 : 0) | (L->aa ? 2 : 0) | (L->aa && L->cur ? 4 : 0)};
     std::memcpy(c, hdr, sizeof hdr);
     CU(cudaMemcpyAsync(c + 64, L->f[L->cur], nf, cudaMemcpyDeviceToHost, L->stream));
     CU(cudaMemcpyAsync(c + 64 + nf, L->F[L->cur], nF, cudaMemcpyDeviceToHost, L->stream));
@@ -1498,8 +1531,10 @@ goc_status goc_set_state(goc_lattice *L, const void *buf, size_t bytes) {
     const size_t nf = 9 * L->plane * es, nF = 2 * L->plane * es, ng = L->mhd.enabled ? 10 * L->plane * es : 0;
     const size_t nr = L->ref64 ? 3 * (size_t)L->ny * sizeof(double) : 0;
     if (hdr[0] != 0x474f434c4154ll || hdr[1] != L->nx || hdr[2] != L->ny || hdr[3] != L->storage ||
-        hdr[4] != L->mhd.enabled || (size_t)hdr[6] != 64 + nf + nF + ng + nr || bytes < 64 + nf + nF + ng + nr)
+        hdr[4] != L->mhd.enabled || (size_t)hdr[6] != 64 + nf + nF + ng + nr || bytes < 64 + nf + nF + ng + nr ||
+        ((hdr[7] & 2) != 0) != L->aa)
         return fail(GOC_EINVAL, "state does not match this lattice");
+    if (L->aa) L->cur = (hdr[7] & 4) ? 1 : 0;   // the layout of the saved populations
     CU(cudaMemcpyAsync(L->f[L->cur], c + 64, nf, cudaMemcpyHostToDevice, L->stream));
     CU(cudaMemcpyAsync(L->F[L->cur], c + 64 + nf, nF, cudaMemcpyHostToDevice, L->stream));
     if (ng) CU(cudaMemcpyAsync(L->g[L->cur], c + 64 + nf + nF, ng, cudaMemcpyHostToDevice, L->stream));
@@ -1514,7 +1549,7 @@ goc_status goc_set_state(goc_lattice *L, const void *buf, size_t bytes) {
     CU(cudaStreamSynchronize(L->stream));
     if (L->hflag) *L->hflag = 0;
     L->steps = hdr[5];
-    L->fresh = hdr[7] != 0;
+    L->fresh = (hdr[7] & 1) != 0;
     if (L->ref_every > 0) L->ref_next = (L->steps / L->ref_every + 1) * L->ref_every;
     return GOC_OK;
 }
@@ -1530,6 +1565,7 @@ goc_status goc_create_slab(const goc_grid *grid, const goc_map *map, const goc_f
     if (st != GOC_OK) return st;
     if (map->kind[0] == GOC_MAP_ANNULUS || map->kind[0] == GOC_MAP_TABLE)
         return fail(GOC_EUNSUPPORTED, "slabs take per-axis maps (straight grids)");
+    if (exec && exec->streaming != 0) return fail(GOC_EUNSUPPORTED, "slabs keep two population buffers");
     const bool per = grid->bc[2] == GOC_BC_PERIODIC;
     if (!(0 <= row_begin && row_begin + kSlabGhost <= row_end && row_end <= grid->ny))
         return fail(GOC_EINVAL, "slab rows [%d, %d) of %d: need 0 <= begin, end - begin >= %d, end <= ny",
@@ -1808,6 +1844,7 @@ goc_status goc_batch_create(long long hbm_budget_bytes, int max_lattices, const 
     if (!out) return fail(GOC_EINVAL, "out is NULL");
     *out = nullptr;
     if (hbm_budget_bytes <= 0 || max_lattices <= 0) return fail(GOC_EINVAL, "budget and max_lattices must be > 0");
+    if (exec && exec->streaming != 0) return fail(GOC_EUNSUPPORTED, "batched lattices keep two population buffers");
     goc_batch *B = new (std::nothrow) goc_batch();
     if (!B) return fail(GOC_ENOMEM, "host allocation failed");
     B->budget = hbm_budget_bytes;

@@ -114,6 +114,13 @@ struct goc_lattice {
     // owned, slab_glo / slab_ghi ghost rows below / above them
     bool slab = false;
     int slab_r0 = 0, slab_r1 = 0, slab_glo = 0, slab_ghi = 0;
+    // in place (goc_exec.streaming = 1, goc_aa.cuh): f[1] and F[1] name the
+    // single buffers f[0], F[0]; cur names the layout of the populations
+    // (fresh: f^0; else 1 after odd steps, 0 after even ones)
+    bool aa = false;
+    float *aa_fld = nullptr;                     // [3][plane] rho - rho0, U1, U2 of the step in progress
+    float *aa_wsum = nullptr;                    // [4][aa_wn] population sums of the wall nodes
+    int aa_wn = 0;
 };
 
 // Per-storage-type launchers (S = float, __half, __nv_bfloat16), defined in
@@ -128,5 +135,9 @@ cudaError_t batch_launch_t(int mhd, int geom, dim3 gd, dim3 bd, size_t smem, cud
     extern template int batch_grid_t<S>(int, int, int *);                                                \
     extern template cudaError_t batch_launch_t<S>(int, int, dim3, dim3, size_t, cudaStream_t, const goc::BatchArgs &);
 GOC_DECLARE_LAUNCHERS(float)
+// in-place lattices (FP32; goc_kernels_f32.cu): one step (fields pass, then
+// collision pass), and the macroscopic fields into out ([5][ny][nx] FP64)
+goc_status launch_aa_step(goc_lattice *L, const StepParams &p);
+goc_status launch_aa_moments(goc_lattice *L, const StepParams &p, double *out);
 GOC_DECLARE_LAUNCHERS(__half)
 GOC_DECLARE_LAUNCHERS(__nv_bfloat16)

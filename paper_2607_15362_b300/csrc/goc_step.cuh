@@ -128,6 +128,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // ---- where the stored values of a tile are read from --------------------------
+// (A source may also say where a node's new populations go, out_slot below,
+// and may carry the population sum of wall nodes, wall_sum: the in-place
+// lattices of goc_aa.cuh.)
 template <class S> struct SrcGlobal {      // direct (read-only path) global loads
     const S *f, *F, *g;
     long long plane;
@@ -143,6 +146,17 @@ template <class S> struct SrcGlobal {      // direct (read-only path) global loa
         return scl<S>(Store<S>::ld(g + k * plane + (long long)j * pitch + i), sg);
     }
 };
+// Offset of the new population a of node (i, j) in the output buffer: its own
+// node and link (two-buffer lattices; idx = j pitch + i).
+template <class Src>
+__device__ __forceinline__ long long out_slot(const Src &, const StepParams &p, int a, int, int, long long idx) {
+    return a * p.plane + idx;
+}
+// Sources that carry the population sums of the wall nodes (the moving-wall
+// density below) define kWallSums = true.
+template <class Src, class = void> struct HasWallSums { static constexpr bool value = false; };
+template <class Src> struct HasWallSums<Src, decltype(void(Src::kWallSums))> { static constexpr bool value = Src::kWallSums; };
+
 template <class S> struct SrcSmem {        // the TMA-staged tile
     using T = Tiling<S>;
     const S *f, *F, *g;
@@ -230,8 +244,12 @@ __device__ __forceinline__ void pull_node(const StepParams &p, const Src &src, i
                 if (uy != 0.f || ux != 0.f) {
                     if (!rhow_ready) {
                         float s = 0.f;
+                        if constexpr (HasWallSums<Src>::value) {
+                            s = src.wall_sum(i, j);   // the same sum, taken before this launch
+                        } else {
 #pragma unroll
-                        for (int b = 0; b < 9; b++) s += src.fv(b, i, j);
+                            for (int b = 0; b < 9; b++) s += src.fv(b, i, j);
+                        }
                         rhow = p.rho0 + s / (h1 * h2);
                         rhow_ready = true;
                     }
@@ -1106,7 +1124,8 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
             put2<S>(fo + 8 * pl, Fo, lane(o[8], q) * is, lane(F1dev, q) * p.isF, sr, rng[q]);
             put2<S>(Fo + pl, static_cast<S *>(nullptr), lane(F2dev, q) * p.isF, 0.f, sr, rng[q]);
         } else {
-            for (int a = 0; a < 9; a++) put<S>(fout + a * p.plane + idx[q], scl<S>(lane(o[a], q), p.isf), sr, rng[q]);
+            for (int a = 0; a < 9; a++)
+                put<S>(fout + out_slot(src, p, a, i, j[q], idx[q]), scl<S>(lane(o[a], q), p.isf), sr, rng[q]);
             put<S>(Fout + idx[q], scl<S>(lane(F1dev, q), p.isF), sr, rng[q]);
             put<S>(Fout + p.plane + idx[q], scl<S>(lane(F2dev, q), p.isF), sr, rng[q]);
         }

@@ -92,8 +92,12 @@ ROUNDING = {"stochastic": 0, "nearest": 1}
 SCHEMES = {"goc": 0, "standard": 1, "goc_srt": 2, "goc_raw": 3}
 
 
+STREAMING = {"two_buffers": 0, "in_place": 1}
+
+
 def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", scheme: str = "goc",
-          fixed_launch: bool = False, plateau_checks: int = 0, reference_every: int = 0) -> GocExec:
+          fixed_launch: bool = False, plateau_checks: int = 0, reference_every: int = 0,
+          streaming: str = "two_buffers") -> GocExec:
     e = GocExec()
     e.storage = _abi.STORAGE[storage]
     e.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
@@ -104,6 +108,7 @@ def _exec(storage: str, stream, check_every: int, rounding: str = "stochastic", 
     e.fixed_launch = 1 if fixed_launch else 0
     e.plateau_checks = int(plateau_checks)
     e.reference_every = int(reference_every)
+    e.streaming = STREAMING[streaming]
     return e
 
 
@@ -112,11 +117,14 @@ class Lattice:
 
     def __init__(self, spec: dict, storage: str = "fp32", stream=None, check_every: int = 100,
                  rounding: str = "stochastic", scheme: str = "goc", fixed_launch: bool = False,
-                 plateau_checks: int = 0, reference_every: int = 0, _handle=None, _owner=None):
+                 plateau_checks: int = 0, reference_every: int = 0, streaming: str = "two_buffers",
+                 _handle=None, _owner=None):
         """scheme "standard": the uniform-grid central-moment LBM comparator
         (uniform maps, spec["gi"] = 0, no MIE).  reference_every: steps between
         refreshes of the per-row storage reference of 16-bit storage on
-        straight grids (0: the library default, < 0: never)."""
+        straight grids (0: the library default, < 0: never).  streaming
+        "in_place": one population buffer updated in place (FP32, straight
+        grids, no MIE; goc_exec.streaming)."""
         self.spec = spec
         self.nx, self.ny = int(spec["nx"]), int(spec["ny"])
         self.storage = storage
@@ -125,7 +133,8 @@ class Lattice:
             self._h = _handle
         else:
             g, m, f, h = structs_from_spec(spec)
-            e = _exec(storage, stream, check_every, rounding, scheme, fixed_launch, plateau_checks, reference_every)
+            e = _exec(storage, stream, check_every, rounding, scheme, fixed_launch, plateau_checks, reference_every,
+                      streaming)
             out = ctypes.c_void_p()
             check(lib().goc_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f),
                                    ctypes.byref(h), ctypes.byref(e), ctypes.byref(out)))

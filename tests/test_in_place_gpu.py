@@ -1,0 +1,121 @@
+"""Lattices updated in place (goc_exec.streaming = 1: one population buffer,
+two alternating access patterns, a fields pass and a collision pass per
+step) against the two-buffer step, which the oracle checks, and against the
+oracle itself."""
+import numpy as np
+import pytest
+
+import goc_inputs as gi
+import oracle
+import paper_2607_15362_b300 as goc
+
+pytestmark = pytest.mark.gpu
+
+
+def cs2_of(problem):
+    return oracle.build_metric(problem.lattice_spec(1.0)).cs2()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+PROBLEMS = {
+    # moving lid (the moving-wall term reads the population sum of the wall nodes), ragged tiles
+    "cavity": gi.Problem("cavity", 200, 90, {"kind": "tanh2", "beta": 1.2}, {"kind": "tanh2", "beta": 1.4},
+                         {"Re": 100.0, "u_lid": 0.05}),
+    # periodic along xi1, body force
+    "channel": gi.poiseuille_channel(),
+    # the benchmark's grid
+    "cavity512": gi.lid_cavity(512),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PROBLEMS))
+def test_in_place_steps_give_the_two_buffer_populations_bitwise(gpu, name):
+    """After 1, 2, 3, 70 (a captured graph and a remainder) and 131 more
+    steps the fields of the in-place lattice equal those of the two-buffer
+    lattice bitwise, and the mass agrees to rounding of the FP64 sum."""
+    prob = PROBLEMS[name]
+    spec = prob.lattice_spec(cs2_of(prob))
+    A = goc.Lattice(spec)
+    B = goc.Lattice(spec, streaming="in_place")
+    for n in (1, 1, 1, 70, 131):
+        A.step(n)
+        B.step(n)
+        for x, y in zip(A.moments(), B.moments()):
+            np.testing.assert_array_equal(x, y)
+        assert B.mass() == pytest.approx(A.mass(), rel=1e-13)
+    assert B.steps_done == A.steps_done == 204
+    A.close()
+    B.close()
+
+
+def test_in_place_lattice_matches_the_oracle(gpu):
+    """The ragged cavity with a moving lid, in place, against the FP64
+    oracle: velocity relative L2 <= 1e-5 after 1000 steps."""
+    prob = PROBLEMS["cavity"]
+    spec = prob.lattice_spec(cs2_of(prob))
+    o = oracle.Oracle(spec, threads=8)
+    L = goc.Lattice(spec, streaming="in_place")
+    o.step(1000)
+    L.step(1000)
+    ro, uo, vo, *_ = o.fields()
+    rg, ug, vg, *_ = L.moments()
+    assert relerr(np.stack([ug, vg]), np.stack([uo, vo])) <= 1e-5
+    assert np.abs(rg - ro).max() <= 1e-6
+    L.close()
+
+
+def test_in_place_state_round_trip(gpu):
+    """A state saved after an odd and after an even number of steps (the two
+    layouts) and restored into a new in-place lattice continues bitwise; it
+    does not fit a two-buffer lattice."""
+    prob = PROBLEMS["cavity"]
+    spec = prob.lattice_spec(cs2_of(prob))
+    for first in (7, 8):
+        A = goc.Lattice(spec, streaming="in_place")
+        A.step(first)
+        st = A.get_state()
+        A.step(25)
+        B = goc.Lattice(spec, streaming="in_place")
+        B.set_state(st)
+        assert B.steps_done == first
+        B.step(25)
+        for x, y in zip(A.moments(), B.moments()):
+            np.testing.assert_array_equal(x, y)
+        C = goc.Lattice(spec)
+        with pytest.raises(goc.GocError):
+            C.set_state(st)
+        for L in (A, B, C):
+            L.close()
+
+
+def test_in_place_lattice_holds_less_memory(gpu):
+    """56 B of populations, force and fields per node instead of 88 B."""
+    prob = gi.lid_cavity(512)
+    spec = prob.lattice_spec(cs2_of(prob))
+    A = goc.Lattice(spec)
+    B = goc.Lattice(spec, streaming="in_place")
+    _, ba = A.footprint()
+    _, bb = B.footprint()
+    nodes = 512 * 512
+    assert bb < 0.67 * ba
+    assert 56 * nodes <= bb < 60 * nodes
+    assert B.bytes_per_node == pytest.approx(156.0, abs=0.5)
+    A.close()
+    B.close()
+
+
+def test_in_place_run_until_matches_the_two_buffer_run(gpu):
+    """The residual checks (snapshots written by the collision pass) stop
+    both lattices at the same step with the same residual."""
+    prob = gi.poiseuille_channel()
+    spec = prob.lattice_spec(cs2_of(prob))
+    A = goc.Lattice(spec, check_every=50)
+    B = goc.Lattice(spec, check_every=50, streaming="in_place")
+    ra = A.run_until(1e-6, 4000)
+    rb = B.run_until(1e-6, 4000)
+    assert ra == rb
+    A.close()
+    B.close()
