@@ -109,13 +109,15 @@ def test_in_place_lattice_holds_less_memory(gpu):
 
 def test_in_place_run_until_matches_the_two_buffer_run(gpu):
     """The residual checks (snapshots written by the collision pass) stop
-    both lattices at the same step with the same residual."""
+    both lattices at the same step with the same residual (to the rounding
+    of its FP64 sum, whose atomics add in any order)."""
     prob = gi.poiseuille_channel()
     spec = prob.lattice_spec(cs2_of(prob))
     A = goc.Lattice(spec, check_every=50)
     B = goc.Lattice(spec, check_every=50, streaming="in_place")
     ra = A.run_until(1e-6, 4000)
     rb = B.run_until(1e-6, 4000)
-    assert ra == rb
+    assert ra[0] == rb[0]
+    assert rb[1] == pytest.approx(ra[1], rel=1e-12)
     A.close()
     B.close()
