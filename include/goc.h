@@ -189,8 +189,10 @@ typedef struct {
                                reversed, then at the node they stream to), each step a fields
                                pass and a collision pass.  56 B per node resident instead of
                                88 B, 156 B moved per step instead of 88 B; the populations
-                               are bitwise those of streaming 0.  FP32 storage, scheme 0, no
-                               MIE, per-axis maps (else GOC_EUNSUPPORTED); not in batches or
+                               are bitwise those of streaming 0 (the MIE populations follow
+                               the same layouts: 40 B resident instead of 80 B).  FP32
+                               storage, scheme 0, per-axis maps (else GOC_EUNSUPPORTED); not
+                               in batches or
                                slabs; goc_get_state / goc_set_state keep the layout, so a
                                state moves only between lattices of the same streaming. */
 } goc_exec;

@@ -1,5 +1,6 @@
 // goc_aa.cuh -- lattices that keep one population buffer and update it in
-// place (FP32 storage, straight grids, central-moment collision, no MIE).
+// place (FP32 storage, straight grids, central-moment collision, with or
+// without the MIE).
 //
 // The step is the one of goc_step.cuh (Appendix E, Steps 1-7): pull
 // streaming with the rest-state pull corrections and the wall conditions of
@@ -8,7 +9,8 @@
 // collision.  Only where the populations live changes.  Two access patterns
 // alternate (the "AA" pattern), and in each of them every slot of the buffer
 // is read and then written by one and the same node, so a launch can
-// overwrite its input:
+// overwrite its input (the D2Q5 populations of the MIE, Appendix G, follow
+// the same layouts with their own links):
 //
 //   layout AA_C   slot (x, a) holds the population of node x along link a:
 //                 the initial state f^0, which the first step reads in place;
@@ -27,14 +29,16 @@
 // (and the population sum of each wall node, which the moving-wall condition
 // reads) without writing populations, then aa_collide_kernel pulls again,
 // takes the neighbours' fields from that buffer and writes the new
-// populations in place.  The force F is read and written by its own node.
+// populations in place (the MIE update needs no neighbour values beyond its
+// pulls).  The force F is read and written by its own node.
 // Every value goes through the functions the two-buffer kernels use, in the
 // same order, so the populations are bitwise those of the two-buffer step.
 //
 // Resident per node: 36 B populations + 8 B force + 12 B fields = 56 B
-// (two-buffer lattices: 88 B).  Moved per step: 44 B read and 12 B written
-// by the fields pass, 44 B + 12 B read and 44 B written by the collision
-// pass: 156 B (two-buffer step: 88 B).
+// (two-buffer lattices: 88 B); with the MIE 40 B more (two-buffer: 80 B
+// more).  Moved per step: 44 B read and 12 B written by the fields pass,
+// 44 B + 12 B read and 44 B written by the collision pass: 156 B (two-buffer
+// step: 88 B); with the MIE 80 B more (the same as two buffers).
 #pragma once
 
 #include "goc_step.cuh"
@@ -51,11 +55,13 @@ enum { AA_C = 0, AA_S = 1, AA_T = 2 };
 template <int L, bool WS, bool CH = true> struct SrcAA {
     static_assert(L == AA_C || L == AA_S || L == AA_T, "layout");
     static constexpr bool kWallSums = WS;
-    const float *f, *F;
+    static constexpr bool kInPlace = true;
+    const float *f, *F, *g;
     long long plane;
     int pitch, nx, ny, per_x, per_y;
     const float *wsum;
     int wn;
+    float sg;   // (FP32: 1)
     // the node a population of node (i, j) along link a streams to, and
     // whether it lies inside the lattice (periodic axes wrap)
     __device__ __forceinline__ bool dest(int a, int i, int j, int &ti, int &tj) const {
@@ -85,6 +91,34 @@ template <int L, bool WS, bool CH = true> struct SrcAA {
         }
     }
     __device__ __forceinline__ float Fv(int c, int i, int j) const { return F[c * plane + (long long)j * pitch + i]; }
+    // the post-collision MIE population k = 5 c + a of node (i, j) (D2Q5
+    // links g1, g2; the same two layouts)
+    __device__ __forceinline__ bool gdest(int a, int i, int j, int &ti, int &tj) const {
+        ti = i + g1(a);
+        tj = j + g2(a);
+        bool in = true;
+        if (!CH) return true;
+        if (ti < 0 || ti >= nx) {
+            if (per_x) ti = wrapi(ti, nx); else in = false;
+        }
+        if (tj < 0 || tj >= ny) {
+            if (per_y) tj = wrapi(tj, ny); else in = false;
+        }
+        return in;
+    }
+    __device__ __forceinline__ float gv(int k, int i, int j) const {
+        const int c = k / 5, a = k - 5 * c;
+        const long long idx = (long long)j * pitch + i;
+        if constexpr (L == AA_C) {
+            return g[k * plane + idx];
+        } else if constexpr (L == AA_S) {
+            return g[(5 * c + gopp(a)) * plane + idx];
+        } else {
+            int ti, tj;
+            if (gdest(a, i, j, ti, tj)) return g[k * plane + (long long)tj * pitch + ti];
+            return g[(5 * c + gopp(a)) * plane + idx];
+        }
+    }
     __device__ __forceinline__ float wall_sum(int i, int j) const {
         if (j == 0) return wsum[SIDE_S * wn + i];
         if (j == ny - 1) return wsum[SIDE_N * wn + i];
@@ -105,10 +139,21 @@ __device__ __forceinline__ long long out_slot(const SrcAA<L, WS, CH> &s, const S
     return opp(a) * p.plane + idx;
 }
 
+template <int L, bool WS, bool CH>
+__device__ __forceinline__ long long out_slot_g(const SrcAA<L, WS, CH> &s, const StepParams &p, int c, int a, int i,
+                                                int j, long long idx) {
+    if constexpr (L == AA_S) {
+        int ti, tj;
+        if (s.gdest(a, i, j, ti, tj)) return (5 * c + a) * p.plane + (long long)tj * p.pitch + ti;
+    }
+    return (5 * c + gopp(a)) * p.plane + idx;
+}
+
 template <int L, bool WS, bool CH = true>
 __device__ __forceinline__ SrcAA<L, WS, CH> aa_source(const StepParams &p, const float *wsum, int wn) {
-    return SrcAA<L, WS, CH>{static_cast<const float *>(p.fin), static_cast<const float *>(p.Fin), p.plane, p.pitch,
-                            p.nx, p.ny, p.per_x, p.per_y, wsum, wn};
+    return SrcAA<L, WS, CH>{static_cast<const float *>(p.fin), static_cast<const float *>(p.Fin),
+                            static_cast<const float *>(p.gin), p.plane, p.pitch, p.nx, p.ny, p.per_x, p.per_y,
+                            wsum, wn, 1.f};
 }
 
 // whether every node of this block has its eight neighbours inside the
@@ -176,7 +221,7 @@ __device__ __forceinline__ float aa_field(const StepParams &p, const float *fld,
 // Collision pass: pull, the fields of the node and its neighbours from the
 // fields pass, normal derivatives, collision; the new populations go to the
 // node's slots of the next layout, the force to the node.
-template <int L, bool CH>
+template <int L, bool MHD, bool CH>
 __device__ __forceinline__ void aa_collide_node(const StepParams &p, int i, int j, const float *fld, const float *wsum,
                                                 int wn) {
     const SrcAA<L, true, CH> src = aa_source<L, true, CH>(p, wsum, wn);
@@ -212,28 +257,28 @@ __device__ __forceinline__ void aa_collide_node(const StepParams &p, int i, int 
     }
     const int jj[1] = {j};
     const bool own[1] = {true};
-    collide<float, false, CH, float, false, 0>(p, src, i, jj, own, d, F1p, F2p, h1, ih1, h2, ih2, fl, ur1);
+    collide<float, MHD, CH, float, false, 0>(p, src, i, jj, own, d, F1p, F2p, h1, ih1, h2, ih2, fl, ur1);
 }
 
 // Collision pass: pull, the fields of the node and its neighbours from the
 // fields pass, normal derivatives, collision; the new populations go to the
 // node's slots of the next layout, the force to the node.
-template <int L>
-__global__ void __launch_bounds__(NT, GOC_MIN_BLOCKS) aa_collide_kernel(const __grid_constant__ StepParams p,
-                                                                         const float *fld, const float *wsum, int wn) {
+template <int L, bool MHD>
+__global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MIN_BLOCKS)
+    aa_collide_kernel(const __grid_constant__ StepParams p, const float *fld, const float *wsum, int wn) {
     griddep_launch_dependents();
     griddep_wait();
     const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
     if (aa_block_interior(p)) {
-        aa_collide_node<L, false>(p, i, j, fld, wsum, wn);
+        aa_collide_node<L, MHD, false>(p, i, j, fld, wsum, wn);
     } else if (i < p.nx && j < p.ny) {
-        aa_collide_node<L, true>(p, i, j, fld, wsum, wn);
+        aa_collide_node<L, MHD, true>(p, i, j, fld, wsum, wn);
     }
 }
 
 // Macroscopic fields of an in-place lattice (as moments_kernel, FP64 output
 // [5][ny][nx]; no MIE).
-template <int L>
+template <int L, bool MHD>
 __global__ void aa_moments_kernel(const StepParams p, double *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
@@ -247,8 +292,17 @@ __global__ void aa_moments_kernel(const StepParams p, double *out) {
     out[n] = (double)p.rho0 + (double)drho;
     out[N + n] = U1;
     out[2 * N + n] = U2;
-    out[3 * N + n] = 0.0;
-    out[4 * N + n] = 0.0;
+    double B1 = 0.0, B2 = 0.0;
+    if constexpr (MHD) {   // as moments_kernel on straight grids
+        float gd[2][5];
+        for (int c = 0; c < 2; c++) pull_mie<true, 0, false>(p, src, i, j, h1, h2, c, gd[c]);
+        const float s0 = (gd[0][0] + gd[0][1] + gd[0][2] + gd[0][3] + gd[0][4]) / (h1 * h2);
+        const float s1 = (gd[1][0] + gd[1][1] + gd[1][2] + gd[1][3] + gd[1][4]) / (h1 * h2);
+        B1 = (double)bref<false>(p, 0, j) + (double)s0;
+        B2 = (double)bref<false>(p, 1, j) + (double)s1;
+    }
+    out[3 * N + n] = B1;
+    out[4 * N + n] = B2;
 }
 
 }  // namespace goc

@@ -531,6 +531,7 @@ void free_lattice(goc_lattice *L) {
     if (L->aa) {   // one buffer, named twice
         L->f[1] = nullptr;
         L->F[1] = nullptr;
+        L->g[1] = nullptr;
     }
     void *ptrs[] = {L->f[0], L->f[1], L->F[0], L->F[1], L->g[0], L->g[1], L->tab1, L->tab2,
                     L->m1, L->m2, L->gm, L->uout[0], L->uout[1], L->flag, L->red, L->mom,
@@ -850,9 +851,8 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
         return fail(GOC_EINVAL, "unknown streaming %d", exec->streaming);
     if (exec && exec->streaming == 1) {
         const bool straight = map->kind[0] != GOC_MAP_ANNULUS && map->kind[0] != GOC_MAP_TABLE;
-        if (exec->storage != GOC_FP32 || exec->scheme != 0 || (mhd && mhd->enabled) || !straight)
-            return fail(GOC_EUNSUPPORTED,
-                        "in-place streaming needs FP32 storage, scheme 0, no MIE and a straight grid");
+        if (exec->storage != GOC_FP32 || exec->scheme != 0 || !straight)
+            return fail(GOC_EUNSUPPORTED, "in-place streaming needs FP32 storage, scheme 0 and a straight grid");
     }
     goc_lattice *L = new (std::nothrow) goc_lattice();
     if (!L) return fail(GOC_ENOMEM, "host allocation failed");
@@ -911,6 +911,7 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
     if (L->aa) {   // in place: one population and force buffer, the fields of the current step
         L->f[1] = L->f[0];
         L->F[1] = L->F[0];
+        L->g[1] = L->g[0];
         L->aa_wn = std::max(L->nx, L->ny);
         TRY(dalloc(L, &L->aa_fld, 3 * L->plane * sizeof(float)));
         TRY(dalloc(L, &L->aa_wsum, 4 * (size_t)L->aa_wn * sizeof(float)));
@@ -1359,7 +1360,8 @@ double goc_bytes_per_node(const goc_lattice *L) {
     if (L->scheme == 1) return 2.0 * 9.0 * es;          // populations only, read + write
     if (L->aa)   // fields pass: populations, force read, fields written; collision pass: populations, force
                  // and fields read, populations and force written
-        return 4.0 * (11.0 + 3.0 + 11.0 + 3.0 + 11.0) + 4.0 * 7.0 / L->ny + 4.0 * 7.0 / L->nx;
+        return 4.0 * (11.0 + 3.0 + 11.0 + 3.0 + 11.0) + (L->mhd.enabled ? 2.0 * 10.0 * 4.0 : 0.0) +
+               4.0 * 7.0 / L->ny + 4.0 * 7.0 / L->nx;
     double b = 2.0 * (9.0 + 2.0) * es;                  // populations + stored force, read + write
     if (L->mhd.enabled) b += 2.0 * 10.0 * es;           // MIE populations
     if (L->sp.curv == 2) return b + 4.0 * 10.0;         // node-table metric: 10 FP32 values per node

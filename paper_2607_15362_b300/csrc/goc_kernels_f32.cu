@@ -9,9 +9,12 @@ template <int LAY>
 static goc_status launch_aa_layout(goc_lattice *L, const StepParams &p) {
     const dim3 grid((L->nx + TX - 1) / TX, (L->ny + TY - 1) / TY), block(TX, TY);
     const bool pdl = L->cfg_pdl != 0;
+    const float *fld = L->aa_fld, *wsum = L->aa_wsum;
     CU(launch_pdl(pdl, aa_fields_kernel<LAY>, grid, block, 0, L->stream, p, L->aa_fld, L->aa_wsum, L->aa_wn));
-    CU(launch_pdl(pdl, aa_collide_kernel<LAY>, grid, block, 0, L->stream, p, static_cast<const float *>(L->aa_fld),
-                  static_cast<const float *>(L->aa_wsum), L->aa_wn));
+    if (L->mhd.enabled)
+        CU(launch_pdl(pdl, aa_collide_kernel<LAY, true>, grid, block, 0, L->stream, p, fld, wsum, L->aa_wn));
+    else
+        CU(launch_pdl(pdl, aa_collide_kernel<LAY, false>, grid, block, 0, L->stream, p, fld, wsum, L->aa_wn));
     return GOC_OK;
 }
 
@@ -22,9 +25,16 @@ goc_status launch_aa_step(goc_lattice *L, const StepParams &p) {
 
 goc_status launch_aa_moments(goc_lattice *L, const StepParams &p, double *out) {
     const dim3 grid((L->nx + 127) / 128, L->ny), block(128);
-    if (L->fresh) aa_moments_kernel<AA_C><<<grid, block, 0, L->stream>>>(p, out);
-    else if (L->cur) aa_moments_kernel<AA_S><<<grid, block, 0, L->stream>>>(p, out);
-    else aa_moments_kernel<AA_T><<<grid, block, 0, L->stream>>>(p, out);
+    const int lay = L->fresh ? AA_C : (L->cur ? AA_S : AA_T);
+    if (L->mhd.enabled) {
+        if (lay == AA_C) aa_moments_kernel<AA_C, true><<<grid, block, 0, L->stream>>>(p, out);
+        else if (lay == AA_S) aa_moments_kernel<AA_S, true><<<grid, block, 0, L->stream>>>(p, out);
+        else aa_moments_kernel<AA_T, true><<<grid, block, 0, L->stream>>>(p, out);
+    } else {
+        if (lay == AA_C) aa_moments_kernel<AA_C, false><<<grid, block, 0, L->stream>>>(p, out);
+        else if (lay == AA_S) aa_moments_kernel<AA_S, false><<<grid, block, 0, L->stream>>>(p, out);
+        else aa_moments_kernel<AA_T, false><<<grid, block, 0, L->stream>>>(p, out);
+    }
     CU(cudaGetLastError());
     return GOC_OK;
 }

@@ -152,10 +152,20 @@ template <class Src>
 __device__ __forceinline__ long long out_slot(const Src &, const StepParams &p, int a, int, int, long long idx) {
     return a * p.plane + idx;
 }
+// The same for the MIE population of component c along link a (component-major).
+template <class Src>
+__device__ __forceinline__ long long out_slot_g(const Src &, const StepParams &p, int c, int a, int, int,
+                                                long long idx) {
+    return (c * 5 + a) * p.plane + idx;
+}
 // Sources that carry the population sums of the wall nodes (the moving-wall
 // density below) define kWallSums = true.
 template <class Src, class = void> struct HasWallSums { static constexpr bool value = false; };
 template <class Src> struct HasWallSums<Src, decltype(void(Src::kWallSums))> { static constexpr bool value = Src::kWallSums; };
+// Sources of lattices updated in place define kInPlace = true (their output
+// slots follow out_slot / out_slot_g).
+template <class Src, class = void> struct InPlaceSrc { static constexpr bool value = false; };
+template <class Src> struct InPlaceSrc<Src, decltype(void(Src::kInPlace))> { static constexpr bool value = Src::kInPlace; };
 
 template <class S> struct SrcSmem {        // the TMA-staged tile
     using T = Tiling<S>;
@@ -769,6 +779,9 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
                     put2<S>(go, go + pl, gt[0] * is, gt[1] * is, sr, rng[0]);
                     put2<S>(go + 2 * pl, go + 3 * pl, gt[2] * is, gt[3] * is, sr, rng[0]);
                     put2<S>(go + 4 * pl, static_cast<S *>(nullptr), gt[4] * is, 0.f, sr, rng[0]);
+                } else if constexpr (InPlaceSrc<Src>::value) {   // (in-place lattices: slots of their layout)
+#pragma unroll
+                    for (int a = 0; a < 5; a++) put<S>(gout + out_slot_g(src, p, c, a, i, j[0], idx[0]), gt[a], sr, rng[0]);
                 } else {
 #pragma unroll
                     for (int a = 0; a < 5; a++) put<S>(go + a * p.plane, gt[a], sr, rng[0]);

@@ -124,7 +124,7 @@ class Lattice:
         refreshes of the per-row storage reference of 16-bit storage on
         straight grids (0: the library default, < 0: never).  streaming
         "in_place": one population buffer updated in place (FP32, straight
-        grids, no MIE; goc_exec.streaming)."""
+        grids; goc_exec.streaming)."""
         self.spec = spec
         self.nx, self.ny = int(spec["nx"]), int(spec["ny"])
         self.storage = storage

@@ -28,42 +28,68 @@ PROBLEMS = {
     "channel": gi.poiseuille_channel(),
     # the benchmark's grid
     "cavity512": gi.lid_cavity(512),
+    # the MIE (Appendix G): periodic along xi1, Hartmann walls with their fields
+    "hartmann": gi.Problem("hartmann", 4, 96, {"kind": "uniform"}, {"kind": "tanh2", "beta": 2.0},
+                           {"Ha": 20.0, "Re": 20.0, "tau": 1.0, "tau_m": 1.0}),
 }
+
+
+def _spec(name):
+    prob = PROBLEMS[name]
+    spec = prob.lattice_spec(cs2_of(prob))
+    if name == "cavity_mie":
+        spec["mhd"] = {"tau_m": 0.9, "mu_m": 2.0, "B_init": (0.01, 0.004)}
+    return spec
+
+
+# the MIE with walls all round and a moving lid (ragged tiles)
+PROBLEMS["cavity_mie"] = PROBLEMS["cavity"]
 
 
 @pytest.mark.parametrize("name", sorted(PROBLEMS))
 def test_in_place_steps_give_the_two_buffer_populations_bitwise(gpu, name):
     """After 1, 2, 3, 70 (a captured graph and a remainder) and 131 more
     steps the fields of the in-place lattice equal those of the two-buffer
-    lattice bitwise, and the mass agrees to rounding of the FP64 sum."""
-    prob = PROBLEMS[name]
-    spec = prob.lattice_spec(cs2_of(prob))
+    lattice bitwise, and the mass agrees to rounding of the FP64 sum.  With
+    the MIE the wall nodes' updates are separate compilations of the same
+    source in the two paths, whose multiply-adds the compiler may fuse
+    differently (measured: one node of the lid row one FP32 unit apart in
+    B1 of the 200 x 90 cavity); there the fields agree to 1e-6 of their
+    largest value."""
+    spec = _spec(name)
+    mie = "mhd" in spec or PROBLEMS[name].mhd
     A = goc.Lattice(spec)
     B = goc.Lattice(spec, streaming="in_place")
     for n in (1, 1, 1, 70, 131):
         A.step(n)
         B.step(n)
         for x, y in zip(A.moments(), B.moments()):
-            np.testing.assert_array_equal(x, y)
+            if mie:
+                assert np.abs(x - y).max() <= 1e-6 * max(np.abs(x).max(), 1e-30)
+            else:
+                np.testing.assert_array_equal(x, y)
         assert B.mass() == pytest.approx(A.mass(), rel=1e-13)
     assert B.steps_done == A.steps_done == 204
     A.close()
     B.close()
 
 
-def test_in_place_lattice_matches_the_oracle(gpu):
-    """The ragged cavity with a moving lid, in place, against the FP64
-    oracle: velocity relative L2 <= 1e-5 after 1000 steps."""
-    prob = PROBLEMS["cavity"]
-    spec = prob.lattice_spec(cs2_of(prob))
+@pytest.mark.parametrize("name", ["cavity", "hartmann"])
+def test_in_place_lattice_matches_the_oracle(gpu, name):
+    """The ragged cavity with a moving lid and the Hartmann strip with the
+    MIE, in place, against the FP64 oracle: velocity (and induced field)
+    relative L2 <= 1e-5 after 1000 steps."""
+    spec = _spec(name)
     o = oracle.Oracle(spec, threads=8)
     L = goc.Lattice(spec, streaming="in_place")
     o.step(1000)
     L.step(1000)
-    ro, uo, vo, *_ = o.fields()
-    rg, ug, vg, *_ = L.moments()
+    ro, uo, vo, bo1, bo2 = o.fields()
+    rg, ug, vg, bg1, bg2 = L.moments()
     assert relerr(np.stack([ug, vg]), np.stack([uo, vo])) <= 1e-5
     assert np.abs(rg - ro).max() <= 1e-6
+    if name == "hartmann":
+        assert relerr(bg1, bo1) <= 1e-5
     L.close()
 
 
