@@ -109,6 +109,14 @@ def test_in_place_streaming_is_refused_outside_its_scope_without_a_gpu():
         assert st == _abi.GOC_EUNSUPPORTED and not out.value, (kw, st)
         assert b"in-place streaming" in _abi.lib().goc_last_error()
     g, m, f, h = structs_from_spec(spec)
+    e = _exec("fp32", None, 100, streaming="in_place")   # slabs and batches keep two buffers
+    out = ctypes.c_void_p()
+    st = _abi.lib().goc_create_slab(ctypes.byref(g), ctypes.byref(m), ctypes.byref(f), ctypes.byref(h),
+                                    ctypes.byref(e), 0, 8, ctypes.byref(out))
+    assert st == _abi.GOC_EUNSUPPORTED and not out.value
+    st = _abi.lib().goc_batch_create(1 << 30, 4, ctypes.byref(e), ctypes.byref(out))
+    assert st == _abi.GOC_EUNSUPPORTED and not out.value
+    assert b"two population buffers" in _abi.lib().goc_last_error()
     e = _exec("fp32", None, 100)
     e.streaming = 2
     out = ctypes.c_void_p()
