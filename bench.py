@@ -840,7 +840,8 @@ def run_accuracy_mhd(args):
         crossing = 2.0 * d["H"] ** 2 / (Ha * d["nu"])
         ua, ba = _hartmann_analytic(spec, ny, y)
         lat = goc.Lattice(spec, stream=stream.cuda_stream, check_every=5000 if stretched else 500,
-                          plateau_checks=20 if stretched else 0)
+                          plateau_checks=20 if stretched else 0,
+                          streaming=args.streaming if stretched else "two_buffers")
         if stretched:
             shape = (ny, args.mhd_nx)
             lat.init_fields(u1=np.broadcast_to(ua[:, None], shape).copy(),
@@ -867,6 +868,7 @@ def run_accuracy_mhd(args):
         eu = float(np.linalg.norm(u - ua) / np.linalg.norm(ua))
         eb = float(np.linalg.norm(b - ba) / np.linalg.norm(ba))
         row = {"grid": goc_name if stretched else "uniform", "ny": ny,
+               "streaming": args.streaming if stretched else "two_buffers",
                "start": "analytic" if stretched else "rest", "steps": int(steps),
                "crossing_steps": round(crossing), "seconds": round(wall, 3),
                "mlups": round(args.mhd_nx * ny * steps / wall / 1e6, 1),
