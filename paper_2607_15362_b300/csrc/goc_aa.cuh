@@ -61,7 +61,6 @@ template <int L, bool WS, bool CH = true> struct SrcAA {
     int pitch, nx, ny, per_x, per_y;
     const float *wsum;
     int wn;
-    float sg;   // (FP32: 1)
     // the node a population of node (i, j) along link a streams to, and
     // whether it lies inside the lattice (periodic axes wrap)
     __device__ __forceinline__ bool dest(int a, int i, int j, int &ti, int &tj) const {
@@ -153,7 +152,7 @@ template <int L, bool WS, bool CH = true>
 __device__ __forceinline__ SrcAA<L, WS, CH> aa_source(const StepParams &p, const float *wsum, int wn) {
     return SrcAA<L, WS, CH>{static_cast<const float *>(p.fin), static_cast<const float *>(p.Fin),
                             static_cast<const float *>(p.gin), p.plane, p.pitch, p.nx, p.ny, p.per_x, p.per_y,
-                            wsum, wn, 1.f};
+                            wsum, wn};
 }
 
 // whether every node of this block has its eight neighbours inside the
