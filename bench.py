@@ -750,6 +750,55 @@ def _vortex_centres(prob, fields):
             "top_left": centre((X < 0.3) & (Y > 0.7), 1.0)}
 
 
+def run_capacity(args):
+    """The largest lattice one GPU holds with two population buffers and in
+    place: a channel with the MIE (Hartmann flow, tanh beta = 3 across,
+    Ha = 100), 40,000 rows and as many columns (a multiple of 32) as fill about
+    80% of the free device memory in place (at most 2e9 nodes).  Each mode is
+    created with uniform initial fields, stepped 2 + 10 times (the 10 timed with
+    CUDA events) and its mass read, or reports why it could not be created."""
+    import torch
+
+    import paper_2607_15362_b300 as goc
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    free, total = torch.cuda.mem_get_info()
+    ny = 40000
+    nodes = min(int(0.8 * free / 96.0), 2_000_000_000)
+    nx = max(32, nodes // ny // 32 * 32)
+    prob = gi.Problem("hartmann", nx, ny, {"kind": "uniform"}, {"kind": "tanh2", "beta": 3.0},
+                      {"Ha": 100.0, "Re": 100.0, "tau": 1.0, "tau_m": 1.0})
+    _, cs2 = goc.metric_info(prob.lattice_spec(1.0))
+    spec = prob.lattice_spec(cs2)
+    runs = []
+    for streaming in ("two_buffers", "in_place"):
+        rec = {"streaming": streaming}
+        try:
+            lat = goc.Lattice(spec, stream=stream.cuda_stream, streaming=streaming, fixed_launch=True)
+        except goc.GocError as e:
+            rec.update(created=False, error=str(e))
+            runs.append(rec)
+            continue
+        _, held = lat.footprint()
+        lat.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(10)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        rec.update(created=True, device_gb=round(held / 1e9, 2), bytes_per_node=round(held / (nx * ny), 2),
+                   ms_per_step=round(ms, 3), mlups=round(nx * ny / ms / 1e3, 1), mass=lat.mass(),
+                   steps=lat.steps_done)
+        lat.close()
+        runs.append(rec)
+    print(json.dumps({"metric": METRIC, "workload": f"capacity: Hartmann channel with the MIE, {nx} x {ny} "
+                      f"({nx * ny / 1e9:.2f} G nodes), FP32", "device_free_gb": round(free / 1e9, 1),
+                      "device_total_gb": round(total / 1e9, 1), "runs": runs}))
+
+
 def run_vortex(args):
     """The cavity of Sec. 7.3 run to its steady state on the GPU, and the
     centres of its primary and bottom-corner vortices (the quantities of the
@@ -1019,7 +1068,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps-per-step", type=int, default=4)
     ap.add_argument("--workload", default="cavity",
-                    choices=["cavity", "batch", "serve", "accuracy", "accuracy_mhd", "oracle_timing", "vortex"])
+                    choices=["cavity", "batch", "serve", "accuracy", "accuracy_mhd", "oracle_timing", "vortex",
+                             "capacity"])
     ap.add_argument("--mhd-nx", type=int, default=256)
     ap.add_argument("--mhd-ha", type=float, default=100.0)
     ap.add_argument("--mhd-re", type=float, default=100.0)
@@ -1061,6 +1111,8 @@ def main():
         run_oracle_timing(args)
     elif args.workload == "vortex":
         run_vortex(args)
+    elif args.workload == "capacity":
+        run_capacity(args)
     elif args.shard or (int(os.environ.get("WORLD_SIZE", "1")) > 1 and not args.replicas and args.grid == "tanh"
                         and not args.mie and args.scheme == "goc"):
         run_sharded(args)   # one lattice over all ranks, slabs along xi2

@@ -623,28 +623,35 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
                     const double *b1, const double *b2, bool persistent_staging = false) {
     const long long N = (long long)L->nx * L->ny;
     if (L->aa) L->cur = 0;   // in place: the parity names the layout, and the first step reads f^0
-    // staging of the five FP64 fields on the device: the moments buffer (kept
-    // for later calls) when asked, else a temporary allocation
+    // staging of the given FP64 fields on the device: the moments buffer
+    // (kept for later calls) when asked, else a temporary allocation; a field
+    // not given is its default constant and takes no memory (so a lattice
+    // created with uniform fields needs no staging beyond its own buffers)
+    const double *src[5] = {rho, u1, u2, b1, b2};
+    const double dflt[5] = {L->flow.rho0, 0.0, 0.0, L->mhd.b_init[0], L->mhd.b_init[1]};
+    int given = 0;
+    for (int k = 0; k < 5; k++) given += src[k] ? 1 : 0;
     double *dev = nullptr;
     bool temporary = false;
-    if (persistent_staging) {
+    if (given && persistent_staging) {
         if (!L->mom) {
             CU(cudaMalloc(&L->mom, 5 * N * sizeof(double)));
             L->device_bytes += 5 * N * sizeof(double);
         }
         dev = L->mom;
-    } else {
-        CU(cudaMalloc(&dev, 5 * N * sizeof(double)));
+    } else if (given) {
+        CU(cudaMalloc(&dev, given * N * sizeof(double)));
         temporary = true;
     }
-    const double *src[5] = {rho, u1, u2, b1, b2};
-    const double dflt[5] = {L->flow.rho0, 0.0, 0.0, L->mhd.b_init[0], L->mhd.b_init[1]};
+    double *fld[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int cmask = 0, slot = 0;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 5 && e == cudaSuccess; k++) {
-        if (src[k]) e = cudaMemcpyAsync(dev + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, L->stream);
-        else {
-            fill_kernel<<<(unsigned)std::min<long long>((N + 255) / 256, 4096), 256, 0, L->stream>>>(dev + k * N, N, dflt[k]);
-            e = cudaGetLastError();
+        if (src[k]) {
+            fld[k] = dev + slot++ * N;
+            e = cudaMemcpyAsync(fld[k], src[k], N * sizeof(double), cudaMemcpyHostToDevice, L->stream);
+        } else {
+            cmask |= 1 << k;
         }
     }
     if (e != cudaSuccess) {
@@ -677,11 +684,13 @@ goc_status run_init(goc_lattice *L, const double *rho, const double *u1, const d
     q.eta = L->eta;
     q.gi = L->flow.gi_correction;
     q.mhd = L->mhd.enabled;
-    q.rho = dev;
-    q.u1 = dev + N;
-    q.u2 = dev + 2 * N;
-    q.b1 = dev + 3 * N;
-    q.b2 = dev + 4 * N;
+    q.rho = fld[0];
+    q.u1 = fld[1];
+    q.u2 = fld[2];
+    q.b1 = fld[3];
+    q.b2 = fld[4];
+    for (int k = 0; k < 5; k++) q.cval[k] = dflt[k];
+    q.cmask = cmask;
     dim3 grid((L->nx + 127) / 128, L->ny), block(128);
     switch (L->storage) {
         case GOC_FP16_DEV: init_kernel<__half><<<grid, block, 0, L->stream>>>(q); break;

@@ -191,11 +191,24 @@ struct InitParams {
     const double *h2x, *t21x;              // curvilinear column metric: h2, theta21 over xi1 (else null)
     double cs2, nu, zeta, rho0, csm2, eta;
     int gi, mhd;
+    // the five fields rho, U1, U2, B1, B2 as [ny][nx] FP64 arrays; field k is
+    // the constant cval[k] instead where bit k of cmask is set (no array)
     const double *rho, *u1, *u2, *b1, *b2;
+    double cval[5];
+    int cmask;
 };
 
-__device__ double dfd64(const double *phi, int i, int j, int nx, int ny, int axis, int per) {
-    auto at = [&](int ii, int jj) { return phi[(long long)jj * nx + ii]; };
+// field k of the initial state at node n
+__device__ __forceinline__ double init_field(const InitParams &q, int k, long long n) {
+    if (q.cmask >> k & 1) return q.cval[k];
+    const double *a[5] = {q.rho, q.u1, q.u2, q.b1, q.b2};
+    return a[k][n];
+}
+
+// second-order derivative of field k along an axis (central; one-sided at
+// the first and last node of a wall axis)
+__device__ double dfd64(const InitParams &q, int fk, int i, int j, int nx, int ny, int axis, int per) {
+    auto at = [&](int ii, int jj) { return init_field(q, fk, (long long)jj * nx + ii); };
     const int k = axis == 0 ? i : j, n = axis == 0 ? nx : ny;
     auto nb = [&](int off) {
         int kk = k + off;
@@ -225,11 +238,11 @@ __global__ void init_kernel(const InitParams q) {
         t21 = gm_at(p.gm, p.plane, p.pitch, 4, i, j);
         t22 = gm_at(p.gm, p.plane, p.pitch, 5, i, j);
     }
-    const double rho = q.rho[n], U1 = q.u1[n], U2 = q.u2[n];
-    const double dU1 = dfd64(q.u1, i, j, p.nx, p.ny, 0, p.per_x);
-    const double dU2 = dfd64(q.u2, i, j, p.nx, p.ny, 1, p.per_y);
-    const double dr1 = dfd64(q.rho, i, j, p.nx, p.ny, 0, p.per_x);
-    const double dr2 = dfd64(q.rho, i, j, p.nx, p.ny, 1, p.per_y);
+    const double rho = init_field(q, 0, n), U1 = init_field(q, 1, n), U2 = init_field(q, 2, n);
+    const double dU1 = dfd64(q, 1, i, j, p.nx, p.ny, 0, p.per_x);
+    const double dU2 = dfd64(q, 2, i, j, p.nx, p.ny, 1, p.per_y);
+    const double dr1 = dfd64(q, 0, i, j, p.nx, p.ny, 0, p.per_x);
+    const double dr2 = dfd64(q, 0, i, j, p.nx, p.ny, 1, p.per_y);
     const double cs2 = q.cs2, nu = q.nu, ze = q.zeta;
     const double gi = q.gi ? 1.0 : 0.0;
     const double a1 = gi * U1 * U1 / cs2, a2 = gi * U2 * U2 / cs2;
@@ -299,11 +312,10 @@ __global__ void init_kernel(const InitParams q) {
     Store<S>::st(Fout + p.plane + idx, (float)(-F2r * p.isF));
     if (!q.mhd) return;
     S *gout = static_cast<S *>(p.gout);
-    const double B[2] = {q.b1[n], q.b2[n]}, U[2] = {U1, U2};
-    const double *Bf[2] = {q.b1, q.b2};
+    const double B[2] = {init_field(q, 3, n), init_field(q, 4, n)}, U[2] = {U1, U2};
     for (int c = 0; c < 2; c++) {
-        const double dB1 = dfd64(Bf[c], i, j, p.nx, p.ny, 0, p.per_x);
-        const double dB2 = dfd64(Bf[c], i, j, p.nx, p.ny, 1, p.per_y);
+        const double dB1 = dfd64(q, 3 + c, i, j, p.nx, p.ny, 0, p.per_x);
+        const double dB2 = dfd64(q, 3 + c, i, j, p.nx, p.ny, 1, p.per_y);
         const double A1 = U1 * B[c] - B[0] * U[c], A2 = U2 * B[c] - B[1] * U[c];
         // Eq. 42_C (theta21, theta12 on curvilinear grids)
         const double lc1 = q.eta * (H - h2 / h1) * dB1 + q.eta * h1 * H * (t11 + t21) * B[c];
