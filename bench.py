@@ -589,8 +589,9 @@ def extra_numbers(args) -> dict:
         spec = prob.lattice_spec(cs2)
         row = {st: lattice_rate(spec, st, 2000 if n == 512 else 400) for st in ("fp32", "fp16", "bf16")}
         row["fp16_over_fp32"] = round(row["fp16"]["mlups"] / row["fp32"]["mlups"], 3)
-        # one population buffer updated in place (goc_exec.streaming = 1), FP32
+        # one population buffer updated in place (goc_exec.streaming = 1)
         row["fp32_in_place"] = lattice_rate(spec, "fp32", 2000 if n == 512 else 400, streaming="in_place")
+        row["fp16_in_place"] = lattice_rate(spec, "fp16", 2000 if n == 512 else 400, streaming="in_place")
         storage[f"cavity_{n}x{n}" + ("" if n == 512 else f"_Re{re:g}")] = row
     out["storage"] = storage
     prob = gi.hartmann_channel()
@@ -1061,7 +1062,7 @@ def main():
                     help="tanh map on both axes (the benchmark cavity), the cavity on a logarithmic-spiral node "
                          "table, or Taylor-Couette flow on the annular sector")
     ap.add_argument("--streaming", default="two_buffers", choices=["two_buffers", "in_place"],
-                    help="in_place: one population buffer updated in place (FP32, straight grids)")
+                    help="in_place: one population buffer updated in place (straight grids)")
     ap.add_argument("--scheme", default="goc", choices=["goc", "goc_srt", "goc_raw"],
                     help="collision: central-moment MRT (the benchmark), SRT (Appendix F), raw-moment MRT (Appendix D)")
     ap.add_argument("--mie", action="store_true", help="couple the MIE (Appendix G)")

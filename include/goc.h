@@ -190,9 +190,10 @@ typedef struct {
                                pass and a collision pass.  56 B per node resident instead of
                                88 B, 156 B moved per step instead of 88 B; the populations
                                are bitwise those of streaming 0 (the MIE populations follow
-                               the same layouts: 40 B resident instead of 80 B).  FP32
-                               storage, scheme 0, per-axis maps (else GOC_EUNSUPPORTED); not
-                               in batches or
+                               the same layouts: 40 B resident instead of 80 B; 16-bit
+                               storage: 34 B instead of 44 B, the fields buffer staying FP32).
+                               Scheme 0, per-axis maps (else GOC_EUNSUPPORTED); not in
+                               batches or
                                slabs; goc_get_state / goc_set_state keep the layout, so a
                                state moves only between lattices of the same streaming. */
 } goc_exec;

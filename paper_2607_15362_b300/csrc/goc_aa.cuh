@@ -52,15 +52,16 @@ enum { AA_C = 0, AA_S = 1, AA_T = 2 };
 // and E by row, along S and N by column) instead of being summed here.  CH:
 // a node may lie on the lattice's edge (links leave it); false for the nodes
 // of blocks whose nodes all have their eight neighbours inside.
-template <int L, bool WS, bool CH = true> struct SrcAA {
+template <class S, int L, bool WS, bool CH = true> struct SrcAA {
     static_assert(L == AA_C || L == AA_S || L == AA_T, "layout");
     static constexpr bool kWallSums = WS;
     static constexpr bool kInPlace = true;
-    const float *f, *F, *g;
+    const S *f, *F, *g;
     long long plane;
     int pitch, nx, ny, per_x, per_y;
     const float *wsum;
     int wn;
+    float sf, sF, sg;   // storage scales (1 for FP32)
     // the node a population of node (i, j) along link a streams to, and
     // whether it lies inside the lattice (periodic axes wrap)
     __device__ __forceinline__ bool dest(int a, int i, int j, int &ti, int &tj) const {
@@ -77,19 +78,22 @@ template <int L, bool WS, bool CH = true> struct SrcAA {
         return in;
     }
     // the post-collision population of node (i, j) along link a
-    __device__ __forceinline__ float fv(int a, int i, int j) const {
+    __device__ __forceinline__ long long fslot(int a, int i, int j) const {
         const long long idx = (long long)j * pitch + i;
         if constexpr (L == AA_C) {
-            return f[a * plane + idx];
+            return a * plane + idx;
         } else if constexpr (L == AA_S) {
-            return f[opp(a) * plane + idx];
+            return opp(a) * plane + idx;
         } else {
             int ti, tj;
-            if (dest(a, i, j, ti, tj)) return f[a * plane + (long long)tj * pitch + ti];
-            return f[opp(a) * plane + idx];
+            if (dest(a, i, j, ti, tj)) return a * plane + (long long)tj * pitch + ti;
+            return opp(a) * plane + idx;
         }
     }
-    __device__ __forceinline__ float Fv(int c, int i, int j) const { return F[c * plane + (long long)j * pitch + i]; }
+    __device__ __forceinline__ float fv(int a, int i, int j) const { return scl<S>(Store<S>::ld(f + fslot(a, i, j)), sf); }
+    __device__ __forceinline__ float Fv(int c, int i, int j) const {
+        return scl<S>(Store<S>::ld(F + c * plane + (long long)j * pitch + i), sF);
+    }
     // the post-collision MIE population k = 5 c + a of node (i, j) (D2Q5
     // links g1, g2; the same two layouts)
     __device__ __forceinline__ bool gdest(int a, int i, int j, int &ti, int &tj) const {
@@ -105,19 +109,20 @@ template <int L, bool WS, bool CH = true> struct SrcAA {
         }
         return in;
     }
-    __device__ __forceinline__ float gv(int k, int i, int j) const {
+    __device__ __forceinline__ long long gslot(int k, int i, int j) const {
         const int c = k / 5, a = k - 5 * c;
         const long long idx = (long long)j * pitch + i;
         if constexpr (L == AA_C) {
-            return g[k * plane + idx];
+            return k * plane + idx;
         } else if constexpr (L == AA_S) {
-            return g[(5 * c + gopp(a)) * plane + idx];
+            return (5 * c + gopp(a)) * plane + idx;
         } else {
             int ti, tj;
-            if (gdest(a, i, j, ti, tj)) return g[k * plane + (long long)tj * pitch + ti];
-            return g[(5 * c + gopp(a)) * plane + idx];
+            if (gdest(a, i, j, ti, tj)) return k * plane + (long long)tj * pitch + ti;
+            return (5 * c + gopp(a)) * plane + idx;
         }
     }
+    __device__ __forceinline__ float gv(int k, int i, int j) const { return scl<S>(Store<S>::ld(g + gslot(k, i, j)), sg); }
     __device__ __forceinline__ float wall_sum(int i, int j) const {
         if (j == 0) return wsum[SIDE_S * wn + i];
         if (j == ny - 1) return wsum[SIDE_N * wn + i];
@@ -128,8 +133,8 @@ template <int L, bool WS, bool CH = true> struct SrcAA {
 
 // Where a step writes the new population of node (i, j) along link a: AA_T
 // after reading AA_S, else AA_S.
-template <int L, bool WS, bool CH>
-__device__ __forceinline__ long long out_slot(const SrcAA<L, WS, CH> &s, const StepParams &p, int a, int i, int j,
+template <class S, int L, bool WS, bool CH>
+__device__ __forceinline__ long long out_slot(const SrcAA<S, L, WS, CH> &s, const StepParams &p, int a, int i, int j,
                                               long long idx) {
     if constexpr (L == AA_S) {
         int ti, tj;
@@ -138,8 +143,8 @@ __device__ __forceinline__ long long out_slot(const SrcAA<L, WS, CH> &s, const S
     return opp(a) * p.plane + idx;
 }
 
-template <int L, bool WS, bool CH>
-__device__ __forceinline__ long long out_slot_g(const SrcAA<L, WS, CH> &s, const StepParams &p, int c, int a, int i,
+template <class S, int L, bool WS, bool CH>
+__device__ __forceinline__ long long out_slot_g(const SrcAA<S, L, WS, CH> &s, const StepParams &p, int c, int a, int i,
                                                 int j, long long idx) {
     if constexpr (L == AA_S) {
         int ti, tj;
@@ -148,11 +153,35 @@ __device__ __forceinline__ long long out_slot_g(const SrcAA<L, WS, CH> &s, const
     return (5 * c + gopp(a)) * p.plane + idx;
 }
 
-template <int L, bool WS, bool CH = true>
-__device__ __forceinline__ SrcAA<L, WS, CH> aa_source(const StepParams &p, const float *wsum, int wn) {
-    return SrcAA<L, WS, CH>{static_cast<const float *>(p.fin), static_cast<const float *>(p.Fin),
-                            static_cast<const float *>(p.gin), p.plane, p.pitch, p.nx, p.ny, p.per_x, p.per_y,
-                            wsum, wn};
+template <class S, int L, bool WS, bool CH = true>
+__device__ __forceinline__ SrcAA<S, L, WS, CH> aa_source(const StepParams &p, const float *wsum, int wn) {
+    return SrcAA<S, L, WS, CH>{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin),
+                               static_cast<const S *>(p.gin), p.plane, p.pitch, p.nx, p.ny, p.per_x, p.per_y,
+                               wsum, wn, p.sf, p.sF, p.sg};
+}
+
+// The offset of the stored population of node (i, j) along D2Q9 link a
+// (k = 5 c + a of the MIE with g5) in layout lay -- the same slots as the
+// sources above, chosen at run time (the reference-row kernels).
+__device__ __forceinline__ long long aa_slot(const StepParams &p, int lay, int a, int i, int j, bool g5 = false,
+                                             int c = 0) {
+    const long long idx = (long long)j * p.pitch + i;
+    const int e1a = g5 ? g1(a) : e1(a), e2a = g5 ? g2(a) : e2(a);
+    const int base = g5 ? 5 * c : 0, ro = g5 ? gopp(a) : opp(a);
+    if (lay == AA_S) return (base + ro) * p.plane + idx;
+    if (lay == AA_T) {
+        int ti = i + e1a, tj = j + e2a;
+        bool in = true;
+        if (ti < 0 || ti >= p.nx) {
+            if (p.per_x) ti = wrapi(ti, p.nx); else in = false;
+        }
+        if (tj < 0 || tj >= p.ny) {
+            if (p.per_y) tj = wrapi(tj, p.ny); else in = false;
+        }
+        if (in) return (base + a) * p.plane + (long long)tj * p.pitch + ti;
+        return (base + ro) * p.plane + idx;
+    }
+    return (base + a) * p.plane + idx;
 }
 
 // whether every node of this block has its eight neighbours inside the
@@ -166,13 +195,15 @@ __device__ __forceinline__ bool aa_block_interior(const StepParams &p) {
 // Fields pass: rho - rho0, U1, U2 of every node into fld ([3][plane]), and
 // the population sum of every wall node into wsum (lattices with a moving
 // wall).  Writes no population.
-template <int L, bool CH>
+template <class S, int L, bool CH>
 __device__ __forceinline__ void aa_fields_node(const StepParams &p, int i, int j, float *fld, float *wsum, int wn) {
-    const SrcAA<L, false, CH> src = aa_source<L, false, CH>(p, nullptr, 0);
+    constexpr bool REF = Store<S>::scaled;   // per-row storage reference (16-bit storage)
+    const SrcAA<S, L, false, CH> src = aa_source<S, L, false, CH>(p, nullptr, 0);
     float h1, h2, ih1, ih2, d[9], drho, U1, U2;
+    const float ur1 = REF ? GOC_U1R(p, j) : 0.f;
     node_metric<0>(p, i, j, h1, h2, ih1, ih2);
-    pull_node<CH, 0, false>(p, src, i, j, h1, h2, d);
-    fields_from<false>(p, d, src.Fv(0, i, j), src.Fv(1, i, j), ih1, ih2, drho, U1, U2);
+    pull_node<CH, 0, REF>(p, src, i, j, h1, h2, d, ur1);
+    fields_from<REF>(p, d, src.Fv(0, i, j), src.Fv(1, i, j), ih1, ih2, drho, U1, U2, ur1);
     const long long idx = (long long)j * p.pitch + i;
     fld[idx] = drho;
     fld[p.plane + idx] = U1;
@@ -190,16 +221,16 @@ __device__ __forceinline__ void aa_fields_node(const StepParams &p, int i, int j
 
 // (6 blocks of 256 threads per SM, 40 registers: at 2048^2 the step took
 // 166 us against 179 us at 4 blocks and 64 registers; 8 blocks spill heavily)
-template <int L>
+template <class S, int L>
 __global__ void __launch_bounds__(NT, 6) aa_fields_kernel(const __grid_constant__ StepParams p, float *fld,
                                                                         float *wsum, int wn) {
     griddep_launch_dependents();
     griddep_wait();
     const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
     if (aa_block_interior(p)) {
-        aa_fields_node<L, false>(p, i, j, fld, wsum, wn);
+        aa_fields_node<S, L, false>(p, i, j, fld, wsum, wn);
     } else if (i < p.nx && j < p.ny) {
-        aa_fields_node<L, true>(p, i, j, fld, wsum, wn);
+        aa_fields_node<S, L, true>(p, i, j, fld, wsum, wn);
     }
 }
 
@@ -220,14 +251,15 @@ __device__ __forceinline__ float aa_field(const StepParams &p, const float *fld,
 // Collision pass: pull, the fields of the node and its neighbours from the
 // fields pass, normal derivatives, collision; the new populations go to the
 // node's slots of the next layout, the force to the node.
-template <int L, bool MHD, bool CH>
+template <class S, int L, bool MHD, bool CH>
 __device__ __forceinline__ void aa_collide_node(const StepParams &p, int i, int j, const float *fld, const float *wsum,
                                                 int wn) {
-    const SrcAA<L, true, CH> src = aa_source<L, true, CH>(p, wsum, wn);
+    constexpr bool REF = Store<S>::scaled;
+    const SrcAA<S, L, true, CH> src = aa_source<S, L, true, CH>(p, wsum, wn);
     float h1, ih1;
-    float h2[1], ih2[1], d[1][9], F1p[1], F2p[1], ur1[1] = {0.f};
+    float h2[1], ih2[1], d[1][9], F1p[1], F2p[1], ur1[1] = {REF ? GOC_U1R(p, j) : 0.f};
     node_metric<0>(p, i, j, h1, h2[0], ih1, ih2[0]);
-    pull_node<CH, 0, false>(p, src, i, j, h1, h2[0], d[0]);
+    pull_node<CH, 0, REF>(p, src, i, j, h1, h2[0], d[0], ur1[0]);
     F1p[0] = src.Fv(0, i, j);
     F2p[0] = src.Fv(1, i, j);
     const long long idx = (long long)j * p.pitch + i, pl = p.plane, pt = p.pitch;
@@ -256,37 +288,43 @@ __device__ __forceinline__ void aa_collide_node(const StepParams &p, int i, int 
     }
     const int jj[1] = {j};
     const bool own[1] = {true};
-    collide<float, MHD, CH, float, false, 0>(p, src, i, jj, own, d, F1p, F2p, h1, ih1, h2, ih2, fl, ur1);
+    collide<S, MHD, CH, float, false, 0>(p, src, i, jj, own, d, F1p, F2p, h1, ih1, h2, ih2, fl, ur1);
 }
 
 // Collision pass: pull, the fields of the node and its neighbours from the
 // fields pass, normal derivatives, collision; the new populations go to the
 // node's slots of the next layout, the force to the node.
-template <int L, bool MHD>
+template <class S, int L, bool MHD>
 __global__ void __launch_bounds__(NT, MHD ? GOC_MIN_BLOCKS_MHD_STRAIGHT : GOC_MIN_BLOCKS)
     aa_collide_kernel(const __grid_constant__ StepParams p, const float *fld, const float *wsum, int wn) {
     griddep_launch_dependents();
     griddep_wait();
+    // stochastic rounding: the step index of the next step, for the launch of
+    // the other parity (as the two-buffer step kernels do)
+    if (Store<S>::scaled && p.sr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        *p.seed_wr = *p.seed_rd + 1u;
     const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
     if (aa_block_interior(p)) {
-        aa_collide_node<L, MHD, false>(p, i, j, fld, wsum, wn);
+        aa_collide_node<S, L, MHD, false>(p, i, j, fld, wsum, wn);
     } else if (i < p.nx && j < p.ny) {
-        aa_collide_node<L, MHD, true>(p, i, j, fld, wsum, wn);
+        aa_collide_node<S, L, MHD, true>(p, i, j, fld, wsum, wn);
     }
 }
 
 // Macroscopic fields of an in-place lattice (as moments_kernel, FP64 output
 // [5][ny][nx]; no MIE).
-template <int L, bool MHD>
+template <class S, int L, bool MHD>
 __global__ void aa_moments_kernel(const StepParams p, double *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= p.nx || j >= p.ny) return;
-    const SrcAA<L, false> src = aa_source<L, false>(p, nullptr, 0);
+    constexpr bool REF = Store<S>::scaled;
+    const SrcAA<S, L, false> src = aa_source<S, L, false>(p, nullptr, 0);
     float h1, h2, ih1, ih2, d[9], drho, U1, U2;
+    const float ur1 = REF ? GOC_U1R(p, j) : 0.f;
     node_metric<0>(p, i, j, h1, h2, ih1, ih2);
-    pull_node<true, 0, false>(p, src, i, j, h1, h2, d);
-    fields_from<false>(p, d, src.Fv(0, i, j), src.Fv(1, i, j), ih1, ih2, drho, U1, U2);
+    pull_node<true, 0, REF>(p, src, i, j, h1, h2, d, ur1);
+    fields_from<REF>(p, d, src.Fv(0, i, j), src.Fv(1, i, j), ih1, ih2, drho, U1, U2, ur1);
     const long long N = (long long)p.nx * p.ny, n = (long long)j * p.nx + i;
     out[n] = (double)p.rho0 + (double)drho;
     out[N + n] = U1;
@@ -294,11 +332,11 @@ __global__ void aa_moments_kernel(const StepParams p, double *out) {
     double B1 = 0.0, B2 = 0.0;
     if constexpr (MHD) {   // as moments_kernel on straight grids
         float gd[2][5];
-        for (int c = 0; c < 2; c++) pull_mie<true, 0, false>(p, src, i, j, h1, h2, c, gd[c]);
+        for (int c = 0; c < 2; c++) pull_mie<true, 0, REF>(p, src, i, j, h1, h2, c, gd[c]);
         const float s0 = (gd[0][0] + gd[0][1] + gd[0][2] + gd[0][3] + gd[0][4]) / (h1 * h2);
         const float s1 = (gd[1][0] + gd[1][1] + gd[1][2] + gd[1][3] + gd[1][4]) / (h1 * h2);
-        B1 = (double)bref<false>(p, 0, j) + (double)s0;
-        B2 = (double)bref<false>(p, 1, j) + (double)s1;
+        B1 = (double)bref<REF>(p, 0, j) + (double)s0;
+        B2 = (double)bref<REF>(p, 1, j) + (double)s1;
     }
     out[3 * N + n] = B1;
     out[4 * N + n] = B2;

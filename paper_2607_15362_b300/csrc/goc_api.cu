@@ -159,7 +159,11 @@ goc_status launch_one(goc_lattice *L, float *uout) {
     p.nopull = L->fresh ? 1 : 0;
     goc_status st;
     if (L->aa) {
-        st = launch_aa_step(L, p);
+        switch (L->storage) {
+            case GOC_FP16_DEV: st = launch_aa_step_t<__half>(L, p); break;
+            case GOC_BF16_DEV: st = launch_aa_step_t<__nv_bfloat16>(L, p); break;
+            default: st = launch_aa_step_t<float>(L, p); break;
+        }
     } else {
         switch (L->storage) {
             case GOC_FP16_DEV: st = launch_step_t<__half>(L, p); break;
@@ -591,10 +595,11 @@ goc_status ref_refresh(goc_lattice *L) {
     const double rho0 = L->flow.rho0, csm2 = L->csm2;
     const int pre = L->fresh ? 1 : 0;
     const bool m = L->mhd.enabled;
-#define GOC_REF_LAUNCH(S, MHD)                                                                           \
-    do {                                                                                                 \
-        ref_rows_kernel<S, MHD><<<L->ny, 256, 0, L->stream>>>(p, next, pre);                              \
-        ref_apply_kernel<S, MHD><<<ag, 128, 0, L->stream>>>(p, h1, t1, h2, t2, next, rho0, csm2, pre, salt); \
+    const int lay = L->aa && !L->fresh ? (L->cur ? AA_S : AA_T) : AA_C;   // where the populations sit
+#define GOC_REF_LAUNCH(S, MHD)                                                                                 \
+    do {                                                                                                       \
+        ref_rows_kernel<S, MHD><<<L->ny, 256, 0, L->stream>>>(p, next, pre, lay);                               \
+        ref_apply_kernel<S, MHD><<<ag, 128, 0, L->stream>>>(p, h1, t1, h2, t2, next, rho0, csm2, pre, salt, lay); \
     } while (0)
     if (L->storage == GOC_FP16_DEV) {
         if (m) GOC_REF_LAUNCH(__half, true);
@@ -731,7 +736,13 @@ goc_status moments_to_device(goc_lattice *L) {
     }
     StepParams p = params_for(L, L->cur, nullptr);
     p.nopull = L->fresh ? 1 : 0;
-    if (L->aa) return launch_aa_moments(L, p, L->mom);
+    if (L->aa) {
+        switch (L->storage) {
+            case GOC_FP16_DEV: return launch_aa_moments_t<__half>(L, p, L->mom);
+            case GOC_BF16_DEV: return launch_aa_moments_t<__nv_bfloat16>(L, p, L->mom);
+            default: return launch_aa_moments_t<float>(L, p, L->mom);
+        }
+    }
     dim3 grid((L->nx + 127) / 128, L->ny), block(128);
     const bool m = L->mhd.enabled;
     switch (L->storage) {
@@ -860,8 +871,8 @@ static goc_status create_impl(const goc_grid *grid, const goc_map *map, const go
         return fail(GOC_EINVAL, "unknown streaming %d", exec->streaming);
     if (exec && exec->streaming == 1) {
         const bool straight = map->kind[0] != GOC_MAP_ANNULUS && map->kind[0] != GOC_MAP_TABLE;
-        if (exec->storage != GOC_FP32 || exec->scheme != 0 || !straight)
-            return fail(GOC_EUNSUPPORTED, "in-place streaming needs FP32 storage, scheme 0 and a straight grid");
+        if (exec->scheme != 0 || !straight)
+            return fail(GOC_EUNSUPPORTED, "in-place streaming needs scheme 0 and a straight grid");
     }
     goc_lattice *L = new (std::nothrow) goc_lattice();
     if (!L) return fail(GOC_ENOMEM, "host allocation failed");
@@ -1369,8 +1380,7 @@ double goc_bytes_per_node(const goc_lattice *L) {
     if (L->scheme == 1) return 2.0 * 9.0 * es;          // populations only, read + write
     if (L->aa)   // fields pass: populations, force read, fields written; collision pass: populations, force
                  // and fields read, populations and force written
-        return 4.0 * (11.0 + 3.0 + 11.0 + 3.0 + 11.0) + (L->mhd.enabled ? 2.0 * 10.0 * 4.0 : 0.0) +
-               4.0 * 7.0 / L->ny + 4.0 * 7.0 / L->nx;
+        return 33.0 * es + 24.0 + (L->mhd.enabled ? 2.0 * 10.0 * es : 0.0) + 4.0 * 7.0 / L->ny + 4.0 * 7.0 / L->nx;
     double b = 2.0 * (9.0 + 2.0) * es;                  // populations + stored force, read + write
     if (L->mhd.enabled) b += 2.0 * 10.0 * es;           // MIE populations
     if (L->sp.curv == 2) return b + 4.0 * 10.0;         // node-table metric: 10 FP32 values per node

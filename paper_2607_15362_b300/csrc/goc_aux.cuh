@@ -2,6 +2,7 @@
 // FP64 reductions.
 #pragma once
 
+#include "goc_aa.cuh"
 #include "goc_device.cuh"
 #include "goc_step.cuh"
 
@@ -440,31 +441,33 @@ __global__ void ref_tables_kernel(const double *h2, const double *t2, int ny, in
 // MIE zeroth moment h1 h2 (B - Bref) = sum g (Y = 0 on straight grids); the
 // initial pre-collision state (pre = 1) gives U1 by Eq.
 // GOChydrodynamicfields, with + (F1 - F1_rest)/2.
+// lay: where the populations sit (AA_C for two-buffer lattices; an in-place
+// lattice's layout, goc_aa.cuh)
 template <class S, bool MHD>
-__global__ void ref_rows_kernel(const StepParams p, double *out, int pre) {
+__global__ void ref_rows_kernel(const StepParams p, double *out, int pre, int lay) {
     static_assert(Store<S>::scaled, "the per-row reference belongs to 16-bit storage");
     __shared__ double red[3][256];
     const int j = blockIdx.x, t = threadIdx.x;
-    const SrcGlobal<S> src{static_cast<const S *>(p.fin), static_cast<const S *>(p.Fin), static_cast<const S *>(p.gin),
-                           p.plane, p.pitch, p.sf, p.sF, p.sg};
+    const S *fb = static_cast<const S *>(p.fin), *gb = static_cast<const S *>(p.gin);
     double acc[3] = {0.0, 0.0, 0.0};
     const float fs = pre ? 0.5f : -0.5f;
     for (int i = t; i < p.nx; i += 256) {
         float h1, h2, ih1, ih2, d[9];
         node_metric<0>(p, i, j, h1, h2, ih1, ih2);
 #pragma unroll
-        for (int a = 0; a < 9; a++) d[a] = src.fv(a, i, j);
+        for (int a = 0; a < 9; a++) d[a] = scl<S>(Store<S>::ld(fb + aa_slot(p, lay, a, i, j)), p.sf);
         float k00 = 0.f;
 #pragma unroll
         for (int a = 0; a < 9; a++) k00 += d[a];
         const float k10 = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
         const float rho = p.rho0 + k00 * (ih1 * ih2);
-        const float U1 = (k10 + fmaf(fs, src.Fv(0, i, j), 2.f * GOC_U1R(p, j))) / rho * ih2;
+        const float F1 = scl<S>(Store<S>::ld(static_cast<const S *>(p.Fin) + (long long)j * p.pitch + i), p.sF);
+        const float U1 = (k10 + fmaf(fs, F1, 2.f * GOC_U1R(p, j))) / rho * ih2;
         acc[0] += (double)U1;
         if constexpr (MHD) {
             for (int c = 0; c < 2; c++) {
                 float sum = 0.f;
-                for (int a = 0; a < 5; a++) sum += src.gv(c * 5 + a, i, j);
+                for (int a = 0; a < 5; a++) sum += scl<S>(Store<S>::ld(gb + aa_slot(p, lay, a, i, j, true, c)), p.sg);
                 acc[1 + c] += (double)GOC_BROW(p, c, j) + (double)(sum * (ih1 * ih2));
             }
         }
@@ -491,7 +494,7 @@ __global__ void ref_rows_kernel(const StepParams p, double *out, int pre) {
 template <class S, bool MHD>
 __global__ void ref_apply_kernel(const StepParams p, const double *h1d, const double *t1d, const double *h2d,
                                  const double *t2d, const double *refn, double rho0, double csm2, int pre,
-                                 unsigned salt) {
+                                 unsigned salt, int lay) {
     static_assert(Store<S>::scaled, "the per-row reference belongs to 16-bit storage");
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= p.nx || j >= p.ny) return;
@@ -501,7 +504,7 @@ __global__ void ref_apply_kernel(const StepParams p, const double *h1d, const do
     S *f = static_cast<S *>(const_cast<void *>(p.fin));
     const double du = (double)GOC_U1R(p, j) - (double)ref_u1r(h2d, refn, rho0, j);
     if (du != 0.0) {
-        S *f1 = f + p.plane + idx, *f3 = f + 3 * p.plane + idx;
+        S *f1 = f + aa_slot(p, lay, 1, i, j), *f3 = f + aa_slot(p, lay, 3, i, j);
         const double v1 = (double)Store<S>::ld(f1) * p.sf + du, v3 = (double)Store<S>::ld(f3) * p.sf - du;
         put<S>(f1, (float)(v1 * p.isf), sr, rng);
         put<S>(f3, (float)(v3 * p.isf), sr, rng);
@@ -516,7 +519,7 @@ __global__ void ref_apply_kernel(const StepParams p, const double *h1d, const do
             for (int a = 0; a < 5; a++) {
                 const double W = a == 0 ? 1.0 - 2.0 * csm2 : 0.5 * csm2;
                 const double shift = W * H * dB + sgn * 0.5 * (g1(a) * M1 + g2(a) * M2);
-                S *ga = g + (c * 5 + a) * p.plane + idx;
+                S *ga = g + aa_slot(p, lay, a, i, j, true, c);
                 put<S>(ga, (float)(((double)Store<S>::ld(ga) * p.sg + shift) * p.isg), sr, rng);
             }
         }

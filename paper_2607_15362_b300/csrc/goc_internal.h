@@ -130,14 +130,16 @@ template <class S> goc_status launch_step_t(goc_lattice *L, const StepParams &p)
 template <class S> int batch_grid_t(int mhd, int geom, int *stage_bytes);
 template <class S>
 cudaError_t batch_launch_t(int mhd, int geom, dim3 gd, dim3 bd, size_t smem, cudaStream_t st, const goc::BatchArgs &a);
+// in-place lattices (goc_kernels_<type>.cu): one step (fields pass, then
+// collision pass), and the macroscopic fields into out ([5][ny][nx] FP64)
+template <class S> goc_status launch_aa_step_t(goc_lattice *L, const StepParams &p);
+template <class S> goc_status launch_aa_moments_t(goc_lattice *L, const StepParams &p, double *out);
 #define GOC_DECLARE_LAUNCHERS(S)                                                                         \
+    extern template goc_status launch_aa_step_t<S>(goc_lattice *, const StepParams &);                  \
+    extern template goc_status launch_aa_moments_t<S>(goc_lattice *, const StepParams &, double *);     \
     extern template goc_status launch_step_t<S>(goc_lattice *, const StepParams &);                     \
     extern template int batch_grid_t<S>(int, int, int *);                                                \
     extern template cudaError_t batch_launch_t<S>(int, int, dim3, dim3, size_t, cudaStream_t, const goc::BatchArgs &);
 GOC_DECLARE_LAUNCHERS(float)
-// in-place lattices (FP32; goc_kernels_f32.cu): one step (fields pass, then
-// collision pass), and the macroscopic fields into out ([5][ny][nx] FP64)
-goc_status launch_aa_step(goc_lattice *L, const StepParams &p);
-goc_status launch_aa_moments(goc_lattice *L, const StepParams &p, double *out);
 GOC_DECLARE_LAUNCHERS(__half)
 GOC_DECLARE_LAUNCHERS(__nv_bfloat16)

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 
+#include "goc_aa.cuh"
 #include "goc_internal.h"
 #include "goc_lean.cuh"
 #include "goc_std.cuh"
@@ -211,7 +212,48 @@ cudaError_t batch_launch_t(int mhd, int geom, dim3 gd, dim3 bd, size_t smem, cud
     }
 }
 
+// In-place lattices (goc_aa.cuh): one step, a fields pass and a collision
+// pass in the kernels of the layout the populations are in (f^0; the link
+// reversed at the node, after odd steps; at the destination, after even ones).
+template <class S, int LAY>
+goc_status launch_aa_layout(goc_lattice *L, const StepParams &p) {
+    const dim3 grid((L->nx + TX - 1) / TX, (L->ny + TY - 1) / TY), block(TX, TY);
+    const bool pdl = L->cfg_pdl != 0;
+    const float *fld = L->aa_fld, *wsum = L->aa_wsum;
+    CU(launch_pdl(pdl, aa_fields_kernel<S, LAY>, grid, block, 0, L->stream, p, L->aa_fld, L->aa_wsum, L->aa_wn));
+    if (L->mhd.enabled)
+        CU(launch_pdl(pdl, aa_collide_kernel<S, LAY, true>, grid, block, 0, L->stream, p, fld, wsum, L->aa_wn));
+    else
+        CU(launch_pdl(pdl, aa_collide_kernel<S, LAY, false>, grid, block, 0, L->stream, p, fld, wsum, L->aa_wn));
+    return GOC_OK;
+}
+
+template <class S>
+goc_status launch_aa_step_t(goc_lattice *L, const StepParams &p) {
+    if (L->fresh) return launch_aa_layout<S, AA_C>(L, p);
+    return L->cur ? launch_aa_layout<S, AA_S>(L, p) : launch_aa_layout<S, AA_T>(L, p);
+}
+
+template <class S>
+goc_status launch_aa_moments_t(goc_lattice *L, const StepParams &p, double *out) {
+    const dim3 grid((L->nx + 127) / 128, L->ny), block(128);
+    const int lay = L->fresh ? AA_C : (L->cur ? AA_S : AA_T);
+    if (L->mhd.enabled) {
+        if (lay == AA_C) aa_moments_kernel<S, AA_C, true><<<grid, block, 0, L->stream>>>(p, out);
+        else if (lay == AA_S) aa_moments_kernel<S, AA_S, true><<<grid, block, 0, L->stream>>>(p, out);
+        else aa_moments_kernel<S, AA_T, true><<<grid, block, 0, L->stream>>>(p, out);
+    } else {
+        if (lay == AA_C) aa_moments_kernel<S, AA_C, false><<<grid, block, 0, L->stream>>>(p, out);
+        else if (lay == AA_S) aa_moments_kernel<S, AA_S, false><<<grid, block, 0, L->stream>>>(p, out);
+        else aa_moments_kernel<S, AA_T, false><<<grid, block, 0, L->stream>>>(p, out);
+    }
+    CU(cudaGetLastError());
+    return GOC_OK;
+}
+
 #define GOC_DEFINE_LAUNCHERS(S)                                                                   \
+    template goc_status launch_aa_step_t<S>(goc_lattice *, const StepParams &);                  \
+    template goc_status launch_aa_moments_t<S>(goc_lattice *, const StepParams &, double *);     \
     template goc_status launch_step_t<S>(goc_lattice *, const StepParams &);                     \
     template int batch_grid_t<S>(int, int, int *);                                                \
     template cudaError_t batch_launch_t<S>(int, int, dim3, dim3, size_t, cudaStream_t, const BatchArgs &);

@@ -773,7 +773,15 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
                 float gt[5];
 #pragma unroll
                 for (int a = 0; a < 5; a++) gt[a] = c ? GT[a].y : GT[a].x;
-                if constexpr (Store<S>::scaled) {   // pairs through one conversion each
+                if constexpr (Store<S>::scaled && InPlaceSrc<Src>::value) {   // in place: slots of the layout
+                    const float is = p.isg;
+                    S *gs[5];
+#pragma unroll
+                    for (int a = 0; a < 5; a++) gs[a] = gout + out_slot_g(src, p, c, a, i, j[0], idx[0]);
+                    put2<S>(gs[0], gs[1], gt[0] * is, gt[1] * is, sr, rng[0]);
+                    put2<S>(gs[2], gs[3], gt[2] * is, gt[3] * is, sr, rng[0]);
+                    put2<S>(gs[4], static_cast<S *>(nullptr), gt[4] * is, 0.f, sr, rng[0]);
+                } else if constexpr (Store<S>::scaled) {   // pairs through one conversion each
                     const float is = p.isg;
                     const long long pl = p.plane;
                     put2<S>(go, go + pl, gt[0] * is, gt[1] * is, sr, rng[0]);
@@ -1127,7 +1135,18 @@ __device__ __forceinline__ void collide(const StepParams &p, const Src &src, int
 #pragma unroll
     for (int q = 0; q < R; q++) {
         if (!own[q]) continue;
-        if constexpr (Store<S>::scaled) {   // pairs through one conversion each
+        if constexpr (Store<S>::scaled && InPlaceSrc<Src>::value) {   // in place: slots of the layout
+            S *Fo = Fout + idx[q];
+            const float is = p.isf;
+            S *fs[9];
+#pragma unroll
+            for (int a = 0; a < 9; a++) fs[a] = fout + out_slot(src, p, a, i, j[q], idx[q]);
+#pragma unroll
+            for (int a = 0; a < 8; a += 2)
+                put2<S>(fs[a], fs[a + 1], lane(o[a], q) * is, lane(o[a + 1], q) * is, sr, rng[q]);
+            put2<S>(fs[8], Fo, lane(o[8], q) * is, lane(F1dev, q) * p.isF, sr, rng[q]);
+            put2<S>(Fo + p.plane, static_cast<S *>(nullptr), lane(F2dev, q) * p.isF, 0.f, sr, rng[q]);
+        } else if constexpr (Store<S>::scaled) {   // pairs through one conversion each
             S *fo = fout + idx[q], *Fo = Fout + idx[q];
             const long long pl = p.plane;
             const float is = p.isf;

@@ -123,8 +123,8 @@ class Lattice:
         (uniform maps, spec["gi"] = 0, no MIE).  reference_every: steps between
         refreshes of the per-row storage reference of 16-bit storage on
         straight grids (0: the library default, < 0: never).  streaming
-        "in_place": one population buffer updated in place (FP32, straight
-        grids; goc_exec.streaming)."""
+        "in_place": one population buffer updated in place (straight grids;
+        goc_exec.streaming)."""
         self.spec = spec
         self.nx, self.ny = int(spec["nx"]), int(spec["ny"])
         self.storage = storage
