@@ -187,15 +187,17 @@ typedef struct {
                                1 = one buffer updated in place: two access patterns alternate
                                (the post-collision populations kept at their node with the link
                                reversed, then at the node they stream to), each step a fields
-                               pass and a collision pass.  56 B per node resident instead of
-                               88 B, 156 B moved per step instead of 88 B; the populations
-                               are bitwise those of streaming 0 (the MIE populations follow
-                               the same layouts: 40 B resident instead of 80 B; 16-bit
-                               storage: 34 B instead of 44 B, the fields buffer staying FP32).
-                               Scheme 0, per-axis maps (else GOC_EUNSUPPORTED); not in
-                               batches or
-                               slabs; goc_get_state / goc_set_state keep the layout, so a
-                               state moves only between lattices of the same streaming. */
+                               pass and a collision pass.  FP32: 56 B per node resident instead
+                               of 88 B, 156 B moved per step instead of 88 B, the populations
+                               bitwise those of streaming 0; the MIE populations follow the
+                               same layouts (40 B resident instead of 80 B; the fields agree to
+                               rounding: the wall nodes' multiply-adds may fuse differently);
+                               16-bit storage: 34 B instead of 44 B, the fields buffer staying
+                               FP32, stochastic rounding from the same random streams (results
+                               within the storage's rounding of streaming 0).  Scheme 0,
+                               per-axis maps (else GOC_EUNSUPPORTED); not in batches or slabs;
+                               goc_get_state / goc_set_state keep the layout, so a state moves
+                               only between lattices of the same streaming. */
 } goc_exec;
 
 /* ---- lifecycle --------------------------------------------------------- */
